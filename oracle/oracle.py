@@ -1,0 +1,222 @@
+"""ctypes binding of the plain C FP64 oracle (emu_oracle.c).
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, the package entry point's
+smoke check and the benchmark's CPU-baseline leg may import this module.  The
+product library never loads it, and it never loads the product library.
+
+The oracle keeps particles as an array of structs with full complex 3x3
+matrices (numpy structured dtype ``PARTICLE``) and the grid as one struct per
+cell (``CELL``).  Every function below forwards to the C routine of the same
+name without touching the arithmetic; see emu_oracle.c for the paper
+passages each one follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "emu_oracle.c"
+_LIB = _HERE / "liboracle.so"
+
+PARTICLE = np.dtype(
+    [
+        ("z", "f8"),
+        ("omega", "f8", (3,)),
+        ("N", "f8"),
+        ("Nbar", "f8"),
+        ("rho", "c16", (3, 3)),
+        ("rhobar", "c16", (3, 3)),
+    ],
+    align=True,
+)
+CELL = np.dtype(
+    [
+        ("n", "c16", (3, 3)),
+        ("nbar", "c16", (3, 3)),
+        ("f", "c16", (3, 3, 3)),
+        ("fbar", "c16", (3, 3, 3)),
+    ],
+    align=True,
+)
+
+
+class OrConfig(ctypes.Structure):
+    _fields_ = [
+        ("nz", ctypes.c_int32),
+        ("ndir", ctypes.c_int32),
+        ("Lz", ctypes.c_double),
+        ("area", ctypes.c_double),
+        ("kappa", ctypes.c_double),
+        ("c_light", ctypes.c_double),
+        ("cfl_adv", ctypes.c_double),
+        ("cfl_flavor", ctypes.c_double),
+    ]
+
+
+def build(force: bool = False) -> Path:
+    """Compile emu_oracle.c with gcc (-O2, no fast-math) into liboracle.so."""
+    if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = _LIB.with_suffix(f".so.tmp{os.getpid()}")
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
+             "-o", str(tmp), str(_SRC), "-lm"]
+        )
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(str(build()))
+        vp, i64, dbl, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64
+        cfgp = ctypes.POINTER(OrConfig)
+        L.or_splitmix64.argtypes = [u64, u64]; L.or_splitmix64.restype = u64
+        L.or_uniform.argtypes = [u64, i64, ctypes.c_int]; L.or_uniform.restype = dbl
+        L.or_fibonacci_direction.argtypes = [ctypes.c_int, ctypes.c_int, vp]; L.or_fibonacci_direction.restype = None
+        L.or_wrap.argtypes = [cfgp, dbl]; L.or_wrap.restype = dbl
+        L.or_shape.argtypes = [cfgp, dbl, vp, vp]; L.or_shape.restype = None
+        L.or_init.argtypes = [cfgp, vp, vp, vp, vp, vp, dbl, u64, vp]; L.or_init.restype = ctypes.c_int
+        L.or_deposit.argtypes = [cfgp, vp, i64, vp]; L.or_deposit.restype = None
+        L.or_hamiltonian.argtypes = [cfgp, vp, vp, vp]; L.or_hamiltonian.restype = None
+        L.or_hamiltonian_bar.argtypes = [vp, vp]; L.or_hamiltonian_bar.restype = None
+        L.or_commutator_rhs.argtypes = [vp, vp, vp]; L.or_commutator_rhs.restype = None
+        L.or_rhs.argtypes = [cfgp, vp, i64, vp, vp, vp]; L.or_rhs.restype = None
+        L.or_rk4_step.argtypes = [cfgp, vp, i64, dbl]; L.or_rk4_step.restype = ctypes.c_int
+        L.or_run.argtypes = [cfgp, vp, i64, dbl, i64]; L.or_run.restype = ctypes.c_int
+        L.or_timestep.argtypes = [cfgp, vp]; L.or_timestep.restype = dbl
+        L.or_eln_matrix.argtypes = [vp, i64, vp]; L.or_eln_matrix.restype = None
+        L.or_domain_averages.argtypes = [cfgp, vp, vp, vp]; L.or_domain_averages.restype = None
+        for name in ("or_sizeof_particle", "or_sizeof_cell", "or_sizeof_config"):
+            getattr(L, name).restype = ctypes.c_int32
+        assert L.or_sizeof_particle() == PARTICLE.itemsize, "particle struct mismatch"
+        assert L.or_sizeof_cell() == CELL.itemsize, "cell struct mismatch"
+        assert L.or_sizeof_config() == ctypes.sizeof(OrConfig), "config struct mismatch"
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def config(nz, ndir, Lz, kappa, c_light, cfl_adv=0.4, cfl_flavor=0.4, area=1.0) -> OrConfig:
+    return OrConfig(int(nz), int(ndir), float(Lz), float(area), float(kappa), float(c_light),
+                    float(cfl_adv), float(cfl_flavor))
+
+
+def splitmix64(seed: int, n: int) -> int:
+    return int(lib().or_splitmix64(seed, n))
+
+
+def uniform(seed: int, p: int, k: int) -> float:
+    return float(lib().or_uniform(seed, p, k))
+
+
+def fibonacci_direction(d: int, M: int) -> np.ndarray:
+    out = np.zeros(3)
+    lib().or_fibonacci_direction(d, M, _ptr(out))
+    return out
+
+
+def shape(cfg: OrConfig, z: float):
+    cells = np.zeros(3, np.int32)
+    w = np.zeros(3)
+    lib().or_shape(ctypes.byref(cfg), float(z), _ptr(cells), _ptr(w))
+    return cells, w
+
+
+def init(cfg: OrConfig, n_nu, n_nubar, f_nu, f_nubar, alpha=1e-6, seed=0, dirs=None):
+    """Particles of Eq. 8/9 (one per direction per cell), numbered p = d*nz + j0."""
+    nz, M = cfg.nz, cfg.ndir
+    n_nu = np.ascontiguousarray(np.broadcast_to(np.asarray(n_nu, float), (nz,)))
+    n_nubar = np.ascontiguousarray(np.broadcast_to(np.asarray(n_nubar, float), (nz,)))
+    f_nu = np.ascontiguousarray(np.broadcast_to(np.asarray(f_nu, float), (nz, 3)))
+    f_nubar = np.ascontiguousarray(np.broadcast_to(np.asarray(f_nubar, float), (nz, 3)))
+    parts = np.zeros(nz * M, PARTICLE)
+    dptr = None
+    if dirs is not None:
+        dirs = np.ascontiguousarray(np.asarray(dirs, float).reshape(M, 3))
+        dptr = _ptr(dirs)
+    rc = lib().or_init(ctypes.byref(cfg), dptr, _ptr(n_nu), _ptr(n_nubar), _ptr(f_nu),
+                       _ptr(f_nubar), float(alpha), int(seed), _ptr(parts))
+    if rc != 0:
+        raise ValueError("negative particle weight: a flux factor exceeds 1/3")
+    return parts
+
+
+def deposit(cfg: OrConfig, parts: np.ndarray) -> np.ndarray:
+    grid = np.zeros(cfg.nz, CELL)
+    lib().or_deposit(ctypes.byref(cfg), _ptr(parts), len(parts), _ptr(grid))
+    return grid
+
+
+def hamiltonian(cfg: OrConfig, grid: np.ndarray, parts: np.ndarray) -> np.ndarray:
+    """H/hbar [1/s] at every particle (Eq. 6 then Eq. 2), shape (P, 3, 3)."""
+    H = np.zeros((len(parts), 3, 3), complex)
+    L = lib()
+    for p in range(len(parts)):
+        L.or_hamiltonian(ctypes.byref(cfg), _ptr(grid), _ptr(parts[p:p + 1]), _ptr(H[p]))
+    return H
+
+
+def hamiltonian_bar(H: np.ndarray) -> np.ndarray:
+    H = np.ascontiguousarray(H, complex)
+    out = np.zeros_like(H)
+    L = lib()
+    for p in range(H.shape[0]):
+        L.or_hamiltonian_bar(_ptr(H[p]), _ptr(out[p]))
+    return out
+
+
+def commutator_rhs(H: np.ndarray, rho: np.ndarray) -> np.ndarray:
+    H = np.ascontiguousarray(H, complex); rho = np.ascontiguousarray(rho, complex)
+    out = np.zeros((3, 3), complex)
+    lib().or_commutator_rhs(_ptr(H), _ptr(rho), _ptr(out))
+    return out
+
+
+def rhs(cfg: OrConfig, parts: np.ndarray):
+    P = len(parts)
+    grid = np.zeros(cfg.nz, CELL)
+    dr = np.zeros((P, 3, 3), complex)
+    db = np.zeros((P, 3, 3), complex)
+    lib().or_rhs(ctypes.byref(cfg), _ptr(parts), P, _ptr(grid), _ptr(dr), _ptr(db))
+    return dr, db, grid
+
+
+def rk4_step(cfg: OrConfig, parts: np.ndarray, dt: float) -> None:
+    if lib().or_rk4_step(ctypes.byref(cfg), _ptr(parts), len(parts), float(dt)) != 0:
+        raise MemoryError("oracle scratch allocation failed")
+
+
+def run(cfg: OrConfig, parts: np.ndarray, dt: float, nsteps: int) -> None:
+    if lib().or_run(ctypes.byref(cfg), _ptr(parts), len(parts), float(dt), int(nsteps)) != 0:
+        raise MemoryError("oracle scratch allocation failed")
+
+
+def timestep(cfg: OrConfig, grid: np.ndarray) -> float:
+    return float(lib().or_timestep(ctypes.byref(cfg), _ptr(grid)))
+
+
+def eln_matrix(parts: np.ndarray) -> np.ndarray:
+    E = np.zeros((3, 3), complex)
+    lib().or_eln_matrix(_ptr(parts), len(parts), _ptr(E))
+    return E
+
+
+def domain_averages(cfg: OrConfig, grid: np.ndarray):
+    """(abs_avgs[4,3,3] = <|n|>, <|nbar|>, <|f_x|>, <|fbar_x|>;  avg[2,3,3] = <n>, <nbar>)."""
+    a = np.zeros((4, 3, 3))
+    m = np.zeros((2, 3, 3), complex)
+    lib().or_domain_averages(ctypes.byref(cfg), _ptr(grid), _ptr(a), _ptr(m))
+    return a, m

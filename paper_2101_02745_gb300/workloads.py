@@ -1,0 +1,143 @@
+"""Seeded synthetic inputs for the particle step (no method arithmetic here).
+
+This module only fixes physical constants and draws the per-cell input
+densities and fluxes of the workloads; both the CUDA library (through its
+binding) and the CPU oracle (in the tests and the CPU baseline) take these
+arrays as inputs.  Particle weights (Eq. 8), directions and the random
+perturbations of the initial flavour state (Eq. 9) are computed by each side
+on its own.
+
+The paper releases no input data: these synthetic workloads stand in for its
+runs (Sec. 3.1, App. B), with the grid sizes, direction counts, densities and
+flux factors its text gives.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+# CODATA 2018 / PDG values.  kappa = sqrt(2) G_F / hbar with G_F in erg cm^3
+# (Eq. 2 carries sqrt(2) G_F (hbar c)^3 with G_F/(hbar c)^3 in GeV^-2).
+GF_GEV2 = 1.1663787e-5          # G_F / (hbar c)^3  [GeV^-2]
+HBARC_GEV_CM = 197.3269804e-3 * 1e-13  # hbar c [GeV cm]
+ERG_PER_GEV = 1.602176634e-3
+HBAR_ERG_S = 1.054571817e-27
+C_LIGHT = 2.99792458e10         # [cm/s]
+KAPPA = math.sqrt(2.0) * GF_GEV2 * HBARC_GEV_CM ** 3 * ERG_PER_GEV / HBAR_ERG_S  # [cm^3/s]
+
+
+@dataclass
+class Workload:
+    """One 1D periodic box: grid, directions and per-cell species inputs."""
+    name: str
+    nz: int
+    ndir: int
+    Lz: float                      # [cm]
+    n_nu: np.ndarray               # (nz,)   nu_e number density [cm^-3]
+    n_nubar: np.ndarray            # (nz,)   nubar_e number density [cm^-3]
+    f_nu: np.ndarray               # (nz, 3) nu_e number flux [cm^-3]
+    f_nubar: np.ndarray            # (nz, 3) nubar_e number flux [cm^-3]
+    dirs: Optional[np.ndarray] = None   # (ndir, 3) or None = Fibonacci sphere
+    alpha: float = 1e-6            # perturbation strength of Eq. 9
+    seed: int = 0                  # seed of the Eq. 9 perturbations
+    steps: int = 100
+    cfl_adv: float = 0.4
+    cfl_flavor: float = 0.4
+    area: float = 1.0              # transverse cell area [cm^2]
+    kappa: float = KAPPA
+    c_light: float = C_LIGHT
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def P(self) -> int:
+        return self.nz * self.ndir
+
+    @property
+    def dz(self) -> float:
+        return self.Lz / self.nz
+
+
+def _uniform_species(nz, n, nbar, fvec, fbarvec):
+    return (np.full(nz, float(n)), np.full(nz, float(nbar)),
+            np.tile(np.asarray(fvec, float), (nz, 1)), np.tile(np.asarray(fbarvec, float), (nz, 1)))
+
+
+def tiny_fiducial(seed: int = 0) -> Workload:
+    """32 cells over 4 fastest-growing wavelengths (Lz = 13.42 cm), 16 Fibonacci
+    directions, n_nue = 4.9e32, n_nuebar = 6.1e32 cm^-3, isotropic nu_e and
+    nubar_e flux factor 1/3 along -z, 100 steps at C = C_F = 0.4."""
+    nz, n, nb = 32, 4.9e32, 6.1e32
+    sp = _uniform_species(nz, n, nb, (0, 0, 0), (0, 0, -nb / 3.0))
+    return Workload("tiny_fiducial_32x16", nz, 16, 13.42, *sp, seed=seed, steps=100)
+
+
+def paper_1d(asymmetric: bool = False, seed: int = 0) -> Workload:
+    """The paper's 1D run shape (Sec. 3.1): 64 cm, 1024 cells, 378 directions
+    per cell (387,072 particles), species of tiny_fiducial; optionally the
+    nubar flux tilted to normalize(0.1, 0, -1) with flux factor 1/3."""
+    nz, n, nb = 1024, 4.9e32, 6.1e32
+    if asymmetric:
+        u = np.array([0.1, 0.0, -1.0]); u /= np.linalg.norm(u)
+        fb = nb / 3.0 * u
+    else:
+        fb = np.array([0.0, 0.0, -nb / 3.0])
+    sp = _uniform_species(nz, n, nb, (0, 0, 0), fb)
+    name = "paper_1d_1024x378" + ("_asym" if asymmetric else "")
+    return Workload(name, nz, 378, 64.0, *sp, seed=seed, steps=20000)
+
+
+def throughput_1d(nz: int = 16384, ndir: int = 1000, seed: int = 0) -> Workload:
+    """Throughput-scale 1D box: dz = 1/16 cm, per-cell n ~ U[1e32, 1e33] and
+    flux factor ~ U[0, 0.3] for each species, flux along +z or -z (random sign),
+    all drawn from numpy PCG64(seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = rng.uniform(1e32, 1e33, nz)
+    nb = rng.uniform(1e32, 1e33, nz)
+    ff = rng.uniform(0.0, 0.3, nz)
+    ffb = rng.uniform(0.0, 0.3, nz)
+    sg = rng.choice([-1.0, 1.0], nz)
+    sgb = rng.choice([-1.0, 1.0], nz)
+    f = np.zeros((nz, 3)); f[:, 2] = sg * ff * n
+    fb = np.zeros((nz, 3)); fb[:, 2] = sgb * ffb * nb
+    return Workload(f"throughput_1d_{nz}x{ndir}", nz, ndir, nz / 16.0, n, nb, f, fb, seed=seed, steps=200)
+
+
+def random_box(nz: int, ndir: int, seed: int = 0, Lz: Optional[float] = None) -> Workload:
+    """Small randomised box for parity tests: per-cell densities in [1e32, 1e33],
+    flux factors in [0, 1/3) with random 3D directions (so the x and y flux
+    terms are exercised)."""
+    rng = np.random.Generator(np.random.PCG64(1000 + seed))
+    n = rng.uniform(1e32, 1e33, nz)
+    nb = rng.uniform(1e32, 1e33, nz)
+
+    def flux(dens):
+        v = rng.normal(size=(nz, 3))
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        return v * (rng.uniform(0.0, 0.33, nz) * dens)[:, None]
+
+    f, fb = flux(n), flux(nb)
+    return Workload(f"random_{nz}x{ndir}_s{seed}", nz, ndir, Lz if Lz else nz / 16.0, n, nb, f, fb,
+                    seed=seed, steps=10)
+
+
+def two_beam(nz: int = 64, n: float = 4.89e32) -> Workload:
+    """Inhomogeneous two-beam test (App. A.4): a 1 cm box, one nu_e beam along
+    +z and one nubar_e beam along -z of equal density n.  With two directions
+    +-z, flux factors of +-1/3 put all neutrinos in the +z particle and all
+    antineutrinos in the -z particle (Eq. 8)."""
+    sp = _uniform_species(nz, n, n, (0, 0, n / 3.0), (0, 0, -n / 3.0))
+    dirs = np.array([[0.0, 0.0, 1.0], [0.0, 0.0, -1.0]])
+    return Workload(f"two_beam_{nz}", nz, 2, 1.0, *sp, dirs=dirs, steps=200)
+
+
+def by_name(name: str) -> Workload:
+    table = {
+        "tiny_fiducial": tiny_fiducial,
+        "paper_1d": paper_1d,
+        "paper_1d_asym": lambda: paper_1d(True),
+        "throughput_1d": throughput_1d,
+    }
+    return table[name]()

@@ -1,0 +1,471 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a number the
+paper prints (tests/golden/paper_numbers.json), a closed form, an exact
+invariant of the scheme, a library routine, or brute force on a tiny input.
+Together they are chosen so that a plausible slip in the oracle (a dropped
+term, a wrong sign or conjugation, a shifted index, a wrong RK coefficient)
+fails at least one of them.
+"""
+import json
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from oracle import dispersion as D
+from oracle import oracle as O
+from paper_2101_02745_gb300 import workloads as W
+
+GOLD = json.loads((Path(__file__).parent / "golden" / "paper_numbers.json").read_text())
+
+
+def _cfg(wl: W.Workload):
+    return O.config(wl.nz, wl.ndir, wl.Lz, wl.kappa, wl.c_light, wl.cfl_adv, wl.cfl_flavor, wl.area)
+
+
+def _init(wl: W.Workload):
+    return O.init(_cfg(wl), wl.n_nu, wl.n_nubar, wl.f_nu, wl.f_nubar, wl.alpha, wl.seed, wl.dirs)
+
+
+def _rand_herm(rng, trace=1.0):
+    a = rng.normal(size=(3, 3)) + 1j * rng.normal(size=(3, 3))
+    h = a @ a.conj().T
+    return h * (trace / np.trace(h).real)
+
+
+def _rand_unit(rng):
+    v = rng.normal(size=3)
+    return v / np.linalg.norm(v)
+
+
+# ------------------------------------------------------------------ RNG ---
+
+def test_splitmix64_reference_outputs():
+    # First outputs of SplitMix64 seeded with 1234567, as printed by the
+    # reference implementation that accompanies the xoshiro generators.
+    expect = [6457827717110365317, 3203168211198807973, 9817491932198370423,
+              4593380528125082431, 16408922859458223821]
+    assert [O.splitmix64(1234567, n) for n in range(1, 6)] == expect
+
+
+def test_uniform_draws_statistics():
+    u = np.array([O.uniform(0, p, k) for p in range(2000) for k in range(8)])
+    assert u.min() >= -1.0 and u.max() < 1.0
+    assert abs(u.mean()) < 0.02
+    assert abs(u.var() - 1.0 / 3.0) < 0.01
+
+
+# ----------------------------------------------------------- directions ---
+
+@pytest.mark.parametrize("M", [2, 16, 92, 378, 1000])
+def test_fibonacci_moments(M):
+    d = np.array([O.fibonacci_direction(i, M) for i in range(M)])
+    assert np.allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-15)
+    # midpoint rule in mu: sum mu = 0 and sum mu^2 / M = 1/3 - 1/(3 M^2) exactly
+    assert abs(d[:, 2].sum()) < 1e-13
+    assert abs((d[:, 2] ** 2).mean() - (1.0 / 3.0 - 1.0 / (3.0 * M * M))) < 1e-15
+
+
+# -------------------------------------------------------- shape function ---
+
+def test_shape_is_the_quadratic_bspline():
+    from scipy.interpolate import BSpline
+    B2 = BSpline.basis_element([-1.5, -0.5, 0.5, 1.5], extrapolate=False)
+    cfg = O.config(8, 1, 8.0, W.KAPPA, W.C_LIGHT)
+    rng = np.random.default_rng(0)
+    for z in np.concatenate([rng.uniform(0, 8, 200), [0.0, 0.5, 1.0, 7.999999, 3.5, 4.0]]):
+        cells, w = O.shape(cfg, z)
+        # brute force: weight of every cell is B2(cell centre - z) in cell units, periodic
+        brute = np.zeros(8)
+        for j in range(8):
+            for img in (-8, 0, 8):
+                x = (j + 0.5 + img) - z
+                v = B2(x)
+                brute[j] += 0.0 if np.isnan(v) else float(v)
+        got = np.zeros(8)
+        np.add.at(got, cells, w)
+        assert np.allclose(got, brute, atol=1e-15), z
+        assert abs(w.sum() - 1.0) < 1e-15
+        # first moment reproduces the position, variance is 1/4 (cell units)
+        jc = cells[1] + 0.5
+        s = np.array([-1.0, 0.0, 1.0])
+        pos = jc + (w * s).sum()
+        assert abs(((pos - z + 4.0) % 8.0) - 4.0) < 1e-14
+        mean = (w * s).sum()
+        assert abs((w * (s - mean) ** 2).sum() - 0.25) < 1e-14
+
+
+# ------------------------------------------------------------ init (Eq. 8, 9) ---
+
+def test_init_weights_and_flavour_state():
+    wl = W.tiny_fiducial()
+    cfg = _cfg(wl)
+    parts = _init(wl)
+    M, nz = wl.ndir, wl.nz
+    dV = wl.dz * wl.area
+    # numbering p = d*nz + j0, particle at the cell centre
+    assert np.allclose(parts["z"][:nz], (np.arange(nz) + 0.5) * wl.dz)
+    assert np.allclose(parts["omega"][nz], O.fibonacci_direction(1, M))
+    # Eq. 8 with f = 0 and fbar = -nbar/3 z
+    mu = parts["omega"][:, 2]
+    assert np.allclose(parts["N"], wl.n_nu[0] * dV / M, rtol=1e-15)
+    assert np.allclose(parts["Nbar"], (wl.n_nubar[0] - wl.n_nubar[0] * mu) * dV / M, rtol=1e-14)
+    for key in ("rho", "rhobar"):
+        r = parts[key]
+        assert np.allclose(r, np.conj(np.swapaxes(r, 1, 2)), atol=0)
+        tr = np.trace(r, axis1=1, axis2=2)
+        assert np.allclose(tr.real, 1.0, atol=1e-15) and np.all(tr.imag == 0)
+        assert np.all(r[:, 1, 2] == 0)
+        em, et = r[:, 0, 1], r[:, 0, 2]
+        assert np.all(np.abs(em.real) <= 1e-6) and np.all(np.abs(em.imag) <= 1e-6)
+        assert np.allclose(r[:, 1, 1].real, np.abs(em) ** 2, rtol=1e-14)
+        assert np.allclose(r[:, 2, 2].real, np.abs(et) ** 2, rtol=1e-14)
+    # the perturbations are the SplitMix64 draws
+    assert parts["rho"][5, 0, 1] == 1e-6 * O.uniform(0, 5, 0) + 1j * (1e-6 * O.uniform(0, 5, 1))
+    assert parts["rhobar"][7, 0, 2] == 1e-6 * O.uniform(0, 7, 6) + 1j * (1e-6 * O.uniform(0, 7, 7))
+    # deposited moments: trace n = n_input; f_z(nubar) = fbar_z (1 - 1/M^2) exactly (Fibonacci midpoints)
+    grid = O.deposit(cfg, parts)
+    assert np.allclose(np.trace(grid["n"], axis1=1, axis2=2).real, wl.n_nu[0], rtol=1e-14)
+    assert np.allclose(np.trace(grid["nbar"], axis1=1, axis2=2).real, wl.n_nubar[0], rtol=1e-14)
+    fbz = np.trace(grid["fbar"][:, 2], axis1=1, axis2=2).real
+    assert np.allclose(fbz, wl.f_nubar[0, 2] * (1 - 1.0 / M**2), rtol=1e-13)
+
+
+def test_init_rejects_negative_weights():
+    wl = W.tiny_fiducial()
+    with pytest.raises(ValueError):
+        O.init(_cfg(wl), wl.n_nu, wl.n_nubar, wl.f_nu, wl.f_nubar * 1.2, 1e-6, 0)
+
+
+# ---------------------------------------------------- deposit / interpolate ---
+
+def _random_particles(rng, nz, P, Lz):
+    parts = np.zeros(P, O.PARTICLE)
+    parts["z"] = rng.uniform(0, Lz, P)
+    parts["omega"] = np.array([_rand_unit(rng) for _ in range(P)])
+    parts["N"] = rng.uniform(0.5, 2.0, P) * 1e28
+    parts["Nbar"] = rng.uniform(0.5, 2.0, P) * 1e28
+    parts["rho"] = np.array([_rand_herm(rng) for _ in range(P)])
+    parts["rhobar"] = np.array([_rand_herm(rng) for _ in range(P)])
+    return parts
+
+
+def test_single_particle_deposit_brute_force():
+    rng = np.random.default_rng(3)
+    cfg = O.config(10, 1, 5.0, W.KAPPA, W.C_LIGHT, area=2.0)
+    parts = _random_particles(rng, 10, 1, 5.0)
+    parts["z"] = 0.13  # near the left edge: wraps into cell 9
+    grid = O.deposit(cfg, parts)
+    dz, dV = 0.5, 0.5 * 2.0
+    xi = 0.13 / dz - 0.5
+    d = xi - np.floor(xi + 0.5)
+    w = {9: 0.5 * (0.5 - d) ** 2, 0: 0.75 - d * d, 1: 0.5 * (0.5 + d) ** 2}
+    q = parts[0]
+    for j in range(10):
+        wj = w.get(j, 0.0)
+        assert np.allclose(grid["n"][j], q["N"] * wj * q["rho"] / dV, rtol=1e-14, atol=0)
+        assert np.allclose(grid["nbar"][j], q["Nbar"] * wj * q["rhobar"] / dV, rtol=1e-14, atol=0)
+        for i in range(3):
+            assert np.allclose(grid["f"][j, i], q["N"] * wj * q["rho"] * q["omega"][i] / dV, rtol=1e-14, atol=0)
+            assert np.allclose(grid["fbar"][j, i], q["Nbar"] * wj * q["rhobar"] * q["omega"][i] / dV,
+                               rtol=1e-14, atol=0)
+
+
+def test_deposit_interpolation_adjoint_and_constants():
+    rng = np.random.default_rng(7)
+    nz, P, Lz = 13, 40, 6.5
+    cfg = O.config(nz, 1, Lz, W.KAPPA, W.C_LIGHT)
+    parts = _random_particles(rng, nz, P, Lz)
+    parts["Nbar"] = 0.0
+    grid = O.deposit(cfg, parts)
+    G = np.zeros(nz, O.CELL)
+    G["n"] = rng.normal(size=(nz, 3, 3)) + 1j * rng.normal(size=(nz, 3, 3))
+    H = O.hamiltonian(cfg, G, parts) / W.KAPPA      # = interpolation of G["n"] (Eq. 6)
+    dV = Lz / nz
+    lhs = np.sum(grid["n"] * G["n"])
+    rhs = np.sum(parts["N"][:, None, None] * parts["rho"] * H) / dV
+    assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
+    # interpolating a constant field returns it at every particle
+    C = np.zeros(nz, O.CELL)
+    M0 = _rand_herm(rng) * 3.0
+    C["n"] = M0
+    HC = O.hamiltonian(cfg, C, parts) / W.KAPPA
+    assert np.allclose(HC, M0[None], rtol=1e-14, atol=1e-15)
+
+
+# --------------------------------------------- fixed-H precession (Eq. 2, 4, RK4) ---
+
+def _static_background_pair(rng, theta_per_step):
+    """Particle 0 is a background (any rho) that feels H = kappa (1 - Om.Om) (...)
+    = 0 from itself; particle 1 carries no weight, so it evolves in the fixed
+    Hamiltonian H = kappa (1 - Om0.Om1) (N0 rho0 - Nbar0 rhobar0^*) / dV (Eq. 2)."""
+    cfg = O.config(1, 2, 1.0, W.KAPPA, W.C_LIGHT)
+    parts = np.zeros(2, O.PARTICLE)
+    parts["z"] = [0.5, 0.3]
+    parts["omega"] = [_rand_unit(rng), _rand_unit(rng)]
+    parts["N"] = [1e30, 0.0]
+    parts["Nbar"] = [6e29, 0.0]
+    parts["rho"] = [_rand_herm(rng), _rand_herm(rng)]
+    parts["rhobar"] = [_rand_herm(rng), _rand_herm(rng)]
+    o0, o1 = parts["omega"]
+    Hexp = W.KAPPA * (1 - o0 @ o1) * (parts["N"][0] * parts["rho"][0] - parts["Nbar"][0] * parts["rhobar"][0].conj())
+    lam = np.linalg.eigvalsh(Hexp)
+    dt = theta_per_step / (lam.max() - lam.min())
+    return cfg, parts, Hexp, dt
+
+
+def _rk4_exact(H, rho, dt, nsteps):
+    lam, V = np.linalg.eigh(H)
+    r = V.conj().T @ rho @ V
+    x = -1j * (lam[:, None] - lam[None, :]) * dt
+    R = 1 + x + x**2 / 2 + x**3 / 6 + x**4 / 24
+    return V @ (r * R**nsteps) @ V.conj().T
+
+
+def test_fixed_hamiltonian_closed_form():
+    rng = np.random.default_rng(11)
+    cfg, parts, Hexp, dt = _static_background_pair(rng, 0.05)
+    grid = O.deposit(cfg, parts)
+    H = O.hamiltonian(cfg, grid, parts)
+    assert np.allclose(H[1], Hexp, rtol=1e-14, atol=1e-14 * np.abs(Hexp).max())
+    assert np.abs(H[0]).max() < 1e-14 * np.abs(Hexp).max()
+    Hb = O.hamiltonian_bar(H)
+    assert np.array_equal(Hb[1], -Hexp.conj()) or np.allclose(Hb[1], -H[1].conj(), rtol=0, atol=0)
+    rho0, rhob0 = parts["rho"][1].copy(), parts["rhobar"][1].copy()
+    nsteps = 40
+    O.run(cfg, parts, dt, nsteps)
+    # RK4 on a constant linear ODE multiplies each eigen-component by the degree-4 Taylor polynomial
+    exp_r = _rk4_exact(H[1], rho0, dt, nsteps)
+    exp_b = _rk4_exact(-H[1].conj(), rhob0, dt, nsteps)
+    assert np.abs(parts["rho"][1] - exp_r).max() < 1e-13
+    assert np.abs(parts["rhobar"][1] - exp_b).max() < 1e-13
+    # and to the continuum precession e^{-iHt} rho e^{iHt} up to the RK4 truncation (theta^5 per step)
+    lam, V = np.linalg.eigh(H[1])
+    U = V @ np.diag(np.exp(-1j * lam * dt * nsteps)) @ V.conj().T
+    assert np.abs(parts["rho"][1] - U @ rho0 @ U.conj().T).max() < 1e-6
+
+
+def test_trace_and_purity_conservation_small_theta():
+    rng = np.random.default_rng(5)
+    cfg, parts, _, dt = _static_background_pair(rng, 0.01)
+    tr0 = np.trace(parts["rho"][1]).real
+    p0 = np.trace(parts["rho"][1] @ parts["rho"][1]).real
+    pb0 = np.trace(parts["rhobar"][1] @ parts["rhobar"][1]).real
+    O.run(cfg, parts, dt, 100)
+    r, rb = parts["rho"][1], parts["rhobar"][1]
+    assert abs(np.trace(r).real - tr0) < 1e-12
+    assert abs(np.trace(r @ r).real - p0) < 1e-12
+    assert abs(np.trace(rb @ rb).real - pb0) < 1e-12
+
+
+# ------------------------------------------------- full-step invariants ---
+
+@pytest.fixture(scope="module")
+def fiducial_run():
+    wl = W.tiny_fiducial()
+    cfg = _cfg(wl)
+    parts = _init(wl)
+    grid0 = O.deposit(cfg, parts)
+    dt = O.timestep(cfg, grid0)
+    snaps = [parts.copy()]
+    for _ in range(10):
+        O.run(cfg, parts, dt, 10)
+        snaps.append(parts.copy())
+    return wl, cfg, dt, grid0, snaps
+
+
+def test_timestep_closed_form(fiducial_run):
+    wl, cfg, dt, grid0, _ = fiducial_run
+    dt_adv = 0.4 * wl.dz / wl.c_light
+    dt_flav = 0.4 / (wl.kappa * wl.n_nubar[0])
+    assert abs(dt - min(dt_adv, dt_flav)) < 1e-9 * dt
+    assert dt_flav < dt_adv
+
+
+def test_trace_exactly_conserved(fiducial_run):
+    *_, snaps = fiducial_run
+    for s in snaps:
+        for key in ("rho", "rhobar"):
+            tr = np.trace(s[key], axis1=1, axis2=2)
+            assert np.abs(tr - 1.0).max() < 1e-12
+
+
+def test_eln_matrix_conserved(fiducial_run):
+    """E = sum_p (N rho - Nbar rhobar^*) is an exact invariant of the scheme
+    (deposit and interpolation share w_pj, Hbar = -H^*), hence Eq. 18."""
+    wl, cfg, dt, grid0, snaps = fiducial_run
+    E0 = O.eln_matrix(snaps[0])
+    scale = np.abs(snaps[0]["N"]).sum() + np.abs(snaps[0]["Nbar"]).sum()
+    for s in snaps[1:]:
+        assert np.abs(O.eln_matrix(s) - E0).max() < 1e-12 * scale
+    # Eq. 18 in domain averages: n_ee(0) - <n_ee> = nbar_ee(0) - <nbar_ee>
+    gN = O.deposit(cfg, snaps[-1])
+    dn = np.mean(grid0["n"][:, 0, 0].real) - np.mean(gN["n"][:, 0, 0].real)
+    dnb = np.mean(grid0["nbar"][:, 0, 0].real) - np.mean(gN["nbar"][:, 0, 0].real)
+    assert abs(dn - dnb) < 1e-11 * wl.n_nu[0]
+    assert abs(dn) > 1e-4 * wl.n_nu[0]   # flavour change really happened
+
+
+def test_flavour_bound(fiducial_run):
+    """Eq. 19: |n_ee(0) - <n_ee>| <= sqrt(3) min(l, lbar), l^2 of Eq. 20."""
+    wl, cfg, dt, grid0, snaps = fiducial_run
+    gN = O.deposit(cfg, snaps[-1])
+    n0 = np.mean(grid0["n"].real, axis=0)
+    nb0 = np.mean(grid0["nbar"].real, axis=0)
+
+    def l(m):
+        a, b, c = m[0, 0], m[1, 1], m[2, 2]
+        return np.sqrt(((a - b) ** 2 + (a - c) ** 2 + (b - c) ** 2) / 6.0)
+
+    bound = np.sqrt(3.0) * min(l(n0), l(nb0))
+    dn = abs(n0[0, 0] - np.mean(gN["n"][:, 0, 0].real))
+    assert dn <= bound
+
+
+def test_instability_grows_exponentially(fiducial_run):
+    """<|n_emu|> (Eq. 10) grows by a steady factor per 10 steps in the linear phase."""
+    wl, cfg, dt, grid0, snaps = fiducial_run
+    amps = []
+    for s in snaps:
+        a, _ = O.domain_averages(cfg, O.deposit(cfg, s))
+        amps.append(a[0, 0, 1])
+    ratios = np.array(amps[4:]) / np.array(amps[3:-1])
+    assert np.all(ratios > 2.0) and ratios.max() / ratios.min() < 1.2
+
+
+def test_homogeneous_state_stays_homogeneous():
+    wl = W.tiny_fiducial()
+    cfg = _cfg(wl)
+    parts = _init(wl)
+    # same perturbation for every particle of a direction: no spatial structure
+    for key in ("rho", "rhobar"):
+        r = parts[key].reshape(wl.ndir, wl.nz, 3, 3)
+        r[:] = r[:, :1]
+    O.run(cfg, parts, O.timestep(cfg, O.deposit(cfg, parts)), 60)
+    g = O.deposit(cfg, parts)
+    for key in ("n", "nbar"):
+        v = g[key]
+        spread = np.abs(v - v.mean(axis=0, keepdims=True)).max()
+        assert spread <= 1e-10 * np.abs(v).max()
+    # and the off-diagonals still evolve (the homogeneous mode is not frozen)
+    assert np.abs(g["n"][:, 0, 1]).max() > 0
+
+
+def test_two_flavour_limit_and_flavour_relabelling():
+    wl = W.tiny_fiducial()
+    cfg = _cfg(wl)
+    base = _init(wl)
+    dt = O.timestep(cfg, O.deposit(cfg, base))
+    # two-flavour limit: tau rows and columns empty stay exactly empty
+    p2 = base.copy()
+    for key in ("rho", "rhobar"):
+        r = p2[key]
+        r[:, 0, 0] += r[:, 2, 2]
+        r[:, 2, :] = 0
+        r[:, :, 2] = 0
+    O.run(cfg, p2, dt, 40)
+    for key in ("rho", "rhobar"):
+        assert np.all(p2[key][:, 2, :] == 0) and np.all(p2[key][:, :, 2] == 0)
+    # relabelling mu <-> tau commutes with the evolution
+    perm = [0, 2, 1]
+    pa, pb = base.copy(), base.copy()
+    for key in ("rho", "rhobar"):
+        pb[key] = pb[key][:, perm][:, :, perm]
+    O.run(cfg, pa, dt, 30)
+    O.run(cfg, pb, dt, 30)
+    for key in ("rho", "rhobar"):
+        assert np.abs(pa[key][:, perm][:, :, perm] - pb[key]).max() < 1e-13
+
+
+# ------------------------------------------------------ growth-rate pins ---
+
+def test_dispersion_solver_reproduces_paper_peaks():
+    n = GOLD["fiducial_density"]["n_per_cm3"]
+    for key, m, kmax in (("dispersion_axisymmetric_peak", 0, 6.0), ("dispersion_asymmetric_peak", 1, 4.0)):
+        f = lambda k: D.continuum_growth(k, n, n, n / 3, -n / 3, W.KAPPA, W.C_LIGHT, m=m, nodes=96)
+        kp, gp = D.peak(f, 0.2, kmax, ngrid=30)
+        g = GOLD[key]
+        assert abs(gp / g["growth_per_s"] - 1) < 0.01, (key, gp)
+        assert abs(2 * np.pi / kp / g["wavelength_cm"] - 1) < 0.01, (key, 2 * np.pi / kp)
+    f0 = lambda k: D.continuum_growth(k, n, n, n / 3, -n / 3, W.KAPPA, W.C_LIGHT, m=0, nodes=96)
+    kp, _ = D.peak(f0, 0.2, 6.0, ngrid=30)
+    ke = D.unstable_edge(f0, kp, 20.0, tol=1e-4)
+    edge = GOLD["dispersion_unstable_edge"]
+    assert abs(ke * W.C_LIGHT / (W.KAPPA * n) / edge["kc_over_kappa_n"] - 1) < 0.01
+    assert abs(2 * np.pi / ke / edge["wavelength_cm"] - 1) < 0.01
+    assert abs(f0(0.0)) < 1e-6 * 6.5e10   # homogeneous mode does not grow
+
+
+def test_tiny_fiducial_box_holds_four_fastest_wavelengths():
+    wl = W.tiny_fiducial()
+    f = lambda k: D.continuum_growth(k, wl.n_nu[0], wl.n_nubar[0], 0.0, wl.f_nubar[0, 2], W.KAPPA, W.C_LIGHT,
+                                     m=0, nodes=96)
+    kp, _ = D.peak(f, 0.3, 4.0, ngrid=30)
+    assert abs(wl.Lz / 4 / (2 * np.pi / kp) - 1) < 0.005
+
+
+def test_two_beam_growth_rate():
+    """App. A.4: nu beam along +z, nubar beam along -z, n = 4.89e32, k = 2 pi/cm,
+    seed Re rho_emu = 1e-6 sin(k z0); Im(omega) = 1.88e11 /s."""
+    g = GOLD["two_beam_inhomogeneous_growth"]
+    wl = W.two_beam(nz=64)
+    cfg = _cfg(wl)
+    parts = O.init(cfg, wl.n_nu, wl.n_nubar, wl.f_nu, wl.f_nubar, 0.0, 0, wl.dirs)
+    z0 = parts["z"]
+    for key in ("rho", "rhobar"):
+        r = parts[key]
+        r[:] = 0
+        em = 1e-6 * np.sin(g["k_per_cm"] * z0)
+        r[:, 0, 1] = em; r[:, 1, 0] = em
+        r[:, 1, 1] = em**2
+        r[:, 0, 0] = 1 - em**2
+    assert np.allclose(parts["N"][:wl.nz], wl.n_nu[0] * wl.dz) and np.all(parts["N"][wl.nz:] == 0)
+    assert np.all(parts["Nbar"][:wl.nz] == 0)
+    dt = O.timestep(cfg, O.deposit(cfg, parts))
+    ts, amp = [], []
+    t = 0.0
+    while t < 53e-12:
+        gr = O.deposit(cfg, parts)
+        ts.append(t)
+        amp.append(abs(np.fft.fft(gr["n"][:, 0, 1])[1]))
+        O.rk4_step(cfg, parts, dt)
+        t += dt
+    ts, amp = np.array(ts), np.array(amp)
+    sel = ts >= 33e-12
+    slope = np.polyfit(ts[sel], np.log(amp[sel]), 1)[0]
+    assert abs(slope / g["growth_per_s"] - 1) < 1e-2, slope
+    # with the closed form of the linearised two-beam problem on this grid
+    mu = W.KAPPA * wl.n_nu[0]
+    kc = g["k_per_cm"] * W.C_LIGHT
+    S = D.shape_transfer(g["k_per_cm"], wl.dz)
+    pred = np.sqrt(kc * (4 * mu * S - kc))
+    assert abs(slope / pred - 1) < 5e-3, (slope, pred)
+
+
+def test_growth_matches_discrete_dispersion():
+    """Fastest box mode of the randomly seeded tiny fiducial box grows at the
+    rate of the discrete linear-stability solve (same 16 directions, box
+    wavenumbers, quadratic-shape transfer) within 5%."""
+    wl = W.tiny_fiducial()
+    cfg = _cfg(wl)
+    parts = _init(wl)
+    M = wl.ndir
+    dirs = parts["omega"][::wl.nz]
+    g = (wl.n_nu[0] + 3 * dirs @ wl.f_nu[0]) / M
+    gb = (wl.n_nubar[0] + 3 * dirs @ wl.f_nubar[0]) / M
+    rates = {}
+    for m in range(1, wl.nz // 2):
+        k = 2 * np.pi * m / wl.Lz
+        rates[m] = D.discrete_growth(k, dirs, g, gb, W.KAPPA, W.C_LIGHT, S=D.shape_transfer(k, wl.dz))
+    mbest = max(rates, key=rates.get)
+    dt = O.timestep(cfg, O.deposit(cfg, parts))
+    amp = []
+    for step in range(81):
+        gr = O.deposit(cfg, parts)
+        amp.append(abs(np.fft.fft(gr["n"][:, 0, 1])[mbest]))
+        O.rk4_step(cfg, parts, dt)
+    amp = np.log(np.array(amp))
+    ts = np.arange(81) * dt
+    slope = np.polyfit(ts[30:], amp[30:], 1)[0]
+    assert abs(slope / rates[mbest] - 1) < 0.05, (mbest, slope, rates[mbest])
