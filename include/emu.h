@@ -1,0 +1,192 @@
+/*
+ * emu.h -- C ABI of the GB300 (sm_103a) particle-in-cell step for the neutrino
+ * fast flavour instability (Richers, Willcox, Ford & Myers, arXiv:2101.02745).
+ *
+ * One box is a 1D periodic grid of nz cells over [0, Lz) with ndir
+ * computational particles per cell.  Each particle carries a position z, a
+ * unit direction Omega, weights N and Nbar, and two 3x3 Hermitian density
+ * matrices rho (neutrino) and rhobar (antineutrino) (Sec. 2.2).  One time step
+ * is one classic fourth-order Runge-Kutta step (Sec. 2.3) of Eq. 4 whose
+ * right-hand side is: deposit the particles onto the grid (Eq. 5), interpolate
+ * back to each particle (Eq. 6), build the self-interaction Hamiltonian and
+ * its antineutrino counterpart (Eq. 2 and Sec. 2.1), and form the commutators.
+ *
+ * Conventions
+ *   - FP64 throughout; CGS units.  Hamiltonians are angular frequencies H/hbar
+ *     [1/s]; kappa = sqrt(2) G_F / hbar [cm^3/s] is a configuration value.
+ *   - Flavour order e, mu, tau.  A Hermitian matrix is stored as 9 reals
+ *     (Sec. 2.2 stores only the upper triangle and diagonal):
+ *       [ee, mumu, tautau, Re emu, Im emu, Re etau, Im etau, Re mutau, Im mutau].
+ *   - Particle arrays are structure-of-arrays: component k of particle p of a
+ *     matrix array lives at [k * P + p].
+ *   - Particle numbering (the lattice contract): particle p = d * nz + i has
+ *     direction d (0 <= d < ndir) and ring index i.  The paper places one
+ *     particle per direction at every cell centre (Sec. 3.1) and every particle
+ *     moves at constant velocity c Omega (Eq. 4), so all particles of one
+ *     direction keep a common offset from their cell centres: particle i of
+ *     ring d sits at ((i + 1/2) dz + X_d) mod Lz, i.e. in cell
+ *     (i + s_d) mod nz where s_d is the cell of the ring's particle 0.
+ *     emu_init_particles establishes this.  The step kernels need only that
+ *     every particle lies in the cell its ring index assigns (within 1e-6
+ *     cells of that cell's boundary) and that a ring shares one direction;
+ *     they report EMU_ELATTICE otherwise.
+ *   - Grid potential A (36 x nz, [c * nz + j]): A0 = kappa (n - nbar^*) in
+ *     components 0..8, then A_x, A_y, A_z = kappa (f_i - fbar_i^*) in 9..35, so
+ *     that H_p = sum_j w_pj (A0_j - Omega_p . A_j)  (Eq. 2, 5, 6).
+ *   - Moments (72 x nz, [c * nz + j], cm^-3): n (0..8), f_x, f_y, f_z
+ *     (9..35), nbar (36..44), fbar_x, fbar_y, fbar_z (45..71)  (Eq. 5).
+ *
+ * Memory and streams
+ *   - The caller owns all device memory: the particle arrays (emu_particles)
+ *     and one workspace of emu_workspace_bytes() bytes.  The library allocates
+ *     no device memory of its own and never frees caller memory.
+ *   - Every call enqueues work on the stream given to emu_bind and returns
+ *     without waiting, except the calls that write host memory (on_host = 1),
+ *     emu_timestep and emu_sync, which synchronise that stream.
+ *   - Calls on one box must not run concurrently from several host threads.
+ *
+ * Errors: every function returns EMU_OK (0) or a negative code; the message
+ * of the last failure is available from emu_last_error.  Errors found by the
+ * kernels (lattice violation, non-finite grid values) are recorded in a word
+ * in the workspace and reported by the next synchronising call.
+ */
+#ifndef EMU_H
+#define EMU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EMU_OK 0
+#define EMU_EINVAL (-1)    /* bad argument: null pointer, size, unsupported option */
+#define EMU_ECUDA (-2)     /* a CUDA runtime call failed */
+#define EMU_ENUMERIC (-3)  /* a non-finite value appeared on the grid */
+#define EMU_ETIMEOUT (-4)  /* reserved: a bounded device-side wait gave up */
+#define EMU_ELATTICE (-5)  /* particles violate the lattice contract */
+
+typedef struct emu_box emu_box;
+
+/* Box parameters. */
+typedef struct {
+  int32_t nz;          /* cells, >= 1 */
+  int32_t ndir;        /* particles per cell (directions), >= 1 */
+  double Lz;           /* domain length [cm], > 0 */
+  double area;         /* transverse cell area [cm^2]; cell volume dV = (Lz/nz) * area */
+  double kappa;        /* sqrt(2) G_F / hbar [cm^3/s] (Eq. 2 divided by hbar) */
+  double c_light;      /* speed of light [cm/s] */
+  double cfl_adv;      /* C of Eq. 7 */
+  double cfl_flavor;   /* C_F of Eq. 7 */
+  int32_t shape_order; /* particle shape order (Sec. 2.2.1); only 2 (quadratic) is supported */
+  int32_t reserved;    /* must be 0 */
+} emu_config;
+
+/* Device pointers to the caller's particle arrays (P = nz * ndir entries each
+ * unless stated).  Rings share one direction: ox/oy/oz/N/Nbar are per particle. */
+typedef struct {
+  double* z;       /* [P] position in [0, Lz) [cm] */
+  double* ox;      /* [P] direction, x component */
+  double* oy;      /* [P] direction, y component */
+  double* oz;      /* [P] direction, z component */
+  double* N;       /* [P] neutrinos represented (Eq. 8) */
+  double* Nbar;    /* [P] antineutrinos represented (Eq. 8) */
+  double* rho;     /* [9][P] neutrino density matrices */
+  double* rhobar;  /* [9][P] antineutrino density matrices */
+  double* acc;     /* [18][P] RK scratch: running sum (rho components, then rhobar) */
+  double* stage;   /* [18][P] RK scratch: state of the next stage */
+  int64_t P;       /* must equal nz * ndir */
+} emu_particles;
+
+/* Bytes of device workspace a box with this configuration needs (grid,
+ * moments, per-direction tables, deposit partial sums, counters, error word).
+ * Returns a negative code for an invalid configuration. */
+int64_t emu_workspace_bytes(const emu_config* cfg);
+
+/* Validate cfg and create a box (host memory only).  *out receives the box. */
+int emu_create(const emu_config* cfg, emu_box** out);
+
+/* Attach caller-owned device memory and a CUDA stream (cudaStream_t, may be
+ * NULL for the legacy default stream).  The workspace must be at least
+ * emu_workspace_bytes(cfg) bytes and 256-byte aligned; it is cleared here. */
+int emu_bind(emu_box* box, const emu_particles* parts, void* workspace, int64_t workspace_bytes,
+             void* stream);
+
+/* Initialise every particle on the device (Sec. 3.1): particle p = d*nz + j0
+ * at the centre of cell j0 with direction d, weights of Eq. 8 from the
+ * per-cell inputs, and the initial flavour state of Eq. 9 with perturbation
+ * strength alpha, its random numbers drawn from SplitMix64 keyed by
+ * (seed, p, draw).  Host arrays: n_nu[nz], n_nubar[nz] [cm^-3],
+ * f_nu[nz*3], f_nubar[nz*3] [cm^-3]; dirs[ndir*3] unit vectors or NULL for the
+ * midpoint Fibonacci sphere.  A weight that is negative only by rounding is
+ * set to 0; a clearly negative weight (|f| > n/3) gives EMU_EINVAL. */
+int emu_init_particles(emu_box* box, const double* n_nu, const double* n_nubar, const double* f_nu,
+                       const double* f_nubar, const double* dirs, double alpha, uint64_t seed);
+
+/* Copy particle fields in from (set) or out to (get) caller buffers laid out
+ * like emu_particles (rho/rhobar as [9][P]).  Any pointer may be NULL to skip
+ * that field.  on_host = 1: host pointers (the call synchronises for get);
+ * 0: device pointers.  emu_set_particles re-validates the rings. */
+int emu_set_particles(emu_box* box, const double* z, const double* ox, const double* oy,
+                      const double* oz, const double* N, const double* Nbar, const double* rho,
+                      const double* rhobar, int on_host);
+int emu_get_particles(emu_box* box, double* z, double* ox, double* oy, double* oz, double* N,
+                      double* Nbar, double* rho, double* rhobar, int on_host);
+
+/* Deposit (Eq. 5) of the state `src` (0: rho/rhobar, 1: the RK stage buffer)
+ * at positions z + pos_dt * c * Omega_z into the box's grid potential A (see
+ * conventions).  If A_out is not NULL, A is also copied there ([36][nz]). */
+int emu_deposit(emu_box* box, int src, double pos_dt, double* A_out, int on_host);
+
+/* Interpolate (Eq. 6) the current grid potential A to every particle at
+ * positions z + pos_dt * c * Omega_z and write H/hbar [1/s] ([9][P], packed
+ * Hermitian) to H_out.  The antineutrino Hamiltonian is -H^* (Sec. 2.1). */
+int emu_interpolate_H(emu_box* box, double pos_dt, double* H_out, int on_host);
+
+/* One stage s (1..4) of the classic RK4 step of size dt: deposit the stage
+ * state, interpolate, form d rho/dt = -i[H, rho] and d rhobar/dt =
+ * -i[-H^*, rhobar] (Eq. 4), and update the scratch (acc, stage); stage 4
+ * writes the new rho, rhobar and z.  Stages must be called in order 1..4. */
+int emu_rk_stage(emu_box* box, int s, double dt);
+
+/* nsteps full RK4 steps of size dt (dt <= 0: the value of emu_timestep). */
+int emu_step(emu_box* box, int64_t nsteps, double dt);
+
+/* Per-species moments of the current state (Eq. 5, cm^-3) into out
+ * ([72][nz], see conventions). */
+int emu_moments(emu_box* box, double* out, int on_host);
+
+/* Domain diagnostics of the current state into out[63]:
+ *   [0:9)   <|n_ab|>      as a real 3x3 matrix, row-major   (Eq. 10)
+ *   [9:18)  <|nbar_ab|>   likewise
+ *   [18:27) <|f^x_ab|>    likewise                          (Eq. 10)
+ *   [27:36) <|fbar^x_ab|> likewise
+ *   [36:45) <n_ab>        packed Hermitian (one snapshot of Eq. B1)
+ *   [45:54) <nbar_ab>     packed Hermitian
+ *   [54:63) <n_ab - nbar_ab^*> packed Hermitian: the domain-averaged electron
+ *           lepton number matrix, conserved by Eq. 4 with this Hamiltonian (Eq. 18).
+ * Averages are over cells. */
+int emu_diagnostics(emu_box* box, double* out, int on_host);
+
+/* Eq. 7 from the moments of the current state (maximum over cells and
+ * diagonal components of n and nbar).  Synchronises. */
+int emu_timestep(emu_box* box, double* dt_out);
+
+/* Wait for the box's stream and report errors recorded by its kernels. */
+int emu_sync(emu_box* box);
+
+/* Kernels launched by this box since creation (for launch accounting). */
+int64_t emu_kernel_launches(const emu_box* box);
+
+/* Message of the last failure on this box ("" if none); box may be NULL for
+ * failures of emu_create. */
+const char* emu_last_error(const emu_box* box);
+
+/* Release the box (host memory only; caller memory is untouched). */
+void emu_destroy(emu_box* box);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EMU_H */

@@ -1,0 +1,307 @@
+"""ctypes binding of the C ABI in include/emu.h (argument marshalling only).
+
+Every function here forwards to the ``emu_*`` function of the same name in
+libemu_gb300.so; all arithmetic runs in the CUDA kernels.  If the library is
+missing, loading fails with an error: there is no CPU path.
+
+``Box`` is a convenience holder that allocates the caller-owned device arrays
+the ABI expects as torch tensors and passes their raw pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+EMU_OK = 0
+EMU_EINVAL = -1
+EMU_ECUDA = -2
+EMU_ENUMERIC = -3
+EMU_ETIMEOUT = -4
+EMU_ELATTICE = -5
+N_DIAG = 63
+
+
+class EmuError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"emu error {code}: {message}")
+        self.code = code
+
+
+class emu_config(ctypes.Structure):
+    _fields_ = [
+        ("nz", ctypes.c_int32),
+        ("ndir", ctypes.c_int32),
+        ("Lz", ctypes.c_double),
+        ("area", ctypes.c_double),
+        ("kappa", ctypes.c_double),
+        ("c_light", ctypes.c_double),
+        ("cfl_adv", ctypes.c_double),
+        ("cfl_flavor", ctypes.c_double),
+        ("shape_order", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class emu_particles(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_void_p) for name in
+                ("z", "ox", "oy", "oz", "N", "Nbar", "rho", "rhobar", "acc", "stage")] + [("P", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib_path() -> Path:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libemu_gb300.so and declare the ABI.  Raises if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and _build.stale():
+        _build.build()
+    if not path.exists():
+        raise RuntimeError(f"CUDA library {path} is not built; run paper_2101_02745_gb300.build.build()")
+    L = ctypes.CDLL(str(path))
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    cfgp = ctypes.POINTER(emu_config)
+    sig = {
+        "emu_workspace_bytes": (i64, [cfgp]),
+        "emu_create": (i32, [cfgp, ctypes.POINTER(vp)]),
+        "emu_bind": (i32, [vp, ctypes.POINTER(emu_particles), vp, i64, vp]),
+        "emu_init_particles": (i32, [vp, vp, vp, vp, vp, vp, dbl, ctypes.c_uint64]),
+        "emu_set_particles": (i32, [vp] + [vp] * 8 + [i32]),
+        "emu_get_particles": (i32, [vp] + [vp] * 8 + [i32]),
+        "emu_deposit": (i32, [vp, i32, dbl, vp, i32]),
+        "emu_interpolate_H": (i32, [vp, dbl, vp, i32]),
+        "emu_rk_stage": (i32, [vp, i32, dbl]),
+        "emu_step": (i32, [vp, i64, dbl]),
+        "emu_moments": (i32, [vp, vp, i32]),
+        "emu_diagnostics": (i32, [vp, vp, i32]),
+        "emu_timestep": (i32, [vp, ctypes.POINTER(dbl)]),
+        "emu_sync": (i32, [vp]),
+        "emu_kernel_launches": (i64, [vp]),
+        "emu_last_error": (ctypes.c_char_p, [vp]),
+        "emu_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(box, rc: int):
+    if rc != EMU_OK:
+        msg = load().emu_last_error(box)
+        raise EmuError(rc, msg.decode() if msg else "")
+
+
+def _host_ptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def make_config(nz, ndir, Lz, kappa, c_light, cfl_adv=0.4, cfl_flavor=0.4, area=1.0, shape_order=2) -> emu_config:
+    return emu_config(int(nz), int(ndir), float(Lz), float(area), float(kappa), float(c_light), float(cfl_adv),
+                      float(cfl_flavor), int(shape_order), 0)
+
+
+# ----------------------------------------------------------- thin wrappers
+
+def emu_workspace_bytes(cfg: emu_config) -> int:
+    n = load().emu_workspace_bytes(ctypes.byref(cfg))
+    if n < 0:
+        raise EmuError(int(n), "invalid configuration")
+    return int(n)
+
+
+def emu_create(cfg: emu_config):
+    box = ctypes.c_void_p()
+    rc = load().emu_create(ctypes.byref(cfg), ctypes.byref(box))
+    _check(None, rc)
+    return box
+
+
+def emu_bind(box, parts: emu_particles, workspace_ptr: int, workspace_bytes: int, stream_ptr: int):
+    _check(box, load().emu_bind(box, ctypes.byref(parts), workspace_ptr, workspace_bytes, stream_ptr))
+
+
+def emu_init_particles(box, n_nu, n_nubar, f_nu, f_nubar, dirs, alpha: float, seed: int):
+    arrs = [np.ascontiguousarray(a, np.float64) for a in (n_nu, n_nubar, f_nu, f_nubar)]
+    d = None if dirs is None else np.ascontiguousarray(dirs, np.float64)
+    _check(box, load().emu_init_particles(box, *map(_host_ptr, arrs), _host_ptr(d), float(alpha), int(seed)))
+
+
+def emu_set_particles(box, z, ox, oy, oz, N, Nbar, rho, rhobar, on_host: int):
+    _check(box, load().emu_set_particles(box, z, ox, oy, oz, N, Nbar, rho, rhobar, int(on_host)))
+
+
+def emu_get_particles(box, z, ox, oy, oz, N, Nbar, rho, rhobar, on_host: int):
+    _check(box, load().emu_get_particles(box, z, ox, oy, oz, N, Nbar, rho, rhobar, int(on_host)))
+
+
+def emu_deposit(box, src: int, pos_dt: float, A_out, on_host: int):
+    _check(box, load().emu_deposit(box, int(src), float(pos_dt), A_out, int(on_host)))
+
+
+def emu_interpolate_H(box, pos_dt: float, H_out, on_host: int):
+    _check(box, load().emu_interpolate_H(box, float(pos_dt), H_out, int(on_host)))
+
+
+def emu_rk_stage(box, s: int, dt: float):
+    _check(box, load().emu_rk_stage(box, int(s), float(dt)))
+
+
+def emu_step(box, nsteps: int, dt: float):
+    _check(box, load().emu_step(box, int(nsteps), float(dt)))
+
+
+def emu_moments(box, out, on_host: int):
+    _check(box, load().emu_moments(box, out, int(on_host)))
+
+
+def emu_diagnostics(box, out, on_host: int):
+    _check(box, load().emu_diagnostics(box, out, int(on_host)))
+
+
+def emu_timestep(box) -> float:
+    dt = ctypes.c_double()
+    _check(box, load().emu_timestep(box, ctypes.byref(dt)))
+    return dt.value
+
+
+def emu_sync(box):
+    _check(box, load().emu_sync(box))
+
+
+def emu_kernel_launches(box) -> int:
+    return int(load().emu_kernel_launches(box))
+
+
+def emu_last_error(box) -> str:
+    m = load().emu_last_error(box)
+    return m.decode() if m else ""
+
+
+def emu_destroy(box):
+    load().emu_destroy(box)
+
+
+# ------------------------------------------------------------ convenience
+
+class Box:
+    """One box with its caller-owned device memory held as torch tensors."""
+
+    FIELDS = ("z", "ox", "oy", "oz", "N", "Nbar")
+
+    def __init__(self, nz, ndir, Lz, kappa, c_light, cfl_adv=0.4, cfl_flavor=0.4, area=1.0,
+                 device="cuda", stream=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        self.cfg = make_config(nz, ndir, Lz, kappa, c_light, cfl_adv, cfl_flavor, area)
+        self.nz, self.ndir, self.P = int(nz), int(ndir), int(nz) * int(ndir)
+        f64 = dict(dtype=torch.float64, device=self.device)
+        self.t = {k: torch.zeros(self.P, **f64) for k in self.FIELDS}
+        self.t["rho"] = torch.zeros(9, self.P, **f64)
+        self.t["rhobar"] = torch.zeros(9, self.P, **f64)
+        self.t["acc"] = torch.zeros(18, self.P, **f64)
+        self.t["stage"] = torch.zeros(18, self.P, **f64)
+        self.ws_bytes = emu_workspace_bytes(self.cfg)
+        self._ws_raw = torch.zeros(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+        base = self._ws_raw.data_ptr()
+        self.ws_ptr = (base + 255) & ~255
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.parts = emu_particles(*[self.t[k].data_ptr() for k in
+                                     ("z", "ox", "oy", "oz", "N", "Nbar", "rho", "rhobar", "acc", "stage")],
+                                   self.P)
+        self.box = emu_create(self.cfg)
+        emu_bind(self.box, self.parts, self.ws_ptr, self.ws_bytes, self.stream.cuda_stream)
+
+    @classmethod
+    def from_workload(cls, wl, device="cuda", init=True):
+        b = cls(wl.nz, wl.ndir, wl.Lz, wl.kappa, wl.c_light, wl.cfl_adv, wl.cfl_flavor, wl.area, device=device)
+        if init:
+            b.init(wl.n_nu, wl.n_nubar, wl.f_nu, wl.f_nubar, wl.dirs, wl.alpha, wl.seed)
+        return b
+
+    def __del__(self):
+        try:
+            if getattr(self, "box", None) is not None:
+                emu_destroy(self.box)
+                self.box = None
+        except Exception:
+            pass
+
+    # -- ABI calls
+    def init(self, n_nu, n_nubar, f_nu, f_nubar, dirs=None, alpha=1e-6, seed=0):
+        nz = self.nz
+        emu_init_particles(self.box, np.broadcast_to(np.asarray(n_nu, float), (nz,)),
+                           np.broadcast_to(np.asarray(n_nubar, float), (nz,)),
+                           np.broadcast_to(np.asarray(f_nu, float), (nz, 3)),
+                           np.broadcast_to(np.asarray(f_nubar, float), (nz, 3)), dirs, alpha, seed)
+
+    def deposit(self, src=0, pos_dt=0.0):
+        out = self.torch.empty(36, self.nz, dtype=self.torch.float64, device=self.device)
+        emu_deposit(self.box, src, pos_dt, out.data_ptr(), 0)
+        return out
+
+    def interpolate_H(self, pos_dt=0.0):
+        out = self.torch.empty(9, self.P, dtype=self.torch.float64, device=self.device)
+        emu_interpolate_H(self.box, pos_dt, out.data_ptr(), 0)
+        return out
+
+    def rk_stage(self, s, dt):
+        emu_rk_stage(self.box, s, dt)
+
+    def step(self, nsteps, dt=0.0):
+        emu_step(self.box, nsteps, dt)
+
+    def moments(self):
+        out = self.torch.empty(72, self.nz, dtype=self.torch.float64, device=self.device)
+        emu_moments(self.box, out.data_ptr(), 0)
+        return out
+
+    def diagnostics(self) -> np.ndarray:
+        out = np.zeros(N_DIAG)
+        emu_diagnostics(self.box, _host_ptr(out), 1)
+        return out
+
+    def timestep(self) -> float:
+        return emu_timestep(self.box)
+
+    def sync(self):
+        emu_sync(self.box)
+
+    def launches(self) -> int:
+        return emu_kernel_launches(self.box)
+
+    def get_host(self) -> dict:
+        """All particle fields copied to host numpy arrays (rho, rhobar as (9, P))."""
+        h = {k: np.zeros(self.P) for k in self.FIELDS}
+        h["rho"] = np.zeros((9, self.P))
+        h["rhobar"] = np.zeros((9, self.P))
+        emu_get_particles(self.box, *[_host_ptr(h[k]) for k in self.FIELDS + ("rho", "rhobar")], 1)
+        return h
+
+    def set_host(self, **fields):
+        args = []
+        for k in self.FIELDS + ("rho", "rhobar"):
+            a = fields.get(k)
+            if a is not None:
+                a = np.ascontiguousarray(a, np.float64)
+                fields[k] = a
+            args.append(_host_ptr(a))
+        emu_set_particles(self.box, *args, 1)

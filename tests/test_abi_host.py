@@ -1,0 +1,81 @@
+"""CPU-side checks of the CUDA library: it builds for sm_103a, loads, exports
+every function include/emu.h declares, and its host-only logic (configuration
+validation, workspace sizing) behaves.  No call here touches a GPU."""
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+
+from paper_2101_02745_gb300 import build as B
+from paper_2101_02745_gb300 import emu as E
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return E.load()
+
+
+def declared_functions():
+    names = set()
+    for h in (ROOT / "include").glob("*.h"):
+        text = h.read_text()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(emu_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("emu_create", "emu_bind", "emu_init_particles", "emu_deposit", "emu_interpolate_H",
+                     "emu_rk_stage", "emu_step", "emu_moments", "emu_timestep", "emu_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_library_has_no_cpu_fallback_symbols(lib):
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", str(B.LIB)], capture_output=True, text=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    assert {n for n in exported if n.startswith("emu_")} == set(declared_functions())
+    assert not any(n.startswith("or_") for n in exported)
+
+
+def test_workspace_and_config_validation(lib):
+    cfg = E.make_config(32, 16, 13.42, 1.9e-22, 3e10)
+    n1 = E.emu_workspace_bytes(cfg)
+    assert n1 > 0 and n1 % 256 == 0
+    big = E.make_config(16384, 1000, 1024.0, 1.9e-22, 3e10)
+    assert E.emu_workspace_bytes(big) > n1
+    for bad in (E.make_config(0, 16, 1.0, 1e-22, 3e10), E.make_config(4, 0, 1.0, 1e-22, 3e10),
+                E.make_config(4, 4, -1.0, 1e-22, 3e10), E.make_config(4, 4, 1.0, 1e-22, 3e10, shape_order=1)):
+        with pytest.raises(E.EmuError) as ei:
+            E.emu_create(bad)
+        assert ei.value.code == E.EMU_EINVAL
+        assert E.emu_workspace_bytes.__name__  # message is set
+        assert E.emu_last_error(None)
+
+
+def test_create_destroy_and_unbound_calls(lib):
+    cfg = E.make_config(8, 4, 1.0, 1.9e-22, 3e10)
+    box = E.emu_create(cfg)
+    with pytest.raises(E.EmuError) as ei:
+        E.emu_step(box, 1, 1e-12)
+    assert ei.value.code == E.EMU_EINVAL and "bind" in str(ei.value)
+    assert E.emu_kernel_launches(box) == 0
+    E.emu_destroy(box)
+
+
+def test_oracle_builds_and_is_separate():
+    from oracle import oracle as O
+    O.build()
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", str(O._LIB)], capture_output=True, text=True).stdout
+    assert "or_rk4_step" in out and "emu_step" not in out

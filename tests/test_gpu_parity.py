@@ -1,0 +1,336 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Both sides start from their own initialisation of the same seeded inputs and
+run their own arithmetic; nothing computed on the GPU feeds the oracle.
+Tolerances (the readings of the parity requirement, see the design notes):
+  - per family the error is max_item ||gpu - ref||_F over a scale: for rho and
+    rhobar the max_item ||ref||_F; for the grid families n, f_i (nbar, fbar_i)
+    the max over cells of ||n||_F (||nbar||_F); for A and H, which contain the
+    cancelling difference n - nbar^*, kappa max_j (||n_j||_F + ||nbar_j||_F):
+    a sum's rounding error scales with its summands, not with its result;
+  - deposit, moments, interpolation of one state: 1e-12;
+  - every step of the first 50 steps: 1e-10;
+  - init: weights and directions to a few ulp, random draws bitwise.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2101_02745_gb300 import workloads as W
+from tests.compare import density_scales, family_err, moment_families, oracle_moments, oracle_potential, pack
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2101_02745_gb300 import build
+    build.build()
+    return torch
+
+
+def _cfg(wl):
+    return O.config(wl.nz, wl.ndir, wl.Lz, wl.kappa, wl.c_light, wl.cfl_adv, wl.cfl_flavor, wl.area)
+
+
+def _oracle_init(wl):
+    return O.init(_cfg(wl), wl.n_nu, wl.n_nubar, wl.f_nu, wl.f_nubar, wl.alpha, wl.seed, wl.dirs)
+
+
+def _box(wl):
+    from paper_2101_02745_gb300.emu import Box
+    return Box.from_workload(wl)
+
+
+def _state_errs(h, parts):
+    return (family_err(h["rho"], pack(parts["rho"])), family_err(h["rhobar"], pack(parts["rhobar"])))
+
+
+def _moment_errs(box, cfg, parts):
+    got = box.moments().cpu().numpy()
+    grid = O.deposit(cfg, parts)
+    ref = oracle_moments(grid)
+    sn, snb, _ = density_scales(grid)
+    scales = [sn] * 4 + [snb] * 4
+    return [family_err(g, r, s) for g, r, s in zip(moment_families(got), moment_families(ref), scales)]
+
+
+def _potential_err(A, grid, kappa):
+    Aref = oracle_potential(grid, kappa)
+    s = kappa * density_scales(grid)[2]
+    return max(family_err(A[9 * f:9 * (f + 1)], Aref[9 * f:9 * (f + 1)], s) for f in range(4))
+
+
+SMALL = [W.tiny_fiducial(), W.random_box(67, 37, seed=1), W.random_box(31, 9, seed=2), W.two_beam(nz=40)]
+
+
+@pytest.mark.parametrize("wl", SMALL, ids=lambda w: w.name)
+def test_init_parity(torch, wl):
+    box = _box(wl)
+    h = box.get_host()
+    parts = _oracle_init(wl)
+    assert np.array_equal(h["z"], parts["z"])
+    for i, k in enumerate(("ox", "oy", "oz")):
+        assert np.abs(h[k] - parts["omega"][:, i]).max() <= 4e-16
+    for k in ("N", "Nbar"):
+        ref = parts[k]
+        assert np.all(np.abs(h[k] - ref) <= 4e-16 * np.abs(ref).max())
+    if wl.dirs is not None:
+        assert np.array_equal(h["N"], parts["N"]) and np.array_equal(h["Nbar"], parts["Nbar"])
+    assert np.array_equal(h["rho"], pack(parts["rho"]))
+    assert np.array_equal(h["rhobar"], pack(parts["rhobar"]))
+
+
+@pytest.mark.parametrize("wl", SMALL, ids=lambda w: w.name)
+def test_deposit_moments_interpolation_parity(torch, wl):
+    box = _box(wl)
+    cfg = _cfg(wl)
+    parts = _oracle_init(wl)
+    grid = O.deposit(cfg, parts)
+    A = box.deposit(0, 0.0).cpu().numpy()
+    assert _potential_err(A, grid, wl.kappa) < 1e-12
+    assert max(_moment_errs(box, cfg, parts)) < 1e-12
+    H = box.interpolate_H(0.0).cpu().numpy()
+    Href = pack(O.hamiltonian(cfg, grid, parts))
+    assert family_err(H, Href, wl.kappa * density_scales(grid)[2]) < 1e-12
+    box.sync()
+
+
+def test_timestep_parity(torch):
+    wl = W.random_box(67, 37, seed=3)
+    box = _box(wl)
+    cfg = _cfg(wl)
+    dt_ref = O.timestep(cfg, O.deposit(cfg, _oracle_init(wl)))
+    assert abs(box.timestep() - dt_ref) <= 1e-13 * dt_ref
+
+
+@pytest.mark.parametrize("wl", [W.tiny_fiducial(), W.random_box(67, 37, seed=1)], ids=lambda w: w.name)
+def test_first_50_steps_parity(torch, wl):
+    """Every one of the first 50 RK4 steps: rho, rhobar and all grid moments
+    within 1e-10 of the oracle (family-wise relative)."""
+    box = _box(wl)
+    cfg = _cfg(wl)
+    parts = _oracle_init(wl)
+    dt = O.timestep(cfg, O.deposit(cfg, parts))
+    worst = 0.0
+    for n in range(50):
+        box.step(1, dt)
+        O.rk4_step(cfg, parts, dt)
+        h = box.get_host()
+        errs = list(_state_errs(h, parts)) + _moment_errs(box, cfg, parts)
+        worst = max(worst, max(errs))
+        assert max(errs) < 1e-10, (n, errs)
+        assert np.abs(h["z"] - parts["z"]).max() <= 1e-13 * wl.Lz
+    box.sync()
+    print(f"{wl.name}: worst family error over 50 steps {worst:.2e}")
+
+
+@pytest.mark.parametrize("nz,ndir", [(1, 3), (2, 5), (3, 1), (29, 17), (30, 8), (31, 9), (61, 40), (90, 2)])
+def test_edge_and_ragged_sizes(torch, nz, ndir):
+    wl = W.random_box(nz, ndir, seed=nz + ndir)
+    box = _box(wl)
+    cfg = _cfg(wl)
+    parts = _oracle_init(wl)
+    dt = O.timestep(cfg, O.deposit(cfg, parts))
+    for _ in range(5):
+        box.step(1, dt)
+        O.rk4_step(cfg, parts, dt)
+    h = box.get_host()
+    assert max(_state_errs(h, parts)) < 1e-10
+    assert max(_moment_errs(box, cfg, parts)) < 1e-10
+    box.sync()
+
+
+def test_stage_api_equals_step_and_is_deterministic(torch):
+    wl = W.random_box(61, 23, seed=4)
+    a, b, c = _box(wl), _box(wl), _box(wl)
+    dt = a.timestep()
+    for _ in range(7):
+        a.step(1, dt)
+        b.step(1, dt)
+        for s in (1, 2, 3, 4):
+            c.rk_stage(s, dt)
+    ha, hb, hc = a.get_host(), b.get_host(), c.get_host()
+    for k in ha:
+        assert np.array_equal(ha[k], hb[k]), k       # run-to-run bitwise reproducible
+        assert np.array_equal(ha[k], hc[k]), k       # stage calls == step
+    assert np.array_equal(a.moments().cpu().numpy(), b.moments().cpu().numpy())
+
+
+def test_invariants_on_gpu(torch):
+    wl = W.tiny_fiducial()
+    box = _box(wl)
+    d0 = box.diagnostics()
+    E0 = d0[54:63]
+    scale = np.abs(d0[36:45]).max() + np.abs(d0[45:54]).max()
+    box.step(100)
+    d1 = box.diagnostics()
+    assert np.abs(d1[54:63] - E0).max() < 1e-12 * scale
+    h = box.get_host()
+    for k in ("rho", "rhobar"):
+        assert np.abs(h[k][0] + h[k][1] + h[k][2] - 1.0).max() < 1e-12
+    # the instability grew: <|n_emu|> (Eq. 10, row-major entry (0, 1))
+    assert d1[1] > 1e3 * d0[1]
+    box.sync()
+
+
+def test_diagnostics_match_oracle(torch):
+    wl = W.random_box(67, 37, seed=5)
+    box = _box(wl)
+    cfg = _cfg(wl)
+    parts = _oracle_init(wl)
+    dt = O.timestep(cfg, O.deposit(cfg, parts))
+    box.step(10, dt)
+    O.run(cfg, parts, dt, 10)
+    d = box.diagnostics()
+    g = O.deposit(cfg, parts)
+    a, m = O.domain_averages(cfg, g)
+    for blk in range(4):
+        assert np.allclose(d[9 * blk:9 * (blk + 1)].reshape(3, 3), a[blk], rtol=1e-10, atol=1e-10 * a[blk].max())
+    assert family_err(d[36:45, None], pack(m[0])[:, None]) < 1e-10
+    assert family_err(d[45:54, None], pack(m[1])[:, None]) < 1e-10
+    eln = pack(np.mean(g["n"] - np.conj(g["nbar"]), axis=0))
+    assert family_err(d[54:63, None], eln[:, None]) < 1e-10
+
+
+def test_lattice_violation_is_reported(torch):
+    from paper_2101_02745_gb300.emu import EmuError, EMU_ELATTICE
+    wl = W.random_box(31, 4, seed=6)
+    box = _box(wl)
+    h = box.get_host()
+    z = h["z"].copy()
+    z[40] += 0.7 * wl.dz      # out of the cell its ring position assigns
+    box.set_host(z=z)
+    box.step(1, 1e-13)
+    with pytest.raises(EmuError) as ei:
+        box.sync()
+    assert ei.value.code == EMU_ELATTICE
+    box.sync()  # the error word was cleared
+
+
+def test_lattice_with_per_direction_offsets_and_ties(torch):
+    """Each ring shifted by its own offset in [-1/2, 1/2) cells, several exactly
+    at the cell boundary (a tie of the shape function), then stepped: same as
+    the oracle, which places each particle by floor()."""
+    wl = W.random_box(37, 11, seed=9)
+    box = _box(wl)
+    cfg = _cfg(wl)
+    parts = _oracle_init(wl)
+    u = np.linspace(-0.5, 0.45, wl.ndir)
+    u[[0, 3, 7]] = -0.5
+    z = parts["z"].reshape(wl.ndir, wl.nz) + u[:, None] * wl.dz
+    z = np.where(z < 0, z + wl.Lz, z).reshape(-1)
+    parts["z"] = z
+    box.set_host(z=z)
+    dt = O.timestep(cfg, O.deposit(cfg, parts))
+    for _ in range(8):
+        box.step(1, dt)
+        O.rk4_step(cfg, parts, dt)
+    h = box.get_host()
+    assert max(_state_errs(h, parts)) < 1e-10
+    assert max(_moment_errs(box, cfg, parts)) < 1e-10
+    box.sync()
+
+
+def test_nonfinite_state_is_reported(torch):
+    from paper_2101_02745_gb300.emu import EmuError, EMU_ENUMERIC
+    wl = W.random_box(31, 4, seed=7)
+    box = _box(wl)
+    h = box.get_host()
+    r = h["rho"].copy()
+    r[3, 17] = np.nan
+    box.set_host(rho=r)
+    box.step(1, 1e-13)
+    with pytest.raises(EmuError) as ei:
+        box.sync()
+    assert ei.value.code == EMU_ENUMERIC
+
+
+def test_bad_calls_are_rejected(torch):
+    from paper_2101_02745_gb300.emu import EmuError, EMU_EINVAL
+    box = _box(W.random_box(31, 4, seed=8))
+    with pytest.raises(EmuError) as ei:
+        box.rk_stage(2, 1e-13)
+    assert ei.value.code == EMU_EINVAL
+    box.rk_stage(1, 1e-13)
+    with pytest.raises(EmuError):
+        box.rk_stage(2, 2e-13)
+    with pytest.raises(EmuError):
+        box.step(1, 1e-13)          # a step is in progress
+    for s in (2, 3, 4):
+        box.rk_stage(s, 1e-13)
+    wl = W.tiny_fiducial()
+    with pytest.raises(EmuError):
+        box2 = _box(wl)
+        box2.init(wl.n_nu, wl.n_nubar, wl.f_nu, wl.f_nubar * 1.5)   # flux factor > 1/3
+    box.sync()
+
+
+# ------------------------------------------------------------ full sizes ---
+
+def test_paper_1d_full_size_first_step(torch):
+    """The paper's 1D run shape (1024 cells x 378 directions): init, deposit,
+    and one full RK4 step against the oracle on all 387,072 particles."""
+    wl = W.paper_1d(asymmetric=True)
+    box = _box(wl)
+    cfg = _cfg(wl)
+    parts = _oracle_init(wl)
+    h = box.get_host()
+    assert np.array_equal(h["rho"], pack(parts["rho"]))
+    grid = O.deposit(cfg, parts)
+    A = box.deposit(0, 0.0).cpu().numpy()
+    assert _potential_err(A, grid, wl.kappa) < 1e-12
+    dt = O.timestep(cfg, grid)
+    box.step(1, dt)
+    O.rk4_step(cfg, parts, dt)
+    h = box.get_host()
+    assert max(_state_errs(h, parts)) < 1e-12
+    assert max(_moment_errs(box, cfg, parts)) < 1e-12
+    box.sync()
+
+
+def test_throughput_full_size_sampled(torch):
+    """The throughput workload at full size (16384 cells x 1000 directions,
+    16.4M particles), in the launch configuration the benchmark times:
+    the full deposit against the oracle, then the first RK stage on 2000
+    sampled particles against the oracle's per-particle H and commutator,
+    then three full steps checked through the exact invariants."""
+    wl = W.throughput_1d()
+    box = _box(wl)
+    cfg = _cfg(wl)
+    parts = _oracle_init(wl)
+    grid = O.deposit(cfg, parts)
+    A = box.deposit(0, 0.0).cpu().numpy()
+    assert _potential_err(A, grid, wl.kappa) < 1e-12
+    dt = O.timestep(cfg, grid)
+    assert abs(box.timestep() - dt) <= 1e-13 * dt
+    rng = np.random.default_rng(0)
+    sample = np.sort(rng.choice(wl.P, 2000, replace=False))
+    Hs = O.hamiltonian(cfg, grid, parts[sample])
+    box.rk_stage(1, dt)
+    stage = box.t["stage"][:, sample].cpu().numpy()
+    accv = box.t["acc"][:, sample].cpu().numpy()
+    kr = np.array([O.commutator_rhs(Hs[i], parts["rho"][p]) for i, p in enumerate(sample)])
+    kb = np.array([O.commutator_rhs(-Hs[i].conj(), parts["rhobar"][p]) for i, p in enumerate(sample)])
+    ref_stage_r = pack(parts["rho"][sample] + 0.5 * dt * kr)
+    ref_stage_b = pack(parts["rhobar"][sample] + 0.5 * dt * kb)
+    ref_acc_r = pack(parts["rho"][sample] + dt / 6.0 * kr)
+    assert family_err(stage[:9], ref_stage_r) < 1e-13
+    assert family_err(stage[9:], ref_stage_b) < 1e-13
+    assert family_err(accv[:9], ref_acc_r) < 1e-13
+    for s in (2, 3, 4):
+        box.rk_stage(s, dt)
+    d0 = None
+    del parts, grid
+    d0 = box.diagnostics()
+    box.step(2, dt)
+    d1 = box.diagnostics()
+    scale = np.abs(d0[36:45]).max() + np.abs(d0[45:54]).max()
+    assert np.abs(d1[54:63] - d0[54:63]).max() < 1e-12 * scale
+    h = box.get_host()
+    for k in ("rho", "rhobar"):
+        assert np.abs(h[k][0] + h[k][1] + h[k][2] - 1.0).max() < 1e-12
+    box.sync()
