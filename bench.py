@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark of the FP64 particle step (one classic RK4 step of every particle:
+deposit, interpolation, Hamiltonian, commutators, update) on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+
+Prints one JSON line (rank 0).  The default workload is the throughput-scale
+1D box: 16384 cells x 1000 directions = 16.4M particles, per-cell densities
+and flux factors drawn from a seeded generator.  `value` is particle-updates/s
+over all ranks (one update = one full RK4 step of one particle), timed with
+CUDA events on the box's stream over exactly K steps with inputs resident in
+HBM.  With N > 1 (torchrun) every rank runs its own independent box
+(replicas, weak scaling; the path has no data exchange between boxes).
+
+`--impl reference` times the CPU oracle (the plain FP64 C implementation the
+tests check the kernels against) on the host cores, each step a bounded sample
+of the workload (its first 256 cells, all directions).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "particle-updates/s (FP64, 1 GB300) & % HBM roofline; batched and adjoint vs plain"
+UNIT = "particle-updates/s"
+# Algorithmic HBM bytes per particle-step: the 313 FP64 values classic RK4 must
+# move when the state crosses the all-particle deposit barrier four times.
+B_ALG_PER_UPDATE = 313 * 8
+# Algorithmic FP64 flops per particle of one RK-stage launch (FMA = 2), counted
+# from the formulation the kernel implements: G = A0 - Omega.A at the own cell
+# (54), shape weights (13), 3-tap interpolation (45), diagonal differences (3),
+# two packed Hermitian commutators (162), RK update (72; stage 4: 36 + 2 for z).
+FLOPS_RK = {1: 349, 2: 349, 3: 349, 4: 315}
+# ... and of one deposit launch: position and weights (15), B = N rho - Nbar rhobar^* (27),
+# 3-tap gather (45), accumulation of (1, Omega) x C (63).
+FLOPS_DEPOSIT = 150
+# FP64 pipe: 2 DFMA per clock per SM (nominal 1.25 TFLOP/s / (2 flop x 152 SMs x 2.07 GHz) = 1.99),
+# so peak = 2 x 2 flop x 152 SMs x 2.07 GHz.
+PEAK_FP64_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
+# Bytes per particle of one launch: RK stage (average over s = 1..4 of 55, 91, 91, 56 doubles), deposit (21).
+BYTES_RK = (55 + 91 + 91 + 56) / 4 * 8
+BYTES_DEPOSIT = 21 * 8
+
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        try:
+            return json.loads(p.read_text())
+        except Exception:
+            pass
+    return {}
+
+
+# ------------------------------------------------------------ distributed
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def dist_init(world: int, use_cuda: bool):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group(backend="nccl" if use_cuda else "gloo")
+    return dist
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None and dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(dist, x: float, device=None) -> float:
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in Path(self.path).read_text().splitlines():
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        loaded = [v for v in sm if mx and v >= 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def oracle_rate(wl, steps: int):
+    """Particle-updates/s of the CPU oracle running `steps` RK4 steps of wl (single thread)."""
+    from oracle import oracle as O
+    cfg = O.config(wl.nz, wl.ndir, wl.Lz, wl.kappa, wl.c_light, wl.cfl_adv, wl.cfl_flavor, wl.area)
+    parts = O.init(cfg, wl.n_nu, wl.n_nubar, wl.f_nu, wl.f_nubar, wl.alpha, wl.seed, wl.dirs)
+    dt = O.timestep(cfg, O.deposit(cfg, parts))
+    t0 = time.perf_counter()
+    O.run(cfg, parts, dt, steps)
+    el = time.perf_counter() - t0
+    return wl.P * steps / el, el
+
+
+def cpu_baseline(wl_full, budget_s: float = 15.0):
+    from paper_2101_02745_gb300 import workloads as W
+    sample = W.head(wl_full, 1024)
+    rate1, el1 = oracle_rate(sample, 1)
+    steps = max(1, int(budget_s / max(el1, 1e-3)) - 1)
+    rate, el = oracle_rate(sample, steps)
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sample.nz} cells x {sample.ndir} directions ({sample.P} particles) of the workload, "
+                      f"{steps} RK4 steps in {el:.1f} s, single-threaded C (-O2)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_2101_02745_gb300 import workloads as W
+    O.build()
+    wl = W.by_name(args.workload)
+    sample = W.head(wl, args.ref_cells)
+    cfg = O.config(sample.nz, sample.ndir, sample.Lz, sample.kappa, sample.c_light, sample.cfl_adv,
+                   sample.cfl_flavor, sample.area)
+    parts = O.init(cfg, sample.n_nu, sample.n_nubar, sample.f_nu, sample.f_nubar, sample.alpha, sample.seed)
+    dt = O.timestep(cfg, O.deposit(cfg, parts))
+    O.run(cfg, parts, dt, args.warmup)
+    t0 = time.perf_counter()
+    O.run(cfg, parts, dt, args.steps)
+    el = time.perf_counter() - t0
+    value = sample.P * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / max(args.steps, 1) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "nz": wl.nz, "ndir": wl.ndir, "particles": wl.P,
+                   "sample": f"first {sample.nz} cells x {sample.ndir} directions ({sample.P} particles) per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{sample.P} particles per step, {args.steps} timed steps, single-threaded C"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU
+
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2101_02745_gb300 import build as B
+    from paper_2101_02745_gb300 import emu as E
+    from paper_2101_02745_gb300 import workloads as W
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the CUDA path has no CPU fallback)")
+    if rank == 0:
+        B.build()
+    dist = dist_init(world, True)
+    device = torch.device("cuda", local_rank)
+    torch.cuda.set_device(device)
+    barrier(dist, device)
+    if rank != 0:
+        B.build()  # no-op once rank 0 built it
+
+    wl = W.by_name(args.workload)
+    box = E.Box.from_workload(wl, device=device)
+    stream = box.stream
+    dt = box.timestep()
+    box.step(args.warmup, dt)
+    box.sync()
+
+    # ---- timed region: exactly K steps, inputs resident in HBM (state 7.9 GB >> 129 MB L2)
+    barrier(dist, device)
+    torch.cuda.synchronize(device)
+    clocks = ClockSampler(device.index).start()
+    E.emu_profile(box.box, True)
+    n0 = box.launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    box.step(args.steps, dt)
+    ev1.record(stream)
+    torch.cuda.synchronize(device)
+    barrier(dist, device)
+    elapsed_ms = ev0.elapsed_time(ev1)
+    launches = box.launches() - n0
+    ktimes = E.emu_kernel_times(box.box)
+    E.emu_profile(box.box, False)
+    box.sync()
+    t_ms = max_over_ranks(dist, elapsed_ms, device)
+    value = world * wl.P * args.steps / (t_ms * 1e-3)
+
+    # ---- end to end through the public API with host buffers
+    host = box.get_host()
+    pin = {k: torch.from_numpy(host[k]).pin_memory() for k in ("z", "rho", "rhobar")}
+    diag = torch.zeros(E.N_DIAG, dtype=torch.float64).pin_memory()
+    ptr = {k: v.data_ptr() for k, v in pin.items()}
+
+    def e2e_step():
+        E.emu_set_particles(box.box, ptr["z"], None, None, None, None, None, ptr["rho"], ptr["rhobar"], 1)
+        E.emu_step(box.box, 1, dt)
+        E.emu_diagnostics(box.box, diag.data_ptr(), 1)
+
+    e2e_step()
+    barrier(dist, device)
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize(device)
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t0, device)
+    clk = clocks.stop()
+    box.sync()
+    e2e_value = world * wl.P * args.steps / e2e_s
+    h2d = sum(v.numel() * 8 for v in pin.values())
+    d2h = E.N_DIAG * 8
+
+    # ---- roofline of the dominant kernel from the live per-launch events
+    per = {k: (ms / n if n else 0.0, n, ms) for k, (ms, n) in ktimes.items()}
+    total = sum(ms for (_, _, ms) in per.values()) or 1.0
+    dominant = max(per, key=lambda k: per[k][2])
+    avg_ms = per[dominant][0]
+    if dominant == "deposit":
+        flops = FLOPS_DEPOSIT * wl.P
+        bytes_ = BYTES_DEPOSIT * wl.P
+    else:
+        flops = sum(FLOPS_RK.values()) / 4 * wl.P
+        bytes_ = BYTES_RK * wl.P
+    achieved = flops / (avg_ms * 1e-3) / 1e12
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / PEAK_FP64_TFLOPS, "traffic": None,
+                "kernel": "k_rk_stage" if dominant == "rk_stage" else f"k_{dominant}",
+                "flops_per_launch": flops, "avg_launch_ms": avg_ms,
+                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                "hbm_gbs_of_kernel": bytes_ / (avg_ms * 1e-3) / 1e9}
+    hbm = {"achieved_gbs": value / world * B_ALG_PER_UPDATE / 1e9, "peak_gbs": hbm_peak,
+           "frac": value / world * B_ALG_PER_UPDATE / 1e9 / hbm_peak, "bytes_per_update": B_ALG_PER_UPDATE,
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "nz": wl.nz, "ndir": wl.ndir, "particles_per_gpu": wl.P,
+                       "dt_s": dt, "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (particle state 7.9 GB per GPU vs 129 MB L2)"},
+            "roofline": roofline, "hbm": hbm,
+            "kernels": {k: {"launches": n, "avg_ms": a, "share": ms / total} for k, (a, n, ms) in per.items() if n},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(wl)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="throughput_1d",
+                    choices=["throughput_1d", "paper_1d", "paper_1d_asym", "tiny_fiducial"])
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--ref-cells", type=int, default=256, help="cells per oracle step in --impl reference")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -178,6 +178,15 @@ int emu_sync(emu_box* box);
 /* Kernels launched by this box since creation (for launch accounting). */
 int64_t emu_kernel_launches(const emu_box* box);
 
+/* Per-launch device timing.  With enable != 0 every later kernel launch of
+ * the box is bracketed by two CUDA events recorded on the box's stream.
+ * emu_kernel_times synchronises the stream, writes the summed duration [ms]
+ * and the number of recorded launches of each kernel class to ms_out[4] and
+ * count_out[4] (0: lattice-shift table, 1: deposit, 2: RK stage, 3: other),
+ * and clears the record.  Timing is a measurement aid with no other effect. */
+int emu_profile(emu_box* box, int enable);
+int emu_kernel_times(emu_box* box, double* ms_out, int64_t* count_out);
+
 /* Message of the last failure on this box ("" if none); box may be NULL for
  * failures of emu_create. */
 const char* emu_last_error(const emu_box* box);

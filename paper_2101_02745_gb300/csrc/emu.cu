@@ -32,6 +32,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 namespace {
 
@@ -589,7 +590,16 @@ struct emu_box {
   double stage_dt = 0.0;
   double dt_cached = 0.0;
   int64_t launches = 0;
+  // optional per-launch timing: events recorded on the box's stream around each kernel
+  struct Rec { int cls; cudaEvent_t a, b; };
+  bool prof = false;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
   char msg[512] = {0};
+  ~emu_box() {
+    for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
 };
 
 namespace {
@@ -610,8 +620,29 @@ int cuda_check(emu_box* b, cudaError_t e, const char* what) {
   return fail(b, EMU_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+enum : int { CLS_SHIFT = 0, CLS_DEPOSIT = 1, CLS_RK = 2, CLS_OTHER = 3, N_CLS = 4 };
+
+cudaEvent_t take_event(emu_box* b) {
+  if (!b->pool.empty()) { cudaEvent_t e = b->pool.back(); b->pool.pop_back(); return e; }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Called right before a launch: records the start event when timing is on.
+void before_launch(emu_box* b, int cls) {
+  if (!b->prof) return;
+  emu_box::Rec r{cls, take_event(b), nullptr};
+  if (r.a) cudaEventRecord(r.a, b->stream);
+  b->recs.push_back(r);
+}
+
 int after_launch(emu_box* b, const char* what) {
   b->launches++;
+  if (b->prof && !b->recs.empty() && b->recs.back().b == nullptr) {
+    b->recs.back().b = take_event(b);
+    if (b->recs.back().b) cudaEventRecord(b->recs.back().b, b->stream);
+  }
   return cuda_check(b, cudaGetLastError(), what);
 }
 
@@ -621,6 +652,7 @@ int launch_shifts(emu_box* b, const double* offs, int nrows) {
   Offsets o{};
   for (int s = 0; s < nrows; ++s) o.v[s] = offs[s];
   const int blocks = (b->g.M + kThreads - 1) / kThreads;
+  before_launch(b, CLS_SHIFT);
   k_shifts<<<blocks, kThreads, 0, b->stream>>>(b->pt.z, b->dirtab, b->g, o, nrows, b->shift);
   return after_launch(b, "shift kernel");
 }
@@ -628,6 +660,7 @@ int launch_shifts(emu_box* b, const double* offs, int nrows) {
 int launch_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, const int* shift_row,
                    double pos_dt, double* out, double scale) {
   const Geo& g = b->g;
+  before_launch(b, CLS_DEPOSIT);
   if (mode == 0)
     k_deposit<0><<<tile_grid(g), kThreads, 0, b->stream>>>(b->pt.z, b->pt.N, b->pt.Nbar, rnu, rnb, b->dirtab,
         shift_row, pos_dt, g, b->partial, b->counters, out, scale, b->err);
@@ -666,6 +699,7 @@ int run_moments(emu_box* b) {
 
 int rebuild_dirtable(emu_box* b) {
   const int blocks = (int)((b->g.P + kThreads - 1) / kThreads);
+  before_launch(b, CLS_OTHER);
   k_dirtable<<<blocks, kThreads, 0, b->stream>>>(b->pt, b->g, b->cfg.c_light, b->dirtab, b->err);
   return after_launch(b, "direction table kernel");
 }
@@ -772,6 +806,7 @@ int emu_init_particles(emu_box* b, const double* n_nu, const double* n_nubar, co
                                                st), "copy directions"))
       return rc;
   const int blocks = (int)((b->g.P + kThreads - 1) / kThreads);
+  before_launch(b, CLS_OTHER);
   k_init<<<blocks, kThreads, 0, st>>>(b->pt, b->g, b->species, b->dirs, dirs ? 1 : 0, alpha, seed, b->err);
   if (int rc = after_launch(b, "init kernel")) return rc;
   if (int rc = rebuild_dirtable(b)) return rc;
@@ -839,6 +874,7 @@ int emu_interpolate_H(emu_box* b, double pos_dt, double* H_out, int on_host) {
   if (int rc = launch_shifts(b, &pos_dt, 1)) return rc;
   double* dst = H_out;
   if (on_host) dst = b->pt.acc;  // staging: the RK scratch holds 18 P doubles
+  before_launch(b, CLS_OTHER);
   k_interpolate<<<tile_grid(b->g), kThreads, 0, b->stream>>>(b->pt.z, b->dirtab, b->shift, b->A, pos_dt, b->g, dst,
                                                              b->err);
   if (int rc = after_launch(b, "interpolation kernel")) return rc;
@@ -864,6 +900,7 @@ int emu_rk_stage(emu_box* b, int s, double dt) {
   const double* rnb = (s == 1) ? b->pt.rhobar : b->pt.stage + 9 * P;
   const int* srow = b->shift + (size_t)(s - 1) * b->g.M;
   if (int rc = launch_deposit(b, 0, rnu, rnb, srow, pos, b->A, b->cfg.kappa / b->g.dV)) return rc;
+  before_launch(b, CLS_RK);
   k_rk_stage<<<tile_grid(b->g), kThreads, 0, b->stream>>>(b->pt, b->dirtab, srow, b->A, b->g, s, dt, b->err);
   if (int rc = after_launch(b, "RK stage kernel")) return rc;
   b->next_stage = s == 4 ? 1 : s + 1;
@@ -874,6 +911,7 @@ int emu_timestep(emu_box* b, double* dt_out) {
   if (int rc = check_bound(b)) return rc;
   if (!dt_out) return fail(b, EMU_EINVAL, "dt_out is NULL");
   if (int rc = run_moments(b)) return rc;
+  before_launch(b, CLS_OTHER);
   k_max_diag<<<1, kThreads, 0, b->stream>>>(b->mom, b->g.nz, b->scalar);
   if (int rc = after_launch(b, "max kernel")) return rc;
   double nmax = 0.0;
@@ -912,6 +950,7 @@ int emu_diagnostics(emu_box* b, double* out, int on_host) {
   if (int rc = check_bound(b)) return rc;
   if (!out) return fail(b, EMU_EINVAL, "out is NULL");
   if (int rc = run_moments(b)) return rc;
+  before_launch(b, CLS_OTHER);
   k_diagnostics<<<1, kThreads, 0, b->stream>>>(b->mom, b->g.nz, b->diag);
   if (int rc = after_launch(b, "diagnostics kernel")) return rc;
   return copy_out(b, out, b->diag, sizeof(double) * 63, on_host);
@@ -924,6 +963,33 @@ int emu_sync(emu_box* b) {
 }
 
 int64_t emu_kernel_launches(const emu_box* b) { return b ? b->launches : 0; }
+
+int emu_profile(emu_box* b, int enable) {
+  if (!b) return EMU_EINVAL;
+  b->prof = enable != 0;
+  return EMU_OK;
+}
+
+int emu_kernel_times(emu_box* b, double* ms_out, int64_t* count_out) {
+  if (int rc = check_bound(b)) return rc;
+  if (!ms_out || !count_out) return fail(b, EMU_EINVAL, "output arrays are NULL");
+  if (int rc = cuda_check(b, cudaStreamSynchronize(b->stream), "synchronise for kernel times")) return rc;
+  for (int c = 0; c < N_CLS; ++c) { ms_out[c] = 0.0; count_out[c] = 0; }
+  int rc = EMU_OK;
+  for (auto& r : b->recs) {
+    float ms = 0.f;
+    if (r.a && r.b && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      ms_out[r.cls] += ms;
+      count_out[r.cls] += 1;
+    } else {
+      rc = fail(b, EMU_ECUDA, "a kernel timing event could not be read");
+    }
+    if (r.a) b->pool.push_back(r.a);
+    if (r.b) b->pool.push_back(r.b);
+  }
+  b->recs.clear();
+  return rc;
+}
 
 const char* emu_last_error(const emu_box* b) { return b ? b->msg : g_create_msg; }
 

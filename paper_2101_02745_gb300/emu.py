@@ -88,6 +88,8 @@ def load(build_if_missing: bool = False):
         "emu_timestep": (i32, [vp, ctypes.POINTER(dbl)]),
         "emu_sync": (i32, [vp]),
         "emu_kernel_launches": (i64, [vp]),
+        "emu_profile": (i32, [vp, i32]),
+        "emu_kernel_times": (i32, [vp, vp, vp]),
         "emu_last_error": (ctypes.c_char_p, [vp]),
         "emu_destroy": (None, [vp]),
     }
@@ -187,6 +189,21 @@ def emu_sync(box):
 
 def emu_kernel_launches(box) -> int:
     return int(load().emu_kernel_launches(box))
+
+
+KERNEL_CLASSES = ("shifts", "deposit", "rk_stage", "other")
+
+
+def emu_profile(box, enable: bool):
+    _check(box, load().emu_profile(box, int(bool(enable))))
+
+
+def emu_kernel_times(box):
+    """{class: (total_ms, launches)} recorded since profiling was enabled."""
+    ms = np.zeros(4)
+    cnt = np.zeros(4, np.int64)
+    _check(box, load().emu_kernel_times(box, _host_ptr(ms), cnt.ctypes.data_as(ctypes.c_void_p)))
+    return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
 
 def emu_last_error(box) -> str:

@@ -133,6 +133,16 @@ def two_beam(nz: int = 64, n: float = 4.89e32) -> Workload:
     return Workload(f"two_beam_{nz}", nz, 2, 1.0, *sp, dirs=dirs, steps=200)
 
 
+def head(wl: Workload, nz: int) -> Workload:
+    """The first nz cells of a workload (same per-cell inputs, cell size and
+    directions): a bounded sample of it."""
+    nz = min(nz, wl.nz)
+    return Workload(f"{wl.name}[:{nz}]", nz, wl.ndir, wl.dz * nz, wl.n_nu[:nz].copy(), wl.n_nubar[:nz].copy(),
+                    wl.f_nu[:nz].copy(), wl.f_nubar[:nz].copy(), dirs=wl.dirs, alpha=wl.alpha, seed=wl.seed,
+                    steps=wl.steps, cfl_adv=wl.cfl_adv, cfl_flavor=wl.cfl_flavor, area=wl.area, kappa=wl.kappa,
+                    c_light=wl.c_light)
+
+
 def by_name(name: str) -> Workload:
     table = {
         "tiny_fiducial": tiny_fiducial,
