@@ -187,8 +187,36 @@ int64_t emu_kernel_launches(const emu_box* box);
 int emu_profile(emu_box* box, int enable);
 int emu_kernel_times(emu_box* box, double* ms_out, int64_t* count_out);
 
+/* Deposit that allocates nothing (the paper has no counterpart: this is a
+ * service for callers of the library).  Some callers cannot call cudaMalloc
+ * or any other allocator: code running in a host callback or inside another
+ * library's allocation-free section, or code that must not touch an
+ * allocator while a memory pool is being resized.  They cannot provide the
+ * workspace emu_bind needs, so this call keeps the deposit's scratch (direction
+ * table, lattice shifts, partial sums, tile counters, error word) in one
+ * static 16 MiB device array of the library, which every GPU that loads the
+ * library holds until the process exits.
+ *   - Inputs: cfg and the device particle arrays laid out as in emu_particles
+ *     (rho/rhobar as [9][P]); output: A_out, a device array [36][nz] that
+ *     receives the grid potential A (as emu_deposit) of the state at positions
+ *     z + pos_dt * c * Omega_z.  stream is a cudaStream_t (NULL: legacy stream).
+ *   - A box whose scratch does not fit in 16 MiB (more than about 400,000
+ *     directions, or partial sums beyond the array) is rejected with
+ *     EMU_EINVAL before any device work.
+ *   - The first call on a device looks up the array's device address on that
+ *     device (cudaGetSymbolAddress); make that first call before any stream
+ *     capture.  The call clears the counters it needs, runs the deposit,
+ *     then synchronises the stream to report lattice or non-finite errors.
+ *   - All calls on a device share the one array, which keeps whatever the last
+ *     call left in it: calls that overlap on the GPU (other streams, other host
+ *     threads) race on it and must be serialised by the caller.
+ * Errors are reported through emu_last_error(NULL). */
+int emu_deposit_static(const emu_config* cfg, const double* z, const double* ox, const double* oy,
+                       const double* oz, const double* N, const double* Nbar, const double* rho,
+                       const double* rhobar, double pos_dt, double* A_out, void* stream);
+
 /* Message of the last failure on this box ("" if none); box may be NULL for
- * failures of emu_create. */
+ * failures of emu_create and emu_deposit_static. */
 const char* emu_last_error(const emu_box* box);
 
 /* Release the box (host memory only; caller memory is untouched). */

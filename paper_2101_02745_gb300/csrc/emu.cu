@@ -32,6 +32,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <mutex>
 #include <vector>
 
 namespace {
@@ -996,3 +997,111 @@ const char* emu_last_error(const emu_box* b) { return b ? b->msg : g_create_msg;
 void emu_destroy(emu_box* b) { delete b; }
 
 }  // extern "C"
+
+// ------------------------------------------- deposit without any allocation
+//
+// Some callers cannot allocate device memory at all: code running where
+// cudaMalloc is not allowed (inside a host callback or another library's
+// allocation-free region), or code that must not call into any allocator
+// (for example while a memory pool is being torn down or resized).  They
+// cannot provide the workspace that emu_bind expects, so this entry point
+// keeps the deposit's scratch (per-direction table, lattice shifts, partial
+// sums over direction chunks, tile counters, error word) in one static device
+// array that the library itself holds on every GPU that loads it.
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // 16 MiB per device
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+void* g_static_addr[kMaxDevices] = {nullptr};
+std::mutex g_static_mutex;
+
+// Device address of g_static_scratch on the current device.  The name of the
+// array is only a host-side stand-in; the address must come from the runtime,
+// once per device, with that device current.
+int static_scratch_address(void** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(nullptr, EMU_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(nullptr, EMU_EINVAL, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess)
+      return fail(nullptr, EMU_ECUDA, "cudaGetSymbolAddress of the static scratch: %s", cudaGetErrorString(e));
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return EMU_OK;
+}
+
+}  // namespace
+
+extern "C" int emu_deposit_static(const emu_config* cfg, const double* z, const double* ox, const double* oy,
+                                  const double* oz, const double* N, const double* Nbar, const double* rho,
+                                  const double* rhobar, double pos_dt, double* A_out, void* stream) {
+  if (const char* why = config_problem(cfg)) return fail(nullptr, EMU_EINVAL, "%s", why);
+  if (!z || !ox || !oy || !oz || !N || !Nbar || !rho || !rhobar || !A_out)
+    return fail(nullptr, EMU_EINVAL, "a particle array or A_out is NULL");
+  if (!std::isfinite(pos_dt)) return fail(nullptr, EMU_EINVAL, "pos_dt must be finite");
+  Geo g;
+  g.nz = cfg->nz;
+  g.M = cfg->ndir;
+  g.P = (int64_t)cfg->nz * cfg->ndir;
+  chunking(cfg, g.ntiles, g.nchunks, g.dchunk);
+  g.Lz = cfg->Lz;
+  g.dz = cfg->Lz / cfg->nz;
+  g.inv_dz = 1.0 / g.dz;
+  g.nz_d = (double)cfg->nz;
+  g.half_nz = 0.5 * cfg->nz;
+  g.dV = g.dz * cfg->area;
+  // carve the static array: partial sums, counters, error word, direction table, shifts
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+  const size_t o_partial = take(g.nchunks > 1 ? sizeof(double) * (size_t)g.nchunks * kNA * (size_t)g.ntiles * kTile : 8);
+  const size_t o_counters = take(sizeof(unsigned) * (size_t)g.ntiles);
+  const size_t o_err = take(sizeof(int));
+  const size_t o_dirtab = take(sizeof(double) * 4 * (size_t)g.M);
+  const size_t o_shift = take(sizeof(int) * (size_t)g.M);
+  if (off > kStaticScratchBytes)
+    return fail(nullptr, EMU_EINVAL,
+                "emu_deposit_static: this box needs %zu bytes of scratch, more than the %zu-byte static array "
+                "(use emu_deposit with a caller workspace)", off, kStaticScratchBytes);
+  void* base = nullptr;
+  if (int rc = static_scratch_address(&base)) return rc;
+  char* s = (char*)base;
+  double* partial = (double*)(s + o_partial);
+  unsigned* counters = (unsigned*)(s + o_counters);
+  int* err = (int*)(s + o_err);
+  double* dirtab = (double*)(s + o_dirtab);
+  int* shift = (int*)(s + o_shift);
+  cudaStream_t st = (cudaStream_t)stream;
+  auto check = [&](cudaError_t e, const char* what) {
+    return e == cudaSuccess ? EMU_OK : fail(nullptr, EMU_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  };
+  // the counters and the error word must start at zero; the array keeps what the last call left
+  if (int rc = check(cudaMemsetAsync(counters, 0, o_dirtab - o_counters, st), "clear static scratch")) return rc;
+  Parts pt{const_cast<double*>(z), const_cast<double*>(ox), const_cast<double*>(oy), const_cast<double*>(oz),
+           const_cast<double*>(N), const_cast<double*>(Nbar), const_cast<double*>(rho),
+           const_cast<double*>(rhobar), nullptr, nullptr};
+  const int pblocks = (int)((g.P + kThreads - 1) / kThreads);
+  k_dirtable<<<pblocks, kThreads, 0, st>>>(pt, g, cfg->c_light, dirtab, err);
+  if (int rc = check(cudaGetLastError(), "direction table kernel")) return rc;
+  Offsets o{};
+  o.v[0] = pos_dt;
+  k_shifts<<<(g.M + kThreads - 1) / kThreads, kThreads, 0, st>>>(z, dirtab, g, o, 1, shift);
+  if (int rc = check(cudaGetLastError(), "shift kernel")) return rc;
+  k_deposit<0><<<tile_grid(g), kThreads, 0, st>>>(z, N, Nbar, rho, rhobar, dirtab, shift, pos_dt, g, partial,
+                                                  counters, A_out, cfg->kappa / g.dV, err);
+  if (int rc = check(cudaGetLastError(), "deposit kernel")) return rc;
+  int h = 0;
+  if (int rc = check(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st), "read error word")) return rc;
+  if (int rc = check(cudaStreamSynchronize(st), "synchronise")) return rc;
+  if (h & ERR_RING) return fail(nullptr, EMU_ELATTICE, "a ring of particles does not share one direction");
+  if (h & ERR_LATTICE) return fail(nullptr, EMU_ELATTICE, "a particle is off its lattice site");
+  if (h & ERR_NONFINITE) return fail(nullptr, EMU_ENUMERIC, "non-finite value on the grid");
+  return EMU_OK;
+}

@@ -90,6 +90,7 @@ def load(build_if_missing: bool = False):
         "emu_kernel_launches": (i64, [vp]),
         "emu_profile": (i32, [vp, i32]),
         "emu_kernel_times": (i32, [vp, vp, vp]),
+        "emu_deposit_static": (i32, [cfgp] + [vp] * 8 + [dbl, vp, vp]),
         "emu_last_error": (ctypes.c_char_p, [vp]),
         "emu_destroy": (None, [vp]),
     }
@@ -204,6 +205,15 @@ def emu_kernel_times(box):
     cnt = np.zeros(4, np.int64)
     _check(box, load().emu_kernel_times(box, _host_ptr(ms), cnt.ctypes.data_as(ctypes.c_void_p)))
     return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def emu_deposit_static(cfg: emu_config, z, ox, oy, oz, N, Nbar, rho, rhobar, pos_dt: float, A_out, stream_ptr):
+    """Deposit into A_out ([36][nz], device) using the library's static scratch
+    instead of a caller workspace, for callers that cannot allocate device
+    memory.  Synchronises the stream.  Calls that overlap on the GPU race."""
+    rc = load().emu_deposit_static(ctypes.byref(cfg), z, ox, oy, oz, N, Nbar, rho, rhobar, float(pos_dt),
+                                   A_out, stream_ptr)
+    _check(None, rc)
 
 
 def emu_last_error(box) -> str:
