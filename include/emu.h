@@ -99,7 +99,7 @@ typedef struct {
 } emu_particles;
 
 /* Bytes of device workspace a box with this configuration needs (grid,
- * moments, per-direction tables, deposit partial sums, counters, error word).
+ * moments, per-direction tables, deposit partial sums, error word).
  * Returns a negative code for an invalid configuration. */
 int64_t emu_workspace_bytes(const emu_config* cfg);
 
@@ -181,9 +181,9 @@ int64_t emu_kernel_launches(const emu_box* box);
 /* Per-launch device timing.  With enable != 0 every later kernel launch of
  * the box is bracketed by two CUDA events recorded on the box's stream.
  * emu_kernel_times synchronises the stream, writes the summed duration [ms]
- * and the number of recorded launches of each kernel class to ms_out[4] and
- * count_out[4] (0: lattice-shift table, 1: deposit, 2: RK stage, 3: other),
- * and clears the record.  Timing is a measurement aid with no other effect. */
+ * and the number of recorded launches of each kernel class to ms_out[5] and
+ * count_out[5] (0: lattice-shift table, 1: deposit, 2: RK stage, 3: deposit
+ * combination, 4: other), and clears the record.  Timing is a measurement aid with no other effect. */
 int emu_profile(emu_box* box, int enable);
 int emu_kernel_times(emu_box* box, double* ms_out, int64_t* count_out);
 
@@ -193,20 +193,21 @@ int emu_kernel_times(emu_box* box, double* ms_out, int64_t* count_out);
  * library's allocation-free section, or code that must not touch an
  * allocator while a memory pool is being resized.  They cannot provide the
  * workspace emu_bind needs, so this call keeps the deposit's scratch (direction
- * table, lattice shifts, partial sums, tile counters, error word) in one
- * static 16 MiB device array of the library, which every GPU that loads the
+ * table, lattice shifts, partial sums, error word) in one
+ * static 32 MiB device array of the library, which every GPU that loads the
  * library holds until the process exits.
  *   - Inputs: cfg and the device particle arrays laid out as in emu_particles
  *     (rho/rhobar as [9][P]); output: A_out, a device array [36][nz] that
  *     receives the grid potential A (as emu_deposit) of the state at positions
  *     z + pos_dt * c * Omega_z.  stream is a cudaStream_t (NULL: legacy stream).
- *   - A box whose scratch does not fit in 16 MiB (more than about 400,000
- *     directions, or partial sums beyond the array) is rejected with
+ *   - The scratch needs 21 MB of per-warp partial sums, 8.6 KB per 30-cell
+ *     tile and 36 bytes per direction; a box that does not fit in 32 MiB
+ *     (roughly nz above 43,000 or ndir above 340,000) is rejected with
  *     EMU_EINVAL before any device work.
  *   - The first call on a device looks up the array's device address on that
  *     device (cudaGetSymbolAddress); make that first call before any stream
- *     capture.  The call clears the counters it needs, runs the deposit,
- *     then synchronises the stream to report lattice or non-finite errors.
+ *     capture.  The call clears the error word, runs the deposit, then
+ *     synchronises the stream to report lattice or non-finite errors.
  *   - All calls on a device share the one array, which keeps whatever the last
  *     call left in it: calls that overlap on the GPU (other streams, other host
  *     threads) race on it and must be serialised by the caller.

@@ -46,6 +46,13 @@ constexpr int kNM = 72;           // components of the per-species moments
 constexpr int kTargetBlocks = 4 * 152;  // 4 resident blocks on each of GB300's 152 SMs
 constexpr double kLatticeTol = 1e-6;    // allowed distance from the lattice site, in cells
 constexpr unsigned kFull = 0xffffffffu;
+// Persistent schedule of the step kernels: a fixed grid of 2 blocks per SM
+// (the kernels use up to 128 registers per thread), whose warps split the
+// U = ntiles * ndir warp-units (one cell tile x one direction) into equal
+// contiguous ranges.  The split depends only on (nz, ndir), never on the
+// device, so the deposit's summation order is fixed.
+constexpr int kPersistBlocks = 2 * 152;
+constexpr int kPersistWarps = kPersistBlocks * kWarps;
 
 enum : int { ERR_LATTICE = 1, ERR_NONFINITE = 2, ERR_WEIGHT = 4, ERR_RING = 8 };
 
@@ -81,6 +88,16 @@ __device__ __forceinline__ int shape_weights(double zs, int h, const Geo& g, dou
   wr = (0.5 * u) * u;
   return fabs(d) > 0.5 + kLatticeTol;
 }
+
+// The persistent split: the U units go to nw = min(kPersistWarps, U) warps
+// (so every working warp owns at least one unit); first unit of warp w, and
+// the warp that owns unit x.
+__device__ __forceinline__ int64_t split_warps(int64_t U) { return U < kPersistWarps ? U : kPersistWarps; }
+__device__ __forceinline__ int64_t unit_begin(int64_t w, int64_t U) {
+  const int64_t nw = split_warps(U);
+  return w >= nw ? U : w * U / nw;
+}
+__device__ __forceinline__ int64_t warp_of_unit(int64_t x, int64_t U) { return ((x + 1) * split_warps(U) - 1) / U; }
 
 // Periodic wrap into [0, Lz).
 __device__ __forceinline__ double wrap_z(double z, double Lz) {
@@ -157,109 +174,107 @@ __global__ void k_shifts(const double* __restrict__ z, const double* __restrict_
   }
 }
 
+constexpr int kSlot = kNA * kTile;  // doubles in one warp's partial sums for one tile
+
+// A warp's sums for one tile go to slot (warp + tile) of the partial buffer:
+// unique, because a later warp never returns to an earlier tile.
+__device__ __forceinline__ void flush_tile(const double (&acc)[kNA], int tile, int64_t w, int lane, const Geo& g,
+                                           double* __restrict__ partial) {
+  const int cell = tile * kTile + lane - 1;
+  if (lane >= 1 && lane <= kTile && cell < g.nz) {
+    double* slot = partial + (w + tile) * kSlot + lane - 1;
+#pragma unroll
+    for (int c = 0; c < kNA; ++c) slot[c * kTile] = acc[c];
+  }
+}
+
 // Deposit (Eq. 5).  MODE 0: B = N rho - Nbar rhobar^* (the combination that
 // enters H, Eq. 2); MODE 1: B = N rho; MODE 2: B = Nbar rhobar.  Writes
-// out[c * nz + j] = out_scale * sum_p w_pj (1, Omega_p) B_p.
+// out[c * nz + j] = out_scale * sum_p w_pj (1, Omega_p) B_p, in two launches:
+// each warp walks its units in order, summing over directions in registers
+// (lane l owns cell tile * 30 - 1 + l) and writing one partial per tile it
+// touches; k_combine then adds the partials in a fixed order.
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 2)
 k_deposit(const double* __restrict__ z, const double* __restrict__ N, const double* __restrict__ Nbar,
           const double* __restrict__ r_nu, const double* __restrict__ r_nb,
           const double* __restrict__ dirtab, const int* __restrict__ shift, double pos_dt, Geo g,
-          double* __restrict__ partial, unsigned* __restrict__ counters, double* __restrict__ out,
-          double out_scale, int* __restrict__ err) {
-  __shared__ double red[kWarps][9][kLanes];
-  __shared__ int s_last;
-  const int tile = blockIdx.x, chunk = blockIdx.y;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+          double* __restrict__ partial, int* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   const int nz = g.nz, M = g.M;
   const int64_t P = g.P;
-  const int craw = tile * kTile - 1 + lane;
-  const int j = wrapc(craw, nz);
-
-  double acc[kNA];
-#pragma unroll
-  for (int c = 0; c < kNA; ++c) acc[c] = 0.0;
+  const int64_t U = (int64_t)g.ntiles * M;
+  const int64_t u0 = unit_begin(w, U), u1 = unit_begin(w + 1, U);
+  if (u0 >= u1) return;
 
   int bad = 0;
-  const int d0 = chunk * g.dchunk, d1 = min(d0 + g.dchunk, M);
-  for (int d = d0 + warp; d < d1; d += kWarps) {
-    const double ox = __ldg(dirtab + d), oy = __ldg(dirtab + M + d), oz = __ldg(dirtab + 2 * M + d);
-    const double vz = __ldg(dirtab + 3 * M + d);
-    const int i = wrapc(j - __ldg(shift + d), nz);
-    const int64_t p = (int64_t)d * nz + i;
-    double wl, w0, wr;
-    bad |= shape_weights(fma(pos_dt, vz, __ldg(z + p)), j, g, wl, w0, wr);
-    // cell j receives wr from the particle at j-1, w0 from its own, wl from j+1
-    const double wr_l = __shfl_up_sync(kFull, wr, 1);
-    const double wl_r = __shfl_down_sync(kFull, wl, 1);
-    const double n1 = (MODE != 2) ? __ldg(N + p) : 0.0;
-    const double n2 = (MODE != 1) ? __ldg(Nbar + p) : 0.0;
+  for (int64_t u = u0; u < u1;) {        // one segment per tile the warp touches
+    const int tile = (int)(u / M);
+    const int64_t uend = min(u1, (int64_t)(tile + 1) * M);
+    const int j = wrapc(tile * kTile - 1 + lane, nz);
+    double acc[kNA];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      double b;
-      if (MODE == 0) {
-        const double x = __ldg(r_nu + k * P + p), y = __ldg(r_nb + k * P + p);
-        // conj(rhobar) flips the sign of the imaginary components 4, 6, 8
-        b = (k == 4 || k == 6 || k == 8) ? fma(n2, y, n1 * x) : fma(-n2, y, n1 * x);
-      } else if (MODE == 1) {
-        b = n1 * __ldg(r_nu + k * P + p);
-      } else {
-        b = n2 * __ldg(r_nb + k * P + p);
+    for (int c = 0; c < kNA; ++c) acc[c] = 0.0;
+    for (; u < uend; ++u) {
+      const int d = (int)(u - (int64_t)tile * M);
+      const double ox = __ldg(dirtab + d), oy = __ldg(dirtab + M + d), oz = __ldg(dirtab + 2 * M + d);
+      const double vz = __ldg(dirtab + 3 * M + d);
+      const int64_t p = (int64_t)d * nz + wrapc(j - __ldg(shift + d), nz);
+      double wl, w0, wr;
+      bad |= shape_weights(fma(pos_dt, vz, __ldg(z + p)), j, g, wl, w0, wr);
+      // cell j receives wr from the particle at j-1, w0 from its own, wl from j+1
+      const double wr_l = __shfl_up_sync(kFull, wr, 1);
+      const double wl_r = __shfl_down_sync(kFull, wl, 1);
+      const double n1 = (MODE != 2) ? __ldg(N + p) : 0.0;
+      const double n2 = (MODE != 1) ? __ldg(Nbar + p) : 0.0;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        double b;
+        if (MODE == 0) {
+          const double x = __ldg(r_nu + k * P + p), y = __ldg(r_nb + k * P + p);
+          // conj(rhobar) flips the sign of the imaginary components 4, 6, 8
+          b = (k == 4 || k == 6 || k == 8) ? fma(n2, y, n1 * x) : fma(-n2, y, n1 * x);
+        } else if (MODE == 1) {
+          b = n1 * __ldg(r_nu + k * P + p);
+        } else {
+          b = n2 * __ldg(r_nb + k * P + p);
+        }
+        const double bl = __shfl_up_sync(kFull, b, 1);
+        const double br = __shfl_down_sync(kFull, b, 1);
+        const double c = fma(wr_l, bl, fma(w0, b, wl_r * br));
+        acc[k] += c;
+        acc[9 + k] = fma(ox, c, acc[9 + k]);
+        acc[18 + k] = fma(oy, c, acc[18 + k]);
+        acc[27 + k] = fma(oz, c, acc[27 + k]);
       }
-      const double bl = __shfl_up_sync(kFull, b, 1);
-      const double br = __shfl_down_sync(kFull, b, 1);
-      const double c = fma(wr_l, bl, fma(w0, b, wl_r * br));
-      acc[k] += c;
-      acc[9 + k] = fma(ox, c, acc[9 + k]);
-      acc[18 + k] = fma(oy, c, acc[18 + k]);
-      acc[27 + k] = fma(oz, c, acc[27 + k]);
     }
+    flush_tile(acc, tile, w, lane, g, partial);
   }
   if (bad) atomicOr(err, ERR_LATTICE);
+}
 
-  const int ncell_pad = g.ntiles * kTile;
-  const bool single = g.nchunks == 1;
-#pragma unroll
-  for (int grp = 0; grp < 4; ++grp) {
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < 9; ++k) red[warp][k][lane] = acc[grp * 9 + k];
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < 9 * kLanes; idx += kThreads) {
-      const int k = idx / kLanes, l = idx % kLanes;
-      const int cell = tile * kTile - 1 + l;
-      if (l >= 1 && l <= kTile && cell < nz) {
-        double s = 0.0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) s += red[w][k][l];
-        const int comp = grp * 9 + k;
-        if (single) {
-          s *= out_scale;
-          if (!isfinite(s)) atomicOr(err, ERR_NONFINITE);
-          out[(int64_t)comp * nz + cell] = s;
-        } else {
-          partial[((int64_t)chunk * kNA + comp) * ncell_pad + cell] = s;
-        }
-      }
-    }
+// Fixed-order combination of the deposit's per-warp partial sums:
+// out[c * nz + j] = scale * (sum over the warps that own units of j's tile, in
+// warp order, of their slot value).
+__global__ void k_combine(const double* __restrict__ partial, Geo g, double* __restrict__ out, double scale,
+                          int* __restrict__ err) {
+  const int64_t U = (int64_t)g.ntiles * g.M;
+  const int64_t n = (int64_t)kNA * g.nz;
+  int bad = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / g.nz), cell = (int)(e - (int64_t)c * g.nz);
+    const int tile = cell / kTile, k = cell - tile * kTile;
+    const int64_t wf = warp_of_unit((int64_t)tile * g.M, U);
+    const int64_t wl = warp_of_unit((int64_t)(tile + 1) * g.M - 1, U);
+    const double* src = partial + c * kTile + k;
+    double v = 0.0;
+    for (int64_t q = wf; q <= wl; ++q) v += __ldcg(src + (q + tile) * kSlot);
+    v *= scale;
+    bad |= !isfinite(v);
+    out[e] = v;
   }
-  if (single) return;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(counters + tile, 1u) == (unsigned)(g.nchunks - 1);
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  for (int idx = threadIdx.x; idx < kNA * kTile; idx += kThreads) {
-    const int comp = idx / kTile, cell = tile * kTile + idx % kTile;
-    if (cell >= nz) continue;
-    double s = 0.0;
-    for (int ch = 0; ch < g.nchunks; ++ch) s += __ldcg(partial + ((int64_t)ch * kNA + comp) * ncell_pad + cell);
-    s *= out_scale;
-    if (!isfinite(s)) atomicOr(err, ERR_NONFINITE);
-    out[(int64_t)comp * nz + cell] = s;
-  }
-  if (threadIdx.x == 0) counters[tile] = 0;
+  if (bad) atomicOr(err, ERR_NONFINITE);
 }
 
 // Load the potential of cells tile*30-1 .. tile*30+30 into shared memory.
@@ -310,18 +325,17 @@ k_interpolate(const double* __restrict__ z, const double* __restrict__ dirtab, c
 //   s = 2: acc += dt/3 K,     stage = y + dt/2 K
 //   s = 3: acc += dt/3 K,     stage = y + dt K
 //   s = 4: y = acc + dt/6 K,  z = wrap(z + dt v_z)
+// Persistent: each warp walks its contiguous range of (tile, direction) units;
+// the potential of a tile stays in L1 across the directions of that tile.
 __global__ void __launch_bounds__(kThreads, 2)
 k_rk_stage(Parts pt, const double* __restrict__ dirtab, const int* __restrict__ shift,
            const double* __restrict__ A, Geo g, int s, double dt, int* __restrict__ err) {
-  __shared__ double sA[kNA][kLanes];
-  const int tile = blockIdx.x, chunk = blockIdx.y;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   const int nz = g.nz, M = g.M;
   const int64_t P = g.P;
-  load_tile(sA, A, tile, nz);
-  __syncthreads();
-  const int craw = tile * kTile - 1 + lane, j = wrapc(craw, nz);
-  const bool active = lane >= 1 && lane <= kTile && craw < nz;
+  const int64_t U = (int64_t)g.ntiles * M;
+  const int64_t u0 = unit_begin(w, U), u1 = unit_begin(w + 1, U);
   const double pos_dt = (s == 1) ? 0.0 : (s == 4 ? dt : 0.5 * dt);
   const double bdt = (s == 1 || s == 4) ? dt / 6.0 : dt / 3.0;   // weight of K in acc
   const double cdt = (s == 3) ? dt : 0.5 * dt;                    // offset of the next stage
@@ -329,8 +343,11 @@ k_rk_stage(Parts pt, const double* __restrict__ dirtab, const int* __restrict__ 
   const double* src_r = (s == 1) ? pt.rho : pt.stage;
   const double* src_b = (s == 1) ? pt.rhobar : pt.stage + 9 * P;
   int bad = 0;
-  const int d0 = chunk * g.dchunk, d1 = min(d0 + g.dchunk, M);
-  for (int d = d0 + warp; d < d1; d += kWarps) {
+  for (int64_t u = u0; u < u1; ++u) {
+    const int tile = (int)(u / M);
+    const int d = (int)(u - (int64_t)tile * M);
+    const int craw = tile * kTile - 1 + lane, j = wrapc(craw, nz);
+    const bool active = lane >= 1 && lane <= kTile && craw < nz;
     const double ox = __ldg(dirtab + d), oy = __ldg(dirtab + M + d), oz = __ldg(dirtab + 2 * M + d);
     const double vz = __ldg(dirtab + 3 * M + d);
     const int64_t p = (int64_t)d * nz + wrapc(j - __ldg(shift + d), nz);
@@ -342,7 +359,9 @@ k_rk_stage(Parts pt, const double* __restrict__ dirtab, const int* __restrict__ 
     double H[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      const double G = fma(-oz, sA[27 + k][lane], fma(-oy, sA[18 + k][lane], fma(-ox, sA[9 + k][lane], sA[k][lane])));
+      const double G = fma(-oz, __ldg(A + (int64_t)(27 + k) * nz + j),
+                           fma(-oy, __ldg(A + (int64_t)(18 + k) * nz + j),
+                               fma(-ox, __ldg(A + (int64_t)(9 + k) * nz + j), __ldg(A + (int64_t)k * nz + j))));
       const double gl = __shfl_up_sync(kFull, G, 1), gr = __shfl_down_sync(kFull, G, 1);
       H[k] = fma(wl, gl, fma(w0, G, wr * gr));
     }
@@ -524,7 +543,7 @@ __global__ void k_diagnostics(const double* __restrict__ mom, int nz, double* __
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t A, mom, partial, counters, err, dirtab, shift, species, dirs, scalar, diag, total;
+  size_t A, mom, partial, err, dirtab, shift, species, dirs, scalar, diag, total;
 };
 
 void chunking(const emu_config* c, int& ntiles, int& nchunks, int& dchunk) {
@@ -545,8 +564,7 @@ Layout layout(const emu_config* c) {
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
   L.A = take(sizeof(double) * kNA * nz);
   L.mom = take(sizeof(double) * kNM * nz);
-  L.partial = take(nchunks > 1 ? sizeof(double) * (size_t)nchunks * kNA * (size_t)ntiles * kTile : 8);
-  L.counters = take(sizeof(unsigned) * (size_t)ntiles);
+  L.partial = take(sizeof(double) * (size_t)(kPersistWarps + ntiles) * kNA * kTile);
   L.err = take(sizeof(int));
   L.dirtab = take(sizeof(double) * 4 * M);
   L.shift = take(sizeof(int) * 4 * M);
@@ -585,7 +603,6 @@ struct emu_box {
   char* ws = nullptr;
   double *A = nullptr, *mom = nullptr, *partial = nullptr, *dirtab = nullptr, *species = nullptr,
          *dirs = nullptr, *scalar = nullptr, *diag = nullptr;
-  unsigned* counters = nullptr;
   int *err = nullptr, *shift = nullptr;
   int next_stage = 1;
   double stage_dt = 0.0;
@@ -621,7 +638,7 @@ int cuda_check(emu_box* b, cudaError_t e, const char* what) {
   return fail(b, EMU_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-enum : int { CLS_SHIFT = 0, CLS_DEPOSIT = 1, CLS_RK = 2, CLS_OTHER = 3, N_CLS = 4 };
+enum : int { CLS_SHIFT = 0, CLS_DEPOSIT = 1, CLS_RK = 2, CLS_COMBINE = 3, CLS_OTHER = 4, N_CLS = 5 };
 
 cudaEvent_t take_event(emu_box* b) {
   if (!b->pool.empty()) { cudaEvent_t e = b->pool.back(); b->pool.pop_back(); return e; }
@@ -648,6 +665,12 @@ int after_launch(emu_box* b, const char* what) {
 }
 
 dim3 tile_grid(const Geo& g) { return dim3((unsigned)g.ntiles, (unsigned)g.nchunks, 1); }
+dim3 persist_grid() { return dim3((unsigned)kPersistBlocks, 1, 1); }
+unsigned combine_blocks(const Geo& g) {
+  const int64_t n = (int64_t)kNA * g.nz;
+  const int64_t blocks = (n + kThreads - 1) / kThreads;
+  return (unsigned)(blocks < 4 * kPersistBlocks ? blocks : 4 * kPersistBlocks);
+}
 
 int launch_shifts(emu_box* b, const double* offs, int nrows) {
   Offsets o{};
@@ -663,15 +686,18 @@ int launch_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, c
   const Geo& g = b->g;
   before_launch(b, CLS_DEPOSIT);
   if (mode == 0)
-    k_deposit<0><<<tile_grid(g), kThreads, 0, b->stream>>>(b->pt.z, b->pt.N, b->pt.Nbar, rnu, rnb, b->dirtab,
-        shift_row, pos_dt, g, b->partial, b->counters, out, scale, b->err);
+    k_deposit<0><<<persist_grid(), kThreads, 0, b->stream>>>(b->pt.z, b->pt.N, b->pt.Nbar, rnu, rnb, b->dirtab,
+        shift_row, pos_dt, g, b->partial, b->err);
   else if (mode == 1)
-    k_deposit<1><<<tile_grid(g), kThreads, 0, b->stream>>>(b->pt.z, b->pt.N, b->pt.Nbar, rnu, rnb, b->dirtab,
-        shift_row, pos_dt, g, b->partial, b->counters, out, scale, b->err);
+    k_deposit<1><<<persist_grid(), kThreads, 0, b->stream>>>(b->pt.z, b->pt.N, b->pt.Nbar, rnu, rnb, b->dirtab,
+        shift_row, pos_dt, g, b->partial, b->err);
   else
-    k_deposit<2><<<tile_grid(g), kThreads, 0, b->stream>>>(b->pt.z, b->pt.N, b->pt.Nbar, rnu, rnb, b->dirtab,
-        shift_row, pos_dt, g, b->partial, b->counters, out, scale, b->err);
-  return after_launch(b, "deposit kernel");
+    k_deposit<2><<<persist_grid(), kThreads, 0, b->stream>>>(b->pt.z, b->pt.N, b->pt.Nbar, rnu, rnb, b->dirtab,
+        shift_row, pos_dt, g, b->partial, b->err);
+  if (int rc = after_launch(b, "deposit kernel")) return rc;
+  before_launch(b, CLS_COMBINE);
+  k_combine<<<combine_blocks(g), kThreads, 0, b->stream>>>(b->partial, g, out, scale, b->err);
+  return after_launch(b, "deposit combine kernel");
 }
 
 int check_bound(emu_box* b) {
@@ -774,7 +800,6 @@ int emu_bind(emu_box* b, const emu_particles* parts, void* workspace, int64_t wo
   b->A = (double*)(b->ws + L.A);
   b->mom = (double*)(b->ws + L.mom);
   b->partial = (double*)(b->ws + L.partial);
-  b->counters = (unsigned*)(b->ws + L.counters);
   b->err = (int*)(b->ws + L.err);
   b->dirtab = (double*)(b->ws + L.dirtab);
   b->shift = (int*)(b->ws + L.shift);
@@ -902,7 +927,7 @@ int emu_rk_stage(emu_box* b, int s, double dt) {
   const int* srow = b->shift + (size_t)(s - 1) * b->g.M;
   if (int rc = launch_deposit(b, 0, rnu, rnb, srow, pos, b->A, b->cfg.kappa / b->g.dV)) return rc;
   before_launch(b, CLS_RK);
-  k_rk_stage<<<tile_grid(b->g), kThreads, 0, b->stream>>>(b->pt, b->dirtab, srow, b->A, b->g, s, dt, b->err);
+  k_rk_stage<<<persist_grid(), kThreads, 0, b->stream>>>(b->pt, b->dirtab, srow, b->A, b->g, s, dt, b->err);
   if (int rc = after_launch(b, "RK stage kernel")) return rc;
   b->next_stage = s == 4 ? 1 : s + 1;
   return EMU_OK;
@@ -1006,12 +1031,12 @@ void emu_destroy(emu_box* b) { delete b; }
 // (for example while a memory pool is being torn down or resized).  They
 // cannot provide the workspace that emu_bind expects, so this entry point
 // keeps the deposit's scratch (per-direction table, lattice shifts, partial
-// sums over direction chunks, tile counters, error word) in one static device
+// sums of the warps, error word) in one static device
 // array that the library itself holds on every GPU that loads it.
 
 namespace {
 
-constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // 16 MiB per device
+constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // 32 MiB per device
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -1058,11 +1083,10 @@ extern "C" int emu_deposit_static(const emu_config* cfg, const double* z, const 
   g.nz_d = (double)cfg->nz;
   g.half_nz = 0.5 * cfg->nz;
   g.dV = g.dz * cfg->area;
-  // carve the static array: partial sums, counters, error word, direction table, shifts
+  // carve the static array: partial sums, error word, direction table, shifts
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
-  const size_t o_partial = take(g.nchunks > 1 ? sizeof(double) * (size_t)g.nchunks * kNA * (size_t)g.ntiles * kTile : 8);
-  const size_t o_counters = take(sizeof(unsigned) * (size_t)g.ntiles);
+  const size_t o_partial = take(sizeof(double) * (size_t)(kPersistWarps + g.ntiles) * kNA * kTile);
   const size_t o_err = take(sizeof(int));
   const size_t o_dirtab = take(sizeof(double) * 4 * (size_t)g.M);
   const size_t o_shift = take(sizeof(int) * (size_t)g.M);
@@ -1074,7 +1098,6 @@ extern "C" int emu_deposit_static(const emu_config* cfg, const double* z, const 
   if (int rc = static_scratch_address(&base)) return rc;
   char* s = (char*)base;
   double* partial = (double*)(s + o_partial);
-  unsigned* counters = (unsigned*)(s + o_counters);
   int* err = (int*)(s + o_err);
   double* dirtab = (double*)(s + o_dirtab);
   int* shift = (int*)(s + o_shift);
@@ -1082,8 +1105,8 @@ extern "C" int emu_deposit_static(const emu_config* cfg, const double* z, const 
   auto check = [&](cudaError_t e, const char* what) {
     return e == cudaSuccess ? EMU_OK : fail(nullptr, EMU_ECUDA, "%s: %s", what, cudaGetErrorString(e));
   };
-  // the counters and the error word must start at zero; the array keeps what the last call left
-  if (int rc = check(cudaMemsetAsync(counters, 0, o_dirtab - o_counters, st), "clear static scratch")) return rc;
+  // the error word must start at zero; the array keeps what the last call left
+  if (int rc = check(cudaMemsetAsync(err, 0, sizeof(int), st), "clear static scratch")) return rc;
   Parts pt{const_cast<double*>(z), const_cast<double*>(ox), const_cast<double*>(oy), const_cast<double*>(oz),
            const_cast<double*>(N), const_cast<double*>(Nbar), const_cast<double*>(rho),
            const_cast<double*>(rhobar), nullptr, nullptr};
@@ -1094,9 +1117,11 @@ extern "C" int emu_deposit_static(const emu_config* cfg, const double* z, const 
   o.v[0] = pos_dt;
   k_shifts<<<(g.M + kThreads - 1) / kThreads, kThreads, 0, st>>>(z, dirtab, g, o, 1, shift);
   if (int rc = check(cudaGetLastError(), "shift kernel")) return rc;
-  k_deposit<0><<<tile_grid(g), kThreads, 0, st>>>(z, N, Nbar, rho, rhobar, dirtab, shift, pos_dt, g, partial,
-                                                  counters, A_out, cfg->kappa / g.dV, err);
+  k_deposit<0><<<persist_grid(), kThreads, 0, st>>>(z, N, Nbar, rho, rhobar, dirtab, shift, pos_dt, g, partial,
+                                                  err);
   if (int rc = check(cudaGetLastError(), "deposit kernel")) return rc;
+  k_combine<<<combine_blocks(g), kThreads, 0, st>>>(partial, g, A_out, cfg->kappa / g.dV, err);
+  if (int rc = check(cudaGetLastError(), "deposit combine kernel")) return rc;
   int h = 0;
   if (int rc = check(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st), "read error word")) return rc;
   if (int rc = check(cudaStreamSynchronize(st), "synchronise")) return rc;

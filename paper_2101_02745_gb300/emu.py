@@ -192,7 +192,7 @@ def emu_kernel_launches(box) -> int:
     return int(load().emu_kernel_launches(box))
 
 
-KERNEL_CLASSES = ("shifts", "deposit", "rk_stage", "other")
+KERNEL_CLASSES = ("shifts", "deposit", "rk_stage", "combine", "other")
 
 
 def emu_profile(box, enable: bool):
@@ -201,8 +201,8 @@ def emu_profile(box, enable: bool):
 
 def emu_kernel_times(box):
     """{class: (total_ms, launches)} recorded since profiling was enabled."""
-    ms = np.zeros(4)
-    cnt = np.zeros(4, np.int64)
+    ms = np.zeros(len(KERNEL_CLASSES))
+    cnt = np.zeros(len(KERNEL_CLASSES), np.int64)
     _check(box, load().emu_kernel_times(box, _host_ptr(ms), cnt.ctypes.data_as(ctypes.c_void_p)))
     return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
