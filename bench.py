@@ -38,18 +38,20 @@ UNIT = "particle-updates/s"
 B_ALG_PER_UPDATE = 313 * 8
 # Algorithmic FP64 flops per particle of one RK-stage launch (FMA = 2), counted
 # from the formulation the kernel implements: G = A0 - Omega.A at the own cell
-# (54), shape weights (13), 3-tap interpolation (45), diagonal differences (3),
-# two packed Hermitian commutators (162), RK update (72; stage 4: 36 + 2 for z).
-FLOPS_RK = {1: 349, 2: 349, 3: 349, 4: 315}
-# ... and of one deposit launch: position and weights (15), B = N rho - Nbar rhobar^* (27),
-# 3-tap gather (45), accumulation of (1, Omega) x C (63).
-FLOPS_DEPOSIT = 150
+# (54), 3-tap interpolation with the deposit's shape weights (45), diagonal
+# differences (3), two packed Hermitian commutators (162), RK update (72;
+# stage 4: 36 + 2 for z).
+FLOPS_RK = {1: 336, 2: 336, 3: 336, 4: 302}
+# ... and of one deposit launch: position and shape weights (12), B = N rho -
+# Nbar rhobar^* (27), 3-tap gather (45), accumulation of (1, Omega) x C (63).
+FLOPS_DEPOSIT = 147
 # FP64 pipe: 2 DFMA per clock per SM (nominal 1.25 TFLOP/s / (2 flop x 152 SMs x 2.07 GHz) = 1.99),
 # so peak = 2 x 2 flop x 152 SMs x 2.07 GHz.
 PEAK_FP64_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
-# Bytes per particle of one launch: RK stage (average over s = 1..4 of 55, 91, 91, 56 doubles), deposit (21).
-BYTES_RK = (55 + 91 + 91 + 56) / 4 * 8
-BYTES_DEPOSIT = 21 * 8
+# Bytes per particle of one launch: RK stage (average over s = 1..4 of 57, 93, 93, 59
+# doubles, the shape weights included), deposit (21 read + 3 weights written).
+BYTES_RK = (57 + 93 + 93 + 59) / 4 * 8
+BYTES_DEPOSIT = 24 * 8
 
 
 def measured_peaks():
@@ -148,6 +150,13 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
+def workload(args):
+    from paper_2101_02745_gb300 import workloads as W
+    if args.workload == "throughput_1d" and (args.nz or args.ndir):
+        return W.throughput_1d(nz=args.nz or 16384, ndir=args.ndir or 1000)
+    return W.by_name(args.workload)
+
+
 # ------------------------------------------------------------ CPU oracle
 
 def oracle_rate(wl, steps: int):
@@ -179,7 +188,7 @@ def run_reference(args, rank, world):
     from oracle import oracle as O
     from paper_2101_02745_gb300 import workloads as W
     O.build()
-    wl = W.by_name(args.workload)
+    wl = workload(args)
     sample = W.head(wl, args.ref_cells)
     cfg = O.config(sample.nz, sample.ndir, sample.Lz, sample.kappa, sample.c_light, sample.cfl_adv,
                    sample.cfl_flavor, sample.area)
@@ -225,7 +234,7 @@ def run_gpu(args, rank, world, local_rank):
     if rank != 0:
         B.build()  # no-op once rank 0 built it
 
-    wl = W.by_name(args.workload)
+    wl = workload(args)
     box = E.Box.from_workload(wl, device=device)
     stream = box.stream
     dt = box.timestep()
@@ -331,6 +340,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="throughput_1d",
                     choices=["throughput_1d", "paper_1d", "paper_1d_asym", "tiny_fiducial"])
+    ap.add_argument("--nz", type=int, default=0, help="cells of the throughput workload (profiling runs)")
+    ap.add_argument("--ndir", type=int, default=0, help="directions of the throughput workload (profiling runs)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-cells", type=int, default=256, help="cells per oracle step in --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")

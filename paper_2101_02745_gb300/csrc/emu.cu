@@ -74,19 +74,33 @@ __device__ __forceinline__ int wrapc(int j, int nz) {
 }
 
 // Quadratic shape weights (Sec. 2.2.1) of a particle at (unwrapped) position zs
-// whose lattice site is cell h: d = zs/dz - (h + 1/2) reduced to the nearest
-// periodic image, weights 1/2 (1/2 - d)^2, 3/4 - d^2, 1/2 (1/2 + d)^2 on cells
-// h-1, h, h+1.  Returns nonzero if the particle is off its lattice site.
-__device__ __forceinline__ int shape_weights(double zs, int h, const Geo& g, double& wl, double& w0,
+// whose lattice site is cell h (hp = h + 1/2): d = zs/dz - hp reduced to the
+// nearest periodic image, weights 1/2 (1/2 - d)^2, 3/4 - d^2, 1/2 (1/2 + d)^2 on
+// cells h-1, h, h+1, written as 1/8 + (d^2 -+ d)/2 and 3/4 - d^2.  The image
+// reduction is only needed next to the domain ends, so it sits behind the
+// lattice test.  Returns nonzero if the particle is off its lattice site.
+__device__ __forceinline__ int shape_weights(double zs, double hp, const Geo& g, double& wl, double& w0,
                                              double& wr) {
-  double d = fma(zs, g.inv_dz, -((double)h + 0.5));
-  if (d > g.half_nz) d -= g.nz_d;
-  else if (d < -g.half_nz) d += g.nz_d;
-  const double t = 0.5 - d, u = 0.5 + d;
-  wl = (0.5 * t) * t;
-  w0 = fma(-d, d, 0.75);
-  wr = (0.5 * u) * u;
-  return fabs(d) > 0.5 + kLatticeTol;
+  double d = fma(zs, g.inv_dz, -hp);
+  int bad = 0;
+  if (fabs(d) > 0.5 + kLatticeTol) {
+    d -= g.nz_d * rint(d / g.nz_d);
+    bad = fabs(d) > 0.5 + kLatticeTol;
+  }
+  const double d2 = d * d;
+  w0 = 0.75 - d2;
+  wl = fma(0.5, d2 - d, 0.125);
+  wr = fma(0.5, d2 + d, 0.125);
+  return bad;
+}
+
+// Bulk prefetch of the doubles [i0, i0 + n) of array a into L2 (a hint; the
+// range is rounded inwards to 16-byte boundaries so it never leaves the array).
+__device__ __forceinline__ void prefetch_l2(const double* a, int64_t i0, int n) {
+  uintptr_t lo = ((uintptr_t)(a + i0) + 15) & ~(uintptr_t)15;
+  uintptr_t hi = ((uintptr_t)(a + i0 + n)) & ~(uintptr_t)15;
+  if (hi > lo)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
 }
 
 // The persistent split: the U units go to nw = min(kPersistWarps, U) warps
@@ -199,7 +213,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 k_deposit(const double* __restrict__ z, const double* __restrict__ N, const double* __restrict__ Nbar,
           const double* __restrict__ r_nu, const double* __restrict__ r_nb,
           const double* __restrict__ dirtab, const int* __restrict__ shift, double pos_dt, Geo g,
-          double* __restrict__ partial, int* __restrict__ err) {
+          double* __restrict__ partial, double* __restrict__ W, int* __restrict__ err) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   const int nz = g.nz, M = g.M;
@@ -212,7 +226,10 @@ k_deposit(const double* __restrict__ z, const double* __restrict__ N, const doub
   for (int64_t u = u0; u < u1;) {        // one segment per tile the warp touches
     const int tile = (int)(u / M);
     const int64_t uend = min(u1, (int64_t)(tile + 1) * M);
-    const int j = wrapc(tile * kTile - 1 + lane, nz);
+    const int craw = tile * kTile - 1 + lane;
+    const int j = wrapc(craw, nz);
+    const double hp = (double)j + 0.5;
+    const bool own = lane >= 1 && lane <= kTile && craw < nz;
     double acc[kNA];
 #pragma unroll
     for (int c = 0; c < kNA; ++c) acc[c] = 0.0;
@@ -222,7 +239,12 @@ k_deposit(const double* __restrict__ z, const double* __restrict__ N, const doub
       const double vz = __ldg(dirtab + 3 * M + d);
       const int64_t p = (int64_t)d * nz + wrapc(j - __ldg(shift + d), nz);
       double wl, w0, wr;
-      bad |= shape_weights(fma(pos_dt, vz, __ldg(z + p)), j, g, wl, w0, wr);
+      bad |= shape_weights(fma(pos_dt, vz, __ldg(z + p)), hp, g, wl, w0, wr);
+      if (MODE == 0 && W != nullptr && own) {   // the RK stage of these positions reads them back
+        W[p] = wl;
+        W[P + p] = w0;
+        W[2 * P + p] = wr;
+      }
       // cell j receives wr from the particle at j-1, w0 from its own, wl from j+1
       const double wr_l = __shfl_up_sync(kFull, wr, 1);
       const double wl_r = __shfl_down_sync(kFull, wl, 1);
@@ -306,7 +328,7 @@ k_interpolate(const double* __restrict__ z, const double* __restrict__ dirtab, c
     const double vz = __ldg(dirtab + 3 * M + d);
     const int64_t p = (int64_t)d * nz + wrapc(j - __ldg(shift + d), nz);
     double wl = 0.0, w0 = 0.0, wr = 0.0;
-    if (active) bad |= shape_weights(fma(pos_dt, vz, z[p]), j, g, wl, w0, wr);
+    if (active) bad |= shape_weights(fma(pos_dt, vz, z[p]), (double)j + 0.5, g, wl, w0, wr);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       const double G = fma(-oz, sA[27 + k][lane], fma(-oy, sA[18 + k][lane], fma(-ox, sA[9 + k][lane], sA[k][lane])));
@@ -325,36 +347,59 @@ k_interpolate(const double* __restrict__ z, const double* __restrict__ dirtab, c
 //   s = 2: acc += dt/3 K,     stage = y + dt/2 K
 //   s = 3: acc += dt/3 K,     stage = y + dt K
 //   s = 4: y = acc + dt/6 K,  z = wrap(z + dt v_z)
-// Persistent: each warp walks its contiguous range of (tile, direction) units;
-// the potential of a tile stays in L1 across the directions of that tile.
+// Persistent: each warp walks its contiguous range of units direction-major
+// (unit u = direction u / ntiles, tile u % ntiles), so it streams along each
+// ring, and prefetches the next unit's particle data into L2.  The shape
+// weights of these positions come from the deposit that precedes the stage.
 __global__ void __launch_bounds__(kThreads, 2)
-k_rk_stage(Parts pt, const double* __restrict__ dirtab, const int* __restrict__ shift,
-           const double* __restrict__ A, Geo g, int s, double dt, int* __restrict__ err) {
+k_rk_stage(Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
+           const int* __restrict__ shift, const double* __restrict__ A, Geo g, int s, double dt) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-  const int nz = g.nz, M = g.M;
+  const int nz = g.nz, M = g.M, nt = g.ntiles;
   const int64_t P = g.P;
-  const int64_t U = (int64_t)g.ntiles * M;
+  const int64_t U = (int64_t)nt * M;
   const int64_t u0 = unit_begin(w, U), u1 = unit_begin(w + 1, U);
-  const double pos_dt = (s == 1) ? 0.0 : (s == 4 ? dt : 0.5 * dt);
   const double bdt = (s == 1 || s == 4) ? dt / 6.0 : dt / 3.0;   // weight of K in acc
   const double cdt = (s == 3) ? dt : 0.5 * dt;                    // offset of the next stage
   const double bdt2 = 2.0 * bdt, cdt2 = 2.0 * cdt;                // diagonal K are returned halved
   const double* src_r = (s == 1) ? pt.rho : pt.stage;
   const double* src_b = (s == 1) ? pt.rhobar : pt.stage + 9 * P;
-  int bad = 0;
+  // arrays this stage reads, for the prefetch: source (18), y (18, s = 2, 3), acc (18, s >= 2), W (3), z (s = 4)
+  const int nsrc = 18, ny = (s == 2 || s == 3) ? 18 : 0, nacc = (s >= 2) ? 18 : 0;
+  const int narr = nsrc + ny + nacc + 3 + (s == 4 ? 1 : 0);
   for (int64_t u = u0; u < u1; ++u) {
-    const int tile = (int)(u / M);
-    const int d = (int)(u - (int64_t)tile * M);
+    const int d = (int)(u / nt);
+    const int tile = (int)(u - (int64_t)d * nt);
+    if (u + 1 < u1) {
+      const int dn = (int)((u + 1) / nt);
+      const int tn = (int)(u + 1 - (int64_t)dn * nt);
+      const int i0 = tn * kTile - __ldg(shift + dn);           // ring index of the next unit's first cell
+      const int n = min(kTile, nz - tn * kTile);
+      if (i0 >= 0 && i0 + n <= nz) {
+        const int64_t base = (int64_t)dn * nz + i0;
+        for (int a = lane; a < narr; a += kLanes) {
+          const double* arr;
+          if (a < nsrc) arr = (a < 9 ? src_r + (int64_t)a * P : src_b + (int64_t)(a - 9) * P);
+          else if (a < nsrc + ny) arr = (a - nsrc < 9 ? pt.rho + (int64_t)(a - nsrc) * P
+                                                      : pt.rhobar + (int64_t)(a - nsrc - 9) * P);
+          else if (a < nsrc + ny + nacc) arr = pt.acc + (int64_t)(a - nsrc - ny) * P;
+          else if (a < nsrc + ny + nacc + 3) arr = W + (int64_t)(a - nsrc - ny - nacc) * P;
+          else arr = pt.z;
+          prefetch_l2(arr, base, n);
+        }
+      }
+    }
     const int craw = tile * kTile - 1 + lane, j = wrapc(craw, nz);
     const bool active = lane >= 1 && lane <= kTile && craw < nz;
     const double ox = __ldg(dirtab + d), oy = __ldg(dirtab + M + d), oz = __ldg(dirtab + 2 * M + d);
     const double vz = __ldg(dirtab + 3 * M + d);
     const int64_t p = (int64_t)d * nz + wrapc(j - __ldg(shift + d), nz);
-    double z0 = 0.0, wl = 0.0, w0 = 0.0, wr = 0.0;
+    double wl = 0.0, w0 = 0.0, wr = 0.0;
     if (active) {
-      z0 = pt.z[p];
-      bad |= shape_weights(fma(pos_dt, vz, z0), j, g, wl, w0, wr);
+      wl = W[p];
+      w0 = W[P + p];
+      wr = W[2 * P + p];
     }
     double H[9];
 #pragma unroll
@@ -403,9 +448,8 @@ k_rk_stage(Parts pt, const double* __restrict__ dirtab, const int* __restrict__ 
         for (int k = 0; k < 6; ++k) yv[(k + 3) * P + p] = fma(bdt, ko[k], av[(k + 3) * P + p]);
       }
     }
-    if (s == 4) pt.z[p] = wrap_z(fma(dt, vz, z0), g.Lz);
+    if (s == 4) pt.z[p] = wrap_z(fma(dt, vz, pt.z[p]), g.Lz);
   }
-  if (bad) atomicOr(err, ERR_LATTICE);
 }
 
 // SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): n-th output of the generator
@@ -543,7 +587,7 @@ __global__ void k_diagnostics(const double* __restrict__ mom, int nz, double* __
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t A, mom, partial, err, dirtab, shift, species, dirs, scalar, diag, total;
+  size_t A, mom, partial, W, err, dirtab, shift, species, dirs, scalar, diag, total;
 };
 
 void chunking(const emu_config* c, int& ntiles, int& nchunks, int& dchunk) {
@@ -565,6 +609,7 @@ Layout layout(const emu_config* c) {
   L.A = take(sizeof(double) * kNA * nz);
   L.mom = take(sizeof(double) * kNM * nz);
   L.partial = take(sizeof(double) * (size_t)(kPersistWarps + ntiles) * kNA * kTile);
+  L.W = take(sizeof(double) * 3 * nz * M);
   L.err = take(sizeof(int));
   L.dirtab = take(sizeof(double) * 4 * M);
   L.shift = take(sizeof(int) * 4 * M);
@@ -601,7 +646,7 @@ struct emu_box {
   bool bound = false;
   cudaStream_t stream = nullptr;
   char* ws = nullptr;
-  double *A = nullptr, *mom = nullptr, *partial = nullptr, *dirtab = nullptr, *species = nullptr,
+  double *A = nullptr, *mom = nullptr, *partial = nullptr, *W = nullptr, *dirtab = nullptr, *species = nullptr,
          *dirs = nullptr, *scalar = nullptr, *diag = nullptr;
   int *err = nullptr, *shift = nullptr;
   int next_stage = 1;
@@ -687,13 +732,13 @@ int launch_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, c
   before_launch(b, CLS_DEPOSIT);
   if (mode == 0)
     k_deposit<0><<<persist_grid(), kThreads, 0, b->stream>>>(b->pt.z, b->pt.N, b->pt.Nbar, rnu, rnb, b->dirtab,
-        shift_row, pos_dt, g, b->partial, b->err);
+        shift_row, pos_dt, g, b->partial, b->W, b->err);
   else if (mode == 1)
     k_deposit<1><<<persist_grid(), kThreads, 0, b->stream>>>(b->pt.z, b->pt.N, b->pt.Nbar, rnu, rnb, b->dirtab,
-        shift_row, pos_dt, g, b->partial, b->err);
+        shift_row, pos_dt, g, b->partial, nullptr, b->err);
   else
     k_deposit<2><<<persist_grid(), kThreads, 0, b->stream>>>(b->pt.z, b->pt.N, b->pt.Nbar, rnu, rnb, b->dirtab,
-        shift_row, pos_dt, g, b->partial, b->err);
+        shift_row, pos_dt, g, b->partial, nullptr, b->err);
   if (int rc = after_launch(b, "deposit kernel")) return rc;
   before_launch(b, CLS_COMBINE);
   k_combine<<<combine_blocks(g), kThreads, 0, b->stream>>>(b->partial, g, out, scale, b->err);
@@ -800,6 +845,7 @@ int emu_bind(emu_box* b, const emu_particles* parts, void* workspace, int64_t wo
   b->A = (double*)(b->ws + L.A);
   b->mom = (double*)(b->ws + L.mom);
   b->partial = (double*)(b->ws + L.partial);
+  b->W = (double*)(b->ws + L.W);
   b->err = (int*)(b->ws + L.err);
   b->dirtab = (double*)(b->ws + L.dirtab);
   b->shift = (int*)(b->ws + L.shift);
@@ -927,7 +973,7 @@ int emu_rk_stage(emu_box* b, int s, double dt) {
   const int* srow = b->shift + (size_t)(s - 1) * b->g.M;
   if (int rc = launch_deposit(b, 0, rnu, rnb, srow, pos, b->A, b->cfg.kappa / b->g.dV)) return rc;
   before_launch(b, CLS_RK);
-  k_rk_stage<<<persist_grid(), kThreads, 0, b->stream>>>(b->pt, b->dirtab, srow, b->A, b->g, s, dt, b->err);
+  k_rk_stage<<<persist_grid(), kThreads, 0, b->stream>>>(b->pt, b->W, b->dirtab, srow, b->A, b->g, s, dt);
   if (int rc = after_launch(b, "RK stage kernel")) return rc;
   b->next_stage = s == 4 ? 1 : s + 1;
   return EMU_OK;
@@ -1118,7 +1164,7 @@ extern "C" int emu_deposit_static(const emu_config* cfg, const double* z, const 
   k_shifts<<<(g.M + kThreads - 1) / kThreads, kThreads, 0, st>>>(z, dirtab, g, o, 1, shift);
   if (int rc = check(cudaGetLastError(), "shift kernel")) return rc;
   k_deposit<0><<<persist_grid(), kThreads, 0, st>>>(z, N, Nbar, rho, rhobar, dirtab, shift, pos_dt, g, partial,
-                                                  err);
+                                                  nullptr, err);
   if (int rc = check(cudaGetLastError(), "deposit kernel")) return rc;
   k_combine<<<combine_blocks(g), kThreads, 0, st>>>(partial, g, A_out, cfg->kappa / g.dV, err);
   if (int rc = check(cudaGetLastError(), "deposit combine kernel")) return rc;
