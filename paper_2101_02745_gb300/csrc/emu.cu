@@ -401,6 +401,12 @@ k_rk_stage(Parts pt, const double* __restrict__ W, const double* __restrict__ di
       w0 = W[P + p];
       wr = W[2 * P + p];
     }
+    // the neutrino source matrix first, so its latency overlaps the interpolation
+    double r[9];
+    if (active) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) r[k] = src_r[k * P + p];
+    }
     double H[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
@@ -415,37 +421,49 @@ k_rk_stage(Parts pt, const double* __restrict__ W, const double* __restrict__ di
     // neutrinos: H;  antineutrinos: Hbar = -H^*  (diagonal differences and real parts flip sign)
 #pragma unroll
     for (int which = 0; which < 2; ++which) {
-      const double* src = which ? src_b : src_r;
-      double r[9];
+      double* __restrict__ yv = which ? pt.rhobar : pt.rho;
+      double* __restrict__ av = pt.acc + which * 9 * P;
+      double* __restrict__ sv = pt.stage + which * 9 * P;
+      // all loads of this matrix before any store (the arrays do not alias)
+      double a[9], y[9];
+      if (s >= 2) {
 #pragma unroll
-      for (int k = 0; k < 9; ++k) r[k] = src[k * P + p];
+        for (int k = 0; k < 9; ++k) a[k] = av[k * P + p];
+      }
+      if (s == 2 || s == 3) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) y[k] = yv[k * P + p];
+      }
+      double rb[9];
+      if (which == 1) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) rb[k] = src_b[k * P + p];
+      }
+      const double* rr = which ? rb : r;
       double kd[3], ko[6];
-      if (which == 0) commutator(d12, d13, d23, H[3], H[4], H[5], H[6], H[7], H[8], r, kd, ko);
-      else commutator(-d12, -d13, -d23, -H[3], H[4], -H[5], H[6], -H[7], H[8], r, kd, ko);
-      double* yv = which ? pt.rhobar : pt.rho;
-      double* av = pt.acc + which * 9 * P;
-      double* sv = pt.stage + which * 9 * P;
+      if (which == 0) commutator(d12, d13, d23, H[3], H[4], H[5], H[6], H[7], H[8], rr, kd, ko);
+      else commutator(-d12, -d13, -d23, -H[3], H[4], -H[5], H[6], -H[7], H[8], rr, kd, ko);
       if (s == 1) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) { av[k * P + p] = fma(bdt2, kd[k], r[k]); sv[k * P + p] = fma(cdt2, kd[k], r[k]); }
-#pragma unroll
-        for (int k = 0; k < 6; ++k) { av[(k + 3) * P + p] = fma(bdt, ko[k], r[k + 3]); sv[(k + 3) * P + p] = fma(cdt, ko[k], r[k + 3]); }
-      } else if (s < 4) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          av[k * P + p] = fma(bdt2, kd[k], av[k * P + p]);
-          sv[k * P + p] = fma(cdt2, kd[k], yv[k * P + p]);
-        }
+        for (int k = 0; k < 3; ++k) { av[k * P + p] = fma(bdt2, kd[k], rr[k]); sv[k * P + p] = fma(cdt2, kd[k], rr[k]); }
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-          av[(k + 3) * P + p] = fma(bdt, ko[k], av[(k + 3) * P + p]);
-          sv[(k + 3) * P + p] = fma(cdt, ko[k], yv[(k + 3) * P + p]);
+          av[(k + 3) * P + p] = fma(bdt, ko[k], rr[k + 3]);
+          sv[(k + 3) * P + p] = fma(cdt, ko[k], rr[k + 3]);
+        }
+      } else if (s < 4) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { av[k * P + p] = fma(bdt2, kd[k], a[k]); sv[k * P + p] = fma(cdt2, kd[k], y[k]); }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          av[(k + 3) * P + p] = fma(bdt, ko[k], a[k + 3]);
+          sv[(k + 3) * P + p] = fma(cdt, ko[k], y[k + 3]);
         }
       } else {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) yv[k * P + p] = fma(bdt2, kd[k], av[k * P + p]);
+        for (int k = 0; k < 3; ++k) yv[k * P + p] = fma(bdt2, kd[k], a[k]);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) yv[(k + 3) * P + p] = fma(bdt, ko[k], av[(k + 3) * P + p]);
+        for (int k = 0; k < 6; ++k) yv[(k + 3) * P + p] = fma(bdt, ko[k], a[k + 3]);
       }
     }
     if (s == 4) pt.z[p] = wrap_z(fma(dt, vz, pt.z[p]), g.Lz);
