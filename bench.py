@@ -333,13 +333,91 @@ def run_gpu(args, rank, world, local_rank):
     return 0
 
 
+def run_sweep(args, rank, world, local_rank):
+    """Batched parameter sweep: 256 independent boxes of uneven sizes advanced
+    by one set of launches per step (CUDA graph replay, autotuned grid),
+    against the same boxes advanced one box at a time with the single-box
+    calls.  Both time K steps with CUDA events on the same stream."""
+    import numpy as np
+    import torch
+
+    from paper_2101_02745_gb300 import build as B
+    from paper_2101_02745_gb300 import emu as E
+    from paper_2101_02745_gb300 import workloads as W
+
+    if rank == 0:
+        B.build()
+    dist = dist_init(world, True)
+    device = torch.device("cuda", local_rank)
+    torch.cuda.set_device(device)
+    barrier(dist, device)
+    wls = W.sweep(args.nbox, seed=rank)
+    P = sum(w.P for w in wls)
+    batch = E.Box.from_workloads(wls, device=device)
+    dts = batch.batch_timestep()
+    choice, cand_ms = batch.autotune(trial_steps=2)
+    batch.batch_step(args.warmup)
+    stream = batch.stream
+    barrier(dist, device)
+    torch.cuda.synchronize(device)
+    clocks = ClockSampler(device.index).start()
+    n0 = batch.launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    batch.batch_step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize(device)
+    batched_ms = max_over_ranks(dist, ev0.elapsed_time(ev1), device)
+    launches = batch.launches() - n0
+    batch.sync()
+    del batch
+    torch.cuda.empty_cache()
+    # the same boxes one at a time, same step sizes, same stream
+    singles = [E.Box.from_workload(w, device=device) for w in wls]
+    for s_, dt in zip(singles, dts):
+        s_.step(args.warmup, dt)
+    torch.cuda.synchronize(device)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        for s_, dt in zip(singles, dts):
+            s_.step(1, dt)
+    ev1.record(stream)
+    torch.cuda.synchronize(device)
+    single_ms = max_over_ranks(dist, ev0.elapsed_time(ev1), device)
+    clk = clocks.stop()
+    for s_ in singles:
+        s_.sync()
+    value = world * P * args.steps / (batched_ms * 1e-3)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": batched_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"sweep_{args.nbox}_boxes", "boxes": args.nbox, "particles_per_gpu": P,
+                       "nz_range": [64, 1024], "ndir_range": [48, 378],
+                       "l2": "inputs larger than L2 (particle state %.1f GB per GPU)" % (P * 480 / 1e9)},
+            "batched": {"value": value, "ms_per_step": batched_ms / args.steps, "launches_per_step":
+                        launches / args.steps, "autotune_choice": choice, "autotune_ms": list(cand_ms)},
+            "one_at_a_time": {"value": world * P * args.steps / (single_ms * 1e-3),
+                              "ms_per_step": single_ms / args.steps},
+            "speedup": single_ms / batched_ms,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="throughput_1d",
-                    choices=["throughput_1d", "paper_1d", "paper_1d_asym", "tiny_fiducial"])
+                    choices=["throughput_1d", "paper_1d", "paper_1d_asym", "tiny_fiducial", "sweep"])
+    ap.add_argument("--nbox", type=int, default=256, help="boxes of the sweep workload")
     ap.add_argument("--nz", type=int, default=0, help="cells of the throughput workload (profiling runs)")
     ap.add_argument("--ndir", type=int, default=0, help="directions of the throughput workload (profiling runs)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
@@ -351,6 +429,8 @@ def main(argv=None):
     rank, world, local_rank = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "sweep":
+        return run_sweep(args, rank, world, local_rank)
     return run_gpu(args, rank, world, local_rank)
 
 

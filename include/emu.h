@@ -172,6 +172,66 @@ int emu_diagnostics(emu_box* box, double* out, int on_host);
  * diagonal components of n and nbar).  Synchronises. */
 int emu_timestep(emu_box* box, double* dt_out);
 
+/* ---------------------------------------------------------------- batches
+ * A batch is nbox independent boxes of any sizes (the parameter sweeps of
+ * Sec. 4 run many such boxes) advanced together by the same kernel launches.
+ * A box created by emu_create is a batch of one.  All arrays of a batch are
+ * concatenated box after box: the particles of box b occupy
+ * [poff_b, poff_b + nz_b * ndir_b) of every emu_particles array (poff_b = sum of
+ * the earlier boxes' particle counts; particle (d, i) of box b is
+ * poff_b + d * nz_b + i; component k of a matrix array at [k * Ptot + p]); grid
+ * columns likewise with cell offsets coff_b.  emu_bind, emu_set/get_particles,
+ * emu_moments (72 x total cells), emu_sync and the timing calls work on batches;
+ * the calls that take one dt or return one value (emu_init_particles,
+ * emu_deposit, emu_interpolate_H, emu_rk_stage, emu_step, emu_timestep,
+ * emu_diagnostics) need a batch of one. */
+
+/* Totals of a batch: particles, cells, workspace bytes (negative on error). */
+int64_t emu_batch_particles(const emu_config* cfgs, int32_t nbox);
+int64_t emu_batch_cells(const emu_config* cfgs, int32_t nbox);
+int64_t emu_batch_workspace_bytes(const emu_config* cfgs, int32_t nbox);
+
+/* Create a batch from nbox configurations (host memory only). */
+int emu_batch_create(const emu_config* cfgs, int32_t nbox, emu_box** out);
+
+/* emu_init_particles for every box (Sec. 3.1, Eq. 8, 9): host arrays
+ * n_nu, n_nubar [total cells], f_nu, f_nubar [3 x total cells] (box after
+ * box), dirs [3 x total directions] or NULL (Fibonacci sphere in every box),
+ * alpha and seed [nbox].  The random draws of box b are keyed by its local
+ * particle numbers, so a box initialises as it would alone. */
+int emu_batch_init_particles(emu_box* box, const double* n_nu, const double* n_nubar, const double* f_nu,
+                             const double* f_nubar, const double* dirs, const double* alpha,
+                             const uint64_t* seed);
+
+/* Eq. 7 for every box from its current state; dt_out [nbox] (may be NULL).
+ * The results become the boxes' step sizes.  Synchronises. */
+int emu_batch_timestep(emu_box* box, double* dt_out);
+
+/* Set the boxes' step sizes dt [nbox] (each positive). */
+int emu_batch_set_dt(emu_box* box, const double* dt);
+
+/* nsteps classic RK4 steps of every box with its own step size (Eq. 7 values
+ * unless set): per step one lattice-shift launch and per stage one deposit,
+ * one deposit combination and one RK-stage launch, each covering all boxes.
+ * On a non-default stream the first call captures one step as a CUDA graph
+ * (make that call outside any other stream capture) and every step replays
+ * it; with per-kernel timing on, or on the legacy default stream, the
+ * kernels are launched directly. */
+int emu_batch_step(emu_box* box, int64_t nsteps);
+
+/* emu_diagnostics of every box: out [nbox][63]. */
+int emu_batch_diagnostics(emu_box* box, double* out, int on_host);
+
+/* Autotuner: times trial_steps steps of each candidate launch configuration
+ * of the step kernels (grids of 304, 152 or 608 blocks of 256 threads, whose
+ * warps split the work) without changing the particle state (the trial steps
+ * write their results into the RK scratch), keeps the fastest for later
+ * steps, and reports its index (0..2) in *choice_out and the per-step times
+ * [ms] of the three candidates in ms_out[3] (either may be NULL).  The
+ * deposit's summation order depends on the choice, so results are bitwise
+ * reproducible for a fixed choice.  Synchronises. */
+int emu_autotune(emu_box* box, int trial_steps, int32_t* choice_out, double* ms_out);
+
 /* Wait for the box's stream and report errors recorded by its kernels. */
 int emu_sync(emu_box* box);
 

@@ -1,0 +1,698 @@
+// kernels.cuh -- GB300 (sm_103a) FP64 device code of the particle-in-cell step
+// for the neutrino fast flavour instability (Richers, Willcox, Ford & Myers,
+// arXiv:2101.02745).  Included once, by emu.cu.
+//
+// A *batch* is a set of independent 1D periodic boxes advanced together; one
+// box is a batch of one.  All arrays of a batch are concatenated:
+//   particles: box b occupies [poff_b, poff_b + nz_b * ndir_b) of every SoA array;
+//              particle (d, i) of box b is poff_b + d * nz_b + i; component k of a
+//              matrix array at [k * Ptot + particle]
+//   grid:      cell j of box b is column coff_b + j of A[36][NZ] and mom[72][NZ]
+//   tables:    direction d of box b is entry doff_b + d of the per-direction tables
+//
+// Parallel layout.  Work is split into *units* = (one 30-cell tile, one
+// direction) of one box: box b has ntiles_b * ndir_b units, numbered box after
+// box.  A warp works on one unit at a time with lane l on cell
+// (tile * 30 - 1 + l): lanes 1..30 own the tile's cells, lanes 0 and 31 are halo
+// lanes that supply the neighbour values of the three-cell stencil.  Because
+// the particles of one direction (a ring) translate rigidly (one per cell at a
+// common offset, Sec. 3.1 and Eq. 4), the particle on cell j is ring entry
+// (j - shift_d) mod nz and its stencil neighbours sit on the adjacent lanes:
+// deposit (Eq. 5) and interpolation (Eq. 6) are warp-shuffle gathers.
+//
+// Persistent schedule.  The step kernels run a fixed grid (2 blocks of 8 warps
+// per SM); the first nw warps split the U units of the batch into equal
+// contiguous ranges.  The deposit's summation order (registers over a warp's
+// directions, one partial per (warp, tile), partials added in warp order by
+// k_combine) depends only on the batch and nw: no atomics, bitwise reproducible.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace emu_dev {
+
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr int kLanes = 32;
+constexpr int kTile = 30;          // cells owned by a warp (lanes 1..30)
+constexpr int kNA = 36;            // components of the grid potential
+constexpr int kNM = 72;            // components of the per-species moments
+constexpr int kSlot = kNA * kTile; // doubles in one warp's partial sums for one tile
+constexpr double kLatticeTol = 1e-6;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kPersistBlocks = 2 * 152;  // default grid: 2 resident blocks on each of GB300's 152 SMs
+constexpr int kMaxBlocks = 4 * 152;      // largest grid the autotuner tries
+constexpr int kMaxWarps = kMaxBlocks * kWarps;
+
+enum : int { ERR_LATTICE = 1, ERR_NONFINITE = 2, ERR_WEIGHT = 4, ERR_RING = 8 };
+
+// One box of a batch (device copy lives in the workspace).
+struct BoxGeo {
+  int nz, M, ntiles, use_dirs;
+  int coff, toff, doff, pad;
+  int64_t P, poff, uoff;
+  double Lz, dz, inv_dz, nz_d, dV, c_light;
+  double kappa_dV;   // kappa / dV: scale of the grid potential
+  double inv_dV;     // 1 / dV: scale of the moments
+  double alpha;      // Eq. 9 perturbation strength (init)
+  uint64_t seed;     // Eq. 9 random stream (init)
+  double cfl_adv, cfl_flavor, kappa;  // Eq. 7
+};
+
+// Kernel view of a batch (passed by value).
+struct Batch {
+  const BoxGeo* box;   // [nbox]
+  const double* dt;    // [nbox] step size of every box
+  int nbox;
+  int nw;              // warps that split the units
+  int NZ, MT, NT;      // total cells, directions, tiles
+  int64_t U, Ptot;     // total units, particles
+};
+
+struct Parts {
+  double *z, *ox, *oy, *oz, *N, *Nbar, *rho, *rhobar, *acc, *stage;
+};
+
+// ------------------------------------------------------------ device helpers
+
+__device__ __forceinline__ int wrapc(int j, int nz) {
+  int r = j % nz;
+  return r < 0 ? r + nz : r;
+}
+
+__device__ __forceinline__ int64_t unit_begin(int64_t w, const Batch& B) {
+  return w >= B.nw ? B.U : w * B.U / B.nw;
+}
+__device__ __forceinline__ int64_t warp_of_unit(int64_t x, const Batch& B) { return ((x + 1) * B.nw - 1) / B.U; }
+
+// Index of the box containing unit u / cell c / particle p / direction d
+// (binary search over the boxes' offsets; all arguments are warp-uniform in
+// the step kernels).
+__device__ __forceinline__ int box_of_unit(const Batch& B, int64_t u) {
+  int lo = 0, hi = B.nbox - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (B.box[mid].uoff <= u) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ int box_of_cell(const Batch& B, int c) {
+  int lo = 0, hi = B.nbox - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (B.box[mid].coff <= c) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ int box_of_particle(const Batch& B, int64_t p) {
+  int lo = 0, hi = B.nbox - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (B.box[mid].poff <= p) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ int box_of_direction(const Batch& B, int d) {
+  int lo = 0, hi = B.nbox - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (B.box[mid].doff <= d) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Quadratic shape weights (Sec. 2.2.1) of a particle at (unwrapped) position zs
+// whose lattice site is cell h (hp = h + 1/2): d = zs/dz - hp reduced to the
+// nearest periodic image, weights 1/2 (1/2 - d)^2, 3/4 - d^2, 1/2 (1/2 + d)^2 on
+// cells h-1, h, h+1, written as 1/8 + (d^2 -+ d)/2 and 3/4 - d^2.  The image
+// reduction is only needed next to the domain ends, so it sits behind the
+// lattice test.  Returns nonzero if the particle is off its lattice site.
+__device__ __forceinline__ int shape_weights(double zs, double hp, double inv_dz, double nz_d, double& wl,
+                                             double& w0, double& wr) {
+  double d = fma(zs, inv_dz, -hp);
+  int bad = 0;
+  if (fabs(d) > 0.5 + kLatticeTol) {
+    d -= nz_d * rint(d / nz_d);
+    bad = fabs(d) > 0.5 + kLatticeTol;
+  }
+  const double d2 = d * d;
+  w0 = 0.75 - d2;
+  wl = fma(0.5, d2 - d, 0.125);
+  wr = fma(0.5, d2 + d, 0.125);
+  return bad;
+}
+
+// Bulk prefetch of the doubles [i0, i0 + n) of array a into L2 (a hint; the
+// range is rounded inwards to 16-byte boundaries so it never leaves the array).
+__device__ __forceinline__ void prefetch_l2(const double* a, int64_t i0, int n) {
+  uintptr_t lo = ((uintptr_t)(a + i0) + 15) & ~(uintptr_t)15;
+  uintptr_t hi = ((uintptr_t)(a + i0 + n)) & ~(uintptr_t)15;
+  if (hi > lo)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
+}
+
+// Periodic wrap into [0, Lz).
+__device__ __forceinline__ double wrap_z(double z, double Lz) {
+  if (z >= Lz) z -= Lz;
+  else if (z < 0.0) {
+    z += Lz;
+    if (z >= Lz) z -= Lz;
+  }
+  return z;
+}
+
+// -i [H, r] for packed Hermitian H and r (Eq. 4 with H in units of hbar).
+// Diagonal outputs are returned HALVED (kd = K_aa / 2); the caller doubles
+// their RK coefficients.  Off-diagonal outputs ko = (Re K12, Im K12, Re K13,
+// Im K13, Re K23, Im K23).  H enters through its diagonal differences
+// d12 = h1 - h2, d13 = h1 - h3, d23 = h2 - h3 and off-diagonals a, b, c.
+__device__ __forceinline__ void commutator(double d12, double d13, double d23, double ar, double ai,
+                                           double br, double bi, double cr, double ci,
+                                           const double r[9], double kd[3], double ko[6]) {
+  const double xr = r[3], xi = r[4], yr = r[5], yi = r[6], zr = r[7], zi = r[8];
+  const double e21 = r[1] - r[0], e31 = r[2] - r[0], e32 = r[2] - r[1];
+  // C = [H, r]; K = -i C  =>  Re K = Im C, Im K = -Re C
+  const double c12r = fma(d12, xr, fma(e21, ar, fma(br, zr, fma(bi, zi, fma(-cr, yr, -ci * yi)))));
+  const double c12i = fma(d12, xi, fma(e21, ai, fma(bi, zr, fma(-br, zi, fma(-cr, yi, ci * yr)))));
+  const double c13r = fma(d13, yr, fma(e31, br, fma(ar, zr, fma(-ai, zi, fma(-cr, xr, ci * xi)))));
+  const double c13i = fma(d13, yi, fma(e31, bi, fma(ar, zi, fma(ai, zr, fma(-cr, xi, -ci * xr)))));
+  const double c23r = fma(d23, zr, fma(e32, cr, fma(ar, yr, fma(ai, yi, fma(-br, xr, -bi * xi)))));
+  const double c23i = fma(d23, zi, fma(e32, ci, fma(ar, yi, fma(-ai, yr, fma(-bi, xr, br * xi)))));
+  ko[0] = c12i; ko[1] = -c12r;
+  ko[2] = c13i; ko[3] = -c13r;
+  ko[4] = c23i; ko[5] = -c23r;
+  // K_11 = 2 (Im(a x*) + Im(b y*)), K_22 = 2 (Im(c z*) - Im(a x*)), K_33 = -2 (Im(b y*) + Im(c z*))
+  const double pp = fma(ai, xr, -ar * xi);
+  const double qq = fma(bi, yr, -br * yi);
+  const double tt = fma(ci, zr, -cr * zi);
+  kd[0] = pp + qq;
+  kd[1] = tt - pp;
+  kd[2] = -qq - tt;
+}
+
+// ------------------------------------------------------------------ kernels
+
+// Per-direction table from each ring's first particle: Omega and v_z = c Omega_z
+// ([4][MT]); also checks that every particle of a ring carries its direction.
+__global__ void k_dirtable(Batch B, Parts pt, double* __restrict__ dirtab, int* __restrict__ err) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= B.Ptot) return;
+  const BoxGeo& g = B.box[box_of_particle(B, p)];
+  const int d = (int)((p - g.poff) / g.nz);
+  const int64_t p0 = g.poff + (int64_t)d * g.nz;
+  const double ox = pt.ox[p0], oy = pt.oy[p0], oz = pt.oz[p0];
+  if (pt.ox[p] != ox || pt.oy[p] != oy || pt.oz[p] != oz) atomicOr(err, ERR_RING);
+  if (p == p0) {
+    const int gd = g.doff + d;
+    dirtab[gd] = ox;
+    dirtab[B.MT + gd] = oy;
+    dirtab[2 * B.MT + gd] = oz;
+    dirtab[3 * B.MT + gd] = g.c_light * oz;
+  }
+}
+
+// Lattice shift of every direction for up to 4 position offsets frac[s] * dt_b:
+// the cell of the ring's first particle at z + frac[s] dt_b v_z ([nrows][MT]).
+struct Fracs { double v[4]; };
+
+__global__ void k_shifts(Batch B, const double* __restrict__ z, const double* __restrict__ dirtab, Fracs fr,
+                         int nrows, int* __restrict__ shift) {
+  const int gd = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gd >= B.MT) return;
+  const int b = box_of_direction(B, gd);
+  const BoxGeo& g = B.box[b];
+  const double z0 = z[g.poff + (int64_t)(gd - g.doff) * g.nz];
+  const double vz = dirtab[3 * B.MT + gd];
+  const double dt = B.dt[b];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (s < nrows) {
+      const double zs = fma(fr.v[s] * dt, vz, z0);
+      shift[s * B.MT + gd] = wrapc((int)floor(zs * g.inv_dz), g.nz);
+    }
+  }
+}
+
+// A warp's sums for one tile go to slot (warp + global tile) of the partial
+// buffer: unique, because a later warp never returns to an earlier tile.
+__device__ __forceinline__ void flush_tile(const double (&acc)[kNA], int64_t gtile, int local_cell, int nz,
+                                           int64_t w, int lane, double* __restrict__ partial) {
+  if (lane >= 1 && lane <= kTile && local_cell < nz) {
+    double* slot = partial + (w + gtile) * kSlot + lane - 1;
+#pragma unroll
+    for (int c = 0; c < kNA; ++c) slot[c * kTile] = acc[c];
+  }
+}
+
+// Deposit (Eq. 5), first launch.  MODE 0: B = N rho - Nbar rhobar^* (the
+// combination that enters H, Eq. 2); MODE 1: B = N rho; MODE 2: B = Nbar rhobar.
+// Each warp walks its units in order (box, tile, direction), summing
+// w_pj (1, Omega_p) B_p over directions in registers (lane l owns cell
+// tile * 30 - 1 + l) and writing one partial per tile it touches; MODE 0 also
+// stores every particle's weights for the RK stage.  Positions: z + frac dt_b v_z.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 2)
+k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, const double* __restrict__ Nbar,
+          const double* __restrict__ r_nu, const double* __restrict__ r_nb, const double* __restrict__ dirtab,
+          const int* __restrict__ shift, double frac, double* __restrict__ partial, double* __restrict__ W,
+          int* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t u0 = unit_begin(w, B), u1 = unit_begin(w + 1, B);
+  if (u0 >= u1) return;
+  const int64_t P = B.Ptot;
+  const int MT = B.MT;
+  int bad = 0;
+  int b = box_of_unit(B, u0);
+  for (int64_t u = u0; u < u1;) {        // one segment per (box, tile) the warp touches
+    while (u >= B.box[b].uoff + (int64_t)B.box[b].ntiles * B.box[b].M) ++b;
+    const BoxGeo& g = B.box[b];
+    const int nz = g.nz, M = g.M;
+    const int tile = (int)((u - g.uoff) / M);
+    const int64_t uend = min(u1, g.uoff + (int64_t)(tile + 1) * M);
+    const int craw = tile * kTile - 1 + lane;
+    const int j = wrapc(craw, nz);
+    const double hp = (double)j + 0.5;
+    const bool own = lane >= 1 && lane <= kTile && craw < nz;
+    const double pos_dt = frac * B.dt[b];
+    const int64_t pbase = g.poff;
+    const int dbase = g.doff;
+    const int64_t ubase = g.uoff + (int64_t)tile * M;
+    const int dfirst = (int)(u - ubase), dlast = (int)(uend - ubase);
+    u = uend;
+    double acc[kNA];
+#pragma unroll
+    for (int c = 0; c < kNA; ++c) acc[c] = 0.0;
+    for (int d = dfirst; d < dlast; ++d) {
+      const int gd = dbase + d;
+      const double ox = __ldg(dirtab + gd), oy = __ldg(dirtab + MT + gd), oz = __ldg(dirtab + 2 * MT + gd);
+      const double vz = __ldg(dirtab + 3 * MT + gd);
+      const int64_t p = pbase + (int64_t)d * nz + wrapc(j - __ldg(shift + gd), nz);
+      double wl, w0, wr;
+      bad |= shape_weights(fma(pos_dt, vz, __ldg(z + p)), hp, __ldg(&g.inv_dz), __ldg(&g.nz_d), wl, w0, wr);
+      if (MODE == 0 && W != nullptr && own) {   // the RK stage of these positions reads them back
+        double* wp = W + p;
+        wp[0] = wl;
+        wp[P] = w0;
+        wp[2 * P] = wr;
+      }
+      // cell j receives wr from the particle at j-1, w0 from its own, wl from j+1
+      const double wr_l = __shfl_up_sync(kFull, wr, 1);
+      const double wl_r = __shfl_down_sync(kFull, wl, 1);
+      const double n1 = (MODE != 2) ? __ldg(N + p) : 0.0;
+      const double n2 = (MODE != 1) ? __ldg(Nbar + p) : 0.0;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        double bv;
+        if (MODE == 0) {
+          const double x = __ldg(r_nu + k * P + p), y = __ldg(r_nb + k * P + p);
+          // conj(rhobar) flips the sign of the imaginary components 4, 6, 8
+          bv = (k == 4 || k == 6 || k == 8) ? fma(n2, y, n1 * x) : fma(-n2, y, n1 * x);
+        } else if (MODE == 1) {
+          bv = n1 * __ldg(r_nu + k * P + p);
+        } else {
+          bv = n2 * __ldg(r_nb + k * P + p);
+        }
+        const double bl = __shfl_up_sync(kFull, bv, 1);
+        const double br = __shfl_down_sync(kFull, bv, 1);
+        const double c = fma(wr_l, bl, fma(w0, bv, wl_r * br));
+        acc[k] += c;
+        acc[9 + k] = fma(ox, c, acc[9 + k]);
+        acc[18 + k] = fma(oy, c, acc[18 + k]);
+        acc[27 + k] = fma(oz, c, acc[27 + k]);
+      }
+    }
+    flush_tile(acc, g.toff + tile, craw, nz, w, lane, partial);
+  }
+  if (bad) atomicOr(err, ERR_LATTICE);
+}
+
+// Deposit, second launch: fixed-order sum of the per-warp partials.
+// out[c * NZ + coff_b + j] = scale_b * (sum over the warps that own units of
+// j's tile, in warp order), scale_b = kappa_b / dV_b (MODE 0) or 1 / dV_b.
+__global__ void k_combine(Batch B, const double* __restrict__ partial, double* __restrict__ out, int potential,
+                          int* __restrict__ err) {
+  const int64_t n = (int64_t)kNA * B.NZ;
+  int bad = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / B.NZ), gc = (int)(e - (int64_t)c * B.NZ);
+    const BoxGeo& g = B.box[box_of_cell(B, gc)];
+    const int lc = gc - g.coff;
+    const int tile = lc / kTile, k = lc - tile * kTile;
+    const int64_t gtile = g.toff + tile;
+    const int64_t wf = warp_of_unit(g.uoff + (int64_t)tile * g.M, B);
+    const int64_t wl = warp_of_unit(g.uoff + (int64_t)(tile + 1) * g.M - 1, B);
+    const double* src = partial + c * kTile + k;
+    double v = 0.0;
+    for (int64_t q = wf; q <= wl; ++q) v += __ldcg(src + (q + gtile) * kSlot);
+    v *= potential ? g.kappa_dV : g.inv_dV;
+    bad |= !isfinite(v);
+    out[e] = v;
+  }
+  if (bad) atomicOr(err, ERR_NONFINITE);
+}
+
+// Interpolation only (Eq. 6 then Eq. 2): H[k * Ptot + p] at z + frac dt_b v_z.
+__global__ void __launch_bounds__(kThreads, 2)
+k_interpolate(Batch B, const double* __restrict__ z, const double* __restrict__ dirtab,
+              const int* __restrict__ shift, const double* __restrict__ A, double frac, double* __restrict__ Hout,
+              int* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t u0 = unit_begin(w, B), u1 = unit_begin(w + 1, B);
+  const int64_t P = B.Ptot;
+  const int MT = B.MT, NZ = B.NZ;
+  int bad = 0;
+  if (u0 >= u1) return;
+  int b = box_of_unit(B, u0);
+  for (int64_t u = u0; u < u1; ++u) {
+    while (u >= B.box[b].uoff + (int64_t)B.box[b].ntiles * B.box[b].M) ++b;
+    const BoxGeo& g = B.box[b];
+    const int nz = g.nz, M = g.M;
+    const int tile = (int)((u - g.uoff) / M), d = (int)(u - g.uoff - (int64_t)tile * M);
+    const int craw = tile * kTile - 1 + lane, j = wrapc(craw, nz);
+    const bool active = lane >= 1 && lane <= kTile && craw < nz;
+    const int gd = g.doff + d;
+    const double ox = __ldg(dirtab + gd), oy = __ldg(dirtab + MT + gd), oz = __ldg(dirtab + 2 * MT + gd);
+    const double vz = __ldg(dirtab + 3 * MT + gd);
+    const int64_t p = g.poff + (int64_t)d * nz + wrapc(j - __ldg(shift + gd), nz);
+    double wl = 0.0, w0 = 0.0, wr = 0.0;
+    if (active)
+      bad |= shape_weights(fma(frac * B.dt[b], vz, z[p]), (double)j + 0.5, g.inv_dz, g.nz_d, wl, w0, wr);
+    const double* Aj = A + g.coff + j;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const double G = fma(-oz, __ldg(Aj + (int64_t)(27 + k) * NZ),
+                           fma(-oy, __ldg(Aj + (int64_t)(18 + k) * NZ),
+                               fma(-ox, __ldg(Aj + (int64_t)(9 + k) * NZ), __ldg(Aj + (int64_t)k * NZ))));
+      const double gl = __shfl_up_sync(kFull, G, 1), gr = __shfl_down_sync(kFull, G, 1);
+      const double h = fma(wl, gl, fma(w0, G, wr * gr));
+      if (active) Hout[k * P + p] = h;
+    }
+  }
+  if (bad) atomicOr(err, ERR_LATTICE);
+}
+
+// One RK4 stage s (1..4) after the deposit of the stage state: interpolate
+// (Eq. 6), H and Hbar = -H^* (Eq. 2, Sec. 2.1), K = -i[H, rho] and
+// Kbar = -i[Hbar, rhobar] (Eq. 4), then the classic RK4 update (Sec. 2.3):
+//   s = 1: acc = y + dt/6 K,  stage = y + dt/2 K
+//   s = 2: acc += dt/3 K,     stage = y + dt/2 K
+//   s = 3: acc += dt/3 K,     stage = y + dt K
+//   s = 4: y = acc + dt/6 K,  z = wrap(z + dt v_z)   (dry: into the stage buffer instead)
+// Persistent: each warp walks its contiguous range of units, direction-major
+// within a box (unit = direction * ntiles + tile) so it streams along each
+// ring, and prefetches the next unit's particle data into L2.  The shape
+// weights come from the deposit.
+__global__ void __launch_bounds__(kThreads, 2)
+k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
+           const int* __restrict__ shift, const double* __restrict__ A, int s, int dry) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t u0 = unit_begin(w, B), u1 = unit_begin(w + 1, B);
+  if (u0 >= u1) return;
+  const int64_t P = B.Ptot;
+  const int MT = B.MT, NZ = B.NZ;
+  const double* src_r = (s == 1) ? pt.rho : pt.stage;
+  const double* src_b = (s == 1) ? pt.rhobar : pt.stage + 9 * P;
+  // arrays this stage reads, for the prefetch: source (18), y (18, s = 2, 3), acc (18, s >= 2), W (3), z (s = 4)
+  const int nsrc = 18, ny = (s == 2 || s == 3) ? 18 : 0, nacc = (s >= 2) ? 18 : 0;
+  const int narr = nsrc + ny + nacc + 3 + (s == 4 ? 1 : 0);
+  int b = box_of_unit(B, u0);
+  double bdt = 0.0, cdt = 0.0;
+  int bcur = -1;
+  for (int64_t u = u0; u < u1; ++u) {
+    while (u >= B.box[b].uoff + (int64_t)B.box[b].ntiles * B.box[b].M) ++b;
+    const BoxGeo& g = B.box[b];
+    const int nz = g.nz, nt = g.ntiles;
+    if (b != bcur) {
+      bcur = b;
+      const double dt = B.dt[b];
+      bdt = (s == 1 || s == 4) ? dt / 6.0 : dt / 3.0;   // weight of K in acc
+      cdt = (s == 3) ? dt : 0.5 * dt;                   // offset of the next stage
+    }
+    const int lu = (int)(u - g.uoff);        // unit within the box: direction-major
+    const int d = lu / nt, tile = lu - d * nt;
+    if (u + 1 < u1 && lu + 1 < nt * g.M) {   // prefetch the next unit of the same box
+      const int dn = (lu + 1) / nt, tn = lu + 1 - dn * nt;
+      const int i0 = tn * kTile - __ldg(shift + g.doff + dn);   // ring index of the next unit's first cell
+      const int n = min(kTile, nz - tn * kTile);
+      if (i0 >= 0 && i0 + n <= nz) {
+        const int64_t base = g.poff + (int64_t)dn * nz + i0;
+        for (int a = lane; a < narr; a += kLanes) {
+          const double* arr;
+          if (a < nsrc) arr = (a < 9 ? src_r + (int64_t)a * P : src_b + (int64_t)(a - 9) * P);
+          else if (a < nsrc + ny) arr = (a - nsrc < 9 ? pt.rho + (int64_t)(a - nsrc) * P
+                                                      : pt.rhobar + (int64_t)(a - nsrc - 9) * P);
+          else if (a < nsrc + ny + nacc) arr = pt.acc + (int64_t)(a - nsrc - ny) * P;
+          else if (a < nsrc + ny + nacc + 3) arr = W + (int64_t)(a - nsrc - ny - nacc) * P;
+          else arr = pt.z;
+          prefetch_l2(arr, base, n);
+        }
+      }
+    }
+    const double bdt2 = 2.0 * bdt, cdt2 = 2.0 * cdt;   // diagonal K are returned halved
+    const int craw = tile * kTile - 1 + lane, j = wrapc(craw, nz);
+    const bool active = lane >= 1 && lane <= kTile && craw < nz;
+    const int gd = g.doff + d;
+    const double ox = __ldg(dirtab + gd), oy = __ldg(dirtab + MT + gd), oz = __ldg(dirtab + 2 * MT + gd);
+    const int64_t p = g.poff + (int64_t)d * nz + wrapc(j - __ldg(shift + gd), nz);
+    double wl = 0.0, w0 = 0.0, wr = 0.0;
+    // the neutrino source matrix first, so its latency overlaps the interpolation
+    double r[9];
+    if (active) {
+      wl = W[p];
+      w0 = W[P + p];
+      wr = W[2 * P + p];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) r[k] = src_r[k * P + p];
+    }
+    double H[9];
+    const double* Aj = A + g.coff + j;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const double G = fma(-oz, __ldg(Aj + (int64_t)(27 + k) * NZ),
+                           fma(-oy, __ldg(Aj + (int64_t)(18 + k) * NZ),
+                               fma(-ox, __ldg(Aj + (int64_t)(9 + k) * NZ), __ldg(Aj + (int64_t)k * NZ))));
+      const double gl = __shfl_up_sync(kFull, G, 1), gr = __shfl_down_sync(kFull, G, 1);
+      H[k] = fma(wl, gl, fma(w0, G, wr * gr));
+    }
+    if (!active) continue;
+    const double d12 = H[0] - H[1], d13 = H[0] - H[2], d23 = H[1] - H[2];
+    // neutrinos: H;  antineutrinos: Hbar = -H^*  (diagonal differences and real parts flip sign)
+#pragma unroll
+    for (int which = 0; which < 2; ++which) {
+      double* __restrict__ yv = which ? pt.rhobar : pt.rho;
+      double* __restrict__ av = pt.acc + which * 9 * P;
+      double* __restrict__ sv = pt.stage + which * 9 * P;
+      // all loads of this matrix before any store (the arrays do not alias)
+      double a[9], y[9], rb[9];
+      if (which == 1) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) rb[k] = src_b[k * P + p];
+      }
+      if (s >= 2) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) a[k] = av[k * P + p];
+      }
+      if (s == 2 || s == 3) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) y[k] = yv[k * P + p];
+      }
+      const double* rr = which ? rb : r;
+      double kd[3], ko[6];
+      if (which == 0) commutator(d12, d13, d23, H[3], H[4], H[5], H[6], H[7], H[8], rr, kd, ko);
+      else commutator(-d12, -d13, -d23, -H[3], H[4], -H[5], H[6], -H[7], H[8], rr, kd, ko);
+      if (s == 1) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { av[k * P + p] = fma(bdt2, kd[k], rr[k]); sv[k * P + p] = fma(cdt2, kd[k], rr[k]); }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          av[(k + 3) * P + p] = fma(bdt, ko[k], rr[k + 3]);
+          sv[(k + 3) * P + p] = fma(cdt, ko[k], rr[k + 3]);
+        }
+      } else if (s < 4) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { av[k * P + p] = fma(bdt2, kd[k], a[k]); sv[k * P + p] = fma(cdt2, kd[k], y[k]); }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          av[(k + 3) * P + p] = fma(bdt, ko[k], a[k + 3]);
+          sv[(k + 3) * P + p] = fma(cdt, ko[k], y[k + 3]);
+        }
+      } else {
+        double* __restrict__ dst = dry ? sv : yv;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dst[k * P + p] = fma(bdt2, kd[k], a[k]);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) dst[(k + 3) * P + p] = fma(bdt, ko[k], a[k + 3]);
+      }
+    }
+    if (s == 4) {
+      const double zn = wrap_z(fma(B.dt[b], __ldg(dirtab + 3 * MT + gd), pt.z[p]), g.Lz);
+      if (dry) pt.stage[p] = zn;  // (only to keep the work of the real stage)
+      else pt.z[p] = zn;
+    }
+  }
+}
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): n-th output of the generator
+// whose state starts at `seed`.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t n) {
+  uint64_t x = seed + n * 0x9E3779B97F4A7C15ULL;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+  return x ^ (x >> 31);
+}
+
+__device__ __forceinline__ double uniform_pm1(uint64_t seed, int64_t p, int k) {
+  const uint64_t h = splitmix64(seed, (uint64_t)p * 8u + (uint64_t)k + 1u);
+  return 2.0 * ((double)(h >> 11) * 0x1.0p-53) - 1.0;
+}
+
+// Initial particles (Sec. 3.1): cell-centre lattice, weights of Eq. 8, flavour
+// state of Eq. 9 (eps_x = |rho_ex|^2, rho_mutau = 0).  Plain roundings (no
+// fused multiply-add) so the weights and states round like the formulas read.
+// Box-local particle numbers key the random draws.  species: per box, at
+// 8 * coff_b: n_nu[nz], n_nubar[nz], f_nu[3 nz], f_nubar[3 nz]; dirs[3 * MT].
+__global__ void k_init(Batch B, Parts pt, const double* __restrict__ species, const double* __restrict__ dirs,
+                       int* __restrict__ err) {
+  const int64_t gp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gp >= B.Ptot) return;
+  const BoxGeo& g = B.box[box_of_particle(B, gp)];
+  const int64_t p = gp - g.poff;
+  const int d = (int)(p / g.nz), j0 = (int)(p % g.nz);
+  double o[3];
+  if (g.use_dirs) {
+    const int gd = g.doff + d;
+    o[0] = dirs[3 * gd]; o[1] = dirs[3 * gd + 1]; o[2] = dirs[3 * gd + 2];
+  } else {
+    const double mu = __dsub_rn(1.0, __ddiv_rn(__dadd_rn(__dmul_rn(2.0, (double)d), 1.0), (double)g.M));
+    const double phi = __dmul_rn(__dmul_rn((double)d, 3.14159265358979323846), __dsub_rn(3.0, sqrt(5.0)));
+    const double sn = sqrt(__dsub_rn(1.0, __dmul_rn(mu, mu)));
+    o[0] = __dmul_rn(sn, cos(phi));
+    o[1] = __dmul_rn(sn, sin(phi));
+    o[2] = mu;
+  }
+  pt.z[gp] = __dmul_rn(__dadd_rn((double)j0, 0.5), g.dz);
+  pt.ox[gp] = o[0]; pt.oy[gp] = o[1]; pt.oz[gp] = o[2];
+  const int nz = g.nz;
+  const double* sp_base = species + 8 * (int64_t)g.coff;
+  double wgt[2];
+  for (int sp = 0; sp < 2; ++sp) {
+    const double n = sp_base[sp * nz + j0];
+    const double* f = sp_base + 2 * nz + sp * 3 * nz + 3 * j0;
+    const double fdo = __dadd_rn(__dadd_rn(__dmul_rn(f[0], o[0]), __dmul_rn(f[1], o[1])), __dmul_rn(f[2], o[2]));
+    double wt = __ddiv_rn(__dmul_rn(__dadd_rn(n, __dmul_rn(3.0, fdo)), g.dV), (double)g.M);
+    const double tol = 1e-12 * (fabs(n) + 3.0 * fabs(fdo)) * g.dV / g.M;
+    if (wt < 0.0 && wt >= -tol) wt = 0.0;
+    if (wt < 0.0) atomicOr(err, ERR_WEIGHT);
+    wgt[sp] = wt;
+  }
+  pt.N[gp] = wgt[0];
+  pt.Nbar[gp] = wgt[1];
+  const int64_t P = B.Ptot;
+  for (int sp = 0; sp < 2; ++sp) {
+    double* r = sp ? pt.rhobar : pt.rho;
+    const double emr = __dmul_rn(g.alpha, uniform_pm1(g.seed, p, 4 * sp + 0));
+    const double emi = __dmul_rn(g.alpha, uniform_pm1(g.seed, p, 4 * sp + 1));
+    const double etr = __dmul_rn(g.alpha, uniform_pm1(g.seed, p, 4 * sp + 2));
+    const double eti = __dmul_rn(g.alpha, uniform_pm1(g.seed, p, 4 * sp + 3));
+    const double eps_mu = __dadd_rn(__dmul_rn(emr, emr), __dmul_rn(emi, emi));
+    const double eps_tau = __dadd_rn(__dmul_rn(etr, etr), __dmul_rn(eti, eti));
+    r[0 * P + gp] = __dsub_rn(__dsub_rn(1.0, eps_mu), eps_tau);
+    r[1 * P + gp] = eps_mu;
+    r[2 * P + gp] = eps_tau;
+    r[3 * P + gp] = emr;
+    r[4 * P + gp] = emi;
+    r[5 * P + gp] = etr;
+    r[6 * P + gp] = eti;
+    r[7 * P + gp] = 0.0;
+    r[8 * P + gp] = 0.0;
+  }
+}
+
+// Per box: maximum over cells of the diagonal components of n and nbar (Eq. 7).
+// One block per box.
+__global__ void k_max_diag(Batch B, const double* __restrict__ mom, double* __restrict__ out) {
+  __shared__ double sm[kThreads];
+  const BoxGeo& g = B.box[blockIdx.x];
+  double m = 0.0;
+  for (int j = threadIdx.x; j < g.nz; j += kThreads)
+    for (int a = 0; a < 3; ++a) {
+      m = fmax(m, mom[(int64_t)a * B.NZ + g.coff + j]);
+      m = fmax(m, mom[(int64_t)(36 + a) * B.NZ + g.coff + j]);
+    }
+  sm[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = sm[0];
+}
+
+// Eq. 7 per box from the maxima: dt_b = min(C dz / c, C_F / (kappa n_max)).
+__global__ void k_dt_from_max(Batch B, const double* __restrict__ nmax, double* __restrict__ dt_out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B.nbox) return;
+  const BoxGeo& g = B.box[b];
+  const double dt_adv = g.cfl_adv * g.dz / g.c_light;
+  const double dt_flav = nmax[b] > 0.0 ? g.cfl_flavor / (g.kappa * nmax[b]) : dt_adv;
+  dt_out[b] = dt_adv < dt_flav ? dt_adv : dt_flav;
+}
+
+// Writes one box descriptor and step size from kernel parameters (used where
+// no host-to-device copy may be issued).
+__global__ void k_write_geo(BoxGeo g, double dt, BoxGeo* __restrict__ dst, double* __restrict__ dt_dst) {
+  *dst = g;
+  *dt_dst = dt;
+}
+
+// Domain diagnostics per box (Eq. 10, one snapshot of Eq. B1, Eq. 18), fixed-
+// order block reduction over the box's cells.  One block per box; out[63 * b + q].
+__device__ __forceinline__ double abs_entry(const double* __restrict__ m, int64_t NZ, int64_t j, int a, int b) {
+  if (a == b) return fabs(m[(int64_t)a * NZ + j]);
+  const int lo = a < b ? a : b, hi = a < b ? b : a;
+  const int k = (lo == 0 && hi == 1) ? 3 : (lo == 0 ? 5 : 7);
+  const double re = m[(int64_t)k * NZ + j], im = m[(int64_t)(k + 1) * NZ + j];
+  return sqrt(re * re + im * im);
+}
+
+__global__ void k_diagnostics(Batch B, const double* __restrict__ mom, double* __restrict__ out) {
+  __shared__ double sm[kThreads];
+  const BoxGeo& g = B.box[blockIdx.x];
+  const int64_t NZ = B.NZ;
+  for (int q = 0; q < 63; ++q) {
+    double s = 0.0;
+    for (int jj = threadIdx.x; jj < g.nz; jj += kThreads) {
+      const int64_t j = g.coff + jj;
+      double v;
+      if (q < 36) {
+        const int blk = q / 9, e = q % 9, a = e / 3, bb = e % 3;
+        const int off = blk == 0 ? 0 : blk == 1 ? 36 : blk == 2 ? 9 : 45;
+        v = abs_entry(mom + (int64_t)off * NZ, NZ, j, a, bb);
+      } else if (q < 45) {
+        v = mom[(int64_t)(q - 36) * NZ + j];
+      } else if (q < 54) {
+        v = mom[(int64_t)(36 + q - 45) * NZ + j];
+      } else {
+        const int k = q - 54;
+        const double nbar = mom[(int64_t)(36 + k) * NZ + j];
+        v = mom[(int64_t)k * NZ + j] + ((k == 4 || k == 6 || k == 8) ? nbar : -nbar);
+      }
+      s += v;
+    }
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[63 * blockIdx.x + q] = sm[0] / g.nz;
+    __syncthreads();
+  }
+}
+
+}  // namespace emu_dev

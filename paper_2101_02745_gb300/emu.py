@@ -91,6 +91,16 @@ def load(build_if_missing: bool = False):
         "emu_profile": (i32, [vp, i32]),
         "emu_kernel_times": (i32, [vp, vp, vp]),
         "emu_deposit_static": (i32, [cfgp] + [vp] * 8 + [dbl, vp, vp]),
+        "emu_batch_particles": (i64, [cfgp, ctypes.c_int32]),
+        "emu_batch_cells": (i64, [cfgp, ctypes.c_int32]),
+        "emu_batch_workspace_bytes": (i64, [cfgp, ctypes.c_int32]),
+        "emu_batch_create": (i32, [cfgp, ctypes.c_int32, ctypes.POINTER(vp)]),
+        "emu_batch_init_particles": (i32, [vp, vp, vp, vp, vp, vp, vp, vp]),
+        "emu_batch_timestep": (i32, [vp, vp]),
+        "emu_batch_set_dt": (i32, [vp, vp]),
+        "emu_batch_step": (i32, [vp, i64]),
+        "emu_batch_diagnostics": (i32, [vp, vp, i32]),
+        "emu_autotune": (i32, [vp, i32, vp, vp]),
         "emu_last_error": (ctypes.c_char_p, [vp]),
         "emu_destroy": (None, [vp]),
     }
@@ -216,6 +226,77 @@ def emu_deposit_static(cfg: emu_config, z, ox, oy, oz, N, Nbar, rho, rhobar, pos
     _check(None, rc)
 
 
+def _cfg_array(cfgs):
+    arr = (emu_config * len(cfgs))(*cfgs)
+    return arr, ctypes.cast(arr, ctypes.POINTER(emu_config))
+
+
+def emu_batch_particles(cfgs) -> int:
+    arr, ptr = _cfg_array(cfgs)
+    n = load().emu_batch_particles(ptr, len(cfgs))
+    if n < 0:
+        raise EmuError(int(n), "invalid configuration")
+    return int(n)
+
+
+def emu_batch_cells(cfgs) -> int:
+    arr, ptr = _cfg_array(cfgs)
+    n = load().emu_batch_cells(ptr, len(cfgs))
+    if n < 0:
+        raise EmuError(int(n), "invalid configuration")
+    return int(n)
+
+
+def emu_batch_workspace_bytes(cfgs) -> int:
+    arr, ptr = _cfg_array(cfgs)
+    n = load().emu_batch_workspace_bytes(ptr, len(cfgs))
+    if n < 0:
+        raise EmuError(int(n), "invalid configuration")
+    return int(n)
+
+
+def emu_batch_create(cfgs):
+    arr, ptr = _cfg_array(cfgs)
+    box = ctypes.c_void_p()
+    _check(None, load().emu_batch_create(ptr, len(cfgs), ctypes.byref(box)))
+    return box
+
+
+def emu_batch_init_particles(box, n_nu, n_nubar, f_nu, f_nubar, dirs, alpha, seed):
+    arrs = [np.ascontiguousarray(a, np.float64) for a in (n_nu, n_nubar, f_nu, f_nubar, alpha)]
+    sd = np.ascontiguousarray(seed, np.uint64)
+    d = None if dirs is None else np.ascontiguousarray(dirs, np.float64)
+    _check(box, load().emu_batch_init_particles(box, *map(_host_ptr, arrs[:4]), _host_ptr(d), _host_ptr(arrs[4]),
+                                                sd.ctypes.data_as(ctypes.c_void_p)))
+
+
+def emu_batch_timestep(box, nbox: int) -> np.ndarray:
+    out = np.zeros(nbox)
+    _check(box, load().emu_batch_timestep(box, _host_ptr(out)))
+    return out
+
+
+def emu_batch_set_dt(box, dt):
+    dt = np.ascontiguousarray(dt, np.float64)
+    _check(box, load().emu_batch_set_dt(box, _host_ptr(dt)))
+
+
+def emu_batch_step(box, nsteps: int):
+    _check(box, load().emu_batch_step(box, int(nsteps)))
+
+
+def emu_batch_diagnostics(box, out, on_host: int):
+    _check(box, load().emu_batch_diagnostics(box, out, int(on_host)))
+
+
+def emu_autotune(box, trial_steps: int):
+    """(choice index, per-step ms of the 3 candidate grids)."""
+    choice = ctypes.c_int32()
+    ms = np.zeros(3)
+    _check(box, load().emu_autotune(box, int(trial_steps), ctypes.byref(choice), _host_ptr(ms)))
+    return int(choice.value), ms
+
+
 def emu_last_error(box) -> str:
     m = load().emu_last_error(box)
     return m.decode() if m else ""
@@ -227,26 +308,36 @@ def emu_destroy(box):
 
 # ------------------------------------------------------------ convenience
 
+def _fibonacci(M):
+    raise ValueError("explicit directions for some boxes of a batch need explicit directions for all")
+
 class Box:
     """One box with its caller-owned device memory held as torch tensors."""
 
     FIELDS = ("z", "ox", "oy", "oz", "N", "Nbar")
 
     def __init__(self, nz, ndir, Lz, kappa, c_light, cfl_adv=0.4, cfl_flavor=0.4, area=1.0,
-                 device="cuda", stream=None):
+                 device="cuda", stream=None, cfgs=None):
         import torch
 
         self.torch = torch
         self.device = torch.device(device)
-        self.cfg = make_config(nz, ndir, Lz, kappa, c_light, cfl_adv, cfl_flavor, area)
-        self.nz, self.ndir, self.P = int(nz), int(ndir), int(nz) * int(ndir)
+        if cfgs is None:
+            self.cfgs = [make_config(nz, ndir, Lz, kappa, c_light, cfl_adv, cfl_flavor, area)]
+        else:
+            self.cfgs = list(cfgs)
+        self.cfg = self.cfgs[0]
+        self.nbox = len(self.cfgs)
+        self.nz = emu_batch_cells(self.cfgs)
+        self.P = emu_batch_particles(self.cfgs)
+        self.ndir = self.cfg.ndir if self.nbox == 1 else None
         f64 = dict(dtype=torch.float64, device=self.device)
         self.t = {k: torch.zeros(self.P, **f64) for k in self.FIELDS}
         self.t["rho"] = torch.zeros(9, self.P, **f64)
         self.t["rhobar"] = torch.zeros(9, self.P, **f64)
         self.t["acc"] = torch.zeros(18, self.P, **f64)
         self.t["stage"] = torch.zeros(18, self.P, **f64)
-        self.ws_bytes = emu_workspace_bytes(self.cfg)
+        self.ws_bytes = emu_batch_workspace_bytes(self.cfgs)
         self._ws_raw = torch.zeros(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
         base = self._ws_raw.data_ptr()
         self.ws_ptr = (base + 255) & ~255
@@ -254,8 +345,25 @@ class Box:
         self.parts = emu_particles(*[self.t[k].data_ptr() for k in
                                      ("z", "ox", "oy", "oz", "N", "Nbar", "rho", "rhobar", "acc", "stage")],
                                    self.P)
-        self.box = emu_create(self.cfg)
+        self.box = emu_batch_create(self.cfgs)
         emu_bind(self.box, self.parts, self.ws_ptr, self.ws_bytes, self.stream.cuda_stream)
+
+    @classmethod
+    def from_workloads(cls, wls, device="cuda", init=True):
+        """A batch of the given workloads (one box each), initialised together."""
+        cfgs = [make_config(w.nz, w.ndir, w.Lz, w.kappa, w.c_light, w.cfl_adv, w.cfl_flavor, w.area) for w in wls]
+        b = cls(0, 0, 0, 0, 0, device=device, cfgs=cfgs)
+        if init:
+            dirs = None
+            if any(w.dirs is not None for w in wls):
+                dirs = np.concatenate([np.asarray(w.dirs if w.dirs is not None else _fibonacci(w.ndir)).reshape(-1)
+                                       for w in wls])
+            emu_batch_init_particles(b.box, np.concatenate([w.n_nu for w in wls]),
+                                     np.concatenate([w.n_nubar for w in wls]),
+                                     np.concatenate([np.asarray(w.f_nu).reshape(-1) for w in wls]),
+                                     np.concatenate([np.asarray(w.f_nubar).reshape(-1) for w in wls]), dirs,
+                                     np.array([w.alpha for w in wls]), np.array([w.seed for w in wls], np.uint64))
+        return b
 
     @classmethod
     def from_workload(cls, wl, device="cuda", init=True):
@@ -311,6 +419,24 @@ class Box:
 
     def sync(self):
         emu_sync(self.box)
+
+    # -- batch calls
+    def batch_timestep(self) -> np.ndarray:
+        return emu_batch_timestep(self.box, self.nbox)
+
+    def batch_set_dt(self, dt):
+        emu_batch_set_dt(self.box, dt)
+
+    def batch_step(self, nsteps):
+        emu_batch_step(self.box, nsteps)
+
+    def batch_diagnostics(self) -> np.ndarray:
+        out = np.zeros((self.nbox, N_DIAG))
+        emu_batch_diagnostics(self.box, _host_ptr(out), 1)
+        return out
+
+    def autotune(self, trial_steps=2):
+        return emu_autotune(self.box, trial_steps)
 
     def launches(self) -> int:
         return emu_kernel_launches(self.box)

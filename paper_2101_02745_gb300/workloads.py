@@ -133,6 +133,28 @@ def two_beam(nz: int = 64, n: float = 4.89e32) -> Workload:
     return Workload(f"two_beam_{nz}", nz, 2, 1.0, *sp, dirs=dirs, steps=200)
 
 
+def sweep(nbox: int = 256, seed: int = 0, nz_range=(64, 1024), ndir_range=(48, 378)) -> list:
+    """Parameter sweep of independent boxes (the density, flux-magnitude and
+    flux-direction sweeps of Sec. 4): per box, from numpy PCG64(seed),
+    nz ~ U{nz_range}, ndir ~ U{ndir_range}, n, nbar ~ U[1e32, 1e33] cm^-3,
+    flux factors |f|/n, |fbar|/nbar ~ U[0, 1/3], nu flux along +z and nubar flux
+    at an angle ~ U[0, pi] from it; dz = 1/16 cm; Eq. 9 seed = box index."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for b in range(nbox):
+        nz = int(rng.integers(nz_range[0], nz_range[1] + 1))
+        M = int(rng.integers(ndir_range[0], ndir_range[1] + 1))
+        n, nb = rng.uniform(1e32, 1e33, 2)
+        ff, ffb = rng.uniform(0.0, 1.0 / 3.0, 2)
+        ang = rng.uniform(0.0, np.pi)
+        fv = np.array([0.0, 0.0, ff * n])
+        fbv = ffb * nb * np.array([np.sin(ang), 0.0, np.cos(ang)])
+        sp = _uniform_species(nz, n, nb, fv, fbv)
+        out.append(Workload(f"sweep{b}_{nz}x{M}", nz, M, nz / 16.0, *sp, seed=b, steps=2000,
+                            meta={"flux_angle": ang, "ff": ff, "ffb": ffb}))
+    return out
+
+
 def head(wl: Workload, nz: int) -> Workload:
     """The first nz cells of a workload (same per-cell inputs, cell size and
     directions): a bounded sample of it."""
