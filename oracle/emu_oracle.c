@@ -64,6 +64,18 @@ typedef struct {
   double c_light;     /* speed of light [cm / s] */
   double cfl_adv;     /* C of Eq. 7 */
   double cfl_flavor;  /* C_F of Eq. 7 */
+  /* Vacuum and matter terms of Eq. 2 (off when osc_on == 0):
+   * masses m_i c^2 [eV], mixing angles theta12, theta13, theta23 and the
+   * phase delta [rad] of the standard three-angle mixing matrix, neutrino
+   * energy [erg], net electron density n_e [cm^-3], hbar [erg s], erg per eV. */
+  int32_t osc_on;
+  int32_t pad;
+  double mass_eV[3];
+  double theta12, theta13, theta23, delta_cp;
+  double energy_erg;
+  double n_e;
+  double hbar;
+  double erg_per_eV;
 } or_config;
 
 /* One computational particle (Sec. 2.2): position, direction, weights and
@@ -255,6 +267,45 @@ void or_hamiltonian(const or_config* cfg, const or_cell* grid, const or_particle
     }
 }
 
+/* Mixing matrix U (flavour <- mass basis) in the standard three-angle form:
+ * U = R23 U13(delta) R12 with c_ij = cos theta_ij, s_ij = sin theta_ij. */
+void or_mixing_matrix(const or_config* cfg, cplx U[3][3]) {
+  double c12 = cos(cfg->theta12), s12 = sin(cfg->theta12);
+  double c13 = cos(cfg->theta13), s13 = sin(cfg->theta13);
+  double c23 = cos(cfg->theta23), s23 = sin(cfg->theta23);
+  cplx ep = cexp(I * cfg->delta_cp), em = cexp(-I * cfg->delta_cp);
+  U[0][0] = c12 * c13;
+  U[0][1] = s12 * c13;
+  U[0][2] = s13 * em;
+  U[1][0] = -s12 * c23 - c12 * s23 * s13 * ep;
+  U[1][1] = c12 * c23 - s12 * s23 * s13 * ep;
+  U[1][2] = s23 * c13;
+  U[2][0] = s12 * s23 - c12 * c23 * s13 * ep;
+  U[2][1] = -c12 * s23 - s12 * c23 * s13 * ep;
+  U[2][2] = c23 * c13;
+}
+
+/* Vacuum term of Eq. 2 divided by hbar: U diag(m_i^2 c^4 / (2 E)) U^dagger / hbar
+ * (the flavour-blind |p| c part cancels in the commutator), and the matter
+ * term kappa n_e diag(1, 0, 0) (comoving frame: no lepton flux). */
+void or_vacuum_matter(const or_config* cfg, cplx Hvac[3][3], cplx Hmat[3][3]) {
+  cplx U[3][3];
+  or_mixing_matrix(cfg, U);
+  double w[3];
+  for (int i = 0; i < 3; ++i) {
+    double mc2 = cfg->mass_eV[i] * cfg->erg_per_eV;
+    w[i] = mc2 * mc2 / (2.0 * cfg->energy_erg) / cfg->hbar;
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      cplx v = 0.0;
+      for (int i = 0; i < 3; ++i) v += U[a][i] * w[i] * conj(U[b][i]);
+      Hvac[a][b] = v;
+      Hmat[a][b] = 0.0;
+    }
+  Hmat[0][0] = cfg->kappa * cfg->n_e;
+}
+
 /* Sec. 2.1: for antineutrinos the self-interaction Hamiltonian is -H^*. */
 void or_hamiltonian_bar(cplx H[3][3], cplx Hbar[3][3]) {
   for (int a = 0; a < 3; ++a)
@@ -276,10 +327,18 @@ void or_commutator_rhs(cplx H[3][3], cplx rho[3][3], cplx out[3][3]) {
 void or_rhs(const or_config* cfg, const or_particle* parts, int64_t P, or_cell* grid,
             cplx (*drho)[3][3], cplx (*drhobar)[3][3]) {
   or_deposit(cfg, parts, P, grid);
+  cplx Hvac[3][3] = {{0}}, Hmat[3][3] = {{0}};
+  if (cfg->osc_on) or_vacuum_matter(cfg, Hvac, Hmat);
   for (int64_t p = 0; p < P; ++p) {
     cplx H[3][3], Hb[3][3];
     or_hamiltonian(cfg, grid, &parts[p], H);
     or_hamiltonian_bar(H, Hb);
+    /* Sec. 2.1: Hbar_vacuum = H_vacuum^*, Hbar_matter = -H_matter^* */
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        H[a][b] += Hvac[a][b] + Hmat[a][b];
+        Hb[a][b] += conj(Hvac[a][b]) - conj(Hmat[a][b]);
+      }
     cplx r[3][3], rb[3][3];
     memcpy(r, parts[p].rho, sizeof(r));
     memcpy(rb, parts[p].rhobar, sizeof(rb));
@@ -344,9 +403,10 @@ int or_run(const or_config* cfg, or_particle* parts, int64_t P, double dt, int64
 /* ------------------------------------------------------------ time step --- */
 
 /* Eq. 7 with the maximum over grid cells and diagonal components of n and
- * nbar (the lepton density n_a is zero here). */
+ * nbar, and the lepton density n_a (the net electron density when the
+ * matter term is on). */
 double or_timestep(const or_config* cfg, const or_cell* grid) {
-  double nmax = 0.0;
+  double nmax = cfg->osc_on ? cfg->n_e : 0.0;
   for (int j = 0; j < cfg->nz; ++j)
     for (int a = 0; a < 3; ++a) {
       if (creal(grid[j].n[a][a]) > nmax) nmax = creal(grid[j].n[a][a]);

@@ -55,6 +55,17 @@ class OrConfig(ctypes.Structure):
         ("c_light", ctypes.c_double),
         ("cfl_adv", ctypes.c_double),
         ("cfl_flavor", ctypes.c_double),
+        ("osc_on", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+        ("mass_eV", ctypes.c_double * 3),
+        ("theta12", ctypes.c_double),
+        ("theta13", ctypes.c_double),
+        ("theta23", ctypes.c_double),
+        ("delta_cp", ctypes.c_double),
+        ("energy_erg", ctypes.c_double),
+        ("n_e", ctypes.c_double),
+        ("hbar", ctypes.c_double),
+        ("erg_per_eV", ctypes.c_double),
     ]
 
 
@@ -94,6 +105,8 @@ def lib():
         L.or_run.argtypes = [cfgp, vp, i64, dbl, i64]; L.or_run.restype = ctypes.c_int
         L.or_timestep.argtypes = [cfgp, vp]; L.or_timestep.restype = dbl
         L.or_eln_matrix.argtypes = [vp, i64, vp]; L.or_eln_matrix.restype = None
+        L.or_mixing_matrix.argtypes = [cfgp, vp]; L.or_mixing_matrix.restype = None
+        L.or_vacuum_matter.argtypes = [cfgp, vp, vp]; L.or_vacuum_matter.restype = None
         L.or_domain_averages.argtypes = [cfgp, vp, vp, vp]; L.or_domain_averages.restype = None
         for name in ("or_sizeof_particle", "or_sizeof_cell", "or_sizeof_config"):
             getattr(L, name).restype = ctypes.c_int32
@@ -109,9 +122,32 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def config(nz, ndir, Lz, kappa, c_light, cfl_adv=0.4, cfl_flavor=0.4, area=1.0) -> OrConfig:
-    return OrConfig(int(nz), int(ndir), float(Lz), float(area), float(kappa), float(c_light),
-                    float(cfl_adv), float(cfl_flavor))
+def config(nz, ndir, Lz, kappa, c_light, cfl_adv=0.4, cfl_flavor=0.4, area=1.0, osc=None) -> OrConfig:
+    """osc: None, or a dict with mass_eV (3), theta12, theta13, theta23, delta_cp [rad],
+    energy_erg, n_e [cm^-3], hbar [erg s], erg_per_eV (vacuum and matter terms of Eq. 2)."""
+    c = OrConfig(int(nz), int(ndir), float(Lz), float(area), float(kappa), float(c_light),
+                 float(cfl_adv), float(cfl_flavor))
+    if osc is not None:
+        c.osc_on = 1
+        for i, m in enumerate(osc["mass_eV"]):
+            c.mass_eV[i] = float(m)
+        for k in ("theta12", "theta13", "theta23", "delta_cp", "energy_erg", "n_e", "hbar", "erg_per_eV"):
+            setattr(c, k, float(osc[k]))
+    return c
+
+
+def mixing_matrix(cfg: OrConfig) -> np.ndarray:
+    U = np.zeros((3, 3), complex)
+    lib().or_mixing_matrix(ctypes.byref(cfg), _ptr(U))
+    return U
+
+
+def vacuum_matter(cfg: OrConfig):
+    """(H_vacuum, H_matter) / hbar [1/s] of Eq. 2."""
+    a = np.zeros((3, 3), complex)
+    b = np.zeros((3, 3), complex)
+    lib().or_vacuum_matter(ctypes.byref(cfg), _ptr(a), _ptr(b))
+    return a, b
 
 
 def splitmix64(seed: int, n: int) -> int:

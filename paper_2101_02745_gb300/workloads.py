@@ -27,6 +27,8 @@ ERG_PER_GEV = 1.602176634e-3
 HBAR_ERG_S = 1.054571817e-27
 C_LIGHT = 2.99792458e10         # [cm/s]
 KAPPA = math.sqrt(2.0) * GF_GEV2 * HBARC_GEV_CM ** 3 * ERG_PER_GEV / HBAR_ERG_S  # [cm^3/s]
+ERG_PER_EV = 1.602176634e-12
+ATOMIC_MASS_G = 1.66053906660e-24   # atomic mass unit [g]
 
 
 @dataclass
@@ -163,6 +165,42 @@ def head(wl: Workload, nz: int) -> Workload:
                     wl.f_nu[:nz].copy(), wl.f_nubar[:nz].copy(), dirs=wl.dirs, alpha=wl.alpha, seed=wl.seed,
                     steps=wl.steps, cfl_adv=wl.cfl_adv, cfl_flavor=wl.cfl_flavor, area=wl.area, kappa=wl.kappa,
                     c_light=wl.c_light)
+
+
+def oscillation(mass_eV=(0.0, 0.0, 0.0), theta12=0.0, theta13=0.0, theta23=0.0, delta_cp=0.0,
+                energy_MeV=50.0, rho_g_cm3=0.0, Ye=0.5) -> dict:
+    """Vacuum and matter parameters of Eq. 2: masses m_i c^2 [eV], mixing angles
+    and phase [rad], neutrino energy, matter density and electron fraction
+    (net electron density n_e = rho Ye / m_u)."""
+    return {"mass_eV": tuple(float(m) for m in mass_eV), "theta12": float(theta12), "theta13": float(theta13),
+            "theta23": float(theta23), "delta_cp": float(delta_cp), "energy_erg": energy_MeV * 1e6 * ERG_PER_EV,
+            "n_e": rho_g_cm3 * Ye / ATOMIC_MASS_G, "hbar": HBAR_ERG_S, "erg_per_eV": ERG_PER_EV}
+
+
+def msw_test() -> tuple:
+    """App. A.1: one 1 cm zone, matter of 1.35e9 g/cm^3 with Ye = 1, m1 = 8.6e-3 eV,
+    m2 = 0, theta12 = 33.82 deg, E = 0.138 eV; two particles, one neutrino and one
+    antineutrino each (negligible self-interaction)."""
+    osc = oscillation(mass_eV=(8.6e-3, 0.0, 0.0), theta12=math.radians(33.82), energy_MeV=0.138e-6,
+                      rho_g_cm3=1.35e9, Ye=1.0)
+    dirs = np.array([[0.0, 0.0, 1.0], [0.0, 0.0, -1.0]])
+    # one physical (anti)neutrino per particle: n = N * M / dV = 2 cm^-3, isotropic
+    sp = _uniform_species(1, 2.0, 2.0, (0, 0, 0), (0, 0, 0))
+    return Workload("msw_1zone", 1, 2, 1.0, *sp, dirs=dirs, alpha=0.0, steps=0, meta={"osc": osc}), osc
+
+
+def homogeneous_two_beam() -> tuple:
+    """App. A.3: one zone, a nu_e beam along +z and a nubar_e beam along -z of
+    equal density n = |dm^2| c^4 / (4 sqrt(2) G_F E) with m1 = 8.6e-3 eV, m2 = 0,
+    theta12 = 1e-6 deg, E = 50 MeV, no matter."""
+    osc = oscillation(mass_eV=(8.6e-3, 0.0, 0.0), theta12=math.radians(1e-6), energy_MeV=50.0)
+    dm2 = (osc["mass_eV"][0] * ERG_PER_EV) ** 2
+    w_vac = dm2 / (2.0 * osc["energy_erg"]) / HBAR_ERG_S
+    n = w_vac / (2.0 * KAPPA)
+    dirs = np.array([[0.0, 0.0, 1.0], [0.0, 0.0, -1.0]])
+    sp = _uniform_species(1, n, n, (0, 0, n / 3.0), (0, 0, -n / 3.0))
+    return Workload("two_beam_homogeneous", 1, 2, 1.0, *sp, dirs=dirs, alpha=0.0, steps=0,
+                    meta={"osc": osc, "growth": w_vac}), osc
 
 
 def by_name(name: str) -> Workload:

@@ -469,3 +469,80 @@ def test_growth_matches_discrete_dispersion():
     ts = np.arange(81) * dt
     slope = np.polyfit(ts[30:], amp[30:], 1)[0]
     assert abs(slope / rates[mbest] - 1) < 0.05, (mbest, slope, rates[mbest])
+
+
+# --------------------------------------------- vacuum and matter terms (Eq. 2) ---
+
+def _osc_cfg(**kw):
+    osc = W.oscillation(**kw)
+    return O.config(1, 2, 1.0, W.KAPPA, W.C_LIGHT, osc=osc), osc
+
+
+def test_mixing_matrix_and_vacuum_spectrum():
+    cfg, osc = _osc_cfg(mass_eV=(0.01, 0.012, 0.05), theta12=0.59, theta13=0.15, theta23=0.84, delta_cp=1.2)
+    U = O.mixing_matrix(cfg)
+    assert np.allclose(U @ U.conj().T, np.eye(3), atol=1e-15)
+    Hv, Hm = O.vacuum_matter(cfg)
+    assert np.allclose(Hv, Hv.conj().T, atol=0)
+    m = np.array(osc["mass_eV"]) * W.ERG_PER_EV
+    expect = np.sort(m ** 2 / (2 * osc["energy_erg"]) / W.HBAR_ERG_S)
+    assert np.allclose(np.linalg.eigvalsh(Hv), expect, rtol=1e-12, atol=1e-12 * expect.max())
+    assert np.all(Hm == 0)
+    # two-flavour reduction: theta13 = theta23 = 0 is a rotation in the e-mu plane
+    cfg2, _ = _osc_cfg(mass_eV=(0.01, 0.0, 0.0), theta12=0.3)
+    U2 = O.mixing_matrix(cfg2)
+    c, s = np.cos(0.3), np.sin(0.3)
+    assert np.allclose(U2, [[c, s, 0], [-s, c, 0], [0, 0, 1]], atol=1e-16)
+    # matter term: kappa n_e on the electron flavour only
+    cfg3, osc3 = _osc_cfg(rho_g_cm3=1e8, Ye=0.4)
+    _, Hm3 = O.vacuum_matter(cfg3)
+    assert Hm3[0, 0] == W.KAPPA * osc3["n_e"] and np.count_nonzero(Hm3) == 1
+
+
+def test_msw_closed_form():
+    """App. A.1: the oracle's flavour evolution against the textbook two-flavour
+    MSW formula P_ee = 1 - sin^2(2 theta_m) sin^2(omega_m t / 2); the paper
+    reports a maximum difference of 3.7e-4 at dt = 6.5e-13 s over ct = 1 cm."""
+    g = GOLD["msw_max_error"]
+    wl, osc = W.msw_test()
+    cfg = O.config(wl.nz, wl.ndir, wl.Lz, wl.kappa, wl.c_light, osc=osc)
+    parts = O.init(cfg, wl.n_nu, wl.n_nubar, wl.f_nu, wl.f_nubar, 0.0, 0, wl.dirs)
+    D = -(osc["mass_eV"][0] * W.ERG_PER_EV) ** 2 / (2 * osc["energy_erg"]) / W.HBAR_ERG_S
+    V = W.KAPPA * osc["n_e"]
+    th = osc["theta12"]
+
+    def pee(t, v):
+        w = np.sqrt((v - D * np.cos(2 * th)) ** 2 + (D * np.sin(2 * th)) ** 2)
+        return 1 - (D * np.sin(2 * th) / w) ** 2 * np.sin(w * t / 2) ** 2
+
+    dt, t, err, rbmin = g["dt_s"], 0.0, 0.0, 1.0
+    while t * W.C_LIGHT < g["ct_cm"]:
+        O.rk4_step(cfg, parts, dt)
+        t += dt
+        err = max(err, abs(parts["rho"][0, 0, 0].real - pee(t, V)), abs(parts["rhobar"][0, 0, 0].real - pee(t, -V)))
+        rbmin = min(rbmin, parts["rhobar"][0, 0, 0].real)
+    assert err <= g["max_abs_error"], err
+    assert err > 0.25 * g["max_abs_error"]      # the same scheme and step give the same size of error
+    assert rbmin < 1e-2                          # antineutrinos in resonance convert completely
+    assert np.all(parts["rho"][:, 2, :] == 0)    # two-flavour problem stays two-flavour
+
+
+def test_homogeneous_two_beam_growth():
+    """App. A.3: growth rate of rho_emu = |dm^2| c^4 / (2 hbar E) = 1123 /s, fitted
+    between 8.4 and 11.7 ms (paper: relative error at most 3.2e-5)."""
+    g = GOLD["two_beam_homogeneous_growth"]
+    wl, osc = W.homogeneous_two_beam()
+    assert abs(wl.n_nu[0] / g["n_per_cm3"] - 1) < 2e-3
+    assert abs(wl.meta["growth"] / g["growth_per_s"] - 1) < 1e-3
+    cfg = O.config(wl.nz, wl.ndir, wl.Lz, wl.kappa, wl.c_light, osc=osc)
+    parts = O.init(cfg, wl.n_nu, wl.n_nubar, wl.f_nu, wl.f_nubar, 0.0, 0, wl.dirs)
+    dt, t, ts, amp = 2e-6, 0.0, [], []
+    while t < g["fit_window_s"][1] + dt / 2:
+        O.rk4_step(cfg, parts, dt)
+        t += dt
+        ts.append(t)
+        amp.append(abs(parts["rho"][0, 0, 1]))
+    ts, amp = np.array(ts), np.array(amp)
+    sel = (ts >= g["fit_window_s"][0]) & (ts <= g["fit_window_s"][1])
+    slope = np.polyfit(ts[sel], np.log(amp[sel]), 1)[0]
+    assert abs(slope / wl.meta["growth"] - 1) <= g["relative_error_reported"], slope
