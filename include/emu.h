@@ -232,6 +232,29 @@ int emu_batch_diagnostics(emu_box* box, double* out, int on_host);
  * reproducible for a fixed choice.  Synchronises. */
 int emu_autotune(emu_box* box, int trial_steps, int32_t* choice_out, double* ms_out);
 
+/* Vacuum and matter terms of Eq. 2 (Sec. 2.1): masses m_i c^2 [eV], the mixing
+ * angles theta12, theta13, theta23 and phase delta_cp [rad] of the standard
+ * three-angle mixing matrix U (the paper does not give a parametrisation),
+ * the neutrino energy [erg] (one energy for all particles, Sec. 3), the net
+ * electron density n_e [cm^-3] (comoving frame: no lepton flux), and the
+ * constants hbar [erg s] and erg per eV. */
+typedef struct {
+  double mass_eV[3];
+  double theta12, theta13, theta23, delta_cp;
+  double energy_erg;
+  double n_e;
+  double hbar;
+  double erg_per_eV;
+} emu_oscillation;
+
+/* Add the vacuum and matter terms to box `box` (-1: every box of the batch):
+ * H = U diag(m_i^2 c^4 / 2E) U^dagger / hbar + kappa n_e diag(1, 0, 0) + H_self
+ * for neutrinos and Hbar = (H_vacuum^* - H_matter^*) / hbar - H_self^* for
+ * antineutrinos; n_e also enters Eq. 7 as the lepton density.  osc = NULL
+ * removes them.  emu_interpolate_H still returns the self-interaction term
+ * only.  Invalidates the step sizes of Eq. 7 (call the time-step call again). */
+int emu_set_oscillation(emu_box* box, int32_t box_index, const emu_oscillation* osc);
+
 /* Wait for the box's stream and report errors recorded by its kernels. */
 int emu_sync(emu_box* box);
 

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <complex>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -142,6 +143,7 @@ struct emu_box {
          *dirtab = nullptr, *species = nullptr, *dirs = nullptr, *diag = nullptr, *scalar = nullptr;
   int *err = nullptr, *shift = nullptr;
   int blocks = kPersistBlocks;  // grid of the step kernels (autotuned); its warps split the units
+  bool pot = false;             // some box has vacuum or matter terms
   int next_stage = 1;
   std::vector<double> dt_h;  // step sizes currently on the device
   bool dt_set = false;
@@ -306,7 +308,12 @@ int launch_stage(emu_box* b, int s, int dry) {
   const int* srow = b->shift + (size_t)(s - 1) * b->S.MT;
   if (int rc = launch_deposit(b, 0, rnu, rnb, srow, kStageFrac[s - 1], b->A)) return rc;
   before_launch(b, CLS_RK);
-  k_rk_stage<<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->W, b->dirtab, srow, b->A, s, dry);
+  if (b->pot)
+    k_rk_stage<true><<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->W, b->dirtab, srow, b->A,
+                                                                  s, dry);
+  else
+    k_rk_stage<false><<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->W, b->dirtab, srow,
+                                                                   b->A, s, dry);
   return after_launch(b, "RK stage kernel");
 }
 
@@ -725,6 +732,63 @@ int emu_autotune(emu_box* b, int trial_steps, int32_t* choice_out, double* ms_ou
   if (rc) return rc;
   if (choice_out) *choice_out = best;
   return read_errors(b);
+}
+
+int emu_set_oscillation(emu_box* b, int32_t box, const emu_oscillation* osc) {
+  if (!b) return EMU_EINVAL;
+  if (box < -1 || box >= b->S.nbox) return fail(b, EMU_EINVAL, "box index %d out of range", box);
+  double vn[9] = {0}, vb[9] = {0}, ne = 0.0;
+  if (osc) {
+    const double* m = osc->mass_eV;
+    if (!(osc->energy_erg > 0) || !(osc->hbar > 0) || !(osc->erg_per_eV > 0) || !std::isfinite(osc->n_e))
+      return fail(b, EMU_EINVAL, "oscillation parameters: energy, hbar and erg_per_eV must be positive");
+    typedef std::complex<double> cd;
+    const double c12 = std::cos(osc->theta12), s12 = std::sin(osc->theta12);
+    const double c13 = std::cos(osc->theta13), s13 = std::sin(osc->theta13);
+    const double c23 = std::cos(osc->theta23), s23 = std::sin(osc->theta23);
+    const cd e = std::polar(1.0, osc->delta_cp);
+    // standard three-angle mixing matrix (flavour <- mass)
+    const cd U[3][3] = {{c12 * c13, s12 * c13, s13 * std::conj(e)},
+                        {-s12 * c23 - c12 * s23 * s13 * e, c12 * c23 - s12 * s23 * s13 * e, s23 * c13},
+                        {s12 * s23 - c12 * c23 * s13 * e, -c12 * s23 - s12 * c23 * s13 * e, c23 * c13}};
+    double w[3];
+    for (int i = 0; i < 3; ++i) {
+      const double mc2 = m[i] * osc->erg_per_eV;
+      w[i] = mc2 * mc2 / (2.0 * osc->energy_erg) / osc->hbar;
+    }
+    cd Hv[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int c = 0; c < 3; ++c) {
+        cd v = 0.0;
+        for (int i = 0; i < 3; ++i) v += U[a][i] * w[i] * std::conj(U[c][i]);
+        Hv[a][c] = v;
+      }
+    ne = osc->n_e;
+    const int pk[6][2] = {{0, 1}, {0, 1}, {0, 2}, {0, 2}, {1, 2}, {1, 2}};
+    for (int k = 0; k < 3; ++k) { vn[k] = Hv[k][k].real(); vb[k] = Hv[k][k].real(); }
+    for (int q = 0; q < 6; ++q) {
+      const cd v = Hv[pk[q][0]][pk[q][1]];
+      vn[3 + q] = (q & 1) ? v.imag() : v.real();
+      vb[3 + q] = (q & 1) ? -v.imag() : v.real();   // H_vacuum^*
+    }
+  }
+  bool any = false;
+  for (int i = 0; i < b->S.nbox; ++i) {
+    BoxGeo& g = b->S.geo[i];
+    if (box == -1 || box == i) {
+      const double mat = b->cfg[i].kappa * ne;   // kappa n_e on the electron flavour; Hbar gets -H_matter
+      for (int k = 0; k < 9; ++k) { g.vnu[k] = vn[k]; g.vnubar[k] = vb[k]; }
+      g.vnu[0] += mat;
+      g.vnubar[0] -= mat;
+      g.n_e = ne;
+    }
+    for (int k = 0; k < 9; ++k) any = any || g.vnu[k] != 0.0 || g.vnubar[k] != 0.0;
+  }
+  b->pot = any;
+  b->step_valid = false;
+  invalidate_graph(b);
+  if (b->bound) return upload_geo(b);
+  return EMU_OK;
 }
 
 int emu_sync(emu_box* b) {

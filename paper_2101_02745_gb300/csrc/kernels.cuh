@@ -59,6 +59,9 @@ struct BoxGeo {
   double alpha;      // Eq. 9 perturbation strength (init)
   uint64_t seed;     // Eq. 9 random stream (init)
   double cfl_adv, cfl_flavor, kappa;  // Eq. 7
+  double n_e;        // net electron density (matter term of Eq. 2, lepton density of Eq. 7)
+  double vnu[9];     // constant part of the neutrino Hamiltonian: (H_vacuum + H_matter) / hbar, packed
+  double vnubar[9];  // constant part of the antineutrino one: (H_vacuum^* - H_matter^*) / hbar
 };
 
 // Kernel view of a batch (passed by value).
@@ -402,10 +405,13 @@ k_interpolate(Batch B, const double* __restrict__ z, const double* __restrict__ 
 //   s = 2: acc += dt/3 K,     stage = y + dt/2 K
 //   s = 3: acc += dt/3 K,     stage = y + dt K
 //   s = 4: y = acc + dt/6 K,  z = wrap(z + dt v_z)   (dry: into the stage buffer instead)
+// With POT the constant vacuum and matter terms of the box are added:
+// H = H_self + V, Hbar = -H_self^* + Vbar (Eq. 2, Sec. 2.1).
 // Persistent: each warp walks its contiguous range of units, direction-major
 // within a box (unit = direction * ntiles + tile) so it streams along each
 // ring, and prefetches the next unit's particle data into L2.  The shape
 // weights come from the deposit.
+template <bool POT>
 __global__ void __launch_bounds__(kThreads, 2)
 k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
            const int* __restrict__ shift, const double* __restrict__ A, int s, int dry) {
@@ -480,8 +486,19 @@ k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __rest
       H[k] = fma(wl, gl, fma(w0, G, wr * gr));
     }
     if (!active) continue;
-    const double d12 = H[0] - H[1], d13 = H[0] - H[2], d23 = H[1] - H[2];
     // neutrinos: H;  antineutrinos: Hbar = -H^*  (diagonal differences and real parts flip sign)
+    double Hb[9];
+    if (POT) {
+      const double* vn = g.vnu;
+      const double* vb = g.vnubar;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const bool im = (k == 4 || k == 6 || k == 8);
+        Hb[k] = (im ? H[k] : -H[k]) + __ldg(vb + k);
+        H[k] += __ldg(vn + k);
+      }
+    }
+    const double d12 = H[0] - H[1], d13 = H[0] - H[2], d23 = H[1] - H[2];
 #pragma unroll
     for (int which = 0; which < 2; ++which) {
       double* __restrict__ yv = which ? pt.rhobar : pt.rho;
@@ -504,6 +521,8 @@ k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __rest
       const double* rr = which ? rb : r;
       double kd[3], ko[6];
       if (which == 0) commutator(d12, d13, d23, H[3], H[4], H[5], H[6], H[7], H[8], rr, kd, ko);
+      else if (POT) commutator(Hb[0] - Hb[1], Hb[0] - Hb[2], Hb[1] - Hb[2], Hb[3], Hb[4], Hb[5], Hb[6], Hb[7], Hb[8],
+                               rr, kd, ko);
       else commutator(-d12, -d13, -d23, -H[3], H[4], -H[5], H[6], -H[7], H[8], rr, kd, ko);
       if (s == 1) {
 #pragma unroll
@@ -639,7 +658,8 @@ __global__ void k_dt_from_max(Batch B, const double* __restrict__ nmax, double* 
   if (b >= B.nbox) return;
   const BoxGeo& g = B.box[b];
   const double dt_adv = g.cfl_adv * g.dz / g.c_light;
-  const double dt_flav = nmax[b] > 0.0 ? g.cfl_flavor / (g.kappa * nmax[b]) : dt_adv;
+  const double nm = nmax[b] > g.n_e ? nmax[b] : g.n_e;
+  const double dt_flav = nm > 0.0 ? g.cfl_flavor / (g.kappa * nm) : dt_adv;
   dt_out[b] = dt_adv < dt_flav ? dt_adv : dt_flav;
 }
 

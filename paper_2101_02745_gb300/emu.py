@@ -47,6 +47,11 @@ class emu_config(ctypes.Structure):
     ]
 
 
+class emu_oscillation(ctypes.Structure):
+    _fields_ = [("mass_eV", ctypes.c_double * 3)] + [(k, ctypes.c_double) for k in
+                ("theta12", "theta13", "theta23", "delta_cp", "energy_erg", "n_e", "hbar", "erg_per_eV")]
+
+
 class emu_particles(ctypes.Structure):
     _fields_ = [(name, ctypes.c_void_p) for name in
                 ("z", "ox", "oy", "oz", "N", "Nbar", "rho", "rhobar", "acc", "stage")] + [("P", ctypes.c_int64)]
@@ -101,6 +106,7 @@ def load(build_if_missing: bool = False):
         "emu_batch_step": (i32, [vp, i64]),
         "emu_batch_diagnostics": (i32, [vp, vp, i32]),
         "emu_autotune": (i32, [vp, i32, vp, vp]),
+        "emu_set_oscillation": (i32, [vp, ctypes.c_int32, ctypes.POINTER(emu_oscillation)]),
         "emu_last_error": (ctypes.c_char_p, [vp]),
         "emu_destroy": (None, [vp]),
     }
@@ -297,6 +303,23 @@ def emu_autotune(box, trial_steps: int):
     return int(choice.value), ms
 
 
+def make_oscillation(d: dict) -> emu_oscillation:
+    o = emu_oscillation()
+    for i, m in enumerate(d["mass_eV"]):
+        o.mass_eV[i] = float(m)
+    for k in ("theta12", "theta13", "theta23", "delta_cp", "energy_erg", "n_e", "hbar", "erg_per_eV"):
+        setattr(o, k, float(d[k]))
+    return o
+
+
+def emu_set_oscillation(box, box_index: int, osc):
+    """osc: emu_oscillation, dict of its fields, or None (remove the terms)."""
+    if isinstance(osc, dict):
+        osc = make_oscillation(osc)
+    ptr = ctypes.byref(osc) if osc is not None else None
+    _check(box, load().emu_set_oscillation(box, int(box_index), ptr))
+
+
 def emu_last_error(box) -> str:
     m = load().emu_last_error(box)
     return m.decode() if m else ""
@@ -437,6 +460,9 @@ class Box:
 
     def autotune(self, trial_steps=2):
         return emu_autotune(self.box, trial_steps)
+
+    def set_oscillation(self, osc, box=-1):
+        emu_set_oscillation(self.box, box, osc)
 
     def launches(self) -> int:
         return emu_kernel_launches(self.box)
