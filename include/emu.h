@@ -255,6 +255,50 @@ typedef struct {
  * only.  Invalidates the step sizes of Eq. 7 (call the time-step call again). */
 int emu_set_oscillation(emu_box* box, int32_t box_index, const emu_oscillation* osc);
 
+/* ------------------------------------------------------------------ adjoint
+ *
+ * Discrete adjoint of the RK4 step (Sec. 2.3) for gradients of a loss L on the
+ * final moments with respect to the particle weights N, Nbar (Eq. 8) and, by
+ * the chain rule through Eq. 8, to the initial densities and fluxes.  The
+ * paper computes no gradients: these calls serve sensitivity studies of its
+ * instability (growth of <|n_emu|>, Eq. 10; final flavour abundances).
+ * All three calls take a single box; vacuum and matter terms are included.
+ * Adjoint vectors are packed like rho (9 reals per matrix, [k * P + p]) and
+ * hold dL/d(packed component): lambda is [18 * P] (rho, then rhobar), gN and
+ * gNbar are [P].  All pointers are device pointers, except where on_host says
+ * otherwise; calls are asynchronous on the box's stream. */
+
+/* Scratch the adjoint step needs: 90 doubles per particle (the stage states
+ * y2, y3, two stage adjoints and their running sum), or EMU_EINVAL. */
+int64_t emu_adjoint_workspace_bytes(const emu_config* cfg);
+
+/* Seed at the current state from dmom = dL/d(moments) ([72][nz], the layout
+ * emu_moments returns): lambda = dL/d(rho, rhobar) is overwritten, the direct
+ * terms dL/dN and dL/dNbar are ADDED to gN and gNbar.  Errors: EMU_EINVAL
+ * (NULL pointer, batch, RK step in progress). */
+int emu_adjoint_seed(emu_box* box, const double* dmom, double* lambda, double* gN, double* gNbar);
+
+/* One adjoint RK4 step.  The box must hold the state at the START of the
+ * step (positions and rho, rhobar, as emu_step(box, 1, dt) would take it).
+ * On entry lambda = dL/dy_{n+1}; on return lambda = dL/dy_n, and the
+ * contributions of this step to dL/dN and dL/dNbar are ADDED to gN, gNbar.
+ * The step recomputes its stage states (three forward stages into the RK
+ * scratch and adj_ws), then runs the stages backward: per stage a deposit of
+ * the stage state (H and shape weights), the transposed commutators, a
+ * deposit of the adjoint dL/dH (the self-interaction operator of Eqs. 5-6 is
+ * symmetric) and its interpolation.  The particle state is unchanged; the RK
+ * scratch (acc, stage) is overwritten.  adj_ws: device, 256-byte aligned,
+ * at least emu_adjoint_workspace_bytes.  Errors: EMU_EINVAL (dt not positive
+ * and finite, NULL or short buffers, batch, step in progress), EMU_ECUDA. */
+int emu_adjoint_step(emu_box* box, double dt, double* lambda, double* gN, double* gNbar, void* adj_ws,
+                     int64_t adj_ws_bytes);
+
+/* Chain rule through Eq. 8 (N_p = (n_c + 3 f_c . Omega_p) dV / M, c the cell
+ * a particle starts on at emu_init_particles): out[8][total cells] =
+ * dL/dn_nu, dL/dn_nubar, dL/df_nu (x, y, z), dL/df_nubar (x, y, z) per cell.
+ * Works on batches.  Errors: EMU_EINVAL (NULL pointer). */
+int emu_weight_gradient(emu_box* box, const double* gN, const double* gNbar, double* out, int on_host);
+
 /* Wait for the box's stream and report errors recorded by its kernels. */
 int emu_sync(emu_box* box);
 

@@ -1,0 +1,107 @@
+"""Gradients of the particle step: a torch.autograd.Function around the
+library's hand-written discrete adjoint.
+
+`Evolve.apply(n_nu, n_nubar, f_nu, f_nubar, sim)` initialises the particles of
+`sim.box` from per-cell densities (nz,) and fluxes (nz, 3) (Eq. 8, with the
+Eq. 9 perturbations of sim.alpha, sim.seed), takes sim.nsteps RK4 steps at
+the fixed step sim.dt (Sec. 2.3) and returns the final moments (72, nz) as
+emu_moments lays them out (Eq. 5: n, f_x, f_y, f_z of the neutrinos, then of
+the antineutrinos, 9 packed reals each).  Any torch loss of those moments
+can then be differentiated with respect to the four species inputs.
+
+Forward keeps a checkpoint of the evolving state (z, rho, rhobar) every
+sim.every steps.  Backward seeds the adjoint from dL/d(moments), then walks
+the segments last to first: it restores a segment's checkpoint, recomputes
+the segment's step-start states forward, and runs one adjoint step per step
+backward (emu_adjoint_step).  The accumulated dL/dN, dL/dNbar go through
+Eq. 8 to the species inputs (emu_weight_gradient).  Every arithmetic step
+runs in the CUDA library; this module only marshals buffers.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from .emu import Box
+
+
+@dataclass
+class Simulation:
+    """Settings of one differentiable run on a single box."""
+    box: Box
+    nsteps: int
+    dt: float
+    every: int = 20
+    alpha: float = 1e-6
+    seed: int = 0
+    dirs: np.ndarray | None = None
+
+
+def _host(t: torch.Tensor, shape) -> np.ndarray:
+    return np.ascontiguousarray(t.detach().to("cpu", torch.float64).numpy().reshape(shape))
+
+
+class Evolve(torch.autograd.Function):
+    """Species inputs -> final moments, with the library's adjoint as backward."""
+
+    @staticmethod
+    def forward(ctx, n_nu, n_nubar, f_nu, f_nubar, sim: Simulation):
+        box = sim.box
+        if box.nbox != 1:
+            raise ValueError("the adjoint takes a single box")
+        if not (sim.dt > 0) or sim.nsteps < 0 or sim.every < 1:
+            raise ValueError("need dt > 0, nsteps >= 0, every >= 1")
+        nz = box.nz
+        box.init(_host(n_nu, (nz,)), _host(n_nubar, (nz,)), _host(f_nu, (nz, 3)), _host(f_nubar, (nz, 3)),
+                 sim.dirs, sim.alpha, sim.seed)
+        checkpoints = []
+        done = 0
+        while done < sim.nsteps:
+            checkpoints.append(box.save_state())
+            k = min(sim.every, sim.nsteps - done)
+            box.step(k, sim.dt)
+            done += k
+        final = box.save_state()
+        mom = box.moments()
+        ctx.sim = sim
+        ctx.checkpoints = checkpoints
+        ctx.final = final
+        ctx.dev = n_nu.device
+        return mom.to(n_nu.device)
+
+    @staticmethod
+    def backward(ctx, dmom):
+        sim: Simulation = ctx.sim
+        box = sim.box
+        P = box.P
+        lam = box._f64(18, P)
+        gN = box._f64(P)
+        gNbar = box._f64(P)
+        box.load_state(ctx.final)
+        box.adjoint_seed(dmom, lam, gN, gNbar)
+        nseg = len(ctx.checkpoints)
+        for seg in range(nseg - 1, -1, -1):
+            start = seg * sim.every
+            k = min(sim.every, sim.nsteps - start)
+            box.load_state(ctx.checkpoints[seg])
+            starts = [box.save_state()]
+            for _ in range(k - 1):
+                box.step(1, sim.dt)
+                starts.append(box.save_state())
+            for st in reversed(starts):
+                box.load_state(st)
+                box.adjoint_step(sim.dt, lam, gN, gNbar)
+        box.load_state(ctx.final)
+        g = box.weight_gradient(gN, gNbar).to(ctx.dev)
+        ctx.lambda0 = lam  # dL/d(initial rho, rhobar), kept for inspection
+        return g[0], g[1], g[2:5].T.contiguous(), g[5:8].T.contiguous(), None
+
+
+def objectives(mom: torch.Tensor) -> torch.Tensor:
+    """(<n_ee>, log <|n_emu|>) of moments laid out as emu_moments returns them:
+    the final nu_e abundance and the growth measure of Eq. 10."""
+    nee = mom[0]
+    nem = torch.hypot(mom[3], mom[4])
+    return torch.stack([nee.mean(), torch.log(nem.mean())])

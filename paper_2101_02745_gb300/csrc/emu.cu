@@ -279,7 +279,8 @@ int launch_shifts(emu_box* b, const double* fracs, int nrows) {
 }
 
 // Deposit (two launches) of the state (rnu, rnb) at positions z + frac dt_b v_z
-// with the shift row shift_row, into out ([36][NZ]).
+// with the shift row shift_row, into out ([36][NZ]).  Modes as k_deposit; the
+// potential scale kappa/dV for modes 0 and 3, 1/dV for the moments.
 int launch_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, const int* shift_row, double frac,
                    double* out) {
   const Batch B = batch_view(b);
@@ -290,12 +291,16 @@ int launch_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, c
   else if (mode == 1)
     k_deposit<1><<<persist_grid(b), kThreads, 0, b->stream>>>(B, b->pt.z, b->pt.N, b->pt.Nbar, rnu, rnb, b->dirtab,
         shift_row, frac, b->partial, nullptr, b->err);
-  else
+  else if (mode == 2)
     k_deposit<2><<<persist_grid(b), kThreads, 0, b->stream>>>(B, b->pt.z, b->pt.N, b->pt.Nbar, rnu, rnb, b->dirtab,
+        shift_row, frac, b->partial, nullptr, b->err);
+  else
+    k_deposit<3><<<persist_grid(b), kThreads, 0, b->stream>>>(B, b->pt.z, b->pt.N, b->pt.Nbar, rnu, rnb, b->dirtab,
         shift_row, frac, b->partial, nullptr, b->err);
   if (int rc = after_launch(b, "deposit kernel")) return rc;
   before_launch(b, CLS_COMBINE);
-  k_combine<<<combine_blocks(B.NZ), kThreads, 0, b->stream>>>(B, b->partial, out, mode == 0 ? 1 : 0, b->err);
+  k_combine<<<combine_blocks(B.NZ), kThreads, 0, b->stream>>>(B, b->partial, out, (mode == 0 || mode == 3) ? 1 : 0,
+                                                                b->err);
   return after_launch(b, "deposit combine kernel");
 }
 
@@ -788,6 +793,102 @@ int emu_set_oscillation(emu_box* b, int32_t box, const emu_oscillation* osc) {
   b->step_valid = false;
   invalidate_graph(b);
   if (b->bound) return upload_geo(b);
+  return EMU_OK;
+}
+
+// ------------------------------------------------------------------ adjoint
+
+int64_t emu_adjoint_workspace_bytes(const emu_config* cfg) {
+  Shape S;
+  if (make_shape(cfg, 1, S)) return EMU_EINVAL;
+  return (int64_t)(sizeof(double) * 90 * (size_t)S.Ptot);
+}
+
+int emu_adjoint_seed(emu_box* b, const double* dmom, double* lambda, double* gN, double* gNbar) {
+  if (int rc = check_single(b)) return rc;
+  if (!dmom || !lambda || !gN || !gNbar) return fail(b, EMU_EINVAL, "adjoint seed: NULL pointer");
+  if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
+  const double zero = 0.0;
+  if (int rc = launch_shifts(b, &zero, 1)) return rc;
+  before_launch(b, CLS_OTHER);
+  k_adj_seed<<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->dirtab, b->shift, dmom, lambda,
+                                                          gN, gNbar, b->err);
+  return after_launch(b, "adjoint seed kernel");
+}
+
+int emu_adjoint_step(emu_box* b, double dt, double* lambda, double* gN, double* gNbar, void* adj_ws,
+                     int64_t adj_ws_bytes) {
+  if (int rc = check_single(b)) return rc;
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(b, EMU_EINVAL, "dt must be positive and finite");
+  if (!lambda || !gN || !gNbar || !adj_ws) return fail(b, EMU_EINVAL, "adjoint step: NULL pointer");
+  const size_t P = (size_t)b->S.Ptot;
+  if (adj_ws_bytes < (int64_t)(sizeof(double) * 90 * P))
+    return fail(b, EMU_EINVAL, "adjoint workspace too small: %lld < %lld bytes", (long long)adj_ws_bytes,
+                (long long)(sizeof(double) * 90 * P));
+  if (((uintptr_t)adj_ws) & 255) return fail(b, EMU_EINVAL, "adjoint workspace must be 256-byte aligned");
+  if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
+  double* Y2 = (double*)adj_ws;  // stage states y2, y3 (y4 stays in the stage buffer)
+  double* Y3 = Y2 + 18 * P;
+  double* La = Y3 + 18 * P;      // adjoints of two consecutive stage states
+  double* Lb = La + 18 * P;
+  double* Lt = Lb + 18 * P;      // running sum: lambda + sum over stages
+  const size_t bytes18 = sizeof(double) * 18 * P;
+  if (int rc = set_dts(b, &dt)) return rc;
+  if (int rc = launch_shifts(b, kStageFrac, 4)) return rc;
+  // forward stages 1..3: y2, y3 copied out, y4 left in the stage buffer
+  for (int s = 1; s <= 3; ++s) {
+    if (int rc = launch_stage(b, s, 0)) return rc;
+    if (s < 3)
+      if (int rc = cuda_check(b, cudaMemcpyAsync(s == 1 ? Y2 : Y3, b->pt.stage, bytes18, cudaMemcpyDeviceToDevice,
+                                                 b->stream), "copy stage state"))
+        return rc;
+  }
+  if (int rc = cuda_check(b, cudaMemcpyAsync(Lt, lambda, bytes18, cudaMemcpyDeviceToDevice, b->stream),
+                          "copy adjoint"))
+    return rc;
+  // backward: stage adjoint lam_s = J(y_s)^T mu_s with mu_4 = dt/6 lam,
+  // mu_3 = dt/3 lam + dt lam_4, mu_2 = dt/3 lam + dt/2 lam_3, mu_1 = dt/6 lam + dt/2 lam_2
+  const Batch B = batch_view(b);
+  double* Lnext = nullptr;
+  for (int s = 4; s >= 1; --s) {
+    double* ys = s == 1 ? b->pt.rho : s == 2 ? Y2 : s == 3 ? Y3 : b->pt.stage;
+    double* ysb = s == 1 ? b->pt.rhobar : ys + 9 * P;
+    const int* srow = b->shift + (size_t)(s - 1) * b->S.MT;
+    const double frac = kStageFrac[s - 1];
+    if (int rc = launch_deposit(b, 0, ys, ysb, srow, frac, b->A)) return rc;
+    Parts ps = b->pt;
+    ps.rho = ys;
+    ps.rhobar = ysb;
+    const double a = (s == 1 || s == 4) ? dt / 6.0 : dt / 3.0;
+    const double bc = (s == 3) ? dt : 0.5 * dt;
+    double* Lcur = (s % 2 == 0) ? La : Lb;
+    before_launch(b, CLS_OTHER);
+    if (b->pot)
+      k_adj_a<true><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, b->W, b->dirtab, srow, b->A, lambda, Lnext,
+                                                                 a, bc, Lcur, b->pt.acc);
+    else
+      k_adj_a<false><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, b->W, b->dirtab, srow, b->A, lambda, Lnext,
+                                                                  a, bc, Lcur, b->pt.acc);
+    if (int rc = after_launch(b, "adjoint stage kernel")) return rc;
+    if (int rc = launch_deposit(b, 3, b->pt.acc, nullptr, srow, frac, b->A)) return rc;
+    before_launch(b, CLS_OTHER);
+    k_adj_b<<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, b->W, b->dirtab, srow, b->A, Lcur, Lt, gN, gNbar);
+    if (int rc = after_launch(b, "adjoint interpolation kernel")) return rc;
+    Lnext = Lcur;
+  }
+  b->next_stage = 1;
+  return cuda_check(b, cudaMemcpyAsync(lambda, Lt, bytes18, cudaMemcpyDeviceToDevice, b->stream), "copy adjoint");
+}
+
+int emu_weight_gradient(emu_box* b, const double* gN, const double* gNbar, double* out, int on_host) {
+  if (int rc = check_bound(b)) return rc;
+  if (!gN || !gNbar || !out) return fail(b, EMU_EINVAL, "weight gradient: NULL pointer");
+  double* dst = on_host ? b->mom : out;  // staging: the moments buffer holds 72 NZ doubles
+  const int blocks = (b->S.NZ + kThreads - 1) / kThreads;
+  before_launch(b, CLS_OTHER);
+  k_weight_grad<<<blocks, kThreads, 0, b->stream>>>(batch_view(b), gN, gNbar, b->dirtab, dst);
+  if (int rc = after_launch(b, "weight gradient kernel")) return rc;
+  if (on_host) return copy_out(b, out, dst, sizeof(double) * 8 * b->S.NZ, 1);
   return EMU_OK;
 }
 

@@ -250,7 +250,8 @@ __device__ __forceinline__ void flush_tile(const double (&acc)[kNA], int64_t gti
 }
 
 // Deposit (Eq. 5), first launch.  MODE 0: B = N rho - Nbar rhobar^* (the
-// combination that enters H, Eq. 2); MODE 1: B = N rho; MODE 2: B = Nbar rhobar.
+// combination that enters H, Eq. 2); MODE 1: B = N rho; MODE 2: B = Nbar rhobar;
+// MODE 3: B = r_nu (packed matrices given per particle: the adjoint's Gamma).
 // Each warp walks its units in order (box, tile, direction), summing
 // w_pj (1, Omega_p) B_p over directions in registers (lane l owns cell
 // tile * 30 - 1 + l) and writing one partial per tile it touches; MODE 0 also
@@ -304,8 +305,8 @@ k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, c
       // cell j receives wr from the particle at j-1, w0 from its own, wl from j+1
       const double wr_l = __shfl_up_sync(kFull, wr, 1);
       const double wl_r = __shfl_down_sync(kFull, wl, 1);
-      const double n1 = (MODE != 2) ? __ldg(N + p) : 0.0;
-      const double n2 = (MODE != 1) ? __ldg(Nbar + p) : 0.0;
+      const double n1 = (MODE == 0 || MODE == 1) ? __ldg(N + p) : 0.0;
+      const double n2 = (MODE == 0 || MODE == 2) ? __ldg(Nbar + p) : 0.0;
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         double bv;
@@ -315,8 +316,10 @@ k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, c
           bv = (k == 4 || k == 6 || k == 8) ? fma(n2, y, n1 * x) : fma(-n2, y, n1 * x);
         } else if (MODE == 1) {
           bv = n1 * __ldg(r_nu + k * P + p);
-        } else {
+        } else if (MODE == 2) {
           bv = n2 * __ldg(r_nb + k * P + p);
+        } else {
+          bv = __ldg(r_nu + k * P + p);
         }
         const double bl = __shfl_up_sync(kFull, bv, 1);
         const double br = __shfl_down_sync(kFull, bv, 1);
@@ -713,6 +716,241 @@ __global__ void k_diagnostics(Batch B, const double* __restrict__ mom, double* _
     if (threadIdx.x == 0) out[63 * blockIdx.x + q] = sm[0] / g.nz;
     __syncthreads();
   }
+}
+
+// ------------------------------------------------------------------ adjoint
+//
+// Discrete adjoint of the RK4 step in the packed 9-real representation.  With
+// the packing metric D = diag(1, 1, 1, 2, ..., 2) (<X, Y>_Frobenius = x^T D y),
+// K(H, r) = -i[H, r] and the sign pattern S of Hbar = -H^* (packed: S H):
+//   transpose of r -> K(H, r):  m -> -D K(H, D^-1 m)   (the generator is anti-self-adjoint)
+//   transpose of H -> K(H, r):  m -> D K(r, D^-1 m)
+//   transpose of H -> K(S H + V, rbar):  m -> S D K(rbar, D^-1 m)
+// The self-interaction operator B -> H (deposit, Eq. 5, then interpolation,
+// Eq. 6, with the shared weights) is symmetric, so its transpose is the same
+// deposit-and-interpolate applied to the adjoint Gamma = dL/dH.
+
+__device__ __forceinline__ void kfull(const double H[9], const double r[9], double out[9]) {
+  double kd[3], ko[6];
+  commutator(H[0] - H[1], H[0] - H[2], H[1] - H[2], H[3], H[4], H[5], H[6], H[7], H[8], r, kd, ko);
+  out[0] = 2.0 * kd[0]; out[1] = 2.0 * kd[1]; out[2] = 2.0 * kd[2];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) out[3 + k] = ko[k];
+}
+
+// First adjoint launch of one stage.  m = a lam + b lamn (the adjoint of this
+// stage's derivative k_s); writes lam_out = J_rho^T m (direct terms) and
+// Gam = dL/dH_self.  pt.rho / pt.rhobar point at the stage state.
+template <bool POT>
+__global__ void __launch_bounds__(kThreads, 2)
+k_adj_a(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
+        const int* __restrict__ shift, const double* __restrict__ A, const double* __restrict__ lam,
+        const double* __restrict__ lamn, double a, double bc, double* __restrict__ lam_out,
+        double* __restrict__ Gam) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t u0 = unit_begin(w, B), u1 = unit_begin(w + 1, B);
+  if (u0 >= u1) return;
+  const int64_t P = B.Ptot;
+  const int MT = B.MT, NZ = B.NZ;
+  int b = box_of_unit(B, u0);
+  for (int64_t u = u0; u < u1; ++u) {
+    while (u >= B.box[b].uoff + (int64_t)B.box[b].ntiles * B.box[b].M) ++b;
+    const BoxGeo& g = B.box[b];
+    const int nz = g.nz, nt = g.ntiles;
+    const int lu = (int)(u - g.uoff);
+    const int d = lu / nt, tile = lu - d * nt;
+    const int craw = tile * kTile - 1 + lane, j = wrapc(craw, nz);
+    const bool active = lane >= 1 && lane <= kTile && craw < nz;
+    const int gd = g.doff + d;
+    const double ox = __ldg(dirtab + gd), oy = __ldg(dirtab + MT + gd), oz = __ldg(dirtab + 2 * MT + gd);
+    const int64_t p = g.poff + (int64_t)d * nz + wrapc(j - __ldg(shift + gd), nz);
+    double wl = 0.0, w0 = 0.0, wr = 0.0;
+    if (active) { wl = W[p]; w0 = W[P + p]; wr = W[2 * P + p]; }
+    double H[9];
+    const double* Aj = A + g.coff + j;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const double G = fma(-oz, __ldg(Aj + (int64_t)(27 + k) * NZ),
+                           fma(-oy, __ldg(Aj + (int64_t)(18 + k) * NZ),
+                               fma(-ox, __ldg(Aj + (int64_t)(9 + k) * NZ), __ldg(Aj + (int64_t)k * NZ))));
+      const double gl = __shfl_up_sync(kFull, G, 1), gr = __shfl_down_sync(kFull, G, 1);
+      H[k] = fma(wl, gl, fma(w0, G, wr * gr));
+    }
+    if (!active) continue;
+    double Gm[9];
+#pragma unroll
+    for (int which = 0; which < 2; ++which) {
+      double Hs[9], r[9], mh[9], t[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const bool im = (k == 4 || k == 6 || k == 8);
+        const double sgn = which ? (im ? 1.0 : -1.0) : 1.0;                 // S for antineutrinos
+        Hs[k] = sgn * H[k] + (POT ? __ldg((which ? g.vnubar : g.vnu) + k) : 0.0);
+        const double mk = a * lam[(which * 9 + k) * P + p] + (lamn ? bc * lamn[(which * 9 + k) * P + p] : 0.0);
+        mh[k] = k < 3 ? mk : 0.5 * mk;                                      // D^-1 m
+        r[k] = (which ? pt.rhobar : pt.rho)[k * P + p];
+      }
+      kfull(Hs, mh, t);                                                     // direct term: -D K(H, D^-1 m)
+#pragma unroll
+      for (int k = 0; k < 9; ++k) lam_out[(which * 9 + k) * P + p] = -(k < 3 ? t[k] : 2.0 * t[k]);
+      kfull(r, mh, t);                                                      // Gamma: D K(r, D^-1 m) (times S)
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const bool im = (k == 4 || k == 6 || k == 8);
+        const double v = k < 3 ? t[k] : 2.0 * t[k];
+        if (which == 0) Gm[k] = v;
+        else Gm[k] += (im ? v : -v);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Gam[k * P + p] = Gm[k];
+  }
+}
+
+// Second adjoint launch of one stage: GB = interpolation of the deposited
+// Gamma grid E (= dL/dB), then lam_out += N GB (rho) and -Nbar conj(GB)
+// (rhobar), gN += <GB, rho>, gNbar -= <conj(GB), rhobar>; finally
+// lam_tot += lam_out.
+__global__ void __launch_bounds__(kThreads, 2)
+k_adj_b(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
+        const int* __restrict__ shift, const double* __restrict__ E, double* __restrict__ lam_out,
+        double* __restrict__ lam_tot, double* __restrict__ gN, double* __restrict__ gNbar) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t u0 = unit_begin(w, B), u1 = unit_begin(w + 1, B);
+  if (u0 >= u1) return;
+  const int64_t P = B.Ptot;
+  const int MT = B.MT, NZ = B.NZ;
+  int b = box_of_unit(B, u0);
+  for (int64_t u = u0; u < u1; ++u) {
+    while (u >= B.box[b].uoff + (int64_t)B.box[b].ntiles * B.box[b].M) ++b;
+    const BoxGeo& g = B.box[b];
+    const int nz = g.nz, nt = g.ntiles;
+    const int lu = (int)(u - g.uoff);
+    const int d = lu / nt, tile = lu - d * nt;
+    const int craw = tile * kTile - 1 + lane, j = wrapc(craw, nz);
+    const bool active = lane >= 1 && lane <= kTile && craw < nz;
+    const int gd = g.doff + d;
+    const double ox = __ldg(dirtab + gd), oy = __ldg(dirtab + MT + gd), oz = __ldg(dirtab + 2 * MT + gd);
+    const int64_t p = g.poff + (int64_t)d * nz + wrapc(j - __ldg(shift + gd), nz);
+    double wl = 0.0, w0 = 0.0, wr = 0.0;
+    if (active) { wl = W[p]; w0 = W[P + p]; wr = W[2 * P + p]; }
+    double GB[9];
+    const double* Ej = E + g.coff + j;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const double G = fma(-oz, __ldg(Ej + (int64_t)(27 + k) * NZ),
+                           fma(-oy, __ldg(Ej + (int64_t)(18 + k) * NZ),
+                               fma(-ox, __ldg(Ej + (int64_t)(9 + k) * NZ), __ldg(Ej + (int64_t)k * NZ))));
+      const double gl = __shfl_up_sync(kFull, G, 1), gr = __shfl_down_sync(kFull, G, 1);
+      GB[k] = fma(wl, gl, fma(w0, G, wr * gr));
+    }
+    if (!active) continue;
+    const double n1 = pt.N[p], n2 = pt.Nbar[p];
+    double sN = 0.0, sNb = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const double c = (k == 4 || k == 6 || k == 8) ? -1.0 : 1.0;          // packed conjugation
+      const double r = pt.rho[k * P + p];
+      const double rb = pt.rhobar[k * P + p];
+      const double lr = fma(n1, GB[k], lam_out[k * P + p]);
+      const double lb = fma(-n2 * c, GB[k], lam_out[(9 + k) * P + p]);
+      lam_out[k * P + p] = lr;
+      lam_out[(9 + k) * P + p] = lb;
+      lam_tot[k * P + p] += lr;
+      lam_tot[(9 + k) * P + p] += lb;
+      sN = fma(GB[k], r, sN);
+      sNb = fma(-c * GB[k], rb, sNb);
+    }
+    gN[p] += sN;
+    gNbar[p] += sNb;
+  }
+}
+
+// Adjoint seed from a loss on the moments at the current positions: with
+// dmom = dL/d(mom) on the [72][NZ] layout of the moments (Eq. 5 per species),
+//   lam_rho,p    = N_p    (1/dV) sum_j w_pj (dmom_n,j    + Omega_p . dmom_f,j)
+//   lam_rhobar,p = Nbar_p (1/dV) sum_j w_pj (dmom_nbar,j + Omega_p . dmom_fbar,j)
+// and gN_p += lam_rho,p . rho_p / N_p (likewise gNbar); lam is overwritten.
+__global__ void __launch_bounds__(kThreads, 2)
+k_adj_seed(Batch B, Parts pt, const double* __restrict__ dirtab, const int* __restrict__ shift,
+           const double* __restrict__ dmom, double* __restrict__ lam, double* __restrict__ gN,
+           double* __restrict__ gNbar, int* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t u0 = unit_begin(w, B), u1 = unit_begin(w + 1, B);
+  if (u0 >= u1) return;
+  const int64_t P = B.Ptot;
+  const int MT = B.MT, NZ = B.NZ;
+  int bad = 0;
+  int b = box_of_unit(B, u0);
+  for (int64_t u = u0; u < u1; ++u) {
+    while (u >= B.box[b].uoff + (int64_t)B.box[b].ntiles * B.box[b].M) ++b;
+    const BoxGeo& g = B.box[b];
+    const int nz = g.nz, nt = g.ntiles;
+    const int lu = (int)(u - g.uoff);
+    const int d = lu / nt, tile = lu - d * nt;
+    const int craw = tile * kTile - 1 + lane, j = wrapc(craw, nz);
+    const bool active = lane >= 1 && lane <= kTile && craw < nz;
+    const int gd = g.doff + d;
+    const double ox = __ldg(dirtab + gd), oy = __ldg(dirtab + MT + gd), oz = __ldg(dirtab + 2 * MT + gd);
+    const int64_t p = g.poff + (int64_t)d * nz + wrapc(j - __ldg(shift + gd), nz);
+    double wl = 0.0, w0 = 0.0, wr = 0.0;
+    if (active) bad |= shape_weights(pt.z[p], (double)j + 0.5, g.inv_dz, g.nz_d, wl, w0, wr);
+    const double* Ej = dmom + g.coff + j;
+#pragma unroll
+    for (int which = 0; which < 2; ++which) {
+      const int64_t base = which * kNA;
+      double GB[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const double G = fma(oz, __ldg(Ej + (base + 27 + k) * NZ),
+                             fma(oy, __ldg(Ej + (base + 18 + k) * NZ),
+                                 fma(ox, __ldg(Ej + (base + 9 + k) * NZ), __ldg(Ej + (base + k) * NZ))));
+        const double gl = __shfl_up_sync(kFull, G, 1), gr = __shfl_down_sync(kFull, G, 1);
+        GB[k] = fma(wl, gl, fma(w0, G, wr * gr)) * g.inv_dV;
+      }
+      if (active) {
+        const double Nw = which ? pt.Nbar[p] : pt.N[p];
+        const double* r = which ? pt.rhobar : pt.rho;
+        double sN = 0.0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          lam[(which * 9 + k) * P + p] = Nw * GB[k];
+          sN = fma(GB[k], r[k * P + p], sN);
+        }
+        if (which) gNbar[p] += sN;
+        else gN[p] += sN;
+      }
+    }
+  }
+  if (bad) atomicOr(err, ERR_LATTICE);
+}
+
+// Chain rule through Eq. 8, N_p = (n_c + 3 f_c . Omega_p) dV / M with c the
+// particle's initial cell: per cell (thread) and in direction order,
+// out[0] dL/dn_nu, out[1] dL/dn_nubar, out[2..4] dL/df_nu, out[5..7] dL/df_nubar ([8][NZ]).
+__global__ void k_weight_grad(Batch B, const double* __restrict__ gN, const double* __restrict__ gNbar,
+                              const double* __restrict__ dirtab, double* __restrict__ out) {
+  const int gc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gc >= B.NZ) return;
+  const BoxGeo& g = B.box[box_of_cell(B, gc)];
+  const int c = gc - g.coff;
+  const double f = g.dV / g.M;
+  double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int d = 0; d < g.M; ++d) {
+    const int64_t p = g.poff + (int64_t)d * g.nz + c;
+    const int gd = g.doff + d;
+    const double o[3] = {dirtab[gd], dirtab[B.MT + gd], dirtab[2 * B.MT + gd]};
+    a[0] += gN[p];
+    a[1] += gNbar[p];
+    for (int i = 0; i < 3; ++i) {
+      a[2 + i] += 3.0 * o[i] * gN[p];
+      a[5 + i] += 3.0 * o[i] * gNbar[p];
+    }
+  }
+  for (int k = 0; k < 8; ++k) out[(int64_t)k * B.NZ + gc] = a[k] * f;
 }
 
 }  // namespace emu_dev

@@ -107,6 +107,10 @@ def load(build_if_missing: bool = False):
         "emu_batch_diagnostics": (i32, [vp, vp, i32]),
         "emu_autotune": (i32, [vp, i32, vp, vp]),
         "emu_set_oscillation": (i32, [vp, ctypes.c_int32, ctypes.POINTER(emu_oscillation)]),
+        "emu_adjoint_workspace_bytes": (i64, [cfgp]),
+        "emu_adjoint_seed": (i32, [vp, vp, vp, vp, vp]),
+        "emu_adjoint_step": (i32, [vp, dbl, vp, vp, vp, vp, i64]),
+        "emu_weight_gradient": (i32, [vp, vp, vp, vp, i32]),
         "emu_last_error": (ctypes.c_char_p, [vp]),
         "emu_destroy": (None, [vp]),
     }
@@ -320,6 +324,25 @@ def emu_set_oscillation(box, box_index: int, osc):
     _check(box, load().emu_set_oscillation(box, int(box_index), ptr))
 
 
+def emu_adjoint_workspace_bytes(cfg: emu_config) -> int:
+    n = load().emu_adjoint_workspace_bytes(ctypes.byref(cfg))
+    if n < 0:
+        raise EmuError(int(n), "invalid configuration")
+    return int(n)
+
+
+def emu_adjoint_seed(box, dmom, lam, gN, gNbar):
+    _check(box, load().emu_adjoint_seed(box, dmom, lam, gN, gNbar))
+
+
+def emu_adjoint_step(box, dt: float, lam, gN, gNbar, adj_ws, adj_ws_bytes: int):
+    _check(box, load().emu_adjoint_step(box, float(dt), lam, gN, gNbar, adj_ws, int(adj_ws_bytes)))
+
+
+def emu_weight_gradient(box, gN, gNbar, out, on_host: int):
+    _check(box, load().emu_weight_gradient(box, gN, gNbar, out, on_host))
+
+
 def emu_last_error(box) -> str:
     m = load().emu_last_error(box)
     return m.decode() if m else ""
@@ -466,6 +489,44 @@ class Box:
 
     def launches(self) -> int:
         return emu_kernel_launches(self.box)
+
+    # -- adjoint (single box; device tensors)
+    def _f64(self, *shape):
+        return self.torch.zeros(*shape, dtype=self.torch.float64, device=self.device)
+
+    def save_state(self, out=None):
+        """Positions and density matrices (the evolving state) copied into a
+        (19, P) device tensor: row 0 z, rows 1-9 rho, rows 10-18 rhobar."""
+        if out is None:
+            out = self.torch.empty(19, self.P, dtype=self.torch.float64, device=self.device)
+        emu_get_particles(self.box, out[0].data_ptr(), None, None, None, None, None, out[1].data_ptr(),
+                          out[10].data_ptr(), 0)
+        return out
+
+    def load_state(self, st):
+        emu_set_particles(self.box, st[0].data_ptr(), None, None, None, None, None, st[1].data_ptr(),
+                          st[10].data_ptr(), 0)
+
+    def adjoint_seed(self, dmom, lam, gN, gNbar):
+        """lam (18, P) = dL/d(rho, rhobar) from dmom = dL/d(moments) (72, nz);
+        adds the direct terms to gN, gNbar (P,)."""
+        dmom = dmom.to(dtype=self.torch.float64, device=self.device).contiguous()
+        emu_adjoint_seed(self.box, dmom.data_ptr(), lam.data_ptr(), gN.data_ptr(), gNbar.data_ptr())
+
+    def adjoint_step(self, dt, lam, gN, gNbar):
+        """One adjoint RK4 step from the step's start state (held by the box)."""
+        if getattr(self, "_adj_ws", None) is None:
+            n = emu_adjoint_workspace_bytes(self.cfg)
+            self._adj_raw = self.torch.empty(n + 256, dtype=self.torch.uint8, device=self.device)
+            self._adj_ws = ((self._adj_raw.data_ptr() + 255) & ~255, n)
+        ptr, n = self._adj_ws
+        emu_adjoint_step(self.box, dt, lam.data_ptr(), gN.data_ptr(), gNbar.data_ptr(), ptr, n)
+
+    def weight_gradient(self, gN, gNbar):
+        """(8, nz): dL/dn_nu, dL/dn_nubar, dL/df_nu (x, y, z), dL/df_nubar (x, y, z) per cell."""
+        out = self._f64(8, self.nz)
+        emu_weight_gradient(self.box, gN.data_ptr(), gNbar.data_ptr(), out.data_ptr(), 0)
+        return out
 
     def get_host(self) -> dict:
         """All particle fields copied to host numpy arrays (rho, rhobar as (9, P))."""

@@ -125,6 +125,17 @@ def random_box(nz: int, ndir: int, seed: int = 0, Lz: Optional[float] = None) ->
                     seed=seed, steps=10)
 
 
+def adjoint_box(alpha: float = 1e-20, seed: int = 0, nz: int = 256, ndir: int = 96, steps: int = 400) -> Workload:
+    """Box for gradients of the growth phase: tiny_fiducial's species and cell
+    size (dz = 13.42/32 cm) over nz cells (nz/8 fastest-growing wavelengths),
+    ndir Fibonacci directions, `steps` steps; alpha small enough that the
+    instability is still in its linear phase at the last step."""
+    n, nb = 4.9e32, 6.1e32
+    sp = _uniform_species(nz, n, nb, (0, 0, 0), (0, 0, -nb / 3.0))
+    return Workload(f"adjoint_{nz}x{ndir}", nz, ndir, 13.42 / 32 * nz, *sp, alpha=alpha, seed=seed, steps=steps,
+                    meta={"checkpoint_every": 20})
+
+
 def two_beam(nz: int = 64, n: float = 4.89e32) -> Workload:
     """Inhomogeneous two-beam test (App. A.4): a 1 cm box, one nu_e beam along
     +z and one nubar_e beam along -z of equal density n.  With two directions

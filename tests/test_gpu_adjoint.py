@@ -1,0 +1,212 @@
+"""Parity of the hand-written adjoint (emu_adjoint_seed / emu_adjoint_step /
+emu_weight_gradient behind paper_2101_02745_gb300.adjoint.Evolve) against
+central finite differences of the GPU forward path and the oracle's
+reference gradient (oracle/gradient.py).
+
+Objectives: final <n_ee> and log <|n_emu|> (Eq. 10); parameters: the species
+inputs of Eq. 8; the time step is held fixed.  Bar: 1e-5 relative (row norm)."""
+import json
+import time
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import gradient as og  # noqa: E402
+from paper_2101_02745_gb300 import workloads as W  # noqa: E402
+from paper_2101_02745_gb300.adjoint import Evolve, Simulation, objectives  # noqa: E402
+from paper_2101_02745_gb300.emu import Box, EmuError  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+GOLDEN = Path(__file__).resolve().parent / "golden"
+TOL = 1e-5
+
+
+def _theta(wl):
+    return np.concatenate([[wl.n_nu[0], wl.n_nubar[0]], wl.f_nu[0], wl.f_nubar[0]])
+
+
+def _fields(t, nz):
+    """Uniform per-cell fields from the 8 scalars (differentiable)."""
+    return t[0].expand(nz), t[1].expand(nz), t[2:5].expand(nz, 3), t[5:8].expand(nz, 3)
+
+
+def adjoint_gradient(sim, theta):
+    """(values (2,), gradient (2, 8)) of the two objectives by the adjoint."""
+    nz = sim.box.nz
+    g = np.zeros((2, 8))
+    vals = None
+    for k in range(2):
+        t = torch.tensor(theta, dtype=torch.float64, device="cuda", requires_grad=True)
+        L = objectives(Evolve.apply(*_fields(t, nz), sim))
+        L[k].backward()
+        g[k] = t.grad.cpu().numpy()
+        vals = L.detach().cpu().numpy()
+    return vals, g
+
+
+def forward_values(sim, theta):
+    nz = sim.box.nz
+    with torch.no_grad():
+        t = torch.tensor(theta, dtype=torch.float64, device="cuda")
+        return objectives(Evolve.apply(*_fields(t, nz), sim)).cpu().numpy()
+
+
+def fd_gradient(sim, theta, h=1e-6):
+    s = h * max(abs(theta[0]), abs(theta[1]))
+    g = np.zeros((2, 8))
+    for i in range(8):
+        e = np.zeros(8); e[i] = s
+        g[:, i] = (forward_values(sim, theta + e) - forward_values(sim, theta - e)) / (2 * s)
+    return g
+
+
+def rel_rows(a, b):
+    return [float(np.linalg.norm(a[k] - b[k]) / np.linalg.norm(b[k])) for k in range(2)]
+
+
+def _kw(wl):
+    return dict(nz=wl.nz, ndir=wl.ndir, Lz=wl.Lz, kappa=wl.kappa, c_light=wl.c_light)
+
+
+def test_small_box_vs_finite_differences_and_oracle():
+    wl = W.adjoint_box(nz=32, ndir=16, steps=60)
+    box = Box.from_workload(wl, init=False)
+    sim = Simulation(box, wl.steps, 3.4e-12, every=7, alpha=wl.alpha, seed=wl.seed)
+    th = _theta(wl)
+    vals, g = adjoint_gradient(sim, th)
+    g_fd = fd_gradient(sim, th)
+    g_or = og.fd_gradient(_kw(wl), th, wl.alpha, wl.seed, 3.4e-12, wl.steps)
+    v_or = og.evaluate(_kw(wl), th, wl.alpha, wl.seed, 3.4e-12, wl.steps)
+    assert np.allclose(vals, v_or, rtol=1e-12, atol=0)
+    assert max(rel_rows(g, g_fd)) < TOL, (g, g_fd)
+    assert max(rel_rows(g, g_or)) < TOL, (g, g_or)
+
+
+def test_per_cell_gradient_directional_derivative():
+    """Per-cell species (random densities, 3D fluxes): <grad, v> equals the
+    central difference of the objective along a random direction v."""
+    wl = W.random_box(40, 12, seed=5)
+    wl.alpha = 1e-8
+    box = Box.from_workload(wl, init=False)
+    sim = Simulation(box, 25, 8.0e-13, every=6, alpha=wl.alpha, seed=wl.seed)
+    base = [torch.tensor(a, dtype=torch.float64, device="cuda") for a in (wl.n_nu, wl.n_nubar, wl.f_nu, wl.f_nubar)]
+    rng = np.random.Generator(np.random.PCG64(9))
+    v = [torch.tensor(rng.normal(size=a.shape) * 1e31, dtype=torch.float64, device="cuda") for a in base]
+    for k in range(2):
+        leaves = [a.clone().requires_grad_(True) for a in base]
+        L = objectives(Evolve.apply(*leaves, sim))[k]
+        L.backward()
+        dirderiv = sum(float((l.grad * vi).sum()) for l, vi in zip(leaves, v))
+        eps = 1e-6 * 1e33 / 1e31
+        with torch.no_grad():
+            lp = objectives(Evolve.apply(*[a + eps * vi for a, vi in zip(base, v)], sim))[k]
+            lm = objectives(Evolve.apply(*[a - eps * vi for a, vi in zip(base, v)], sim))[k]
+        fd = float(lp - lm) / (2 * eps)
+        assert abs(dirderiv - fd) <= TOL * abs(fd), (k, dirderiv, fd)
+
+
+def test_with_vacuum_and_matter_terms():
+    """POT kernels: the constant H_vac + H_mat enters the transposed commutators."""
+    wl = W.adjoint_box(nz=32, ndir=16, steps=40)
+    osc = W.oscillation(mass_eV=(0.0, 8.6e-3, 5.0e-2), theta12=0.59, theta13=0.15, theta23=0.84, delta_cp=1.2,
+                        energy_MeV=5e-5, rho_g_cm3=1e9, Ye=0.4)
+    box = Box.from_workload(wl, init=False)
+    box.set_oscillation(osc)
+    sim = Simulation(box, wl.steps, 3.0e-12, every=9, alpha=1e-10, seed=wl.seed)
+    th = _theta(wl)
+    _, g = adjoint_gradient(sim, th)
+    g_fd = fd_gradient(sim, th)
+    kw = _kw(wl); kw["osc"] = osc
+    g_or = og.fd_gradient(kw, th, 1e-10, wl.seed, 3.0e-12, wl.steps)
+    assert max(rel_rows(g, g_fd)) < TOL, (g, g_fd)
+    assert max(rel_rows(g, g_or)) < TOL, (g, g_or)
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    wl = W.adjoint_box(nz=32, ndir=16, steps=24)
+    box = Box.from_workload(wl, init=False)
+    th = _theta(wl)
+    ref = None
+    for every in (1, 5, 24, 100):
+        _, g = adjoint_gradient(Simulation(box, wl.steps, 3.4e-12, every=every, alpha=wl.alpha, seed=wl.seed), th)
+        if ref is None:
+            ref = g
+        assert np.array_equal(g, ref), every
+
+
+def test_zero_steps_seed_only():
+    """nsteps = 0: the gradient is the seed's direct term through Eq. 8 alone."""
+    wl = W.adjoint_box(nz=30, ndir=8, steps=0)
+    box = Box.from_workload(wl, init=False)
+    sim = Simulation(box, 0, 3.4e-12, alpha=1e-6, seed=1)
+    th = _theta(wl)
+    _, g = adjoint_gradient(sim, th)
+    g_or = og.fd_gradient(_kw(wl), th, 1e-6, 1, 3.4e-12, 0)
+    assert max(rel_rows(g, g_or)) < TOL
+
+
+def test_adjoint_box_full_size_vs_oracle_reference_gradient():
+    """256 cells x 96 directions, 400 steps, checkpoints every 20 steps: the
+    adjoint against the oracle's stored central-difference gradient and against
+    central differences of the GPU forward path; backward cost reported."""
+    ref = json.loads((GOLDEN / "adjoint_256x96.json").read_text())
+    wl = W.adjoint_box()
+    assert (wl.nz, wl.ndir, wl.steps) == (ref["config"]["nz"], ref["config"]["ndir"], ref["nsteps"])
+    box = Box.from_workload(wl, init=False)
+    sim = Simulation(box, wl.steps, ref["dt"], every=20, alpha=ref["alpha"], seed=ref["seed"])
+    th = np.array(ref["theta"])
+    nz = box.nz
+    t = torch.tensor(th, dtype=torch.float64, device="cuda", requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L = objectives(Evolve.apply(*_fields(t, nz), sim))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    L[1].backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    g1 = t.grad.cpu().numpy()
+    vals, g = adjoint_gradient(sim, th)
+    assert np.array_equal(g[1], g1)
+    assert np.allclose(vals, ref["values"], rtol=1e-10, atol=0)
+    g_ref = np.array(ref["gradient"])
+    assert max(rel_rows(g, g_ref)) < TOL, (g, g_ref)
+    g_fd = fd_gradient(sim, th)
+    assert max(rel_rows(g, g_fd)) < TOL, (g, g_fd)
+    print(f"\nadjoint {wl.name}: forward {1e3 * (t1 - t0):.1f} ms, backward {1e3 * (t2 - t1):.1f} ms "
+          f"({(t2 - t1) / (t1 - t0):.2f}x), rel err vs oracle {rel_rows(g, g_ref)}, vs GPU FD {rel_rows(g, g_fd)}")
+
+
+def test_adjoint_bad_calls():
+    from paper_2101_02745_gb300 import emu as E
+
+    wl = W.adjoint_box(nz=32, ndir=4, steps=1)
+    box = Box.from_workload(wl)
+    P = box.P
+    lam = box._f64(18, P); gN = box._f64(P); gNb = box._f64(P)
+    n = E.emu_adjoint_workspace_bytes(box.cfg)
+    assert n == 90 * 8 * P
+    ws = torch.empty(n + 256, dtype=torch.uint8, device="cuda")
+    p = (ws.data_ptr() + 255) & ~255
+    with pytest.raises(EmuError):
+        E.emu_adjoint_step(box.box, 3e-12, lam.data_ptr(), gN.data_ptr(), gNb.data_ptr(), p, n - 8)
+    with pytest.raises(EmuError):
+        E.emu_adjoint_step(box.box, -1.0, lam.data_ptr(), gN.data_ptr(), gNb.data_ptr(), p, n)
+    with pytest.raises(EmuError):
+        E.emu_adjoint_step(box.box, 3e-12, lam.data_ptr(), gN.data_ptr(), gNb.data_ptr(), p + 8, n)
+    box.rk_stage(1, 3e-12)   # a step in progress
+    with pytest.raises(EmuError):
+        E.emu_adjoint_step(box.box, 3e-12, lam.data_ptr(), gN.data_ptr(), gNb.data_ptr(), p, n)
+    with pytest.raises(EmuError):
+        box.adjoint_seed(box._f64(72, box.nz), lam, gN, gNb)
+    for s in (2, 3, 4):
+        box.rk_stage(s, 3e-12)
+    E.emu_adjoint_step(box.box, 3e-12, lam.data_ptr(), gN.data_ptr(), gNb.data_ptr(), p, n)
+    box.sync()
+    batch = Box.from_workloads([wl, wl])
+    with pytest.raises(EmuError):
+        batch.adjoint_seed(batch._f64(72, batch.nz), batch._f64(18, batch.P), batch._f64(batch.P),
+                           batch._f64(batch.P))
