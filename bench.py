@@ -326,13 +326,21 @@ def run_gpu(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl.name, "nz": wl.nz, "ndir": wl.ndir, "particles_per_gpu": wl.P,
                        "dt_s": dt, "parallelism": f"replicas{world}" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (particle state 7.9 GB per GPU vs 129 MB L2)"},
+                       "l2": "inputs larger than L2 (particle state %.2f GB per GPU vs 129 MB L2)" % (wl.P * 480 / 1e9)},
             "roofline": roofline, "hbm": hbm,
             "kernels": {k: {"launches": n, "avg_ms": a, "share": ms / total} for k, (a, n, ms) in per.items() if n},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clk,
         }
+    del box, pin
+    torch.cuda.empty_cache()
+    extras = {}
+    if not args.no_extras:
+        extras["batched"] = measure_sweep(args, dist, device, rank, world, min(args.steps, 5))
+        extras["adjoint"] = measure_adjoint(dist, device, world, reps=1)
+    if rank == 0:
+        line.update(extras)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl)
         print(json.dumps(line), flush=True)
@@ -341,24 +349,16 @@ def run_gpu(args, rank, world, local_rank):
     return 0
 
 
-def run_sweep(args, rank, world, local_rank):
-    """Batched parameter sweep: 256 independent boxes of uneven sizes advanced
-    by one set of launches per step (CUDA graph replay, autotuned grid),
-    against the same boxes advanced one box at a time with the single-box
-    calls.  Both time K steps with CUDA events on the same stream."""
-    import numpy as np
+def measure_sweep(args, dist, device, rank, world, steps):
+    """Batched sweep against the same boxes one at a time: the parameter sweep's
+    independent boxes of uneven sizes advanced by one set of launches per step
+    (CUDA graph replay, autotuned grid) and, for comparison, by the single-box
+    calls box after box; both timed over `steps` steps with CUDA events."""
     import torch
 
-    from paper_2101_02745_gb300 import build as B
     from paper_2101_02745_gb300 import emu as E
     from paper_2101_02745_gb300 import workloads as W
 
-    if rank == 0:
-        B.build()
-    dist = dist_init(world, True)
-    device = torch.device("cuda", local_rank)
-    torch.cuda.set_device(device)
-    barrier(dist, device)
     wls = W.sweep(args.nbox, seed=rank)
     P = sum(w.P for w in wls)
     batch = E.Box.from_workloads(wls, device=device)
@@ -368,11 +368,10 @@ def run_sweep(args, rank, world, local_rank):
     stream = batch.stream
     barrier(dist, device)
     torch.cuda.synchronize(device)
-    clocks = ClockSampler(device.index).start()
     n0 = batch.launches()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    batch.batch_step(args.steps)
+    batch.batch_step(steps)
     ev1.record(stream)
     torch.cuda.synchronize(device)
     batched_ms = max_over_ranks(dist, ev0.elapsed_time(ev1), device)
@@ -380,37 +379,133 @@ def run_sweep(args, rank, world, local_rank):
     batch.sync()
     del batch
     torch.cuda.empty_cache()
-    # the same boxes one at a time, same step sizes, same stream
     singles = [E.Box.from_workload(w, device=device) for w in wls]
     for s_, dt in zip(singles, dts):
         s_.step(args.warmup, dt)
     torch.cuda.synchronize(device)
     ev0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         for s_, dt in zip(singles, dts):
             s_.step(1, dt)
     ev1.record(stream)
     torch.cuda.synchronize(device)
     single_ms = max_over_ranks(dist, ev0.elapsed_time(ev1), device)
-    clk = clocks.stop()
     for s_ in singles:
         s_.sync()
-    value = world * P * args.steps / (batched_ms * 1e-3)
+    del singles
+    torch.cuda.empty_cache()
+    return {"workload": f"sweep_{args.nbox}_boxes", "particles_per_gpu": P, "steps": steps,
+            "value": world * P * steps / (batched_ms * 1e-3), "ms_per_step": batched_ms / steps,
+            "launches_per_step": launches / steps, "autotune_choice": choice, "autotune_ms": list(cand_ms),
+            "one_at_a_time": {"value": world * P * steps / (single_ms * 1e-3), "ms_per_step": single_ms / steps},
+            "vs_plain": single_ms / batched_ms}
+
+
+def measure_adjoint(dist, device, world, reps=1):
+    """Gradient of log <|n_emu|> after the growth-phase run (256 cells x 96
+    directions, 400 steps, checkpoints every 20 steps) through the adjoint's
+    autograd Function, against the plain forward steps of the same run.
+    Times (CUDA events): plain = the 400 steps alone; forward = initialisation,
+    checkpointed steps and moments; backward = seed, checkpoint recomputation,
+    400 adjoint steps and the chain rule through Eq. 8."""
+    import torch
+
+    from paper_2101_02745_gb300 import emu as E
+    from paper_2101_02745_gb300 import workloads as W
+    from paper_2101_02745_gb300.adjoint import Evolve, Simulation, objectives
+
+    wl = W.adjoint_box()
+    box = E.Box.from_workload(wl, device=device)
+    dt = box.timestep()
+    sim = Simulation(box, wl.steps, dt, every=wl.meta["checkpoint_every"], alpha=wl.alpha, seed=wl.seed)
+    stream = box.stream
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    best = None
+    for r in range(reps + 1):            # the first pass is a warm-up
+        box.init(wl.n_nu, wl.n_nubar, wl.f_nu, wl.f_nubar, wl.dirs, wl.alpha, wl.seed)
+        torch.cuda.synchronize(device)
+        ev[0].record(stream)
+        box.step(wl.steps, dt)
+        ev[1].record(stream)
+        leaves = [torch.tensor(a, dtype=torch.float64, device=device, requires_grad=True)
+                  for a in (wl.n_nu, wl.n_nubar, wl.f_nu, wl.f_nubar)]
+        n0 = box.launches()
+        ev[2].record(stream)
+        L = objectives(Evolve.apply(*leaves, sim))
+        ev[3].record(stream)
+        L[1].backward()
+        ev[4].record(stream)
+        torch.cuda.synchronize(device)
+        launches = box.launches() - n0
+        t = [ev[i].elapsed_time(ev[i + 1]) for i in (0, 2, 3)]
+        if r > 0 and (best is None or sum(t[1:]) < sum(best[1:])):
+            best = t
+    plain, fwd, bwd = (max_over_ranks(dist, x, device) for x in best)
+    upd = wl.P * wl.steps
+    return {"workload": wl.name, "particles": wl.P, "steps": wl.steps, "checkpoint_every": sim.every,
+            "value": world * upd / ((fwd + bwd) * 1e-3), "unit": "differentiated particle-updates/s",
+            "plain_value": world * upd / (plain * 1e-3),
+            "plain_ms": plain, "forward_ms": fwd, "backward_ms": bwd,
+            "backward_over_forward": bwd / fwd, "vs_plain": plain / (fwd + bwd),
+            "launches_per_gradient": launches}
+
+
+def run_adjoint(args, rank, world, local_rank):
+    """--workload adjoint: one line whose value is the gradient's throughput."""
+    import torch
+
+    from paper_2101_02745_gb300 import build as B
+
+    if rank == 0:
+        B.build()
+    dist = dist_init(world, True)
+    device = torch.device("cuda", local_rank)
+    torch.cuda.set_device(device)
+    barrier(dist, device)
+    clocks = ClockSampler(device.index).start()
+    a = measure_adjoint(dist, device, world, reps=args.steps)
+    clk = clocks.stop()
+    if rank == 0:
+        line = {"metric": METRIC, "value": a["value"], "unit": a["unit"], "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": (a["forward_ms"] + a["backward_ms"]) / a["steps"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": a["workload"], "particles_per_gpu": a["particles"], "steps": a["steps"],
+                           "checkpoint_every": a["checkpoint_every"],
+                           "l2": "working set below L2 (small box; the adjoint's own config)"},
+                "adjoint": a, "gpu_launches": a["launches_per_gradient"], "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_sweep(args, rank, world, local_rank):
+    """--workload sweep: the batched sweep's own line (value = batched rate)."""
+    import torch
+
+    from paper_2101_02745_gb300 import build as B
+
+    if rank == 0:
+        B.build()
+    dist = dist_init(world, True)
+    device = torch.device("cuda", local_rank)
+    torch.cuda.set_device(device)
+    barrier(dist, device)
+    clocks = ClockSampler(device.index).start()
+    r = measure_sweep(args, dist, device, rank, world, args.steps)
+    clk = clocks.stop()
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": batched_ms / args.steps, "higher_is_better": True,
+            "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"sweep_{args.nbox}_boxes", "boxes": args.nbox, "particles_per_gpu": P,
+            "config": {"workload": r["workload"], "boxes": args.nbox, "particles_per_gpu": r["particles_per_gpu"],
                        "nz_range": [64, 1024], "ndir_range": [48, 378],
-                       "l2": "inputs larger than L2 (particle state %.1f GB per GPU)" % (P * 480 / 1e9)},
-            "batched": {"value": value, "ms_per_step": batched_ms / args.steps, "launches_per_step":
-                        launches / args.steps, "autotune_choice": choice, "autotune_ms": list(cand_ms)},
-            "one_at_a_time": {"value": world * P * args.steps / (single_ms * 1e-3),
-                              "ms_per_step": single_ms / args.steps},
-            "speedup": single_ms / batched_ms,
-            "gpu_launches": launches,
-            "clocks": clk,
+                       "l2": "inputs larger than L2 (particle state %.1f GB per GPU)"
+                             % (r["particles_per_gpu"] * 480 / 1e9)},
+            "batched": r, "speedup": r["vs_plain"],
+            "gpu_launches": int(r["launches_per_step"] * args.steps), "clocks": clk,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -424,13 +519,15 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="throughput_1d",
-                    choices=["throughput_1d", "paper_1d", "paper_1d_asym", "tiny_fiducial", "sweep"])
+                    choices=["throughput_1d", "paper_1d", "paper_1d_asym", "tiny_fiducial", "sweep", "adjoint"])
     ap.add_argument("--nbox", type=int, default=256, help="boxes of the sweep workload")
     ap.add_argument("--nz", type=int, default=0, help="cells of the throughput workload (profiling runs)")
     ap.add_argument("--ndir", type=int, default=0, help="directions of the throughput workload (profiling runs)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-cells", type=int, default=256, help="cells per oracle step in --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-sweep and adjoint comparisons of the default line")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -439,6 +536,8 @@ def main(argv=None):
         return run_reference(args, rank, world)
     if args.workload == "sweep":
         return run_sweep(args, rank, world, local_rank)
+    if args.workload == "adjoint":
+        return run_adjoint(args, rank, world, local_rank)
     return run_gpu(args, rank, world, local_rank)
 
 

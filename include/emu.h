@@ -78,7 +78,8 @@ typedef struct {
   double c_light;      /* speed of light [cm/s] */
   double cfl_adv;      /* C of Eq. 7 */
   double cfl_flavor;   /* C_F of Eq. 7 */
-  int32_t shape_order; /* particle shape order (Sec. 2.2.1); only 2 (quadratic) is supported */
+  int32_t shape_order; /* particle shape (Sec. 2.2.1): degree 0-3 of the B-spline, 2 = quadratic (the
+                          paper's choice); all boxes of a batch use one order */
   int32_t reserved;    /* must be 0 */
 } emu_config;
 
@@ -327,6 +328,7 @@ int emu_kernel_times(emu_box* box, double* ms_out, int64_t* count_out);
  *     (rho/rhobar as [9][P]); output: A_out, a device array [36][nz] that
  *     receives the grid potential A (as emu_deposit) of the state at positions
  *     z + pos_dt * c * Omega_z.  stream is a cudaStream_t (NULL: legacy stream).
+ *     The quadratic shape only (cfg->shape_order 2, else EMU_EINVAL).
  *   - The scratch needs 21 MB of per-warp partial sums, 8.6 KB per 30-cell
  *     tile and 36 bytes per direction; a box that does not fit in 32 MiB
  *     (roughly nz above 43,000 or ndir above 340,000) is rejected with

@@ -75,9 +75,26 @@ def discrete_growth(k, dirs, g, gbar, kappa, c_light, S=1.0):
     return _growth(k * c_light, eps, dirs[:, 2], K, g, gbar, kappa, S)
 
 
-def shape_transfer(k, dz):
-    """W(k)^2 for the quadratic shape with particles at cell centres."""
-    W = 0.75 + 0.25 * np.cos(k * dz)
+def shape_transfer(k, dz, order=2, spread=False):
+    """W(k)^2, the deposit-then-interpolate factor of a Fourier mode.
+    spread=False: particles at cell centres, W(k) = sum_m M(m) cos(k m dz)
+    with M the B-spline shape of the given order sampled at the integers
+    (order 0 and 1: W = 1; 2: 3/4 + cos(k dz)/4; 3: 2/3 + cos(k dz)/3).
+    spread=True: particle offsets spread evenly over the cell (moving
+    particles of many directions), W(k) = the B-spline's Fourier transform
+    sinc(k dz / 2)^(order + 1)."""
+    if spread:
+        x = 0.5 * k * dz
+        return (np.sin(x) / x if x != 0 else 1.0) ** (2 * (order + 1))
+    from scipy.interpolate import BSpline
+
+    knots = np.arange(order + 2) - 0.5 * (order + 1)
+    B = BSpline.basis_element(knots, extrapolate=False)
+    W = 0.0
+    for m in range(-(order // 2) - 1, order // 2 + 2):
+        v = B(float(m)) if knots[0] <= m < knots[-1] else 0.0
+        v = 0.0 if np.isnan(v) else float(v)
+        W = W + v * np.cos(k * m * dz)
     return W * W
 
 

@@ -12,7 +12,8 @@
  *
  * What it computes (one explicit RK4 step of the 1D periodic PIC scheme):
  *   - particle -> grid deposit of n_ab, f_ab (neutrinos) and nbar_ab, fbar_ab
- *     (antineutrinos) with the quadratic shape function        (Eq. 5, Sec. 2.2.1)
+ *     (antineutrinos) with a shape function of order 0-3
+ *     (quadratic by default)                                   (Eq. 5, Sec. 2.2.1)
  *   - grid -> particle interpolation                          (Eq. 6, Sec. 2.2.2)
  *   - the self-interaction Hamiltonian and its antineutrino
  *     counterpart Hbar = -H*                                   (Eq. 2, Sec. 2.1)
@@ -29,9 +30,10 @@
  *     [cm^3/s] is an input.
  *   - Cell volume dV = dz * area (area is an input, 1 cm^2 by default); it
  *     cancels between the weights of Eq. 8 and the deposit of Eq. 5.
- *   - Quadratic shape: xi = z/dz - 1/2, j* = floor(xi + 1/2), d = xi - j*,
- *     weights 1/2 (1/2 - d)^2, 3/4 - d^2, 1/2 (1/2 + d)^2 on cells j*-1, j*, j*+1
- *     (textbook quadratic B-spline), indices taken modulo nz (periodic, Sec. 2.3).
+ *   - Shape of order n (the paper offers orders 0 to 3 and uses 2): the
+ *     cardinal B-spline of degree n, w_pj = M_{n+1}(z_p/dz - (j + 1/2)), on
+ *     the n+1 cells it reaches, indices taken modulo nz (periodic, Sec. 2.3).
+ *     Order 0 puts a particle on z = j dz in cell j (the cell containing it).
  *   - "Fourth-order explicit Runge-Kutta" is the classic tableau
  *     (0, 1/2, 1/2, 1; weights 1/6, 1/3, 1/3, 1/6).  No renormalisation of rho.
  *   - Eq. 9: eps_mu = |rho_emu|^2, eps_tau = |rho_etau|^2, rho_mutau = 0.
@@ -69,7 +71,7 @@ typedef struct {
    * phase delta [rad] of the standard three-angle mixing matrix, neutrino
    * energy [erg], net electron density n_e [cm^-3], hbar [erg s], erg per eV. */
   int32_t osc_on;
-  int32_t pad;
+  int32_t shape_order; /* 0..3: degree of the B-spline shape (Sec. 2.2.1), 2 = quadratic */
   double mass_eV[3];
   double theta12, theta13, theta23, delta_cp;
   double energy_erg;
@@ -133,22 +135,40 @@ double or_wrap(const or_config* cfg, double z) {
   return w;
 }
 
-/* Quadratic shape function: the three cells touched by a particle at z and
- * the fraction w_pj of the particle in each (Sec. 2.2.1, the w_pj of Eq. 5). */
-void or_shape(const or_config* cfg, double z, int32_t cells[3], double w[3]) {
-  double dz = or_dz(cfg);
-  double xi = z / dz - 0.5;          /* position in units of cells, measured from cell-0 centre */
-  double jstar = floor(xi + 0.5);    /* nearest cell centre */
-  double d = xi - jstar;             /* offset from it, in [-1/2, 1/2) */
-  w[0] = 0.5 * (0.5 - d) * (0.5 - d);
-  w[1] = 0.75 - d * d;
-  w[2] = 0.5 * (0.5 + d) * (0.5 + d);
-  long long j = (long long)jstar;
-  for (int s = 0; s < 3; ++s) {
-    long long c = (j - 1 + s) % cfg->nz;
+/* Cardinal B-spline of degree n (support (-(n+1)/2, (n+1)/2), unit integral)
+ * from its truncated-power form
+ *   M_{n+1}(x) = (1/n!) sum_{k=0}^{n+1} (-1)^k C(n+1, k) (x + (n+1)/2 - k)_+^n,
+ * with t_+^0 = 1 for t >= 0 (so that M_1 is 1 on [-1/2, 1/2)). */
+double or_bspline(int n, double x) {
+  double sum = 0.0, binom = 1.0, fact = 1.0;
+  for (int k = 2; k <= n; ++k) fact *= k;
+  for (int k = 0; k <= n + 1; ++k) {
+    double t = x + 0.5 * (n + 1) - k;
+    double tp = 0.0;
+    if (n == 0) tp = t >= 0.0 ? 1.0 : 0.0;
+    else if (t > 0.0) tp = pow(t, n);
+    sum += (k % 2 ? -binom : binom) * tp;
+    binom = binom * (n + 1 - k) / (k + 1);
+  }
+  return sum / fact;
+}
+
+/* Shape function of order n = cfg->shape_order (Sec. 2.2.1): the n+1 cells
+ * j with |x_j| < (n+1)/2, x_j = z/dz - (j + 1/2) the particle's offset from
+ * the centre of cell j in cell units, and the fraction w_pj = M_{n+1}(x_j)
+ * of the particle in each (the w_pj of Eq. 5).  Returns the count n+1. */
+int or_shape(const or_config* cfg, double z, int32_t cells[4], double w[4]) {
+  int n = cfg->shape_order;
+  double xi = z / or_dz(cfg) - 0.5;                 /* offset from the centre of cell 0 */
+  long long j0 = (long long)floor(xi - 0.5 * (n + 1)) + 1;   /* first cell inside the support */
+  for (int s = 0; s <= n; ++s) {
+    long long j = j0 + s;
+    w[s] = or_bspline(n, xi - (double)j);
+    long long c = j % cfg->nz;
     if (c < 0) c += cfg->nz;
     cells[s] = (int32_t)c;
   }
+  return n + 1;
 }
 
 /* ------------------------------------------------------- initialisation --- */
@@ -219,9 +239,9 @@ void or_deposit(const or_config* cfg, const or_particle* parts, int64_t P, or_ce
   memset(grid, 0, sizeof(or_cell) * (size_t)cfg->nz);
   for (int64_t p = 0; p < P; ++p) {
     const or_particle* q = &parts[p];
-    int32_t cells[3]; double w[3];
-    or_shape(cfg, q->z, cells, w);
-    for (int s = 0; s < 3; ++s) {
+    int32_t cells[4]; double w[4];
+    int ns = or_shape(cfg, q->z, cells, w);
+    for (int s = 0; s < ns; ++s) {
       or_cell* g = &grid[cells[s]];
       double cn = q->N * w[s] / dV, cb = q->Nbar * w[s] / dV;
       for (int a = 0; a < 3; ++a)
@@ -244,10 +264,10 @@ void or_deposit(const or_config* cfg, const or_particle* parts, int64_t P, or_ce
  *   H = kappa [ (n - nbar^*) - Omega . (f - fbar^*) ].
  * Vacuum and matter terms are not part of this path. */
 void or_hamiltonian(const or_config* cfg, const or_cell* grid, const or_particle* q, cplx H[3][3]) {
-  int32_t cells[3]; double w[3];
-  or_shape(cfg, q->z, cells, w);
+  int32_t cells[4]; double w[4];
+  int ns = or_shape(cfg, q->z, cells, w);
   cplx n[3][3] = {{0}}, nb[3][3] = {{0}}, f[3][3][3] = {{{0}}}, fb[3][3][3] = {{{0}}};
-  for (int s = 0; s < 3; ++s) {
+  for (int s = 0; s < ns; ++s) {
     const or_cell* g = &grid[cells[s]];
     for (int a = 0; a < 3; ++a)
       for (int b = 0; b < 3; ++b) {

@@ -56,7 +56,7 @@ class OrConfig(ctypes.Structure):
         ("cfl_adv", ctypes.c_double),
         ("cfl_flavor", ctypes.c_double),
         ("osc_on", ctypes.c_int32),
-        ("pad", ctypes.c_int32),
+        ("shape_order", ctypes.c_int32),
         ("mass_eV", ctypes.c_double * 3),
         ("theta12", ctypes.c_double),
         ("theta13", ctypes.c_double),
@@ -94,7 +94,8 @@ def lib():
         L.or_uniform.argtypes = [u64, i64, ctypes.c_int]; L.or_uniform.restype = dbl
         L.or_fibonacci_direction.argtypes = [ctypes.c_int, ctypes.c_int, vp]; L.or_fibonacci_direction.restype = None
         L.or_wrap.argtypes = [cfgp, dbl]; L.or_wrap.restype = dbl
-        L.or_shape.argtypes = [cfgp, dbl, vp, vp]; L.or_shape.restype = None
+        L.or_shape.argtypes = [cfgp, dbl, vp, vp]; L.or_shape.restype = ctypes.c_int
+        L.or_bspline.argtypes = [ctypes.c_int, dbl]; L.or_bspline.restype = dbl
         L.or_init.argtypes = [cfgp, vp, vp, vp, vp, vp, dbl, u64, vp]; L.or_init.restype = ctypes.c_int
         L.or_deposit.argtypes = [cfgp, vp, i64, vp]; L.or_deposit.restype = None
         L.or_hamiltonian.argtypes = [cfgp, vp, vp, vp]; L.or_hamiltonian.restype = None
@@ -122,11 +123,16 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def config(nz, ndir, Lz, kappa, c_light, cfl_adv=0.4, cfl_flavor=0.4, area=1.0, osc=None) -> OrConfig:
+def config(nz, ndir, Lz, kappa, c_light, cfl_adv=0.4, cfl_flavor=0.4, area=1.0, osc=None,
+           shape_order=2) -> OrConfig:
     """osc: None, or a dict with mass_eV (3), theta12, theta13, theta23, delta_cp [rad],
-    energy_erg, n_e [cm^-3], hbar [erg s], erg_per_eV (vacuum and matter terms of Eq. 2)."""
+    energy_erg, n_e [cm^-3], hbar [erg s], erg_per_eV (vacuum and matter terms of Eq. 2).
+    shape_order: degree 0..3 of the B-spline particle shape (Sec. 2.2.1)."""
+    if shape_order not in (0, 1, 2, 3):
+        raise ValueError("shape_order must be 0, 1, 2 or 3")
     c = OrConfig(int(nz), int(ndir), float(Lz), float(area), float(kappa), float(c_light),
                  float(cfl_adv), float(cfl_flavor))
+    c.shape_order = int(shape_order)
     if osc is not None:
         c.osc_on = 1
         for i, m in enumerate(osc["mass_eV"]):
@@ -164,11 +170,21 @@ def fibonacci_direction(d: int, M: int) -> np.ndarray:
     return out
 
 
+def wrap(cfg: OrConfig, z: float) -> float:
+    """z mapped into [0, Lz) (periodic domain)."""
+    return float(lib().or_wrap(ctypes.byref(cfg), float(z)))
+
+
 def shape(cfg: OrConfig, z: float):
-    cells = np.zeros(3, np.int32)
-    w = np.zeros(3)
-    lib().or_shape(ctypes.byref(cfg), float(z), _ptr(cells), _ptr(w))
-    return cells, w
+    """(cells, weights) of a particle at z: shape_order + 1 of each."""
+    cells = np.zeros(4, np.int32)
+    w = np.zeros(4)
+    n = lib().or_shape(ctypes.byref(cfg), float(z), _ptr(cells), _ptr(w))
+    return cells[:n], w[:n]
+
+
+def bspline(n: int, x: float) -> float:
+    return float(lib().or_bspline(int(n), float(x)))
 
 
 def init(cfg: OrConfig, n_nu, n_nubar, f_nu, f_nubar, alpha=1e-6, seed=0, dirs=None):

@@ -17,6 +17,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.cuh"
@@ -34,8 +35,27 @@ struct Shape {
   int nbox = 0;
   int64_t Ptot = 0, U = 0;
   int NZ = 0, MT = 0, NT = 0;
+  int order = 2;   // shape order of every box (Sec. 2.2.1)
+  int T = 30;      // cells per tile for that order
   std::vector<BoxGeo> geo;
 };
+
+// Cells per tile and kept weight arrays of a shape order (Sten<> on the host).
+int tile_cells(int order) { return order == 3 ? Sten<3>::T : Sten<2>::T; }
+int kept_weights(int order) {
+  return order == 0 ? Sten<0>::NWS : order == 1 ? Sten<1>::NWS : order == 2 ? Sten<2>::NWS : Sten<3>::NWS;
+}
+
+// Calls f(std::integral_constant<int, ORDER>) for the runtime shape order.
+template <typename F>
+int by_order(int order, F&& f) {
+  switch (order) {
+    case 0: return f(std::integral_constant<int, 0>{});
+    case 1: return f(std::integral_constant<int, 1>{});
+    case 2: return f(std::integral_constant<int, 2>{});
+    default: return f(std::integral_constant<int, 3>{});
+  }
+}
 
 const char* config_problem(const emu_config* c) {
   if (!c) return "config is NULL";
@@ -47,7 +67,7 @@ const char* config_problem(const emu_config* c) {
   if (!(c->kappa > 0) || !std::isfinite(c->kappa)) return "kappa must be positive and finite";
   if (!(c->c_light > 0) || !std::isfinite(c->c_light)) return "c_light must be positive and finite";
   if (!(c->cfl_adv > 0) || !(c->cfl_flavor > 0)) return "CFL factors must be positive";
-  if (c->shape_order != 2) return "only the quadratic shape (shape_order = 2) is supported";
+  if (c->shape_order < 0 || c->shape_order > 3) return "shape_order must be 0, 1, 2 or 3";
   if (c->reserved != 0) return "reserved must be 0";
   return nullptr;
 }
@@ -58,15 +78,18 @@ const char* make_shape(const emu_config* cfgs, int nbox, Shape& S) {
   S = Shape();
   S.nbox = nbox;
   S.geo.resize(nbox);
+  S.order = cfgs[0].shape_order;
+  S.T = tile_cells(S.order);
   int64_t NZ = 0, MT = 0, NT = 0;
   for (int b = 0; b < nbox; ++b) {
     const emu_config* c = &cfgs[b];
     if (const char* why = config_problem(c)) return why;
+    if (c->shape_order != S.order) return "all boxes of a batch must use the same shape order";
     BoxGeo& g = S.geo[b];
     std::memset(&g, 0, sizeof(g));
     g.nz = c->nz;
     g.M = c->ndir;
-    g.ntiles = (c->nz + kTile - 1) / kTile;
+    g.ntiles = (c->nz + S.T - 1) / S.T;
     g.P = (int64_t)c->nz * c->ndir;
     g.poff = S.Ptot;
     g.uoff = S.U;
@@ -112,7 +135,7 @@ Layout layout(const Shape& S) {
   L.A = take(sizeof(double) * kNA * NZ);
   L.mom = take(sizeof(double) * kNM * NZ);
   L.partial = take(sizeof(double) * (size_t)(kMaxWarps + S.NT) * kSlot);
-  L.W = take(sizeof(double) * 3 * (size_t)S.Ptot);
+  L.W = take(sizeof(double) * kept_weights(S.order) * (size_t)S.Ptot);
   L.err = take(sizeof(int));
   L.dirtab = take(sizeof(double) * 4 * MT);
   L.shift = take(sizeof(int) * 4 * MT);
@@ -194,6 +217,7 @@ Batch batch_view(const emu_box* b) {
   B.NZ = b->S.NZ;
   B.MT = b->S.MT;
   B.NT = b->S.NT;
+  B.T = b->S.T;
   B.U = b->S.U;
   B.Ptot = b->S.Ptot;
   return B;
@@ -285,18 +309,27 @@ int launch_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, c
                    double* out) {
   const Batch B = batch_view(b);
   before_launch(b, CLS_DEPOSIT);
-  if (mode == 0)
-    k_deposit<0><<<persist_grid(b), kThreads, 0, b->stream>>>(B, b->pt.z, b->pt.N, b->pt.Nbar, rnu, rnb, b->dirtab,
-        shift_row, frac, b->partial, b->W, b->err);
-  else if (mode == 1)
-    k_deposit<1><<<persist_grid(b), kThreads, 0, b->stream>>>(B, b->pt.z, b->pt.N, b->pt.Nbar, rnu, rnb, b->dirtab,
-        shift_row, frac, b->partial, nullptr, b->err);
-  else if (mode == 2)
-    k_deposit<2><<<persist_grid(b), kThreads, 0, b->stream>>>(B, b->pt.z, b->pt.N, b->pt.Nbar, rnu, rnb, b->dirtab,
-        shift_row, frac, b->partial, nullptr, b->err);
-  else
-    k_deposit<3><<<persist_grid(b), kThreads, 0, b->stream>>>(B, b->pt.z, b->pt.N, b->pt.Nbar, rnu, rnb, b->dirtab,
-        shift_row, frac, b->partial, nullptr, b->err);
+  const dim3 grid = persist_grid(b);
+  cudaStream_t st = b->stream;
+  const double* z = b->pt.z;
+  const double* N = b->pt.N;
+  const double* Nb = b->pt.Nbar;
+  by_order(b->S.order, [&](auto O) {
+    constexpr int R = decltype(O)::value;
+    if (mode == 0)
+      k_deposit<0, R><<<grid, kThreads, 0, st>>>(B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
+                                                 b->W, b->err);
+    else if (mode == 1)
+      k_deposit<1, R><<<grid, kThreads, 0, st>>>(B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
+                                                 nullptr, b->err);
+    else if (mode == 2)
+      k_deposit<2, R><<<grid, kThreads, 0, st>>>(B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
+                                                 nullptr, b->err);
+    else
+      k_deposit<3, R><<<grid, kThreads, 0, st>>>(B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
+                                                 nullptr, b->err);
+    return 0;
+  });
   if (int rc = after_launch(b, "deposit kernel")) return rc;
   before_launch(b, CLS_COMBINE);
   k_combine<<<combine_blocks(B.NZ), kThreads, 0, b->stream>>>(B, b->partial, out, (mode == 0 || mode == 3) ? 1 : 0,
@@ -313,12 +346,16 @@ int launch_stage(emu_box* b, int s, int dry) {
   const int* srow = b->shift + (size_t)(s - 1) * b->S.MT;
   if (int rc = launch_deposit(b, 0, rnu, rnb, srow, kStageFrac[s - 1], b->A)) return rc;
   before_launch(b, CLS_RK);
-  if (b->pot)
-    k_rk_stage<true><<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->W, b->dirtab, srow, b->A,
-                                                                  s, dry);
-  else
-    k_rk_stage<false><<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->W, b->dirtab, srow,
-                                                                   b->A, s, dry);
+  by_order(b->S.order, [&](auto O) {
+    constexpr int R = decltype(O)::value;
+    if (b->pot)
+      k_rk_stage<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->W, b->dirtab, srow,
+                                                                       b->A, s, dry);
+    else
+      k_rk_stage<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->W, b->dirtab, srow,
+                                                                        b->A, s, dry);
+    return 0;
+  });
   return after_launch(b, "RK stage kernel");
 }
 
@@ -582,8 +619,11 @@ int emu_interpolate_H(emu_box* b, double pos_dt, double* H_out, int on_host) {
   double* dst = H_out;
   if (on_host) dst = b->pt.acc;  // staging: the RK scratch holds 18 P doubles
   before_launch(b, CLS_OTHER);
-  k_interpolate<<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt.z, b->dirtab, b->shift, b->A, 1.0,
-                                                            dst, b->err);
+  by_order(b->S.order, [&](auto O) {
+    k_interpolate<decltype(O)::value><<<persist_grid(b), kThreads, 0, b->stream>>>(
+        batch_view(b), b->pt.z, b->dirtab, b->shift, b->A, 1.0, dst, b->err);
+    return 0;
+  });
   if (int rc = after_launch(b, "interpolation kernel")) return rc;
   b->next_stage = 1;  // the staging above may overwrite the RK scratch
   if (on_host) return copy_out(b, H_out, dst, sizeof(double) * 9 * (size_t)b->S.Ptot, 1);
@@ -811,8 +851,11 @@ int emu_adjoint_seed(emu_box* b, const double* dmom, double* lambda, double* gN,
   const double zero = 0.0;
   if (int rc = launch_shifts(b, &zero, 1)) return rc;
   before_launch(b, CLS_OTHER);
-  k_adj_seed<<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->dirtab, b->shift, dmom, lambda,
-                                                          gN, gNbar, b->err);
+  by_order(b->S.order, [&](auto O) {
+    k_adj_seed<decltype(O)::value><<<persist_grid(b), kThreads, 0, b->stream>>>(
+        batch_view(b), b->pt, b->dirtab, b->shift, dmom, lambda, gN, gNbar, b->err);
+    return 0;
+  });
   return after_launch(b, "adjoint seed kernel");
 }
 
@@ -863,16 +906,24 @@ int emu_adjoint_step(emu_box* b, double dt, double* lambda, double* gN, double* 
     const double bc = (s == 3) ? dt : 0.5 * dt;
     double* Lcur = (s % 2 == 0) ? La : Lb;
     before_launch(b, CLS_OTHER);
-    if (b->pot)
-      k_adj_a<true><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, b->W, b->dirtab, srow, b->A, lambda, Lnext,
-                                                                 a, bc, Lcur, b->pt.acc);
-    else
-      k_adj_a<false><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, b->W, b->dirtab, srow, b->A, lambda, Lnext,
-                                                                  a, bc, Lcur, b->pt.acc);
+    by_order(b->S.order, [&](auto O) {
+      constexpr int R = decltype(O)::value;
+      if (b->pot)
+        k_adj_a<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, b->W, b->dirtab, srow, b->A, lambda,
+                                                                      Lnext, a, bc, Lcur, b->pt.acc);
+      else
+        k_adj_a<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, b->W, b->dirtab, srow, b->A, lambda,
+                                                                       Lnext, a, bc, Lcur, b->pt.acc);
+      return 0;
+    });
     if (int rc = after_launch(b, "adjoint stage kernel")) return rc;
     if (int rc = launch_deposit(b, 3, b->pt.acc, nullptr, srow, frac, b->A)) return rc;
     before_launch(b, CLS_OTHER);
-    k_adj_b<<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, b->W, b->dirtab, srow, b->A, Lcur, Lt, gN, gNbar);
+    by_order(b->S.order, [&](auto O) {
+      k_adj_b<decltype(O)::value><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, b->W, b->dirtab, srow, b->A,
+                                                                              Lcur, Lt, gN, gNbar);
+      return 0;
+    });
     if (int rc = after_launch(b, "adjoint interpolation kernel")) return rc;
     Lnext = Lcur;
   }
@@ -980,6 +1031,7 @@ extern "C" int emu_deposit_static(const emu_config* cfg, const double* z, const 
                                   const double* rhobar, double pos_dt, double* A_out, void* stream) {
   Shape S;
   if (const char* why = make_shape(cfg, 1, S)) return fail(nullptr, EMU_EINVAL, "%s", why);
+  if (S.order != 2) return fail(nullptr, EMU_EINVAL, "emu_deposit_static takes the quadratic shape (shape_order 2)");
   if (!z || !ox || !oy || !oz || !N || !Nbar || !rho || !rhobar || !A_out)
     return fail(nullptr, EMU_EINVAL, "a particle array or A_out is NULL");
   if (!std::isfinite(pos_dt)) return fail(nullptr, EMU_EINVAL, "pos_dt must be finite");
@@ -1021,6 +1073,7 @@ extern "C" int emu_deposit_static(const emu_config* cfg, const double* z, const 
   B.NZ = S.NZ;
   B.MT = S.MT;
   B.NT = S.NT;
+  B.T = S.T;
   B.U = S.U;
   B.Ptot = S.Ptot;
   Parts pt{const_cast<double*>(z), const_cast<double*>(ox), const_cast<double*>(oy), const_cast<double*>(oz),
@@ -1033,8 +1086,8 @@ extern "C" int emu_deposit_static(const emu_config* cfg, const double* z, const 
   f.v[0] = 1.0;
   k_shifts<<<(S.MT + kThreads - 1) / kThreads, kThreads, 0, st>>>(B, z, dirtab, f, 1, shift);
   if (int rc = check(cudaGetLastError(), "shift kernel")) return rc;
-  k_deposit<0><<<dim3(kPersistBlocks), kThreads, 0, st>>>(B, z, N, Nbar, rho, rhobar, dirtab, shift, 1.0, partial, nullptr,
-                                                    err);
+  k_deposit<0, 2><<<dim3(kPersistBlocks), kThreads, 0, st>>>(B, z, N, Nbar, rho, rhobar, dirtab, shift, 1.0, partial,
+                                                            nullptr, err);
   if (int rc = check(cudaGetLastError(), "deposit kernel")) return rc;
   k_combine<<<combine_blocks(S.NZ), kThreads, 0, st>>>(B, partial, A_out, 1, err);
   if (int rc = check(cudaGetLastError(), "deposit combine kernel")) return rc;

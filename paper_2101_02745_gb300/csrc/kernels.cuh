@@ -10,11 +10,13 @@
 //   grid:      cell j of box b is column coff_b + j of A[36][NZ] and mom[72][NZ]
 //   tables:    direction d of box b is entry doff_b + d of the per-direction tables
 //
-// Parallel layout.  Work is split into *units* = (one 30-cell tile, one
+// Parallel layout.  Work is split into *units* = (one tile of T cells, one
 // direction) of one box: box b has ntiles_b * ndir_b units, numbered box after
 // box.  A warp works on one unit at a time with lane l on cell
-// (tile * 30 - 1 + l): lanes 1..30 own the tile's cells, lanes 0 and 31 are halo
-// lanes that supply the neighbour values of the three-cell stencil.  Because
+// (tile * T - H + l): lanes H..H+T-1 own the tile's cells, the H lanes on each
+// side are halo lanes that supply the neighbour values of the stencil.  The
+// shape orders 0-2 (Sec. 2.2.1) reach one cell on each side (H = 1, T = 30),
+// the cubic shape two (H = 2, T = 28).  Because
 // the particles of one direction (a ring) translate rigidly (one per cell at a
 // common offset, Sec. 3.1 and Eq. 4), the particle on cell j is ring entry
 // (j - shift_d) mod nz and its stencil neighbours sit on the adjacent lanes:
@@ -36,10 +38,10 @@ namespace emu_dev {
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 constexpr int kLanes = 32;
-constexpr int kTile = 30;          // cells owned by a warp (lanes 1..30)
+constexpr int kTileMax = 30;       // most cells a warp owns (shape orders 0-2)
 constexpr int kNA = 36;            // components of the grid potential
 constexpr int kNM = 72;            // components of the per-species moments
-constexpr int kSlot = kNA * kTile; // doubles in one warp's partial sums for one tile
+constexpr int kSlot = kNA * kTileMax; // doubles in one warp's partial sums for one tile
 constexpr double kLatticeTol = 1e-6;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPersistBlocks = 2 * 152;  // default grid: 2 resident blocks on each of GB300's 152 SMs
@@ -47,6 +49,20 @@ constexpr int kMaxBlocks = 4 * 152;      // largest grid the autotuner tries
 constexpr int kMaxWarps = kMaxBlocks * kWarps;
 
 enum : int { ERR_LATTICE = 1, ERR_NONFINITE = 2, ERR_WEIGHT = 4, ERR_RING = 8 };
+
+// Stencil of the shape of order ORDER (Sec. 2.2.1, orders 0-3): a particle on
+// lattice site h (the cell containing it) reaches cells h-H .. h+H, weight
+// slots 0 .. NW-1; NWS weight arrays are kept from the deposit for the RK stage
+// (none for order 0, whose only weight is 1).
+template <int ORDER>
+struct Sten {
+  static_assert(ORDER >= 0 && ORDER <= 3, "shape orders 0..3");
+  static constexpr int H = ORDER == 3 ? 2 : 1;
+  static constexpr int T = kLanes - 2 * H;
+  static constexpr int NW = 2 * H + 1;
+  static constexpr int NWS = ORDER == 0 ? 0 : NW;
+  static_assert(T <= kTileMax, "a tile's partial sums must fit a slot");
+};
 
 // One box of a batch (device copy lives in the workspace).
 struct BoxGeo {
@@ -71,6 +87,7 @@ struct Batch {
   int nbox;
   int nw;              // warps that split the units
   int NZ, MT, NT;      // total cells, directions, tiles
+  int T;               // cells per tile (the shape order's Sten<>::T)
   int64_t U, Ptot;     // total units, particles
 };
 
@@ -126,26 +143,123 @@ __device__ __forceinline__ int box_of_direction(const Batch& B, int d) {
   return lo;
 }
 
-// Quadratic shape weights (Sec. 2.2.1) of a particle at (unwrapped) position zs
-// whose lattice site is cell h (hp = h + 1/2): d = zs/dz - hp reduced to the
-// nearest periodic image, weights 1/2 (1/2 - d)^2, 3/4 - d^2, 1/2 (1/2 + d)^2 on
-// cells h-1, h, h+1, written as 1/8 + (d^2 -+ d)/2 and 3/4 - d^2.  The image
-// reduction is only needed next to the domain ends, so it sits behind the
-// lattice test.  Returns nonzero if the particle is off its lattice site.
-__device__ __forceinline__ int shape_weights(double zs, double hp, double inv_dz, double nz_d, double& wl,
-                                             double& w0, double& wr) {
+// Shape weights (Sec. 2.2.1) of order ORDER of a particle at (unwrapped)
+// position zs whose lattice site is cell h (hp = h + 1/2): the offset
+// d = zs/dz - hp, reduced to the nearest periodic image, lies in [-1/2, 1/2),
+// and w[s] is the weight of cell h + s - H, the cardinal B-spline of degree
+// ORDER at the cell centre's distance:
+//   order 0: 1 on cell h;   order 1: -d_+ , 1 - |d|, d_+ on h-1, h, h+1;
+//   order 2: 1/2 (1/2 - d)^2, 3/4 - d^2, 1/2 (1/2 + d)^2, written as
+//            1/8 + (d^2 -+ d)/2 and 3/4 - d^2;
+//   order 3: from the base cell j0 = h (d >= 0) or h - 1 (d < 0) and
+//            f = d - (j0 - h) in [0, 1): (1-f)^3/6, 2/3 - f^2 + f^3/2,
+//            2/3 - (1-f)^2 + (1-f)^3/2, f^3/6 on cells j0-1 .. j0+2.
+// The image reduction is only needed next to the domain ends, so it sits
+// behind the lattice test.  Returns nonzero if the particle is off its site.
+template <int ORDER>
+__device__ __forceinline__ int shape_weights(double zs, double hp, double inv_dz, double nz_d,
+                                             double (&w)[Sten<ORDER>::NW]) {
   double d = fma(zs, inv_dz, -hp);
   int bad = 0;
   if (fabs(d) > 0.5 + kLatticeTol) {
     d -= nz_d * rint(d / nz_d);
     bad = fabs(d) > 0.5 + kLatticeTol;
   }
-  const double d2 = d * d;
-  w0 = 0.75 - d2;
-  wl = fma(0.5, d2 - d, 0.125);
-  wr = fma(0.5, d2 + d, 0.125);
+  if constexpr (ORDER == 0) {
+    w[0] = 0.0; w[1] = 1.0; w[2] = 0.0;
+  } else if constexpr (ORDER == 1) {
+    w[0] = fmax(-d, 0.0);
+    w[1] = 1.0 - fabs(d);
+    w[2] = fmax(d, 0.0);
+  } else if constexpr (ORDER == 2) {
+    const double d2 = d * d;
+    w[1] = 0.75 - d2;
+    w[0] = fma(0.5, d2 - d, 0.125);
+    w[2] = fma(0.5, d2 + d, 0.125);
+  } else {
+    const bool up = d >= 0.0;
+    const double f = up ? d : 1.0 + d, g = 1.0 - f;
+    const double a = g * g * g * (1.0 / 6.0);
+    const double bb = fma(f * f, fma(0.5, f, -1.0), 2.0 / 3.0);
+    const double c = fma(g * g, fma(0.5, g, -1.0), 2.0 / 3.0);
+    const double e = f * f * f * (1.0 / 6.0);
+    w[0] = up ? 0.0 : a;
+    w[1] = up ? a : bb;
+    w[2] = up ? bb : c;
+    w[3] = up ? c : e;
+    w[4] = up ? e : 0.0;
+  }
   return bad;
 }
+
+// The weights kept by the deposit for the RK stage (order 0: 1 on the own cell).
+template <int ORDER>
+__device__ __forceinline__ void load_weights(const double* __restrict__ W, int64_t P, int64_t p,
+                                             double (&w)[Sten<ORDER>::NW]) {
+  if constexpr (ORDER == 0) {
+    w[0] = 0.0; w[1] = 1.0; w[2] = 0.0;
+  } else {
+#pragma unroll
+    for (int s = 0; s < Sten<ORDER>::NW; ++s) w[s] = W[s * P + p];
+  }
+}
+
+template <int ORDER>
+__device__ __forceinline__ void zero_weights(double (&w)[Sten<ORDER>::NW]) {
+#pragma unroll
+  for (int s = 0; s < Sten<ORDER>::NW; ++s) w[s] = 0.0;
+}
+
+// Interpolation through the stencil (Eq. 6): sum over s of w[s] times the
+// value v on the lane of cell h + s - H.  Every lane must call it.
+template <int ORDER>
+__device__ __forceinline__ double gather(const double (&w)[Sten<ORDER>::NW], double v) {
+  if constexpr (ORDER == 0) {
+    return v;
+  } else {
+    constexpr int H = Sten<ORDER>::H, NW = Sten<ORDER>::NW;
+    double h = w[NW - 1] * __shfl_down_sync(kFull, v, H);
+#pragma unroll
+    for (int s = NW - 2; s >= 0; --s) {
+      const int o = s - H;
+      const double x = o > 0 ? __shfl_down_sync(kFull, v, o) : o < 0 ? __shfl_up_sync(kFull, v, -o) : v;
+      h = fma(w[s], x, h);
+    }
+    return h;
+  }
+}
+
+// Deposit through the stencil (Eq. 5): a lane's cell receives from the
+// particle o lanes to its left the weight that particle gives to cell
+// (its site + o), and likewise from the right.  init() shuffles the weights
+// once per unit; apply(v) returns the sum over those particles of weight x v.
+// Every lane must call both.
+template <int ORDER>
+struct Spread {
+  static constexpr int H = Sten<ORDER>::H;
+  double w0, fl[H], fr[H];
+  __device__ __forceinline__ void init(const double (&w)[Sten<ORDER>::NW]) {
+    w0 = w[H];
+#pragma unroll
+    for (int o = 1; o <= H; ++o) {
+      fl[o - 1] = __shfl_up_sync(kFull, w[H + o], o);
+      fr[o - 1] = __shfl_down_sync(kFull, w[H - o], o);
+    }
+  }
+  __device__ __forceinline__ double apply(double v) const {
+    if constexpr (ORDER == 0) {
+      return v;
+    } else {
+      double c = fr[H - 1] * __shfl_down_sync(kFull, v, H);
+#pragma unroll
+      for (int o = H - 1; o >= 1; --o) c = fma(fr[o - 1], __shfl_down_sync(kFull, v, o), c);
+      c = fma(w0, v, c);
+#pragma unroll
+      for (int o = 1; o <= H; ++o) c = fma(fl[o - 1], __shfl_up_sync(kFull, v, o), c);
+      return c;
+    }
+  }
+};
 
 // Bulk prefetch of the doubles [i0, i0 + n) of array a into L2 (a hint; the
 // range is rounded inwards to 16-byte boundaries so it never leaves the array).
@@ -240,12 +354,14 @@ __global__ void k_shifts(Batch B, const double* __restrict__ z, const double* __
 
 // A warp's sums for one tile go to slot (warp + global tile) of the partial
 // buffer: unique, because a later warp never returns to an earlier tile.
+template <int ORDER>
 __device__ __forceinline__ void flush_tile(const double (&acc)[kNA], int64_t gtile, int local_cell, int nz,
                                            int64_t w, int lane, double* __restrict__ partial) {
-  if (lane >= 1 && lane <= kTile && local_cell < nz) {
-    double* slot = partial + (w + gtile) * kSlot + lane - 1;
+  constexpr int H = Sten<ORDER>::H, T = Sten<ORDER>::T;
+  if (lane >= H && lane < H + T && local_cell < nz) {
+    double* slot = partial + (w + gtile) * kSlot + lane - H;
 #pragma unroll
-    for (int c = 0; c < kNA; ++c) slot[c * kTile] = acc[c];
+    for (int c = 0; c < kNA; ++c) slot[c * T] = acc[c];
   }
 }
 
@@ -254,9 +370,9 @@ __device__ __forceinline__ void flush_tile(const double (&acc)[kNA], int64_t gti
 // MODE 3: B = r_nu (packed matrices given per particle: the adjoint's Gamma).
 // Each warp walks its units in order (box, tile, direction), summing
 // w_pj (1, Omega_p) B_p over directions in registers (lane l owns cell
-// tile * 30 - 1 + l) and writing one partial per tile it touches; MODE 0 also
+// tile * T - H + l) and writing one partial per tile it touches; MODE 0 also
 // stores every particle's weights for the RK stage.  Positions: z + frac dt_b v_z.
-template <int MODE>
+template <int MODE, int ORDER>
 __global__ void __launch_bounds__(kThreads, 2)
 k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, const double* __restrict__ Nbar,
           const double* __restrict__ r_nu, const double* __restrict__ r_nb, const double* __restrict__ dirtab,
@@ -276,10 +392,11 @@ k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, c
     const int nz = g.nz, M = g.M;
     const int tile = (int)((u - g.uoff) / M);
     const int64_t uend = min(u1, g.uoff + (int64_t)(tile + 1) * M);
-    const int craw = tile * kTile - 1 + lane;
+    constexpr int H = Sten<ORDER>::H, T = Sten<ORDER>::T;
+    const int craw = tile * T - H + lane;
     const int j = wrapc(craw, nz);
     const double hp = (double)j + 0.5;
-    const bool own = lane >= 1 && lane <= kTile && craw < nz;
+    const bool own = lane >= H && lane < H + T && craw < nz;
     const double pos_dt = frac * B.dt[b];
     const int64_t pbase = g.poff;
     const int dbase = g.doff;
@@ -294,21 +411,19 @@ k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, c
       const double ox = __ldg(dirtab + gd), oy = __ldg(dirtab + MT + gd), oz = __ldg(dirtab + 2 * MT + gd);
       const double vz = __ldg(dirtab + 3 * MT + gd);
       const int64_t p = pbase + (int64_t)d * nz + wrapc(j - __ldg(shift + gd), nz);
-      double wl, w0, wr;
-      bad |= shape_weights(fma(pos_dt, vz, __ldg(z + p)), hp, __ldg(&g.inv_dz), __ldg(&g.nz_d), wl, w0, wr);
+      double wt[Sten<ORDER>::NW];
+      bad |= shape_weights<ORDER>(fma(pos_dt, vz, __ldg(z + p)), hp, __ldg(&g.inv_dz), __ldg(&g.nz_d), wt);
       if (MODE == 0 && W != nullptr && own) {   // the RK stage of these positions reads them back
-        double* wp = W + p;
-        wp[0] = wl;
-        wp[P] = w0;
-        wp[2 * P] = wr;
+#pragma unroll
+        for (int q = 0; q < Sten<ORDER>::NWS; ++q) W[q * P + p] = wt[q];
       }
-      // cell j receives wr from the particle at j-1, w0 from its own, wl from j+1
-      const double wr_l = __shfl_up_sync(kFull, wr, 1);
-      const double wl_r = __shfl_down_sync(kFull, wl, 1);
-      const double n1 = (MODE == 0 || MODE == 1) ? __ldg(N + p) : 0.0;
-      const double n2 = (MODE == 0 || MODE == 2) ? __ldg(Nbar + p) : 0.0;
+      Spread<ORDER> spread;
+      spread.init(wt);
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
+        // (the weights are read inside the loop: fewer live registers across it)
+        const double n1 = (MODE == 0 || MODE == 1) ? __ldg(N + p) : 0.0;
+        const double n2 = (MODE == 0 || MODE == 2) ? __ldg(Nbar + p) : 0.0;
         double bv;
         if (MODE == 0) {
           const double x = __ldg(r_nu + k * P + p), y = __ldg(r_nb + k * P + p);
@@ -321,16 +436,14 @@ k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, c
         } else {
           bv = __ldg(r_nu + k * P + p);
         }
-        const double bl = __shfl_up_sync(kFull, bv, 1);
-        const double br = __shfl_down_sync(kFull, bv, 1);
-        const double c = fma(wr_l, bl, fma(w0, bv, wl_r * br));
+        const double c = spread.apply(bv);
         acc[k] += c;
         acc[9 + k] = fma(ox, c, acc[9 + k]);
         acc[18 + k] = fma(oy, c, acc[18 + k]);
         acc[27 + k] = fma(oz, c, acc[27 + k]);
       }
     }
-    flush_tile(acc, g.toff + tile, craw, nz, w, lane, partial);
+    flush_tile<ORDER>(acc, g.toff + tile, craw, nz, w, lane, partial);
   }
   if (bad) atomicOr(err, ERR_LATTICE);
 }
@@ -346,11 +459,11 @@ __global__ void k_combine(Batch B, const double* __restrict__ partial, double* _
     const int c = (int)(e / B.NZ), gc = (int)(e - (int64_t)c * B.NZ);
     const BoxGeo& g = B.box[box_of_cell(B, gc)];
     const int lc = gc - g.coff;
-    const int tile = lc / kTile, k = lc - tile * kTile;
+    const int tile = lc / B.T, k = lc - tile * B.T;
     const int64_t gtile = g.toff + tile;
     const int64_t wf = warp_of_unit(g.uoff + (int64_t)tile * g.M, B);
     const int64_t wl = warp_of_unit(g.uoff + (int64_t)(tile + 1) * g.M - 1, B);
-    const double* src = partial + c * kTile + k;
+    const double* src = partial + c * B.T + k;
     double v = 0.0;
     for (int64_t q = wf; q <= wl; ++q) v += __ldcg(src + (q + gtile) * kSlot);
     v *= potential ? g.kappa_dV : g.inv_dV;
@@ -361,6 +474,7 @@ __global__ void k_combine(Batch B, const double* __restrict__ partial, double* _
 }
 
 // Interpolation only (Eq. 6 then Eq. 2): H[k * Ptot + p] at z + frac dt_b v_z.
+template <int ORDER>
 __global__ void __launch_bounds__(kThreads, 2)
 k_interpolate(Batch B, const double* __restrict__ z, const double* __restrict__ dirtab,
               const int* __restrict__ shift, const double* __restrict__ A, double frac, double* __restrict__ Hout,
@@ -378,23 +492,23 @@ k_interpolate(Batch B, const double* __restrict__ z, const double* __restrict__ 
     const BoxGeo& g = B.box[b];
     const int nz = g.nz, M = g.M;
     const int tile = (int)((u - g.uoff) / M), d = (int)(u - g.uoff - (int64_t)tile * M);
-    const int craw = tile * kTile - 1 + lane, j = wrapc(craw, nz);
-    const bool active = lane >= 1 && lane <= kTile && craw < nz;
+    constexpr int H = Sten<ORDER>::H, T = Sten<ORDER>::T;
+    const int craw = tile * T - H + lane, j = wrapc(craw, nz);
+    const bool active = lane >= H && lane < H + T && craw < nz;
     const int gd = g.doff + d;
     const double ox = __ldg(dirtab + gd), oy = __ldg(dirtab + MT + gd), oz = __ldg(dirtab + 2 * MT + gd);
     const double vz = __ldg(dirtab + 3 * MT + gd);
     const int64_t p = g.poff + (int64_t)d * nz + wrapc(j - __ldg(shift + gd), nz);
-    double wl = 0.0, w0 = 0.0, wr = 0.0;
-    if (active)
-      bad |= shape_weights(fma(frac * B.dt[b], vz, z[p]), (double)j + 0.5, g.inv_dz, g.nz_d, wl, w0, wr);
+    double wt[Sten<ORDER>::NW];
+    zero_weights<ORDER>(wt);
+    if (active) bad |= shape_weights<ORDER>(fma(frac * B.dt[b], vz, z[p]), (double)j + 0.5, g.inv_dz, g.nz_d, wt);
     const double* Aj = A + g.coff + j;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       const double G = fma(-oz, __ldg(Aj + (int64_t)(27 + k) * NZ),
                            fma(-oy, __ldg(Aj + (int64_t)(18 + k) * NZ),
                                fma(-ox, __ldg(Aj + (int64_t)(9 + k) * NZ), __ldg(Aj + (int64_t)k * NZ))));
-      const double gl = __shfl_up_sync(kFull, G, 1), gr = __shfl_down_sync(kFull, G, 1);
-      const double h = fma(wl, gl, fma(w0, G, wr * gr));
+      const double h = gather<ORDER>(wt, G);
       if (active) Hout[k * P + p] = h;
     }
   }
@@ -414,7 +528,7 @@ k_interpolate(Batch B, const double* __restrict__ z, const double* __restrict__ 
 // within a box (unit = direction * ntiles + tile) so it streams along each
 // ring, and prefetches the next unit's particle data into L2.  The shape
 // weights come from the deposit.
-template <bool POT>
+template <bool POT, int ORDER>
 __global__ void __launch_bounds__(kThreads, 2)
 k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
            const int* __restrict__ shift, const double* __restrict__ A, int s, int dry) {
@@ -426,9 +540,10 @@ k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __rest
   const int MT = B.MT, NZ = B.NZ;
   const double* src_r = (s == 1) ? pt.rho : pt.stage;
   const double* src_b = (s == 1) ? pt.rhobar : pt.stage + 9 * P;
-  // arrays this stage reads, for the prefetch: source (18), y (18, s = 2, 3), acc (18, s >= 2), W (3), z (s = 4)
+  // arrays this stage reads, for the prefetch: source (18), y (18, s = 2, 3), acc (18, s >= 2), W (NWS), z (s = 4)
+  constexpr int H = Sten<ORDER>::H, T = Sten<ORDER>::T, NWS = Sten<ORDER>::NWS;
   const int nsrc = 18, ny = (s == 2 || s == 3) ? 18 : 0, nacc = (s >= 2) ? 18 : 0;
-  const int narr = nsrc + ny + nacc + 3 + (s == 4 ? 1 : 0);
+  const int narr = nsrc + ny + nacc + NWS + (s == 4 ? 1 : 0);
   int b = box_of_unit(B, u0);
   double bdt = 0.0, cdt = 0.0;
   int bcur = -1;
@@ -446,8 +561,8 @@ k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __rest
     const int d = lu / nt, tile = lu - d * nt;
     if (u + 1 < u1 && lu + 1 < nt * g.M) {   // prefetch the next unit of the same box
       const int dn = (lu + 1) / nt, tn = lu + 1 - dn * nt;
-      const int i0 = tn * kTile - __ldg(shift + g.doff + dn);   // ring index of the next unit's first cell
-      const int n = min(kTile, nz - tn * kTile);
+      const int i0 = tn * T - __ldg(shift + g.doff + dn);   // ring index of the next unit's first cell
+      const int n = min(T, nz - tn * T);
       if (i0 >= 0 && i0 + n <= nz) {
         const int64_t base = g.poff + (int64_t)dn * nz + i0;
         for (int a = lane; a < narr; a += kLanes) {
@@ -456,37 +571,35 @@ k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __rest
           else if (a < nsrc + ny) arr = (a - nsrc < 9 ? pt.rho + (int64_t)(a - nsrc) * P
                                                       : pt.rhobar + (int64_t)(a - nsrc - 9) * P);
           else if (a < nsrc + ny + nacc) arr = pt.acc + (int64_t)(a - nsrc - ny) * P;
-          else if (a < nsrc + ny + nacc + 3) arr = W + (int64_t)(a - nsrc - ny - nacc) * P;
+          else if (a < nsrc + ny + nacc + NWS) arr = W + (int64_t)(a - nsrc - ny - nacc) * P;
           else arr = pt.z;
           prefetch_l2(arr, base, n);
         }
       }
     }
     const double bdt2 = 2.0 * bdt, cdt2 = 2.0 * cdt;   // diagonal K are returned halved
-    const int craw = tile * kTile - 1 + lane, j = wrapc(craw, nz);
-    const bool active = lane >= 1 && lane <= kTile && craw < nz;
+    const int craw = tile * T - H + lane, j = wrapc(craw, nz);
+    const bool active = lane >= H && lane < H + T && craw < nz;
     const int gd = g.doff + d;
     const double ox = __ldg(dirtab + gd), oy = __ldg(dirtab + MT + gd), oz = __ldg(dirtab + 2 * MT + gd);
     const int64_t p = g.poff + (int64_t)d * nz + wrapc(j - __ldg(shift + gd), nz);
-    double wl = 0.0, w0 = 0.0, wr = 0.0;
+    double wt[Sten<ORDER>::NW];
+    zero_weights<ORDER>(wt);
     // the neutrino source matrix first, so its latency overlaps the interpolation
     double r[9];
     if (active) {
-      wl = W[p];
-      w0 = W[P + p];
-      wr = W[2 * P + p];
+      load_weights<ORDER>(W, P, p, wt);
 #pragma unroll
       for (int k = 0; k < 9; ++k) r[k] = src_r[k * P + p];
     }
-    double H[9];
+    double Hm[9];
     const double* Aj = A + g.coff + j;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       const double G = fma(-oz, __ldg(Aj + (int64_t)(27 + k) * NZ),
                            fma(-oy, __ldg(Aj + (int64_t)(18 + k) * NZ),
                                fma(-ox, __ldg(Aj + (int64_t)(9 + k) * NZ), __ldg(Aj + (int64_t)k * NZ))));
-      const double gl = __shfl_up_sync(kFull, G, 1), gr = __shfl_down_sync(kFull, G, 1);
-      H[k] = fma(wl, gl, fma(w0, G, wr * gr));
+      Hm[k] = gather<ORDER>(wt, G);
     }
     if (!active) continue;
     // neutrinos: H;  antineutrinos: Hbar = -H^*  (diagonal differences and real parts flip sign)
@@ -497,11 +610,11 @@ k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __rest
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         const bool im = (k == 4 || k == 6 || k == 8);
-        Hb[k] = (im ? H[k] : -H[k]) + __ldg(vb + k);
-        H[k] += __ldg(vn + k);
+        Hb[k] = (im ? Hm[k] : -Hm[k]) + __ldg(vb + k);
+        Hm[k] += __ldg(vn + k);
       }
     }
-    const double d12 = H[0] - H[1], d13 = H[0] - H[2], d23 = H[1] - H[2];
+    const double d12 = Hm[0] - Hm[1], d13 = Hm[0] - Hm[2], d23 = Hm[1] - Hm[2];
 #pragma unroll
     for (int which = 0; which < 2; ++which) {
       double* __restrict__ yv = which ? pt.rhobar : pt.rho;
@@ -523,10 +636,10 @@ k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __rest
       }
       const double* rr = which ? rb : r;
       double kd[3], ko[6];
-      if (which == 0) commutator(d12, d13, d23, H[3], H[4], H[5], H[6], H[7], H[8], rr, kd, ko);
+      if (which == 0) commutator(d12, d13, d23, Hm[3], Hm[4], Hm[5], Hm[6], Hm[7], Hm[8], rr, kd, ko);
       else if (POT) commutator(Hb[0] - Hb[1], Hb[0] - Hb[2], Hb[1] - Hb[2], Hb[3], Hb[4], Hb[5], Hb[6], Hb[7], Hb[8],
                                rr, kd, ko);
-      else commutator(-d12, -d13, -d23, -H[3], H[4], -H[5], H[6], -H[7], H[8], rr, kd, ko);
+      else commutator(-d12, -d13, -d23, -Hm[3], Hm[4], -Hm[5], Hm[6], -Hm[7], Hm[8], rr, kd, ko);
       if (s == 1) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) { av[k * P + p] = fma(bdt2, kd[k], rr[k]); sv[k * P + p] = fma(cdt2, kd[k], rr[k]); }
@@ -741,7 +854,7 @@ __device__ __forceinline__ void kfull(const double H[9], const double r[9], doub
 // First adjoint launch of one stage.  m = a lam + b lamn (the adjoint of this
 // stage's derivative k_s); writes lam_out = J_rho^T m (direct terms) and
 // Gam = dL/dH_self.  pt.rho / pt.rhobar point at the stage state.
-template <bool POT>
+template <bool POT, int ORDER>
 __global__ void __launch_bounds__(kThreads, 2)
 k_adj_a(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
         const int* __restrict__ shift, const double* __restrict__ A, const double* __restrict__ lam,
@@ -760,13 +873,15 @@ k_adj_a(Batch B, Parts pt, const double* __restrict__ W, const double* __restric
     const int nz = g.nz, nt = g.ntiles;
     const int lu = (int)(u - g.uoff);
     const int d = lu / nt, tile = lu - d * nt;
-    const int craw = tile * kTile - 1 + lane, j = wrapc(craw, nz);
-    const bool active = lane >= 1 && lane <= kTile && craw < nz;
+    constexpr int Hh = Sten<ORDER>::H, T = Sten<ORDER>::T;
+    const int craw = tile * T - Hh + lane, j = wrapc(craw, nz);
+    const bool active = lane >= Hh && lane < Hh + T && craw < nz;
     const int gd = g.doff + d;
     const double ox = __ldg(dirtab + gd), oy = __ldg(dirtab + MT + gd), oz = __ldg(dirtab + 2 * MT + gd);
     const int64_t p = g.poff + (int64_t)d * nz + wrapc(j - __ldg(shift + gd), nz);
-    double wl = 0.0, w0 = 0.0, wr = 0.0;
-    if (active) { wl = W[p]; w0 = W[P + p]; wr = W[2 * P + p]; }
+    double wt[Sten<ORDER>::NW];
+    zero_weights<ORDER>(wt);
+    if (active) load_weights<ORDER>(W, P, p, wt);
     double H[9];
     const double* Aj = A + g.coff + j;
 #pragma unroll
@@ -774,8 +889,7 @@ k_adj_a(Batch B, Parts pt, const double* __restrict__ W, const double* __restric
       const double G = fma(-oz, __ldg(Aj + (int64_t)(27 + k) * NZ),
                            fma(-oy, __ldg(Aj + (int64_t)(18 + k) * NZ),
                                fma(-ox, __ldg(Aj + (int64_t)(9 + k) * NZ), __ldg(Aj + (int64_t)k * NZ))));
-      const double gl = __shfl_up_sync(kFull, G, 1), gr = __shfl_down_sync(kFull, G, 1);
-      H[k] = fma(wl, gl, fma(w0, G, wr * gr));
+      H[k] = gather<ORDER>(wt, G);
     }
     if (!active) continue;
     double Gm[9];
@@ -812,6 +926,7 @@ k_adj_a(Batch B, Parts pt, const double* __restrict__ W, const double* __restric
 // Gamma grid E (= dL/dB), then lam_out += N GB (rho) and -Nbar conj(GB)
 // (rhobar), gN += <GB, rho>, gNbar -= <conj(GB), rhobar>; finally
 // lam_tot += lam_out.
+template <int ORDER>
 __global__ void __launch_bounds__(kThreads, 2)
 k_adj_b(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
         const int* __restrict__ shift, const double* __restrict__ E, double* __restrict__ lam_out,
@@ -829,13 +944,15 @@ k_adj_b(Batch B, Parts pt, const double* __restrict__ W, const double* __restric
     const int nz = g.nz, nt = g.ntiles;
     const int lu = (int)(u - g.uoff);
     const int d = lu / nt, tile = lu - d * nt;
-    const int craw = tile * kTile - 1 + lane, j = wrapc(craw, nz);
-    const bool active = lane >= 1 && lane <= kTile && craw < nz;
+    constexpr int Hh = Sten<ORDER>::H, T = Sten<ORDER>::T;
+    const int craw = tile * T - Hh + lane, j = wrapc(craw, nz);
+    const bool active = lane >= Hh && lane < Hh + T && craw < nz;
     const int gd = g.doff + d;
     const double ox = __ldg(dirtab + gd), oy = __ldg(dirtab + MT + gd), oz = __ldg(dirtab + 2 * MT + gd);
     const int64_t p = g.poff + (int64_t)d * nz + wrapc(j - __ldg(shift + gd), nz);
-    double wl = 0.0, w0 = 0.0, wr = 0.0;
-    if (active) { wl = W[p]; w0 = W[P + p]; wr = W[2 * P + p]; }
+    double wt[Sten<ORDER>::NW];
+    zero_weights<ORDER>(wt);
+    if (active) load_weights<ORDER>(W, P, p, wt);
     double GB[9];
     const double* Ej = E + g.coff + j;
 #pragma unroll
@@ -843,8 +960,7 @@ k_adj_b(Batch B, Parts pt, const double* __restrict__ W, const double* __restric
       const double G = fma(-oz, __ldg(Ej + (int64_t)(27 + k) * NZ),
                            fma(-oy, __ldg(Ej + (int64_t)(18 + k) * NZ),
                                fma(-ox, __ldg(Ej + (int64_t)(9 + k) * NZ), __ldg(Ej + (int64_t)k * NZ))));
-      const double gl = __shfl_up_sync(kFull, G, 1), gr = __shfl_down_sync(kFull, G, 1);
-      GB[k] = fma(wl, gl, fma(w0, G, wr * gr));
+      GB[k] = gather<ORDER>(wt, G);
     }
     if (!active) continue;
     const double n1 = pt.N[p], n2 = pt.Nbar[p];
@@ -873,6 +989,7 @@ k_adj_b(Batch B, Parts pt, const double* __restrict__ W, const double* __restric
 //   lam_rho,p    = N_p    (1/dV) sum_j w_pj (dmom_n,j    + Omega_p . dmom_f,j)
 //   lam_rhobar,p = Nbar_p (1/dV) sum_j w_pj (dmom_nbar,j + Omega_p . dmom_fbar,j)
 // and gN_p += lam_rho,p . rho_p / N_p (likewise gNbar); lam is overwritten.
+template <int ORDER>
 __global__ void __launch_bounds__(kThreads, 2)
 k_adj_seed(Batch B, Parts pt, const double* __restrict__ dirtab, const int* __restrict__ shift,
            const double* __restrict__ dmom, double* __restrict__ lam, double* __restrict__ gN,
@@ -891,13 +1008,15 @@ k_adj_seed(Batch B, Parts pt, const double* __restrict__ dirtab, const int* __re
     const int nz = g.nz, nt = g.ntiles;
     const int lu = (int)(u - g.uoff);
     const int d = lu / nt, tile = lu - d * nt;
-    const int craw = tile * kTile - 1 + lane, j = wrapc(craw, nz);
-    const bool active = lane >= 1 && lane <= kTile && craw < nz;
+    constexpr int Hh = Sten<ORDER>::H, T = Sten<ORDER>::T;
+    const int craw = tile * T - Hh + lane, j = wrapc(craw, nz);
+    const bool active = lane >= Hh && lane < Hh + T && craw < nz;
     const int gd = g.doff + d;
     const double ox = __ldg(dirtab + gd), oy = __ldg(dirtab + MT + gd), oz = __ldg(dirtab + 2 * MT + gd);
     const int64_t p = g.poff + (int64_t)d * nz + wrapc(j - __ldg(shift + gd), nz);
-    double wl = 0.0, w0 = 0.0, wr = 0.0;
-    if (active) bad |= shape_weights(pt.z[p], (double)j + 0.5, g.inv_dz, g.nz_d, wl, w0, wr);
+    double wt[Sten<ORDER>::NW];
+    zero_weights<ORDER>(wt);
+    if (active) bad |= shape_weights<ORDER>(pt.z[p], (double)j + 0.5, g.inv_dz, g.nz_d, wt);
     const double* Ej = dmom + g.coff + j;
 #pragma unroll
     for (int which = 0; which < 2; ++which) {
@@ -908,8 +1027,7 @@ k_adj_seed(Batch B, Parts pt, const double* __restrict__ dirtab, const int* __re
         const double G = fma(oz, __ldg(Ej + (base + 27 + k) * NZ),
                              fma(oy, __ldg(Ej + (base + 18 + k) * NZ),
                                  fma(ox, __ldg(Ej + (base + 9 + k) * NZ), __ldg(Ej + (base + k) * NZ))));
-        const double gl = __shfl_up_sync(kFull, G, 1), gr = __shfl_down_sync(kFull, G, 1);
-        GB[k] = fma(wl, gl, fma(w0, G, wr * gr)) * g.inv_dV;
+        GB[k] = gather<ORDER>(wt, G) * g.inv_dV;
       }
       if (active) {
         const double Nw = which ? pt.Nbar[p] : pt.N[p];

@@ -363,13 +363,13 @@ class Box:
     FIELDS = ("z", "ox", "oy", "oz", "N", "Nbar")
 
     def __init__(self, nz, ndir, Lz, kappa, c_light, cfl_adv=0.4, cfl_flavor=0.4, area=1.0,
-                 device="cuda", stream=None, cfgs=None):
+                 device="cuda", stream=None, cfgs=None, shape_order=2):
         import torch
 
         self.torch = torch
         self.device = torch.device(device)
         if cfgs is None:
-            self.cfgs = [make_config(nz, ndir, Lz, kappa, c_light, cfl_adv, cfl_flavor, area)]
+            self.cfgs = [make_config(nz, ndir, Lz, kappa, c_light, cfl_adv, cfl_flavor, area, shape_order)]
         else:
             self.cfgs = list(cfgs)
         self.cfg = self.cfgs[0]
@@ -397,7 +397,8 @@ class Box:
     @classmethod
     def from_workloads(cls, wls, device="cuda", init=True):
         """A batch of the given workloads (one box each), initialised together."""
-        cfgs = [make_config(w.nz, w.ndir, w.Lz, w.kappa, w.c_light, w.cfl_adv, w.cfl_flavor, w.area) for w in wls]
+        cfgs = [make_config(w.nz, w.ndir, w.Lz, w.kappa, w.c_light, w.cfl_adv, w.cfl_flavor, w.area, w.shape_order)
+                for w in wls]
         b = cls(0, 0, 0, 0, 0, device=device, cfgs=cfgs)
         if init:
             dirs = None
@@ -413,7 +414,8 @@ class Box:
 
     @classmethod
     def from_workload(cls, wl, device="cuda", init=True):
-        b = cls(wl.nz, wl.ndir, wl.Lz, wl.kappa, wl.c_light, wl.cfl_adv, wl.cfl_flavor, wl.area, device=device)
+        b = cls(wl.nz, wl.ndir, wl.Lz, wl.kappa, wl.c_light, wl.cfl_adv, wl.cfl_flavor, wl.area, device=device,
+                shape_order=wl.shape_order)
         if init:
             b.init(wl.n_nu, wl.n_nubar, wl.f_nu, wl.f_nubar, wl.dirs, wl.alpha, wl.seed)
         return b

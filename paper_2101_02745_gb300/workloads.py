@@ -51,6 +51,7 @@ class Workload:
     area: float = 1.0              # transverse cell area [cm^2]
     kappa: float = KAPPA
     c_light: float = C_LIGHT
+    shape_order: int = 2           # degree of the B-spline particle shape (Sec. 2.2.1)
     meta: dict = field(default_factory=dict)
 
     @property
@@ -175,7 +176,7 @@ def head(wl: Workload, nz: int) -> Workload:
     return Workload(f"{wl.name}[:{nz}]", nz, wl.ndir, wl.dz * nz, wl.n_nu[:nz].copy(), wl.n_nubar[:nz].copy(),
                     wl.f_nu[:nz].copy(), wl.f_nubar[:nz].copy(), dirs=wl.dirs, alpha=wl.alpha, seed=wl.seed,
                     steps=wl.steps, cfl_adv=wl.cfl_adv, cfl_flavor=wl.cfl_flavor, area=wl.area, kappa=wl.kappa,
-                    c_light=wl.c_light)
+                    c_light=wl.c_light, shape_order=wl.shape_order)
 
 
 def oscillation(mass_eV=(0.0, 0.0, 0.0), theta12=0.0, theta13=0.0, theta23=0.0, delta_cp=0.0,
@@ -212,6 +213,12 @@ def homogeneous_two_beam() -> tuple:
     sp = _uniform_species(1, n, n, (0, 0, n / 3.0), (0, 0, -n / 3.0))
     return Workload("two_beam_homogeneous", 1, 2, 1.0, *sp, dirs=dirs, alpha=0.0, steps=0,
                     meta={"osc": osc, "growth": w_vac}), osc
+
+
+def with_shape(wl: Workload, order: int) -> Workload:
+    """The same workload with particles of shape order `order` (0..3)."""
+    import dataclasses
+    return dataclasses.replace(wl, name=f"{wl.name}_o{order}", shape_order=int(order))
 
 
 def by_name(name: str) -> Workload:

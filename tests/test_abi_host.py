@@ -55,12 +55,29 @@ def test_workspace_and_config_validation(lib):
     big = E.make_config(16384, 1000, 1024.0, 1.9e-22, 3e10)
     assert E.emu_workspace_bytes(big) > n1
     for bad in (E.make_config(0, 16, 1.0, 1e-22, 3e10), E.make_config(4, 0, 1.0, 1e-22, 3e10),
-                E.make_config(4, 4, -1.0, 1e-22, 3e10), E.make_config(4, 4, 1.0, 1e-22, 3e10, shape_order=1)):
+                E.make_config(4, 4, -1.0, 1e-22, 3e10), E.make_config(4, 4, 1.0, 1e-22, 3e10, shape_order=4),
+                E.make_config(4, 4, 1.0, 1e-22, 3e10, shape_order=-1)):
         with pytest.raises(E.EmuError) as ei:
             E.emu_create(bad)
         assert ei.value.code == E.EMU_EINVAL
         assert E.emu_workspace_bytes.__name__  # message is set
         assert E.emu_last_error(None)
+
+
+def test_shape_orders_geometry(lib):
+    """Orders 0-2 tile 30 cells per warp, order 3 (two halo lanes a side) 28;
+    the kept shape weights: none (order 0), 3 (1, 2) or 5 (3) per particle."""
+    sizes = {o: E.emu_workspace_bytes(E.make_config(840, 10, 52.5, 1.9e-22, 3e10, shape_order=o)) for o in range(4)}
+    for o in range(4):
+        box = E.emu_create(E.make_config(840, 10, 52.5, 1.9e-22, 3e10, shape_order=o))
+        E.emu_destroy(box)
+    P = 8400
+    assert sizes[1] == sizes[2]
+    assert sizes[1] - sizes[0] >= 3 * 8 * P - 256
+    assert sizes[3] - sizes[2] >= 2 * 8 * P - 256
+    mixed = [E.make_config(20, 4, 1.0, 1.9e-22, 3e10, shape_order=1), E.make_config(20, 4, 1.0, 1.9e-22, 3e10)]
+    _, ptr = E._cfg_array(mixed)
+    assert E.load().emu_batch_workspace_bytes(ptr, 2) == E.EMU_EINVAL
 
 
 def test_create_destroy_and_unbound_calls(lib):
