@@ -401,7 +401,7 @@ def measure_sweep(args, dist, device, rank, world, steps):
             "vs_plain": single_ms / batched_ms}
 
 
-def measure_adjoint(dist, device, world, reps=1):
+def measure_adjoint(dist, device, world, reps=1, nz=0, ndir=0, steps=0):
     """Gradient of log <|n_emu|> after the growth-phase run (256 cells x 96
     directions, 400 steps, checkpoints every 20 steps) through the adjoint's
     autograd Function, against the plain forward steps of the same run.
@@ -415,6 +415,8 @@ def measure_adjoint(dist, device, world, reps=1):
     from paper_2101_02745_gb300.adjoint import Evolve, Simulation, objectives
 
     wl = W.adjoint_box()
+    if nz or ndir or steps:
+        wl = W.adjoint_box(nz=nz or wl.nz, ndir=ndir or wl.ndir, steps=steps or wl.steps)
     box = E.Box.from_workload(wl, device=device)
     dt = box.timestep()
     sim = Simulation(box, wl.steps, dt, every=wl.meta["checkpoint_every"], alpha=wl.alpha, seed=wl.seed)
@@ -463,7 +465,7 @@ def run_adjoint(args, rank, world, local_rank):
     torch.cuda.set_device(device)
     barrier(dist, device)
     clocks = ClockSampler(device.index).start()
-    a = measure_adjoint(dist, device, world, reps=args.steps)
+    a = measure_adjoint(dist, device, world, reps=args.steps, nz=args.nz, ndir=args.ndir, steps=args.adj_steps)
     clk = clocks.stop()
     if rank == 0:
         line = {"metric": METRIC, "value": a["value"], "unit": a["unit"], "n_gpus": world, "steps": args.steps,
@@ -472,7 +474,9 @@ def run_adjoint(args, rank, world, local_rank):
                 "data": "synthetic",
                 "config": {"workload": a["workload"], "particles_per_gpu": a["particles"], "steps": a["steps"],
                            "checkpoint_every": a["checkpoint_every"],
-                           "l2": "working set below L2 (small box; the adjoint's own config)"},
+                           "l2": ("particle state %.2f GB %s L2 (129 MB)"
+                                  % (a["particles"] * 480 / 1e9,
+                                     "above" if a["particles"] * 480 > 129e6 else "below"))},
                 "adjoint": a, "gpu_launches": a["launches_per_gradient"], "clocks": clk}
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -526,6 +530,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-cells", type=int, default=256, help="cells per oracle step in --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--adj-steps", type=int, default=0, help="steps of the adjoint workload (default 400)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-sweep and adjoint comparisons of the default line")
     args = ap.parse_args(argv)

@@ -150,7 +150,8 @@ int emu_interpolate_H(emu_box* box, double pos_dt, double* H_out, int on_host);
  * writes the new rho, rhobar and z.  Stages must be called in order 1..4. */
 int emu_rk_stage(emu_box* box, int s, double dt);
 
-/* nsteps full RK4 steps of size dt (dt <= 0: the value of emu_timestep). */
+/* nsteps full RK4 steps of size dt (dt <= 0: the value of emu_timestep).
+ * Replays one captured step as a CUDA graph, as emu_batch_step does. */
 int emu_step(emu_box* box, int64_t nsteps, double dt);
 
 /* Per-species moments of the current state (Eq. 5, cm^-3) into out
@@ -214,10 +215,12 @@ int emu_batch_set_dt(emu_box* box, const double* dt);
 /* nsteps classic RK4 steps of every box with its own step size (Eq. 7 values
  * unless set): per step one lattice-shift launch and per stage one deposit,
  * one deposit combination and one RK-stage launch, each covering all boxes.
- * On a non-default stream the first call captures one step as a CUDA graph
- * (make that call outside any other stream capture) and every step replays
- * it; with per-kernel timing on, or on the legacy default stream, the
- * kernels are launched directly. */
+ * The first call captures one step as a CUDA graph (make that call outside
+ * any other stream capture) and every step replays it: on the box's stream,
+ * or for a box bound to the legacy default stream on a blocking stream the
+ * library creates, which the legacy stream orders implicitly before and after
+ * its own work.  With per-kernel timing on, the kernels are launched
+ * directly.  Binding, autotuning and emu_set_oscillation drop the graph. */
 int emu_batch_step(emu_box* box, int64_t nsteps);
 
 /* emu_diagnostics of every box: out [nbox][63]. */
@@ -289,8 +292,10 @@ int emu_adjoint_seed(emu_box* box, const double* dmom, double* lambda, double* g
  * deposit of the adjoint dL/dH (the self-interaction operator of Eqs. 5-6 is
  * symmetric) and its interpolation.  The particle state is unchanged; the RK
  * scratch (acc, stage) is overwritten.  adj_ws: device, 256-byte aligned,
- * at least emu_adjoint_workspace_bytes.  Errors: EMU_EINVAL (dt not positive
- * and finite, NULL or short buffers, batch, step in progress), EMU_ECUDA. */
+ * at least emu_adjoint_workspace_bytes.  The step is captured as a CUDA graph
+ * (as emu_batch_step) and replayed while lambda, gN, gNbar, adj_ws and dt
+ * stay the same.  Errors: EMU_EINVAL (dt not positive and finite, NULL or
+ * short buffers, batch, step in progress), EMU_ECUDA. */
 int emu_adjoint_step(emu_box* box, double dt, double* lambda, double* gN, double* gNbar, void* adj_ws,
                      int64_t adj_ws_bytes);
 

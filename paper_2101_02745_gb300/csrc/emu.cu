@@ -179,13 +179,23 @@ struct emu_box {
   bool capturing = false;
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph = nullptr;   // one step of every box
   int64_t graph_launches = 0;
+  // one adjoint step, for the buffers and step size it was captured with
+  cudaGraphExec_t adj_graph = nullptr;
+  int64_t adj_launches = 0;
+  const void* adj_key[4] = {nullptr, nullptr, nullptr, nullptr};
+  double adj_dt = 0.0;
+  // graphs of a box bound to the legacy default stream run on this blocking
+  // stream, which the legacy stream orders implicitly with its own work
+  cudaStream_t cap = nullptr;
   char msg[512] = {0};
   ~emu_box() {
     for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : pool) cudaEventDestroy(e);
     if (graph) cudaGraphExecDestroy(graph);
+    if (adj_graph) cudaGraphExecDestroy(adj_graph);
+    if (cap) cudaStreamDestroy(cap);
   }
 };
 
@@ -272,6 +282,55 @@ void invalidate_graph(emu_box* b) {
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
   }
+  if (b->adj_graph) {
+    cudaGraphExecDestroy(b->adj_graph);
+    b->adj_graph = nullptr;
+  }
+}
+
+// Stream the box's graphs are captured on and replayed on: its own stream, or
+// for the legacy default stream (which cannot be captured) a blocking stream
+// of the box, implicitly ordered with the legacy stream in both directions.
+int graph_stream(emu_box* b, cudaStream_t* out) {
+  if (b->stream) { *out = b->stream; return EMU_OK; }
+  if (!b->cap)
+    if (int rc = cuda_check(b, cudaStreamCreate(&b->cap), "create graph stream")) return rc;
+  *out = b->cap;
+  return EMU_OK;
+}
+
+// Captures the launches of body() into *exec (their count into *count).
+template <typename F>
+int capture(emu_box* b, cudaGraphExec_t* exec, int64_t* count, F&& body) {
+  cudaStream_t gs = nullptr;
+  if (int rc = graph_stream(b, &gs)) return rc;
+  const int64_t before = b->launches;
+  if (int rc = cuda_check(b, cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal), "begin capture"))
+    return rc;
+  cudaStream_t saved = b->stream;
+  b->stream = gs;
+  b->capturing = true;
+  int rc = body();
+  b->capturing = false;
+  b->stream = saved;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(gs, &g);
+  if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+  if (e != cudaSuccess) return cuda_check(b, e, "end capture");
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { *exec = nullptr; return cuda_check(b, e, "instantiate graph"); }
+  *count = b->launches - before;
+  b->launches = before;
+  return EMU_OK;
+}
+
+int launch_graph(emu_box* b, cudaGraphExec_t exec, int64_t count) {
+  cudaStream_t gs = nullptr;
+  if (int rc = graph_stream(b, &gs)) return rc;
+  if (int rc = cuda_check(b, cudaGraphLaunch(exec, gs), "graph launch")) return rc;
+  b->launches += count;
+  return EMU_OK;
 }
 
 int copy_out(emu_box* b, void* dst, const void* src, size_t bytes, int on_host) {
@@ -363,6 +422,23 @@ int launch_step(emu_box* b, int dry) {
   if (int rc = launch_shifts(b, kStageFrac, 4)) return rc;
   for (int s = 1; s <= 4; ++s)
     if (int rc = launch_stage(b, s, dry)) return rc;
+  return EMU_OK;
+}
+
+// nsteps steps of every box with the step sizes on the device: one step is
+// captured as a CUDA graph and replayed (kernels launched directly while
+// per-kernel timing is on).
+int run_steps(emu_box* b, int64_t nsteps) {
+  if (nsteps == 0) return EMU_OK;
+  if (b->prof) {
+    for (int64_t n = 0; n < nsteps; ++n)
+      if (int rc = launch_step(b, 0)) return rc;
+    return EMU_OK;
+  }
+  if (!b->graph)
+    if (int rc = capture(b, &b->graph, &b->graph_launches, [&] { return launch_step(b, 0); })) return rc;
+  for (int64_t n = 0; n < nsteps; ++n)
+    if (int rc = launch_graph(b, b->graph, b->graph_launches)) return rc;
   return EMU_OK;
 }
 
@@ -660,10 +736,9 @@ int emu_step(emu_box* b, int64_t nsteps, double dt) {
       if (int rc = run_timestep(b, nullptr)) return rc;
     dt = b->step_dt[0];
   }
-  for (int64_t n = 0; n < nsteps; ++n)
-    for (int s = 1; s <= 4; ++s)
-      if (int rc = emu_rk_stage(b, s, dt)) return rc;
-  return EMU_OK;
+  if (!std::isfinite(dt)) return fail(b, EMU_EINVAL, "dt must be positive and finite");
+  if (int rc = set_dts(b, &dt)) return rc;
+  return run_steps(b, nsteps);
 }
 
 int emu_batch_timestep(emu_box* b, double* dt_out) {
@@ -688,34 +763,7 @@ int emu_batch_step(emu_box* b, int64_t nsteps) {
   if (!b->step_valid)
     if (int rc = run_timestep(b, nullptr)) return rc;
   if (int rc = set_dts(b, b->step_dt.data())) return rc;
-  if (nsteps == 0) return EMU_OK;
-  if (b->prof || b->stream == nullptr) {  // per-kernel timing, or the legacy stream (not capturable): eager
-    for (int64_t n = 0; n < nsteps; ++n)
-      if (int rc = launch_step(b, 0)) return rc;
-    return EMU_OK;
-  }
-  if (!b->graph) {  // capture one step of every box as a graph, replayed per step
-    const int64_t before = b->launches;
-    if (int rc = cuda_check(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture"))
-      return rc;
-    b->capturing = true;
-    int rc = launch_step(b, 0);
-    b->capturing = false;
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
-    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
-    if (e != cudaSuccess) return cuda_check(b, e, "end capture");
-    e = cudaGraphInstantiate(&b->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) { b->graph = nullptr; return cuda_check(b, e, "instantiate graph"); }
-    b->graph_launches = b->launches - before;
-    b->launches = before;
-  }
-  for (int64_t n = 0; n < nsteps; ++n) {
-    if (int rc = cuda_check(b, cudaGraphLaunch(b->graph, b->stream), "graph launch")) return rc;
-    b->launches += b->graph_launches;
-  }
-  return EMU_OK;
+  return run_steps(b, nsteps);
 }
 
 int emu_moments(emu_box* b, double* out, int on_host) {
@@ -838,45 +886,18 @@ int emu_set_oscillation(emu_box* b, int32_t box, const emu_oscillation* osc) {
 
 // ------------------------------------------------------------------ adjoint
 
-int64_t emu_adjoint_workspace_bytes(const emu_config* cfg) {
-  Shape S;
-  if (make_shape(cfg, 1, S)) return EMU_EINVAL;
-  return (int64_t)(sizeof(double) * 90 * (size_t)S.Ptot);
-}
+}  // extern "C"
 
-int emu_adjoint_seed(emu_box* b, const double* dmom, double* lambda, double* gN, double* gNbar) {
-  if (int rc = check_single(b)) return rc;
-  if (!dmom || !lambda || !gN || !gNbar) return fail(b, EMU_EINVAL, "adjoint seed: NULL pointer");
-  if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
-  const double zero = 0.0;
-  if (int rc = launch_shifts(b, &zero, 1)) return rc;
-  before_launch(b, CLS_OTHER);
-  by_order(b->S.order, [&](auto O) {
-    k_adj_seed<decltype(O)::value><<<persist_grid(b), kThreads, 0, b->stream>>>(
-        batch_view(b), b->pt, b->dirtab, b->shift, dmom, lambda, gN, gNbar, b->err);
-    return 0;
-  });
-  return after_launch(b, "adjoint seed kernel");
-}
-
-int emu_adjoint_step(emu_box* b, double dt, double* lambda, double* gN, double* gNbar, void* adj_ws,
-                     int64_t adj_ws_bytes) {
-  if (int rc = check_single(b)) return rc;
-  if (!(dt > 0) || !std::isfinite(dt)) return fail(b, EMU_EINVAL, "dt must be positive and finite");
-  if (!lambda || !gN || !gNbar || !adj_ws) return fail(b, EMU_EINVAL, "adjoint step: NULL pointer");
+namespace {
+// The launches of one adjoint step (emu_adjoint_step; the step size is on the device).
+int adjoint_body(emu_box* b, double dt, double* lambda, double* gN, double* gNbar, void* adj_ws) {
   const size_t P = (size_t)b->S.Ptot;
-  if (adj_ws_bytes < (int64_t)(sizeof(double) * 90 * P))
-    return fail(b, EMU_EINVAL, "adjoint workspace too small: %lld < %lld bytes", (long long)adj_ws_bytes,
-                (long long)(sizeof(double) * 90 * P));
-  if (((uintptr_t)adj_ws) & 255) return fail(b, EMU_EINVAL, "adjoint workspace must be 256-byte aligned");
-  if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
   double* Y2 = (double*)adj_ws;  // stage states y2, y3 (y4 stays in the stage buffer)
   double* Y3 = Y2 + 18 * P;
   double* La = Y3 + 18 * P;      // adjoints of two consecutive stage states
   double* Lb = La + 18 * P;
   double* Lt = Lb + 18 * P;      // running sum: lambda + sum over stages
   const size_t bytes18 = sizeof(double) * 18 * P;
-  if (int rc = set_dts(b, &dt)) return rc;
   if (int rc = launch_shifts(b, kStageFrac, 4)) return rc;
   // forward stages 1..3: y2, y3 copied out, y4 left in the stage buffer
   for (int s = 1; s <= 3; ++s) {
@@ -927,8 +948,59 @@ int emu_adjoint_step(emu_box* b, double dt, double* lambda, double* gN, double* 
     if (int rc = after_launch(b, "adjoint interpolation kernel")) return rc;
     Lnext = Lcur;
   }
-  b->next_stage = 1;
   return cuda_check(b, cudaMemcpyAsync(lambda, Lt, bytes18, cudaMemcpyDeviceToDevice, b->stream), "copy adjoint");
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t emu_adjoint_workspace_bytes(const emu_config* cfg) {
+  Shape S;
+  if (make_shape(cfg, 1, S)) return EMU_EINVAL;
+  return (int64_t)(sizeof(double) * 90 * (size_t)S.Ptot);
+}
+
+int emu_adjoint_seed(emu_box* b, const double* dmom, double* lambda, double* gN, double* gNbar) {
+  if (int rc = check_single(b)) return rc;
+  if (!dmom || !lambda || !gN || !gNbar) return fail(b, EMU_EINVAL, "adjoint seed: NULL pointer");
+  if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
+  const double zero = 0.0;
+  if (int rc = launch_shifts(b, &zero, 1)) return rc;
+  before_launch(b, CLS_OTHER);
+  by_order(b->S.order, [&](auto O) {
+    k_adj_seed<decltype(O)::value><<<persist_grid(b), kThreads, 0, b->stream>>>(
+        batch_view(b), b->pt, b->dirtab, b->shift, dmom, lambda, gN, gNbar, b->err);
+    return 0;
+  });
+  return after_launch(b, "adjoint seed kernel");
+}
+
+int emu_adjoint_step(emu_box* b, double dt, double* lambda, double* gN, double* gNbar, void* adj_ws,
+                     int64_t adj_ws_bytes) {
+  if (int rc = check_single(b)) return rc;
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(b, EMU_EINVAL, "dt must be positive and finite");
+  if (!lambda || !gN || !gNbar || !adj_ws) return fail(b, EMU_EINVAL, "adjoint step: NULL pointer");
+  const size_t P = (size_t)b->S.Ptot;
+  if (adj_ws_bytes < (int64_t)(sizeof(double) * 90 * P))
+    return fail(b, EMU_EINVAL, "adjoint workspace too small: %lld < %lld bytes", (long long)adj_ws_bytes,
+                (long long)(sizeof(double) * 90 * P));
+  if (((uintptr_t)adj_ws) & 255) return fail(b, EMU_EINVAL, "adjoint workspace must be 256-byte aligned");
+  if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
+  if (int rc = set_dts(b, &dt)) return rc;
+  b->next_stage = 1;
+  if (b->prof) return adjoint_body(b, dt, lambda, gN, gNbar, adj_ws);
+  const void* key[4] = {lambda, gN, gNbar, adj_ws};
+  const bool same = b->adj_graph && b->adj_dt == dt && std::memcmp(key, b->adj_key, sizeof(key)) == 0;
+  if (!same) {
+    if (b->adj_graph) { cudaGraphExecDestroy(b->adj_graph); b->adj_graph = nullptr; }
+    if (int rc = capture(b, &b->adj_graph, &b->adj_launches,
+                         [&] { return adjoint_body(b, dt, lambda, gN, gNbar, adj_ws); }))
+      return rc;
+    std::memcpy(b->adj_key, key, sizeof(key));
+    b->adj_dt = dt;
+  }
+  return launch_graph(b, b->adj_graph, b->adj_launches);
 }
 
 int emu_weight_gradient(emu_box* b, const double* gN, const double* gNbar, double* out, int on_host) {
@@ -946,6 +1018,8 @@ int emu_weight_gradient(emu_box* b, const double* gN, const double* gNbar, doubl
 int emu_sync(emu_box* b) {
   if (int rc = check_bound(b)) return rc;
   if (int rc = cuda_check(b, cudaStreamSynchronize(b->stream), "synchronise")) return rc;
+  if (b->cap)
+    if (int rc = cuda_check(b, cudaStreamSynchronize(b->cap), "synchronise graph stream")) return rc;
   return read_errors(b);
 }
 
