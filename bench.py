@@ -267,17 +267,22 @@ def run_gpu(args, rank, world, local_rank):
     t_ms = max_over_ranks(dist, elapsed_ms, device)
     value = world * wl.P * args.steps / (t_ms * 1e-3)
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers: every step the
+    # state (z, rho, rhobar) comes from pinned host memory (the next step's copy
+    # overlaps the current step on a side stream, E.HostFeed) and the step's
+    # diagnostics are read back to the host
     host = box.get_host()
     pin = {k: torch.from_numpy(host[k]).pin_memory() for k in ("z", "rho", "rhobar")}
     diag = torch.zeros(E.N_DIAG, dtype=torch.float64).pin_memory()
-    ptr = {k: v.data_ptr() for k, v in pin.items()}
+    feed = E.HostFeed(box, pin)
 
     def e2e_step():
-        E.emu_set_particles(box.box, ptr["z"], None, None, None, None, None, ptr["rho"], ptr["rhobar"], 1)
+        feed.load()
+        feed.prefetch()
         E.emu_step(box.box, 1, dt)
         E.emu_diagnostics(box.box, diag.data_ptr(), 1)
 
+    feed.prefetch()
     e2e_step()
     barrier(dist, device)
     torch.cuda.synchronize(device)
@@ -289,8 +294,9 @@ def run_gpu(args, rank, world, local_rank):
     clk = clocks.stop()
     box.sync()
     e2e_value = world * wl.P * args.steps / e2e_s
-    h2d = sum(v.numel() * 8 for v in pin.values())
+    h2d = feed.h2d_bytes
     d2h = E.N_DIAG * 8
+    del feed
 
     # ---- roofline of the dominant kernel from the live per-launch events
     per = {k: (ms / n if n else 0.0, n, ms) for k, (ms, n) in ktimes.items()}

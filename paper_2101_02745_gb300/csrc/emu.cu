@@ -778,7 +778,7 @@ int emu_batch_diagnostics(emu_box* b, double* out, int on_host) {
   if (!out) return fail(b, EMU_EINVAL, "out is NULL");
   if (int rc = run_moments(b)) return rc;
   before_launch(b, CLS_OTHER);
-  k_diagnostics<<<b->S.nbox, kThreads, 0, b->stream>>>(batch_view(b), b->mom, b->diag);
+  k_diagnostics<<<dim3((unsigned)b->S.nbox, 63), kThreads, 0, b->stream>>>(batch_view(b), b->mom, b->diag);
   if (int rc = after_launch(b, "diagnostics kernel")) return rc;
   return copy_out(b, out, b->diag, sizeof(double) * 63 * b->S.nbox, on_host);
 }

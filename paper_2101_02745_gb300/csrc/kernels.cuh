@@ -787,7 +787,8 @@ __global__ void k_write_geo(BoxGeo g, double dt, BoxGeo* __restrict__ dst, doubl
 }
 
 // Domain diagnostics per box (Eq. 10, one snapshot of Eq. B1, Eq. 18), fixed-
-// order block reduction over the box's cells.  One block per box; out[63 * b + q].
+// order block reduction over the box's cells.  One block per (box, quantity):
+// blockIdx.x = box, blockIdx.y = q; out[63 * b + q].
 __device__ __forceinline__ double abs_entry(const double* __restrict__ m, int64_t NZ, int64_t j, int a, int b) {
   if (a == b) return fabs(m[(int64_t)a * NZ + j]);
   const int lo = a < b ? a : b, hi = a < b ? b : a;
@@ -800,35 +801,33 @@ __global__ void k_diagnostics(Batch B, const double* __restrict__ mom, double* _
   __shared__ double sm[kThreads];
   const BoxGeo& g = B.box[blockIdx.x];
   const int64_t NZ = B.NZ;
-  for (int q = 0; q < 63; ++q) {
-    double s = 0.0;
-    for (int jj = threadIdx.x; jj < g.nz; jj += kThreads) {
-      const int64_t j = g.coff + jj;
-      double v;
-      if (q < 36) {
-        const int blk = q / 9, e = q % 9, a = e / 3, bb = e % 3;
-        const int off = blk == 0 ? 0 : blk == 1 ? 36 : blk == 2 ? 9 : 45;
-        v = abs_entry(mom + (int64_t)off * NZ, NZ, j, a, bb);
-      } else if (q < 45) {
-        v = mom[(int64_t)(q - 36) * NZ + j];
-      } else if (q < 54) {
-        v = mom[(int64_t)(36 + q - 45) * NZ + j];
-      } else {
-        const int k = q - 54;
-        const double nbar = mom[(int64_t)(36 + k) * NZ + j];
-        v = mom[(int64_t)k * NZ + j] + ((k == 4 || k == 6 || k == 8) ? nbar : -nbar);
-      }
-      s += v;
+  const int q = blockIdx.y;
+  double s = 0.0;
+  for (int jj = threadIdx.x; jj < g.nz; jj += kThreads) {
+    const int64_t j = g.coff + jj;
+    double v;
+    if (q < 36) {
+      const int blk = q / 9, e = q % 9, a = e / 3, bb = e % 3;
+      const int off = blk == 0 ? 0 : blk == 1 ? 36 : blk == 2 ? 9 : 45;
+      v = abs_entry(mom + (int64_t)off * NZ, NZ, j, a, bb);
+    } else if (q < 45) {
+      v = mom[(int64_t)(q - 36) * NZ + j];
+    } else if (q < 54) {
+      v = mom[(int64_t)(36 + q - 45) * NZ + j];
+    } else {
+      const int k = q - 54;
+      const double nbar = mom[(int64_t)(36 + k) * NZ + j];
+      v = mom[(int64_t)k * NZ + j] + ((k == 4 || k == 6 || k == 8) ? nbar : -nbar);
     }
-    sm[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = kThreads / 2; w > 0; w >>= 1) {
-      if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) out[63 * blockIdx.x + q] = sm[0] / g.nz;
+    s += v;
+  }
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
     __syncthreads();
   }
+  if (threadIdx.x == 0) out[63 * blockIdx.x + q] = sm[0] / g.nz;
 }
 
 // ------------------------------------------------------------------ adjoint
@@ -937,6 +936,14 @@ k_adj_b(Batch B, Parts pt, const double* __restrict__ W, const double* __restric
   if (u0 >= u1) return;
   const int64_t P = B.Ptot;
   const int MT = B.MT, NZ = B.NZ;
+  constexpr int Hh = Sten<ORDER>::H, T = Sten<ORDER>::T, NWS = Sten<ORDER>::NWS;
+  const double* __restrict__ rho = pt.rho;
+  const double* __restrict__ rhobar = pt.rhobar;
+  const double* __restrict__ Nw = pt.N;
+  const double* __restrict__ Nbw = pt.Nbar;
+  // arrays read per particle, for the L2 prefetch of the next unit: rho, rhobar (18),
+  // lam_out, lam_tot (36), N, Nbar, gN, gNbar (4), weights (NWS)
+  constexpr int narr = 18 + 36 + 4 + NWS;
   int b = box_of_unit(B, u0);
   for (int64_t u = u0; u < u1; ++u) {
     while (u >= B.box[b].uoff + (int64_t)B.box[b].ntiles * B.box[b].M) ++b;
@@ -944,7 +951,27 @@ k_adj_b(Batch B, Parts pt, const double* __restrict__ W, const double* __restric
     const int nz = g.nz, nt = g.ntiles;
     const int lu = (int)(u - g.uoff);
     const int d = lu / nt, tile = lu - d * nt;
-    constexpr int Hh = Sten<ORDER>::H, T = Sten<ORDER>::T;
+    if (u + 1 < u1 && lu + 1 < nt * g.M) {   // prefetch the next unit of the same box (same ring or the next)
+      const int dn = (lu + 1) / nt, tn = lu + 1 - dn * nt;
+      const int i0 = tn * T - __ldg(shift + g.doff + dn);
+      const int n = min(T, nz - tn * T);
+      if (i0 >= 0 && i0 + n <= nz) {
+        const int64_t base = g.poff + (int64_t)dn * nz + i0;
+        for (int a = lane; a < narr; a += kLanes) {
+          const double* arr;
+          if (a < 9) arr = rho + (int64_t)a * P;
+          else if (a < 18) arr = rhobar + (int64_t)(a - 9) * P;
+          else if (a < 36) arr = lam_out + (int64_t)(a - 18) * P;
+          else if (a < 54) arr = lam_tot + (int64_t)(a - 36) * P;
+          else if (a == 54) arr = Nw;
+          else if (a == 55) arr = Nbw;
+          else if (a == 56) arr = gN;
+          else if (a == 57) arr = gNbar;
+          else arr = W + (int64_t)(a - 58) * P;
+          prefetch_l2(arr, base, n);
+        }
+      }
+    }
     const int craw = tile * T - Hh + lane, j = wrapc(craw, nz);
     const bool active = lane >= Hh && lane < Hh + T && craw < nz;
     const int gd = g.doff + d;
@@ -952,7 +979,12 @@ k_adj_b(Batch B, Parts pt, const double* __restrict__ W, const double* __restric
     const int64_t p = g.poff + (int64_t)d * nz + wrapc(j - __ldg(shift + gd), nz);
     double wt[Sten<ORDER>::NW];
     zero_weights<ORDER>(wt);
-    if (active) load_weights<ORDER>(W, P, p, wt);
+    double n1 = 0.0, n2 = 0.0;
+    if (active) {
+      load_weights<ORDER>(W, P, p, wt);
+      n1 = Nw[p];
+      n2 = Nbw[p];
+    }
     double GB[9];
     const double* Ej = E + g.coff + j;
 #pragma unroll
@@ -963,24 +995,31 @@ k_adj_b(Batch B, Parts pt, const double* __restrict__ W, const double* __restric
       GB[k] = gather<ORDER>(wt, G);
     }
     if (!active) continue;
-    const double n1 = pt.N[p], n2 = pt.Nbar[p];
-    double sN = 0.0, sNb = 0.0;
+    // neutrinos, then antineutrinos: every load of a half before its stores
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      const double c = (k == 4 || k == 6 || k == 8) ? -1.0 : 1.0;          // packed conjugation
-      const double r = pt.rho[k * P + p];
-      const double rb = pt.rhobar[k * P + p];
-      const double lr = fma(n1, GB[k], lam_out[k * P + p]);
-      const double lb = fma(-n2 * c, GB[k], lam_out[(9 + k) * P + p]);
-      lam_out[k * P + p] = lr;
-      lam_out[(9 + k) * P + p] = lb;
-      lam_tot[k * P + p] += lr;
-      lam_tot[(9 + k) * P + p] += lb;
-      sN = fma(GB[k], r, sN);
-      sNb = fma(-c * GB[k], rb, sNb);
+    for (int which = 0; which < 2; ++which) {
+      const double* __restrict__ r = which ? rhobar : rho;
+      double rv[9], lo[9], lt[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        rv[k] = r[k * P + p];
+        lo[k] = lam_out[(which * 9 + k) * P + p];
+        lt[k] = lam_tot[(which * 9 + k) * P + p];
+      }
+      double sum = 0.0;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        // B = N rho - Nbar conj(rhobar): dB/drhobar = -Nbar conj(.), conjugation
+        // flipping the imaginary components 4, 6, 8
+        const double sg = which ? ((k == 4 || k == 6 || k == 8) ? 1.0 : -1.0) : 1.0;
+        const double l = fma((which ? n2 : n1) * sg, GB[k], lo[k]);
+        lam_out[(which * 9 + k) * P + p] = l;
+        lam_tot[(which * 9 + k) * P + p] = lt[k] + l;
+        sum = fma(sg * GB[k], rv[k], sum);
+      }
+      if (which) gNbar[p] += sum;
+      else gN[p] += sum;
     }
-    gN[p] += sN;
-    gNbar[p] += sNb;
   }
 }
 

@@ -547,3 +547,48 @@ class Box:
                 fields[k] = a
             args.append(_host_ptr(a))
         emu_set_particles(self.box, *args, 1)
+
+
+class HostFeed:
+    """Double-buffered feed of per-step particle state from pinned host memory.
+
+    `prefetch()` starts copying the host arrays (z, rho, rhobar) into a device
+    staging copy on a side stream; `load()` makes the box's stream wait for
+    that copy and moves the staging copy into the box's bound arrays with
+    emu_set_particles (device to device), after which the next prefetch may
+    overwrite the staging copy.  The host-to-device transfer of the next step's
+    inputs thus runs while the box computes the current step."""
+
+    KEYS = ("z", "rho", "rhobar")
+
+    def __init__(self, box: "Box", pinned: dict):
+        torch = box.torch
+        self.box = box
+        self.pinned = {k: pinned[k] for k in self.KEYS}
+        self.staging = {k: torch.empty_like(box.t[k]) for k in self.KEYS}
+        self.copy = torch.cuda.Stream(box.device)
+        self.ready = torch.cuda.Event()
+        self.consumed = None
+
+    @property
+    def h2d_bytes(self) -> int:
+        return sum(v.numel() * v.element_size() for v in self.pinned.values())
+
+    def prefetch(self):
+        torch = self.box.torch
+        if self.consumed is not None:
+            self.copy.wait_event(self.consumed)
+        with torch.cuda.stream(self.copy):
+            for k in self.KEYS:
+                self.staging[k].copy_(self.pinned[k], non_blocking=True)
+        self.ready.record(self.copy)
+
+    def load(self):
+        torch = self.box.torch
+        self.box.stream.wait_event(self.ready)
+        st = self.staging
+        emu_set_particles(self.box.box, st["z"].data_ptr(), None, None, None, None, None, st["rho"].data_ptr(),
+                          st["rhobar"].data_ptr(), 0)
+        self.consumed = torch.cuda.Event()
+        self.consumed.record(self.box.stream)
+
