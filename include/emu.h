@@ -272,8 +272,10 @@ int emu_set_oscillation(emu_box* box, int32_t box_index, const emu_oscillation* 
  * gNbar are [P].  All pointers are device pointers, except where on_host says
  * otherwise; calls are asynchronous on the box's stream. */
 
-/* Scratch the adjoint step needs: 90 doubles per particle (the stage states
- * y2, y3, two stage adjoints and their running sum), or EMU_EINVAL. */
+/* Scratch the adjoint step needs, or EMU_EINVAL: 90 doubles per particle (the
+ * stage states y2, y3, two stage adjoints and their running sum) plus the
+ * shape weights and grid potential of stages 1-3, kept from the recomputed
+ * forward stages (3 x (kept weights per particle + 36 per cell)). */
 int64_t emu_adjoint_workspace_bytes(const emu_config* cfg);
 
 /* Seed at the current state from dmom = dL/d(moments) ([72][nz], the layout

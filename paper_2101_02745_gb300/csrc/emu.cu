@@ -889,6 +889,13 @@ int emu_set_oscillation(emu_box* b, int32_t box, const emu_oscillation* osc) {
 }  // extern "C"
 
 namespace {
+// Adjoint scratch: stage states y2, y3 and three stage adjoints [18][P] each,
+// then the shape weights and grid potential of stages 1-3 kept from the
+// recomputed forward stages ([3][NWS][P] and [3][36][NZ]).
+size_t adjoint_doubles(const Shape& S) {
+  return (size_t)90 * S.Ptot + 3 * ((size_t)kept_weights(S.order) * S.Ptot + (size_t)kNA * S.NZ);
+}
+
 // The launches of one adjoint step (emu_adjoint_step; the step size is on the device).
 int adjoint_body(emu_box* b, double dt, double* lambda, double* gN, double* gNbar, void* adj_ws) {
   const size_t P = (size_t)b->S.Ptot;
@@ -897,11 +904,22 @@ int adjoint_body(emu_box* b, double dt, double* lambda, double* gN, double* gNba
   double* La = Y3 + 18 * P;      // adjoints of two consecutive stage states
   double* Lb = La + 18 * P;
   double* Lt = Lb + 18 * P;      // running sum: lambda + sum over stages
+  const size_t nws = (size_t)kept_weights(b->S.order) * P, na = (size_t)kNA * b->S.NZ;
+  double* Wk = Lt + 18 * P;      // weights of stages 1..3
+  double* Ak = Wk + 3 * nws;     // grid potential of stages 1..3
   const size_t bytes18 = sizeof(double) * 18 * P;
   if (int rc = launch_shifts(b, kStageFrac, 4)) return rc;
-  // forward stages 1..3: y2, y3 copied out, y4 left in the stage buffer
+  // forward stages 1..3: y2, y3 copied out, y4 left in the stage buffer; each
+  // stage's weights and potential kept for the backward pass
   for (int s = 1; s <= 3; ++s) {
     if (int rc = launch_stage(b, s, 0)) return rc;
+    if (nws)
+      if (int rc = cuda_check(b, cudaMemcpyAsync(Wk + (s - 1) * nws, b->W, sizeof(double) * nws,
+                                                 cudaMemcpyDeviceToDevice, b->stream), "keep stage weights"))
+        return rc;
+    if (int rc = cuda_check(b, cudaMemcpyAsync(Ak + (s - 1) * na, b->A, sizeof(double) * na,
+                                               cudaMemcpyDeviceToDevice, b->stream), "keep stage potential"))
+      return rc;
     if (s < 3)
       if (int rc = cuda_check(b, cudaMemcpyAsync(s == 1 ? Y2 : Y3, b->pt.stage, bytes18, cudaMemcpyDeviceToDevice,
                                                  b->stream), "copy stage state"))
@@ -919,7 +937,11 @@ int adjoint_body(emu_box* b, double dt, double* lambda, double* gN, double* gNba
     double* ysb = s == 1 ? b->pt.rhobar : ys + 9 * P;
     const int* srow = b->shift + (size_t)(s - 1) * b->S.MT;
     const double frac = kStageFrac[s - 1];
-    if (int rc = launch_deposit(b, 0, ys, ysb, srow, frac, b->A)) return rc;
+    // H and weights of the stage state: stage 4 deposits them now, stages 1-3 kept theirs
+    const double* Hs = s == 4 ? b->A : Ak + (s - 1) * na;
+    const double* Ws = s == 4 ? b->W : Wk + (s - 1) * nws;
+    if (s == 4)
+      if (int rc = launch_deposit(b, 0, ys, ysb, srow, frac, b->A)) return rc;
     Parts ps = b->pt;
     ps.rho = ys;
     ps.rhobar = ysb;
@@ -930,10 +952,10 @@ int adjoint_body(emu_box* b, double dt, double* lambda, double* gN, double* gNba
     by_order(b->S.order, [&](auto O) {
       constexpr int R = decltype(O)::value;
       if (b->pot)
-        k_adj_a<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, b->W, b->dirtab, srow, b->A, lambda,
+        k_adj_a<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, Ws, b->dirtab, srow, Hs, lambda,
                                                                       Lnext, a, bc, Lcur, b->pt.acc);
       else
-        k_adj_a<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, b->W, b->dirtab, srow, b->A, lambda,
+        k_adj_a<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, Ws, b->dirtab, srow, Hs, lambda,
                                                                        Lnext, a, bc, Lcur, b->pt.acc);
       return 0;
     });
@@ -941,7 +963,7 @@ int adjoint_body(emu_box* b, double dt, double* lambda, double* gN, double* gNba
     if (int rc = launch_deposit(b, 3, b->pt.acc, nullptr, srow, frac, b->A)) return rc;
     before_launch(b, CLS_OTHER);
     by_order(b->S.order, [&](auto O) {
-      k_adj_b<decltype(O)::value><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, b->W, b->dirtab, srow, b->A,
+      k_adj_b<decltype(O)::value><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, Ws, b->dirtab, srow, b->A,
                                                                               Lcur, Lt, gN, gNbar);
       return 0;
     });
@@ -958,7 +980,7 @@ extern "C" {
 int64_t emu_adjoint_workspace_bytes(const emu_config* cfg) {
   Shape S;
   if (make_shape(cfg, 1, S)) return EMU_EINVAL;
-  return (int64_t)(sizeof(double) * 90 * (size_t)S.Ptot);
+  return (int64_t)(sizeof(double) * adjoint_doubles(S));
 }
 
 int emu_adjoint_seed(emu_box* b, const double* dmom, double* lambda, double* gN, double* gNbar) {
@@ -981,10 +1003,10 @@ int emu_adjoint_step(emu_box* b, double dt, double* lambda, double* gN, double* 
   if (int rc = check_single(b)) return rc;
   if (!(dt > 0) || !std::isfinite(dt)) return fail(b, EMU_EINVAL, "dt must be positive and finite");
   if (!lambda || !gN || !gNbar || !adj_ws) return fail(b, EMU_EINVAL, "adjoint step: NULL pointer");
-  const size_t P = (size_t)b->S.Ptot;
-  if (adj_ws_bytes < (int64_t)(sizeof(double) * 90 * P))
+  const size_t need = sizeof(double) * adjoint_doubles(b->S);
+  if (adj_ws_bytes < (int64_t)need)
     return fail(b, EMU_EINVAL, "adjoint workspace too small: %lld < %lld bytes", (long long)adj_ws_bytes,
-                (long long)(sizeof(double) * 90 * P));
+                (long long)need);
   if (((uintptr_t)adj_ws) & 255) return fail(b, EMU_EINVAL, "adjoint workspace must be 256-byte aligned");
   if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
   if (int rc = set_dts(b, &dt)) return rc;

@@ -188,7 +188,7 @@ def test_adjoint_bad_calls():
     P = box.P
     lam = box._f64(18, P); gN = box._f64(P); gNb = box._f64(P)
     n = E.emu_adjoint_workspace_bytes(box.cfg)
-    assert n == 90 * 8 * P
+    assert n == 8 * (90 * P + 3 * (3 * P + 36 * box.nz))   # quadratic shape: 3 kept weights
     ws = torch.empty(n + 256, dtype=torch.uint8, device="cuda")
     p = (ws.data_ptr() + 255) & ~255
     with pytest.raises(EmuError):
