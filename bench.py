@@ -45,6 +45,11 @@ FLOPS_RK = {1: 336, 2: 336, 3: 336, 4: 302}
 # ... and of one deposit launch: position and shape weights (12), B = N rho -
 # Nbar rhobar^* (27), 3-tap gather (45), accumulation of (1, Omega) x C (63).
 FLOPS_DEPOSIT = 147
+# Other shape orders change the stencil's taps (per component: order 0 has no
+# gather, the cubic shape 5 taps instead of 3): RK stage -45 / +36, deposit
+# -45 / +36 (+8 for the cubic weights); the vacuum and matter terms add 18 adds.
+TAPS_DELTA = {0: -45, 1: 0, 2: 0, 3: 36}
+WEIGHTS_DELTA = {0: -12, 1: -6, 2: 0, 3: 8}
 # FP64 pipe: 2 DFMA per clock per SM (nominal 1.25 TFLOP/s / (2 flop x 152 SMs x 2.07 GHz) = 1.99),
 # so peak = 2 x 2 flop x 152 SMs x 2.07 GHz.
 PEAK_FP64_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
@@ -155,19 +160,30 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
+# Vacuum and matter terms of the --osc runs: three masses and angles, the phase,
+# 50 MeV (the paper's energy), matter of 1e9 g/cm^3 with Ye 0.4.
+OSC_BENCH = dict(mass_eV=(0.0, 8.6e-3, 5.0e-2), theta12=0.59, theta13=0.15, theta23=0.84, delta_cp=1.2,
+                 energy_MeV=50.0, rho_g_cm3=1e9, Ye=0.4)
+
+
 def workload(args):
     from paper_2101_02745_gb300 import workloads as W
     if args.workload == "throughput_1d" and (args.nz or args.ndir):
-        return W.throughput_1d(nz=args.nz or 16384, ndir=args.ndir or 1000)
-    return W.by_name(args.workload)
+        wl = W.throughput_1d(nz=args.nz or 16384, ndir=args.ndir or 1000)
+    else:
+        wl = W.by_name(args.workload)
+    if args.shape_order != 2:
+        wl = W.with_shape(wl, args.shape_order)
+    return wl
 
 
 # ------------------------------------------------------------ CPU oracle
 
-def oracle_rate(wl, steps: int):
+def oracle_rate(wl, steps: int, osc=None):
     """Particle-updates/s of the CPU oracle running `steps` RK4 steps of wl (single thread)."""
     from oracle import oracle as O
-    cfg = O.config(wl.nz, wl.ndir, wl.Lz, wl.kappa, wl.c_light, wl.cfl_adv, wl.cfl_flavor, wl.area)
+    cfg = O.config(wl.nz, wl.ndir, wl.Lz, wl.kappa, wl.c_light, wl.cfl_adv, wl.cfl_flavor, wl.area,
+                   shape_order=wl.shape_order, osc=osc)
     parts = O.init(cfg, wl.n_nu, wl.n_nubar, wl.f_nu, wl.f_nubar, wl.alpha, wl.seed, wl.dirs)
     dt = O.timestep(cfg, O.deposit(cfg, parts))
     t0 = time.perf_counter()
@@ -177,11 +193,11 @@ def oracle_rate(wl, steps: int):
 
 
 def _oracle_job(job):
-    wl, steps = job
-    return oracle_rate(wl, steps)
+    wl, steps, osc = job
+    return oracle_rate(wl, steps, osc)
 
 
-def cpu_baseline(wl_full, budget_s: float = 12.0):
+def cpu_baseline(wl_full, budget_s: float = 12.0, osc=None):
     """The oracle, unchanged, on the host: single-threaded on a sample of the
     workload (the reported value), the same program in one process per host
     core on samples of the workload (aggregate rate), and single-threaded on
@@ -191,9 +207,9 @@ def cpu_baseline(wl_full, budget_s: float = 12.0):
 
     from paper_2101_02745_gb300 import workloads as W
     sample = W.head(wl_full, 1024)
-    rate1, el1 = oracle_rate(sample, 1)
+    rate1, el1 = oracle_rate(sample, 1, osc)
     steps = max(1, int(budget_s / max(el1, 1e-3)) - 1)
-    rate, el = oracle_rate(sample, steps)
+    rate, el = oracle_rate(sample, steps, osc)
     out = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
            "sample": f"{sample.nz} cells x {sample.ndir} directions ({sample.P} particles) of the workload, "
                      f"{steps} RK4 steps in {el:.1f} s, single-threaded C (-O2)"}
@@ -202,9 +218,9 @@ def cpu_baseline(wl_full, budget_s: float = 12.0):
     psteps = max(1, int(0.6 * budget_s / max(el1 / 4, 1e-3)))
     try:
         with ProcessPoolExecutor(ncores, mp_context=mp.get_context("spawn")) as ex:
-            list(ex.map(_oracle_job, [(W.head(wl_full, 8), 1)] * ncores))     # start the workers
+            list(ex.map(_oracle_job, [(W.head(wl_full, 8), 1, osc)] * ncores))     # start the workers
             t0 = time.perf_counter()
-            list(ex.map(_oracle_job, [(small, psteps)] * ncores))
+            list(ex.map(_oracle_job, [(small, psteps, osc)] * ncores))
             wall = time.perf_counter() - t0
         out["all_cores"] = {"value": ncores * small.P * psteps / wall, "cores": ncores,
                             "sample": f"{ncores} processes, each {small.nz} cells x {small.ndir} directions, "
@@ -213,7 +229,7 @@ def cpu_baseline(wl_full, budget_s: float = 12.0):
         out["all_cores"] = {"unavailable": str(e)[:200]}
     per = {}
     for wl, st in ((W.tiny_fiducial(), 100), (W.paper_1d(), 3)):
-        r, e = oracle_rate(wl, st)
+        r, e = oracle_rate(wl, st, osc)
         per[wl.name] = {"value": r, "steps": st, "seconds": e}
     out["per_config"] = per
     return out
@@ -273,6 +289,8 @@ def run_gpu(args, rank, world, local_rank):
 
     wl = workload(args)
     box = E.Box.from_workload(wl, device=device)
+    if args.osc:
+        box.set_oscillation(W.oscillation(**OSC_BENCH))
     stream = box.stream
     dt = box.timestep()
     box.step(args.warmup, dt)
@@ -336,11 +354,11 @@ def run_gpu(args, rank, world, local_rank):
     dominant = max(per, key=lambda k: per[k][2])
     avg_ms = per[dominant][0]
     if dominant == "deposit":
-        flops = FLOPS_DEPOSIT * wl.P
+        flops = (FLOPS_DEPOSIT + TAPS_DELTA[wl.shape_order] + WEIGHTS_DELTA[wl.shape_order]) * wl.P
         bytes_ = BYTES_DEPOSIT * wl.P
         traffic = TRAFFIC_DEPOSIT * wl.P
     else:
-        flops = sum(FLOPS_RK.values()) / 4 * wl.P
+        flops = (sum(FLOPS_RK.values()) / 4 + TAPS_DELTA[wl.shape_order] + (18 if args.osc else 0)) * wl.P
         bytes_ = BYTES_RK * wl.P
         traffic = TRAFFIC_RK * wl.P
     achieved = flops / (avg_ms * 1e-3) / 1e12
@@ -363,6 +381,7 @@ def run_gpu(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl.name, "nz": wl.nz, "ndir": wl.ndir, "particles_per_gpu": wl.P,
+                       "shape_order": wl.shape_order, "vacuum_matter": bool(args.osc),
                        "dt_s": dt, "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "inputs larger than L2 (particle state %.2f GB per GPU vs 129 MB L2)" % (wl.P * 480 / 1e9)},
             "roofline": roofline, "hbm": hbm,
@@ -380,7 +399,7 @@ def run_gpu(args, rank, world, local_rank):
     if rank == 0:
         line.update(extras)
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(wl)
+            line["cpu_baseline"] = cpu_baseline(wl, osc=W.oscillation(**OSC_BENCH) if args.osc else None)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -569,6 +588,8 @@ def main(argv=None):
     ap.add_argument("--ref-cells", type=int, default=256, help="cells per oracle step in --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--adj-steps", type=int, default=0, help="steps of the adjoint workload (default 400)")
+    ap.add_argument("--shape-order", type=int, default=2, choices=[0, 1, 2, 3], help="particle shape (Sec. 2.2.1)")
+    ap.add_argument("--osc", action="store_true", help="add the vacuum and matter terms of Eq. 2")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-sweep and adjoint comparisons of the default line")
     args = ap.parse_args(argv)
