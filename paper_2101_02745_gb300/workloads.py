@@ -201,6 +201,21 @@ def msw_test() -> tuple:
     return Workload("msw_1zone", 1, 2, 1.0, *sp, dirs=dirs, alpha=0.0, steps=0, meta={"osc": osc}), osc
 
 
+def bipolar() -> tuple:
+    """App. A.2: one zone, one particle along +z and one along -z, each carrying
+    nu_e and nubar_e of equal density n = nbar with sqrt(2) G_F n / hbar = 10 x
+    the vacuum frequency |dm^2| c^4 / (2 E hbar) (m1 = 8.6e-3 eV, m2 = 0,
+    theta12 = 0.01 rad, E = 50 MeV, no matter)."""
+    osc = oscillation(mass_eV=(8.6e-3, 0.0, 0.0), theta12=0.01, energy_MeV=50.0)
+    dm2 = (osc["mass_eV"][0] * ERG_PER_EV) ** 2
+    w_vac = dm2 / (2.0 * osc["energy_erg"]) / HBAR_ERG_S
+    n = 10.0 * w_vac / KAPPA
+    dirs = np.array([[0.0, 0.0, 1.0], [0.0, 0.0, -1.0]])
+    sp = _uniform_species(1, n, n, (0, 0, 0), (0, 0, 0))
+    return (Workload("bipolar_1zone", 1, 2, 1.0, *sp, dirs=dirs, alpha=0.0, steps=0,
+                     meta={"omega": w_vac, "mu": KAPPA * n}), osc)
+
+
 def homogeneous_two_beam() -> tuple:
     """App. A.3: one zone, a nu_e beam along +z and a nubar_e beam along -z of
     equal density n = |dm^2| c^4 / (4 sqrt(2) G_F E) with m1 = 8.6e-3 eV, m2 = 0,
