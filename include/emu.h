@@ -266,7 +266,8 @@ int emu_set_oscillation(emu_box* box, int32_t box_index, const emu_oscillation* 
  * the chain rule through Eq. 8, to the initial densities and fluxes.  The
  * paper computes no gradients: these calls serve sensitivity studies of its
  * instability (growth of <|n_emu|>, Eq. 10; final flavour abundances).
- * All three calls take a single box; vacuum and matter terms are included.
+ * The calls work on single boxes and on batches (every box of a batch at
+ * once); vacuum and matter terms and all shape orders are included.
  * Adjoint vectors are packed like rho (9 reals per matrix, [k * P + p]) and
  * hold dL/d(packed component): lambda is [18 * P] (rho, then rhobar), gN and
  * gNbar are [P].  All pointers are device pointers, except where on_host says
@@ -278,14 +279,19 @@ int emu_set_oscillation(emu_box* box, int32_t box_index, const emu_oscillation* 
  * forward stages (3 x (kept weights per particle + 36 per cell)). */
 int64_t emu_adjoint_workspace_bytes(const emu_config* cfg);
 
+/* The same for a batch of nbox boxes. */
+int64_t emu_batch_adjoint_workspace_bytes(const emu_config* cfgs, int32_t nbox);
+
 /* Seed at the current state from dmom = dL/d(moments) ([72][nz], the layout
  * emu_moments returns): lambda = dL/d(rho, rhobar) is overwritten, the direct
  * terms dL/dN and dL/dNbar are ADDED to gN and gNbar.  Errors: EMU_EINVAL
- * (NULL pointer, batch, RK step in progress). */
+ * (NULL pointer, RK step in progress). */
 int emu_adjoint_seed(emu_box* box, const double* dmom, double* lambda, double* gN, double* gNbar);
 
 /* One adjoint RK4 step.  The box must hold the state at the START of the
  * step (positions and rho, rhobar, as emu_step(box, 1, dt) would take it).
+ * dt > 0: the step size of a single box; dt = 0: every box's own step size
+ * (emu_batch_set_dt or a time-step call; the only form a batch takes).
  * On entry lambda = dL/dy_{n+1}; on return lambda = dL/dy_n, and the
  * contributions of this step to dL/dN and dL/dNbar are ADDED to gN, gNbar.
  * The step recomputes its stage states (three forward stages into the RK
@@ -294,10 +300,11 @@ int emu_adjoint_seed(emu_box* box, const double* dmom, double* lambda, double* g
  * deposit of the adjoint dL/dH (the self-interaction operator of Eqs. 5-6 is
  * symmetric) and its interpolation.  The particle state is unchanged; the RK
  * scratch (acc, stage) is overwritten.  adj_ws: device, 256-byte aligned,
- * at least emu_adjoint_workspace_bytes.  The step is captured as a CUDA graph
- * (as emu_batch_step) and replayed while lambda, gN, gNbar, adj_ws and dt
- * stay the same.  Errors: EMU_EINVAL (dt not positive and finite, NULL or
- * short buffers, batch, step in progress), EMU_ECUDA. */
+ * at least emu_(batch_)adjoint_workspace_bytes.  The step is captured as a
+ * CUDA graph (as emu_batch_step) and replayed while lambda, gN, gNbar and
+ * adj_ws stay the same.  Errors: EMU_EINVAL (dt negative or not finite, dt > 0
+ * for a batch, dt = 0 with no step sizes set, NULL or short buffers, step in
+ * progress), EMU_ECUDA. */
 int emu_adjoint_step(emu_box* box, double dt, double* lambda, double* gN, double* gNbar, void* adj_ws,
                      int64_t adj_ws_bytes);
 

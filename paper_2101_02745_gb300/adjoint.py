@@ -7,7 +7,10 @@ Eq. 9 perturbations of sim.alpha, sim.seed), takes sim.nsteps RK4 steps at
 the fixed step sim.dt (Sec. 2.3) and returns the final moments (72, nz) as
 emu_moments lays them out (Eq. 5: n, f_x, f_y, f_z of the neutrinos, then of
 the antineutrinos, 9 packed reals each).  Any torch loss of those moments
-can then be differentiated with respect to the four species inputs.
+can then be differentiated with respect to the four species inputs.  For a
+batch of boxes the inputs and the moments cover all cells of the batch
+(boxes concatenated), sim.dt, sim.alpha and sim.seed are per box, and one
+backward pass gives the gradients of every box.
 
 Forward keeps a checkpoint of the evolving state (z, rho, rhobar) every
 sim.every steps.  Backward seeds the adjoint from dL/d(moments), then walks
@@ -29,14 +32,24 @@ from .emu import Box
 
 @dataclass
 class Simulation:
-    """Settings of one differentiable run on a single box."""
+    """Settings of one differentiable run on a box or a batch of boxes (then
+    dt, alpha and seed are sequences with one entry per box)."""
     box: Box
     nsteps: int
-    dt: float
+    dt: object
     every: int = 20
-    alpha: float = 1e-6
-    seed: int = 0
+    alpha: object = 1e-6
+    seed: object = 0
     dirs: np.ndarray | None = None
+
+    @property
+    def batched(self) -> bool:
+        return self.box.nbox > 1
+
+    def step_dt(self) -> float:
+        """The dt argument of the step calls: the step size, or 0 for a batch
+        (each box's own size, set on the box)."""
+        return 0.0 if self.batched else float(self.dt)
 
 
 def _host(t: torch.Tensor, shape) -> np.ndarray:
@@ -48,20 +61,28 @@ class Evolve(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, n_nu, n_nubar, f_nu, f_nubar, sim: Simulation):
+        from . import emu as E
         box = sim.box
-        if box.nbox != 1:
-            raise ValueError("the adjoint takes a single box")
-        if not (sim.dt > 0) or sim.nsteps < 0 or sim.every < 1:
-            raise ValueError("need dt > 0, nsteps >= 0, every >= 1")
+        dts = np.atleast_1d(np.asarray(sim.dt, float))
+        if len(dts) != box.nbox or not np.all(dts > 0) or sim.nsteps < 0 or sim.every < 1:
+            raise ValueError("need one dt > 0 per box, nsteps >= 0, every >= 1")
         nz = box.nz
-        box.init(_host(n_nu, (nz,)), _host(n_nubar, (nz,)), _host(f_nu, (nz, 3)), _host(f_nubar, (nz, 3)),
-                 sim.dirs, sim.alpha, sim.seed)
+        host = (_host(n_nu, (nz,)), _host(n_nubar, (nz,)), _host(f_nu, (nz, 3)), _host(f_nubar, (nz, 3)))
+        if sim.batched:
+            alpha = np.broadcast_to(np.asarray(sim.alpha, float), (box.nbox,)).copy()
+            seed = np.broadcast_to(np.asarray(sim.seed, np.uint64), (box.nbox,)).copy()
+            dirs = None if sim.dirs is None else np.ascontiguousarray(sim.dirs, float).reshape(-1)
+            E.emu_batch_init_particles(box.box, host[0], host[1], host[2].reshape(-1), host[3].reshape(-1), dirs,
+                                       alpha, seed)
+            box.batch_set_dt(dts)
+        else:
+            box.init(*host, sim.dirs, sim.alpha, sim.seed)
         checkpoints = []
         done = 0
         while done < sim.nsteps:
             checkpoints.append(box.save_state())
             k = min(sim.every, sim.nsteps - done)
-            box.step(k, sim.dt)
+            _steps(sim, k)
             done += k
         final = box.save_state()
         mom = box.moments()
@@ -88,15 +109,22 @@ class Evolve(torch.autograd.Function):
             box.load_state(ctx.checkpoints[seg])
             starts = [box.save_state()]
             for _ in range(k - 1):
-                box.step(1, sim.dt)
+                _steps(sim, 1)
                 starts.append(box.save_state())
             for st in reversed(starts):
                 box.load_state(st)
-                box.adjoint_step(sim.dt, lam, gN, gNbar)
+                box.adjoint_step(sim.step_dt(), lam, gN, gNbar)
         box.load_state(ctx.final)
         g = box.weight_gradient(gN, gNbar).to(ctx.dev)
         ctx.lambda0 = lam  # dL/d(initial rho, rhobar), kept for inspection
         return g[0], g[1], g[2:5].T.contiguous(), g[5:8].T.contiguous(), None
+
+
+def _steps(sim: Simulation, k: int):
+    if sim.batched:
+        sim.box.batch_step(k)
+    else:
+        sim.box.step(k, float(sim.dt))
 
 
 def objectives(mom: torch.Tensor) -> torch.Tensor:

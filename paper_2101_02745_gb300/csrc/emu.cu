@@ -185,7 +185,6 @@ struct emu_box {
   cudaGraphExec_t adj_graph = nullptr;
   int64_t adj_launches = 0;
   const void* adj_key[4] = {nullptr, nullptr, nullptr, nullptr};
-  double adj_dt = 0.0;
   // graphs of a box bound to the legacy default stream run on this blocking
   // stream, which the legacy stream orders implicitly with its own work
   cudaStream_t cap = nullptr;
@@ -896,8 +895,8 @@ size_t adjoint_doubles(const Shape& S) {
   return (size_t)90 * S.Ptot + 3 * ((size_t)kept_weights(S.order) * S.Ptot + (size_t)kNA * S.NZ);
 }
 
-// The launches of one adjoint step (emu_adjoint_step; the step size is on the device).
-int adjoint_body(emu_box* b, double dt, double* lambda, double* gN, double* gNbar, void* adj_ws) {
+// The launches of one adjoint step (emu_adjoint_step; the step sizes are on the device).
+int adjoint_body(emu_box* b, double* lambda, double* gN, double* gNbar, void* adj_ws) {
   const size_t P = (size_t)b->S.Ptot;
   double* Y2 = (double*)adj_ws;  // stage states y2, y3 (y4 stays in the stage buffer)
   double* Y3 = Y2 + 18 * P;
@@ -945,18 +944,16 @@ int adjoint_body(emu_box* b, double dt, double* lambda, double* gN, double* gNba
     Parts ps = b->pt;
     ps.rho = ys;
     ps.rhobar = ysb;
-    const double a = (s == 1 || s == 4) ? dt / 6.0 : dt / 3.0;
-    const double bc = (s == 3) ? dt : 0.5 * dt;
     double* Lcur = (s % 2 == 0) ? La : Lb;
     before_launch(b, CLS_OTHER);
     by_order(b->S.order, [&](auto O) {
       constexpr int R = decltype(O)::value;
       if (b->pot)
         k_adj_a<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, Ws, b->dirtab, srow, Hs, lambda,
-                                                                      Lnext, a, bc, Lcur, b->pt.acc);
+                                                                      Lnext, s, Lcur, b->pt.acc);
       else
         k_adj_a<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, Ws, b->dirtab, srow, Hs, lambda,
-                                                                       Lnext, a, bc, Lcur, b->pt.acc);
+                                                                       Lnext, s, Lcur, b->pt.acc);
       return 0;
     });
     if (int rc = after_launch(b, "adjoint stage kernel")) return rc;
@@ -977,14 +974,16 @@ int adjoint_body(emu_box* b, double dt, double* lambda, double* gN, double* gNba
 
 extern "C" {
 
-int64_t emu_adjoint_workspace_bytes(const emu_config* cfg) {
+int64_t emu_adjoint_workspace_bytes(const emu_config* cfg) { return emu_batch_adjoint_workspace_bytes(cfg, 1); }
+
+int64_t emu_batch_adjoint_workspace_bytes(const emu_config* cfgs, int32_t nbox) {
   Shape S;
-  if (make_shape(cfg, 1, S)) return EMU_EINVAL;
+  if (make_shape(cfgs, nbox, S)) return EMU_EINVAL;
   return (int64_t)(sizeof(double) * adjoint_doubles(S));
 }
 
 int emu_adjoint_seed(emu_box* b, const double* dmom, double* lambda, double* gN, double* gNbar) {
-  if (int rc = check_single(b)) return rc;
+  if (int rc = check_bound(b)) return rc;
   if (!dmom || !lambda || !gN || !gNbar) return fail(b, EMU_EINVAL, "adjoint seed: NULL pointer");
   if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
   const double zero = 0.0;
@@ -1000,8 +999,13 @@ int emu_adjoint_seed(emu_box* b, const double* dmom, double* lambda, double* gN,
 
 int emu_adjoint_step(emu_box* b, double dt, double* lambda, double* gN, double* gNbar, void* adj_ws,
                      int64_t adj_ws_bytes) {
-  if (int rc = check_single(b)) return rc;
-  if (!(dt > 0) || !std::isfinite(dt)) return fail(b, EMU_EINVAL, "dt must be positive and finite");
+  if (int rc = check_bound(b)) return rc;
+  if (dt != 0.0) {
+    if (b->S.nbox != 1) return fail(b, EMU_EINVAL, "a batch takes dt = 0 (each box's own step size)");
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(b, EMU_EINVAL, "dt must be positive and finite, or 0");
+  } else if (!b->step_valid) {
+    return fail(b, EMU_EINVAL, "dt = 0 needs the boxes' step sizes (emu_batch_set_dt or a time-step call)");
+  }
   if (!lambda || !gN || !gNbar || !adj_ws) return fail(b, EMU_EINVAL, "adjoint step: NULL pointer");
   const size_t need = sizeof(double) * adjoint_doubles(b->S);
   if (adj_ws_bytes < (int64_t)need)
@@ -1009,18 +1013,18 @@ int emu_adjoint_step(emu_box* b, double dt, double* lambda, double* gN, double* 
                 (long long)need);
   if (((uintptr_t)adj_ws) & 255) return fail(b, EMU_EINVAL, "adjoint workspace must be 256-byte aligned");
   if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
-  if (int rc = set_dts(b, &dt)) return rc;
+  if (int rc = set_dts(b, dt != 0.0 ? &dt : b->step_dt.data())) return rc;
   b->next_stage = 1;
-  if (b->prof) return adjoint_body(b, dt, lambda, gN, gNbar, adj_ws);
+  if (b->prof) return adjoint_body(b, lambda, gN, gNbar, adj_ws);
+  // the graph reads the step sizes from the device: it depends on the buffers only
   const void* key[4] = {lambda, gN, gNbar, adj_ws};
-  const bool same = b->adj_graph && b->adj_dt == dt && std::memcmp(key, b->adj_key, sizeof(key)) == 0;
+  const bool same = b->adj_graph && std::memcmp(key, b->adj_key, sizeof(key)) == 0;
   if (!same) {
     if (b->adj_graph) { cudaGraphExecDestroy(b->adj_graph); b->adj_graph = nullptr; }
     if (int rc = capture(b, &b->adj_graph, &b->adj_launches,
-                         [&] { return adjoint_body(b, dt, lambda, gN, gNbar, adj_ws); }))
+                         [&] { return adjoint_body(b, lambda, gN, gNbar, adj_ws); }))
       return rc;
     std::memcpy(b->adj_key, key, sizeof(key));
-    b->adj_dt = dt;
   }
   return launch_graph(b, b->adj_graph, b->adj_launches);
 }

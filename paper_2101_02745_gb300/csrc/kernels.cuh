@@ -850,15 +850,16 @@ __device__ __forceinline__ void kfull(const double H[9], const double r[9], doub
   for (int k = 0; k < 6; ++k) out[3 + k] = ko[k];
 }
 
-// First adjoint launch of one stage.  m = a lam + b lamn (the adjoint of this
-// stage's derivative k_s); writes lam_out = J_rho^T m (direct terms) and
-// Gam = dL/dH_self.  pt.rho / pt.rhobar point at the stage state.
+// First adjoint launch of stage s.  m = a lam + c lamn, the adjoint of this
+// stage's derivative k_s, with the box's step dt: a = dt/6 (s = 1, 4) or dt/3,
+// c = dt/2 (s = 1, 2) or dt (s = 3), lamn the adjoint of stage s + 1 (NULL
+// for s = 4); writes lam_out = J_rho^T m (direct terms) and Gam = dL/dH_self.
+// pt.rho / pt.rhobar point at the stage state.
 template <bool POT, int ORDER>
 __global__ void __launch_bounds__(kThreads, 2)
 k_adj_a(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
         const int* __restrict__ shift, const double* __restrict__ A, const double* __restrict__ lam,
-        const double* __restrict__ lamn, double a, double bc, double* __restrict__ lam_out,
-        double* __restrict__ Gam) {
+        const double* __restrict__ lamn, int s, double* __restrict__ lam_out, double* __restrict__ Gam) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   const int64_t u0 = unit_begin(w, B), u1 = unit_begin(w + 1, B);
@@ -869,6 +870,9 @@ k_adj_a(Batch B, Parts pt, const double* __restrict__ W, const double* __restric
   for (int64_t u = u0; u < u1; ++u) {
     while (u >= B.box[b].uoff + (int64_t)B.box[b].ntiles * B.box[b].M) ++b;
     const BoxGeo& g = B.box[b];
+    const double dtb = B.dt[b];
+    const double a = (s == 1 || s == 4) ? dtb / 6.0 : dtb / 3.0;
+    const double bc = (s == 3) ? dtb : 0.5 * dtb;
     const int nz = g.nz, nt = g.ntiles;
     const int lu = (int)(u - g.uoff);
     const int d = lu / nt, tile = lu - d * nt;

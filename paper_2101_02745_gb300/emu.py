@@ -108,6 +108,7 @@ def load(build_if_missing: bool = False):
         "emu_autotune": (i32, [vp, i32, vp, vp]),
         "emu_set_oscillation": (i32, [vp, ctypes.c_int32, ctypes.POINTER(emu_oscillation)]),
         "emu_adjoint_workspace_bytes": (i64, [cfgp]),
+        "emu_batch_adjoint_workspace_bytes": (i64, [cfgp, ctypes.c_int32]),
         "emu_adjoint_seed": (i32, [vp, vp, vp, vp, vp]),
         "emu_adjoint_step": (i32, [vp, dbl, vp, vp, vp, vp, i64]),
         "emu_weight_gradient": (i32, [vp, vp, vp, vp, i32]),
@@ -331,6 +332,14 @@ def emu_adjoint_workspace_bytes(cfg: emu_config) -> int:
     return int(n)
 
 
+def emu_batch_adjoint_workspace_bytes(cfgs) -> int:
+    arr, ptr = _cfg_array(cfgs)
+    n = load().emu_batch_adjoint_workspace_bytes(ptr, len(cfgs))
+    if n < 0:
+        raise EmuError(int(n), "invalid configuration")
+    return int(n)
+
+
 def emu_adjoint_seed(box, dmom, lam, gN, gNbar):
     _check(box, load().emu_adjoint_seed(box, dmom, lam, gN, gNbar))
 
@@ -516,9 +525,10 @@ class Box:
         emu_adjoint_seed(self.box, dmom.data_ptr(), lam.data_ptr(), gN.data_ptr(), gNbar.data_ptr())
 
     def adjoint_step(self, dt, lam, gN, gNbar):
-        """One adjoint RK4 step from the step's start state (held by the box)."""
+        """One adjoint RK4 step from the step's start state (held by the box);
+        dt = 0: every box's own step size (batches)."""
         if getattr(self, "_adj_ws", None) is None:
-            n = emu_adjoint_workspace_bytes(self.cfg)
+            n = emu_batch_adjoint_workspace_bytes(self.cfgs)
             self._adj_raw = self.torch.empty(n + 256, dtype=self.torch.uint8, device=self.device)
             self._adj_ws = ((self._adj_raw.data_ptr() + 255) & ~255, n)
         ptr, n = self._adj_ws

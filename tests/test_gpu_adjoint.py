@@ -180,6 +180,38 @@ def test_adjoint_box_full_size_vs_oracle_reference_gradient():
           f"({(t2 - t1) / (t1 - t0):.2f}x), rel err vs oracle {rel_rows(g, g_ref)}, vs GPU FD {rel_rows(g, g_fd)}")
 
 
+def test_batch_adjoint_matches_single_boxes():
+    """One backward pass over a batch of two uneven boxes (different sizes,
+    step sizes, per-cell species) gives each box the gradient its own
+    single-box run gives (the boxes are independent; summation orders differ)."""
+    wl1 = W.adjoint_box(nz=32, ndir=16, steps=18)
+    wl2 = W.random_box(41, 10, seed=3)
+    wl2.alpha = 1e-8
+    wls, dts = [wl1, wl2], [3.4e-12, 1.1e-12]
+    ins = [[torch.tensor(a, dtype=torch.float64, device="cuda") for a in (w.n_nu, w.n_nubar, w.f_nu, w.f_nubar)]
+           for w in wls]
+
+    def run(box, sim, parts, slices):
+        leaves = [p.clone().requires_grad_(True) for p in parts]
+        mom = Evolve.apply(*leaves, sim)
+        L = sum(objectives(mom[:, sl])[1] for sl in slices)
+        L.backward()
+        return [l.grad.cpu().numpy() for l in leaves]
+
+    batch = Box.from_workloads(wls, init=False)
+    simb = Simulation(batch, 18, dts, every=5, alpha=[w.alpha for w in wls], seed=[w.seed for w in wls])
+    cat = [torch.cat([ins[0][i], ins[1][i]]) for i in range(4)]
+    gb = run(batch, simb, cat, [slice(0, 32), slice(32, 73)])
+    off = 0
+    for w, dt, parts in zip(wls, dts, ins):
+        box = Box.from_workload(w, init=False)
+        g = run(box, Simulation(box, 18, dt, every=5, alpha=w.alpha, seed=w.seed), parts, [slice(0, w.nz)])
+        for a, b in zip(gb, g):
+            part = a[off:off + w.nz]
+            assert np.abs(part - b).max() <= 1e-9 * np.abs(b).max(), (w.name, np.abs(part - b).max(), np.abs(b).max())
+        off += w.nz
+
+
 def test_adjoint_bad_calls():
     from paper_2101_02745_gb300 import emu as E
 
@@ -207,6 +239,6 @@ def test_adjoint_bad_calls():
     E.emu_adjoint_step(box.box, 3e-12, lam.data_ptr(), gN.data_ptr(), gNb.data_ptr(), p, n)
     box.sync()
     batch = Box.from_workloads([wl, wl])
-    with pytest.raises(EmuError):
-        batch.adjoint_seed(batch._f64(72, batch.nz), batch._f64(18, batch.P), batch._f64(batch.P),
-                           batch._f64(batch.P))
+    blam = batch._f64(18, batch.P)
+    with pytest.raises(EmuError):     # a batch takes dt = 0 (its boxes' own step sizes)
+        batch.adjoint_step(3e-12, blam, batch._f64(batch.P), batch._f64(batch.P))
