@@ -366,6 +366,26 @@ def emu_destroy(box):
 def _fibonacci(M):
     raise ValueError("explicit directions for some boxes of a batch need explicit directions for all")
 
+def _ordered(fn):
+    """Box methods run the library on the box's stream: order that stream after
+    the caller's current stream (tensors torch just filled) and the current
+    stream after it (results, and memory torch may reuse).  No-op when the
+    box uses the current stream."""
+    import functools
+
+    @functools.wraps(fn)
+    def wrapper(self, *args, **kwargs):
+        cur = self.torch.cuda.current_stream(self.device)
+        same = cur == self.stream
+        if not same:
+            self.stream.wait_stream(cur)
+        out = fn(self, *args, **kwargs)
+        if not same:
+            cur.wait_stream(self.stream)
+        return out
+    return wrapper
+
+
 class Box:
     """One box with its caller-owned device memory held as torch tensors."""
 
@@ -401,6 +421,7 @@ class Box:
                                      ("z", "ox", "oy", "oz", "N", "Nbar", "rho", "rhobar", "acc", "stage")],
                                    self.P)
         self.box = emu_batch_create(self.cfgs)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))   # the zero fills above
         emu_bind(self.box, self.parts, self.ws_ptr, self.ws_bytes, self.stream.cuda_stream)
 
     @classmethod
@@ -438,6 +459,7 @@ class Box:
             pass
 
     # -- ABI calls
+    @_ordered
     def init(self, n_nu, n_nubar, f_nu, f_nubar, dirs=None, alpha=1e-6, seed=0):
         nz = self.nz
         emu_init_particles(self.box, np.broadcast_to(np.asarray(n_nu, float), (nz,)),
@@ -445,32 +467,39 @@ class Box:
                            np.broadcast_to(np.asarray(f_nu, float), (nz, 3)),
                            np.broadcast_to(np.asarray(f_nubar, float), (nz, 3)), dirs, alpha, seed)
 
+    @_ordered
     def deposit(self, src=0, pos_dt=0.0):
         out = self.torch.empty(36, self.nz, dtype=self.torch.float64, device=self.device)
         emu_deposit(self.box, src, pos_dt, out.data_ptr(), 0)
         return out
 
+    @_ordered
     def interpolate_H(self, pos_dt=0.0):
         out = self.torch.empty(9, self.P, dtype=self.torch.float64, device=self.device)
         emu_interpolate_H(self.box, pos_dt, out.data_ptr(), 0)
         return out
 
+    @_ordered
     def rk_stage(self, s, dt):
         emu_rk_stage(self.box, s, dt)
 
+    @_ordered
     def step(self, nsteps, dt=0.0):
         emu_step(self.box, nsteps, dt)
 
+    @_ordered
     def moments(self):
         out = self.torch.empty(72, self.nz, dtype=self.torch.float64, device=self.device)
         emu_moments(self.box, out.data_ptr(), 0)
         return out
 
+    @_ordered
     def diagnostics(self) -> np.ndarray:
         out = np.zeros(N_DIAG)
         emu_diagnostics(self.box, _host_ptr(out), 1)
         return out
 
+    @_ordered
     def timestep(self) -> float:
         return emu_timestep(self.box)
 
@@ -478,23 +507,29 @@ class Box:
         emu_sync(self.box)
 
     # -- batch calls
+    @_ordered
     def batch_timestep(self) -> np.ndarray:
         return emu_batch_timestep(self.box, self.nbox)
 
+    @_ordered
     def batch_set_dt(self, dt):
         emu_batch_set_dt(self.box, dt)
 
+    @_ordered
     def batch_step(self, nsteps):
         emu_batch_step(self.box, nsteps)
 
+    @_ordered
     def batch_diagnostics(self) -> np.ndarray:
         out = np.zeros((self.nbox, N_DIAG))
         emu_batch_diagnostics(self.box, _host_ptr(out), 1)
         return out
 
+    @_ordered
     def autotune(self, trial_steps=2):
         return emu_autotune(self.box, trial_steps)
 
+    @_ordered
     def set_oscillation(self, osc, box=-1):
         emu_set_oscillation(self.box, box, osc)
 
@@ -505,6 +540,7 @@ class Box:
     def _f64(self, *shape):
         return self.torch.zeros(*shape, dtype=self.torch.float64, device=self.device)
 
+    @_ordered
     def save_state(self, out=None):
         """Positions and density matrices (the evolving state) copied into a
         (19, P) device tensor: row 0 z, rows 1-9 rho, rows 10-18 rhobar."""
@@ -514,16 +550,19 @@ class Box:
                           out[10].data_ptr(), 0)
         return out
 
+    @_ordered
     def load_state(self, st):
         emu_set_particles(self.box, st[0].data_ptr(), None, None, None, None, None, st[1].data_ptr(),
                           st[10].data_ptr(), 0)
 
+    @_ordered
     def adjoint_seed(self, dmom, lam, gN, gNbar):
         """lam (18, P) = dL/d(rho, rhobar) from dmom = dL/d(moments) (72, nz);
         adds the direct terms to gN, gNbar (P,)."""
         dmom = dmom.to(dtype=self.torch.float64, device=self.device).contiguous()
         emu_adjoint_seed(self.box, dmom.data_ptr(), lam.data_ptr(), gN.data_ptr(), gNbar.data_ptr())
 
+    @_ordered
     def adjoint_step(self, dt, lam, gN, gNbar):
         """One adjoint RK4 step from the step's start state (held by the box);
         dt = 0: every box's own step size (batches)."""
@@ -534,12 +573,14 @@ class Box:
         ptr, n = self._adj_ws
         emu_adjoint_step(self.box, dt, lam.data_ptr(), gN.data_ptr(), gNbar.data_ptr(), ptr, n)
 
+    @_ordered
     def weight_gradient(self, gN, gNbar):
         """(8, nz): dL/dn_nu, dL/dn_nubar, dL/df_nu (x, y, z), dL/df_nubar (x, y, z) per cell."""
         out = self._f64(8, self.nz)
         emu_weight_gradient(self.box, gN.data_ptr(), gNbar.data_ptr(), out.data_ptr(), 0)
         return out
 
+    @_ordered
     def get_host(self) -> dict:
         """All particle fields copied to host numpy arrays (rho, rhobar as (9, P))."""
         h = {k: np.zeros(self.P) for k in self.FIELDS}
@@ -548,6 +589,7 @@ class Box:
         emu_get_particles(self.box, *[_host_ptr(h[k]) for k in self.FIELDS + ("rho", "rhobar")], 1)
         return h
 
+    @_ordered
     def set_host(self, **fields):
         args = []
         for k in self.FIELDS + ("rho", "rhobar"):
