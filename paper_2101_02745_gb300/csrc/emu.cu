@@ -107,6 +107,8 @@ const char* make_shape(const emu_config* cfgs, int nbox, Shape& S) {
     g.cfl_adv = c->cfl_adv;
     g.cfl_flavor = c->cfl_flavor;
     g.kappa = c->kappa;
+    // the kernels index a box's units with int (unit = direction * ntiles + tile)
+    if ((int64_t)g.ntiles * g.M > INT32_MAX) return "box too large: its tiles x directions exceed 2^31";
     S.Ptot += g.P;
     S.U += (int64_t)g.ntiles * g.M;
     NZ += c->nz;

@@ -64,6 +64,12 @@ def test_workspace_and_config_validation(lib):
         assert E.emu_last_error(None)
 
 
+def test_oversized_box_rejected(lib):
+    """A box whose units (tiles x directions) overflow the kernels' int index is rejected."""
+    cfg = E.make_config(30 * 40000, 60000, 1.0e5, 1.9e-22, 3e10)   # 40000 tiles x 60000 directions > 2^31
+    assert E.load().emu_workspace_bytes(cfg) == E.EMU_EINVAL
+
+
 def test_shape_orders_geometry(lib):
     """Orders 0-2 tile 30 cells per warp, order 3 (two halo lanes a side) 28;
     the kept shape weights: none (order 0), 3 (1, 2) or 5 (3) per particle."""
