@@ -127,3 +127,36 @@ def test_batch_invariants_each_box(torch):
         scale = np.abs(d0[b, 36:45]).max() + np.abs(d0[b, 45:54]).max()
         assert np.abs(d1[b, 54:63] - d0[b, 54:63]).max() < 1e-12 * scale
     box.sync()
+
+
+def test_full_sweep_sampled_boxes(torch):
+    """The benchmark's sweep at full size (256 boxes, 31.7M particles) in its
+    launch configuration (autotuned grid, graph replay): two steps of the whole
+    batch, then the smallest, the largest and two other boxes against the
+    oracle run of each box alone."""
+    from paper_2101_02745_gb300.emu import Box
+    wls = W.sweep(256, seed=0)
+    box = Box.from_workloads(wls)
+    dts = box.batch_timestep()
+    box.autotune(trial_steps=1)
+    box.batch_step(2)
+    sizes = [w.P for w in wls]
+    picks = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 17, 200})
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    P = offs[-1]
+    for b in picks:
+        w = wls[b]
+        cfg = _cfg(w)
+        parts = O.init(cfg, w.n_nu, w.n_nubar, w.f_nu, w.f_nubar, w.alpha, w.seed)
+        assert abs(dts[b] / O.timestep(cfg, O.deposit(cfg, parts)) - 1) < 1e-14
+        O.run(cfg, parts, dts[b], 2)
+        # this box's slice of the batch state (device to host, this box only)
+        sl = slice(int(offs[b]), int(offs[b + 1]))
+        rho = box.t["rho"][:, sl].cpu().numpy()
+        rhob = box.t["rhobar"][:, sl].cpu().numpy()
+        z = box.t["z"][sl].cpu().numpy()
+        assert family_err(rho, pack(parts["rho"])) < 1e-10, w.name
+        assert family_err(rhob, pack(parts["rhobar"])) < 1e-10, w.name
+        assert np.abs(z - parts["z"]).max() <= 1e-13 * w.Lz
+    assert P == box.P
+    box.sync()
