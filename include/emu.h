@@ -43,6 +43,10 @@
  *   - Every call enqueues work on the stream given to emu_bind and returns
  *     without waiting, except the calls that write host memory (on_host = 1),
  *     emu_timestep and emu_sync, which synchronise that stream.
+ *   - A box bound to the legacy default stream (which cannot be captured)
+ *     captures and replays its CUDA graphs on a blocking stream the library
+ *     creates for it; the legacy stream orders that stream's work implicitly
+ *     before and after its own.  No device memory is involved.
  *   - Calls on one box must not run concurrently from several host threads.
  *
  * Errors: every function returns EMU_OK (0) or a negative code; the message
