@@ -36,6 +36,7 @@ struct Shape {
   int64_t Ptot = 0, U = 0;
   int NZ = 0, MT = 0, NT = 0;
   int order = 2;   // shape order of every box (Sec. 2.2.1)
+  int Mmax = 0;    // most directions of a box
   int T = 30;      // cells per tile for that order
   std::vector<BoxGeo> geo;
 };
@@ -111,6 +112,7 @@ const char* make_shape(const emu_config* cfgs, int nbox, Shape& S) {
     if ((int64_t)g.ntiles * g.M > INT32_MAX) return "box too large: its tiles x directions exceed 2^31";
     S.Ptot += g.P;
     S.U += (int64_t)g.ntiles * g.M;
+    S.Mmax = g.M > S.Mmax ? g.M : S.Mmax;
     NZ += c->nz;
     MT += c->ndir;
     NT += g.ntiles;
@@ -260,10 +262,25 @@ int after_launch(emu_box* b, const char* what) {
 
 dim3 persist_grid(const emu_box* b) { return dim3((unsigned)b->blocks, 1, 1); }
 
-unsigned combine_blocks(int NZ) {
-  const int64_t n = (int64_t)kNA * NZ;
-  const int64_t blocks = (n + kThreads - 1) / kThreads;
-  return (unsigned)(blocks < 4 * kPersistBlocks ? blocks : 4 * kPersistBlocks);
+// Warps per group of 32 outputs in k_combine.  Long sums (more than 8
+// partials per tile: small boxes, whose warps own one unit or few) are split
+// over more warps, as far as needed to fill about one wave of the persistent
+// grid (304 blocks x 8 warps); short sums and boxes with enough outputs to
+// fill the GPU keep one warp (coalesced, latency hidden by the other warps).
+int combine_split(const Shape& S, int64_t nw) {
+  const int64_t per_warp = nw > 0 && S.U / nw > 0 ? S.U / nw : 1;   // fewest units a warp takes
+  const int64_t most = (S.Mmax + per_warp - 1) / per_warp + 1;        // most warps over one tile
+  if (most <= 8) return 1;
+  const int64_t out_warps = ((int64_t)kNA * S.NZ + kLanes - 1) / kLanes;
+  int split = 1;
+  while (split < kWarps && out_warps * split * 2 <= (int64_t)kPersistBlocks * kWarps && split * 8 < most) split <<= 1;
+  return split;
+}
+
+unsigned combine_blocks(int NZ, int split) {
+  const int64_t groups = (int64_t)(kWarps / split);
+  const int64_t blocks = ((int64_t)kNA * NZ + groups * kLanes - 1) / (groups * kLanes);
+  return (unsigned)(blocks < 8 * kPersistBlocks ? blocks : 8 * kPersistBlocks);
 }
 
 int check_bound(emu_box* b) {
@@ -392,7 +409,8 @@ int launch_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, c
   });
   if (int rc = after_launch(b, "deposit kernel")) return rc;
   before_launch(b, CLS_COMBINE);
-  k_combine<<<combine_blocks(B.NZ), kThreads, 0, b->stream>>>(B, b->partial, out, (mode == 0 || mode == 3) ? 1 : 0,
+  const int split = combine_split(b->S, B.nw);
+  k_combine<<<combine_blocks(B.NZ, split), kThreads, 0, b->stream>>>(B, b->partial, out, (mode == 0 || mode == 3) ? 1 : 0, split,
                                                                 b->err);
   return after_launch(b, "deposit combine kernel");
 }
@@ -1191,7 +1209,8 @@ extern "C" int emu_deposit_static(const emu_config* cfg, const double* z, const 
   k_deposit<0, 2><<<dim3(kPersistBlocks), kThreads, 0, st>>>(B, z, N, Nbar, rho, rhobar, dirtab, shift, 1.0, partial,
                                                             nullptr, err);
   if (int rc = check(cudaGetLastError(), "deposit kernel")) return rc;
-  k_combine<<<combine_blocks(S.NZ), kThreads, 0, st>>>(B, partial, A_out, 1, err);
+  const int split = combine_split(S, B.nw);
+  k_combine<<<combine_blocks(S.NZ, split), kThreads, 0, st>>>(B, partial, A_out, 1, split, err);
   if (int rc = check(cudaGetLastError(), "deposit combine kernel")) return rc;
   int h = 0;
   if (int rc = check(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st), "read error word")) return rc;

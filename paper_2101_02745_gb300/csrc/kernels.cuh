@@ -450,25 +450,49 @@ k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, c
 
 // Deposit, second launch: fixed-order sum of the per-warp partials.
 // out[c * NZ + coff_b + j] = scale_b * (sum over the warps that own units of
-// j's tile, in warp order), scale_b = kappa_b / dV_b (MODE 0) or 1 / dV_b.
+// j's tile), scale_b = kappa_b / dV_b (MODE 0) or 1 / dV_b.  Lane l of a warp
+// takes output e0 + l (consecutive cells: coalesced reads of the partials).
+// With `split` > 1 (a power of two <= 8), `split` warps of a block take the
+// same 32 outputs: warp i adds the partials of warps wf + i, wf + i + split,
+// ... in order, and the first adds the split sums in warp order through shared
+// memory.  The order depends only on the batch, the grid and `split`: results
+// are bitwise reproducible.
 __global__ void k_combine(Batch B, const double* __restrict__ partial, double* __restrict__ out, int potential,
-                          int* __restrict__ err) {
+                          int split, int* __restrict__ err) {
+  __shared__ double sums[kWarps][kLanes];
   const int64_t n = (int64_t)kNA * B.NZ;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int grp = wib / split, wi = wib - grp * split;       // output group of this warp, rank within it
+  const int groups = kWarps / split;
   int bad = 0;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e / B.NZ), gc = (int)(e - (int64_t)c * B.NZ);
-    const BoxGeo& g = B.box[box_of_cell(B, gc)];
-    const int lc = gc - g.coff;
-    const int tile = lc / B.T, k = lc - tile * B.T;
-    const int64_t gtile = g.toff + tile;
-    const int64_t wf = warp_of_unit(g.uoff + (int64_t)tile * g.M, B);
-    const int64_t wl = warp_of_unit(g.uoff + (int64_t)(tile + 1) * g.M - 1, B);
-    const double* src = partial + c * B.T + k;
+  // every block runs the same number of rounds (it synchronises inside)
+  for (int64_t base = (int64_t)blockIdx.x * groups * kLanes; base < n; base += (int64_t)gridDim.x * groups * kLanes) {
+    const int64_t e = base + (int64_t)grp * kLanes + lane;
     double v = 0.0;
-    for (int64_t q = wf; q <= wl; ++q) v += __ldcg(src + (q + gtile) * kSlot);
-    v *= potential ? g.kappa_dV : g.inv_dV;
-    bad |= !isfinite(v);
-    out[e] = v;
+    const BoxGeo* g = nullptr;
+    if (e < n) {
+      const int c = (int)(e / B.NZ), gc = (int)(e - (int64_t)c * B.NZ);
+      g = &B.box[box_of_cell(B, gc)];
+      const int lc = gc - g->coff;
+      const int tile = lc / B.T, k = lc - tile * B.T;
+      const int64_t gtile = g->toff + tile;
+      const int64_t wf = warp_of_unit(g->uoff + (int64_t)tile * g->M, B);
+      const int64_t wl = warp_of_unit(g->uoff + (int64_t)(tile + 1) * g->M - 1, B);
+      const double* src = partial + c * B.T + k;
+      for (int64_t q = wf + wi; q <= wl; q += split) v += __ldcg(src + (q + gtile) * kSlot);
+    }
+    if (split > 1) {
+      sums[wib][lane] = v;
+      __syncthreads();
+      if (wi == 0)
+        for (int i = 1; i < split; ++i) v += sums[wib + i][lane];
+      __syncthreads();
+    }
+    if (e < n && wi == 0) {
+      v *= potential ? g->kappa_dV : g->inv_dV;
+      bad |= !isfinite(v);
+      out[e] = v;
+    }
   }
   if (bad) atomicOr(err, ERR_NONFINITE);
 }
