@@ -60,7 +60,7 @@ BYTES_DEPOSIT = 24 * 8
 # DRAM read + write per particle of one launch, from an ncu capture of the current
 # kernels (2048 cells x 1000 directions, 2.048M particles, stages 1-4 averaged):
 # scaled by the particles of the timed launch.
-TRAFFIC_RK = 761.9
+TRAFFIC_RK = None    # the 32-cell RK stage: counters not taken yet
 TRAFFIC_DEPOSIT = 297.9
 
 
@@ -360,7 +360,7 @@ def run_gpu(args, rank, world, local_rank):
     else:
         flops = (sum(FLOPS_RK.values()) / 4 + TAPS_DELTA[wl.shape_order] + (18 if args.osc else 0)) * wl.P
         bytes_ = BYTES_RK * wl.P
-        traffic = TRAFFIC_RK * wl.P
+        traffic = TRAFFIC_RK * wl.P if TRAFFIC_RK else None
     achieved = flops / (avg_ms * 1e-3) / 1e12
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)

@@ -33,7 +33,7 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 // Geometry of a batch, from its configurations only (no device needed).
 struct Shape {
   int nbox = 0;
-  int64_t Ptot = 0, U = 0;
+  int64_t Ptot = 0, U = 0, U32 = 0;
   int NZ = 0, MT = 0, NT = 0;
   int order = 2;   // shape order of every box (Sec. 2.2.1)
   int Mmax = 0;    // most directions of a box
@@ -94,6 +94,8 @@ const char* make_shape(const emu_config* cfgs, int nbox, Shape& S) {
     g.P = (int64_t)c->nz * c->ndir;
     g.poff = S.Ptot;
     g.uoff = S.U;
+    g.ntiles32 = (c->nz + kLanes - 1) / kLanes;
+    g.uoff32 = S.U32;
     g.coff = (int)NZ;
     g.toff = (int)NT;
     g.doff = (int)MT;
@@ -112,6 +114,7 @@ const char* make_shape(const emu_config* cfgs, int nbox, Shape& S) {
     if ((int64_t)g.ntiles * g.M > INT32_MAX) return "box too large: its tiles x directions exceed 2^31";
     S.Ptot += g.P;
     S.U += (int64_t)g.ntiles * g.M;
+    S.U32 += (int64_t)g.ntiles32 * g.M;
     S.Mmax = g.M > S.Mmax ? g.M : S.Mmax;
     NZ += c->nz;
     MT += c->ndir;
@@ -232,6 +235,8 @@ Batch batch_view(const emu_box* b) {
   B.NT = b->S.NT;
   B.T = b->S.T;
   B.U = b->S.U;
+  B.U32 = b->S.U32;
+  B.nw32 = (int)(b->S.U32 < nw ? b->S.U32 : nw);
   B.Ptot = b->S.Ptot;
   return B;
 }
@@ -426,12 +431,34 @@ int launch_stage(emu_box* b, int s, int dry) {
   before_launch(b, CLS_RK);
   by_order(b->S.order, [&](auto O) {
     constexpr int R = decltype(O)::value;
-    if (b->pot)
-      k_rk_stage<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->W, b->dirtab, srow,
-                                                                       b->A, s, dry);
-    else
-      k_rk_stage<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->W, b->dirtab, srow,
-                                                                        b->A, s, dry);
+    // 32 cells per warp, no halo lanes, when every warp walks at least 8 units (the
+    // tile ends at ring and range boundaries are computed directly); otherwise
+    // the halo-lane kernel, which gives bitwise the same results
+    const Batch Bv = batch_view(b);
+    if constexpr (Sten<R>::H == 1) {
+      if (Bv.U32 < 8 * (int64_t)Bv.nw32) {
+        if (b->pot)
+          k_rk_stage<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(Bv, b->pt, b->W, b->dirtab, srow, b->A, s,
+                                                                           dry);
+        else
+          k_rk_stage<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(Bv, b->pt, b->W, b->dirtab, srow, b->A, s,
+                                                                            dry);
+        return 0;
+      }
+      if (b->pot)
+        k_rk_stage32<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->W, b->dirtab,
+                                                                           srow, b->A, s, dry);
+      else
+        k_rk_stage32<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->W, b->dirtab,
+                                                                            srow, b->A, s, dry);
+    } else {
+      if (b->pot)
+        k_rk_stage<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->W, b->dirtab,
+                                                                         srow, b->A, s, dry);
+      else
+        k_rk_stage<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->W, b->dirtab,
+                                                                          srow, b->A, s, dry);
+    }
     return 0;
   });
   return after_launch(b, "RK stage kernel");
@@ -1196,6 +1223,8 @@ extern "C" int emu_deposit_static(const emu_config* cfg, const double* z, const 
   B.T = S.T;
   B.U = S.U;
   B.Ptot = S.Ptot;
+  B.U32 = 0;
+  B.nw32 = 0;
   Parts pt{const_cast<double*>(z), const_cast<double*>(ox), const_cast<double*>(oy), const_cast<double*>(oz),
            const_cast<double*>(N), const_cast<double*>(Nbar), const_cast<double*>(rho),
            const_cast<double*>(rhobar), nullptr, nullptr};

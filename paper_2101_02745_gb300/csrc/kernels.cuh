@@ -67,8 +67,8 @@ struct Sten {
 // One box of a batch (device copy lives in the workspace).
 struct BoxGeo {
   int nz, M, ntiles, use_dirs;
-  int coff, toff, doff, pad;
-  int64_t P, poff, uoff;
+  int coff, toff, doff, ntiles32;  // ntiles32: 32-cell tiles of the RK stage (shape orders 0-2)
+  int64_t P, poff, uoff, uoff32;   // uoff32: first 32-cell unit of the box
   double Lz, dz, inv_dz, nz_d, dV, c_light;
   double kappa_dV;   // kappa / dV: scale of the grid potential
   double inv_dV;     // 1 / dV: scale of the moments
@@ -89,6 +89,8 @@ struct Batch {
   int NZ, MT, NT;      // total cells, directions, tiles
   int T;               // cells per tile (the shape order's Sten<>::T)
   int64_t U, Ptot;     // total units, particles
+  int64_t U32;         // total 32-cell units of the RK stage (shape orders 0-2)
+  int nw32;            // warps that split them
 };
 
 struct Parts {
@@ -106,6 +108,9 @@ __device__ __forceinline__ int64_t unit_begin(int64_t w, const Batch& B) {
   return w >= B.nw ? B.U : w * B.U / B.nw;
 }
 __device__ __forceinline__ int64_t warp_of_unit(int64_t x, const Batch& B) { return ((x + 1) * B.nw - 1) / B.U; }
+__device__ __forceinline__ int64_t unit32_begin(int64_t w, const Batch& B) {
+  return w >= B.nw32 ? B.U32 : w * B.U32 / B.nw32;
+}
 
 // Index of the box containing unit u / cell c / particle p / direction d
 // (binary search over the boxes' offsets; all arguments are warp-uniform in
@@ -115,6 +120,14 @@ __device__ __forceinline__ int box_of_unit(const Batch& B, int64_t u) {
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (B.box[mid].uoff <= u) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ int box_of_unit32(const Batch& B, int64_t u) {
+  int lo = 0, hi = B.nbox - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (B.box[mid].uoff32 <= u) lo = mid; else hi = mid - 1;
   }
   return lo;
 }
@@ -539,6 +552,86 @@ k_interpolate(Batch B, const double* __restrict__ z, const double* __restrict__ 
   if (bad) atomicOr(err, ERR_LATTICE);
 }
 
+// The RK4 update (Sec. 2.3) of particle p of box g at stage s, given its
+// interpolated self-interaction Hamiltonian Hm (Eq. 6, Eq. 2) and its
+// neutrino source matrix r (already loaded): K = -i[H, rho], Kbar =
+// -i[Hbar, rhobar] (Eq. 4) with Hbar = -H^* (plus the vacuum and matter terms
+// with POT), then the accumulator and next stage state (stage 4: the new
+// state and position).  vz points at the particle's v_z in the direction table.
+template <bool POT>
+__device__ __forceinline__ void rk_particle(const BoxGeo& g, const Parts& pt, const double* __restrict__ src_b,
+                                            int64_t P, int64_t p, int s, int dry, double bdt, double cdt, double dtb,
+                                            const double* __restrict__ vz, double (&Hm)[9], const double (&r)[9]) {
+  const double bdt2 = 2.0 * bdt, cdt2 = 2.0 * cdt;   // diagonal K are returned halved
+  // neutrinos: H;  antineutrinos: Hbar = -H^*  (diagonal differences and real parts flip sign)
+  double Hb[9];
+  if (POT) {
+    const double* vn = g.vnu;
+    const double* vb = g.vnubar;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const bool im = (k == 4 || k == 6 || k == 8);
+      Hb[k] = (im ? Hm[k] : -Hm[k]) + __ldg(vb + k);
+      Hm[k] += __ldg(vn + k);
+    }
+  }
+  const double d12 = Hm[0] - Hm[1], d13 = Hm[0] - Hm[2], d23 = Hm[1] - Hm[2];
+#pragma unroll
+  for (int which = 0; which < 2; ++which) {
+    double* __restrict__ yv = which ? pt.rhobar : pt.rho;
+    double* __restrict__ av = pt.acc + which * 9 * P;
+    double* __restrict__ sv = pt.stage + which * 9 * P;
+    // all loads of this matrix before any store (the arrays do not alias)
+    double a[9], y[9], rb[9];
+    if (which == 1) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) rb[k] = src_b[k * P + p];
+    }
+    if (s >= 2) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) a[k] = av[k * P + p];
+    }
+    if (s == 2 || s == 3) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) y[k] = yv[k * P + p];
+    }
+    const double* rr = which ? rb : r;
+    double kd[3], ko[6];
+    if (which == 0) commutator(d12, d13, d23, Hm[3], Hm[4], Hm[5], Hm[6], Hm[7], Hm[8], rr, kd, ko);
+    else if (POT) commutator(Hb[0] - Hb[1], Hb[0] - Hb[2], Hb[1] - Hb[2], Hb[3], Hb[4], Hb[5], Hb[6], Hb[7], Hb[8],
+                             rr, kd, ko);
+    else commutator(-d12, -d13, -d23, -Hm[3], Hm[4], -Hm[5], Hm[6], -Hm[7], Hm[8], rr, kd, ko);
+    if (s == 1) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { av[k * P + p] = fma(bdt2, kd[k], rr[k]); sv[k * P + p] = fma(cdt2, kd[k], rr[k]); }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        av[(k + 3) * P + p] = fma(bdt, ko[k], rr[k + 3]);
+        sv[(k + 3) * P + p] = fma(cdt, ko[k], rr[k + 3]);
+      }
+    } else if (s < 4) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { av[k * P + p] = fma(bdt2, kd[k], a[k]); sv[k * P + p] = fma(cdt2, kd[k], y[k]); }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        av[(k + 3) * P + p] = fma(bdt, ko[k], a[k + 3]);
+        sv[(k + 3) * P + p] = fma(cdt, ko[k], y[k + 3]);
+      }
+    } else {
+      double* __restrict__ dst = dry ? sv : yv;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) dst[k * P + p] = fma(bdt2, kd[k], a[k]);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) dst[(k + 3) * P + p] = fma(bdt, ko[k], a[k + 3]);
+    }
+  }
+  if (s == 4) {
+    const double zn = wrap_z(fma(dtb, __ldg(vz), pt.z[p]), g.Lz);
+    if (dry) pt.stage[p] = zn;  // (only to keep the work of the real stage)
+    else pt.z[p] = zn;
+  }
+}
+
 // One RK4 stage s (1..4) after the deposit of the stage state: interpolate
 // (Eq. 6), H and Hbar = -H^* (Eq. 2, Sec. 2.1), K = -i[H, rho] and
 // Kbar = -i[Hbar, rhobar] (Eq. 4), then the classic RK4 update (Sec. 2.3):
@@ -601,7 +694,6 @@ k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __rest
         }
       }
     }
-    const double bdt2 = 2.0 * bdt, cdt2 = 2.0 * cdt;   // diagonal K are returned halved
     const int craw = tile * T - H + lane, j = wrapc(craw, nz);
     const bool active = lane >= H && lane < H + T && craw < nz;
     const int gd = g.doff + d;
@@ -626,73 +718,160 @@ k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __rest
       Hm[k] = gather<ORDER>(wt, G);
     }
     if (!active) continue;
-    // neutrinos: H;  antineutrinos: Hbar = -H^*  (diagonal differences and real parts flip sign)
-    double Hb[9];
-    if (POT) {
-      const double* vn = g.vnu;
-      const double* vb = g.vnubar;
+    rk_particle<POT>(g, pt, src_b, P, p, s, dry, bdt, cdt, B.dt[b], dirtab + 3 * MT + gd, Hm, r);
+  }
+}
+
+// The RK stage with 32 cells per warp (shape orders 0-2, stencil reach one
+// cell): the same arithmetic as k_rk_stage, without its two halo lanes.  Units
+// are (32-cell tile, direction), direction-major, split evenly over the warps.
+// A warp writes G = A0 - Omega . A of a unit's cells into shared memory and
+// finishes that unit one iteration later, when the next tile's first cell is
+// known: the stencil neighbours of its end cells come from the adjacent tiles
+// of the same ring when the warp handles them in order, and are computed
+// directly (one cell, by the whole warp) at ring and range boundaries.
+__device__ __forceinline__ void ring_cell_G(const double* __restrict__ A, int NZ, int coff, int cell, double ox,
+                                            double oy, double oz, double (&G)[9]) {
+  const double* Aj = A + coff + cell;
 #pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        const bool im = (k == 4 || k == 6 || k == 8);
-        Hb[k] = (im ? Hm[k] : -Hm[k]) + __ldg(vb + k);
-        Hm[k] += __ldg(vn + k);
+  for (int k = 0; k < 9; ++k)
+    G[k] = fma(-oz, __ldg(Aj + (int64_t)(27 + k) * NZ),
+               fma(-oy, __ldg(Aj + (int64_t)(18 + k) * NZ), fma(-ox, __ldg(Aj + (int64_t)(9 + k) * NZ),
+                                                                __ldg(Aj + (int64_t)k * NZ))));
+}
+
+template <bool POT, int ORDER>
+__global__ void __launch_bounds__(kThreads, 2)
+k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
+             const int* __restrict__ shift, const double* __restrict__ A, int s, int dry) {
+  static_assert(Sten<ORDER>::H == 1, "one neighbour on each side");
+  __shared__ double gsm[kWarps][2][9][kLanes];   // G of the last two units, per warp
+  __shared__ double edge[kWarps][2][9];          // left / right neighbour of the unit being finished
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t w = (int64_t)blockIdx.x * kWarps + wib;
+  const int64_t u0 = unit32_begin(w, B), u1 = unit32_begin(w + 1, B);
+  if (u0 >= u1) return;
+  const int64_t P = B.Ptot;
+  const int MT = B.MT, NZ = B.NZ;
+  const double* src_r = (s == 1) ? pt.rho : pt.stage;
+  const double* src_b = (s == 1) ? pt.rhobar : pt.stage + 9 * P;
+  constexpr int NWS = Sten<ORDER>::NWS;
+  const int nsrc = 18, ny = (s == 2 || s == 3) ? 18 : 0, nacc = (s >= 2) ? 18 : 0;
+  const int narr = nsrc + ny + nacc + NWS + (s == 4 ? 1 : 0);
+  // the unit being finished (previous iteration's)
+  int pb = -1, pd = 0, pt_ = 0, pn = 0, pgd = 0;
+  int bcur = -1;                    // box of the RK coefficients below (divisions once per box)
+  double dtb = 0.0, bdt = 0.0, cdt = 0.0;
+  int b = box_of_unit32(B, u0);
+  for (int64_t u = u0; u <= u1; ++u) {
+    const int slot = (int)((u - u0) & 1);
+    int cb = -1, cd = 0, ct = 0, cn = 0, cgd = 0;   // this iteration's unit (none at u == u1)
+    if (u < u1) {
+      while (u >= B.box[b].uoff32 + (int64_t)B.box[b].ntiles32 * B.box[b].M) ++b;
+      const BoxGeo& g = B.box[b];
+      const int lu = (int)(u - g.uoff32);
+      cb = b;
+      cd = lu / g.ntiles32;
+      ct = lu - cd * g.ntiles32;
+      cn = min(kLanes, g.nz - ct * kLanes);
+      cgd = g.doff + cd;
+      // prefetch this unit's particle data into L2 (it is finished next iteration)
+      const int i0 = ct * kLanes - __ldg(shift + cgd);
+      if (i0 >= 0 && i0 + cn <= g.nz) {
+        const int64_t base = g.poff + (int64_t)cd * g.nz + i0;
+        for (int a = lane; a < narr; a += kLanes) {
+          const double* arr;
+          if (a < nsrc) arr = (a < 9 ? src_r + (int64_t)a * P : src_b + (int64_t)(a - 9) * P);
+          else if (a < nsrc + ny) arr = (a - nsrc < 9 ? pt.rho + (int64_t)(a - nsrc) * P
+                                                      : pt.rhobar + (int64_t)(a - nsrc - 9) * P);
+          else if (a < nsrc + ny + nacc) arr = pt.acc + (int64_t)(a - nsrc - ny) * P;
+          else if (a < nsrc + ny + nacc + NWS) arr = W + (int64_t)(a - nsrc - ny - nacc) * P;
+          else arr = pt.z;
+          prefetch_l2(arr, base, cn);
+        }
+      }
+      // G of this unit's cells
+      if (lane < cn) {
+        double G[9];
+        ring_cell_G(A, NZ, g.coff, ct * kLanes + lane, __ldg(dirtab + cgd), __ldg(dirtab + MT + cgd),
+                    __ldg(dirtab + 2 * MT + cgd), G);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) gsm[wib][slot][k][lane] = G[k];
       }
     }
-    const double d12 = Hm[0] - Hm[1], d13 = Hm[0] - Hm[2], d23 = Hm[1] - Hm[2];
+    // does this unit continue the ring of the one being finished?
+    const bool next_in_ring = pb >= 0 && cb == pb && cd == pd && ct == pt_ + 1;
+    if (pb >= 0) {
+      const BoxGeo& g = B.box[pb];
+      const double ox = __ldg(dirtab + pgd), oy = __ldg(dirtab + MT + pgd), oz = __ldg(dirtab + 2 * MT + pgd);
+      // right neighbour of the finished unit's last cell
+      if (!next_in_ring) {
+        double G[9];
+        const int cell = pt_ * kLanes + pn;                 // one past its last cell, on the ring
+        ring_cell_G(A, NZ, g.coff, cell >= g.nz ? cell - g.nz : cell, ox, oy, oz, G);
+        if (lane == 0) {
 #pragma unroll
-    for (int which = 0; which < 2; ++which) {
-      double* __restrict__ yv = which ? pt.rhobar : pt.rho;
-      double* __restrict__ av = pt.acc + which * 9 * P;
-      double* __restrict__ sv = pt.stage + which * 9 * P;
-      // all loads of this matrix before any store (the arrays do not alias)
-      double a[9], y[9], rb[9];
-      if (which == 1) {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) rb[k] = src_b[k * P + p];
-      }
-      if (s >= 2) {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) a[k] = av[k * P + p];
-      }
-      if (s == 2 || s == 3) {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) y[k] = yv[k * P + p];
-      }
-      const double* rr = which ? rb : r;
-      double kd[3], ko[6];
-      if (which == 0) commutator(d12, d13, d23, Hm[3], Hm[4], Hm[5], Hm[6], Hm[7], Hm[8], rr, kd, ko);
-      else if (POT) commutator(Hb[0] - Hb[1], Hb[0] - Hb[2], Hb[1] - Hb[2], Hb[3], Hb[4], Hb[5], Hb[6], Hb[7], Hb[8],
-                               rr, kd, ko);
-      else commutator(-d12, -d13, -d23, -Hm[3], Hm[4], -Hm[5], Hm[6], -Hm[7], Hm[8], rr, kd, ko);
-      if (s == 1) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) { av[k * P + p] = fma(bdt2, kd[k], rr[k]); sv[k * P + p] = fma(cdt2, kd[k], rr[k]); }
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          av[(k + 3) * P + p] = fma(bdt, ko[k], rr[k + 3]);
-          sv[(k + 3) * P + p] = fma(cdt, ko[k], rr[k + 3]);
+          for (int k = 0; k < 9; ++k) edge[wib][1][k] = G[k];
         }
-      } else if (s < 4) {
+      }
+      __syncwarp();
+      if (next_in_ring && lane == 0) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) { av[k * P + p] = fma(bdt2, kd[k], a[k]); sv[k * P + p] = fma(cdt2, kd[k], y[k]); }
+        for (int k = 0; k < 9; ++k) edge[wib][1][k] = gsm[wib][slot][k][0];
+      }
+      __syncwarp();
+      // finish the previous unit: interpolation, commutators, RK update
+      const int psl = slot ^ 1;
+      if (lane < pn) {
+        const int64_t p = g.poff + (int64_t)pd * g.nz + wrapc(pt_ * kLanes + lane - __ldg(shift + pgd), g.nz);
+        double wt[Sten<ORDER>::NW];
+        double r[9];
+        load_weights<ORDER>(W, P, p, wt);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          av[(k + 3) * P + p] = fma(bdt, ko[k], a[k + 3]);
-          sv[(k + 3) * P + p] = fma(cdt, ko[k], y[k + 3]);
+        for (int k = 0; k < 9; ++k) r[k] = src_r[k * P + p];
+        double Hm[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          const double G = gsm[wib][psl][k][lane];
+          if (ORDER == 0) {
+            Hm[k] = G;
+          } else {
+            const double gl = lane == 0 ? edge[wib][0][k] : gsm[wib][psl][k][lane - 1];
+            const double gr = lane == pn - 1 ? edge[wib][1][k] : gsm[wib][psl][k][lane + 1];
+            Hm[k] = fma(wt[0], gl, fma(wt[1], G, wt[2] * gr));
+          }
+        }
+        if (pb != bcur) {
+          bcur = pb;
+          dtb = B.dt[pb];
+          bdt = (s == 1 || s == 4) ? dtb / 6.0 : dtb / 3.0;   // weight of K in acc
+          cdt = (s == 3) ? dtb : 0.5 * dtb;                   // offset of the next stage
+        }
+        rk_particle<POT>(g, pt, src_b, P, p, s, dry, bdt, cdt, dtb, dirtab + 3 * MT + pgd, Hm, r);
+      }
+      __syncwarp();
+    }
+    // left neighbour of this unit's first cell, for when it is finished
+    if (cb >= 0) {
+      if (next_in_ring) {
+        if (lane == 0) {
+#pragma unroll
+          for (int k = 0; k < 9; ++k) edge[wib][0][k] = gsm[wib][slot ^ 1][k][kLanes - 1];
         }
       } else {
-        double* __restrict__ dst = dry ? sv : yv;
+        const BoxGeo& g = B.box[cb];
+        double G[9];
+        const int cell = ct * kLanes - 1;                    // one before its first cell, on the ring
+        ring_cell_G(A, NZ, g.coff, cell < 0 ? cell + g.nz : cell, __ldg(dirtab + cgd), __ldg(dirtab + MT + cgd),
+                    __ldg(dirtab + 2 * MT + cgd), G);
+        if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) dst[k * P + p] = fma(bdt2, kd[k], a[k]);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) dst[(k + 3) * P + p] = fma(bdt, ko[k], a[k + 3]);
+          for (int k = 0; k < 9; ++k) edge[wib][0][k] = G[k];
+        }
       }
+      __syncwarp();
     }
-    if (s == 4) {
-      const double zn = wrap_z(fma(B.dt[b], __ldg(dirtab + 3 * MT + gd), pt.z[p]), g.Lz);
-      if (dry) pt.stage[p] = zn;  // (only to keep the work of the real stage)
-      else pt.z[p] = zn;
-    }
+    pb = cb; pd = cd; pt_ = ct; pn = cn; pgd = cgd;
   }
 }
 
