@@ -60,7 +60,7 @@ BYTES_DEPOSIT = 24 * 8
 # DRAM read + write per particle of one launch, from an ncu capture of the current
 # kernels (2048 cells x 1000 directions, 2.048M particles, stages 1-4 averaged):
 # scaled by the particles of the timed launch.
-TRAFFIC_RK = None    # the 32-cell RK stage: counters not taken yet
+TRAFFIC_RK = 711.2   # k_rk_stage32 (32 cells per warp)
 TRAFFIC_DEPOSIT = 297.9
 
 
