@@ -240,6 +240,15 @@ int emu_batch_diagnostics(emu_box* box, double* out, int on_host);
  * reproducible for a fixed choice.  Synchronises. */
 int emu_autotune(emu_box* box, int trial_steps, int32_t* choice_out, double* ms_out);
 
+/* Set the grid of the step kernels to `blocks` blocks of 256 threads (1..608;
+ * the default is 304, two per SM; emu_autotune picks among 152, 304 and 608),
+ * for callers that share the GPU with other work.  The blocks' warps split the
+ * work, so the choice changes the deposit's summation order (results stay
+ * bitwise reproducible for a fixed choice) and, for shape orders 0-2, whether
+ * the RK stage runs with 32 cells per warp (every warp walking at least 8
+ * units) or the halo-lane form (the same results).  Errors: EMU_EINVAL. */
+int emu_set_grid(emu_box* box, int32_t blocks);
+
 /* Vacuum and matter terms of Eq. 2 (Sec. 2.1): masses m_i c^2 [eV], the mixing
  * angles theta12, theta13, theta23 and phase delta_cp [rad] of the standard
  * three-angle mixing matrix U (the paper does not give a parametrisation),

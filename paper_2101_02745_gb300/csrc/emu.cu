@@ -834,6 +834,15 @@ int emu_diagnostics(emu_box* b, double* out, int on_host) {
   return emu_batch_diagnostics(b, out, on_host);
 }
 
+int emu_set_grid(emu_box* b, int32_t blocks) {
+  if (int rc = check_bound(b)) return rc;
+  if (blocks < 1 || blocks > kMaxBlocks) return fail(b, EMU_EINVAL, "blocks must be in 1..%d", kMaxBlocks);
+  if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
+  b->blocks = blocks;
+  invalidate_graph(b);
+  return EMU_OK;
+}
+
 int emu_autotune(emu_box* b, int trial_steps, int32_t* choice_out, double* ms_out) {
   if (int rc = check_bound(b)) return rc;
   if (trial_steps < 1) return fail(b, EMU_EINVAL, "trial_steps must be >= 1");

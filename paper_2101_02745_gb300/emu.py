@@ -106,6 +106,7 @@ def load(build_if_missing: bool = False):
         "emu_batch_step": (i32, [vp, i64]),
         "emu_batch_diagnostics": (i32, [vp, vp, i32]),
         "emu_autotune": (i32, [vp, i32, vp, vp]),
+        "emu_set_grid": (i32, [vp, ctypes.c_int32]),
         "emu_set_oscillation": (i32, [vp, ctypes.c_int32, ctypes.POINTER(emu_oscillation)]),
         "emu_adjoint_workspace_bytes": (i64, [cfgp]),
         "emu_batch_adjoint_workspace_bytes": (i64, [cfgp, ctypes.c_int32]),
@@ -306,6 +307,10 @@ def emu_autotune(box, trial_steps: int):
     ms = np.zeros(3)
     _check(box, load().emu_autotune(box, int(trial_steps), ctypes.byref(choice), _host_ptr(ms)))
     return int(choice.value), ms
+
+
+def emu_set_grid(box, blocks: int):
+    _check(box, load().emu_set_grid(box, int(blocks)))
 
 
 def make_oscillation(d: dict) -> emu_oscillation:
@@ -528,6 +533,9 @@ class Box:
     @_ordered
     def autotune(self, trial_steps=2):
         return emu_autotune(self.box, trial_steps)
+
+    def set_grid(self, blocks: int):
+        emu_set_grid(self.box, blocks)
 
     @_ordered
     def set_oscillation(self, osc, box=-1):
