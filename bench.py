@@ -458,7 +458,7 @@ def measure_sweep(args, dist, device, rank, world, steps):
             "vs_plain": single_ms / batched_ms}
 
 
-def measure_adjoint(dist, device, world, reps=1, nz=0, ndir=0, steps=0):
+def measure_adjoint(dist, device, world, reps=1, nz=0, ndir=0, steps=0, record=None):
     """Gradient of log <|n_emu|> after the growth-phase run (256 cells x 96
     directions, 400 steps, checkpoints every 20 steps) through the adjoint's
     autograd Function, against the plain forward steps of the same run.
@@ -476,7 +476,8 @@ def measure_adjoint(dist, device, world, reps=1, nz=0, ndir=0, steps=0):
         wl = W.adjoint_box(nz=nz or wl.nz, ndir=ndir or wl.ndir, steps=steps or wl.steps)
     box = E.Box.from_workload(wl, device=device)
     dt = box.timestep()
-    sim = Simulation(box, wl.steps, dt, every=wl.meta["checkpoint_every"], alpha=wl.alpha, seed=wl.seed)
+    sim = Simulation(box, wl.steps, dt, every=wl.meta["checkpoint_every"], alpha=wl.alpha, seed=wl.seed,
+                     record=record)
     stream = box.stream
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
     best = None
@@ -505,7 +506,7 @@ def measure_adjoint(dist, device, world, reps=1, nz=0, ndir=0, steps=0):
             "value": world * upd / ((fwd + bwd) * 1e-3), "unit": "differentiated particle-updates/s",
             "plain_value": world * upd / (plain * 1e-3),
             "plain_ms": plain, "forward_ms": fwd, "backward_ms": bwd,
-            "backward_over_forward": bwd / fwd, "vs_plain": plain / (fwd + bwd),
+            "backward_over_forward": bwd / fwd, "vs_plain": plain / (fwd + bwd), "recorded": sim.use_record(),
             "launches_per_gradient": launches}
 
 
@@ -522,7 +523,9 @@ def run_adjoint(args, rank, world, local_rank):
     torch.cuda.set_device(device)
     barrier(dist, device)
     clocks = ClockSampler(device.index).start()
-    a = measure_adjoint(dist, device, world, reps=args.steps, nz=args.nz, ndir=args.ndir, steps=args.adj_steps)
+    record = {"auto": None, "on": True, "off": False}[args.adj_record]
+    a = measure_adjoint(dist, device, world, reps=args.steps, nz=args.nz, ndir=args.ndir, steps=args.adj_steps,
+                        record=record)
     clk = clocks.stop()
     if rank == 0:
         line = {"metric": METRIC, "value": a["value"], "unit": a["unit"], "n_gpus": world, "steps": args.steps,
@@ -530,7 +533,7 @@ def run_adjoint(args, rank, world, local_rank):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
                 "config": {"workload": a["workload"], "particles_per_gpu": a["particles"], "steps": a["steps"],
-                           "checkpoint_every": a["checkpoint_every"],
+                           "checkpoint_every": a["checkpoint_every"], "recorded": a["recorded"],
                            "l2": ("particle state %.2f GB %s L2 (129 MB)"
                                   % (a["particles"] * 480 / 1e9,
                                      "above" if a["particles"] * 480 > 129e6 else "below"))},
@@ -588,6 +591,8 @@ def main(argv=None):
     ap.add_argument("--ref-cells", type=int, default=256, help="cells per oracle step in --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--adj-steps", type=int, default=0, help="steps of the adjoint workload (default 400)")
+    ap.add_argument("--adj-record", choices=["auto", "on", "off"], default="auto",
+                    help="adjoint backward with per-step records (auto: large boxes)")
     ap.add_argument("--shape-order", type=int, default=2, choices=[0, 1, 2, 3], help="particle shape (Sec. 2.2.1)")
     ap.add_argument("--osc", action="store_true", help="add the vacuum and matter terms of Eq. 2")
     ap.add_argument("--no-extras", action="store_true",

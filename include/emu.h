@@ -321,6 +321,21 @@ int emu_adjoint_seed(emu_box* box, const double* dmom, double* lambda, double* g
 int emu_adjoint_step(emu_box* box, double dt, double* lambda, double* gN, double* gNbar, void* adj_ws,
                      int64_t adj_ws_bytes);
 
+/* Recorded form of the adjoint step, for boxes where memory is cheaper than
+ * recomputation.  emu_adjoint_record_step takes one forward step exactly as
+ * emu_step (the state advances) and writes its record: the stage states y2,
+ * y3, y4, and the shape weights and grid potential of the four stages
+ * (emu_batch_adjoint_record_bytes per step).  emu_adjoint_step_recorded then
+ * runs that step's adjoint (as emu_adjoint_step, same results) from the
+ * record, with no recomputed stages; the box must hold the state at the
+ * START of the step again, and adj_ws needs 54 doubles per particle.  dt as
+ * in emu_adjoint_step.  Buffers: device, 256-byte aligned.  Errors: as
+ * emu_adjoint_step. */
+int64_t emu_batch_adjoint_record_bytes(const emu_config* cfgs, int32_t nbox);
+int emu_adjoint_record_step(emu_box* box, double dt, void* rec, int64_t rec_bytes);
+int emu_adjoint_step_recorded(emu_box* box, double dt, const void* rec, double* lambda, double* gN, double* gNbar,
+                              void* adj_ws, int64_t adj_ws_bytes);
+
 /* Chain rule through Eq. 8 (N_p = (n_c + 3 f_c . Omega_p) dV / M, c the cell
  * a particle starts on at emu_init_particles): out[8][total cells] =
  * dL/dn_nu, dL/dn_nubar, dL/df_nu (x, y, z), dL/df_nubar (x, y, z) per cell.

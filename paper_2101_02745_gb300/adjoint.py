@@ -16,9 +16,15 @@ Forward keeps a checkpoint of the evolving state (z, rho, rhobar) every
 sim.every steps.  Backward seeds the adjoint from dL/d(moments), then walks
 the segments last to first: it restores a segment's checkpoint, recomputes
 the segment's step-start states forward, and runs one adjoint step per step
-backward (emu_adjoint_step).  The accumulated dL/dN, dL/dNbar go through
-Eq. 8 to the species inputs (emu_weight_gradient).  Every arithmetic step
-runs in the CUDA library; this module only marshals buffers.
+backward (emu_adjoint_step, which recomputes the step's forward stages).
+With sim.record the recomputation writes each step's record (stage states,
+weights, potentials; emu_adjoint_record_step) and the adjoint steps read it
+(emu_adjoint_step_recorded), so the forward stages run once instead of
+twice; the default turns it on for boxes of 2^18 particles and more when a
+segment's records fit in half the free device memory.  The accumulated
+dL/dN, dL/dNbar go through Eq. 8 to the species inputs
+(emu_weight_gradient).  Every arithmetic step runs in the CUDA library; this
+module only marshals buffers.
 """
 from __future__ import annotations
 
@@ -41,6 +47,9 @@ class Simulation:
     alpha: object = 1e-6
     seed: object = 0
     dirs: np.ndarray | None = None
+    record: bool | None = None
+
+    RECORD_MIN_PARTICLES = 1 << 18
 
     @property
     def batched(self) -> bool:
@@ -50,6 +59,16 @@ class Simulation:
         """The dt argument of the step calls: the step size, or 0 for a batch
         (each box's own size, set on the box)."""
         return 0.0 if self.batched else float(self.dt)
+
+    def use_record(self) -> bool:
+        """Whether backward keeps per-step records (see the module notes)."""
+        if self.record is not None:
+            return bool(self.record)
+        if self.box.P < self.RECORD_MIN_PARTICLES:
+            return False
+        import torch
+        free, _ = torch.cuda.mem_get_info(self.box.device)
+        return min(self.every, max(self.nsteps, 1)) * self.box.record_stride() <= free // 2
 
 
 def _host(t: torch.Tensor, shape) -> np.ndarray:
@@ -103,17 +122,27 @@ class Evolve(torch.autograd.Function):
         box.load_state(ctx.final)
         box.adjoint_seed(dmom, lam, gN, gNbar)
         nseg = len(ctx.checkpoints)
+        dt = sim.step_dt()
+        rec = box.record_buffer(min(sim.every, sim.nsteps)) if nseg and sim.use_record() else None
         for seg in range(nseg - 1, -1, -1):
             start = seg * sim.every
             k = min(sim.every, sim.nsteps - start)
             box.load_state(ctx.checkpoints[seg])
             starts = [box.save_state()]
-            for _ in range(k - 1):
-                _steps(sim, 1)
+            for j in range(k - 1):
+                if rec is None:
+                    _steps(sim, 1)
+                else:
+                    box.adjoint_record_step(dt, rec, j)
                 starts.append(box.save_state())
-            for st in reversed(starts):
-                box.load_state(st)
-                box.adjoint_step(sim.step_dt(), lam, gN, gNbar)
+            if rec is not None:
+                box.adjoint_record_step(dt, rec, k - 1)
+            for j in range(k - 1, -1, -1):
+                box.load_state(starts[j])
+                if rec is None:
+                    box.adjoint_step(dt, lam, gN, gNbar)
+                else:
+                    box.adjoint_step_recorded(dt, rec, j, lam, gN, gNbar)
         box.load_state(ctx.final)
         g = box.weight_gradient(gN, gNbar).to(ctx.dev)
         ctx.lambda0 = lam  # dL/d(initial rho, rhobar), kept for inspection

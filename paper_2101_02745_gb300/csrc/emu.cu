@@ -422,12 +422,19 @@ int launch_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, c
 
 // One RK stage of every box with its device step size (the shift rows of the
 // step must have been computed by stage 1's caller).
+int launch_rk(emu_box* b, int s, const int* srow, int dry);
+
 int launch_stage(emu_box* b, int s, int dry) {
   const size_t P = (size_t)b->S.Ptot;
   const double* rnu = (s == 1) ? b->pt.rho : b->pt.stage;
   const double* rnb = (s == 1) ? b->pt.rhobar : b->pt.stage + 9 * P;
   const int* srow = b->shift + (size_t)(s - 1) * b->S.MT;
   if (int rc = launch_deposit(b, 0, rnu, rnb, srow, kStageFrac[s - 1], b->A)) return rc;
+  return launch_rk(b, s, srow, dry);
+}
+
+// The RK-stage kernel of stage s from the deposit in b->A and b->W.
+int launch_rk(emu_box* b, int s, const int* srow, int dry) {
   before_launch(b, CLS_RK);
   by_order(b->S.order, [&](auto O) {
     constexpr int R = decltype(O)::value;
@@ -951,6 +958,94 @@ size_t adjoint_doubles(const Shape& S) {
   return (size_t)90 * S.Ptot + 3 * ((size_t)kept_weights(S.order) * S.Ptot + (size_t)kNA * S.NZ);
 }
 
+// Record of one step for the adjoint: the stage states y2, y3, y4 ([3][18][P]),
+// the shape weights of stages 1-4 ([4][NWS][P]) and their grid potentials
+// ([4][36][NZ]).
+size_t record_doubles(const Shape& S) {
+  return (size_t)54 * S.Ptot + 4 * ((size_t)kept_weights(S.order) * S.Ptot + (size_t)kNA * S.NZ);
+}
+
+// One forward step (as launch_step) that also writes its record.
+int record_step(emu_box* b, double* rec) {
+  const size_t P = (size_t)b->S.Ptot;
+  const size_t nws = (size_t)kept_weights(b->S.order) * P, na = (size_t)kNA * b->S.NZ;
+  double* Y = rec;                 // y2, y3, y4
+  double* Wr = Y + 54 * P;         // weights of stages 1..4
+  double* Ar = Wr + 4 * nws;       // potentials of stages 1..4
+  if (int rc = launch_shifts(b, kStageFrac, 4)) return rc;
+  for (int s = 1; s <= 4; ++s) {
+    const double* rnu = (s == 1) ? b->pt.rho : b->pt.stage;
+    const double* rnb = (s == 1) ? b->pt.rhobar : b->pt.stage + 9 * P;
+    const int* srow = b->shift + (size_t)(s - 1) * b->S.MT;
+    if (int rc = launch_deposit(b, 0, rnu, rnb, srow, kStageFrac[s - 1], b->A)) return rc;
+    if (nws)
+      if (int rc = cuda_check(b, cudaMemcpyAsync(Wr + (s - 1) * nws, b->W, sizeof(double) * nws,
+                                                 cudaMemcpyDeviceToDevice, b->stream), "record weights"))
+        return rc;
+    if (int rc = cuda_check(b, cudaMemcpyAsync(Ar + (s - 1) * na, b->A, sizeof(double) * na,
+                                               cudaMemcpyDeviceToDevice, b->stream), "record potential"))
+      return rc;
+    if (int rc = launch_rk(b, s, srow, 0)) return rc;
+    if (s < 4)
+      if (int rc = cuda_check(b, cudaMemcpyAsync(Y + (s - 1) * 18 * P, b->pt.stage, sizeof(double) * 18 * P,
+                                                 cudaMemcpyDeviceToDevice, b->stream), "record stage state"))
+        return rc;
+  }
+  return EMU_OK;
+}
+
+// The backward stages of one adjoint step from a record (no recomputation).
+int adjoint_recorded_body(emu_box* b, const double* rec, double* lambda, double* gN, double* gNbar, void* adj_ws) {
+  const size_t P = (size_t)b->S.Ptot;
+  const size_t nws = (size_t)kept_weights(b->S.order) * P, na = (size_t)kNA * b->S.NZ;
+  const double* Y = rec;
+  const double* Wr = Y + 54 * P;
+  const double* Ar = Wr + 4 * nws;
+  double* La = (double*)adj_ws;
+  double* Lb = La + 18 * P;
+  double* Lt = Lb + 18 * P;
+  const size_t bytes18 = sizeof(double) * 18 * P;
+  if (int rc = launch_shifts(b, kStageFrac, 4)) return rc;
+  if (int rc = cuda_check(b, cudaMemcpyAsync(Lt, lambda, bytes18, cudaMemcpyDeviceToDevice, b->stream),
+                          "copy adjoint"))
+    return rc;
+  const Batch B = batch_view(b);
+  double* Lnext = nullptr;
+  for (int s = 4; s >= 1; --s) {
+    double* ys = s == 1 ? b->pt.rho : const_cast<double*>(Y + (s - 2) * 18 * P);
+    double* ysb = s == 1 ? b->pt.rhobar : ys + 9 * P;
+    const int* srow = b->shift + (size_t)(s - 1) * b->S.MT;
+    const double* Hs = Ar + (s - 1) * na;
+    const double* Ws = Wr + (s - 1) * nws;
+    Parts ps = b->pt;
+    ps.rho = ys;
+    ps.rhobar = ysb;
+    double* Lcur = (s % 2 == 0) ? La : Lb;
+    before_launch(b, CLS_OTHER);
+    by_order(b->S.order, [&](auto O) {
+      constexpr int R = decltype(O)::value;
+      if (b->pot)
+        k_adj_a<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, Ws, b->dirtab, srow, Hs, lambda,
+                                                                      Lnext, s, Lcur, b->pt.acc);
+      else
+        k_adj_a<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, Ws, b->dirtab, srow, Hs, lambda,
+                                                                       Lnext, s, Lcur, b->pt.acc);
+      return 0;
+    });
+    if (int rc = after_launch(b, "adjoint stage kernel")) return rc;
+    if (int rc = launch_deposit(b, 3, b->pt.acc, nullptr, srow, kStageFrac[s - 1], b->A)) return rc;
+    before_launch(b, CLS_OTHER);
+    by_order(b->S.order, [&](auto O) {
+      k_adj_b<decltype(O)::value><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, Ws, b->dirtab, srow, b->A,
+                                                                              Lcur, Lt, gN, gNbar);
+      return 0;
+    });
+    if (int rc = after_launch(b, "adjoint interpolation kernel")) return rc;
+    Lnext = Lcur;
+  }
+  return cuda_check(b, cudaMemcpyAsync(lambda, Lt, bytes18, cudaMemcpyDeviceToDevice, b->stream), "copy adjoint");
+}
+
 // The launches of one adjoint step (emu_adjoint_step; the step sizes are on the device).
 int adjoint_body(emu_box* b, double* lambda, double* gN, double* gNbar, void* adj_ws) {
   const size_t P = (size_t)b->S.Ptot;
@@ -1083,6 +1178,50 @@ int emu_adjoint_step(emu_box* b, double dt, double* lambda, double* gN, double* 
     std::memcpy(b->adj_key, key, sizeof(key));
   }
   return launch_graph(b, b->adj_graph, b->adj_launches);
+}
+
+int64_t emu_batch_adjoint_record_bytes(const emu_config* cfgs, int32_t nbox) {
+  Shape S;
+  if (make_shape(cfgs, nbox, S)) return EMU_EINVAL;
+  return (int64_t)(sizeof(double) * record_doubles(S));
+}
+
+// Shared checks of the recording calls: step size (dt > 0 single box, 0 =
+// each box's own), a buffer of at least `need` bytes, 256-byte aligned.
+static int record_checks(emu_box* b, double dt, const void* buf, int64_t bytes, size_t need, const char* what) {
+  if (int rc = check_bound(b)) return rc;
+  if (dt != 0.0) {
+    if (b->S.nbox != 1) return fail(b, EMU_EINVAL, "a batch takes dt = 0 (each box's own step size)");
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(b, EMU_EINVAL, "dt must be positive and finite, or 0");
+  } else if (!b->step_valid) {
+    return fail(b, EMU_EINVAL, "dt = 0 needs the boxes' step sizes (emu_batch_set_dt or a time-step call)");
+  }
+  if (!buf) return fail(b, EMU_EINVAL, "%s: NULL pointer", what);
+  if (bytes < (int64_t)need)
+    return fail(b, EMU_EINVAL, "%s too small: %lld < %lld bytes", what, (long long)bytes, (long long)need);
+  if (((uintptr_t)buf) & 255) return fail(b, EMU_EINVAL, "%s must be 256-byte aligned", what);
+  if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
+  return EMU_OK;
+}
+
+int emu_adjoint_record_step(emu_box* b, double dt, void* rec, int64_t rec_bytes) {
+  if (int rc = record_checks(b, dt, rec, rec_bytes, b ? sizeof(double) * record_doubles(b->S) : 0, "record"))
+    return rc;
+  if (int rc = set_dts(b, dt != 0.0 ? &dt : b->step_dt.data())) return rc;
+  b->next_stage = 1;
+  return record_step(b, (double*)rec);
+}
+
+int emu_adjoint_step_recorded(emu_box* b, double dt, const void* rec, double* lambda, double* gN, double* gNbar,
+                              void* adj_ws, int64_t adj_ws_bytes) {
+  if (int rc = record_checks(b, dt, adj_ws, adj_ws_bytes, b ? sizeof(double) * 54 * (size_t)b->S.Ptot : 0,
+                             "adjoint workspace"))
+    return rc;
+  if (!rec || (((uintptr_t)rec) & 255)) return fail(b, EMU_EINVAL, "record: NULL or not 256-byte aligned");
+  if (!lambda || !gN || !gNbar) return fail(b, EMU_EINVAL, "adjoint step: NULL pointer");
+  if (int rc = set_dts(b, dt != 0.0 ? &dt : b->step_dt.data())) return rc;
+  b->next_stage = 1;
+  return adjoint_recorded_body(b, (const double*)rec, lambda, gN, gNbar, adj_ws);
 }
 
 int emu_weight_gradient(emu_box* b, const double* gN, const double* gNbar, double* out, int on_host) {

@@ -112,6 +112,9 @@ def load(build_if_missing: bool = False):
         "emu_batch_adjoint_workspace_bytes": (i64, [cfgp, ctypes.c_int32]),
         "emu_adjoint_seed": (i32, [vp, vp, vp, vp, vp]),
         "emu_adjoint_step": (i32, [vp, dbl, vp, vp, vp, vp, i64]),
+        "emu_batch_adjoint_record_bytes": (i64, [cfgp, ctypes.c_int32]),
+        "emu_adjoint_record_step": (i32, [vp, dbl, vp, i64]),
+        "emu_adjoint_step_recorded": (i32, [vp, dbl, vp, vp, vp, vp, vp, i64]),
         "emu_weight_gradient": (i32, [vp, vp, vp, vp, i32]),
         "emu_last_error": (ctypes.c_char_p, [vp]),
         "emu_destroy": (None, [vp]),
@@ -353,6 +356,22 @@ def emu_adjoint_step(box, dt: float, lam, gN, gNbar, adj_ws, adj_ws_bytes: int):
     _check(box, load().emu_adjoint_step(box, float(dt), lam, gN, gNbar, adj_ws, int(adj_ws_bytes)))
 
 
+def emu_batch_adjoint_record_bytes(cfgs) -> int:
+    arr, ptr = _cfg_array(cfgs)
+    n = load().emu_batch_adjoint_record_bytes(ptr, len(cfgs))
+    if n < 0:
+        raise EmuError(int(n), "invalid configuration")
+    return int(n)
+
+
+def emu_adjoint_record_step(box, dt: float, rec, rec_bytes: int):
+    _check(box, load().emu_adjoint_record_step(box, float(dt), rec, int(rec_bytes)))
+
+
+def emu_adjoint_step_recorded(box, dt: float, rec, lam, gN, gNbar, adj_ws, adj_ws_bytes: int):
+    _check(box, load().emu_adjoint_step_recorded(box, float(dt), rec, lam, gN, gNbar, adj_ws, int(adj_ws_bytes)))
+
+
 def emu_weight_gradient(box, gN, gNbar, out, on_host: int):
     _check(box, load().emu_weight_gradient(box, gN, gNbar, out, on_host))
 
@@ -570,16 +589,46 @@ class Box:
         dmom = dmom.to(dtype=self.torch.float64, device=self.device).contiguous()
         emu_adjoint_seed(self.box, dmom.data_ptr(), lam.data_ptr(), gN.data_ptr(), gNbar.data_ptr())
 
-    @_ordered
-    def adjoint_step(self, dt, lam, gN, gNbar):
-        """One adjoint RK4 step from the step's start state (held by the box);
-        dt = 0: every box's own step size (batches)."""
+    def _adjoint_ws(self):
         if getattr(self, "_adj_ws", None) is None:
             n = emu_batch_adjoint_workspace_bytes(self.cfgs)
             self._adj_raw = self.torch.empty(n + 256, dtype=self.torch.uint8, device=self.device)
             self._adj_ws = ((self._adj_raw.data_ptr() + 255) & ~255, n)
-        ptr, n = self._adj_ws
+        return self._adj_ws
+
+    @_ordered
+    def adjoint_step(self, dt, lam, gN, gNbar):
+        """One adjoint RK4 step from the step's start state (held by the box);
+        dt = 0: every box's own step size (batches)."""
+        ptr, n = self._adjoint_ws()
         emu_adjoint_step(self.box, dt, lam.data_ptr(), gN.data_ptr(), gNbar.data_ptr(), ptr, n)
+
+    def record_stride(self) -> int:
+        """Bytes of one step's adjoint record, rounded up to 256."""
+        return (emu_batch_adjoint_record_bytes(self.cfgs) + 255) & ~255
+
+    def record_buffer(self, nsteps: int):
+        """A device buffer for the records of nsteps steps (256-byte aligned
+        slots); its slot pointers come from record_slot."""
+        stride = self.record_stride()
+        raw = self.torch.empty(nsteps * stride + 256, dtype=self.torch.uint8, device=self.device)
+        return raw, (raw.data_ptr() + 255) & ~255, stride
+
+    @_ordered
+    def adjoint_record_step(self, dt, buf, slot: int):
+        """One forward step (the state advances) that writes its adjoint record
+        into slot `slot` of a record_buffer."""
+        raw, base, stride = buf
+        emu_adjoint_record_step(self.box, dt, base + slot * stride, stride)
+
+    @_ordered
+    def adjoint_step_recorded(self, dt, buf, slot: int, lam, gN, gNbar):
+        """adjoint_step from the record in slot `slot` (no recomputed stages);
+        the box holds that step's start state."""
+        raw, base, stride = buf
+        ptr, n = self._adjoint_ws()
+        emu_adjoint_step_recorded(self.box, dt, base + slot * stride, lam.data_ptr(), gN.data_ptr(),
+                                  gNbar.data_ptr(), ptr, n)
 
     @_ordered
     def weight_gradient(self, gN, gNbar):

@@ -242,3 +242,102 @@ def test_adjoint_bad_calls():
     blam = batch._f64(18, batch.P)
     with pytest.raises(EmuError):     # a batch takes dt = 0 (its boxes' own step sizes)
         batch.adjoint_step(3e-12, blam, batch._f64(batch.P), batch._f64(batch.P))
+
+
+def _grads(sim, parts):
+    leaves = [p.clone().requires_grad_(True) for p in parts]
+    mom = Evolve.apply(*leaves, sim)
+    objectives(mom)[1].backward()
+    return [l.grad.cpu().numpy() for l in leaves]
+
+
+@pytest.mark.parametrize("case", ["quadratic", "cubic_osc", "ngp", "batch"])
+def test_recorded_adjoint_equals_recomputed(case):
+    """The recorded backward (each step's stage states, weights and potentials
+    kept from one forward pass) runs the same kernels on the same data as the
+    recomputing one: the gradients agree bit for bit."""
+    if case == "batch":
+        wl2 = W.random_box(41, 10, seed=3)
+        wl2.alpha = 1e-8
+        wls, dts = [W.adjoint_box(nz=32, ndir=16, steps=13), wl2], [3.4e-12, 1.1e-12]
+        box = Box.from_workloads(wls, init=False)
+        mk = lambda rec: Simulation(box, 13, dts, every=5, alpha=[w.alpha for w in wls],
+                                    seed=[w.seed for w in wls], record=rec)
+        parts = [torch.cat([torch.tensor(getattr(w, a), dtype=torch.float64, device="cuda") for w in wls])
+                 for a in ("n_nu", "n_nubar", "f_nu", "f_nubar")]
+    else:
+        order = {"quadratic": 2, "cubic_osc": 3, "ngp": 0}[case]
+        wl = W.with_shape(W.adjoint_box(nz=33, ndir=16, steps=17), order)
+        box = Box.from_workload(wl, init=False)
+        if case == "cubic_osc":
+            box.set_oscillation(W.oscillation(mass_eV=(0.0, 8.6e-3, 5.0e-2), theta12=0.59, theta13=0.15,
+                                              theta23=0.84, delta_cp=1.2, energy_MeV=5e-5, rho_g_cm3=1e9, Ye=0.4))
+        mk = lambda rec: Simulation(box, wl.steps, 3.1e-12, every=6, alpha=wl.alpha, seed=wl.seed, record=rec)
+        parts = [torch.tensor(a, dtype=torch.float64, device="cuda") for a in (wl.n_nu, wl.n_nubar, wl.f_nu,
+                                                                              wl.f_nubar)]
+    ga = _grads(mk(False), parts)
+    gb = _grads(mk(True), parts)
+    for a, b in zip(ga, gb):
+        assert np.array_equal(a, b), np.abs(a - b).max()
+
+
+def test_recorded_adjoint_cost_large_box():
+    """1024 cells x 1000 directions (above the recording threshold), 24 steps
+    in segments of 8: the recorded backward matches the recomputing one bit for
+    bit and runs in less time; the forward/backward costs are reported."""
+    wl = W.adjoint_box(nz=1024, ndir=1000, steps=24)
+    box = Box.from_workload(wl, init=False)
+    parts = [torch.tensor(a, dtype=torch.float64, device="cuda") for a in (wl.n_nu, wl.n_nubar, wl.f_nu, wl.f_nubar)]
+    times, grads = {}, {}
+    for rec in (False, True, False, True):
+        sim = Simulation(box, wl.steps, 3.4e-12, every=8, alpha=wl.alpha, seed=wl.seed, record=rec)
+        leaves = [p.clone().requires_grad_(True) for p in parts]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L = objectives(Evolve.apply(*leaves, sim))[1]
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        L.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        times[rec] = (t1 - t0, t2 - t1)
+        grads[rec] = [l.grad.cpu().numpy() for l in leaves]
+    assert Simulation(box, wl.steps, 3.4e-12, every=8).use_record()
+    for a, b in zip(grads[False], grads[True]):
+        assert np.array_equal(a, b)
+    (f0, b0), (f1, b1) = times[False], times[True]
+    print(f"\nadjoint 1024x1000, 24 steps: forward {1e3 * f0:.1f} ms, backward recomputing {1e3 * b0:.1f} ms "
+          f"({b0 / f0:.2f}x), recorded {1e3 * b1:.1f} ms ({b1 / f1:.2f}x)")
+    assert b1 < b0
+
+
+def test_record_bad_calls():
+    from paper_2101_02745_gb300 import emu as E
+
+    wl = W.adjoint_box(nz=32, ndir=4, steps=1)
+    box = Box.from_workload(wl)
+    P = box.P
+    n = E.emu_batch_adjoint_record_bytes([box.cfg])
+    assert n == 8 * (54 * P + 4 * (3 * P + 36 * box.nz))
+    raw, base, stride = box.record_buffer(1)
+    with pytest.raises(EmuError):
+        E.emu_adjoint_record_step(box.box, 3e-12, base, n - 8)
+    with pytest.raises(EmuError):
+        E.emu_adjoint_record_step(box.box, 3e-12, base + 8, n)
+    with pytest.raises(EmuError):
+        E.emu_adjoint_record_step(box.box, 0.0, base, n)   # no step size set on the box
+    lam = box._f64(18, P); gN = box._f64(P); gNb = box._f64(P)
+    ptr, m = box._adjoint_ws()
+    box.rk_stage(1, 3e-12)   # a step in progress
+    with pytest.raises(EmuError):
+        E.emu_adjoint_record_step(box.box, 3e-12, base, n)
+    with pytest.raises(EmuError):
+        E.emu_adjoint_step_recorded(box.box, 3e-12, base, lam.data_ptr(), gN.data_ptr(), gNb.data_ptr(), ptr, m)
+    for s in (2, 3, 4):
+        box.rk_stage(s, 3e-12)
+    with pytest.raises(EmuError):     # workspace below 54 doubles per particle
+        E.emu_adjoint_step_recorded(box.box, 3e-12, base, lam.data_ptr(), gN.data_ptr(), gNb.data_ptr(), ptr,
+                                    8 * 54 * P - 8)
+    E.emu_adjoint_record_step(box.box, 3e-12, base, n)
+    E.emu_adjoint_step_recorded(box.box, 3e-12, base, lam.data_ptr(), gN.data_ptr(), gNb.data_ptr(), ptr, m)
+    box.sync()
