@@ -407,8 +407,11 @@ int launch_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, c
     else if (mode == 2)
       k_deposit<2, R><<<grid, kThreads, 0, st>>>(B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
                                                  nullptr, b->err);
-    else
+    else if (mode == 3)
       k_deposit<3, R><<<grid, kThreads, 0, st>>>(B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
+                                                 nullptr, b->err);
+    else
+      k_deposit<4, R><<<grid, kThreads, 0, st>>>(B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
                                                  nullptr, b->err);
     return 0;
   });
@@ -829,7 +832,10 @@ int emu_moments(emu_box* b, double* out, int on_host) {
 int emu_batch_diagnostics(emu_box* b, double* out, int on_host) {
   if (int rc = check_bound(b)) return rc;
   if (!out) return fail(b, EMU_EINVAL, "out is NULL");
-  if (int rc = run_moments(b)) return rc;
+  // the diagnostics read n, f_x, nbar, fbar_x: one deposit pass of both species
+  const double zero = 0.0;
+  if (int rc = launch_shifts(b, &zero, 1)) return rc;
+  if (int rc = launch_deposit(b, 4, b->pt.rho, b->pt.rhobar, b->shift, 0.0, b->mom)) return rc;
   before_launch(b, CLS_OTHER);
   k_diagnostics<<<dim3((unsigned)b->S.nbox, 63), kThreads, 0, b->stream>>>(batch_view(b), b->mom, b->diag);
   if (int rc = after_launch(b, "diagnostics kernel")) return rc;

@@ -380,7 +380,9 @@ __device__ __forceinline__ void flush_tile(const double (&acc)[kNA], int64_t gti
 
 // Deposit (Eq. 5), first launch.  MODE 0: B = N rho - Nbar rhobar^* (the
 // combination that enters H, Eq. 2); MODE 1: B = N rho; MODE 2: B = Nbar rhobar;
-// MODE 3: B = r_nu (packed matrices given per particle: the adjoint's Gamma).
+// MODE 3: B = r_nu (packed matrices given per particle: the adjoint's Gamma);
+// MODE 4: the moments the diagnostics read (Eq. 10), both species in one
+// pass: rows 0-8 n, 9-17 f_x (from N rho), 18-26 nbar, 27-35 fbar_x (Nbar rhobar).
 // Each warp walks its units in order (box, tile, direction), summing
 // w_pj (1, Omega_p) B_p over directions in registers (lane l owns cell
 // tile * T - H + l) and writing one partial per tile it touches; MODE 0 also
@@ -435,8 +437,17 @@ k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, c
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         // (the weights are read inside the loop: fewer live registers across it)
-        const double n1 = (MODE == 0 || MODE == 1) ? __ldg(N + p) : 0.0;
-        const double n2 = (MODE == 0 || MODE == 2) ? __ldg(Nbar + p) : 0.0;
+        const double n1 = (MODE == 0 || MODE == 1 || MODE == 4) ? __ldg(N + p) : 0.0;
+        const double n2 = (MODE == 0 || MODE == 2 || MODE == 4) ? __ldg(Nbar + p) : 0.0;
+        if constexpr (MODE == 4) {
+          const double c1 = spread.apply(n1 * __ldg(r_nu + k * P + p));
+          const double c2 = spread.apply(n2 * __ldg(r_nb + k * P + p));
+          acc[k] += c1;
+          acc[9 + k] = fma(ox, c1, acc[9 + k]);
+          acc[18 + k] += c2;
+          acc[27 + k] = fma(ox, c2, acc[27 + k]);
+          continue;
+        }
         double bv;
         if (MODE == 0) {
           const double x = __ldg(r_nu + k * P + p), y = __ldg(r_nb + k * P + p);
@@ -991,7 +1002,8 @@ __global__ void k_write_geo(BoxGeo g, double dt, BoxGeo* __restrict__ dst, doubl
 
 // Domain diagnostics per box (Eq. 10, one snapshot of Eq. B1, Eq. 18), fixed-
 // order block reduction over the box's cells.  One block per (box, quantity):
-// blockIdx.x = box, blockIdx.y = q; out[63 * b + q].
+// blockIdx.x = box, blockIdx.y = q; out[63 * b + q].  mom: the [36][NZ] moments
+// of the diagnostic deposit (rows 0-8 n, 9-17 f_x, 18-26 nbar, 27-35 fbar_x).
 __device__ __forceinline__ double abs_entry(const double* __restrict__ m, int64_t NZ, int64_t j, int a, int b) {
   if (a == b) return fabs(m[(int64_t)a * NZ + j]);
   const int lo = a < b ? a : b, hi = a < b ? b : a;
@@ -1011,15 +1023,15 @@ __global__ void k_diagnostics(Batch B, const double* __restrict__ mom, double* _
     double v;
     if (q < 36) {
       const int blk = q / 9, e = q % 9, a = e / 3, bb = e % 3;
-      const int off = blk == 0 ? 0 : blk == 1 ? 36 : blk == 2 ? 9 : 45;
+      const int off = blk == 0 ? 0 : blk == 1 ? 18 : blk == 2 ? 9 : 27;
       v = abs_entry(mom + (int64_t)off * NZ, NZ, j, a, bb);
     } else if (q < 45) {
       v = mom[(int64_t)(q - 36) * NZ + j];
     } else if (q < 54) {
-      v = mom[(int64_t)(36 + q - 45) * NZ + j];
+      v = mom[(int64_t)(18 + q - 45) * NZ + j];
     } else {
       const int k = q - 54;
-      const double nbar = mom[(int64_t)(36 + k) * NZ + j];
+      const double nbar = mom[(int64_t)(18 + k) * NZ + j];
       v = mom[(int64_t)k * NZ + j] + ((k == 4 || k == 6 || k == 8) ? nbar : -nbar);
     }
     s += v;

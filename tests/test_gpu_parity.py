@@ -33,7 +33,8 @@ def torch():
 
 
 def _cfg(wl):
-    return O.config(wl.nz, wl.ndir, wl.Lz, wl.kappa, wl.c_light, wl.cfl_adv, wl.cfl_flavor, wl.area)
+    return O.config(wl.nz, wl.ndir, wl.Lz, wl.kappa, wl.c_light, wl.cfl_adv, wl.cfl_flavor, wl.area,
+                    shape_order=wl.shape_order)
 
 
 def _oracle_init(wl):
@@ -177,12 +178,15 @@ def test_invariants_on_gpu(torch):
     box.sync()
 
 
-def test_diagnostics_match_oracle(torch):
-    wl = W.random_box(67, 37, seed=5)
+@pytest.mark.parametrize("order", [2, 0, 1, 3])
+def test_diagnostics_match_oracle(torch, order):
+    """The one-pass deposit of n, f_x, nbar, fbar_x behind the diagnostics, at
+    every shape order (steps at 0.917 x Eq. 7: no order-0 stage position on a face)."""
+    wl = W.with_shape(W.random_box(67, 37, seed=5), order)
     box = _box(wl)
     cfg = _cfg(wl)
     parts = _oracle_init(wl)
-    dt = O.timestep(cfg, O.deposit(cfg, parts))
+    dt = 0.917 * O.timestep(cfg, O.deposit(cfg, parts))
     box.step(10, dt)
     O.run(cfg, parts, dt, 10)
     d = box.diagnostics()
