@@ -37,18 +37,20 @@ UNIT = "particle-updates/s"
 # move when the state crosses the all-particle deposit barrier four times.
 B_ALG_PER_UPDATE = 313 * 8
 # Algorithmic FP64 flops per particle of one RK-stage launch (FMA = 2), counted
-# from the formulation the kernel implements: G = A0 - Omega.A at the own cell
-# (54), 3-tap interpolation with the deposit's shape weights (45), diagonal
-# differences (3), two packed Hermitian commutators (162), RK update (72;
-# stage 4: 36 + 2 for z).
-FLOPS_RK = {1: 336, 2: 336, 3: 336, 4: 302}
-# ... and of one deposit launch: position and shape weights (12), B = N rho -
-# Nbar rhobar^* (27), 3-tap gather (45), accumulation of (1, Omega) x C (63).
-FLOPS_DEPOSIT = 147
+# from the formulation the kernel implements, on the 8 traceless components of
+# H (the trace drops out of the commutator): G = A0 - Omega.A at the own cell
+# (48), 3-tap interpolation with the deposit's shape weights (40), the third
+# diagonal difference (1), two packed Hermitian commutators (162), RK update
+# (72; stage 4: 36 + 2 for z).
+FLOPS_RK = {1: 323, 2: 323, 3: 323, 4: 289}
+# ... and of one deposit launch: position and shape weights (12), the 8
+# traceless components of B = N rho - Nbar rhobar^* (29), 3-tap gather (40),
+# accumulation of (1, Omega) x C (56).
+FLOPS_DEPOSIT = 137
 # Other shape orders change the stencil's taps (per component: order 0 has no
-# gather, the cubic shape 5 taps instead of 3): RK stage -45 / +36, deposit
-# -45 / +36 (+8 for the cubic weights); the vacuum and matter terms add 18 adds.
-TAPS_DELTA = {0: -45, 1: 0, 2: 0, 3: 36}
+# gather, the cubic shape 5 taps instead of 3): RK stage -40 / +32, deposit
+# -40 / +32 (+8 for the cubic weights); the vacuum and matter terms add 16 adds.
+TAPS_DELTA = {0: -40, 1: 0, 2: 0, 3: 32}
 WEIGHTS_DELTA = {0: -12, 1: -6, 2: 0, 3: 8}
 # FP64 pipe: 2 DFMA per clock per SM (nominal 1.25 TFLOP/s / (2 flop x 152 SMs x 2.07 GHz) = 1.99),
 # so peak = 2 x 2 flop x 152 SMs x 2.07 GHz.
@@ -60,8 +62,8 @@ BYTES_DEPOSIT = 24 * 8
 # DRAM read + write per particle of one launch, from an ncu capture of the current
 # kernels (2048 cells x 1000 directions, 2.048M particles, stages 1-4 averaged):
 # scaled by the particles of the timed launch.
-TRAFFIC_RK = 711.2   # k_rk_stage32 (32 cells per warp)
-TRAFFIC_DEPOSIT = 297.9
+TRAFFIC_RK = 707.9   # k_rk_stage32 (32 cells per warp, traceless potential)
+TRAFFIC_DEPOSIT = 295.3   # k_deposit<5> (traceless potential)
 
 
 def measured_peaks():
@@ -358,7 +360,7 @@ def run_gpu(args, rank, world, local_rank):
         bytes_ = BYTES_DEPOSIT * wl.P
         traffic = TRAFFIC_DEPOSIT * wl.P
     else:
-        flops = (sum(FLOPS_RK.values()) / 4 + TAPS_DELTA[wl.shape_order] + (18 if args.osc else 0)) * wl.P
+        flops = (sum(FLOPS_RK.values()) / 4 + TAPS_DELTA[wl.shape_order] + (16 if args.osc else 0)) * wl.P
         bytes_ = BYTES_RK * wl.P
         traffic = TRAFFIC_RK * wl.P if TRAFFIC_RK else None
     achieved = flops / (avg_ms * 1e-3) / 1e12

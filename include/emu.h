@@ -32,7 +32,11 @@
  *     they report EMU_ELATTICE otherwise.
  *   - Grid potential A (36 x nz, [c * nz + j]): A0 = kappa (n - nbar^*) in
  *     components 0..8, then A_x, A_y, A_z = kappa (f_i - fbar_i^*) in 9..35, so
- *     that H_p = sum_j w_pj (A0_j - Omega_p . A_j)  (Eq. 2, 5, 6).
+ *     that H_p = sum_j w_pj (A0_j - Omega_p . A_j)  (Eq. 2, 5, 6).  This is
+ *     what emu_deposit returns.  The step itself deposits the traceless part
+ *     only (32 x nz: per moment A0, A_x, A_y, A_z the diagonal differences
+ *     11 - 22, 22 - 33 and the six off-diagonal reals): the trace of H
+ *     commutes with rho and drops out of Eq. 4.
  *   - Moments (72 x nz, [c * nz + j], cm^-3): n (0..8), f_x, f_y, f_z
  *     (9..35), nbar (36..44), fbar_x, fbar_y, fbar_z (45..71)  (Eq. 5).
  *
@@ -143,9 +147,9 @@ int emu_get_particles(emu_box* box, double* z, double* ox, double* oy, double* o
  * conventions).  If A_out is not NULL, A is also copied there ([36][nz]). */
 int emu_deposit(emu_box* box, int src, double pos_dt, double* A_out, int on_host);
 
-/* Interpolate (Eq. 6) the current grid potential A to every particle at
- * positions z + pos_dt * c * Omega_z and write H/hbar [1/s] ([9][P], packed
- * Hermitian) to H_out.  The antineutrino Hamiltonian is -H^* (Sec. 2.1). */
+/* Interpolate (Eq. 6) the grid potential A of the last emu_deposit to every
+ * particle at positions z + pos_dt * c * Omega_z and write H/hbar [1/s]
+ * ([9][P], packed Hermitian) to H_out.  The antineutrino Hamiltonian is -H^* (Sec. 2.1). */
 int emu_interpolate_H(emu_box* box, double pos_dt, double* H_out, int on_host);
 
 /* One stage s (1..4) of the classic RK4 step of size dt: deposit the stage
@@ -288,8 +292,8 @@ int emu_set_oscillation(emu_box* box, int32_t box_index, const emu_oscillation* 
 
 /* Scratch the adjoint step needs, or EMU_EINVAL: 90 doubles per particle (the
  * stage states y2, y3, two stage adjoints and their running sum) plus the
- * shape weights and grid potential of stages 1-3, kept from the recomputed
- * forward stages (3 x (kept weights per particle + 36 per cell)). */
+ * shape weights and traceless grid potential of stages 1-3, kept from the
+ * recomputed forward stages (3 x (kept weights per particle + 32 per cell)). */
 int64_t emu_adjoint_workspace_bytes(const emu_config* cfg);
 
 /* The same for a batch of nbox boxes. */

@@ -128,7 +128,7 @@ const char* make_shape(const emu_config* cfgs, int nbox, Shape& S) {
 }
 
 struct Layout {
-  size_t geo, dts, nmax, A, mom, partial, W, err, dirtab, shift, species, dirs, diag, scalar, total;
+  size_t geo, dts, nmax, A, At, mom, partial, W, err, dirtab, shift, species, dirs, diag, scalar, total;
 };
 
 Layout layout(const Shape& S) {
@@ -140,6 +140,7 @@ Layout layout(const Shape& S) {
   L.dts = take(sizeof(double) * nb);
   L.nmax = take(sizeof(double) * nb);
   L.A = take(sizeof(double) * kNA * NZ);
+  L.At = take(sizeof(double) * kNT * NZ);
   L.mom = take(sizeof(double) * kNM * NZ);
   L.partial = take(sizeof(double) * (size_t)(kMaxWarps + S.NT) * kSlot);
   L.W = take(sizeof(double) * kept_weights(S.order) * (size_t)S.Ptot);
@@ -169,8 +170,9 @@ struct emu_box {
   cudaStream_t stream = nullptr;
   char* ws = nullptr;
   BoxGeo* geo_d = nullptr;
-  double *dts = nullptr, *nmax = nullptr, *A = nullptr, *mom = nullptr, *partial = nullptr, *W = nullptr,
-         *dirtab = nullptr, *species = nullptr, *dirs = nullptr, *diag = nullptr, *scalar = nullptr;
+  // A: full grid potential of emu_deposit; At: the step's traceless potential
+  double *dts = nullptr, *nmax = nullptr, *A = nullptr, *At = nullptr, *mom = nullptr, *partial = nullptr,
+         *W = nullptr, *dirtab = nullptr, *species = nullptr, *dirs = nullptr, *diag = nullptr, *scalar = nullptr;
   int *err = nullptr, *shift = nullptr;
   int blocks = kPersistBlocks;  // grid of the step kernels (autotuned); its warps split the units
   bool pot = false;             // some box has vacuum or matter terms
@@ -282,9 +284,9 @@ int combine_split(const Shape& S, int64_t nw) {
   return split;
 }
 
-unsigned combine_blocks(int NZ, int split) {
+unsigned combine_blocks(int rows, int NZ, int split) {
   const int64_t groups = (int64_t)(kWarps / split);
-  const int64_t blocks = ((int64_t)kNA * NZ + groups * kLanes - 1) / (groups * kLanes);
+  const int64_t blocks = ((int64_t)rows * NZ + groups * kLanes - 1) / (groups * kLanes);
   return (unsigned)(blocks < 8 * kPersistBlocks ? blocks : 8 * kPersistBlocks);
 }
 
@@ -385,7 +387,7 @@ int launch_shifts(emu_box* b, const double* fracs, int nrows) {
 }
 
 // Deposit (two launches) of the state (rnu, rnb) at positions z + frac dt_b v_z
-// with the shift row shift_row, into out ([36][NZ]).  Modes as k_deposit; the
+// with the shift row shift_row, into out ([36][NZ]; mode 5: [32][NZ]).  Modes as k_deposit; the
 // potential scale kappa/dV for modes 0 and 3, 1/dV for the moments.
 int launch_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, const int* shift_row, double frac,
                    double* out) {
@@ -410,16 +412,21 @@ int launch_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, c
     else if (mode == 3)
       k_deposit<3, R><<<grid, kThreads, 0, st>>>(B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
                                                  nullptr, b->err);
-    else
+    else if (mode == 4)
       k_deposit<4, R><<<grid, kThreads, 0, st>>>(B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
                                                  nullptr, b->err);
+    else
+      k_deposit<5, R><<<grid, kThreads, 0, st>>>(B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
+                                                 b->W, b->err);
     return 0;
   });
   if (int rc = after_launch(b, "deposit kernel")) return rc;
   before_launch(b, CLS_COMBINE);
   const int split = combine_split(b->S, B.nw);
-  k_combine<<<combine_blocks(B.NZ, split), kThreads, 0, b->stream>>>(B, b->partial, out, (mode == 0 || mode == 3) ? 1 : 0, split,
-                                                                b->err);
+  const int rows = mode == 5 ? kNT : kNA;
+  const int potential = (mode == 0 || mode == 3 || mode == 5) ? 1 : 0;
+  k_combine<<<combine_blocks(rows, B.NZ, split), kThreads, 0, b->stream>>>(B, b->partial, out, rows, potential,
+                                                                          split, b->err);
   return after_launch(b, "deposit combine kernel");
 }
 
@@ -432,11 +439,11 @@ int launch_stage(emu_box* b, int s, int dry) {
   const double* rnu = (s == 1) ? b->pt.rho : b->pt.stage;
   const double* rnb = (s == 1) ? b->pt.rhobar : b->pt.stage + 9 * P;
   const int* srow = b->shift + (size_t)(s - 1) * b->S.MT;
-  if (int rc = launch_deposit(b, 0, rnu, rnb, srow, kStageFrac[s - 1], b->A)) return rc;
+  if (int rc = launch_deposit(b, 5, rnu, rnb, srow, kStageFrac[s - 1], b->At)) return rc;
   return launch_rk(b, s, srow, dry);
 }
 
-// The RK-stage kernel of stage s from the deposit in b->A and b->W.
+// The RK-stage kernel of stage s from the deposit in b->At (traceless) and b->W.
 int launch_rk(emu_box* b, int s, const int* srow, int dry) {
   before_launch(b, CLS_RK);
   by_order(b->S.order, [&](auto O) {
@@ -448,26 +455,26 @@ int launch_rk(emu_box* b, int s, const int* srow, int dry) {
     if constexpr (Sten<R>::H == 1) {
       if (Bv.U32 < 8 * (int64_t)Bv.nw32) {
         if (b->pot)
-          k_rk_stage<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(Bv, b->pt, b->W, b->dirtab, srow, b->A, s,
+          k_rk_stage<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(Bv, b->pt, b->W, b->dirtab, srow, b->At, s,
                                                                            dry);
         else
-          k_rk_stage<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(Bv, b->pt, b->W, b->dirtab, srow, b->A, s,
+          k_rk_stage<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(Bv, b->pt, b->W, b->dirtab, srow, b->At, s,
                                                                             dry);
         return 0;
       }
       if (b->pot)
         k_rk_stage32<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->W, b->dirtab,
-                                                                           srow, b->A, s, dry);
+                                                                           srow, b->At, s, dry);
       else
         k_rk_stage32<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->W, b->dirtab,
-                                                                            srow, b->A, s, dry);
+                                                                            srow, b->At, s, dry);
     } else {
       if (b->pot)
         k_rk_stage<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->W, b->dirtab,
-                                                                         srow, b->A, s, dry);
+                                                                         srow, b->At, s, dry);
       else
         k_rk_stage<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->W, b->dirtab,
-                                                                          srow, b->A, s, dry);
+                                                                          srow, b->At, s, dry);
     }
     return 0;
   });
@@ -656,6 +663,7 @@ int emu_bind(emu_box* b, const emu_particles* parts, void* workspace, int64_t wo
   b->dts = (double*)(b->ws + L.dts);
   b->nmax = (double*)(b->ws + L.nmax);
   b->A = (double*)(b->ws + L.A);
+  b->At = (double*)(b->ws + L.At);
   b->mom = (double*)(b->ws + L.mom);
   b->partial = (double*)(b->ws + L.partial);
   b->W = (double*)(b->ws + L.W);
@@ -938,12 +946,15 @@ int emu_set_oscillation(emu_box* b, int32_t box, const emu_oscillation* osc) {
     BoxGeo& g = b->S.geo[i];
     if (box == -1 || box == i) {
       const double mat = b->cfg[i].kappa * ne;   // kappa n_e on the electron flavour; Hbar gets -H_matter
-      for (int k = 0; k < 9; ++k) { g.vnu[k] = vn[k]; g.vnubar[k] = vb[k]; }
-      g.vnu[0] += mat;
-      g.vnubar[0] -= mat;
+      // traceless components (the trace commutes with every rho): H_11 - H_22, H_22 - H_33, off-diagonals
+      g.vnu[0] = (vn[0] + mat) - vn[1];
+      g.vnu[1] = vn[1] - vn[2];
+      g.vnubar[0] = (vb[0] - mat) - vb[1];
+      g.vnubar[1] = vb[1] - vb[2];
+      for (int q = 0; q < 6; ++q) { g.vnu[2 + q] = vn[3 + q]; g.vnubar[2 + q] = vb[3 + q]; }
       g.n_e = ne;
     }
-    for (int k = 0; k < 9; ++k) any = any || g.vnu[k] != 0.0 || g.vnubar[k] != 0.0;
+    for (int c = 0; c < kNC; ++c) any = any || g.vnu[c] != 0.0 || g.vnubar[c] != 0.0;
   }
   b->pot = any;
   b->step_valid = false;
@@ -959,22 +970,22 @@ int emu_set_oscillation(emu_box* b, int32_t box, const emu_oscillation* osc) {
 namespace {
 // Adjoint scratch: stage states y2, y3 and three stage adjoints [18][P] each,
 // then the shape weights and grid potential of stages 1-3 kept from the
-// recomputed forward stages ([3][NWS][P] and [3][36][NZ]).
+// recomputed forward stages ([3][NWS][P] and [3][32][NZ], traceless potentials).
 size_t adjoint_doubles(const Shape& S) {
-  return (size_t)90 * S.Ptot + 3 * ((size_t)kept_weights(S.order) * S.Ptot + (size_t)kNA * S.NZ);
+  return (size_t)90 * S.Ptot + 3 * ((size_t)kept_weights(S.order) * S.Ptot + (size_t)kNT * S.NZ);
 }
 
 // Record of one step for the adjoint: the stage states y2, y3, y4 ([3][18][P]),
 // the shape weights of stages 1-4 ([4][NWS][P]) and their grid potentials
-// ([4][36][NZ]).
+// ([4][32][NZ], traceless).
 size_t record_doubles(const Shape& S) {
-  return (size_t)54 * S.Ptot + 4 * ((size_t)kept_weights(S.order) * S.Ptot + (size_t)kNA * S.NZ);
+  return (size_t)54 * S.Ptot + 4 * ((size_t)kept_weights(S.order) * S.Ptot + (size_t)kNT * S.NZ);
 }
 
 // One forward step (as launch_step) that also writes its record.
 int record_step(emu_box* b, double* rec) {
   const size_t P = (size_t)b->S.Ptot;
-  const size_t nws = (size_t)kept_weights(b->S.order) * P, na = (size_t)kNA * b->S.NZ;
+  const size_t nws = (size_t)kept_weights(b->S.order) * P, na = (size_t)kNT * b->S.NZ;
   double* Y = rec;                 // y2, y3, y4
   double* Wr = Y + 54 * P;         // weights of stages 1..4
   double* Ar = Wr + 4 * nws;       // potentials of stages 1..4
@@ -983,12 +994,12 @@ int record_step(emu_box* b, double* rec) {
     const double* rnu = (s == 1) ? b->pt.rho : b->pt.stage;
     const double* rnb = (s == 1) ? b->pt.rhobar : b->pt.stage + 9 * P;
     const int* srow = b->shift + (size_t)(s - 1) * b->S.MT;
-    if (int rc = launch_deposit(b, 0, rnu, rnb, srow, kStageFrac[s - 1], b->A)) return rc;
+    if (int rc = launch_deposit(b, 5, rnu, rnb, srow, kStageFrac[s - 1], b->At)) return rc;
     if (nws)
       if (int rc = cuda_check(b, cudaMemcpyAsync(Wr + (s - 1) * nws, b->W, sizeof(double) * nws,
                                                  cudaMemcpyDeviceToDevice, b->stream), "record weights"))
         return rc;
-    if (int rc = cuda_check(b, cudaMemcpyAsync(Ar + (s - 1) * na, b->A, sizeof(double) * na,
+    if (int rc = cuda_check(b, cudaMemcpyAsync(Ar + (s - 1) * na, b->At, sizeof(double) * na,
                                                cudaMemcpyDeviceToDevice, b->stream), "record potential"))
       return rc;
     if (int rc = launch_rk(b, s, srow, 0)) return rc;
@@ -1003,7 +1014,7 @@ int record_step(emu_box* b, double* rec) {
 // The backward stages of one adjoint step from a record (no recomputation).
 int adjoint_recorded_body(emu_box* b, const double* rec, double* lambda, double* gN, double* gNbar, void* adj_ws) {
   const size_t P = (size_t)b->S.Ptot;
-  const size_t nws = (size_t)kept_weights(b->S.order) * P, na = (size_t)kNA * b->S.NZ;
+  const size_t nws = (size_t)kept_weights(b->S.order) * P, na = (size_t)kNT * b->S.NZ;
   const double* Y = rec;
   const double* Wr = Y + 54 * P;
   const double* Ar = Wr + 4 * nws;
@@ -1039,10 +1050,10 @@ int adjoint_recorded_body(emu_box* b, const double* rec, double* lambda, double*
       return 0;
     });
     if (int rc = after_launch(b, "adjoint stage kernel")) return rc;
-    if (int rc = launch_deposit(b, 3, b->pt.acc, nullptr, srow, kStageFrac[s - 1], b->A)) return rc;
+    if (int rc = launch_deposit(b, 3, b->pt.acc, nullptr, srow, kStageFrac[s - 1], b->mom)) return rc;
     before_launch(b, CLS_OTHER);
     by_order(b->S.order, [&](auto O) {
-      k_adj_b<decltype(O)::value><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, Ws, b->dirtab, srow, b->A,
+      k_adj_b<decltype(O)::value><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, Ws, b->dirtab, srow, b->mom,
                                                                               Lcur, Lt, gN, gNbar);
       return 0;
     });
@@ -1060,7 +1071,7 @@ int adjoint_body(emu_box* b, double* lambda, double* gN, double* gNbar, void* ad
   double* La = Y3 + 18 * P;      // adjoints of two consecutive stage states
   double* Lb = La + 18 * P;
   double* Lt = Lb + 18 * P;      // running sum: lambda + sum over stages
-  const size_t nws = (size_t)kept_weights(b->S.order) * P, na = (size_t)kNA * b->S.NZ;
+  const size_t nws = (size_t)kept_weights(b->S.order) * P, na = (size_t)kNT * b->S.NZ;
   double* Wk = Lt + 18 * P;      // weights of stages 1..3
   double* Ak = Wk + 3 * nws;     // grid potential of stages 1..3
   const size_t bytes18 = sizeof(double) * 18 * P;
@@ -1073,7 +1084,7 @@ int adjoint_body(emu_box* b, double* lambda, double* gN, double* gNbar, void* ad
       if (int rc = cuda_check(b, cudaMemcpyAsync(Wk + (s - 1) * nws, b->W, sizeof(double) * nws,
                                                  cudaMemcpyDeviceToDevice, b->stream), "keep stage weights"))
         return rc;
-    if (int rc = cuda_check(b, cudaMemcpyAsync(Ak + (s - 1) * na, b->A, sizeof(double) * na,
+    if (int rc = cuda_check(b, cudaMemcpyAsync(Ak + (s - 1) * na, b->At, sizeof(double) * na,
                                                cudaMemcpyDeviceToDevice, b->stream), "keep stage potential"))
       return rc;
     if (s < 3)
@@ -1094,10 +1105,10 @@ int adjoint_body(emu_box* b, double* lambda, double* gN, double* gNbar, void* ad
     const int* srow = b->shift + (size_t)(s - 1) * b->S.MT;
     const double frac = kStageFrac[s - 1];
     // H and weights of the stage state: stage 4 deposits them now, stages 1-3 kept theirs
-    const double* Hs = s == 4 ? b->A : Ak + (s - 1) * na;
+    const double* Hs = s == 4 ? b->At : Ak + (s - 1) * na;
     const double* Ws = s == 4 ? b->W : Wk + (s - 1) * nws;
     if (s == 4)
-      if (int rc = launch_deposit(b, 0, ys, ysb, srow, frac, b->A)) return rc;
+      if (int rc = launch_deposit(b, 5, ys, ysb, srow, frac, b->At)) return rc;
     Parts ps = b->pt;
     ps.rho = ys;
     ps.rhobar = ysb;
@@ -1114,10 +1125,10 @@ int adjoint_body(emu_box* b, double* lambda, double* gN, double* gNbar, void* ad
       return 0;
     });
     if (int rc = after_launch(b, "adjoint stage kernel")) return rc;
-    if (int rc = launch_deposit(b, 3, b->pt.acc, nullptr, srow, frac, b->A)) return rc;
+    if (int rc = launch_deposit(b, 3, b->pt.acc, nullptr, srow, frac, b->mom)) return rc;
     before_launch(b, CLS_OTHER);
     by_order(b->S.order, [&](auto O) {
-      k_adj_b<decltype(O)::value><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, Ws, b->dirtab, srow, b->A,
+      k_adj_b<decltype(O)::value><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, Ws, b->dirtab, srow, b->mom,
                                                                               Lcur, Lt, gN, gNbar);
       return 0;
     });
@@ -1393,7 +1404,7 @@ extern "C" int emu_deposit_static(const emu_config* cfg, const double* z, const 
                                                             nullptr, err);
   if (int rc = check(cudaGetLastError(), "deposit kernel")) return rc;
   const int split = combine_split(S, B.nw);
-  k_combine<<<combine_blocks(S.NZ, split), kThreads, 0, st>>>(B, partial, A_out, 1, split, err);
+  k_combine<<<combine_blocks(kNA, S.NZ, split), kThreads, 0, st>>>(B, partial, A_out, kNA, 1, split, err);
   if (int rc = check(cudaGetLastError(), "deposit combine kernel")) return rc;
   int h = 0;
   if (int rc = check(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st), "read error word")) return rc;

@@ -39,7 +39,13 @@ constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 constexpr int kLanes = 32;
 constexpr int kTileMax = 30;       // most cells a warp owns (shape orders 0-2)
-constexpr int kNA = 36;            // components of the grid potential
+constexpr int kNA = 36;            // components of the grid potential (and of a deposit's partial sums)
+// Components of the traceless grid potential the step reads: per moment (n,
+// f_x, f_y, f_z) the diagonal differences B_11 - B_22, B_22 - B_33 and the
+// six off-diagonal reals.  The trace of H commutes with every rho, so
+// -i[H, rho] (Eq. 4) depends on H only through these 8 (per moment: 32).
+constexpr int kNT = 32;
+constexpr int kNC = 8;             // components of one traceless matrix
 constexpr int kNM = 72;            // components of the per-species moments
 constexpr int kSlot = kNA * kTileMax; // doubles in one warp's partial sums for one tile
 constexpr double kLatticeTol = 1e-6;
@@ -76,8 +82,11 @@ struct BoxGeo {
   uint64_t seed;     // Eq. 9 random stream (init)
   double cfl_adv, cfl_flavor, kappa;  // Eq. 7
   double n_e;        // net electron density (matter term of Eq. 2, lepton density of Eq. 7)
-  double vnu[9];     // constant part of the neutrino Hamiltonian: (H_vacuum + H_matter) / hbar, packed
-  double vnubar[9];  // constant part of the antineutrino one: (H_vacuum^* - H_matter^*) / hbar
+  // constant parts of the Hamiltonians in the traceless components (H_11 - H_22,
+  // H_22 - H_33, off-diagonal reals): (H_vacuum + H_matter) / hbar for neutrinos,
+  // (H_vacuum^* - H_matter^*) / hbar for antineutrinos
+  double vnu[kNC];
+  double vnubar[kNC];
 };
 
 // Kernel view of a batch (passed by value).
@@ -367,14 +376,14 @@ __global__ void k_shifts(Batch B, const double* __restrict__ z, const double* __
 
 // A warp's sums for one tile go to slot (warp + global tile) of the partial
 // buffer: unique, because a later warp never returns to an earlier tile.
-template <int ORDER>
-__device__ __forceinline__ void flush_tile(const double (&acc)[kNA], int64_t gtile, int local_cell, int nz,
+template <int ORDER, int NA>
+__device__ __forceinline__ void flush_tile(const double (&acc)[NA], int64_t gtile, int local_cell, int nz,
                                            int64_t w, int lane, double* __restrict__ partial) {
   constexpr int H = Sten<ORDER>::H, T = Sten<ORDER>::T;
   if (lane >= H && lane < H + T && local_cell < nz) {
     double* slot = partial + (w + gtile) * kSlot + lane - H;
 #pragma unroll
-    for (int c = 0; c < kNA; ++c) slot[c * T] = acc[c];
+    for (int c = 0; c < NA; ++c) slot[c * T] = acc[c];
   }
 }
 
@@ -382,11 +391,14 @@ __device__ __forceinline__ void flush_tile(const double (&acc)[kNA], int64_t gti
 // combination that enters H, Eq. 2); MODE 1: B = N rho; MODE 2: B = Nbar rhobar;
 // MODE 3: B = r_nu (packed matrices given per particle: the adjoint's Gamma);
 // MODE 4: the moments the diagnostics read (Eq. 10), both species in one
-// pass: rows 0-8 n, 9-17 f_x (from N rho), 18-26 nbar, 27-35 fbar_x (Nbar rhobar).
+// pass: rows 0-8 n, 9-17 f_x (from N rho), 18-26 nbar, 27-35 fbar_x (Nbar rhobar);
+// MODE 5: MODE 0's B in the traceless components the step reads (kNT rows:
+// moment m, component c at row m * kNC + c; c = 0, 1 the diagonal differences
+// B_11 - B_22 and B_22 - B_33, c = 2..7 the off-diagonal reals 3..8).
 // Each warp walks its units in order (box, tile, direction), summing
 // w_pj (1, Omega_p) B_p over directions in registers (lane l owns cell
-// tile * T - H + l) and writing one partial per tile it touches; MODE 0 also
-// stores every particle's weights for the RK stage.  Positions: z + frac dt_b v_z.
+// tile * T - H + l) and writing one partial per tile it touches; MODES 0 and 5
+// also store every particle's weights for the RK stage.  Positions: z + frac dt_b v_z.
 template <int MODE, int ORDER>
 __global__ void __launch_bounds__(kThreads, 2)
 k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, const double* __restrict__ Nbar,
@@ -418,9 +430,10 @@ k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, c
     const int64_t ubase = g.uoff + (int64_t)tile * M;
     const int dfirst = (int)(u - ubase), dlast = (int)(uend - ubase);
     u = uend;
-    double acc[kNA];
+    constexpr int NA = MODE == 5 ? kNT : kNA;
+    double acc[NA];
 #pragma unroll
-    for (int c = 0; c < kNA; ++c) acc[c] = 0.0;
+    for (int c = 0; c < NA; ++c) acc[c] = 0.0;
     for (int d = dfirst; d < dlast; ++d) {
       const int gd = dbase + d;
       const double ox = __ldg(dirtab + gd), oy = __ldg(dirtab + MT + gd), oz = __ldg(dirtab + 2 * MT + gd);
@@ -428,43 +441,68 @@ k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, c
       const int64_t p = pbase + (int64_t)d * nz + wrapc(j - __ldg(shift + gd), nz);
       double wt[Sten<ORDER>::NW];
       bad |= shape_weights<ORDER>(fma(pos_dt, vz, __ldg(z + p)), hp, __ldg(&g.inv_dz), __ldg(&g.nz_d), wt);
-      if (MODE == 0 && W != nullptr && own) {   // the RK stage of these positions reads them back
+      if ((MODE == 0 || MODE == 5) && W != nullptr && own) {   // the RK stage of these positions reads them back
 #pragma unroll
         for (int q = 0; q < Sten<ORDER>::NWS; ++q) W[q * P + p] = wt[q];
       }
       Spread<ORDER> spread;
       spread.init(wt);
+      if constexpr (MODE == 5) {
+        const double n1 = __ldg(N + p), n2 = __ldg(Nbar + p);
+        double bprev = 0.0;   // B of the previous diagonal entry
 #pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        // (the weights are read inside the loop: fewer live registers across it)
-        const double n1 = (MODE == 0 || MODE == 1 || MODE == 4) ? __ldg(N + p) : 0.0;
-        const double n2 = (MODE == 0 || MODE == 2 || MODE == 4) ? __ldg(Nbar + p) : 0.0;
-        if constexpr (MODE == 4) {
-          const double c1 = spread.apply(n1 * __ldg(r_nu + k * P + p));
-          const double c2 = spread.apply(n2 * __ldg(r_nb + k * P + p));
+        for (int c = 0; c < kNC; ++c) {
+          double bv;
+          if (c < 2) {
+            if (c == 0) bprev = fma(-n2, __ldg(r_nb + p), n1 * __ldg(r_nu + p));
+            const double bn = fma(-n2, __ldg(r_nb + (c + 1) * P + p), n1 * __ldg(r_nu + (c + 1) * P + p));
+            bv = bprev - bn;
+            bprev = bn;
+          } else {
+            const int k = c + 1;
+            const double x = __ldg(r_nu + k * P + p), y = __ldg(r_nb + k * P + p);
+            bv = (k == 4 || k == 6 || k == 8) ? fma(n2, y, n1 * x) : fma(-n2, y, n1 * x);
+          }
+          const double cc = spread.apply(bv);
+          acc[c] += cc;
+          acc[kNC + c] = fma(ox, cc, acc[kNC + c]);
+          acc[2 * kNC + c] = fma(oy, cc, acc[2 * kNC + c]);
+          acc[3 * kNC + c] = fma(oz, cc, acc[3 * kNC + c]);
+        }
+      } else if constexpr (MODE == 4) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          const double c1 = spread.apply(__ldg(N + p) * __ldg(r_nu + k * P + p));
+          const double c2 = spread.apply(__ldg(Nbar + p) * __ldg(r_nb + k * P + p));
           acc[k] += c1;
           acc[9 + k] = fma(ox, c1, acc[9 + k]);
           acc[18 + k] += c2;
           acc[27 + k] = fma(ox, c2, acc[27 + k]);
-          continue;
         }
-        double bv;
-        if (MODE == 0) {
-          const double x = __ldg(r_nu + k * P + p), y = __ldg(r_nb + k * P + p);
-          // conj(rhobar) flips the sign of the imaginary components 4, 6, 8
-          bv = (k == 4 || k == 6 || k == 8) ? fma(n2, y, n1 * x) : fma(-n2, y, n1 * x);
-        } else if (MODE == 1) {
-          bv = n1 * __ldg(r_nu + k * P + p);
-        } else if (MODE == 2) {
-          bv = n2 * __ldg(r_nb + k * P + p);
-        } else {
-          bv = __ldg(r_nu + k * P + p);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          // (the weights are read inside the loop: fewer live registers across it)
+          const double n1 = (MODE == 0 || MODE == 1) ? __ldg(N + p) : 0.0;
+          const double n2 = (MODE == 0 || MODE == 2) ? __ldg(Nbar + p) : 0.0;
+          double bv;
+          if (MODE == 0) {
+            const double x = __ldg(r_nu + k * P + p), y = __ldg(r_nb + k * P + p);
+            // conj(rhobar) flips the sign of the imaginary components 4, 6, 8
+            bv = (k == 4 || k == 6 || k == 8) ? fma(n2, y, n1 * x) : fma(-n2, y, n1 * x);
+          } else if (MODE == 1) {
+            bv = n1 * __ldg(r_nu + k * P + p);
+          } else if (MODE == 2) {
+            bv = n2 * __ldg(r_nb + k * P + p);
+          } else {
+            bv = __ldg(r_nu + k * P + p);
+          }
+          const double c = spread.apply(bv);
+          acc[k] += c;
+          acc[9 + k] = fma(ox, c, acc[9 + k]);
+          acc[18 + k] = fma(oy, c, acc[18 + k]);
+          acc[27 + k] = fma(oz, c, acc[27 + k]);
         }
-        const double c = spread.apply(bv);
-        acc[k] += c;
-        acc[9 + k] = fma(ox, c, acc[9 + k]);
-        acc[18 + k] = fma(oy, c, acc[18 + k]);
-        acc[27 + k] = fma(oz, c, acc[27 + k]);
       }
     }
     flush_tile<ORDER>(acc, g.toff + tile, craw, nz, w, lane, partial);
@@ -473,18 +511,18 @@ k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, c
 }
 
 // Deposit, second launch: fixed-order sum of the per-warp partials.
-// out[c * NZ + coff_b + j] = scale_b * (sum over the warps that own units of
-// j's tile), scale_b = kappa_b / dV_b (MODE 0) or 1 / dV_b.  Lane l of a warp
+// out[c * NZ + coff_b + j] (c < rows) = scale_b * (sum over the warps that own
+// units of j's tile), scale_b = kappa_b / dV_b (potential) or 1 / dV_b.  Lane l of a warp
 // takes output e0 + l (consecutive cells: coalesced reads of the partials).
 // With `split` > 1 (a power of two <= 8), `split` warps of a block take the
 // same 32 outputs: warp i adds the partials of warps wf + i, wf + i + split,
 // ... in order, and the first adds the split sums in warp order through shared
 // memory.  The order depends only on the batch, the grid and `split`: results
 // are bitwise reproducible.
-__global__ void k_combine(Batch B, const double* __restrict__ partial, double* __restrict__ out, int potential,
-                          int split, int* __restrict__ err) {
+__global__ void k_combine(Batch B, const double* __restrict__ partial, double* __restrict__ out, int rows,
+                          int potential, int split, int* __restrict__ err) {
   __shared__ double sums[kWarps][kLanes];
-  const int64_t n = (int64_t)kNA * B.NZ;
+  const int64_t n = (int64_t)rows * B.NZ;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int grp = wib / split, wi = wib - grp * split;       // output group of this warp, rank within it
   const int groups = kWarps / split;
@@ -572,21 +610,22 @@ k_interpolate(Batch B, const double* __restrict__ z, const double* __restrict__ 
 template <bool POT>
 __device__ __forceinline__ void rk_particle(const BoxGeo& g, const Parts& pt, const double* __restrict__ src_b,
                                             int64_t P, int64_t p, int s, int dry, double bdt, double cdt, double dtb,
-                                            const double* __restrict__ vz, double (&Hm)[9], const double (&r)[9]) {
+                                            const double* __restrict__ vz, double (&Hm)[kNC], const double (&r)[9]) {
   const double bdt2 = 2.0 * bdt, cdt2 = 2.0 * cdt;   // diagonal K are returned halved
-  // neutrinos: H;  antineutrinos: Hbar = -H^*  (diagonal differences and real parts flip sign)
-  double Hb[9];
+  // Hm: H in the traceless components.  Antineutrinos: Hbar = -H^* (diagonal
+  // differences and real parts flip sign, imaginary parts stay)
+  double Hb[kNC];
   if (POT) {
     const double* vn = g.vnu;
     const double* vb = g.vnubar;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      const bool im = (k == 4 || k == 6 || k == 8);
-      Hb[k] = (im ? Hm[k] : -Hm[k]) + __ldg(vb + k);
-      Hm[k] += __ldg(vn + k);
+    for (int c = 0; c < kNC; ++c) {
+      const bool im = (c == 3 || c == 5 || c == 7);
+      Hb[c] = (im ? Hm[c] : -Hm[c]) + __ldg(vb + c);
+      Hm[c] += __ldg(vn + c);
     }
   }
-  const double d12 = Hm[0] - Hm[1], d13 = Hm[0] - Hm[2], d23 = Hm[1] - Hm[2];
+  const double d12 = Hm[0], d23 = Hm[1], d13 = d12 + d23;
 #pragma unroll
   for (int which = 0; which < 2; ++which) {
     double* __restrict__ yv = which ? pt.rhobar : pt.rho;
@@ -608,10 +647,9 @@ __device__ __forceinline__ void rk_particle(const BoxGeo& g, const Parts& pt, co
     }
     const double* rr = which ? rb : r;
     double kd[3], ko[6];
-    if (which == 0) commutator(d12, d13, d23, Hm[3], Hm[4], Hm[5], Hm[6], Hm[7], Hm[8], rr, kd, ko);
-    else if (POT) commutator(Hb[0] - Hb[1], Hb[0] - Hb[2], Hb[1] - Hb[2], Hb[3], Hb[4], Hb[5], Hb[6], Hb[7], Hb[8],
-                             rr, kd, ko);
-    else commutator(-d12, -d13, -d23, -Hm[3], Hm[4], -Hm[5], Hm[6], -Hm[7], Hm[8], rr, kd, ko);
+    if (which == 0) commutator(d12, d13, d23, Hm[2], Hm[3], Hm[4], Hm[5], Hm[6], Hm[7], rr, kd, ko);
+    else if (POT) commutator(Hb[0], Hb[0] + Hb[1], Hb[1], Hb[2], Hb[3], Hb[4], Hb[5], Hb[6], Hb[7], rr, kd, ko);
+    else commutator(-d12, -d13, -d23, -Hm[2], Hm[3], -Hm[4], Hm[5], -Hm[6], Hm[7], rr, kd, ko);
     if (s == 1) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) { av[k * P + p] = fma(bdt2, kd[k], rr[k]); sv[k * P + p] = fma(cdt2, kd[k], rr[k]); }
@@ -719,14 +757,14 @@ k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __rest
 #pragma unroll
       for (int k = 0; k < 9; ++k) r[k] = src_r[k * P + p];
     }
-    double Hm[9];
+    double Hm[kNC];
     const double* Aj = A + g.coff + j;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      const double G = fma(-oz, __ldg(Aj + (int64_t)(27 + k) * NZ),
-                           fma(-oy, __ldg(Aj + (int64_t)(18 + k) * NZ),
-                               fma(-ox, __ldg(Aj + (int64_t)(9 + k) * NZ), __ldg(Aj + (int64_t)k * NZ))));
-      Hm[k] = gather<ORDER>(wt, G);
+    for (int c = 0; c < kNC; ++c) {
+      const double G = fma(-oz, __ldg(Aj + (int64_t)(3 * kNC + c) * NZ),
+                           fma(-oy, __ldg(Aj + (int64_t)(2 * kNC + c) * NZ),
+                               fma(-ox, __ldg(Aj + (int64_t)(kNC + c) * NZ), __ldg(Aj + (int64_t)c * NZ))));
+      Hm[c] = gather<ORDER>(wt, G);
     }
     if (!active) continue;
     rk_particle<POT>(g, pt, src_b, P, p, s, dry, bdt, cdt, B.dt[b], dirtab + 3 * MT + gd, Hm, r);
@@ -742,13 +780,13 @@ k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __rest
 // of the same ring when the warp handles them in order, and are computed
 // directly (one cell, by the whole warp) at ring and range boundaries.
 __device__ __forceinline__ void ring_cell_G(const double* __restrict__ A, int NZ, int coff, int cell, double ox,
-                                            double oy, double oz, double (&G)[9]) {
+                                            double oy, double oz, double (&G)[kNC]) {
   const double* Aj = A + coff + cell;
 #pragma unroll
-  for (int k = 0; k < 9; ++k)
-    G[k] = fma(-oz, __ldg(Aj + (int64_t)(27 + k) * NZ),
-               fma(-oy, __ldg(Aj + (int64_t)(18 + k) * NZ), fma(-ox, __ldg(Aj + (int64_t)(9 + k) * NZ),
-                                                                __ldg(Aj + (int64_t)k * NZ))));
+  for (int c = 0; c < kNC; ++c)
+    G[c] = fma(-oz, __ldg(Aj + (int64_t)(3 * kNC + c) * NZ),
+               fma(-oy, __ldg(Aj + (int64_t)(2 * kNC + c) * NZ), fma(-ox, __ldg(Aj + (int64_t)(kNC + c) * NZ),
+                                                                     __ldg(Aj + (int64_t)c * NZ))));
 }
 
 template <bool POT, int ORDER>
@@ -756,8 +794,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
              const int* __restrict__ shift, const double* __restrict__ A, int s, int dry) {
   static_assert(Sten<ORDER>::H == 1, "one neighbour on each side");
-  __shared__ double gsm[kWarps][2][9][kLanes];   // G of the last two units, per warp
-  __shared__ double edge[kWarps][2][9];          // left / right neighbour of the unit being finished
+  __shared__ double gsm[kWarps][2][kNC][kLanes];   // G of the last two units, per warp
+  __shared__ double edge[kWarps][2][kNC];          // left / right neighbour of the unit being finished
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t w = (int64_t)blockIdx.x * kWarps + wib;
   const int64_t u0 = unit32_begin(w, B), u1 = unit32_begin(w + 1, B);
@@ -803,11 +841,11 @@ k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __re
       }
       // G of this unit's cells
       if (lane < cn) {
-        double G[9];
+        double G[kNC];
         ring_cell_G(A, NZ, g.coff, ct * kLanes + lane, __ldg(dirtab + cgd), __ldg(dirtab + MT + cgd),
                     __ldg(dirtab + 2 * MT + cgd), G);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) gsm[wib][slot][k][lane] = G[k];
+        for (int k = 0; k < kNC; ++k) gsm[wib][slot][k][lane] = G[k];
       }
     }
     // does this unit continue the ring of the one being finished?
@@ -817,18 +855,18 @@ k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __re
       const double ox = __ldg(dirtab + pgd), oy = __ldg(dirtab + MT + pgd), oz = __ldg(dirtab + 2 * MT + pgd);
       // right neighbour of the finished unit's last cell
       if (!next_in_ring) {
-        double G[9];
+        double G[kNC];
         const int cell = pt_ * kLanes + pn;                 // one past its last cell, on the ring
         ring_cell_G(A, NZ, g.coff, cell >= g.nz ? cell - g.nz : cell, ox, oy, oz, G);
         if (lane == 0) {
 #pragma unroll
-          for (int k = 0; k < 9; ++k) edge[wib][1][k] = G[k];
+          for (int k = 0; k < kNC; ++k) edge[wib][1][k] = G[k];
         }
       }
       __syncwarp();
       if (next_in_ring && lane == 0) {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) edge[wib][1][k] = gsm[wib][slot][k][0];
+        for (int k = 0; k < kNC; ++k) edge[wib][1][k] = gsm[wib][slot][k][0];
       }
       __syncwarp();
       // finish the previous unit: interpolation, commutators, RK update
@@ -840,9 +878,9 @@ k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __re
         load_weights<ORDER>(W, P, p, wt);
 #pragma unroll
         for (int k = 0; k < 9; ++k) r[k] = src_r[k * P + p];
-        double Hm[9];
+        double Hm[kNC];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
+        for (int k = 0; k < kNC; ++k) {
           const double G = gsm[wib][psl][k][lane];
           if (ORDER == 0) {
             Hm[k] = G;
@@ -867,17 +905,17 @@ k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __re
       if (next_in_ring) {
         if (lane == 0) {
 #pragma unroll
-          for (int k = 0; k < 9; ++k) edge[wib][0][k] = gsm[wib][slot ^ 1][k][kLanes - 1];
+          for (int k = 0; k < kNC; ++k) edge[wib][0][k] = gsm[wib][slot ^ 1][k][kLanes - 1];
         }
       } else {
         const BoxGeo& g = B.box[cb];
-        double G[9];
+        double G[kNC];
         const int cell = ct * kLanes - 1;                    // one before its first cell, on the ring
         ring_cell_G(A, NZ, g.coff, cell < 0 ? cell + g.nz : cell, __ldg(dirtab + cgd), __ldg(dirtab + MT + cgd),
                     __ldg(dirtab + 2 * MT + cgd), G);
         if (lane == 0) {
 #pragma unroll
-          for (int k = 0; k < 9; ++k) edge[wib][0][k] = G[k];
+          for (int k = 0; k < kNC; ++k) edge[wib][0][k] = G[k];
         }
       }
       __syncwarp();
@@ -1065,6 +1103,15 @@ __device__ __forceinline__ void kfull(const double H[9], const double r[9], doub
   for (int k = 0; k < 6; ++k) out[3 + k] = ko[k];
 }
 
+// kfull with H given by its traceless components (H_11 - H_22, H_22 - H_33, off-diagonal reals).
+__device__ __forceinline__ void kfull_t(const double H[kNC], const double r[9], double out[9]) {
+  double kd[3], ko[6];
+  commutator(H[0], H[0] + H[1], H[1], H[2], H[3], H[4], H[5], H[6], H[7], r, kd, ko);
+  out[0] = 2.0 * kd[0]; out[1] = 2.0 * kd[1]; out[2] = 2.0 * kd[2];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) out[3 + k] = ko[k];
+}
+
 // First adjoint launch of stage s.  m = a lam + c lamn, the adjoint of this
 // stage's derivative k_s, with the box's step dt: a = dt/6 (s = 1, 4) or dt/3,
 // c = dt/2 (s = 1, 2) or dt (s = 3), lamn the adjoint of stage s + 1 (NULL
@@ -1100,30 +1147,33 @@ k_adj_a(Batch B, Parts pt, const double* __restrict__ W, const double* __restric
     double wt[Sten<ORDER>::NW];
     zero_weights<ORDER>(wt);
     if (active) load_weights<ORDER>(W, P, p, wt);
-    double H[9];
+    double H[kNC];   // traceless components of the stage's H
     const double* Aj = A + g.coff + j;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      const double G = fma(-oz, __ldg(Aj + (int64_t)(27 + k) * NZ),
-                           fma(-oy, __ldg(Aj + (int64_t)(18 + k) * NZ),
-                               fma(-ox, __ldg(Aj + (int64_t)(9 + k) * NZ), __ldg(Aj + (int64_t)k * NZ))));
-      H[k] = gather<ORDER>(wt, G);
+    for (int c = 0; c < kNC; ++c) {
+      const double G = fma(-oz, __ldg(Aj + (int64_t)(3 * kNC + c) * NZ),
+                           fma(-oy, __ldg(Aj + (int64_t)(2 * kNC + c) * NZ),
+                               fma(-ox, __ldg(Aj + (int64_t)(kNC + c) * NZ), __ldg(Aj + (int64_t)c * NZ))));
+      H[c] = gather<ORDER>(wt, G);
     }
     if (!active) continue;
     double Gm[9];
 #pragma unroll
     for (int which = 0; which < 2; ++which) {
-      double Hs[9], r[9], mh[9], t[9];
+      double Hs[kNC], r[9], mh[9], t[9];
+#pragma unroll
+      for (int c = 0; c < kNC; ++c) {
+        const bool im = (c == 3 || c == 5 || c == 7);
+        const double sgn = which ? (im ? 1.0 : -1.0) : 1.0;                 // S for antineutrinos
+        Hs[c] = sgn * H[c] + (POT ? __ldg((which ? g.vnubar : g.vnu) + c) : 0.0);
+      }
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
-        const bool im = (k == 4 || k == 6 || k == 8);
-        const double sgn = which ? (im ? 1.0 : -1.0) : 1.0;                 // S for antineutrinos
-        Hs[k] = sgn * H[k] + (POT ? __ldg((which ? g.vnubar : g.vnu) + k) : 0.0);
         const double mk = a * lam[(which * 9 + k) * P + p] + (lamn ? bc * lamn[(which * 9 + k) * P + p] : 0.0);
         mh[k] = k < 3 ? mk : 0.5 * mk;                                      // D^-1 m
         r[k] = (which ? pt.rhobar : pt.rho)[k * P + p];
       }
-      kfull(Hs, mh, t);                                                     // direct term: -D K(H, D^-1 m)
+      kfull_t(Hs, mh, t);                                                   // direct term: -D K(H, D^-1 m)
 #pragma unroll
       for (int k = 0; k < 9; ++k) lam_out[(which * 9 + k) * P + p] = -(k < 3 ? t[k] : 2.0 * t[k]);
       kfull(r, mh, t);                                                      // Gamma: D K(r, D^-1 m) (times S)

@@ -220,7 +220,7 @@ def test_adjoint_bad_calls():
     P = box.P
     lam = box._f64(18, P); gN = box._f64(P); gNb = box._f64(P)
     n = E.emu_adjoint_workspace_bytes(box.cfg)
-    assert n == 8 * (90 * P + 3 * (3 * P + 36 * box.nz))   # quadratic shape: 3 kept weights
+    assert n == 8 * (90 * P + 3 * (3 * P + 32 * box.nz))   # quadratic shape: 3 kept weights, 32-row potentials
     ws = torch.empty(n + 256, dtype=torch.uint8, device="cuda")
     p = (ws.data_ptr() + 255) & ~255
     with pytest.raises(EmuError):
@@ -318,7 +318,7 @@ def test_record_bad_calls():
     box = Box.from_workload(wl)
     P = box.P
     n = E.emu_batch_adjoint_record_bytes([box.cfg])
-    assert n == 8 * (54 * P + 4 * (3 * P + 36 * box.nz))
+    assert n == 8 * (54 * P + 4 * (3 * P + 32 * box.nz))
     raw, base, stride = box.record_buffer(1)
     with pytest.raises(EmuError):
         E.emu_adjoint_record_step(box.box, 3e-12, base, n - 8)
