@@ -334,7 +334,14 @@ def run_gpu(args, rank, world, local_rank):
         E.emu_step(box.box, 1, dt)
         E.emu_diagnostics(box.box, diag.data_ptr(), 1)
 
+    # the host link's copy rate alone (the e2e step cannot beat the copy of its inputs)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(device)
+    c0.record(feed.copy)
     feed.prefetch()
+    c1.record(feed.copy)
+    torch.cuda.synchronize(device)
+    h2d_gbs = feed.h2d_bytes / (c0.elapsed_time(c1) * 1e-3) / 1e9
     e2e_step()
     barrier(dist, device)
     torch.cuda.synchronize(device)
@@ -388,7 +395,9 @@ def run_gpu(args, rank, world, local_rank):
                        "l2": "inputs larger than L2 (particle state %.2f GB per GPU vs 129 MB L2)" % (wl.P * 480 / 1e9)},
             "roofline": roofline, "hbm": hbm,
             "kernels": {k: {"launches": n, "avg_ms": a, "share": ms / total} for k, (a, n, ms) in per.items() if n},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": e2e_s / args.steps * 1e3, "h2d_gbs_alone": h2d_gbs,
+                    "h2d_ms_alone": h2d / h2d_gbs / 1e6},
             "gpu_launches": launches,
             "clocks": clk,
         }
