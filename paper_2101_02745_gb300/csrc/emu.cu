@@ -452,30 +452,21 @@ int launch_rk(emu_box* b, int s, const int* srow, int dry) {
     // tile ends at ring and range boundaries are computed directly); otherwise
     // the halo-lane kernel, which gives bitwise the same results
     const Batch Bv = batch_view(b);
-    if constexpr (Sten<R>::H == 1) {
-      if (Bv.U32 < 8 * (int64_t)Bv.nw32) {
-        if (b->pot)
-          k_rk_stage<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(Bv, b->pt, b->W, b->dirtab, srow, b->At, s,
-                                                                           dry);
-        else
-          k_rk_stage<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(Bv, b->pt, b->W, b->dirtab, srow, b->At, s,
-                                                                            dry);
-        return 0;
-      }
+    if (Bv.U32 < 8 * (int64_t)Bv.nw32) {
       if (b->pot)
-        k_rk_stage32<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->W, b->dirtab,
-                                                                           srow, b->At, s, dry);
+        k_rk_stage<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(Bv, b->pt, b->W, b->dirtab, srow, b->At, s,
+                                                                         dry);
       else
-        k_rk_stage32<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->W, b->dirtab,
-                                                                            srow, b->At, s, dry);
-    } else {
-      if (b->pot)
-        k_rk_stage<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->W, b->dirtab,
-                                                                         srow, b->At, s, dry);
-      else
-        k_rk_stage<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->W, b->dirtab,
-                                                                          srow, b->At, s, dry);
+        k_rk_stage<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(Bv, b->pt, b->W, b->dirtab, srow, b->At, s,
+                                                                          dry);
+      return 0;
     }
+    if (b->pot)
+      k_rk_stage32<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(Bv, b->pt, b->W, b->dirtab, srow, b->At, s,
+                                                                         dry);
+    else
+      k_rk_stage32<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(Bv, b->pt, b->W, b->dirtab, srow, b->At, s,
+                                                                          dry);
     return 0;
   });
   return after_launch(b, "RK stage kernel");

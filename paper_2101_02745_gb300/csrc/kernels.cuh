@@ -73,7 +73,7 @@ struct Sten {
 // One box of a batch (device copy lives in the workspace).
 struct BoxGeo {
   int nz, M, ntiles, use_dirs;
-  int coff, toff, doff, ntiles32;  // ntiles32: 32-cell tiles of the RK stage (shape orders 0-2)
+  int coff, toff, doff, ntiles32;  // ntiles32: 32-cell tiles of the RK stage
   int64_t P, poff, uoff, uoff32;   // uoff32: first 32-cell unit of the box
   double Lz, dz, inv_dz, nz_d, dV, c_light;
   double kappa_dV;   // kappa / dV: scale of the grid potential
@@ -771,14 +771,15 @@ k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __rest
   }
 }
 
-// The RK stage with 32 cells per warp (shape orders 0-2, stencil reach one
-// cell): the same arithmetic as k_rk_stage, without its two halo lanes.  Units
-// are (32-cell tile, direction), direction-major, split evenly over the warps.
-// A warp writes G = A0 - Omega . A of a unit's cells into shared memory and
-// finishes that unit one iteration later, when the next tile's first cell is
-// known: the stencil neighbours of its end cells come from the adjacent tiles
-// of the same ring when the warp handles them in order, and are computed
-// directly (one cell, by the whole warp) at ring and range boundaries.
+// The RK stage with 32 cells per warp: the same arithmetic as k_rk_stage,
+// without its halo lanes (two for shape orders 0-2, four for the cubic
+// shape).  Units are (32-cell tile, direction), direction-major, split evenly
+// over the warps.  A warp writes G = A0 - Omega . A of a unit's cells into
+// shared memory and finishes that unit one iteration later, when the next
+// tile's first cells are known: the stencil neighbours of its end cells (H on
+// each side) come from the adjacent tiles of the same ring when the warp
+// handles them in order, and are computed directly (one cell at a time, by the
+// whole warp) at ring and range boundaries.
 __device__ __forceinline__ void ring_cell_G(const double* __restrict__ A, int NZ, int coff, int cell, double ox,
                                             double oy, double oz, double (&G)[kNC]) {
   const double* Aj = A + coff + cell;
@@ -789,13 +790,21 @@ __device__ __forceinline__ void ring_cell_G(const double* __restrict__ A, int NZ
                                                                      __ldg(Aj + (int64_t)c * NZ))));
 }
 
+// Cell index on a ring of nz cells for cells within two rings of it (the
+// stencil reaches at most two cells past a tile; rings may be shorter).
+__device__ __forceinline__ int ring_wrap(int cell, int nz) {
+  while (cell < 0) cell += nz;
+  while (cell >= nz) cell -= nz;
+  return cell;
+}
+
 template <bool POT, int ORDER>
 __global__ void __launch_bounds__(kThreads, 2)
 k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
              const int* __restrict__ shift, const double* __restrict__ A, int s, int dry) {
-  static_assert(Sten<ORDER>::H == 1, "one neighbour on each side");
+  constexpr int H = Sten<ORDER>::H, NW = Sten<ORDER>::NW;
   __shared__ double gsm[kWarps][2][kNC][kLanes];   // G of the last two units, per warp
-  __shared__ double edge[kWarps][2][kNC];          // left / right neighbour of the unit being finished
+  __shared__ double edge[kWarps][2][H][kNC];       // the H cells left / right of the unit being finished
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t w = (int64_t)blockIdx.x * kWarps + wib;
   const int64_t u0 = unit32_begin(w, B), u1 = unit32_begin(w + 1, B);
@@ -853,27 +862,37 @@ k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __re
     if (pb >= 0) {
       const BoxGeo& g = B.box[pb];
       const double ox = __ldg(dirtab + pgd), oy = __ldg(dirtab + MT + pgd), oz = __ldg(dirtab + 2 * MT + pgd);
-      // right neighbour of the finished unit's last cell
-      if (!next_in_ring) {
-        double G[kNC];
-        const int cell = pt_ * kLanes + pn;                 // one past its last cell, on the ring
-        ring_cell_G(A, NZ, g.coff, cell >= g.nz ? cell - g.nz : cell, ox, oy, oz, G);
-        if (lane == 0) {
+      // the H cells right of the finished unit's last cell: from this unit's
+      // first cells when it continues the ring and has them, else computed
 #pragma unroll
-          for (int k = 0; k < kNC; ++k) edge[wib][1][k] = G[k];
+      for (int o = 0; o < H; ++o) {
+        if (!(next_in_ring && (H == 1 || o < cn))) {   // (a unit that continues a ring has a first cell)
+          double G[kNC];
+          const int cell = pt_ * kLanes + pn + o;
+          ring_cell_G(A, NZ, g.coff, H == 1 ? (cell >= g.nz ? cell - g.nz : cell) : ring_wrap(cell, g.nz), ox, oy,
+                      oz, G);
+          if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < kNC; ++k) edge[wib][1][o][k] = G[k];
+          }
         }
       }
       __syncwarp();
       if (next_in_ring && lane == 0) {
 #pragma unroll
-        for (int k = 0; k < kNC; ++k) edge[wib][1][k] = gsm[wib][slot][k][0];
+        for (int o = 0; o < H; ++o)
+          if (H == 1 || o < cn) {
+#pragma unroll
+            for (int k = 0; k < kNC; ++k) edge[wib][1][o][k] = gsm[wib][slot][k][o];
+          }
       }
       __syncwarp();
-      // finish the previous unit: interpolation, commutators, RK update
+      // finish the previous unit: interpolation (the taps in k_rk_stage's
+      // order), commutators, RK update
       const int psl = slot ^ 1;
       if (lane < pn) {
         const int64_t p = g.poff + (int64_t)pd * g.nz + wrapc(pt_ * kLanes + lane - __ldg(shift + pgd), g.nz);
-        double wt[Sten<ORDER>::NW];
+        double wt[NW];
         double r[9];
         load_weights<ORDER>(W, P, p, wt);
 #pragma unroll
@@ -881,13 +900,22 @@ k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __re
         double Hm[kNC];
 #pragma unroll
         for (int k = 0; k < kNC; ++k) {
-          const double G = gsm[wib][psl][k][lane];
           if (ORDER == 0) {
-            Hm[k] = G;
+            Hm[k] = gsm[wib][psl][k][lane];
+          } else if (H == 1) {
+            const double gl = lane == 0 ? edge[wib][0][0][k] : gsm[wib][psl][k][lane - 1];
+            const double gr = lane == pn - 1 ? edge[wib][1][0][k] : gsm[wib][psl][k][lane + 1];
+            Hm[k] = fma(wt[0], gl, fma(wt[1], gsm[wib][psl][k][lane], wt[2] * gr));
           } else {
-            const double gl = lane == 0 ? edge[wib][0][k] : gsm[wib][psl][k][lane - 1];
-            const double gr = lane == pn - 1 ? edge[wib][1][k] : gsm[wib][psl][k][lane + 1];
-            Hm[k] = fma(wt[0], gl, fma(wt[1], G, wt[2] * gr));
+            // value of G at tap offset o: this unit's cells, or the edges
+            auto gv = [&](int o) {
+              const int i = lane + o;
+              return i < 0 ? edge[wib][0][-i - 1][k] : i >= pn ? edge[wib][1][i - pn][k] : gsm[wib][psl][k][i];
+            };
+            double h = wt[NW - 1] * gv(H);
+#pragma unroll
+            for (int t = NW - 2; t >= 0; --t) h = fma(wt[t], gv(t - H), h);
+            Hm[k] = h;
           }
         }
         if (pb != bcur) {
@@ -900,22 +928,30 @@ k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __re
       }
       __syncwarp();
     }
-    // left neighbour of this unit's first cell, for when it is finished
+    // the H cells left of this unit's first cell, for when it is finished:
+    // the previous unit's last cells when this one continues its ring (that
+    // unit then has all 32 cells), else computed
     if (cb >= 0) {
       if (next_in_ring) {
         if (lane == 0) {
 #pragma unroll
-          for (int k = 0; k < kNC; ++k) edge[wib][0][k] = gsm[wib][slot ^ 1][k][kLanes - 1];
+          for (int o = 1; o <= H; ++o) {
+#pragma unroll
+            for (int k = 0; k < kNC; ++k) edge[wib][0][o - 1][k] = gsm[wib][slot ^ 1][k][kLanes - o];
+          }
         }
       } else {
         const BoxGeo& g = B.box[cb];
-        double G[kNC];
-        const int cell = ct * kLanes - 1;                    // one before its first cell, on the ring
-        ring_cell_G(A, NZ, g.coff, cell < 0 ? cell + g.nz : cell, __ldg(dirtab + cgd), __ldg(dirtab + MT + cgd),
-                    __ldg(dirtab + 2 * MT + cgd), G);
-        if (lane == 0) {
 #pragma unroll
-          for (int k = 0; k < kNC; ++k) edge[wib][0][k] = G[k];
+        for (int o = 1; o <= H; ++o) {
+          double G[kNC];
+          const int cell = ct * kLanes - o;
+          ring_cell_G(A, NZ, g.coff, H == 1 ? (cell < 0 ? cell + g.nz : cell) : ring_wrap(cell, g.nz),
+                      __ldg(dirtab + cgd), __ldg(dirtab + MT + cgd), __ldg(dirtab + 2 * MT + cgd), G);
+          if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < kNC; ++k) edge[wib][0][o - 1][k] = G[k];
+          }
         }
       }
       __syncwarp();
