@@ -333,7 +333,10 @@ int emu_adjoint_step(emu_box* box, double dt, double* lambda, double* gN, double
  * runs that step's adjoint (as emu_adjoint_step, same results) from the
  * record, with no recomputed stages; the box must hold the state at the
  * START of the step again, and adj_ws needs 54 doubles per particle.  dt as
- * in emu_adjoint_step.  Buffers: device, 256-byte aligned.  Errors: as
+ * in emu_adjoint_step.  Buffers: device, 256-byte aligned.  Each call is
+ * captured as a CUDA graph on first use with its buffers (the record; for the
+ * adjoint step also lambda, gN, gNbar, adj_ws) and replayed on later calls
+ * with the same buffers (up to 256 graphs per box).  Errors: as
  * emu_adjoint_step. */
 int64_t emu_batch_adjoint_record_bytes(const emu_config* cfgs, int32_t nbox);
 int emu_adjoint_record_step(emu_box* box, double dt, void* rec, int64_t rec_bytes);

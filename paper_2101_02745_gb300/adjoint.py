@@ -20,8 +20,9 @@ backward (emu_adjoint_step, which recomputes the step's forward stages).
 With sim.record the recomputation writes each step's record (stage states,
 weights, potentials; emu_adjoint_record_step) and the adjoint steps read it
 (emu_adjoint_step_recorded), so the forward stages run once instead of
-twice; the default turns it on for boxes of 2^18 particles and more when a
-segment's records fit in half the free device memory.  The accumulated
+twice; the library replays both calls as CUDA graphs per record slot.  The
+default records whenever a segment's records fit in half the free device
+memory.  The accumulated
 dL/dN, dL/dNbar go through Eq. 8 to the species inputs
 (emu_weight_gradient).  Every arithmetic step runs in the CUDA library; this
 module only marshals buffers.
@@ -49,8 +50,6 @@ class Simulation:
     dirs: np.ndarray | None = None
     record: bool | None = None
 
-    RECORD_MIN_PARTICLES = 1 << 18
-
     @property
     def batched(self) -> bool:
         return self.box.nbox > 1
@@ -64,8 +63,6 @@ class Simulation:
         """Whether backward keeps per-step records (see the module notes)."""
         if self.record is not None:
             return bool(self.record)
-        if self.box.P < self.RECORD_MIN_PARTICLES:
-            return False
         import torch
         free, _ = torch.cuda.mem_get_info(self.box.device)
         return min(self.every, max(self.nsteps, 1)) * self.box.record_stride() <= free // 2
@@ -115,10 +112,7 @@ class Evolve(torch.autograd.Function):
     def backward(ctx, dmom):
         sim: Simulation = ctx.sim
         box = sim.box
-        P = box.P
-        lam = box._f64(18, P)
-        gN = box._f64(P)
-        gNbar = box._f64(P)
+        lam, gN, gNbar = box.adjoint_buffers()
         box.load_state(ctx.final)
         box.adjoint_seed(dmom, lam, gN, gNbar)
         nseg = len(ctx.checkpoints)
@@ -145,7 +139,6 @@ class Evolve(torch.autograd.Function):
                     box.adjoint_step_recorded(dt, rec, j, lam, gN, gNbar)
         box.load_state(ctx.final)
         g = box.weight_gradient(gN, gNbar).to(ctx.dev)
-        ctx.lambda0 = lam  # dL/d(initial rho, rhobar), kept for inspection
         return g[0], g[1], g[2:5].T.contiguous(), g[5:8].T.contiguous(), None
 
 

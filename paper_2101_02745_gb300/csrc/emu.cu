@@ -194,6 +194,9 @@ struct emu_box {
   cudaGraphExec_t adj_graph = nullptr;
   int64_t adj_launches = 0;
   const void* adj_key[4] = {nullptr, nullptr, nullptr, nullptr};
+  // recorded-adjoint steps (record / backward), one graph per set of buffers
+  struct KeyedGraph { const void* key[6]; cudaGraphExec_t exec; int64_t launches; };
+  std::vector<KeyedGraph> rec_graphs;
   // graphs of a box bound to the legacy default stream run on this blocking
   // stream, which the legacy stream orders implicitly with its own work
   cudaStream_t cap = nullptr;
@@ -203,6 +206,7 @@ struct emu_box {
     for (auto e : pool) cudaEventDestroy(e);
     if (graph) cudaGraphExecDestroy(graph);
     if (adj_graph) cudaGraphExecDestroy(adj_graph);
+    for (auto& g : rec_graphs) cudaGraphExecDestroy(g.exec);
     if (cap) cudaStreamDestroy(cap);
   }
 };
@@ -311,6 +315,8 @@ void invalidate_graph(emu_box* b) {
     cudaGraphExecDestroy(b->adj_graph);
     b->adj_graph = nullptr;
   }
+  for (auto& g : b->rec_graphs) cudaGraphExecDestroy(g.exec);
+  b->rec_graphs.clear();
 }
 
 // Stream the box's graphs are captured on and replayed on: its own stream, or
@@ -358,6 +364,24 @@ int launch_graph(emu_box* b, cudaGraphExec_t exec, int64_t count) {
   return EMU_OK;
 }
 
+// Replays the graph captured from body() for these buffers (key), capturing
+// it on first use; at most kKeyedGraphs are kept (the oldest is dropped).
+constexpr size_t kKeyedGraphs = 256;
+template <class F>
+int keyed_graph(emu_box* b, const void* const (&key)[6], F&& body) {
+  for (auto& g : b->rec_graphs)
+    if (std::memcmp(g.key, key, sizeof(g.key)) == 0) return launch_graph(b, g.exec, g.launches);
+  if (b->rec_graphs.size() >= kKeyedGraphs) {
+    cudaGraphExecDestroy(b->rec_graphs.front().exec);
+    b->rec_graphs.erase(b->rec_graphs.begin());
+  }
+  emu_box::KeyedGraph g{};
+  std::memcpy(g.key, key, sizeof(g.key));
+  if (int rc = capture(b, &g.exec, &g.launches, body)) return rc;
+  b->rec_graphs.push_back(g);
+  return launch_graph(b, g.exec, g.launches);
+}
+
 int copy_out(emu_box* b, void* dst, const void* src, size_t bytes, int on_host) {
   cudaError_t e = cudaMemcpyAsync(dst, src, bytes, on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
                                   b->stream);
@@ -390,7 +414,8 @@ int launch_shifts(emu_box* b, const double* fracs, int nrows) {
 // with the shift row shift_row, into out ([36][NZ]; mode 5: [32][NZ]).  Modes as k_deposit; the
 // potential scale kappa/dV for modes 0 and 3, 1/dV for the moments.
 int launch_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, const int* shift_row, double frac,
-                   double* out) {
+                   double* out, double* W = nullptr) {
+  if (!W) W = b->W;   // where modes 0 and 5 keep the shape weights
   const Batch B = batch_view(b);
   before_launch(b, CLS_DEPOSIT);
   const dim3 grid = persist_grid(b);
@@ -402,7 +427,7 @@ int launch_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, c
     constexpr int R = decltype(O)::value;
     if (mode == 0)
       k_deposit<0, R><<<grid, kThreads, 0, st>>>(B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
-                                                 b->W, b->err);
+                                                 W, b->err);
     else if (mode == 1)
       k_deposit<1, R><<<grid, kThreads, 0, st>>>(B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
                                                  nullptr, b->err);
@@ -417,7 +442,7 @@ int launch_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, c
                                                  nullptr, b->err);
     else
       k_deposit<5, R><<<grid, kThreads, 0, st>>>(B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
-                                                 b->W, b->err);
+                                                 W, b->err);
     return 0;
   });
   if (int rc = after_launch(b, "deposit kernel")) return rc;
@@ -443,8 +468,11 @@ int launch_stage(emu_box* b, int s, int dry) {
   return launch_rk(b, s, srow, dry);
 }
 
-// The RK-stage kernel of stage s from the deposit in b->At (traceless) and b->W.
-int launch_rk(emu_box* b, int s, const int* srow, int dry) {
+// The RK-stage kernel of stage s from the shape weights W and the traceless
+// potential At of its deposit; stages 2-4 read their state from stage_src and
+// write the next one to pt.stage.
+int launch_rk_on(emu_box* b, int s, const int* srow, int dry, const Parts& pt, const double* W, const double* At,
+                 const double* stage_src) {
   before_launch(b, CLS_RK);
   by_order(b->S.order, [&](auto O) {
     constexpr int R = decltype(O)::value;
@@ -452,24 +480,25 @@ int launch_rk(emu_box* b, int s, const int* srow, int dry) {
     // tile ends at ring and range boundaries are computed directly); otherwise
     // the halo-lane kernel, which gives bitwise the same results
     const Batch Bv = batch_view(b);
+    const dim3 grid = persist_grid(b);
     if (Bv.U32 < 8 * (int64_t)Bv.nw32) {
       if (b->pot)
-        k_rk_stage<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(Bv, b->pt, b->W, b->dirtab, srow, b->At, s,
-                                                                         dry);
+        k_rk_stage<true, R><<<grid, kThreads, 0, b->stream>>>(Bv, pt, W, b->dirtab, srow, At, stage_src, s, dry);
       else
-        k_rk_stage<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(Bv, b->pt, b->W, b->dirtab, srow, b->At, s,
-                                                                          dry);
+        k_rk_stage<false, R><<<grid, kThreads, 0, b->stream>>>(Bv, pt, W, b->dirtab, srow, At, stage_src, s, dry);
       return 0;
     }
     if (b->pot)
-      k_rk_stage32<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(Bv, b->pt, b->W, b->dirtab, srow, b->At, s,
-                                                                         dry);
+      k_rk_stage32<true, R><<<grid, kThreads, 0, b->stream>>>(Bv, pt, W, b->dirtab, srow, At, stage_src, s, dry);
     else
-      k_rk_stage32<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(Bv, b->pt, b->W, b->dirtab, srow, b->At, s,
-                                                                          dry);
+      k_rk_stage32<false, R><<<grid, kThreads, 0, b->stream>>>(Bv, pt, W, b->dirtab, srow, At, stage_src, s, dry);
     return 0;
   });
   return after_launch(b, "RK stage kernel");
+}
+
+int launch_rk(emu_box* b, int s, const int* srow, int dry) {
+  return launch_rk_on(b, s, srow, dry, b->pt, b->W, b->At, b->pt.stage);
 }
 
 int launch_step(emu_box* b, int dry) {
@@ -973,7 +1002,8 @@ size_t record_doubles(const Shape& S) {
   return (size_t)54 * S.Ptot + 4 * ((size_t)kept_weights(S.order) * S.Ptot + (size_t)kNT * S.NZ);
 }
 
-// One forward step (as launch_step) that also writes its record.
+// One forward step (as launch_step) that also writes its record: the stage
+// kernels write their weights, potentials and next stage states straight into it.
 int record_step(emu_box* b, double* rec) {
   const size_t P = (size_t)b->S.Ptot;
   const size_t nws = (size_t)kept_weights(b->S.order) * P, na = (size_t)kNT * b->S.NZ;
@@ -982,22 +1012,16 @@ int record_step(emu_box* b, double* rec) {
   double* Ar = Wr + 4 * nws;       // potentials of stages 1..4
   if (int rc = launch_shifts(b, kStageFrac, 4)) return rc;
   for (int s = 1; s <= 4; ++s) {
-    const double* rnu = (s == 1) ? b->pt.rho : b->pt.stage;
-    const double* rnb = (s == 1) ? b->pt.rhobar : b->pt.stage + 9 * P;
+    const double* src = s == 1 ? b->pt.stage : Y + (s - 2) * 18 * P;   // y_s (stages 2-4)
+    const double* rnu = (s == 1) ? b->pt.rho : src;
+    const double* rnb = (s == 1) ? b->pt.rhobar : src + 9 * P;
     const int* srow = b->shift + (size_t)(s - 1) * b->S.MT;
-    if (int rc = launch_deposit(b, 5, rnu, rnb, srow, kStageFrac[s - 1], b->At)) return rc;
-    if (nws)
-      if (int rc = cuda_check(b, cudaMemcpyAsync(Wr + (s - 1) * nws, b->W, sizeof(double) * nws,
-                                                 cudaMemcpyDeviceToDevice, b->stream), "record weights"))
-        return rc;
-    if (int rc = cuda_check(b, cudaMemcpyAsync(Ar + (s - 1) * na, b->At, sizeof(double) * na,
-                                               cudaMemcpyDeviceToDevice, b->stream), "record potential"))
-      return rc;
-    if (int rc = launch_rk(b, s, srow, 0)) return rc;
-    if (s < 4)
-      if (int rc = cuda_check(b, cudaMemcpyAsync(Y + (s - 1) * 18 * P, b->pt.stage, sizeof(double) * 18 * P,
-                                                 cudaMemcpyDeviceToDevice, b->stream), "record stage state"))
-        return rc;
+    double* Ws = nws ? Wr + (s - 1) * nws : b->W;   // (order 0 keeps no weights)
+    double* As = Ar + (s - 1) * na;
+    if (int rc = launch_deposit(b, 5, rnu, rnb, srow, kStageFrac[s - 1], As, Ws)) return rc;
+    Parts ps = b->pt;
+    if (s < 4) ps.stage = Y + (s - 1) * 18 * P;   // y_{s+1}
+    if (int rc = launch_rk_on(b, s, srow, 0, ps, Ws, As, src)) return rc;
   }
   return EMU_OK;
 }
@@ -1217,7 +1241,10 @@ int emu_adjoint_record_step(emu_box* b, double dt, void* rec, int64_t rec_bytes)
     return rc;
   if (int rc = set_dts(b, dt != 0.0 ? &dt : b->step_dt.data())) return rc;
   b->next_stage = 1;
-  return record_step(b, (double*)rec);
+  if (b->prof) return record_step(b, (double*)rec);
+  // the graph reads the step sizes from the device: it depends on the buffer only
+  const void* key[6] = {(const void*)1, rec, nullptr, nullptr, nullptr, nullptr};
+  return keyed_graph(b, key, [&] { return record_step(b, (double*)rec); });
 }
 
 int emu_adjoint_step_recorded(emu_box* b, double dt, const void* rec, double* lambda, double* gN, double* gNbar,
@@ -1229,7 +1256,9 @@ int emu_adjoint_step_recorded(emu_box* b, double dt, const void* rec, double* la
   if (!lambda || !gN || !gNbar) return fail(b, EMU_EINVAL, "adjoint step: NULL pointer");
   if (int rc = set_dts(b, dt != 0.0 ? &dt : b->step_dt.data())) return rc;
   b->next_stage = 1;
-  return adjoint_recorded_body(b, (const double*)rec, lambda, gN, gNbar, adj_ws);
+  if (b->prof) return adjoint_recorded_body(b, (const double*)rec, lambda, gN, gNbar, adj_ws);
+  const void* key[6] = {(const void*)2, rec, lambda, gN, gNbar, adj_ws};
+  return keyed_graph(b, key, [&] { return adjoint_recorded_body(b, (const double*)rec, lambda, gN, gNbar, adj_ws); });
 }
 
 int emu_weight_gradient(emu_box* b, const double* gN, const double* gNbar, double* out, int on_host) {

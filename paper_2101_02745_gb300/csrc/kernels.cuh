@@ -693,19 +693,21 @@ __device__ __forceinline__ void rk_particle(const BoxGeo& g, const Parts& pt, co
 // Persistent: each warp walks its contiguous range of units, direction-major
 // within a box (unit = direction * ntiles + tile) so it streams along each
 // ring, and prefetches the next unit's particle data into L2.  The shape
-// weights come from the deposit.
+// weights come from the deposit.  Stages 2-4 read their state from stage_src
+// (normally the stage buffer itself, updated in place; a separate buffer when
+// the stage states are kept for the adjoint).
 template <bool POT, int ORDER>
 __global__ void __launch_bounds__(kThreads, 2)
 k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
-           const int* __restrict__ shift, const double* __restrict__ A, int s, int dry) {
+           const int* __restrict__ shift, const double* __restrict__ A, const double* stage_src, int s, int dry) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   const int64_t u0 = unit_begin(w, B), u1 = unit_begin(w + 1, B);
   if (u0 >= u1) return;
   const int64_t P = B.Ptot;
   const int MT = B.MT, NZ = B.NZ;
-  const double* src_r = (s == 1) ? pt.rho : pt.stage;
-  const double* src_b = (s == 1) ? pt.rhobar : pt.stage + 9 * P;
+  const double* src_r = (s == 1) ? pt.rho : stage_src;
+  const double* src_b = (s == 1) ? pt.rhobar : stage_src + 9 * P;
   // arrays this stage reads, for the prefetch: source (18), y (18, s = 2, 3), acc (18, s >= 2), W (NWS), z (s = 4)
   constexpr int H = Sten<ORDER>::H, T = Sten<ORDER>::T, NWS = Sten<ORDER>::NWS;
   const int nsrc = 18, ny = (s == 2 || s == 3) ? 18 : 0, nacc = (s >= 2) ? 18 : 0;
@@ -801,7 +803,7 @@ __device__ __forceinline__ int ring_wrap(int cell, int nz) {
 template <bool POT, int ORDER>
 __global__ void __launch_bounds__(kThreads, 2)
 k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
-             const int* __restrict__ shift, const double* __restrict__ A, int s, int dry) {
+             const int* __restrict__ shift, const double* __restrict__ A, const double* stage_src, int s, int dry) {
   constexpr int H = Sten<ORDER>::H, NW = Sten<ORDER>::NW;
   __shared__ double gsm[kWarps][2][kNC][kLanes];   // G of the last two units, per warp
   __shared__ double edge[kWarps][2][H][kNC];       // the H cells left / right of the unit being finished
@@ -811,8 +813,8 @@ k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __re
   if (u0 >= u1) return;
   const int64_t P = B.Ptot;
   const int MT = B.MT, NZ = B.NZ;
-  const double* src_r = (s == 1) ? pt.rho : pt.stage;
-  const double* src_b = (s == 1) ? pt.rhobar : pt.stage + 9 * P;
+  const double* src_r = (s == 1) ? pt.rho : stage_src;
+  const double* src_b = (s == 1) ? pt.rhobar : stage_src + 9 * P;
   constexpr int NWS = Sten<ORDER>::NWS;
   const int nsrc = 18, ny = (s == 2 || s == 3) ? 18 : 0, nacc = (s >= 2) ? 18 : 0;
   const int narr = nsrc + ny + nacc + NWS + (s == 4 ? 1 : 0);

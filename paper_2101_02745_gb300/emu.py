@@ -608,11 +608,28 @@ class Box:
         return (emu_batch_adjoint_record_bytes(self.cfgs) + 255) & ~255
 
     def record_buffer(self, nsteps: int):
-        """A device buffer for the records of nsteps steps (256-byte aligned
-        slots); its slot pointers come from record_slot."""
+        """(raw tensor, base pointer, slot stride): device memory for the records
+        of nsteps steps in 256-byte aligned slots.  The box keeps the largest
+        one asked for and hands it out again (the library replays one graph per
+        slot, keyed on its address)."""
         stride = self.record_stride()
-        raw = self.torch.empty(nsteps * stride + 256, dtype=self.torch.uint8, device=self.device)
-        return raw, (raw.data_ptr() + 255) & ~255, stride
+        c = getattr(self, "_rec", None)
+        if c is None or c[3] < nsteps:
+            self._rec = None
+            raw = self.torch.empty(nsteps * stride + 256, dtype=self.torch.uint8, device=self.device)
+            c = self._rec = (raw, (raw.data_ptr() + 255) & ~255, stride, nsteps)
+        return c[:3]
+
+    def adjoint_buffers(self):
+        """(lam (18, P), gN (P,), gNbar (P,)) device buffers kept by the box
+        (the adjoint steps' graphs are keyed on them); gN and gNbar are zeroed."""
+        c = getattr(self, "_adj_bufs", None)
+        if c is None:
+            c = self._adj_bufs = (self._f64(18, self.P), self._f64(self.P), self._f64(self.P))
+        else:
+            c[1].zero_()
+            c[2].zero_()
+        return c
 
     @_ordered
     def adjoint_record_step(self, dt, buf, slot: int):
