@@ -1133,28 +1133,14 @@ __global__ void k_diagnostics(Batch B, const double* __restrict__ mom, double* _
 // Eq. 6, with the shared weights) is symmetric, so its transpose is the same
 // deposit-and-interpolate applied to the adjoint Gamma = dL/dH.
 
-__device__ __forceinline__ void kfull(const double H[9], const double r[9], double out[9]) {
-  double kd[3], ko[6];
-  commutator(H[0] - H[1], H[0] - H[2], H[1] - H[2], H[3], H[4], H[5], H[6], H[7], H[8], r, kd, ko);
-  out[0] = 2.0 * kd[0]; out[1] = 2.0 * kd[1]; out[2] = 2.0 * kd[2];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) out[3 + k] = ko[k];
-}
-
-// kfull with H given by its traceless components (H_11 - H_22, H_22 - H_33, off-diagonal reals).
-__device__ __forceinline__ void kfull_t(const double H[kNC], const double r[9], double out[9]) {
-  double kd[3], ko[6];
-  commutator(H[0], H[0] + H[1], H[1], H[2], H[3], H[4], H[5], H[6], H[7], r, kd, ko);
-  out[0] = 2.0 * kd[0]; out[1] = 2.0 * kd[1]; out[2] = 2.0 * kd[2];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) out[3 + k] = ko[k];
-}
-
 // First adjoint launch of stage s.  m = a lam + c lamn, the adjoint of this
 // stage's derivative k_s, with the box's step dt: a = dt/6 (s = 1, 4) or dt/3,
 // c = dt/2 (s = 1, 2) or dt (s = 3), lamn the adjoint of stage s + 1 (NULL
 // for s = 4); writes lam_out = J_rho^T m (direct terms) and Gam = dL/dH_self.
-// pt.rho / pt.rhobar point at the stage state.
+// pt.rho / pt.rhobar point at the stage state.  The metric D folds into the
+// commutator: D K(X, D^-1 m) is the commutator's raw output (halved diagonal,
+// off-diagonals) for X and m2 = m with its diagonal doubled, so
+//   lam_out = -D K(H, D^-1 m) = raw(-H, m2),   Gamma += S D K(r, D^-1 m) = S raw(r, m2).
 template <bool POT, int ORDER>
 __global__ void __launch_bounds__(kThreads, 2)
 k_adj_a(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
@@ -1195,30 +1181,34 @@ k_adj_a(Batch B, Parts pt, const double* __restrict__ W, const double* __restric
       H[c] = gather<ORDER>(wt, G);
     }
     if (!active) continue;
+    const double a2 = 2.0 * a, bc2 = 2.0 * bc;
     double Gm[9];
 #pragma unroll
     for (int which = 0; which < 2; ++which) {
-      double Hs[kNC], r[9], mh[9], t[9];
+      double nH[kNC], r[9], m2[9], kd[3], ko[6];
 #pragma unroll
-      for (int c = 0; c < kNC; ++c) {
+      for (int c = 0; c < kNC; ++c) {                                       // -(S H + V), S for antineutrinos
         const bool im = (c == 3 || c == 5 || c == 7);
-        const double sgn = which ? (im ? 1.0 : -1.0) : 1.0;                 // S for antineutrinos
-        Hs[c] = sgn * H[c] + (POT ? __ldg((which ? g.vnubar : g.vnu) + c) : 0.0);
+        const double nsgn = which ? (im ? -1.0 : 1.0) : -1.0;
+        nH[c] = nsgn * H[c] - (POT ? __ldg((which ? g.vnubar : g.vnu) + c) : 0.0);
       }
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
-        const double mk = a * lam[(which * 9 + k) * P + p] + (lamn ? bc * lamn[(which * 9 + k) * P + p] : 0.0);
-        mh[k] = k < 3 ? mk : 0.5 * mk;                                      // D^-1 m
+        const double l = lam[(which * 9 + k) * P + p];
+        const double ln = lamn ? lamn[(which * 9 + k) * P + p] : 0.0;
+        m2[k] = k < 3 ? fma(a2, l, bc2 * ln) : fma(a, l, bc * ln);
         r[k] = (which ? pt.rhobar : pt.rho)[k * P + p];
       }
-      kfull_t(Hs, mh, t);                                                   // direct term: -D K(H, D^-1 m)
+      commutator(nH[0], nH[0] + nH[1], nH[1], nH[2], nH[3], nH[4], nH[5], nH[6], nH[7], m2, kd, ko);
 #pragma unroll
-      for (int k = 0; k < 9; ++k) lam_out[(which * 9 + k) * P + p] = -(k < 3 ? t[k] : 2.0 * t[k]);
-      kfull(r, mh, t);                                                      // Gamma: D K(r, D^-1 m) (times S)
+      for (int k = 0; k < 3; ++k) lam_out[(which * 9 + k) * P + p] = kd[k];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) lam_out[(which * 9 + 3 + k) * P + p] = ko[k];
+      commutator(r[0] - r[1], r[0] - r[2], r[1] - r[2], r[3], r[4], r[5], r[6], r[7], r[8], m2, kd, ko);
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         const bool im = (k == 4 || k == 6 || k == 8);
-        const double v = k < 3 ? t[k] : 2.0 * t[k];
+        const double v = k < 3 ? kd[k] : ko[k - 3];
         if (which == 0) Gm[k] = v;
         else Gm[k] += (im ? v : -v);
       }
