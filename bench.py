@@ -334,7 +334,9 @@ def run_gpu(args, rank, world, local_rank):
         E.emu_step(box.box, 1, dt)
         E.emu_diagnostics(box.box, diag.data_ptr(), 1)
 
-    # the host link's copy rate alone (the e2e step cannot beat the copy of its inputs)
+    # the host link's copy rate alone (the e2e step cannot beat the copy of its
+    # inputs), timed on the second copy (the first touches the pinned pages)
+    feed.prefetch()
     c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(device)
     c0.record(feed.copy)
@@ -407,6 +409,7 @@ def run_gpu(args, rank, world, local_rank):
     if not args.no_extras:
         extras["batched"] = measure_sweep(args, dist, device, rank, world, min(args.steps, 20))
         extras["adjoint"] = measure_adjoint(dist, device, world, reps=1)
+        extras["paper_shape"] = measure_paper_shape(args, dist, device, world)
     if rank == 0:
         line.update(extras)
         if world == 1 and not args.no_cpu_baseline:
@@ -415,6 +418,38 @@ def run_gpu(args, rank, world, local_rank):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def measure_paper_shape(args, dist, device, world, steps=100):
+    """The paper's 1D run shape (1024 cells x 378 directions, 387,072 particles;
+    the nubar flux along z, and tilted to normalize(0.1, 0, -1)): `steps` steps
+    of each box on its autotuned grid, CUDA events on the box's stream.  The
+    particle state (186 MB) is larger than L2."""
+    import torch
+
+    from paper_2101_02745_gb300 import emu as E
+    from paper_2101_02745_gb300 import workloads as W
+
+    out = {}
+    for wl in (W.paper_1d(), W.paper_1d(True)):
+        box = E.Box.from_workload(wl, device=device)
+        dt = box.timestep()
+        choice, cand_ms = box.autotune(trial_steps=2)
+        box.step(args.warmup, dt)
+        barrier(dist, device)
+        torch.cuda.synchronize(device)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(box.stream)
+        box.step(steps, dt)
+        ev1.record(box.stream)
+        torch.cuda.synchronize(device)
+        ms = max_over_ranks(dist, ev0.elapsed_time(ev1), device)
+        box.sync()
+        out[wl.name] = {"particles_per_gpu": wl.P, "steps": steps, "value": world * wl.P * steps / (ms * 1e-3),
+                        "ms_per_step": ms / steps, "autotune_choice": choice, "autotune_ms": list(cand_ms)}
+        del box
+    torch.cuda.empty_cache()
+    return out
 
 
 def measure_sweep(args, dist, device, rank, world, steps):
