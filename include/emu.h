@@ -236,21 +236,29 @@ int emu_batch_diagnostics(emu_box* box, double* out, int on_host);
 
 /* Autotuner: times trial_steps steps of each candidate launch configuration
  * of the step kernels (grids of 304, 152 or 608 blocks of 256 threads, whose
- * warps split the work) without changing the particle state (the trial steps
- * write their results into the RK scratch), keeps the fastest for later
- * steps, and reports its index (0..2) in *choice_out and the per-step times
- * [ms] of the three candidates in ms_out[3] (either may be NULL).  The
- * deposit's summation order depends on the choice, so results are bitwise
- * reproducible for a fixed choice.  Synchronises. */
+ * warps split the work, each with the RK stage in its halo-lane or its
+ * 32-cell form) without changing the particle state (the trial steps write
+ * their results into the RK scratch), keeps the fastest for later steps, and
+ * reports its index c (0..5: grid c / 2, form c % 2, 1 = 32-cell) in
+ * *choice_out and the per-step times [ms] of the six candidates in ms_out[6]
+ * (either may be NULL).  The deposit's summation order depends on the grid,
+ * so results are bitwise reproducible for a fixed choice; the two RK forms
+ * give bitwise the same results.  Synchronises. */
 int emu_autotune(emu_box* box, int trial_steps, int32_t* choice_out, double* ms_out);
+
+/* Form of the RK stage kernel: 1 = 32 cells per warp, 0 = the halo-lane form
+ * (both give bitwise the same results), -1 = chosen by units per warp (the
+ * default; emu_autotune and emu_set_grid set it too).  Errors: EMU_EINVAL. */
+int emu_set_rk_form(emu_box* box, int32_t form);
 
 /* Set the grid of the step kernels to `blocks` blocks of 256 threads (1..608;
  * the default is 304, two per SM; emu_autotune picks among 152, 304 and 608),
  * for callers that share the GPU with other work.  The blocks' warps split the
  * work, so the choice changes the deposit's summation order (results stay
- * bitwise reproducible for a fixed choice) and, for shape orders 0-2, whether
- * the RK stage runs with 32 cells per warp (every warp walking at least 8
- * units) or the halo-lane form (the same results).  Errors: EMU_EINVAL. */
+ * bitwise reproducible for a fixed choice) and whether the RK stage runs with
+ * 32 cells per warp (every warp walking at least 8 units) or the halo-lane
+ * form (the same results); it drops the RK form emu_autotune chose.  Errors:
+ * EMU_EINVAL. */
 int emu_set_grid(emu_box* box, int32_t blocks);
 
 /* Vacuum and matter terms of Eq. 2 (Sec. 2.1): masses m_i c^2 [eV], the mixing

@@ -175,6 +175,7 @@ struct emu_box {
          *W = nullptr, *dirtab = nullptr, *species = nullptr, *dirs = nullptr, *diag = nullptr, *scalar = nullptr;
   int *err = nullptr, *shift = nullptr;
   int blocks = kPersistBlocks;  // grid of the step kernels (autotuned); its warps split the units
+  int rk_form = -1;             // RK stage: 0 halo-lane, 1 32-cell, -1 by units per warp (autotuned)
   bool pot = false;             // some box has vacuum or matter terms
   int next_stage = 1;
   std::vector<double> dt_h;  // step sizes currently on the device
@@ -481,7 +482,8 @@ int launch_rk_on(emu_box* b, int s, const int* srow, int dry, const Parts& pt, c
     // the halo-lane kernel, which gives bitwise the same results
     const Batch Bv = batch_view(b);
     const dim3 grid = persist_grid(b);
-    if (Bv.U32 < 8 * (int64_t)Bv.nw32) {
+    const bool use32 = b->rk_form >= 0 ? b->rk_form == 1 : Bv.U32 >= 8 * (int64_t)Bv.nw32;
+    if (!use32) {
       if (b->pot)
         k_rk_stage<true, R><<<grid, kThreads, 0, b->stream>>>(Bv, pt, W, b->dirtab, srow, At, stage_src, s, dry);
       else
@@ -880,6 +882,16 @@ int emu_set_grid(emu_box* b, int32_t blocks) {
   if (blocks < 1 || blocks > kMaxBlocks) return fail(b, EMU_EINVAL, "blocks must be in 1..%d", kMaxBlocks);
   if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
   b->blocks = blocks;
+  b->rk_form = -1;
+  invalidate_graph(b);
+  return EMU_OK;
+}
+
+int emu_set_rk_form(emu_box* b, int32_t form) {
+  if (int rc = check_bound(b)) return rc;
+  if (form < -1 || form > 1) return fail(b, EMU_EINVAL, "form must be -1, 0 or 1");
+  if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
+  b->rk_form = form;
   invalidate_graph(b);
   return EMU_OK;
 }
@@ -898,8 +910,9 @@ int emu_autotune(emu_box* b, int trial_steps, int32_t* choice_out, double* ms_ou
   int best = 0;
   float best_ms = 0.f;
   int rc = EMU_OK;
-  for (int c = 0; c < 3 && rc == EMU_OK; ++c) {
-    b->blocks = cand[c];
+  for (int c = 0; c < 6 && rc == EMU_OK; ++c) {   // candidate c: grid c / 2, RK form c % 2
+    b->blocks = cand[c / 2];
+    b->rk_form = c % 2;
     rc = launch_step(b, 1);  // warm-up (dry: the particle state is left as it was)
     if (rc) break;
     cudaEventRecord(e0, b->stream);
@@ -916,7 +929,8 @@ int emu_autotune(emu_box* b, int trial_steps, int32_t* choice_out, double* ms_ou
   b->pool.push_back(e0);
   b->pool.push_back(e1);
   b->prof = prof;
-  b->blocks = cand[best];
+  b->blocks = cand[best / 2];
+  b->rk_form = best % 2;
   invalidate_graph(b);
   if (rc) return rc;
   if (choice_out) *choice_out = best;

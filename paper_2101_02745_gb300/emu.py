@@ -107,6 +107,7 @@ def load(build_if_missing: bool = False):
         "emu_batch_diagnostics": (i32, [vp, vp, i32]),
         "emu_autotune": (i32, [vp, i32, vp, vp]),
         "emu_set_grid": (i32, [vp, ctypes.c_int32]),
+        "emu_set_rk_form": (i32, [vp, ctypes.c_int32]),
         "emu_set_oscillation": (i32, [vp, ctypes.c_int32, ctypes.POINTER(emu_oscillation)]),
         "emu_adjoint_workspace_bytes": (i64, [cfgp]),
         "emu_batch_adjoint_workspace_bytes": (i64, [cfgp, ctypes.c_int32]),
@@ -305,15 +306,19 @@ def emu_batch_diagnostics(box, out, on_host: int):
 
 
 def emu_autotune(box, trial_steps: int):
-    """(choice index, per-step ms of the 3 candidate grids)."""
+    """(choice index, per-step ms of the 6 candidates: grid index // 2, RK form % 2)."""
     choice = ctypes.c_int32()
-    ms = np.zeros(3)
+    ms = np.zeros(6)
     _check(box, load().emu_autotune(box, int(trial_steps), ctypes.byref(choice), _host_ptr(ms)))
     return int(choice.value), ms
 
 
 def emu_set_grid(box, blocks: int):
     _check(box, load().emu_set_grid(box, int(blocks)))
+
+
+def emu_set_rk_form(box, form: int):
+    _check(box, load().emu_set_rk_form(box, int(form)))
 
 
 def make_oscillation(d: dict) -> emu_oscillation:
@@ -555,6 +560,10 @@ class Box:
 
     def set_grid(self, blocks: int):
         emu_set_grid(self.box, blocks)
+
+    def set_rk_form(self, form: int):
+        """1: RK stage with 32 cells per warp, 0: halo-lane form, -1: by units per warp."""
+        emu_set_rk_form(self.box, form)
 
     @_ordered
     def set_oscillation(self, osc, box=-1):

@@ -125,3 +125,38 @@ def test_set_grid_validation(torch):
             box.set_grid(bad)
     box.set_grid(608)
     box.sync()
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_rk32_with_few_units_per_warp(torch, order):
+    """The 32-cell form forced on the default grid, where warps walk one unit or
+    none (every tile end computed directly): parity with the oracle and bitwise
+    the halo-lane form's results."""
+    from paper_2101_02745_gb300.emu import Box
+    wl = W.with_shape(W.random_box(67, 30, seed=13), order)
+    out = []
+    for form in (1, 0):
+        box = Box.from_workload(wl)
+        box.set_rk_form(form)
+        dt = 0.917 * box.timestep()
+        box.step(10, dt)
+        out.append(box.get_host())
+        box.sync()
+    for k in ("rho", "rhobar", "z"):
+        assert np.array_equal(out[0][k], out[1][k]), k
+    cfg = O.config(wl.nz, wl.ndir, wl.Lz, wl.kappa, wl.c_light, wl.cfl_adv, wl.cfl_flavor, wl.area,
+                   shape_order=order)
+    parts = O.init(cfg, wl.n_nu, wl.n_nubar, wl.f_nu, wl.f_nubar, wl.alpha, wl.seed, wl.dirs)
+    O.run(cfg, parts, dt, 10)
+    assert family_err(out[0]["rho"], pack(parts["rho"])) < 1e-10
+    assert family_err(out[0]["rhobar"], pack(parts["rhobar"])) < 1e-10
+
+
+def test_set_rk_form_validation(torch):
+    from paper_2101_02745_gb300.emu import Box, EmuError
+    box = Box.from_workload(W.random_box(20, 4, seed=1))
+    for bad in (-2, 2):
+        with pytest.raises(EmuError):
+            box.set_rk_form(bad)
+    box.set_rk_form(-1)
+    box.sync()
