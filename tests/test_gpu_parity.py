@@ -275,9 +275,12 @@ def test_bad_calls_are_rejected(torch):
 
 # ------------------------------------------------------------ full sizes ---
 
-def test_paper_1d_full_size_first_step(torch):
-    """The paper's 1D run shape (1024 cells x 378 directions): init, deposit,
-    and one full RK4 step against the oracle on all 387,072 particles."""
+def test_paper_1d_full_size_50_steps(torch):
+    """The paper's 1D run shape (1024 cells x 378 directions, the tilted nubar
+    flux): init and deposit, then every one of the first 50 RK4 steps against
+    the oracle on all 387,072 particles, in the launch configuration the
+    benchmark picks for this shape (autotuned): rho, rhobar and every grid
+    moment within 1e-10 (family-wise relative), positions within 1e-13 Lz."""
     wl = W.paper_1d(asymmetric=True)
     box = _box(wl)
     cfg = _cfg(wl)
@@ -288,12 +291,19 @@ def test_paper_1d_full_size_first_step(torch):
     A = box.deposit(0, 0.0).cpu().numpy()
     assert _potential_err(A, grid, wl.kappa) < 1e-12
     dt = O.timestep(cfg, grid)
-    box.step(1, dt)
-    O.rk4_step(cfg, parts, dt)
-    h = box.get_host()
-    assert max(_state_errs(h, parts)) < 1e-12
-    assert max(_moment_errs(box, cfg, parts)) < 1e-12
+    box.timestep()
+    box.autotune(trial_steps=1)
+    worst = 0.0
+    for n in range(50):
+        box.step(1, dt)
+        O.rk4_step(cfg, parts, dt)
+        h = box.get_host()
+        errs = list(_state_errs(h, parts)) + _moment_errs(box, cfg, parts)
+        worst = max(worst, max(errs))
+        assert max(errs) < 1e-10, (n, errs)
+        assert np.abs(h["z"] - parts["z"]).max() <= 1e-13 * wl.Lz
     box.sync()
+    print(f"{wl.name}: worst family error over 50 steps {worst:.2e}")
 
 
 def test_throughput_full_size_sampled(torch):
