@@ -320,31 +320,35 @@ def run_gpu(args, rank, world, local_rank):
     value = world * wl.P * args.steps / (t_ms * 1e-3)
 
     # ---- end to end through the public API with host buffers: every step the
-    # state (z, rho, rhobar) comes from pinned host memory (the next step's copy
-    # overlaps the current step on a side stream, E.HostFeed) and the step's
-    # diagnostics are read back to the host
+    # state (z, rho, rhobar) comes from pinned host memory and the step's
+    # diagnostics are read back to the host.  Two boxes take turns
+    # (E.PingPongFeed): the next step's host-to-device copy goes straight into
+    # the idle box's arrays on a side stream while the other box steps.
     host = box.get_host()
     pin = {k: torch.from_numpy(host[k]).pin_memory() for k in ("z", "rho", "rhobar")}
     diag = torch.zeros(E.N_DIAG, dtype=torch.float64).pin_memory()
-    feed = E.HostFeed(box, pin)
+    box2 = E.Box.from_workload(wl, device=device)
+    if args.osc:
+        box2.set_oscillation(W.oscillation(**OSC_BENCH))
+    feed = E.PingPongFeed([box, box2], pin)
 
     def e2e_step():
-        feed.load()
-        feed.prefetch()
-        E.emu_step(box.box, 1, dt)
-        E.emu_diagnostics(box.box, diag.data_ptr(), 1)
+        b = feed.next_box()
+        E.emu_step(b.box, 1, dt)
+        E.emu_diagnostics(b.box, diag.data_ptr(), 1)
 
     # the host link's copy rate alone (the e2e step cannot beat the copy of its
     # inputs), timed on the second copy (the first touches the pinned pages)
-    feed.prefetch()
+    feed.prefetch(1)
     c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(device)
     c0.record(feed.copy)
-    feed.prefetch()
+    feed.prefetch(0)
     c1.record(feed.copy)
     torch.cuda.synchronize(device)
     h2d_gbs = feed.h2d_bytes / (c0.elapsed_time(c1) * 1e-3) / 1e9
     e2e_step()
+    e2e_step()   # both boxes have captured their step graphs
     barrier(dist, device)
     torch.cuda.synchronize(device)
     t0 = time.perf_counter()
@@ -354,10 +358,11 @@ def run_gpu(args, rank, world, local_rank):
     e2e_s = max_over_ranks(dist, time.perf_counter() - t0, device)
     clk = clocks.stop()
     box.sync()
+    box2.sync()
     e2e_value = world * wl.P * args.steps / e2e_s
     h2d = feed.h2d_bytes
     d2h = E.N_DIAG * 8
-    del feed
+    del feed, box2
 
     # ---- roofline of the dominant kernel from the live per-launch events
     per = {k: (ms / n if n else 0.0, n, ms) for k, (ms, n) in ktimes.items()}

@@ -727,3 +727,47 @@ class HostFeed:
         self.consumed = torch.cuda.Event()
         self.consumed.record(self.box.stream)
 
+
+
+class PingPongFeed:
+    """Per-step particle state from pinned host memory for two boxes of one
+    configuration that take turns.  While one box steps, the next step's state
+    (z, rho, rhobar) is copied from the host straight into the other box's
+    particle arrays on a side stream, so nothing is installed on the device
+    between steps.  `next_box()` returns the box whose state is loaded for this
+    step (its stream waits for that copy) and starts the copy for the
+    following step into the other box."""
+
+    KEYS = ("z", "rho", "rhobar")
+
+    def __init__(self, boxes, pinned: dict):
+        if len(boxes) != 2 or boxes[0].P != boxes[1].P:
+            raise ValueError("two boxes of the same configuration")
+        torch = boxes[0].torch
+        self.boxes = list(boxes)
+        self.pinned = {k: pinned[k] for k in self.KEYS}
+        self.copy = torch.cuda.Stream(boxes[0].device)
+        self.ready = [torch.cuda.Event(), torch.cuda.Event()]
+        self.turn = 0
+
+    @property
+    def h2d_bytes(self) -> int:
+        return sum(v.numel() * v.element_size() for v in self.pinned.values())
+
+    def prefetch(self, k: int):
+        """Copy the host state into box k's arrays once box k is done with them."""
+        torch = self.boxes[0].torch
+        b = self.boxes[k]
+        self.copy.wait_stream(b.stream)
+        with torch.cuda.stream(self.copy):
+            for key in self.KEYS:
+                b.t[key].copy_(self.pinned[key], non_blocking=True)
+        self.ready[k].record(self.copy)
+
+    def next_box(self) -> "Box":
+        k = self.turn % 2
+        b = self.boxes[k]
+        b.stream.wait_event(self.ready[k])
+        self.prefetch(1 - k)
+        self.turn += 1
+        return b

@@ -341,3 +341,19 @@ def test_record_bad_calls():
     E.emu_adjoint_record_step(box.box, 3e-12, base, n)
     E.emu_adjoint_step_recorded(box.box, 3e-12, base, lam.data_ptr(), gN.data_ptr(), gNb.data_ptr(), ptr, m)
     box.sync()
+
+
+def test_recorded_adjoint_graph_cache_eviction():
+    """One segment of 140 recorded steps needs 280 step graphs, more than the
+    256 a box keeps: the oldest are dropped and recaptured, and the gradient
+    still equals the recomputing backward's bit for bit (twice, so the second
+    pass replays the cache the first one left)."""
+    wl = W.adjoint_box(nz=16, ndir=8, steps=140)
+    box = Box.from_workload(wl, init=False)
+    parts = [torch.tensor(a, dtype=torch.float64, device="cuda") for a in (wl.n_nu, wl.n_nubar, wl.f_nu, wl.f_nubar)]
+    mk = lambda rec: Simulation(box, wl.steps, 3.4e-12, every=140, alpha=wl.alpha, seed=wl.seed, record=rec)
+    ref = _grads(mk(False), parts)
+    for _ in range(2):
+        got = _grads(mk(True), parts)
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b), np.abs(a - b).max()
