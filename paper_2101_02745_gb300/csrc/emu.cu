@@ -402,12 +402,31 @@ int set_dts(emu_box* b, const double* dt) {
                                        cudaMemcpyHostToDevice, b->stream), "upload step sizes");
 }
 
+// Launch with programmatic dependent launch: the kernel's blocks may be
+// scheduled while the previous kernel of the stream drains; the step kernels
+// begin with griddepcontrol.wait, so they touch memory only once it is done.
+// A failed launch is left for after_launch's cudaGetLastError.
+template <typename... KArgs, typename... Args>
+void pdl(cudaStream_t st, void (*kernel)(KArgs...), dim3 grid, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  (void)cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 int launch_shifts(emu_box* b, const double* fracs, int nrows) {
   Fracs f{};
   for (int s = 0; s < nrows; ++s) f.v[s] = fracs[s];
   const int blocks = (b->S.MT + kThreads - 1) / kThreads;
   before_launch(b, CLS_SHIFT);
-  k_shifts<<<blocks, kThreads, 0, b->stream>>>(batch_view(b), b->pt.z, b->dirtab, f, nrows, b->shift);
+  pdl(b->stream, k_shifts, dim3(blocks), batch_view(b), b->pt.z, b->dirtab, f, nrows, b->shift);
   return after_launch(b, "shift kernel");
 }
 
@@ -427,23 +446,23 @@ int launch_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, c
   by_order(b->S.order, [&](auto O) {
     constexpr int R = decltype(O)::value;
     if (mode == 0)
-      k_deposit<0, R><<<grid, kThreads, 0, st>>>(B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
-                                                 W, b->err);
+      pdl(st, k_deposit<0, R>, grid, B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
+          W, b->err);
     else if (mode == 1)
-      k_deposit<1, R><<<grid, kThreads, 0, st>>>(B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
-                                                 nullptr, b->err);
+      pdl(st, k_deposit<1, R>, grid, B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
+          nullptr, b->err);
     else if (mode == 2)
-      k_deposit<2, R><<<grid, kThreads, 0, st>>>(B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
-                                                 nullptr, b->err);
+      pdl(st, k_deposit<2, R>, grid, B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
+          nullptr, b->err);
     else if (mode == 3)
-      k_deposit<3, R><<<grid, kThreads, 0, st>>>(B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
-                                                 nullptr, b->err);
+      pdl(st, k_deposit<3, R>, grid, B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
+          nullptr, b->err);
     else if (mode == 4)
-      k_deposit<4, R><<<grid, kThreads, 0, st>>>(B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
-                                                 nullptr, b->err);
+      pdl(st, k_deposit<4, R>, grid, B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
+          nullptr, b->err);
     else
-      k_deposit<5, R><<<grid, kThreads, 0, st>>>(B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
-                                                 W, b->err);
+      pdl(st, k_deposit<5, R>, grid, B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
+          W, b->err);
     return 0;
   });
   if (int rc = after_launch(b, "deposit kernel")) return rc;
@@ -451,8 +470,8 @@ int launch_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, c
   const int split = combine_split(b->S, B.nw);
   const int rows = mode == 5 ? kNT : kNA;
   const int potential = (mode == 0 || mode == 3 || mode == 5) ? 1 : 0;
-  k_combine<<<combine_blocks(rows, B.NZ, split), kThreads, 0, b->stream>>>(B, b->partial, out, rows, potential,
-                                                                          split, b->err);
+  pdl(b->stream, k_combine, dim3(combine_blocks(rows, B.NZ, split)), B, b->partial, out, rows, potential,
+      split, b->err);
   return after_launch(b, "deposit combine kernel");
 }
 
@@ -485,15 +504,15 @@ int launch_rk_on(emu_box* b, int s, const int* srow, int dry, const Parts& pt, c
     const bool use32 = b->rk_form >= 0 ? b->rk_form == 1 : Bv.U32 >= 8 * (int64_t)Bv.nw32;
     if (!use32) {
       if (b->pot)
-        k_rk_stage<true, R><<<grid, kThreads, 0, b->stream>>>(Bv, pt, W, b->dirtab, srow, At, stage_src, s, dry);
+        pdl(b->stream, k_rk_stage<true, R>, grid, Bv, pt, W, b->dirtab, srow, At, stage_src, s, dry);
       else
-        k_rk_stage<false, R><<<grid, kThreads, 0, b->stream>>>(Bv, pt, W, b->dirtab, srow, At, stage_src, s, dry);
+        pdl(b->stream, k_rk_stage<false, R>, grid, Bv, pt, W, b->dirtab, srow, At, stage_src, s, dry);
       return 0;
     }
     if (b->pot)
-      k_rk_stage32<true, R><<<grid, kThreads, 0, b->stream>>>(Bv, pt, W, b->dirtab, srow, At, stage_src, s, dry);
+      pdl(b->stream, k_rk_stage32<true, R>, grid, Bv, pt, W, b->dirtab, srow, At, stage_src, s, dry);
     else
-      k_rk_stage32<false, R><<<grid, kThreads, 0, b->stream>>>(Bv, pt, W, b->dirtab, srow, At, stage_src, s, dry);
+      pdl(b->stream, k_rk_stage32<false, R>, grid, Bv, pt, W, b->dirtab, srow, At, stage_src, s, dry);
     return 0;
   });
   return after_launch(b, "RK stage kernel");
@@ -1071,19 +1090,19 @@ int adjoint_recorded_body(emu_box* b, const double* rec, double* lambda, double*
     by_order(b->S.order, [&](auto O) {
       constexpr int R = decltype(O)::value;
       if (b->pot)
-        k_adj_a<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, Ws, b->dirtab, srow, Hs, lambda,
-                                                                      Lnext, s, Lcur, b->pt.acc);
+        pdl(b->stream, k_adj_a<true, R>, persist_grid(b), B, ps, Ws, b->dirtab, srow, Hs, lambda,
+            Lnext, s, Lcur, b->pt.acc);
       else
-        k_adj_a<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, Ws, b->dirtab, srow, Hs, lambda,
-                                                                       Lnext, s, Lcur, b->pt.acc);
+        pdl(b->stream, k_adj_a<false, R>, persist_grid(b), B, ps, Ws, b->dirtab, srow, Hs, lambda,
+            Lnext, s, Lcur, b->pt.acc);
       return 0;
     });
     if (int rc = after_launch(b, "adjoint stage kernel")) return rc;
     if (int rc = launch_deposit(b, 3, b->pt.acc, nullptr, srow, kStageFrac[s - 1], b->mom)) return rc;
     before_launch(b, CLS_OTHER);
     by_order(b->S.order, [&](auto O) {
-      k_adj_b<decltype(O)::value><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, Ws, b->dirtab, srow, b->mom,
-                                                                              Lcur, Lt, gN, gNbar);
+      pdl(b->stream, k_adj_b<decltype(O)::value>, persist_grid(b), B, ps, Ws, b->dirtab, srow, b->mom,
+          Lcur, Lt, gN, gNbar);
       return 0;
     });
     if (int rc = after_launch(b, "adjoint interpolation kernel")) return rc;
@@ -1146,19 +1165,19 @@ int adjoint_body(emu_box* b, double* lambda, double* gN, double* gNbar, void* ad
     by_order(b->S.order, [&](auto O) {
       constexpr int R = decltype(O)::value;
       if (b->pot)
-        k_adj_a<true, R><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, Ws, b->dirtab, srow, Hs, lambda,
-                                                                      Lnext, s, Lcur, b->pt.acc);
+        pdl(b->stream, k_adj_a<true, R>, persist_grid(b), B, ps, Ws, b->dirtab, srow, Hs, lambda,
+            Lnext, s, Lcur, b->pt.acc);
       else
-        k_adj_a<false, R><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, Ws, b->dirtab, srow, Hs, lambda,
-                                                                       Lnext, s, Lcur, b->pt.acc);
+        pdl(b->stream, k_adj_a<false, R>, persist_grid(b), B, ps, Ws, b->dirtab, srow, Hs, lambda,
+            Lnext, s, Lcur, b->pt.acc);
       return 0;
     });
     if (int rc = after_launch(b, "adjoint stage kernel")) return rc;
     if (int rc = launch_deposit(b, 3, b->pt.acc, nullptr, srow, frac, b->mom)) return rc;
     before_launch(b, CLS_OTHER);
     by_order(b->S.order, [&](auto O) {
-      k_adj_b<decltype(O)::value><<<persist_grid(b), kThreads, 0, b->stream>>>(B, ps, Ws, b->dirtab, srow, b->mom,
-                                                                              Lcur, Lt, gN, gNbar);
+      pdl(b->stream, k_adj_b<decltype(O)::value>, persist_grid(b), B, ps, Ws, b->dirtab, srow, b->mom,
+          Lcur, Lt, gN, gNbar);
       return 0;
     });
     if (int rc = after_launch(b, "adjoint interpolation kernel")) return rc;

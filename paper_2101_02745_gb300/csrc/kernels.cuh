@@ -108,6 +108,12 @@ struct Parts {
 
 // ------------------------------------------------------------ device helpers
 
+// The step kernels are launched with programmatic dependent launch: their
+// blocks may be scheduled while the previous kernel of the stream drains.  Each
+// calls this first, before any memory access: it returns once the previous
+// kernel has completed and its writes are visible (at once without one).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ int wrapc(int j, int nz) {
   int r = j % nz;
   return r < 0 ? r + nz : r;
@@ -358,6 +364,7 @@ struct Fracs { double v[4]; };
 
 __global__ void k_shifts(Batch B, const double* __restrict__ z, const double* __restrict__ dirtab, Fracs fr,
                          int nrows, int* __restrict__ shift) {
+  griddep_wait();
   const int gd = blockIdx.x * blockDim.x + threadIdx.x;
   if (gd >= B.MT) return;
   const int b = box_of_direction(B, gd);
@@ -405,6 +412,7 @@ k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, c
           const double* __restrict__ r_nu, const double* __restrict__ r_nb, const double* __restrict__ dirtab,
           const int* __restrict__ shift, double frac, double* __restrict__ partial, double* __restrict__ W,
           int* __restrict__ err) {
+  griddep_wait();
   const int lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   const int64_t u0 = unit_begin(w, B), u1 = unit_begin(w + 1, B);
@@ -521,6 +529,7 @@ k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, c
 // are bitwise reproducible.
 __global__ void k_combine(Batch B, const double* __restrict__ partial, double* __restrict__ out, int rows,
                           int potential, int split, int* __restrict__ err) {
+  griddep_wait();
   __shared__ double sums[kWarps][kLanes];
   const int64_t n = (int64_t)rows * B.NZ;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -700,6 +709,7 @@ template <bool POT, int ORDER>
 __global__ void __launch_bounds__(kThreads, 2)
 k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
            const int* __restrict__ shift, const double* __restrict__ A, const double* stage_src, int s, int dry) {
+  griddep_wait();
   const int lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   const int64_t u0 = unit_begin(w, B), u1 = unit_begin(w + 1, B);
@@ -804,6 +814,7 @@ template <bool POT, int ORDER>
 __global__ void __launch_bounds__(kThreads, 2)
 k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
              const int* __restrict__ shift, const double* __restrict__ A, const double* stage_src, int s, int dry) {
+  griddep_wait();
   constexpr int H = Sten<ORDER>::H, NW = Sten<ORDER>::NW;
   __shared__ double gsm[kWarps][2][kNC][kLanes];   // G of the last two units, per warp
   __shared__ double edge[kWarps][2][H][kNC];       // the H cells left / right of the unit being finished
@@ -1146,6 +1157,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 k_adj_a(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
         const int* __restrict__ shift, const double* __restrict__ A, const double* __restrict__ lam,
         const double* __restrict__ lamn, int s, double* __restrict__ lam_out, double* __restrict__ Gam) {
+  griddep_wait();
   const int lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   const int64_t u0 = unit_begin(w, B), u1 = unit_begin(w + 1, B);
@@ -1227,6 +1239,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 k_adj_b(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
         const int* __restrict__ shift, const double* __restrict__ E, double* __restrict__ lam_out,
         double* __restrict__ lam_tot, double* __restrict__ gN, double* __restrict__ gNbar) {
+  griddep_wait();
   const int lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   const int64_t u0 = unit_begin(w, B), u1 = unit_begin(w + 1, B);
