@@ -7,7 +7,8 @@
 //   particles: box b occupies [poff_b, poff_b + nz_b * ndir_b) of every SoA array;
 //              particle (d, i) of box b is poff_b + d * nz_b + i; component k of a
 //              matrix array at [k * Ptot + particle]
-//   grid:      cell j of box b is column coff_b + j of A[36][NZ] and mom[72][NZ]
+//   grid:      cell j of box b is column coff_b + j of A[36][NZ] (the full
+//              potential), At[32][NZ] (the step's traceless potential) and mom[72][NZ]
 //   tables:    direction d of box b is entry doff_b + d of the per-direction tables
 //
 // Parallel layout.  Work is split into *units* = (one tile of T cells, one
@@ -20,7 +21,9 @@
 // the particles of one direction (a ring) translate rigidly (one per cell at a
 // common offset, Sec. 3.1 and Eq. 4), the particle on cell j is ring entry
 // (j - shift_d) mod nz and its stencil neighbours sit on the adjacent lanes:
-// deposit (Eq. 5) and interpolation (Eq. 6) are warp-shuffle gathers.
+// deposit (Eq. 5) and interpolation (Eq. 6) are warp-shuffle gathers.  The
+// RK stage also has a form without halo lanes (k_rk_stage32: 32-cell tiles,
+// the tile ends through shared memory).
 //
 // Persistent schedule.  The step kernels run a fixed grid (2 blocks of 8 warps
 // per SM); the first nw warps split the U units of the batch into equal
