@@ -52,6 +52,8 @@ FLOPS_DEPOSIT = 137
 # -40 / +32 (+8 for the cubic weights); the vacuum and matter terms add 16 adds.
 TAPS_DELTA = {0: -40, 1: 0, 2: 0, 3: 32}
 WEIGHTS_DELTA = {0: -12, 1: -6, 2: 0, 3: 8}
+# Grids the autotuner tries (blocks of 256 threads), in the order of its choice index // 2.
+AUTOTUNE_GRIDS = (304, 152, 608)
 # FP64 pipe: 2 DFMA per clock per SM (nominal 1.25 TFLOP/s / (2 flop x 152 SMs x 2.07 GHz) = 1.99),
 # so peak = 2 x 2 flop x 152 SMs x 2.07 GHz.
 PEAK_FP64_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
@@ -295,6 +297,8 @@ def run_gpu(args, rank, world, local_rank):
         box.set_oscillation(W.oscillation(**OSC_BENCH))
     stream = box.stream
     dt = box.timestep()
+    # launch configuration: grid x RK-stage form, timed on dry steps (state untouched)
+    tune_choice, tune_ms = box.autotune(trial_steps=2)
     box.step(args.warmup, dt)
     box.sync()
 
@@ -330,6 +334,8 @@ def run_gpu(args, rank, world, local_rank):
     box2 = E.Box.from_workload(wl, device=device)
     if args.osc:
         box2.set_oscillation(W.oscillation(**OSC_BENCH))
+    box2.set_grid(AUTOTUNE_GRIDS[tune_choice // 2])   # the first box's tuned configuration
+    box2.set_rk_form(tune_choice % 2)
     feed = E.PingPongFeed([box, box2], pin)
 
     def e2e_step():
@@ -399,6 +405,7 @@ def run_gpu(args, rank, world, local_rank):
             "config": {"workload": wl.name, "nz": wl.nz, "ndir": wl.ndir, "particles_per_gpu": wl.P,
                        "shape_order": wl.shape_order, "vacuum_matter": bool(args.osc),
                        "dt_s": dt, "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "autotune_choice": tune_choice, "autotune_ms": [round(float(x), 4) for x in tune_ms],
                        "l2": "inputs larger than L2 (particle state %.2f GB per GPU vs 129 MB L2)" % (wl.P * 480 / 1e9)},
             "roofline": roofline, "hbm": hbm,
             "kernels": {k: {"launches": n, "avg_ms": a, "share": ms / total} for k, (a, n, ms) in per.items() if n},

@@ -277,15 +277,16 @@ dim3 persist_grid(const emu_box* b) { return dim3((unsigned)b->blocks, 1, 1); }
 // Warps per group of 32 outputs in k_combine.  Long sums (more than 8
 // partials per tile: small boxes, whose warps own one unit or few) are split
 // over more warps, as far as needed to fill about one wave of the persistent
-// grid (304 blocks x 8 warps); short sums and boxes with enough outputs to
-// fill the GPU keep one warp (coalesced, latency hidden by the other warps).
+// grid (304 blocks x 8 warps); short sums keep one warp (coalesced, latency
+// hidden by the other warps).
 int combine_split(const Shape& S, int64_t nw) {
   const int64_t per_warp = nw > 0 && S.U / nw > 0 ? S.U / nw : 1;   // fewest units a warp takes
   const int64_t most = (S.Mmax + per_warp - 1) / per_warp + 1;        // most warps over one tile
   if (most <= 8) return 1;
   const int64_t out_warps = ((int64_t)kNA * S.NZ + kLanes - 1) / kLanes;
   int split = 1;
-  while (split < kWarps && out_warps * split * 2 <= (int64_t)kPersistBlocks * kWarps && split * 8 < most) split <<= 1;
+  while (split < kWarps && out_warps * split * 2 <= (int64_t)kPersistBlocks * kWarps && split * 8 < most)
+    split <<= 1;
   return split;
 }
 

@@ -527,9 +527,12 @@ k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, c
 // takes output e0 + l (consecutive cells: coalesced reads of the partials).
 // With `split` > 1 (a power of two <= 8), `split` warps of a block take the
 // same 32 outputs: warp i adds the partials of warps wf + i, wf + i + split,
-// ... in order, and the first adds the split sums in warp order through shared
-// memory.  The order depends only on the batch, the grid and `split`: results
-// are bitwise reproducible.
+// ..., and the first adds the split sums in warp order through shared
+// memory.  A warp keeps kCombineILP running sums (its partials taken
+// round-robin, then added pairwise) so that many loads are in flight.  The
+// order depends only on the batch, the grid and `split`: results are bitwise
+// reproducible.
+constexpr int kCombineILP = 8;
 __global__ void k_combine(Batch B, const double* __restrict__ partial, double* __restrict__ out, int rows,
                           int potential, int split, int* __restrict__ err) {
   griddep_wait();
@@ -553,7 +556,19 @@ __global__ void k_combine(Batch B, const double* __restrict__ partial, double* _
       const int64_t wf = warp_of_unit(g->uoff + (int64_t)tile * g->M, B);
       const int64_t wl = warp_of_unit(g->uoff + (int64_t)(tile + 1) * g->M - 1, B);
       const double* src = partial + c * B.T + k;
-      for (int64_t q = wf + wi; q <= wl; q += split) v += __ldcg(src + (q + gtile) * kSlot);
+      double a[kCombineILP] = {};
+      int64_t q = wf + wi;
+      for (; q + (kCombineILP - 1) * split <= wl; q += kCombineILP * split) {
+#pragma unroll
+        for (int i = 0; i < kCombineILP; ++i) a[i] += __ldcg(src + (q + i * split + gtile) * kSlot);
+      }
+      for (; q <= wl; q += split) a[0] += __ldcg(src + (q + gtile) * kSlot);
+#pragma unroll
+      for (int h = kCombineILP / 2; h >= 1; h /= 2) {   // pairwise: ((a0 + a4) + (a2 + a6)) + ...
+#pragma unroll
+        for (int i = 0; i < h; ++i) a[i] += a[i + h];
+      }
+      v = a[0];
     }
     if (split > 1) {
       sums[wib][lane] = v;
