@@ -368,7 +368,7 @@ def run_gpu(args, rank, world, local_rank):
     e2e_value = world * wl.P * args.steps / e2e_s
     h2d = feed.h2d_bytes
     d2h = E.N_DIAG * 8
-    del feed, box2
+    del feed, box2, pin
 
     # ---- roofline of the dominant kernel from the live per-launch events
     per = {k: (ms / n if n else 0.0, n, ms) for k, (ms, n) in ktimes.items()}
@@ -415,7 +415,7 @@ def run_gpu(args, rank, world, local_rank):
             "gpu_launches": launches,
             "clocks": clk,
         }
-    del box, pin
+    del box
     torch.cuda.empty_cache()
     extras = {}
     if not args.no_extras:
