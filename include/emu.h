@@ -228,7 +228,10 @@ int emu_batch_set_dt(emu_box* box, const double* dt);
  * or for a box bound to the legacy default stream on a blocking stream the
  * library creates, which the legacy stream orders implicitly before and after
  * its own work.  With per-kernel timing on, the kernels are launched
- * directly.  Binding, autotuning and emu_set_oscillation drop the graph. */
+ * directly.  The step kernels use programmatic dependent launch (each waits in
+ * hardware for its predecessor's results, so the next kernel's blocks can be
+ * scheduled while the previous one drains).  Binding, autotuning,
+ * emu_set_grid, emu_set_rk_form and emu_set_oscillation drop the graph. */
 int emu_batch_step(emu_box* box, int64_t nsteps);
 
 /* emu_diagnostics of every box: out [nbox][63]. */
