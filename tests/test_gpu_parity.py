@@ -161,6 +161,29 @@ def test_stage_api_equals_step_and_is_deterministic(torch):
     assert np.array_equal(a.moments().cpu().numpy(), b.moments().cpu().numpy())
 
 
+def test_timed_launch_path_equals_graph_replay(torch):
+    """The benchmark times steps with per-kernel CUDA events, which launches the
+    step kernels one by one (programmatic dependent launch, events between
+    kernels) instead of replaying the captured graph: both give bitwise the
+    same states, on the default grid and on the 32-cell RK form."""
+    from paper_2101_02745_gb300 import emu as E
+    wl = W.random_box(200, 40, seed=12)
+    for form in (-1, 1):
+        a, b = _box(wl), _box(wl)
+        for x in (a, b):
+            x.set_rk_form(form)
+        dt = a.timestep()
+        E.emu_profile(b.box, True)
+        a.step(6, dt)
+        b.step(6, dt)
+        times = E.emu_kernel_times(b.box)
+        E.emu_profile(b.box, False)
+        assert times["rk_stage"][1] == 24 and times["deposit"][1] == 24
+        ha, hb = a.get_host(), b.get_host()
+        for k in ha:
+            assert np.array_equal(ha[k], hb[k]), (form, k)
+
+
 def test_invariants_on_gpu(torch):
     wl = W.tiny_fiducial()
     box = _box(wl)
