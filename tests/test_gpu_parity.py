@@ -344,6 +344,7 @@ def test_throughput_full_size_sampled(torch):
     assert _potential_err(A, grid, wl.kappa) < 1e-12
     dt = O.timestep(cfg, grid)
     assert abs(box.timestep() - dt) <= 1e-13 * dt
+    box.autotune(trial_steps=1)   # the benchmark's launch configuration (dry steps: state untouched)
     rng = np.random.default_rng(0)
     sample = np.sort(rng.choice(wl.P, 2000, replace=False))
     Hs = O.hamiltonian(cfg, grid, parts[sample])
