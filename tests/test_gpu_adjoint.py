@@ -284,7 +284,8 @@ def test_recorded_adjoint_equals_recomputed(case):
 def test_recorded_adjoint_cost_large_box():
     """1024 cells x 1000 directions (above the recording threshold), 24 steps
     in segments of 8: the recorded backward matches the recomputing one bit for
-    bit and runs in less time; the forward/backward costs are reported."""
+    bit and runs in less time (best of two passes each); the forward/backward
+    costs are reported."""
     wl = W.adjoint_box(nz=1024, ndir=1000, steps=24)
     box = Box.from_workload(wl, init=False)
     parts = [torch.tensor(a, dtype=torch.float64, device="cuda") for a in (wl.n_nu, wl.n_nubar, wl.f_nu, wl.f_nubar)]
@@ -300,7 +301,8 @@ def test_recorded_adjoint_cost_large_box():
         L.backward()
         torch.cuda.synchronize()
         t2 = time.perf_counter()
-        times[rec] = (t1 - t0, t2 - t1)
+        prev = times.get(rec)
+        times[rec] = (t1 - t0, t2 - t1) if prev is None else (min(prev[0], t1 - t0), min(prev[1], t2 - t1))
         grads[rec] = [l.grad.cpu().numpy() for l in leaves]
     assert Simulation(box, wl.steps, 3.4e-12, every=8).use_record()
     for a, b in zip(grads[False], grads[True]):
