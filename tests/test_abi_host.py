@@ -1,7 +1,6 @@
 """CPU-side checks of the CUDA library: it builds for sm_103a, loads, exports
 every function include/emu.h declares, and its host-only logic (configuration
 validation, workspace sizing) behaves.  No call here touches a GPU."""
-import ctypes
 import re
 from pathlib import Path
 
