@@ -50,8 +50,10 @@ def _run(wl, osc, steps, blocks):
 
 # (cells, directions): partial tiles (33 and 65: a last tile of one cell, shorter
 # than the cubic stencil's reach), fewer cells than a tile, fewer cells than the
-# stencil (1, 2), one cell; at least 64 units
-CASES = [(67, 30), (33, 40), (96, 30), (1, 70), (2, 70), (5, 70), (31, 64), (65, 32)]
+# stencil (1, 2), one cell, one full tile per ring (32), long rings of few
+# directions (1000 x 2: warp ranges that start and end inside rings); at least
+# 64 units
+CASES = [(67, 30), (33, 40), (96, 30), (1, 70), (2, 70), (5, 70), (31, 64), (65, 32), (32, 64), (1000, 2)]
 
 
 @pytest.mark.parametrize("order", [0, 1, 2, 3])
