@@ -251,16 +251,21 @@ def _grads(sim, parts):
     return [l.grad.cpu().numpy() for l in leaves]
 
 
-@pytest.mark.parametrize("case", ["quadratic", "cubic_osc", "ngp", "batch"])
+@pytest.mark.parametrize("case", ["quadratic", "cubic_osc", "ngp", "batch", "batch_osc_linear"])
 def test_recorded_adjoint_equals_recomputed(case):
     """The recorded backward (each step's stage states, weights and potentials
     kept from one forward pass) runs the same kernels on the same data as the
     recomputing one: the gradients agree bit for bit."""
-    if case == "batch":
-        wl2 = W.random_box(41, 10, seed=3)
+    if case.startswith("batch"):
+        order = 1 if case == "batch_osc_linear" else 2
+        wl2 = W.with_shape(W.random_box(41, 10, seed=3), order)
         wl2.alpha = 1e-8
-        wls, dts = [W.adjoint_box(nz=32, ndir=16, steps=13), wl2], [3.4e-12, 1.1e-12]
+        wls, dts = [W.with_shape(W.adjoint_box(nz=32, ndir=16, steps=13), order), wl2], [3.4e-12, 1.1e-12]
         box = Box.from_workloads(wls, init=False)
+        if case == "batch_osc_linear":   # vacuum and matter terms on the second box only
+            box.set_oscillation(W.oscillation(mass_eV=(0.0, 8.6e-3, 5.0e-2), theta12=0.59, theta13=0.15,
+                                              theta23=0.84, delta_cp=1.2, energy_MeV=5e-5, rho_g_cm3=1e9, Ye=0.4),
+                                box=1)
         mk = lambda rec: Simulation(box, 13, dts, every=5, alpha=[w.alpha for w in wls],
                                     seed=[w.seed for w in wls], record=rec)
         parts = [torch.cat([torch.tensor(getattr(w, a), dtype=torch.float64, device="cuda") for w in wls])
