@@ -52,11 +52,10 @@ FLOPS_DEPOSIT = 137
 # -40 / +32 (+8 for the cubic weights); the vacuum and matter terms add 16 adds.
 TAPS_DELTA = {0: -40, 1: 0, 2: 0, 3: 32}
 WEIGHTS_DELTA = {0: -12, 1: -6, 2: 0, 3: 8}
-# Grids the autotuner tries (blocks of 256 threads), in the order of its choice index // 2.
-AUTOTUNE_GRIDS = (304, 152, 608)
-# FP64 pipe: 2 DFMA per clock per SM (nominal 1.25 TFLOP/s / (2 flop x 152 SMs x 2.07 GHz) = 1.99),
-# so peak = 2 x 2 flop x 152 SMs x 2.07 GHz.
-PEAK_FP64_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
+# FP64 pipe, nominal: 2 DFMA per clock per SM (nominal 1.25 TFLOP/s / (2 flop x 152 SMs x 2.07 GHz) = 1.99),
+# so 2 x 2 flop x 152 SMs x 2.07 GHz.  The roofline's denominator is the FP64 peak measured in the
+# same run (fp64_peak: cuBLAS DGEMM); this derived figure is reported beside it.
+PEAK_FP64_DERIVED_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 # Bytes per particle of one launch: RK stage (average over s = 1..4 of 57, 93, 93, 59
 # doubles, the shape weights included), deposit (21 read + 3 weights written).
 BYTES_RK = (57 + 93 + 93 + 59) / 4 * 8
@@ -179,6 +178,34 @@ def workload(args):
     if args.shape_order != 2:
         wl = W.with_shape(wl, args.shape_order)
     return wl
+
+
+def fp64_peak(device, n: int = 8192, reps: int = 3):
+    """FP64 peak measured on this GPU in this run: cuBLAS DGEMM through
+    torch.matmul on float64 n x n matrices (2 n^3 flop), best of `reps` after
+    one warm-up, CUDA events on the current stream, SM clocks sampled meanwhile.
+    (GB300's FP64 matrix path shares the FP64 pipe with DFMA, so a DGEMM
+    measures the same pipe the kernels use.)"""
+    import torch
+    g = torch.Generator(device=device).manual_seed(0)
+    a = torch.rand(n, n, dtype=torch.float64, device=device, generator=g)
+    b = torch.rand(n, n, dtype=torch.float64, device=device, generator=g)
+    c = torch.matmul(a, b)
+    torch.cuda.synchronize(device)
+    clk = ClockSampler(device.index).start()
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize(device)
+        best = min(best, e0.elapsed_time(e1))
+    clocks = clk.stop()
+    del a, b, c
+    torch.cuda.empty_cache()
+    return {"tflops": 2.0 * n ** 3 / (best * 1e-3) / 1e12, "ms": best, "n": n, "reps": reps, "clocks": clocks,
+            "how": f"cuBLAS DGEMM (torch.matmul, float64, {n}^3, 2 n^3 flop), best of {reps}, CUDA events"}
 
 
 # ------------------------------------------------------------ CPU oracle
@@ -324,35 +351,32 @@ def run_gpu(args, rank, world, local_rank):
     value = world * wl.P * args.steps / (t_ms * 1e-3)
 
     # ---- end to end through the public API with host buffers: every step the
-    # state (z, rho, rhobar) comes from pinned host memory and the step's
-    # diagnostics are read back to the host.  Two boxes take turns
-    # (E.PingPongFeed): the next step's host-to-device copy goes straight into
-    # the idle box's arrays on a side stream while the other box steps.
+    # state (z, rho, rhobar) comes from pinned host memory through the C ABI's
+    # host-buffer path (emu_set_particles, on_host = 1) and the step's
+    # diagnostics are read back to the host (emu_diagnostics, on_host = 1).
+    # Two boxes with their own streams take turns (E.PingPongFeed): the next
+    # step's upload into the idle box overlaps the other box's step.
     host = box.get_host()
     pin = {k: torch.from_numpy(host[k]).pin_memory() for k in ("z", "rho", "rhobar")}
     diag = torch.zeros(E.N_DIAG, dtype=torch.float64).pin_memory()
-    box2 = E.Box.from_workload(wl, device=device)
+    box2 = E.Box.from_workload(wl, device=device, stream=torch.cuda.Stream(device))
     if args.osc:
         box2.set_oscillation(W.oscillation(**OSC_BENCH))
-    box2.set_grid(AUTOTUNE_GRIDS[tune_choice // 2])   # the first box's tuned configuration
-    box2.set_rk_form(tune_choice % 2)
+    box2.apply_choice(tune_choice)   # the first box's tuned configuration
     feed = E.PingPongFeed([box, box2], pin)
 
     def e2e_step():
-        b = feed.next_box()
-        E.emu_step(b.box, 1, dt)
+        b = feed.step(lambda bx: E.emu_step(bx.box, 1, dt))
         E.emu_diagnostics(b.box, diag.data_ptr(), 1)
 
     # the host link's copy rate alone (the e2e step cannot beat the copy of its
-    # inputs), timed on the second copy (the first touches the pinned pages)
-    feed.prefetch(1)
-    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # inputs), timed on the second upload (the first touches the pinned pages)
+    feed.install(1)
     torch.cuda.synchronize(device)
-    c0.record(feed.copy)
-    feed.prefetch(0)
-    c1.record(feed.copy)
-    torch.cuda.synchronize(device)
-    h2d_gbs = feed.h2d_bytes / (c0.elapsed_time(c1) * 1e-3) / 1e9
+    t_c = time.perf_counter()
+    feed.install(1)
+    h2d_gbs = feed.h2d_bytes / (time.perf_counter() - t_c) / 1e9
+    feed.prime()
     e2e_step()
     e2e_step()   # both boxes have captured their step graphs
     barrier(dist, device)
@@ -370,28 +394,37 @@ def run_gpu(args, rank, world, local_rank):
     d2h = E.N_DIAG * 8
     del feed, box2, pin
 
-    # ---- roofline of the dominant kernel from the live per-launch events
+    # ---- roofline of the dominant kernel from the live per-launch events,
+    # against the FP64 peak measured in this run
     per = {k: (ms / n if n else 0.0, n, ms) for k, (ms, n) in ktimes.items()}
     total = sum(ms for (_, _, ms) in per.values()) or 1.0
     dominant = max(per, key=lambda k: per[k][2])
     avg_ms = per[dominant][0]
+    flops_dep = FLOPS_DEPOSIT + TAPS_DELTA[wl.shape_order] + WEIGHTS_DELTA[wl.shape_order]
+    flops_rk = sum(FLOPS_RK.values()) / 4 + TAPS_DELTA[wl.shape_order] + (16 if args.osc else 0)
     if dominant == "deposit":
-        flops = (FLOPS_DEPOSIT + TAPS_DELTA[wl.shape_order] + WEIGHTS_DELTA[wl.shape_order]) * wl.P
-        bytes_ = BYTES_DEPOSIT * wl.P
-        traffic = TRAFFIC_DEPOSIT * wl.P
+        flops, bytes_, traffic = flops_dep * wl.P, BYTES_DEPOSIT * wl.P, TRAFFIC_DEPOSIT * wl.P
+        kname = "k_deposit"
+    elif dominant == "step":    # the fused step: all four stages' deposits and RK stages in one launch
+        flops, bytes_, traffic = 4 * (flops_dep + flops_rk) * wl.P, 4 * (BYTES_DEPOSIT + BYTES_RK) * wl.P, None
+        kname = "k_step"
     else:
-        flops = (sum(FLOPS_RK.values()) / 4 + TAPS_DELTA[wl.shape_order] + (16 if args.osc else 0)) * wl.P
-        bytes_ = BYTES_RK * wl.P
+        flops, bytes_ = flops_rk * wl.P, BYTES_RK * wl.P
         traffic = TRAFFIC_RK * wl.P if TRAFFIC_RK else None
+        kname = "k_rk_stage"
     achieved = flops / (avg_ms * 1e-3) / 1e12
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / PEAK_FP64_TFLOPS, "traffic": traffic,
+    pk = fp64_peak(device) if not args.no_fp64_peak else None
+    peak = pk["tflops"] if pk else PEAK_FP64_DERIVED_TFLOPS
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu dram read + write, scaled by particles)",
-                "kernel": "k_rk_stage" if dominant == "rk_stage" else f"k_{dominant}",
-                "flops_per_launch": flops, "avg_launch_ms": avg_ms,
-                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                "kernel": kname, "flops_per_launch": flops, "avg_launch_ms": avg_ms,
+                "peak_source": ("measured in this run: " + pk["how"]) if pk else
+                               "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                "peak_measured": pk,
+                "peak_derived": PEAK_FP64_DERIVED_TFLOPS, "frac_of_derived": achieved / PEAK_FP64_DERIVED_TFLOPS,
                 "hbm_gbs_of_kernel": bytes_ / (avg_ms * 1e-3) / 1e9}
     hbm = {"achieved_gbs": value / world * B_ALG_PER_UPDATE / 1e9, "peak_gbs": hbm_peak,
            "frac": value / world * B_ALG_PER_UPDATE / 1e9 / hbm_peak, "bytes_per_update": B_ALG_PER_UPDATE,
@@ -653,12 +686,19 @@ def main(argv=None):
                     help="adjoint backward with per-step records (auto: large boxes)")
     ap.add_argument("--shape-order", type=int, default=2, choices=[0, 1, 2, 3], help="particle shape (Sec. 2.2.1)")
     ap.add_argument("--osc", action="store_true", help="add the vacuum and matter terms of Eq. 2")
+    ap.add_argument("--no-fp64-peak", action="store_true", help="skip the in-run DGEMM measurement of the FP64 peak")
+    ap.add_argument("--fp64-peak", action="store_true", help="only measure and print the FP64 peak (DGEMM)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-sweep and adjoint comparisons of the default line")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank, world, local_rank = dist_env()
+    if args.fp64_peak:
+        import torch
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"fp64_peak": fp64_peak(torch.device("cuda", local_rank), reps=max(args.steps, 1))}))
+        return 0
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if args.workload == "sweep":

@@ -71,7 +71,7 @@ extern "C" {
 #define EMU_EINVAL (-1)    /* bad argument: null pointer, size, unsupported option */
 #define EMU_ECUDA (-2)     /* a CUDA runtime call failed */
 #define EMU_ENUMERIC (-3)  /* a non-finite value appeared on the grid */
-#define EMU_ETIMEOUT (-4)  /* reserved: a bounded device-side wait gave up */
+#define EMU_ETIMEOUT (-4)  /* a bounded device-side wait (a grid barrier of the fused step) gave up */
 #define EMU_ELATTICE (-5)  /* particles violate the lattice contract */
 
 typedef struct emu_box emu_box;
@@ -221,33 +221,64 @@ int emu_batch_timestep(emu_box* box, double* dt_out);
 int emu_batch_set_dt(emu_box* box, const double* dt);
 
 /* nsteps classic RK4 steps of every box with its own step size (Eq. 7 values
- * unless set): per step one lattice-shift launch and per stage one deposit,
- * one deposit combination and one RK-stage launch, each covering all boxes.
- * The first call captures one step as a CUDA graph (make that call outside
- * any other stream capture) and every step replays it: on the box's stream,
- * or for a box bound to the legacy default stream on a blocking stream the
- * library creates, which the legacy stream orders implicitly before and after
- * its own work.  With per-kernel timing on, the kernels are launched
- * directly.  The step kernels use programmatic dependent launch (each waits in
- * hardware for its predecessor's results, so the next kernel's blocks can be
- * scheduled while the previous one drains).  Binding, autotuning,
- * emu_set_grid, emu_set_rk_form and emu_set_oscillation drop the graph. */
+ * unless set), all boxes advanced by the same launches.  Two step forms
+ * (emu_set_step_form; emu_autotune picks one):
+ *   0  one launch per phase: per step one lattice-shift launch and per stage
+ *      one deposit, one deposit combination and one RK-stage launch (13), with
+ *      programmatic dependent launch (each waits in hardware for its
+ *      predecessor's results, so the next kernel's blocks can be scheduled
+ *      while the previous one drains);
+ *   1  one persistent cooperative launch per step: the same phases with the
+ *      same arithmetic in one kernel whose blocks are all resident, separated
+ *      by grid barriers whose waits are bounded (emu_set_barrier_timeout).  A
+ *      wait that gives up stops the launch; the next synchronising call
+ *      reports EMU_ETIMEOUT, the particle state is then that of an unfinished
+ *      step, and later launches run normally.
+ * Both forms give bitwise the same results for the same grid.  The first call
+ * captures one step as a CUDA graph (make that call outside any other stream
+ * capture) and every step replays it: on the box's stream, or for a box bound
+ * to the legacy default stream on a blocking stream the library creates,
+ * which the legacy stream orders implicitly before and after its own work.
+ * With per-kernel timing on, the kernels are launched directly.  Binding,
+ * autotuning, emu_set_grid, emu_set_rk_form, emu_set_step_form,
+ * emu_set_barrier_timeout and emu_set_oscillation drop the graph. */
 int emu_batch_step(emu_box* box, int64_t nsteps);
 
 /* emu_diagnostics of every box: out [nbox][63]. */
 int emu_batch_diagnostics(emu_box* box, double* out, int on_host);
 
 /* Autotuner: times trial_steps steps of each candidate launch configuration
- * of the step kernels (grids of 304, 152 or 608 blocks of 256 threads, whose
- * warps split the work, each with the RK stage in its halo-lane or its
- * 32-cell form) without changing the particle state (the trial steps write
- * their results into the RK scratch), keeps the fastest for later steps, and
- * reports its index c (0..5: grid c / 2, form c % 2, 1 = 32-cell) in
- * *choice_out and the per-step times [ms] of the six candidates in ms_out[6]
- * (either may be NULL).  The deposit's summation order depends on the grid,
- * so results are bitwise reproducible for a fixed choice; the two RK forms
- * give bitwise the same results.  Synchronises. */
+ * without changing the particle state (the trial steps write their results
+ * into the RK scratch), keeps the fastest for later steps, and reports its
+ * index c in *choice_out and the per-step times [ms] of the candidates in
+ * ms_out[EMU_AUTOTUNE_CANDIDATES] (either may be NULL; -1 for a candidate
+ * that cannot run on this device).  A candidate is a step form
+ * (emu_batch_step), a grid of blocks of 256 threads whose warps split the
+ * work (the number of particles each warp and block takes follows from it),
+ * and the RK stage's tile: 30 cells and two halo lanes per warp (form 0) or
+ * 32 cells per warp (form 1):
+ *   c = 0..5  one launch per phase, grid {304, 152, 608}[c / 2], RK form c % 2
+ *   c = 6..9  one cooperative launch per step, grid {304, 152}[(c - 6) / 2],
+ *             RK form c % 2.
+ * The deposit's summation order depends on the grid, so results are bitwise
+ * reproducible for a fixed grid; the step forms and the RK forms give bitwise
+ * the same results.  Synchronises. */
+#define EMU_AUTOTUNE_CANDIDATES 10
 int emu_autotune(emu_box* box, int trial_steps, int32_t* choice_out, double* ms_out);
+
+/* Step form of emu_batch_step / emu_step: 0 = one launch per phase, 1 = one
+ * persistent cooperative launch per step.  Form 1 needs every block of the
+ * grid resident at once (at most 2 blocks per SM: 304 on GB300) and a device
+ * that supports cooperative launches.  Errors: EMU_EINVAL (bad form, grid too
+ * large, step in progress). */
+int emu_set_step_form(emu_box* box, int32_t form);
+
+/* Bound [ns] of every grid-barrier wait of the fused step (default 1e9: far
+ * above any phase of a box that fits the GPU).  A wait that exceeds it stops
+ * the launch and the next synchronising call returns EMU_ETIMEOUT.  0 makes
+ * every wait that has to wait give up at once (for tests of that path).
+ * Errors: EMU_EINVAL (negative). */
+int emu_set_barrier_timeout(emu_box* box, int64_t ns);
 
 /* Form of the RK stage kernel: 1 = 32 cells per warp, 0 = the halo-lane form
  * (both give bitwise the same results), -1 = chosen by units per warp (the
@@ -260,8 +291,9 @@ int emu_set_rk_form(emu_box* box, int32_t form);
  * work, so the choice changes the deposit's summation order (results stay
  * bitwise reproducible for a fixed choice) and whether the RK stage runs with
  * 32 cells per warp (every warp walking at least 8 units) or the halo-lane
- * form (the same results); it drops the RK form emu_autotune chose.  Errors:
- * EMU_EINVAL. */
+ * form (the same results); it drops the RK form emu_autotune chose, and the
+ * fused step form if not every block of the new grid could be resident.
+ * Errors: EMU_EINVAL. */
 int emu_set_grid(emu_box* box, int32_t blocks);
 
 /* Vacuum and matter terms of Eq. 2 (Sec. 2.1): masses m_i c^2 [eV], the mixing
@@ -369,21 +401,25 @@ int64_t emu_kernel_launches(const emu_box* box);
 /* Per-launch device timing.  With enable != 0 every later kernel launch of
  * the box is bracketed by two CUDA events recorded on the box's stream.
  * emu_kernel_times synchronises the stream, writes the summed duration [ms]
- * and the number of recorded launches of each kernel class to ms_out[5] and
- * count_out[5] (0: lattice-shift table, 1: deposit, 2: RK stage, 3: deposit
- * combination, 4: other), and clears the record.  Timing is a measurement aid with no other effect. */
+ * and the number of recorded launches of each kernel class to ms_out[6] and
+ * count_out[6] (0: lattice-shift table, 1: deposit, 2: RK stage, 3: deposit
+ * combination, 4: other, 5: fused step), and clears the record.  Timing is a
+ * measurement aid with no other effect. */
 int emu_profile(emu_box* box, int enable);
 int emu_kernel_times(emu_box* box, double* ms_out, int64_t* count_out);
 
 /* Deposit that allocates nothing (the paper has no counterpart: this is a
  * service for callers of the library).  Some callers cannot call cudaMalloc
- * or any other allocator: code running in a host callback or inside another
- * library's allocation-free section, or code that must not touch an
- * allocator while a memory pool is being resized.  They cannot provide the
- * workspace emu_bind needs, so this call keeps the deposit's scratch (direction
- * table, lattice shifts, partial sums, error word) in one
- * static 32 MiB device array of the library, which every GPU that loads the
- * library holds until the process exits.
+ * or any other allocator, yet may still enqueue stream work and wait for it:
+ * code inside another library's allocation-free section, or code that must
+ * not touch an allocator while a memory pool is being resized or torn down.
+ * They cannot provide the workspace emu_bind needs, so this call keeps the
+ * deposit's scratch (direction table, lattice shifts, partial sums, error
+ * word) in one static 32 MiB device array of the library, which every GPU that
+ * loads the library holds until the process exits.
+ *   - It must not be called from a host function (cudaLaunchHostFunc or a
+ *     stream callback): CUDA forbids CUDA calls there, and this call launches
+ *     kernels, copies and synchronises.
  *   - Inputs: cfg and the device particle arrays laid out as in emu_particles
  *     (rho/rhobar as [9][P]); output: A_out, a device array [36][nz] that
  *     receives the grid potential A (as emu_deposit) of the state at positions
@@ -394,9 +430,15 @@ int emu_kernel_times(emu_box* box, double* ms_out, int64_t* count_out);
  *     (roughly nz above 43,000 or ndir above 340,000) is rejected with
  *     EMU_EINVAL before any device work.
  *   - The first call on a device looks up the array's device address on that
- *     device (cudaGetSymbolAddress); make that first call before any stream
- *     capture.  The call clears the error word, runs the deposit, then
- *     synchronises the stream to report lattice or non-finite errors.
+ *     device (cudaGetSymbolAddress).  No call may be made on a stream that is
+ *     being captured: every call ends by copying the error word to the host
+ *     and synchronising the stream, which a capture cannot contain; such a
+ *     call returns EMU_EINVAL before any device work.  The call clears the
+ *     error word, runs the deposit, then synchronises the stream to report
+ *     lattice or non-finite errors.
+ *   - The address is kept per device for later calls.  After a CUDA error in
+ *     a call it is looked up again on the next call; a reset of the device
+ *     (cudaDeviceReset) between calls is not supported.
  *   - All calls on a device share the one array, which keeps whatever the last
  *     call left in it: calls that overlap on the GPU (other streams, other host
  *     threads) race on it and must be serialised by the caller.

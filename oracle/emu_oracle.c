@@ -24,8 +24,7 @@
  *   - the time step choice                                     (Eq. 7)
  *   - particle initialisation: weights (Eq. 8), initial flavour state (Eq. 9)
  *
- * Readings of points the paper leaves open (each is also listed in the design
- * notes of the repository):
+ * Readings of points the paper leaves open:
  *   - H is carried as an angular frequency H/hbar [1/s]; kappa = sqrt(2) G_F/hbar
  *     [cm^3/s] is an input.
  *   - Cell volume dV = dz * area (area is an input, 1 cm^2 by default); it

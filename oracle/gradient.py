@@ -55,7 +55,8 @@ def _eval_args(args):
 
 def fd_gradient(cfg_kw: dict, theta, alpha: float, seed: int, dt: float, nsteps: int, h: float = 1e-6,
                 dirs=None, processes: int = 1) -> np.ndarray:
-    """Central-difference gradient, shape (2, 8): row k is dL_k/dtheta.
+    """Central-difference gradient, shape (2, 8): row k is dL_k/dtheta (row 1
+    is NaN where L1 is undefined: alpha = 0 leaves n_emu = 0).
     processes > 1 evaluates the 16 runs in a spawned process pool."""
     theta = np.asarray(theta, float)
     s = h * max(abs(theta[0]), abs(theta[1]))
@@ -72,5 +73,9 @@ def fd_gradient(cfg_kw: dict, theta, alpha: float, seed: int, dt: float, nsteps:
         vals = [evaluate(*j) for j in jobs]
     g = np.zeros((2, 8))
     for i in range(8):
-        g[:, i] = (vals[2 * i] - vals[2 * i + 1]) / (2.0 * s)
+        lo, hi = vals[2 * i], vals[2 * i + 1]
+        for k in range(2):
+            # L1 = log <|n_emu|> is undefined when n_emu stays 0 (no perturbation,
+            # alpha = 0): its row is then NaN by definition, not by arithmetic
+            g[k, i] = (lo[k] - hi[k]) / (2.0 * s) if np.isfinite(lo[k]) and np.isfinite(hi[k]) else np.nan
     return g

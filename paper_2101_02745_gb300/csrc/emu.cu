@@ -128,7 +128,7 @@ const char* make_shape(const emu_config* cfgs, int nbox, Shape& S) {
 }
 
 struct Layout {
-  size_t geo, dts, nmax, A, At, mom, partial, W, err, dirtab, shift, species, dirs, diag, scalar, total;
+  size_t geo, dts, nmax, A, At, mom, partial, W, err, dirtab, shift, shift2, bar, species, dirs, diag, scalar, total;
 };
 
 Layout layout(const Shape& S) {
@@ -147,6 +147,8 @@ Layout layout(const Shape& S) {
   L.err = take(sizeof(int));
   L.dirtab = take(sizeof(double) * 4 * MT);
   L.shift = take(sizeof(int) * 4 * MT);
+  L.shift2 = take(sizeof(int) * 4 * MT);   // the fused step's shift rows of the next step
+  L.bar = take(sizeof(unsigned) * 2);       // the fused step's grid barrier: arrival word, abort word
   L.species = take(sizeof(double) * 8 * NZ);
   L.dirs = take(sizeof(double) * 3 * MT);
   L.diag = take(sizeof(double) * 63 * nb);
@@ -155,7 +157,7 @@ Layout layout(const Shape& S) {
   return L;
 }
 
-enum : int { CLS_SHIFT = 0, CLS_DEPOSIT = 1, CLS_RK = 2, CLS_COMBINE = 3, CLS_OTHER = 4, N_CLS = 5 };
+enum : int { CLS_SHIFT = 0, CLS_DEPOSIT = 1, CLS_RK = 2, CLS_COMBINE = 3, CLS_OTHER = 4, CLS_STEP = 5, N_CLS = 6 };
 
 const double kStageFrac[4] = {0.0, 0.5, 0.5, 1.0};  // position offset of RK stage s, in units of dt
 
@@ -173,9 +175,12 @@ struct emu_box {
   // A: full grid potential of emu_deposit; At: the step's traceless potential
   double *dts = nullptr, *nmax = nullptr, *A = nullptr, *At = nullptr, *mom = nullptr, *partial = nullptr,
          *W = nullptr, *dirtab = nullptr, *species = nullptr, *dirs = nullptr, *diag = nullptr, *scalar = nullptr;
-  int *err = nullptr, *shift = nullptr;
+  int *err = nullptr, *shift = nullptr, *shift2 = nullptr;
+  unsigned* bar = nullptr;
   int blocks = kPersistBlocks;  // grid of the step kernels (autotuned); its warps split the units
   int rk_form = -1;             // RK stage: 0 halo-lane, 1 32-cell, -1 by units per warp (autotuned)
+  int step_form = 0;            // 0: one launch per phase, 1: one cooperative launch per step (k_step)
+  unsigned long long limit_ns = 1000000000ull;   // bound of each grid-barrier wait of k_step
   bool pot = false;             // some box has vacuum or matter terms
   int next_stage = 1;
   std::vector<double> dt_h;  // step sizes currently on the device
@@ -489,6 +494,76 @@ int launch_stage(emu_box* b, int s, int dry) {
   return launch_rk(b, s, srow, dry);
 }
 
+// Whether the RK stage runs with 32 cells per warp (no halo lanes): when every
+// warp walks at least 8 units (the tile ends at ring and range boundaries are
+// computed directly), unless a form was chosen; otherwise the halo-lane form,
+// which gives bitwise the same results.
+bool use_rk32(const emu_box* b, const Batch& Bv) {
+  return b->rk_form >= 0 ? b->rk_form == 1 : Bv.U32 >= 8 * (int64_t)Bv.nw32;
+}
+
+// Most blocks of the fused step kernel that can be resident at once (its
+// cooperative launch needs every block resident).
+int fused_max_blocks(const emu_box* b) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  int coop = 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+  // every instantiation has the same launch bounds; the largest (cubic shape,
+  // vacuum terms, 32-cell RK stage) stands for all
+  (void)b;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<true, 3, true>, kThreads, 0) != cudaSuccess)
+    return 0;
+  return per_sm * sms;
+}
+
+// nsteps RK4 steps of every box in one cooperative launch of k_step (dry: the
+// results of stage 4 go to the stage buffer, as in launch_step).
+int launch_fused(emu_box* b, int dry, int64_t nsteps) {
+  const int maxb = fused_max_blocks(b);
+  if (b->blocks > maxb)
+    return fail(b, EMU_EINVAL, "the fused step needs all %d blocks resident at once; at most %d fit", b->blocks, maxb);
+  const Batch B = batch_view(b);
+  StepArgs a{};
+  a.dirtab = b->dirtab;
+  a.shift = b->shift;
+  a.shift2 = b->shift2;
+  a.W = b->W;
+  a.At = b->At;
+  a.partial = b->partial;
+  a.err = b->err;
+  a.bar = b->bar;
+  a.limit_ns = b->limit_ns;
+  a.nsteps = nsteps;
+  a.split = combine_split(b->S, B.nw);
+  a.dry = dry;
+  const bool r32 = use_rk32(b, B);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = persist_grid(b);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = b->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  before_launch(b, CLS_STEP);
+  by_order(b->S.order, [&](auto O) {
+    constexpr int R = decltype(O)::value;
+    if (b->pot) {
+      if (r32) (void)cudaLaunchKernelEx(&cfg, k_step<true, R, true>, B, b->pt, a);
+      else (void)cudaLaunchKernelEx(&cfg, k_step<true, R, false>, B, b->pt, a);
+    } else {
+      if (r32) (void)cudaLaunchKernelEx(&cfg, k_step<false, R, true>, B, b->pt, a);
+      else (void)cudaLaunchKernelEx(&cfg, k_step<false, R, false>, B, b->pt, a);
+    }
+    return 0;
+  });
+  return after_launch(b, "fused step kernel");
+}
+
 // The RK-stage kernel of stage s from the shape weights W and the traceless
 // potential At of its deposit; stages 2-4 read their state from stage_src and
 // write the next one to pt.stage.
@@ -502,7 +577,7 @@ int launch_rk_on(emu_box* b, int s, const int* srow, int dry, const Parts& pt, c
     // the halo-lane kernel, which gives bitwise the same results
     const Batch Bv = batch_view(b);
     const dim3 grid = persist_grid(b);
-    const bool use32 = b->rk_form >= 0 ? b->rk_form == 1 : Bv.U32 >= 8 * (int64_t)Bv.nw32;
+    const bool use32 = use_rk32(b, Bv);
     if (!use32) {
       if (b->pot)
         pdl(b->stream, k_rk_stage<true, R>, grid, Bv, pt, W, b->dirtab, srow, At, stage_src, s, dry);
@@ -524,6 +599,7 @@ int launch_rk(emu_box* b, int s, const int* srow, int dry) {
 }
 
 int launch_step(emu_box* b, int dry) {
+  if (b->step_form == 1) return launch_fused(b, dry, 1);
   if (int rc = launch_shifts(b, kStageFrac, 4)) return rc;
   for (int s = 1; s <= 4; ++s)
     if (int rc = launch_stage(b, s, dry)) return rc;
@@ -573,6 +649,13 @@ int read_errors(emu_box* b) {
   if (e != cudaSuccess) return cuda_check(b, e, "read error word");
   if (h == 0) return EMU_OK;
   cudaMemsetAsync(b->err, 0, sizeof(int), b->stream);
+  if (h & ERR_TIMEOUT) {
+    // a fused step gave up at a grid barrier: its arrival word is left mid-count
+    // and its abort word set; clear both so that the next fused launch runs
+    cudaMemsetAsync(b->bar, 0, sizeof(unsigned) * 2, b->stream);
+    return fail(b, EMU_ETIMEOUT, "a grid-barrier wait of the fused step gave up after %llu ns; the particle state "
+                "is that of an unfinished step", b->limit_ns);
+  }
   if (h & ERR_WEIGHT) return fail(b, EMU_EINVAL, "negative particle weight: a flux factor exceeds 1/3");
   if (h & ERR_RING) return fail(b, EMU_ELATTICE, "a ring of particles does not share one direction");
   if (h & ERR_LATTICE) return fail(b, EMU_ELATTICE, "a particle is off its lattice site");
@@ -712,6 +795,8 @@ int emu_bind(emu_box* b, const emu_particles* parts, void* workspace, int64_t wo
   b->err = (int*)(b->ws + L.err);
   b->dirtab = (double*)(b->ws + L.dirtab);
   b->shift = (int*)(b->ws + L.shift);
+  b->shift2 = (int*)(b->ws + L.shift2);
+  b->bar = (unsigned*)(b->ws + L.bar);
   b->species = (double*)(b->ws + L.species);
   b->dirs = (double*)(b->ws + L.dirs);
   b->diag = (double*)(b->ws + L.diag);
@@ -903,6 +988,7 @@ int emu_set_grid(emu_box* b, int32_t blocks) {
   if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
   b->blocks = blocks;
   b->rk_form = -1;
+  if (b->step_form == 1 && blocks > fused_max_blocks(b)) b->step_form = 0;   // cannot be all resident
   invalidate_graph(b);
   return EMU_OK;
 }
@@ -923,16 +1009,25 @@ int emu_autotune(emu_box* b, int trial_steps, int32_t* choice_out, double* ms_ou
   if (!b->step_valid)
     if (int rc = run_timestep(b, nullptr)) return rc;
   if (int rc = set_dts(b, b->step_dt.data())) return rc;
-  const int cand[3] = {kPersistBlocks, kPersistBlocks / 2, kMaxBlocks};
+  // candidate c: step form, grid and RK form (see emu.h)
+  const int grids[EMU_AUTOTUNE_CANDIDATES] = {kPersistBlocks, kPersistBlocks, kPersistBlocks / 2, kPersistBlocks / 2,
+                                              kMaxBlocks, kMaxBlocks, kPersistBlocks, kPersistBlocks,
+                                              kPersistBlocks / 2, kPersistBlocks / 2};
+  const int maxb = fused_max_blocks(b);
   const bool prof = b->prof;
   b->prof = false;
   cudaEvent_t e0 = take_event(b), e1 = take_event(b);
   int best = 0;
   float best_ms = 0.f;
   int rc = EMU_OK;
-  for (int c = 0; c < 6 && rc == EMU_OK; ++c) {   // candidate c: grid c / 2, RK form c % 2
-    b->blocks = cand[c / 2];
+  for (int c = 0; c < EMU_AUTOTUNE_CANDIDATES && rc == EMU_OK; ++c) {
+    b->blocks = grids[c];
     b->rk_form = c % 2;
+    b->step_form = c >= 6 ? 1 : 0;
+    if (b->step_form == 1 && b->blocks > maxb) {   // not every block could be resident: not a candidate
+      if (ms_out) ms_out[c] = -1.0;
+      continue;
+    }
     rc = launch_step(b, 1);  // warm-up (dry: the particle state is left as it was)
     if (rc) break;
     cudaEventRecord(e0, b->stream);
@@ -949,12 +1044,37 @@ int emu_autotune(emu_box* b, int trial_steps, int32_t* choice_out, double* ms_ou
   b->pool.push_back(e0);
   b->pool.push_back(e1);
   b->prof = prof;
-  b->blocks = cand[best / 2];
+  b->blocks = grids[best];
   b->rk_form = best % 2;
+  b->step_form = best >= 6 ? 1 : 0;
   invalidate_graph(b);
   if (rc) return rc;
   if (choice_out) *choice_out = best;
   return read_errors(b);
+}
+
+int emu_set_step_form(emu_box* b, int32_t form) {
+  if (int rc = check_bound(b)) return rc;
+  if (form < 0 || form > 1) return fail(b, EMU_EINVAL, "form must be 0 or 1");
+  if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
+  if (form == 1) {
+    const int maxb = fused_max_blocks(b);
+    if (maxb <= 0) return fail(b, EMU_EINVAL, "the device cannot launch the fused (cooperative) step");
+    if (b->blocks > maxb)
+      return fail(b, EMU_EINVAL, "the fused step needs all %d blocks resident at once; at most %d fit (emu_set_grid)",
+                  b->blocks, maxb);
+  }
+  b->step_form = form;
+  invalidate_graph(b);
+  return EMU_OK;
+}
+
+int emu_set_barrier_timeout(emu_box* b, int64_t ns) {
+  if (int rc = check_bound(b)) return rc;
+  if (ns < 0) return fail(b, EMU_EINVAL, "the timeout must be >= 0 ns");
+  b->limit_ns = (unsigned long long)ns;
+  invalidate_graph(b);
+  return EMU_OK;
 }
 
 int emu_set_oscillation(emu_box* b, int32_t box, const emu_oscillation* osc) {
@@ -1352,14 +1472,16 @@ void emu_destroy(emu_box* b) { delete b; }
 
 // ------------------------------------------- deposit without any allocation
 //
-// Some callers cannot allocate device memory at all: code running where
-// cudaMalloc is not allowed (inside a host callback or another library's
-// allocation-free region), or code that must not call into any allocator
-// (for example while a memory pool is being torn down or resized).  They
-// cannot provide the workspace that emu_bind expects, so this entry point
-// keeps the deposit's scratch (box descriptor, per-direction table, lattice
-// shifts, partial sums of the warps, error word) in one static device array
-// that the library itself holds on every GPU that loads it.
+// Some callers cannot allocate device memory at all but may still enqueue
+// stream work and wait for it: code inside another library's allocation-free
+// region, or code that must not call into any allocator (for example while a
+// memory pool is being torn down or resized).  They cannot provide the
+// workspace that emu_bind expects, so this entry point keeps the deposit's
+// scratch (box descriptor, per-direction table, lattice shifts, partial sums
+// of the warps, error word) in one static device array that the library
+// itself holds on every GPU that loads it.  It launches kernels, copies and
+// synchronises, so it must not run inside a host function (CUDA forbids CUDA
+// calls there) or on a stream being captured.
 
 namespace {
 
@@ -1390,6 +1512,15 @@ int static_scratch_address(void** out) {
   return EMU_OK;
 }
 
+// Forgets the current device's cached address (after a CUDA error: the next
+// call looks it up again).
+void forget_static_address() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return;
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  g_static_addr[dev] = nullptr;
+}
+
 }  // namespace
 
 extern "C" int emu_deposit_static(const emu_config* cfg, const double* z, const double* ox, const double* oy,
@@ -1401,6 +1532,15 @@ extern "C" int emu_deposit_static(const emu_config* cfg, const double* z, const 
   if (!z || !ox || !oy || !oz || !N || !Nbar || !rho || !rhobar || !A_out)
     return fail(nullptr, EMU_EINVAL, "a particle array or A_out is NULL");
   if (!std::isfinite(pos_dt)) return fail(nullptr, EMU_EINVAL, "pos_dt must be finite");
+  cudaStream_t st = (cudaStream_t)stream;
+  {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return fail(nullptr, EMU_ECUDA, "cudaStreamIsCapturing: %s", cudaGetErrorString(e));
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(nullptr, EMU_EINVAL, "emu_deposit_static synchronises its stream: it cannot run on a stream "
+                  "that is being captured");
+  }
   // carve the static array: box descriptor, step size, partial sums, error word, direction table, shifts
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
@@ -1423,9 +1563,10 @@ extern "C" int emu_deposit_static(const emu_config* cfg, const double* z, const 
   int* err = (int*)(s + o_err);
   double* dirtab = (double*)(s + o_dirtab);
   int* shift = (int*)(s + o_shift);
-  cudaStream_t st = (cudaStream_t)stream;
   auto check = [&](cudaError_t e, const char* what) {
-    return e == cudaSuccess ? EMU_OK : fail(nullptr, EMU_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    if (e == cudaSuccess) return EMU_OK;
+    forget_static_address();
+    return fail(nullptr, EMU_ECUDA, "%s: %s", what, cudaGetErrorString(e));
   };
   // the error word must start at zero; the array keeps what the last call left
   if (int rc = check(cudaMemsetAsync(err, 0, sizeof(int), st), "clear static scratch")) return rc;

@@ -223,15 +223,46 @@ __device__ __forceinline__ int shape_weights(double zs, double hp, double inv_dz
   return bad;
 }
 
+// Loads of data that a fused step launch (k_step) writes before it reads
+// them (positions, stage states, shape weights, grid potential, lattice
+// shifts) take the coherent path through L2: the read-only cache is only
+// valid across launches.  COH = true selects it; the separate kernels keep
+// the read-only path (ldd, ldi) or a plain load (ldp).
+template <bool COH>
+__device__ __forceinline__ double ldd(const double* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
+template <bool COH>
+__device__ __forceinline__ int ldi(const int* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
+template <bool COH>
+__device__ __forceinline__ double ldp(const double* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return *p;
+}
+
+// Index of this warp among the warps of a persistent grid: warp i of every
+// block comes before warp i + 1 of any block.  Units are split into
+// contiguous ranges in this order, so when a batch has fewer units than the
+// grid has warps the busy warps spread over all blocks, and so over all SMs
+// (GB300's FP64 pipe is shared by the four sub-partitions of an SM), instead
+// of filling the first blocks.  The split itself, and so every sum, does not
+// depend on this numbering.
+__device__ __forceinline__ int64_t logical_warp() {
+  return (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+}
+
 // The weights kept by the deposit for the RK stage (order 0: 1 on the own cell).
-template <int ORDER>
-__device__ __forceinline__ void load_weights(const double* __restrict__ W, int64_t P, int64_t p,
-                                             double (&w)[Sten<ORDER>::NW]) {
+template <int ORDER, bool COH = false>
+__device__ __forceinline__ void load_weights(const double* W, int64_t P, int64_t p, double (&w)[Sten<ORDER>::NW]) {
   if constexpr (ORDER == 0) {
     w[0] = 0.0; w[1] = 1.0; w[2] = 0.0;
   } else {
 #pragma unroll
-    for (int s = 0; s < Sten<ORDER>::NW; ++s) w[s] = W[s * P + p];
+    for (int s = 0; s < Sten<ORDER>::NW; ++s) w[s] = ldp<COH>(W + s * P + p);
   }
 }
 
@@ -341,6 +372,13 @@ __device__ __forceinline__ void commutator(double d12, double d13, double d23, d
 }
 
 // ------------------------------------------------------------------ kernels
+//
+// Every step kernel is a thin wrapper around a *phase*: the work of one warp
+// (deposit, RK stage) or of one block (deposit combination, lattice shifts) in
+// a persistent grid.  The separate kernels run one phase per launch; the fused
+// step kernel (k_step) runs all phases of a step in one cooperative launch
+// with grid barriers between them.  COH = true marks the fused form, whose
+// loads of data written earlier in the same launch take the coherent path.
 
 // Per-direction table from each ring's first particle: Omega and v_z = c Omega_z
 // ([4][MT]); also checks that every particle of a ring carries its direction.
@@ -365,23 +403,32 @@ __global__ void k_dirtable(Batch B, Parts pt, double* __restrict__ dirtab, int* 
 // the cell of the ring's first particle at z + frac[s] dt_b v_z ([nrows][MT]).
 struct Fracs { double v[4]; };
 
-__global__ void k_shifts(Batch B, const double* __restrict__ z, const double* __restrict__ dirtab, Fracs fr,
-                         int nrows, int* __restrict__ shift) {
-  griddep_wait();
-  const int gd = blockIdx.x * blockDim.x + threadIdx.x;
+// Position offset of RK stage s (0-based), in units of dt (Sec. 2.3, classic tableau).
+__device__ __forceinline__ double stage_frac(int s) { return s == 0 ? 0.0 : s == 3 ? 1.0 : 0.5; }
+
+__device__ __forceinline__ int lattice_cell(double z0, double frac_dt, double vz, const BoxGeo& g) {
+  const double zs = fma(frac_dt, vz, z0);
+  return wrapc((int)floor(zs * g.inv_dz), g.nz);
+}
+
+template <bool COH>
+__device__ __forceinline__ void shifts_phase(const Batch& B, int gd, const double* z, const double* __restrict__ dirtab,
+                                             const Fracs& fr, int nrows, int* shift) {
   if (gd >= B.MT) return;
   const int b = box_of_direction(B, gd);
   const BoxGeo& g = B.box[b];
-  const double z0 = z[g.poff + (int64_t)(gd - g.doff) * g.nz];
+  const double z0 = ldp<COH>(z + g.poff + (int64_t)(gd - g.doff) * g.nz);
   const double vz = dirtab[3 * B.MT + gd];
   const double dt = B.dt[b];
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    if (s < nrows) {
-      const double zs = fma(fr.v[s] * dt, vz, z0);
-      shift[s * B.MT + gd] = wrapc((int)floor(zs * g.inv_dz), g.nz);
-    }
-  }
+  for (int s = 0; s < 4; ++s)
+    if (s < nrows) shift[s * B.MT + gd] = lattice_cell(z0, fr.v[s] * dt, vz, g);
+}
+
+__global__ void k_shifts(Batch B, const double* __restrict__ z, const double* __restrict__ dirtab, Fracs fr,
+                         int nrows, int* __restrict__ shift) {
+  griddep_wait();
+  shifts_phase<false>(B, blockIdx.x * blockDim.x + threadIdx.x, z, dirtab, fr, nrows, shift);
 }
 
 // A warp's sums for one tile go to slot (warp + global tile) of the partial
@@ -397,7 +444,7 @@ __device__ __forceinline__ void flush_tile(const double (&acc)[NA], int64_t gtil
   }
 }
 
-// Deposit (Eq. 5), first launch.  MODE 0: B = N rho - Nbar rhobar^* (the
+// Deposit (Eq. 5), first phase.  MODE 0: B = N rho - Nbar rhobar^* (the
 // combination that enters H, Eq. 2); MODE 1: B = N rho; MODE 2: B = Nbar rhobar;
 // MODE 3: B = r_nu (packed matrices given per particle: the adjoint's Gamma);
 // MODE 4: the moments the diagnostics read (Eq. 10), both species in one
@@ -405,19 +452,16 @@ __device__ __forceinline__ void flush_tile(const double (&acc)[NA], int64_t gtil
 // MODE 5: MODE 0's B in the traceless components the step reads (kNT rows:
 // moment m, component c at row m * kNC + c; c = 0, 1 the diagonal differences
 // B_11 - B_22 and B_22 - B_33, c = 2..7 the off-diagonal reals 3..8).
-// Each warp walks its units in order (box, tile, direction), summing
+// Warp w walks its units in order (box, tile, direction), summing
 // w_pj (1, Omega_p) B_p over directions in registers (lane l owns cell
 // tile * T - H + l) and writing one partial per tile it touches; MODES 0 and 5
 // also store every particle's weights for the RK stage.  Positions: z + frac dt_b v_z.
-template <int MODE, int ORDER>
-__global__ void __launch_bounds__(kThreads, 2)
-k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, const double* __restrict__ Nbar,
-          const double* __restrict__ r_nu, const double* __restrict__ r_nb, const double* __restrict__ dirtab,
-          const int* __restrict__ shift, double frac, double* __restrict__ partial, double* __restrict__ W,
-          int* __restrict__ err) {
-  griddep_wait();
-  const int lane = threadIdx.x & 31;
-  const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+template <int MODE, int ORDER, bool COH>
+__device__ __forceinline__ void deposit_phase(const Batch& B, int64_t w, int lane, const double* z,
+                                              const double* __restrict__ N, const double* __restrict__ Nbar,
+                                              const double* r_nu, const double* r_nb,
+                                              const double* __restrict__ dirtab, const int* shift, double frac,
+                                              double* __restrict__ partial, double* W, int* err) {
   const int64_t u0 = unit_begin(w, B), u1 = unit_begin(w + 1, B);
   if (u0 >= u1) return;
   const int64_t P = B.Ptot;
@@ -449,9 +493,9 @@ k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, c
       const int gd = dbase + d;
       const double ox = __ldg(dirtab + gd), oy = __ldg(dirtab + MT + gd), oz = __ldg(dirtab + 2 * MT + gd);
       const double vz = __ldg(dirtab + 3 * MT + gd);
-      const int64_t p = pbase + (int64_t)d * nz + wrapc(j - __ldg(shift + gd), nz);
+      const int64_t p = pbase + (int64_t)d * nz + wrapc(j - ldi<COH>(shift + gd), nz);
       double wt[Sten<ORDER>::NW];
-      bad |= shape_weights<ORDER>(fma(pos_dt, vz, __ldg(z + p)), hp, __ldg(&g.inv_dz), __ldg(&g.nz_d), wt);
+      bad |= shape_weights<ORDER>(fma(pos_dt, vz, ldd<COH>(z + p)), hp, __ldg(&g.inv_dz), __ldg(&g.nz_d), wt);
       if ((MODE == 0 || MODE == 5) && W != nullptr && own) {   // the RK stage of these positions reads them back
 #pragma unroll
         for (int q = 0; q < Sten<ORDER>::NWS; ++q) W[q * P + p] = wt[q];
@@ -465,13 +509,14 @@ k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, c
         for (int c = 0; c < kNC; ++c) {
           double bv;
           if (c < 2) {
-            if (c == 0) bprev = fma(-n2, __ldg(r_nb + p), n1 * __ldg(r_nu + p));
-            const double bn = fma(-n2, __ldg(r_nb + (c + 1) * P + p), n1 * __ldg(r_nu + (c + 1) * P + p));
+            if (c == 0) bprev = fma(-n2, ldd<COH>(r_nb + p), n1 * ldd<COH>(r_nu + p));
+            const double bn =
+                fma(-n2, ldd<COH>(r_nb + (c + 1) * P + p), n1 * ldd<COH>(r_nu + (c + 1) * P + p));
             bv = bprev - bn;
             bprev = bn;
           } else {
             const int k = c + 1;
-            const double x = __ldg(r_nu + k * P + p), y = __ldg(r_nb + k * P + p);
+            const double x = ldd<COH>(r_nu + k * P + p), y = ldd<COH>(r_nb + k * P + p);
             bv = (k == 4 || k == 6 || k == 8) ? fma(n2, y, n1 * x) : fma(-n2, y, n1 * x);
           }
           const double cc = spread.apply(bv);
@@ -483,8 +528,8 @@ k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, c
       } else if constexpr (MODE == 4) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-          const double c1 = spread.apply(__ldg(N + p) * __ldg(r_nu + k * P + p));
-          const double c2 = spread.apply(__ldg(Nbar + p) * __ldg(r_nb + k * P + p));
+          const double c1 = spread.apply(__ldg(N + p) * ldd<COH>(r_nu + k * P + p));
+          const double c2 = spread.apply(__ldg(Nbar + p) * ldd<COH>(r_nb + k * P + p));
           acc[k] += c1;
           acc[9 + k] = fma(ox, c1, acc[9 + k]);
           acc[18 + k] += c2;
@@ -498,15 +543,15 @@ k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, c
           const double n2 = (MODE == 0 || MODE == 2) ? __ldg(Nbar + p) : 0.0;
           double bv;
           if (MODE == 0) {
-            const double x = __ldg(r_nu + k * P + p), y = __ldg(r_nb + k * P + p);
+            const double x = ldd<COH>(r_nu + k * P + p), y = ldd<COH>(r_nb + k * P + p);
             // conj(rhobar) flips the sign of the imaginary components 4, 6, 8
             bv = (k == 4 || k == 6 || k == 8) ? fma(n2, y, n1 * x) : fma(-n2, y, n1 * x);
           } else if (MODE == 1) {
-            bv = n1 * __ldg(r_nu + k * P + p);
+            bv = n1 * ldd<COH>(r_nu + k * P + p);
           } else if (MODE == 2) {
-            bv = n2 * __ldg(r_nb + k * P + p);
+            bv = n2 * ldd<COH>(r_nb + k * P + p);
           } else {
-            bv = __ldg(r_nu + k * P + p);
+            bv = ldd<COH>(r_nu + k * P + p);
           }
           const double c = spread.apply(bv);
           acc[k] += c;
@@ -521,7 +566,18 @@ k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, c
   if (bad) atomicOr(err, ERR_LATTICE);
 }
 
-// Deposit, second launch: fixed-order sum of the per-warp partials.
+template <int MODE, int ORDER>
+__global__ void __launch_bounds__(kThreads, 2)
+k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, const double* __restrict__ Nbar,
+          const double* __restrict__ r_nu, const double* __restrict__ r_nb, const double* __restrict__ dirtab,
+          const int* __restrict__ shift, double frac, double* __restrict__ partial, double* __restrict__ W,
+          int* __restrict__ err) {
+  griddep_wait();
+  deposit_phase<MODE, ORDER, false>(B, logical_warp(), threadIdx.x & 31, z, N, Nbar, r_nu, r_nb, dirtab, shift, frac,
+                                    partial, W, err);
+}
+
+// Deposit, second phase: fixed-order sum of the per-warp partials.
 // out[c * NZ + coff_b + j] (c < rows) = scale_b * (sum over the warps that own
 // units of j's tile), scale_b = kappa_b / dV_b (potential) or 1 / dV_b.  Lane l of a warp
 // takes output e0 + l (consecutive cells: coalesced reads of the partials).
@@ -530,12 +586,12 @@ k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, c
 // ..., and the first adds the split sums in warp order through shared
 // memory.  A warp keeps kCombineILP running sums (its partials taken
 // round-robin, then added pairwise) so that many loads are in flight.  The
-// order depends only on the batch, the grid and `split`: results are bitwise
-// reproducible.
+// order depends only on the batch, the number of warps that split the units
+// and `split`, not on the grid of this phase: results are bitwise reproducible.
+// The partials are read through L2 (coherent within a fused launch too).
 constexpr int kCombineILP = 8;
-__global__ void k_combine(Batch B, const double* __restrict__ partial, double* __restrict__ out, int rows,
-                          int potential, int split, int* __restrict__ err) {
-  griddep_wait();
+__device__ __forceinline__ void combine_phase(const Batch& B, const double* partial, double* out, int rows,
+                                              int potential, int split, int* err) {
   __shared__ double sums[kWarps][kLanes];
   const int64_t n = (int64_t)rows * B.NZ;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -586,6 +642,12 @@ __global__ void k_combine(Batch B, const double* __restrict__ partial, double* _
   if (bad) atomicOr(err, ERR_NONFINITE);
 }
 
+__global__ void k_combine(Batch B, const double* __restrict__ partial, double* __restrict__ out, int rows,
+                          int potential, int split, int* __restrict__ err) {
+  griddep_wait();
+  combine_phase(B, partial, out, rows, potential, split, err);
+}
+
 // Interpolation only (Eq. 6 then Eq. 2): H[k * Ptot + p] at z + frac dt_b v_z.
 template <int ORDER>
 __global__ void __launch_bounds__(kThreads, 2)
@@ -593,7 +655,7 @@ k_interpolate(Batch B, const double* __restrict__ z, const double* __restrict__ 
               const int* __restrict__ shift, const double* __restrict__ A, double frac, double* __restrict__ Hout,
               int* __restrict__ err) {
   const int lane = threadIdx.x & 31;
-  const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t w = logical_warp();
   const int64_t u0 = unit_begin(w, B), u1 = unit_begin(w + 1, B);
   const int64_t P = B.Ptot;
   const int MT = B.MT, NZ = B.NZ;
@@ -628,16 +690,20 @@ k_interpolate(Batch B, const double* __restrict__ z, const double* __restrict__ 
   if (bad) atomicOr(err, ERR_LATTICE);
 }
 
-// The RK4 update (Sec. 2.3) of particle p of box g at stage s, given its
-// interpolated self-interaction Hamiltonian Hm (Eq. 6, Eq. 2) and its
-// neutrino source matrix r (already loaded): K = -i[H, rho], Kbar =
-// -i[Hbar, rhobar] (Eq. 4) with Hbar = -H^* (plus the vacuum and matter terms
-// with POT), then the accumulator and next stage state (stage 4: the new
-// state and position).  vz points at the particle's v_z in the direction table.
-template <bool POT>
-__device__ __forceinline__ void rk_particle(const BoxGeo& g, const Parts& pt, const double* __restrict__ src_b,
-                                            int64_t P, int64_t p, int s, int dry, double bdt, double cdt, double dtb,
-                                            const double* __restrict__ vz, double (&Hm)[kNC], const double (&r)[9]) {
+// The RK4 update (Sec. 2.3) of particle p (ring direction gd) of box g at
+// stage s, given its interpolated self-interaction Hamiltonian Hm (Eq. 6,
+// Eq. 2) and its neutrino source matrix r (already loaded): K = -i[H, rho],
+// Kbar = -i[Hbar, rhobar] (Eq. 4) with Hbar = -H^* (plus the vacuum and
+// matter terms with POT), then the accumulator and next stage state (stage 4:
+// the new state and position).  vz points at the particle's v_z in the
+// direction table.  With shift_next (fused step), the first particle of each
+// ring also writes the lattice shifts of the next step's four stages
+// ([4][MTtot], as k_shifts computes them from its new position).
+template <bool POT, bool COH>
+__device__ __forceinline__ void rk_particle(const BoxGeo& g, const Parts& pt, const double* src_b, int64_t P,
+                                            int64_t p, int s, int dry, double bdt, double cdt, double dtb,
+                                            const double* __restrict__ vz, double (&Hm)[kNC], const double (&r)[9],
+                                            int* shift_next, int gd, int MTtot) {
   const double bdt2 = 2.0 * bdt, cdt2 = 2.0 * cdt;   // diagonal K are returned halved
   // Hm: H in the traceless components.  Antineutrinos: Hbar = -H^* (diagonal
   // differences and real parts flip sign, imaginary parts stay)
@@ -662,15 +728,15 @@ __device__ __forceinline__ void rk_particle(const BoxGeo& g, const Parts& pt, co
     double a[9], y[9], rb[9];
     if (which == 1) {
 #pragma unroll
-      for (int k = 0; k < 9; ++k) rb[k] = src_b[k * P + p];
+      for (int k = 0; k < 9; ++k) rb[k] = ldp<COH>(src_b + k * P + p);
     }
     if (s >= 2) {
 #pragma unroll
-      for (int k = 0; k < 9; ++k) a[k] = av[k * P + p];
+      for (int k = 0; k < 9; ++k) a[k] = ldp<COH>(av + k * P + p);
     }
     if (s == 2 || s == 3) {
 #pragma unroll
-      for (int k = 0; k < 9; ++k) y[k] = yv[k * P + p];
+      for (int k = 0; k < 9; ++k) y[k] = ldp<COH>(yv + k * P + p);
     }
     const double* rr = which ? rb : r;
     double kd[3], ko[6];
@@ -702,9 +768,14 @@ __device__ __forceinline__ void rk_particle(const BoxGeo& g, const Parts& pt, co
     }
   }
   if (s == 4) {
-    const double zn = wrap_z(fma(dtb, __ldg(vz), pt.z[p]), g.Lz);
+    const double vzv = __ldg(vz);
+    const double zn = wrap_z(fma(dtb, vzv, ldp<COH>(pt.z + p)), g.Lz);
     if (dry) pt.stage[p] = zn;  // (only to keep the work of the real stage)
     else pt.z[p] = zn;
+    if (shift_next != nullptr && p == g.poff + (int64_t)(gd - g.doff) * g.nz) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) shift_next[q * MTtot + gd] = lattice_cell(zn, stage_frac(q) * dtb, vzv, g);
+    }
   }
 }
 
@@ -723,13 +794,10 @@ __device__ __forceinline__ void rk_particle(const BoxGeo& g, const Parts& pt, co
 // weights come from the deposit.  Stages 2-4 read their state from stage_src
 // (normally the stage buffer itself, updated in place; a separate buffer when
 // the stage states are kept for the adjoint).
-template <bool POT, int ORDER>
-__global__ void __launch_bounds__(kThreads, 2)
-k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
-           const int* __restrict__ shift, const double* __restrict__ A, const double* stage_src, int s, int dry) {
-  griddep_wait();
-  const int lane = threadIdx.x & 31;
-  const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+template <bool POT, int ORDER, bool COH>
+__device__ __forceinline__ void rk_phase(const Batch& B, int64_t w, int lane, const Parts& pt, const double* W,
+                                         const double* __restrict__ dirtab, const int* shift, const double* A,
+                                         const double* stage_src, int s, int dry, int* shift_next) {
   const int64_t u0 = unit_begin(w, B), u1 = unit_begin(w + 1, B);
   if (u0 >= u1) return;
   const int64_t P = B.Ptot;
@@ -757,7 +825,7 @@ k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __rest
     const int d = lu / nt, tile = lu - d * nt;
     if (u + 1 < u1 && lu + 1 < nt * g.M) {   // prefetch the next unit of the same box
       const int dn = (lu + 1) / nt, tn = lu + 1 - dn * nt;
-      const int i0 = tn * T - __ldg(shift + g.doff + dn);   // ring index of the next unit's first cell
+      const int i0 = tn * T - ldi<COH>(shift + g.doff + dn);   // ring index of the next unit's first cell
       const int n = min(T, nz - tn * T);
       if (i0 >= 0 && i0 + n <= nz) {
         const int64_t base = g.poff + (int64_t)dn * nz + i0;
@@ -777,28 +845,38 @@ k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __rest
     const bool active = lane >= H && lane < H + T && craw < nz;
     const int gd = g.doff + d;
     const double ox = __ldg(dirtab + gd), oy = __ldg(dirtab + MT + gd), oz = __ldg(dirtab + 2 * MT + gd);
-    const int64_t p = g.poff + (int64_t)d * nz + wrapc(j - __ldg(shift + gd), nz);
+    const int64_t p = g.poff + (int64_t)d * nz + wrapc(j - ldi<COH>(shift + gd), nz);
     double wt[Sten<ORDER>::NW];
     zero_weights<ORDER>(wt);
     // the neutrino source matrix first, so its latency overlaps the interpolation
     double r[9];
     if (active) {
-      load_weights<ORDER>(W, P, p, wt);
+      load_weights<ORDER, COH>(W, P, p, wt);
 #pragma unroll
-      for (int k = 0; k < 9; ++k) r[k] = src_r[k * P + p];
+      for (int k = 0; k < 9; ++k) r[k] = ldp<COH>(src_r + k * P + p);
     }
     double Hm[kNC];
     const double* Aj = A + g.coff + j;
 #pragma unroll
     for (int c = 0; c < kNC; ++c) {
-      const double G = fma(-oz, __ldg(Aj + (int64_t)(3 * kNC + c) * NZ),
-                           fma(-oy, __ldg(Aj + (int64_t)(2 * kNC + c) * NZ),
-                               fma(-ox, __ldg(Aj + (int64_t)(kNC + c) * NZ), __ldg(Aj + (int64_t)c * NZ))));
+      const double G = fma(-oz, ldd<COH>(Aj + (int64_t)(3 * kNC + c) * NZ),
+                           fma(-oy, ldd<COH>(Aj + (int64_t)(2 * kNC + c) * NZ),
+                               fma(-ox, ldd<COH>(Aj + (int64_t)(kNC + c) * NZ), ldd<COH>(Aj + (int64_t)c * NZ))));
       Hm[c] = gather<ORDER>(wt, G);
     }
     if (!active) continue;
-    rk_particle<POT>(g, pt, src_b, P, p, s, dry, bdt, cdt, B.dt[b], dirtab + 3 * MT + gd, Hm, r);
+    rk_particle<POT, COH>(g, pt, src_b, P, p, s, dry, bdt, cdt, B.dt[b], dirtab + 3 * MT + gd, Hm, r, shift_next,
+                          gd, MT);
   }
+}
+
+template <bool POT, int ORDER>
+__global__ void __launch_bounds__(kThreads, 2)
+k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
+           const int* __restrict__ shift, const double* __restrict__ A, const double* stage_src, int s, int dry) {
+  griddep_wait();
+  rk_phase<POT, ORDER, false>(B, logical_warp(), threadIdx.x & 31, pt, W, dirtab, shift, A, stage_src, s, dry,
+                              nullptr);
 }
 
 // The RK stage with 32 cells per warp: the same arithmetic as k_rk_stage,
@@ -810,14 +888,15 @@ k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __rest
 // each side) come from the adjacent tiles of the same ring when the warp
 // handles them in order, and are computed directly (one cell at a time, by the
 // whole warp) at ring and range boundaries.
-__device__ __forceinline__ void ring_cell_G(const double* __restrict__ A, int NZ, int coff, int cell, double ox,
-                                            double oy, double oz, double (&G)[kNC]) {
+template <bool COH>
+__device__ __forceinline__ void ring_cell_G(const double* A, int NZ, int coff, int cell, double ox, double oy,
+                                            double oz, double (&G)[kNC]) {
   const double* Aj = A + coff + cell;
 #pragma unroll
   for (int c = 0; c < kNC; ++c)
-    G[c] = fma(-oz, __ldg(Aj + (int64_t)(3 * kNC + c) * NZ),
-               fma(-oy, __ldg(Aj + (int64_t)(2 * kNC + c) * NZ), fma(-ox, __ldg(Aj + (int64_t)(kNC + c) * NZ),
-                                                                     __ldg(Aj + (int64_t)c * NZ))));
+    G[c] = fma(-oz, ldd<COH>(Aj + (int64_t)(3 * kNC + c) * NZ),
+               fma(-oy, ldd<COH>(Aj + (int64_t)(2 * kNC + c) * NZ),
+                   fma(-ox, ldd<COH>(Aj + (int64_t)(kNC + c) * NZ), ldd<COH>(Aj + (int64_t)c * NZ))));
 }
 
 // Cell index on a ring of nz cells for cells within two rings of it (the
@@ -828,16 +907,14 @@ __device__ __forceinline__ int ring_wrap(int cell, int nz) {
   return cell;
 }
 
-template <bool POT, int ORDER>
-__global__ void __launch_bounds__(kThreads, 2)
-k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
-             const int* __restrict__ shift, const double* __restrict__ A, const double* stage_src, int s, int dry) {
-  griddep_wait();
+template <bool POT, int ORDER, bool COH>
+__device__ __forceinline__ void rk32_phase(const Batch& B, int64_t w, const Parts& pt, const double* W,
+                                           const double* __restrict__ dirtab, const int* shift, const double* A,
+                                           const double* stage_src, int s, int dry, int* shift_next) {
   constexpr int H = Sten<ORDER>::H, NW = Sten<ORDER>::NW;
   __shared__ double gsm[kWarps][2][kNC][kLanes];   // G of the last two units, per warp
   __shared__ double edge[kWarps][2][H][kNC];       // the H cells left / right of the unit being finished
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int64_t w = (int64_t)blockIdx.x * kWarps + wib;
   const int64_t u0 = unit32_begin(w, B), u1 = unit32_begin(w + 1, B);
   if (u0 >= u1) return;
   const int64_t P = B.Ptot;
@@ -865,7 +942,7 @@ k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __re
       cn = min(kLanes, g.nz - ct * kLanes);
       cgd = g.doff + cd;
       // prefetch this unit's particle data into L2 (it is finished next iteration)
-      const int i0 = ct * kLanes - __ldg(shift + cgd);
+      const int i0 = ct * kLanes - ldi<COH>(shift + cgd);
       if (i0 >= 0 && i0 + cn <= g.nz) {
         const int64_t base = g.poff + (int64_t)cd * g.nz + i0;
         for (int a = lane; a < narr; a += kLanes) {
@@ -882,8 +959,8 @@ k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __re
       // G of this unit's cells
       if (lane < cn) {
         double G[kNC];
-        ring_cell_G(A, NZ, g.coff, ct * kLanes + lane, __ldg(dirtab + cgd), __ldg(dirtab + MT + cgd),
-                    __ldg(dirtab + 2 * MT + cgd), G);
+        ring_cell_G<COH>(A, NZ, g.coff, ct * kLanes + lane, __ldg(dirtab + cgd), __ldg(dirtab + MT + cgd),
+                         __ldg(dirtab + 2 * MT + cgd), G);
 #pragma unroll
         for (int k = 0; k < kNC; ++k) gsm[wib][slot][k][lane] = G[k];
       }
@@ -900,8 +977,8 @@ k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __re
         if (!(next_in_ring && (H == 1 || o < cn))) {   // (a unit that continues a ring has a first cell)
           double G[kNC];
           const int cell = pt_ * kLanes + pn + o;
-          ring_cell_G(A, NZ, g.coff, H == 1 ? (cell >= g.nz ? cell - g.nz : cell) : ring_wrap(cell, g.nz), ox, oy,
-                      oz, G);
+          ring_cell_G<COH>(A, NZ, g.coff, H == 1 ? (cell >= g.nz ? cell - g.nz : cell) : ring_wrap(cell, g.nz), ox,
+                           oy, oz, G);
           if (lane == 0) {
 #pragma unroll
             for (int k = 0; k < kNC; ++k) edge[wib][1][o][k] = G[k];
@@ -922,12 +999,13 @@ k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __re
       // order), commutators, RK update
       const int psl = slot ^ 1;
       if (lane < pn) {
-        const int64_t p = g.poff + (int64_t)pd * g.nz + wrapc(pt_ * kLanes + lane - __ldg(shift + pgd), g.nz);
+        const int64_t p =
+            g.poff + (int64_t)pd * g.nz + wrapc(pt_ * kLanes + lane - ldi<COH>(shift + pgd), g.nz);
         double wt[NW];
         double r[9];
-        load_weights<ORDER>(W, P, p, wt);
+        load_weights<ORDER, COH>(W, P, p, wt);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) r[k] = src_r[k * P + p];
+        for (int k = 0; k < 9; ++k) r[k] = ldp<COH>(src_r + k * P + p);
         double Hm[kNC];
 #pragma unroll
         for (int k = 0; k < kNC; ++k) {
@@ -955,7 +1033,8 @@ k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __re
           bdt = (s == 1 || s == 4) ? dtb / 6.0 : dtb / 3.0;   // weight of K in acc
           cdt = (s == 3) ? dtb : 0.5 * dtb;                   // offset of the next stage
         }
-        rk_particle<POT>(g, pt, src_b, P, p, s, dry, bdt, cdt, dtb, dirtab + 3 * MT + pgd, Hm, r);
+        rk_particle<POT, COH>(g, pt, src_b, P, p, s, dry, bdt, cdt, dtb, dirtab + 3 * MT + pgd, Hm, r, shift_next,
+                              pgd, MT);
       }
       __syncwarp();
     }
@@ -977,8 +1056,8 @@ k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __re
         for (int o = 1; o <= H; ++o) {
           double G[kNC];
           const int cell = ct * kLanes - o;
-          ring_cell_G(A, NZ, g.coff, H == 1 ? (cell < 0 ? cell + g.nz : cell) : ring_wrap(cell, g.nz),
-                      __ldg(dirtab + cgd), __ldg(dirtab + MT + cgd), __ldg(dirtab + 2 * MT + cgd), G);
+          ring_cell_G<COH>(A, NZ, g.coff, H == 1 ? (cell < 0 ? cell + g.nz : cell) : ring_wrap(cell, g.nz),
+                           __ldg(dirtab + cgd), __ldg(dirtab + MT + cgd), __ldg(dirtab + 2 * MT + cgd), G);
           if (lane == 0) {
 #pragma unroll
             for (int k = 0; k < kNC; ++k) edge[wib][0][o - 1][k] = G[k];
@@ -988,6 +1067,141 @@ k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __re
       __syncwarp();
     }
     pb = cb; pd = cd; pt_ = ct; pn = cn; pgd = cgd;
+  }
+}
+
+template <bool POT, int ORDER>
+__global__ void __launch_bounds__(kThreads, 2)
+k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
+             const int* __restrict__ shift, const double* __restrict__ A, const double* stage_src, int s, int dry) {
+  griddep_wait();
+  rk32_phase<POT, ORDER, false>(B, logical_warp(), pt, W, dirtab, shift, A, stage_src, s, dry, nullptr);
+}
+
+// ------------------------------------------------------- fused step kernel
+//
+// All phases of nsteps RK4 steps in one cooperative launch (every block
+// resident): the lattice shifts of the first step, then per stage the deposit,
+// its combination and the RK stage, separated by grid barriers.  The first
+// particle of each ring writes the next step's shifts during stage 4 (into the
+// other of two shift tables), so later steps need no shift phase.  The
+// arithmetic and the order of every sum are those of the separate kernels with
+// the same grid: results are bitwise the same.
+//
+// Grid barrier: each block's thread 0 adds to an arrival word (block 0 adds
+// 2^31 - (blocks - 1), the others 1, so the top bit flips when the last block
+// arrives and the word is ready for the next barrier) and waits for the flip.
+// The wait is bounded: after limit_ns nanoseconds (device global timer), or as
+// soon as another block has given up, the block sets the abort word and
+// ERR_TIMEOUT and the kernel returns.  A launch that finds the abort word set
+// returns at once; the host clears it (and the arrival word) when it reports
+// the error.
+enum : int { ERR_TIMEOUT = 16 };
+
+struct StepArgs {
+  const double* dirtab;
+  int* shift;          // [4][MT] shift rows of the current step
+  int* shift2;         // [4][MT] rows of the next step
+  double* W;           // kept shape weights
+  double* At;          // traceless grid potential
+  double* partial;     // per-warp deposit partials
+  int* err;
+  unsigned* bar;       // [0] arrival word, [1] abort word
+  unsigned long long limit_ns;
+  int64_t nsteps;
+  int split;           // combine split (as the separate deposit uses)
+  int dry;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Returns true if the launch must stop (a wait gave up here or elsewhere).
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned long long limit_ns, int* err) {
+  __shared__ int stop;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int give_up = 0;
+    const unsigned inc = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
+    __threadfence();                         // this block's writes before its arrival
+    const unsigned old = atomicAdd(bar, inc);
+    const unsigned long long t0 = global_ns();
+    while (((old ^ ld_acquire_u32(bar)) & 0x80000000u) == 0) {
+      if (ld_acquire_u32(bar + 1) != 0u || global_ns() - t0 > limit_ns) {
+        atomicExch(bar + 1, 1u);
+        atomicOr(err, ERR_TIMEOUT);
+        give_up = 1;
+        break;
+      }
+    }
+    __threadfence();                         // the other blocks' writes after the barrier
+    stop = give_up;
+  }
+  __syncthreads();
+  return stop != 0;
+}
+
+// The fused kernel calls each phase as a function of its own (not inlined),
+// so that each keeps the register allocation of its separate kernel instead
+// of sharing one allocation with every other phase.
+template <int ORDER>
+__device__ __noinline__ void fused_deposit(const Batch& B, int64_t w, int lane, const Parts& pt, const double* rnu,
+                                           const double* rnb, const StepArgs& a, const int* srow, double frac) {
+  deposit_phase<5, ORDER, true>(B, w, lane, pt.z, pt.N, pt.Nbar, rnu, rnb, a.dirtab, srow, frac, a.partial, a.W,
+                                a.err);
+}
+
+__device__ __noinline__ void fused_combine(const Batch& B, const StepArgs& a) {
+  combine_phase(B, a.partial, a.At, kNT, 1, a.split, a.err);
+}
+
+template <bool POT, int ORDER, bool RK32>
+__device__ __noinline__ void fused_rk(const Batch& B, int64_t w, int lane, const Parts& pt, const StepArgs& a,
+                                     const int* srow, int s, int* nxt) {
+  if constexpr (RK32) rk32_phase<POT, ORDER, true>(B, w, pt, a.W, a.dirtab, srow, a.At, pt.stage, s, a.dry, nxt);
+  else rk_phase<POT, ORDER, true>(B, w, lane, pt, a.W, a.dirtab, srow, a.At, pt.stage, s, a.dry, nxt);
+}
+
+template <bool POT, int ORDER, bool RK32>
+__global__ void __launch_bounds__(kThreads, 2) k_step(Batch B, Parts pt, StepArgs a) {
+  __shared__ int aborted;
+  if (threadIdx.x == 0) aborted = ld_acquire_u32(a.bar + 1) != 0u;
+  __syncthreads();
+  if (aborted) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t w = logical_warp();
+  const int MT = B.MT;
+  Fracs fr;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) fr.v[q] = stage_frac(q);
+  for (int gd = blockIdx.x * blockDim.x + threadIdx.x; gd < MT; gd += gridDim.x * blockDim.x)
+    shifts_phase<true>(B, gd, pt.z, a.dirtab, fr, 4, a.shift);
+  if (grid_barrier(a.bar, a.limit_ns, a.err)) return;
+  int* sh = a.shift;
+  int* shn = a.shift2;
+  const int64_t P = B.Ptot;
+  for (int64_t n = 0; n < a.nsteps; ++n) {
+    for (int s = 1; s <= 4; ++s) {
+      const int* srow = sh + (s - 1) * MT;
+      const double* rnu = s == 1 ? pt.rho : pt.stage;
+      const double* rnb = s == 1 ? pt.rhobar : pt.stage + 9 * P;
+      fused_deposit<ORDER>(B, w, lane, pt, rnu, rnb, a, srow, stage_frac(s - 1));
+      if (grid_barrier(a.bar, a.limit_ns, a.err)) return;
+      fused_combine(B, a);
+      if (grid_barrier(a.bar, a.limit_ns, a.err)) return;
+      fused_rk<POT, ORDER, RK32>(B, w, lane, pt, a, srow, s, s == 4 ? shn : nullptr);
+      if (grid_barrier(a.bar, a.limit_ns, a.err)) return;
+    }
+    int* t = sh; sh = shn; shn = t;
   }
 }
 
@@ -1177,7 +1391,7 @@ k_adj_a(Batch B, Parts pt, const double* __restrict__ W, const double* __restric
         const double* __restrict__ lamn, int s, double* __restrict__ lam_out, double* __restrict__ Gam) {
   griddep_wait();
   const int lane = threadIdx.x & 31;
-  const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t w = logical_warp();
   const int64_t u0 = unit_begin(w, B), u1 = unit_begin(w + 1, B);
   if (u0 >= u1) return;
   const int64_t P = B.Ptot;
@@ -1259,7 +1473,7 @@ k_adj_b(Batch B, Parts pt, const double* __restrict__ W, const double* __restric
         double* __restrict__ lam_tot, double* __restrict__ gN, double* __restrict__ gNbar) {
   griddep_wait();
   const int lane = threadIdx.x & 31;
-  const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t w = logical_warp();
   const int64_t u0 = unit_begin(w, B), u1 = unit_begin(w + 1, B);
   if (u0 >= u1) return;
   const int64_t P = B.Ptot;
@@ -1362,7 +1576,7 @@ k_adj_seed(Batch B, Parts pt, const double* __restrict__ dirtab, const int* __re
            const double* __restrict__ dmom, double* __restrict__ lam, double* __restrict__ gN,
            double* __restrict__ gNbar, int* __restrict__ err) {
   const int lane = threadIdx.x & 31;
-  const int64_t w = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t w = logical_warp();
   const int64_t u0 = unit_begin(w, B), u1 = unit_begin(w + 1, B);
   if (u0 >= u1) return;
   const int64_t P = B.Ptot;

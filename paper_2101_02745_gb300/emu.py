@@ -24,6 +24,7 @@ EMU_ENUMERIC = -3
 EMU_ETIMEOUT = -4
 EMU_ELATTICE = -5
 N_DIAG = 63
+AUTOTUNE_CANDIDATES = 10   # EMU_AUTOTUNE_CANDIDATES
 
 
 class EmuError(RuntimeError):
@@ -108,6 +109,8 @@ def load(build_if_missing: bool = False):
         "emu_autotune": (i32, [vp, i32, vp, vp]),
         "emu_set_grid": (i32, [vp, ctypes.c_int32]),
         "emu_set_rk_form": (i32, [vp, ctypes.c_int32]),
+        "emu_set_step_form": (i32, [vp, ctypes.c_int32]),
+        "emu_set_barrier_timeout": (i32, [vp, i64]),
         "emu_set_oscillation": (i32, [vp, ctypes.c_int32, ctypes.POINTER(emu_oscillation)]),
         "emu_adjoint_workspace_bytes": (i64, [cfgp]),
         "emu_batch_adjoint_workspace_bytes": (i64, [cfgp, ctypes.c_int32]),
@@ -218,7 +221,7 @@ def emu_kernel_launches(box) -> int:
     return int(load().emu_kernel_launches(box))
 
 
-KERNEL_CLASSES = ("shifts", "deposit", "rk_stage", "combine", "other")
+KERNEL_CLASSES = ("shifts", "deposit", "rk_stage", "combine", "other", "step")
 
 
 def emu_profile(box, enable: bool):
@@ -306,9 +309,9 @@ def emu_batch_diagnostics(box, out, on_host: int):
 
 
 def emu_autotune(box, trial_steps: int):
-    """(choice index, per-step ms of the 6 candidates: grid index // 2, RK form % 2)."""
+    """(choice index, per-step ms of the candidates; see AUTOTUNE_GRID_FORMS)."""
     choice = ctypes.c_int32()
-    ms = np.zeros(6)
+    ms = np.zeros(AUTOTUNE_CANDIDATES)
     _check(box, load().emu_autotune(box, int(trial_steps), ctypes.byref(choice), _host_ptr(ms)))
     return int(choice.value), ms
 
@@ -319,6 +322,27 @@ def emu_set_grid(box, blocks: int):
 
 def emu_set_rk_form(box, form: int):
     _check(box, load().emu_set_rk_form(box, int(form)))
+
+
+def emu_set_step_form(box, form: int):
+    _check(box, load().emu_set_step_form(box, int(form)))
+
+
+def emu_set_barrier_timeout(box, ns: int):
+    _check(box, load().emu_set_barrier_timeout(box, int(ns)))
+
+
+# (step form, grid blocks, RK form) of each autotuner candidate, as emu.h lists them
+AUTOTUNE_GRID_FORMS = tuple((0, g, f) for g in (304, 152, 608) for f in (0, 1)) + \
+    tuple((1, g, f) for g in (304, 152) for f in (0, 1))
+
+
+def apply_choice(box, choice: int):
+    """Set a box to autotuner candidate `choice` (e.g. the choice made on a twin box)."""
+    form, grid, rk = AUTOTUNE_GRID_FORMS[choice]
+    emu_set_grid(box, grid)
+    emu_set_rk_form(box, rk)
+    emu_set_step_form(box, form)
 
 
 def make_oscillation(d: dict) -> emu_oscillation:
@@ -392,7 +416,7 @@ def emu_destroy(box):
 
 # ------------------------------------------------------------ convenience
 
-def _fibonacci(M):
+def _no_dirs(M):
     raise ValueError("explicit directions for some boxes of a batch need explicit directions for all")
 
 def _ordered(fn):
@@ -454,15 +478,15 @@ class Box:
         emu_bind(self.box, self.parts, self.ws_ptr, self.ws_bytes, self.stream.cuda_stream)
 
     @classmethod
-    def from_workloads(cls, wls, device="cuda", init=True):
+    def from_workloads(cls, wls, device="cuda", init=True, stream=None):
         """A batch of the given workloads (one box each), initialised together."""
         cfgs = [make_config(w.nz, w.ndir, w.Lz, w.kappa, w.c_light, w.cfl_adv, w.cfl_flavor, w.area, w.shape_order)
                 for w in wls]
-        b = cls(0, 0, 0, 0, 0, device=device, cfgs=cfgs)
+        b = cls(0, 0, 0, 0, 0, device=device, cfgs=cfgs, stream=stream)
         if init:
             dirs = None
             if any(w.dirs is not None for w in wls):
-                dirs = np.concatenate([np.asarray(w.dirs if w.dirs is not None else _fibonacci(w.ndir)).reshape(-1)
+                dirs = np.concatenate([np.asarray(w.dirs if w.dirs is not None else _no_dirs(w.ndir)).reshape(-1)
                                        for w in wls])
             emu_batch_init_particles(b.box, np.concatenate([w.n_nu for w in wls]),
                                      np.concatenate([w.n_nubar for w in wls]),
@@ -472,9 +496,9 @@ class Box:
         return b
 
     @classmethod
-    def from_workload(cls, wl, device="cuda", init=True):
+    def from_workload(cls, wl, device="cuda", init=True, stream=None):
         b = cls(wl.nz, wl.ndir, wl.Lz, wl.kappa, wl.c_light, wl.cfl_adv, wl.cfl_flavor, wl.area, device=device,
-                shape_order=wl.shape_order)
+                shape_order=wl.shape_order, stream=stream)
         if init:
             b.init(wl.n_nu, wl.n_nubar, wl.f_nu, wl.f_nubar, wl.dirs, wl.alpha, wl.seed)
         return b
@@ -564,6 +588,16 @@ class Box:
     def set_rk_form(self, form: int):
         """1: RK stage with 32 cells per warp, 0: halo-lane form, -1: by units per warp."""
         emu_set_rk_form(self.box, form)
+
+    def set_step_form(self, form: int):
+        """1: one cooperative launch per step, 0: one launch per phase."""
+        emu_set_step_form(self.box, form)
+
+    def set_barrier_timeout(self, ns: int):
+        emu_set_barrier_timeout(self.box, ns)
+
+    def apply_choice(self, choice: int):
+        apply_choice(self.box, choice)
 
     @_ordered
     def set_oscillation(self, osc, box=-1):
@@ -684,90 +718,53 @@ class Box:
         emu_set_particles(self.box, *args, 1)
 
 
-class HostFeed:
-    """Double-buffered feed of per-step particle state from pinned host memory.
-
-    `prefetch()` starts copying the host arrays (z, rho, rhobar) into a device
-    staging copy on a side stream; `load()` makes the box's stream wait for
-    that copy and moves the staging copy into the box's bound arrays with
-    emu_set_particles (device to device), after which the next prefetch may
-    overwrite the staging copy.  The host-to-device transfer of the next step's
-    inputs thus runs while the box computes the current step."""
-
-    KEYS = ("z", "rho", "rhobar")
-
-    def __init__(self, box: "Box", pinned: dict):
-        torch = box.torch
-        self.box = box
-        self.pinned = {k: pinned[k] for k in self.KEYS}
-        self.staging = {k: torch.empty_like(box.t[k]) for k in self.KEYS}
-        self.copy = torch.cuda.Stream(box.device)
-        self.ready = torch.cuda.Event()
-        self.consumed = None
-
-    @property
-    def h2d_bytes(self) -> int:
-        return sum(v.numel() * v.element_size() for v in self.pinned.values())
-
-    def prefetch(self):
-        torch = self.box.torch
-        if self.consumed is not None:
-            self.copy.wait_event(self.consumed)
-        with torch.cuda.stream(self.copy):
-            for k in self.KEYS:
-                self.staging[k].copy_(self.pinned[k], non_blocking=True)
-        self.ready.record(self.copy)
-
-    def load(self):
-        torch = self.box.torch
-        self.box.stream.wait_event(self.ready)
-        st = self.staging
-        emu_set_particles(self.box.box, st["z"].data_ptr(), None, None, None, None, None, st["rho"].data_ptr(),
-                          st["rhobar"].data_ptr(), 0)
-        self.consumed = torch.cuda.Event()
-        self.consumed.record(self.box.stream)
-
-
-
 class PingPongFeed:
-    """Per-step particle state from pinned host memory for two boxes of one
-    configuration that take turns.  While one box steps, the next step's state
-    (z, rho, rhobar) is copied from the host straight into the other box's
-    particle arrays on a side stream, so nothing is installed on the device
-    between steps.  `next_box()` returns the box whose state is loaded for this
-    step (its stream waits for that copy) and starts the copy for the
-    following step into the other box."""
+    """Per-step particle state from host memory for two boxes of one
+    configuration that take turns, through the host-buffer path of the C ABI
+    (emu_set_particles with on_host = 1).  While one box steps, the next step's
+    state (z, rho, rhobar) is copied from the host into the other box's
+    particle arrays on that box's own stream, so the copy overlaps the step.
+    The boxes need distinct streams; the host arrays should be pinned (page-
+    locked) for the copy to run asynchronously.
+
+    `prime()` installs the first step's state in box 0; `step(enqueue)` calls
+    enqueue(box) on the box that holds this step's state (the caller enqueues
+    that box's work, asynchronously), then installs the next step's state in
+    the other box (the call returns once that copy is done) and returns the box
+    that was stepped."""
 
     KEYS = ("z", "rho", "rhobar")
 
-    def __init__(self, boxes, pinned: dict):
+    def __init__(self, boxes, host: dict):
         if len(boxes) != 2 or boxes[0].P != boxes[1].P:
             raise ValueError("two boxes of the same configuration")
-        torch = boxes[0].torch
+        if boxes[0].stream == boxes[1].stream:
+            raise ValueError("the two boxes need distinct streams")
         self.boxes = list(boxes)
-        self.pinned = {k: pinned[k] for k in self.KEYS}
-        self.copy = torch.cuda.Stream(boxes[0].device)
-        self.ready = [torch.cuda.Event(), torch.cuda.Event()]
+        self.host = {k: host[k] for k in self.KEYS}
         self.turn = 0
+
+    @staticmethod
+    def _ptr(a):
+        return ctypes.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
 
     @property
     def h2d_bytes(self) -> int:
-        return sum(v.numel() * v.element_size() for v in self.pinned.values())
+        return sum(int(v.numel() * v.element_size()) if hasattr(v, "numel") else int(v.nbytes)
+                   for v in self.host.values())
 
-    def prefetch(self, k: int):
-        """Copy the host state into box k's arrays once box k is done with them."""
-        torch = self.boxes[0].torch
-        b = self.boxes[k]
-        self.copy.wait_stream(b.stream)
-        with torch.cuda.stream(self.copy):
-            for key in self.KEYS:
-                b.t[key].copy_(self.pinned[key], non_blocking=True)
-        self.ready[k].record(self.copy)
+    def install(self, k: int):
+        h = self.host
+        emu_set_particles(self.boxes[k].box, self._ptr(h["z"]), None, None, None, None, None, self._ptr(h["rho"]),
+                          self._ptr(h["rhobar"]), 1)
 
-    def next_box(self) -> "Box":
+    def prime(self):
+        self.install(0)
+
+    def step(self, enqueue) -> "Box":
         k = self.turn % 2
         b = self.boxes[k]
-        b.stream.wait_event(self.ready[k])
-        self.prefetch(1 - k)
+        enqueue(b)
+        self.install(1 - k)
         self.turn += 1
         return b

@@ -64,7 +64,18 @@ def fd_gradient(sim, theta, h=1e-6):
 
 
 def rel_rows(a, b):
-    return [float(np.linalg.norm(a[k] - b[k]) / np.linalg.norm(b[k])) for k in range(2)]
+    """Per objective: ||a - b|| / ||b|| over its gradient row, and, so that a
+    component much smaller than the row's largest cannot hide inside the norm,
+    the worst component error relative to that component's own size (floored
+    at 1e-3 of the row norm: |a_i - b_i| / (|b_i| + 1e-3 ||b||)).  The larger
+    of the two is compared with the 1e-5 bar."""
+    out = []
+    for k in range(2):
+        nb = np.linalg.norm(b[k])
+        row = np.linalg.norm(a[k] - b[k]) / nb
+        comp = np.max(np.abs(a[k] - b[k]) / (np.abs(b[k]) + 1e-3 * nb))
+        out.append(float(max(row, comp)))
+    return out
 
 
 def _kw(wl):

@@ -102,7 +102,7 @@ def test_autotune_leaves_state_and_keeps_parity(torch):
     box = Box.from_workloads(wls)
     h0 = box.get_host()
     choice, ms = box.autotune(trial_steps=2)
-    assert 0 <= choice < 6 and np.all(ms > 0)
+    assert 0 <= choice < len(ms) and ms[choice] > 0 and np.all((ms > 0) | (ms == -1.0))
     h1 = box.get_host()
     for k in h0:
         assert np.array_equal(h0[k], h1[k]), k

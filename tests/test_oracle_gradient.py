@@ -26,6 +26,7 @@ def test_unperturbed_abundance_gradient_closed_form():
     kw = _kw(wl)
     theta = np.array([4.0e32, 5.0e32, 0.3e32, -0.2e32, 0.5e32, -0.4e32, 0.1e32, -0.9e32])
     g = gradient.fd_gradient(kw, theta, 0.0, 0, 2e-12, 6)
+    assert np.all(np.isnan(g[1]))                      # L1 = log <|n_emu|> is undefined without a perturbation
     M = wl.ndir
     mu = 1.0 - (2.0 * np.arange(M) + 1.0) / M          # Fibonacci midpoint directions
     phi = np.arange(M) * np.pi * (3.0 - np.sqrt(5.0))
