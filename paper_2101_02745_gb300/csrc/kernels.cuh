@@ -225,22 +225,34 @@ __device__ __forceinline__ int shape_weights(double zs, double hp, double inv_dz
 
 // Loads of data that a fused step launch (k_step) writes before it reads
 // them (positions, stage states, shape weights, grid potential, lattice
-// shifts) take the coherent path through L2: the read-only cache is only
-// valid across launches.  COH = true selects it; the separate kernels keep
-// the read-only path (ldd, ldi) or a plain load (ldp).
+// shifts) must not take the read-only (non-coherent) path, which is only
+// valid across launches.  COH = true selects a weak global load instead: it
+// may hit in L1, which the acquire fence of every grid barrier invalidates,
+// so after a barrier it sees what other blocks wrote before it.  The
+// separate kernels keep the read-only path (ldd, ldi) or a plain load (ldp).
+__device__ __forceinline__ double ld_weak(const double* p) {
+  double v;
+  asm volatile("ld.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int ld_weak(const int* p) {
+  int v;
+  asm volatile("ld.global.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
 template <bool COH>
 __device__ __forceinline__ double ldd(const double* p) {
-  if constexpr (COH) return __ldcg(p);
+  if constexpr (COH) return ld_weak(p);
   else return __ldg(p);
 }
 template <bool COH>
 __device__ __forceinline__ int ldi(const int* p) {
-  if constexpr (COH) return __ldcg(p);
+  if constexpr (COH) return ld_weak(p);
   else return __ldg(p);
 }
 template <bool COH>
 __device__ __forceinline__ double ldp(const double* p) {
-  if constexpr (COH) return __ldcg(p);
+  if constexpr (COH) return ld_weak(p);
   else return *p;
 }
 
@@ -1150,22 +1162,22 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned long long l
   return stop != 0;
 }
 
-// The fused kernel calls each phase as a function of its own (not inlined),
-// so that each keeps the register allocation of its separate kernel instead
-// of sharing one allocation with every other phase.
+// The phases of the fused kernel, inlined (measured on GB300: calling them as
+// separate functions, which keeps each phase's register allocation but saves
+// and restores registers around every call, was 4-5% slower per step).
 template <int ORDER>
-__device__ __noinline__ void fused_deposit(const Batch& B, int64_t w, int lane, const Parts& pt, const double* rnu,
+__device__ __forceinline__ void fused_deposit(const Batch& B, int64_t w, int lane, const Parts& pt, const double* rnu,
                                            const double* rnb, const StepArgs& a, const int* srow, double frac) {
   deposit_phase<5, ORDER, true>(B, w, lane, pt.z, pt.N, pt.Nbar, rnu, rnb, a.dirtab, srow, frac, a.partial, a.W,
                                 a.err);
 }
 
-__device__ __noinline__ void fused_combine(const Batch& B, const StepArgs& a) {
+__device__ __forceinline__ void fused_combine(const Batch& B, const StepArgs& a) {
   combine_phase(B, a.partial, a.At, kNT, 1, a.split, a.err);
 }
 
 template <bool POT, int ORDER, bool RK32>
-__device__ __noinline__ void fused_rk(const Batch& B, int64_t w, int lane, const Parts& pt, const StepArgs& a,
+__device__ __forceinline__ void fused_rk(const Batch& B, int64_t w, int lane, const Parts& pt, const StepArgs& a,
                                      const int* srow, int s, int* nxt) {
   if constexpr (RK32) rk32_phase<POT, ORDER, true>(B, w, pt, a.W, a.dirtab, srow, a.At, pt.stage, s, a.dry, nxt);
   else rk_phase<POT, ORDER, true>(B, w, lane, pt, a.W, a.dirtab, srow, a.At, pt.stage, s, a.dry, nxt);
