@@ -51,51 +51,9 @@
 #include <stdlib.h>
 #include <string.h>
 
-typedef double complex cplx;
+#include "emu_oracle.h"
 
 static const double OR_PI = 3.14159265358979323846;
-
-/* Simulation parameters.  Layout mirrored by a ctypes Structure. */
-typedef struct {
-  int32_t nz;         /* number of cells on the periodic grid */
-  int32_t ndir;       /* particles (directions) per cell, N_ppz of Eq. 8 */
-  double Lz;          /* domain length [cm] */
-  double area;        /* transverse cell area [cm^2] */
-  double kappa;       /* sqrt(2) G_F / hbar [cm^3 / s] */
-  double c_light;     /* speed of light [cm / s] */
-  double cfl_adv;     /* C of Eq. 7 */
-  double cfl_flavor;  /* C_F of Eq. 7 */
-  /* Vacuum and matter terms of Eq. 2 (off when osc_on == 0):
-   * masses m_i c^2 [eV], mixing angles theta12, theta13, theta23 and the
-   * phase delta [rad] of the standard three-angle mixing matrix, neutrino
-   * energy [erg], net electron density n_e [cm^-3], hbar [erg s], erg per eV. */
-  int32_t osc_on;
-  int32_t shape_order; /* 0..3: degree of the B-spline shape (Sec. 2.2.1), 2 = quadratic */
-  double mass_eV[3];
-  double theta12, theta13, theta23, delta_cp;
-  double energy_erg;
-  double n_e;
-  double hbar;
-  double erg_per_eV;
-} or_config;
-
-/* One computational particle (Sec. 2.2): position, direction, weights and
- * the two full 3x3 density matrices.  Flavour index order e, mu, tau. */
-typedef struct {
-  double z;
-  double omega[3];
-  double N, Nbar;
-  cplx rho[3][3];
-  cplx rhobar[3][3];
-} or_particle;
-
-/* One grid cell: the direction-integrated quantities of Eq. 5. */
-typedef struct {
-  cplx n[3][3];
-  cplx nbar[3][3];
-  cplx f[3][3][3];    /* f[i][a][b]: spatial component i of f_ab */
-  cplx fbar[3][3][3];
-} or_cell;
 
 /* ---------------------------------------------------------------- RNG --- */
 

@@ -21,6 +21,8 @@ import numpy as np
 
 _HERE = Path(__file__).resolve().parent
 _SRC = _HERE / "emu_oracle.c"
+_SRCS = (_SRC, _HERE / "emu_oracle3d.c")
+_HDR = _HERE / "emu_oracle.h"
 _LIB = _HERE / "liboracle.so"
 
 PARTICLE = np.dtype(
@@ -70,12 +72,13 @@ class OrConfig(ctypes.Structure):
 
 
 def build(force: bool = False) -> Path:
-    """Compile emu_oracle.c with gcc (-O2, no fast-math) into liboracle.so."""
-    if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
+    """Compile emu_oracle.c and emu_oracle3d.c with gcc (-O2, no fast-math) into liboracle.so."""
+    newest = max(f.stat().st_mtime for f in _SRCS + (_HDR,))
+    if force or not _LIB.exists() or _LIB.stat().st_mtime < newest:
         tmp = _LIB.with_suffix(f".so.tmp{os.getpid()}")
         subprocess.check_call(
             ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
-             "-o", str(tmp), str(_SRC), "-lm"]
+             "-o", str(tmp), *map(str, _SRCS), "-lm"]
         )
         os.replace(tmp, _LIB)
     return _LIB
@@ -109,11 +112,24 @@ def lib():
         L.or_mixing_matrix.argtypes = [cfgp, vp]; L.or_mixing_matrix.restype = None
         L.or_vacuum_matter.argtypes = [cfgp, vp, vp]; L.or_vacuum_matter.restype = None
         L.or_domain_averages.argtypes = [cfgp, vp, vp, vp]; L.or_domain_averages.restype = None
-        for name in ("or_sizeof_particle", "or_sizeof_cell", "or_sizeof_config"):
+        cfg3p = ctypes.POINTER(OrConfig3)
+        L.or3_shape.argtypes = [cfg3p, vp, vp, vp]; L.or3_shape.restype = ctypes.c_int
+        L.or3_cell_volume.argtypes = [cfg3p]; L.or3_cell_volume.restype = dbl
+        L.or3_init.argtypes = [cfg3p, vp, vp, vp, vp, vp, dbl, u64, vp]; L.or3_init.restype = ctypes.c_int
+        L.or3_deposit.argtypes = [cfg3p, vp, i64, vp]; L.or3_deposit.restype = None
+        L.or3_hamiltonian.argtypes = [cfg3p, vp, vp, vp]; L.or3_hamiltonian.restype = None
+        L.or3_rhs.argtypes = [cfg3p, vp, i64, vp, vp, vp]; L.or3_rhs.restype = None
+        L.or3_rk4_step.argtypes = [cfg3p, vp, i64, dbl]; L.or3_rk4_step.restype = ctypes.c_int
+        L.or3_run.argtypes = [cfg3p, vp, i64, dbl, i64]; L.or3_run.restype = ctypes.c_int
+        L.or3_timestep.argtypes = [cfg3p, vp]; L.or3_timestep.restype = dbl
+        for name in ("or_sizeof_particle", "or_sizeof_cell", "or_sizeof_config", "or3_sizeof_particle",
+                     "or3_sizeof_config"):
             getattr(L, name).restype = ctypes.c_int32
         assert L.or_sizeof_particle() == PARTICLE.itemsize, "particle struct mismatch"
         assert L.or_sizeof_cell() == CELL.itemsize, "cell struct mismatch"
         assert L.or_sizeof_config() == ctypes.sizeof(OrConfig), "config struct mismatch"
+        assert L.or3_sizeof_particle() == PARTICLE3.itemsize, "3D particle struct mismatch"
+        assert L.or3_sizeof_config() == ctypes.sizeof(OrConfig3), "3D config struct mismatch"
         _lib = L
     return _lib
 
@@ -272,3 +288,105 @@ def domain_averages(cfg: OrConfig, grid: np.ndarray):
     m = np.zeros((2, 3, 3), complex)
     lib().or_domain_averages(ctypes.byref(cfg), _ptr(grid), _ptr(a), _ptr(m))
     return a, m
+
+
+# ------------------------------------------------------------------ 3D grid
+
+PARTICLE3 = np.dtype(
+    [
+        ("x", "f8", (3,)),
+        ("omega", "f8", (3,)),
+        ("N", "f8"),
+        ("Nbar", "f8"),
+        ("rho", "c16", (3, 3)),
+        ("rhobar", "c16", (3, 3)),
+    ],
+    align=True,
+)
+
+
+class OrConfig3(ctypes.Structure):
+    _fields_ = [("c", OrConfig), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("Lx", ctypes.c_double),
+                ("Ly", ctypes.c_double)]
+
+
+def config3(nx, ny, nz, ndir, Lx, Ly, Lz, kappa, c_light, cfl_adv=0.4, cfl_flavor=0.4, osc=None,
+            shape_order=2) -> OrConfig3:
+    """3D periodic box of nx x ny x nz cells (see emu_oracle3d.c)."""
+    c = OrConfig3()
+    c.c = config(nz, ndir, Lz, kappa, c_light, cfl_adv, cfl_flavor, Lx * Ly, osc, shape_order)
+    c.nx, c.ny, c.Lx, c.Ly = int(nx), int(ny), float(Lx), float(Ly)
+    return c
+
+
+def ncells3(cfg: OrConfig3) -> int:
+    return cfg.nx * cfg.ny * cfg.c.nz
+
+
+def cell_volume3(cfg: OrConfig3) -> float:
+    return float(lib().or3_cell_volume(ctypes.byref(cfg)))
+
+
+def shape3(cfg: OrConfig3, x):
+    """(cell indices, weights) of the tensor-product shape of a particle at x (3,)."""
+    x = np.ascontiguousarray(x, float)
+    cells = np.zeros(64, np.int32)
+    w = np.zeros(64)
+    n = lib().or3_shape(ctypes.byref(cfg), _ptr(x), _ptr(cells), _ptr(w))
+    return cells[:n], w[:n]
+
+
+def init3(cfg: OrConfig3, n_nu, n_nubar, f_nu, f_nubar, alpha=1e-6, seed=0, dirs=None):
+    """Particles of Eq. 8/9 on the 3D lattice, numbered p = d * ncells + c0."""
+    C, M = ncells3(cfg), cfg.c.ndir
+    n_nu = np.ascontiguousarray(np.broadcast_to(np.asarray(n_nu, float), (C,)))
+    n_nubar = np.ascontiguousarray(np.broadcast_to(np.asarray(n_nubar, float), (C,)))
+    f_nu = np.ascontiguousarray(np.broadcast_to(np.asarray(f_nu, float), (C, 3)))
+    f_nubar = np.ascontiguousarray(np.broadcast_to(np.asarray(f_nubar, float), (C, 3)))
+    parts = np.zeros(C * M, PARTICLE3)
+    dptr = None
+    if dirs is not None:
+        dirs = np.ascontiguousarray(np.asarray(dirs, float).reshape(M, 3))
+        dptr = _ptr(dirs)
+    rc = lib().or3_init(ctypes.byref(cfg), dptr, _ptr(n_nu), _ptr(n_nubar), _ptr(f_nu), _ptr(f_nubar),
+                        float(alpha), int(seed), _ptr(parts))
+    if rc != 0:
+        raise ValueError("negative particle weight: a flux factor exceeds 1/3")
+    return parts
+
+
+def deposit3(cfg: OrConfig3, parts: np.ndarray) -> np.ndarray:
+    grid = np.zeros(ncells3(cfg), CELL)
+    lib().or3_deposit(ctypes.byref(cfg), _ptr(parts), len(parts), _ptr(grid))
+    return grid
+
+
+def hamiltonian3(cfg: OrConfig3, grid: np.ndarray, parts: np.ndarray) -> np.ndarray:
+    H = np.zeros((len(parts), 3, 3), complex)
+    L = lib()
+    for p in range(len(parts)):
+        L.or3_hamiltonian(ctypes.byref(cfg), _ptr(grid), _ptr(parts[p:p + 1]), _ptr(H[p]))
+    return H
+
+
+def rhs3(cfg: OrConfig3, parts: np.ndarray):
+    P = len(parts)
+    grid = np.zeros(ncells3(cfg), CELL)
+    dr = np.zeros((P, 3, 3), complex)
+    db = np.zeros((P, 3, 3), complex)
+    lib().or3_rhs(ctypes.byref(cfg), _ptr(parts), P, _ptr(grid), _ptr(dr), _ptr(db))
+    return dr, db, grid
+
+
+def rk4_step3(cfg: OrConfig3, parts: np.ndarray, dt: float) -> None:
+    if lib().or3_rk4_step(ctypes.byref(cfg), _ptr(parts), len(parts), float(dt)) != 0:
+        raise MemoryError("oracle scratch allocation failed")
+
+
+def run3(cfg: OrConfig3, parts: np.ndarray, dt: float, nsteps: int) -> None:
+    if lib().or3_run(ctypes.byref(cfg), _ptr(parts), len(parts), float(dt), int(nsteps)) != 0:
+        raise MemoryError("oracle scratch allocation failed")
+
+
+def timestep3(cfg: OrConfig3, grid: np.ndarray) -> float:
+    return float(lib().or3_timestep(ctypes.byref(cfg), _ptr(grid)))
