@@ -392,6 +392,66 @@ int emu_adjoint_step_recorded(emu_box* box, double dt, const void* rec, double* 
  * Works on batches.  Errors: EMU_EINVAL (NULL pointer). */
 int emu_weight_gradient(emu_box* box, const double* gN, const double* gNbar, double* out, int on_host);
 
+/* --------------------------------------------------------------- 3D boxes
+ *
+ * The method on a 3D periodic grid (the paper's runs are 1D; Sec. 5 names 3D
+ * runs as future work; Eq. 5 and Eq. 6 are stated for any grid).  A 3D box has
+ * nx x ny x nz cells over [0, Lx) x [0, Ly) x [0, Lz), cell index
+ * c = (jx * ny + jy) * nz + jz, and ndir particles per cell: particle
+ * p = d * C + c0 (C = nx ny nz) starts at the centre of cell c0 with direction
+ * d.  Its shape is the tensor product of the 1D shape of order shape_order on
+ * each axis (w_pj = product of the three 1D weights), the cell volume is
+ * dx dy dz, and Eq. 7 takes the smallest cell edge.  The lattice contract of
+ * 1D holds on every axis: the particles of a direction keep a common offset
+ * from their cells, so particle (d, site) lies in cell site + s_d (mod the
+ * cell counts) with one shift per axis; the step kernels report EMU_ELATTICE
+ * otherwise.
+ *
+ * A 3D box is an emu_box created by emu3_create and bound by emu3_bind (which
+ * adds the x and y position arrays to emu_particles: z stays in
+ * emu_particles).  These calls work on it as on a 1D box: emu_set_particles,
+ * emu_get_particles (z, Omega, weights, rho, rhobar), emu_deposit,
+ * emu_interpolate_H, emu_rk_stage, emu_step, emu_batch_step, emu_moments
+ * ([72][C]), emu_diagnostics, emu_timestep, emu_batch_timestep,
+ * emu_batch_set_dt, emu_set_grid, emu_autotune (the one-launch-per-phase
+ * candidates), emu_set_oscillation, emu_sync, the timing calls, emu_destroy.
+ * The others (the adjoint calls, emu_weight_gradient, the fused step form)
+ * return EMU_EINVAL for a 3D box. */
+typedef struct {
+  int32_t nx, ny, nz;  /* cells per axis, each >= 1 */
+  int32_t ndir;        /* particles per cell (directions), >= 1 */
+  double Lx, Ly, Lz;   /* domain lengths [cm], > 0 */
+  double kappa;        /* sqrt(2) G_F / hbar [cm^3/s] */
+  double c_light;      /* speed of light [cm/s] */
+  double cfl_adv;      /* C of Eq. 7 (with the smallest cell edge) */
+  double cfl_flavor;   /* C_F of Eq. 7 */
+  int32_t shape_order; /* 0-3, the 1D shape of every axis (2 = quadratic) */
+  int32_t reserved;    /* must be 0 */
+} emu3_config;
+
+/* Workspace bytes of a 3D box (negative for an invalid configuration). */
+int64_t emu3_workspace_bytes(const emu3_config* cfg);
+
+/* Validate cfg and create a 3D box (host memory only). */
+int emu3_create(const emu3_config* cfg, emu_box** out);
+
+/* As emu_bind, plus the device arrays x[P], y[P] of the positions on the x
+ * and y axes (caller-owned; P = ndir nx ny nz). */
+int emu3_bind(emu_box* box, const emu_particles* parts, double* x, double* y, void* workspace,
+              int64_t workspace_bytes, void* stream);
+
+/* Initialise every particle (Sec. 3.1, Eq. 8, 9) as emu_init_particles does,
+ * on the 3D lattice: host arrays n_nu[C], n_nubar[C], f_nu[3C], f_nubar[3C]
+ * in cell-index order; dirs[3 ndir] or NULL (Fibonacci sphere). */
+int emu3_init_particles(emu_box* box, const double* n_nu, const double* n_nubar, const double* f_nu,
+                        const double* f_nubar, const double* dirs, double alpha, uint64_t seed);
+
+/* Copy the x and y positions in or out (either may be NULL; on_host as in
+ * emu_get_particles).  Setting positions re-validates nothing until the next
+ * kernel that checks the lattice. */
+int emu3_get_positions(emu_box* box, double* x, double* y, int on_host);
+int emu3_set_positions(emu_box* box, const double* x, const double* y, int on_host);
+
 /* Wait for the box's stream and report errors recorded by its kernels. */
 int emu_sync(emu_box* box);
 

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "kernels3d.cuh"
 
 using namespace emu_dev;
 
@@ -129,6 +130,7 @@ const char* make_shape(const emu_config* cfgs, int nbox, Shape& S) {
 
 struct Layout {
   size_t geo, dts, nmax, A, At, mom, partial, W, err, dirtab, shift, shift2, bar, species, dirs, diag, scalar, total;
+  size_t rowgeo = 0;   // 3D boxes: one descriptor per cell row (the deposit combination's batch view)
 };
 
 Layout layout(const Shape& S) {
@@ -181,6 +183,14 @@ struct emu_box {
   int rk_form = -1;             // RK stage: 0 halo-lane, 1 32-cell, -1 by units per warp (autotuned)
   int step_form = 0;            // 0: one launch per phase, 1: one cooperative launch per step (k_step)
   unsigned long long limit_ns = 1000000000ull;   // bound of each grid-barrier wait of k_step
+  // 3D boxes (emu3_create): the box is S's single box (cells in 3D index order),
+  // positions x, y beside the particle arrays, and one descriptor per cell row
+  bool is3d = false;
+  emu3_config c3{};
+  double *x3 = nullptr, *y3 = nullptr;
+  std::vector<BoxGeo> rows;
+  BoxGeo* rows_d = nullptr;
+  int ntz = 0;
   bool pot = false;             // some box has vacuum or matter terms
   int next_stage = 1;
   std::vector<double> dt_h;  // step sizes currently on the device
@@ -485,6 +495,15 @@ int launch_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, c
 // step must have been computed by stage 1's caller).
 int launch_rk(emu_box* b, int s, const int* srow, int dry);
 
+// The 3D box's launches (defined with the other 3D helpers below).
+int launch3_step(emu_box* b, int dry);
+int launch3_stage(emu_box* b, int s, int dry);
+int launch3_shifts(emu_box* b, const double* fracs, int nrows);
+int launch3_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, const int* srow, double frac,
+                    double* out);
+int run3_moments(emu_box* b);
+int rebuild_dirtable3(emu_box* b);
+
 int launch_stage(emu_box* b, int s, int dry) {
   const size_t P = (size_t)b->S.Ptot;
   const double* rnu = (s == 1) ? b->pt.rho : b->pt.stage;
@@ -599,6 +618,7 @@ int launch_rk(emu_box* b, int s, const int* srow, int dry) {
 }
 
 int launch_step(emu_box* b, int dry) {
+  if (b->is3d) return launch3_step(b, dry);
   if (b->step_form == 1) return launch_fused(b, dry, 1);
   if (int rc = launch_shifts(b, kStageFrac, 4)) return rc;
   for (int s = 1; s <= 4; ++s)
@@ -624,6 +644,7 @@ int run_steps(emu_box* b, int64_t nsteps) {
 }
 
 int run_moments(emu_box* b) {
+  if (b->is3d) return run3_moments(b);
   const double zero = 0.0;
   if (int rc = launch_shifts(b, &zero, 1)) return rc;
   if (int rc = launch_deposit(b, 1, b->pt.rho, b->pt.rhobar, b->shift, 0.0, b->mom)) return rc;
@@ -631,6 +652,7 @@ int run_moments(emu_box* b) {
 }
 
 int rebuild_dirtable(emu_box* b) {
+  if (b->is3d) return rebuild_dirtable3(b);
   const int blocks = (int)((b->S.Ptot + kThreads - 1) / kThreads);
   before_launch(b, CLS_OTHER);
   k_dirtable<<<blocks, kThreads, 0, b->stream>>>(batch_view(b), b->pt, b->dirtab, b->err);
@@ -683,6 +705,245 @@ int run_timestep(emu_box* b, double* dt_out) {
   if (dt_out) std::memcpy(dt_out, b->dt_h.data(), sizeof(double) * b->S.nbox);
   return EMU_OK;
 }
+
+
+// ------------------------------------------------------------------ 3D boxes
+//
+// A 3D box is S's single box with its cells in 3D index order (the time
+// step, the diagnostics and the vacuum and matter terms read that
+// descriptor), plus one descriptor per cell row, which the deposit
+// combination (k_combine) takes as its batch: row r holds cells
+// [r nz, (r + 1) nz) and the units of its z tiles.
+
+const char* config3_problem(const emu3_config* c) {
+  if (!c) return "config is NULL";
+  if (c->nx < 1 || c->ny < 1 || c->nz < 1) return "nx, ny and nz must be >= 1";
+  if (c->ndir < 1) return "ndir must be >= 1";
+  for (double L : {c->Lx, c->Ly, c->Lz})
+    if (!(L > 0) || !std::isfinite(L)) return "Lx, Ly and Lz must be positive and finite";
+  if (!(c->kappa > 0) || !std::isfinite(c->kappa)) return "kappa must be positive and finite";
+  if (!(c->c_light > 0) || !std::isfinite(c->c_light)) return "c_light must be positive and finite";
+  if (!(c->cfl_adv > 0) || !(c->cfl_flavor > 0)) return "CFL factors must be positive";
+  if (c->shape_order < 0 || c->shape_order > 3) return "shape_order must be 0, 1, 2 or 3";
+  if (c->reserved != 0) return "reserved must be 0";
+  return nullptr;
+}
+
+const char* make_shape3(const emu3_config* c, Shape& S, std::vector<BoxGeo>& rows, int& ntz) {
+  if (const char* why = config3_problem(c)) return why;
+  const int64_t R = (int64_t)c->nx * c->ny, C = R * c->nz;
+  if (R > kMaxBoxes) return "too many cell rows (nx * ny)";
+  if (C > INT32_MAX / kNM) return "too many cells";
+  if (C * c->ndir > ((int64_t)1 << 40)) return "too many particles";
+  S = Shape();
+  S.nbox = 1;
+  S.order = c->shape_order;
+  S.T = tile_cells(S.order);
+  ntz = (c->nz + S.T - 1) / S.T;
+  const double dx = c->Lx / c->nx, dy = c->Ly / c->ny, dz = c->Lz / c->nz;
+  const double dV = dx * dy * dz;
+  double hmin = dx;
+  if (dy < hmin) hmin = dy;
+  if (dz < hmin) hmin = dz;
+  BoxGeo g;
+  std::memset(&g, 0, sizeof(g));
+  g.nz = (int)C;            // the whole box as one list of cells (time step, diagnostics)
+  g.M = c->ndir;
+  g.ntiles = (int)(R * ntz);
+  g.P = C * c->ndir;
+  g.Lz = c->Lz;             // rk_particle wraps z with it
+  g.dz = hmin;              // Eq. 7 with the smallest cell edge
+  g.inv_dz = 1.0 / dz;
+  g.nz_d = (double)c->nz;
+  g.dV = dV;
+  g.c_light = c->c_light;
+  g.kappa_dV = c->kappa / dV;
+  g.inv_dV = 1.0 / dV;
+  g.cfl_adv = c->cfl_adv;
+  g.cfl_flavor = c->cfl_flavor;
+  g.kappa = c->kappa;
+  S.geo.assign(1, g);
+  rows.assign((size_t)R, BoxGeo{});
+  for (int64_t r = 0; r < R; ++r) {
+    BoxGeo& q = rows[(size_t)r];
+    std::memset(&q, 0, sizeof(q));
+    q.nz = c->nz;
+    q.M = c->ndir;
+    q.ntiles = ntz;
+    q.coff = (int)(r * c->nz);
+    q.toff = (int)(r * ntz);
+    q.uoff = r * ntz * c->ndir;
+    q.kappa_dV = g.kappa_dV;
+    q.inv_dV = g.inv_dV;
+  }
+  S.Ptot = C * c->ndir;
+  S.U = R * ntz * c->ndir;
+  S.U32 = 0;
+  S.NZ = (int)C;
+  S.MT = c->ndir;
+  S.NT = (int)(R * ntz);
+  S.Mmax = c->ndir;
+  return nullptr;
+}
+
+Layout layout3(const Shape& S, size_t nrows) {
+  Layout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+  const size_t NZ = (size_t)S.NZ, MT = (size_t)S.MT;
+  L.geo = take(sizeof(BoxGeo));
+  L.dts = take(sizeof(double));
+  L.nmax = take(sizeof(double));
+  L.A = take(sizeof(double) * kNA * NZ);
+  L.At = take(sizeof(double) * kNT * NZ);
+  L.mom = take(sizeof(double) * kNM * NZ);
+  L.partial = take(sizeof(double) * (size_t)(kMaxWarps + S.NT) * kSlot);
+  L.W = take(0);
+  L.err = take(sizeof(int));
+  L.dirtab = take(sizeof(double) * 6 * MT);
+  L.shift = take(sizeof(int) * 12 * MT);
+  L.shift2 = take(0);
+  L.bar = take(sizeof(unsigned) * 2);
+  L.species = take(sizeof(double) * 8 * NZ);
+  L.dirs = take(sizeof(double) * 3 * MT);
+  L.diag = take(sizeof(double) * 63);
+  L.scalar = take(sizeof(double) * 4);
+  L.rowgeo = take(sizeof(BoxGeo) * nrows);
+  L.total = off;
+  return L;
+}
+
+Box3 box3_view(const emu_box* b) {
+  const emu3_config& c = b->c3;
+  Box3 v;
+  v.n[0] = c.nx; v.n[1] = c.ny; v.n[2] = c.nz;
+  v.M = c.ndir;
+  v.R = c.nx * c.ny;
+  v.C = v.R * c.nz;
+  v.ntz = b->ntz;
+  v.T = b->S.T;
+  v.nw = batch_view(b).nw;
+  v.use_dirs = b->S.geo[0].use_dirs;
+  v.U = b->S.U;
+  v.P = b->S.Ptot;
+  const double L[3] = {c.Lx, c.Ly, c.Lz};
+  for (int a = 0; a < 3; ++a) {
+    v.L[a] = L[a];
+    v.h[a] = L[a] / v.n[a];
+    v.inv_h[a] = 1.0 / v.h[a];
+    v.n_d[a] = (double)v.n[a];
+  }
+  v.kappa_dV = b->S.geo[0].kappa_dV;
+  v.inv_dV = b->S.geo[0].inv_dV;
+  v.c_light = c.c_light;
+  v.alpha = b->S.geo[0].alpha;
+  v.seed = b->S.geo[0].seed;
+  v.dt = b->dts;
+  v.g = b->geo_d;
+  return v;
+}
+
+// The deposit combination's batch: the box's cell rows.
+Batch row_view(const emu_box* b) {
+  Batch B = batch_view(b);
+  B.box = b->rows_d;
+  B.nbox = (int)b->rows.size();
+  return B;
+}
+
+int launch3_shifts(emu_box* b, const double* fracs, int nrows) {
+  Fracs f{};
+  for (int s = 0; s < nrows; ++s) f.v[s] = fracs[s];
+  before_launch(b, CLS_SHIFT);
+  pdl(b->stream, k3_shifts, dim3((unsigned)((b->c3.ndir + kThreads - 1) / kThreads)), box3_view(b), b->x3, b->y3,
+      b->pt.z, b->dirtab, f, nrows, b->shift);
+  return after_launch(b, "3D shift kernel");
+}
+
+// Deposit of the state (rnu, rnb) at positions x + frac dt c Omega with the
+// shift rows srow ([3][M]) into out; modes as k3_deposit.
+int launch3_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, const int* srow, double frac,
+                    double* out) {
+  const Box3 v = box3_view(b);
+  const dim3 grid = persist_grid(b);
+  cudaStream_t st = b->stream;
+  const double *x = b->x3, *y = b->y3, *z = b->pt.z, *N = b->pt.N, *Nb = b->pt.Nbar;
+  before_launch(b, CLS_DEPOSIT);
+  by_order(b->S.order, [&](auto O) {
+    constexpr int R = decltype(O)::value;
+    if (mode == 0)
+      pdl(st, k3_deposit<0, R>, grid, v, x, y, z, N, Nb, rnu, rnb, b->dirtab, srow, frac, b->partial, b->err);
+    else if (mode == 1)
+      pdl(st, k3_deposit<1, R>, grid, v, x, y, z, N, Nb, rnu, rnb, b->dirtab, srow, frac, b->partial, b->err);
+    else if (mode == 2)
+      pdl(st, k3_deposit<2, R>, grid, v, x, y, z, N, Nb, rnu, rnb, b->dirtab, srow, frac, b->partial, b->err);
+    else if (mode == 4)
+      pdl(st, k3_deposit<4, R>, grid, v, x, y, z, N, Nb, rnu, rnb, b->dirtab, srow, frac, b->partial, b->err);
+    else
+      pdl(st, k3_deposit<5, R>, grid, v, x, y, z, N, Nb, rnu, rnb, b->dirtab, srow, frac, b->partial, b->err);
+    return 0;
+  });
+  if (int rc = after_launch(b, "3D deposit kernel")) return rc;
+  const Batch B = row_view(b);
+  const int split = combine_split(b->S, B.nw);
+  const int rows = mode == 5 ? kNT : kNA;
+  const int potential = (mode == 0 || mode == 5) ? 1 : 0;
+  before_launch(b, CLS_COMBINE);
+  pdl(st, k_combine, dim3(combine_blocks(rows, B.NZ, split)), B, b->partial, out, rows, potential, split, b->err);
+  return after_launch(b, "deposit combine kernel");
+}
+
+int launch3_rk(emu_box* b, int s, const int* srow, int dry) {
+  const Box3 v = box3_view(b);
+  before_launch(b, CLS_RK);
+  by_order(b->S.order, [&](auto O) {
+    constexpr int R = decltype(O)::value;
+    if (b->pot)
+      pdl(b->stream, k3_rk_stage<true, R>, persist_grid(b), v, b->pt, b->x3, b->y3, b->dirtab, srow, b->At, s, dry,
+          b->err);
+    else
+      pdl(b->stream, k3_rk_stage<false, R>, persist_grid(b), v, b->pt, b->x3, b->y3, b->dirtab, srow, b->At, s,
+          dry, b->err);
+    return 0;
+  });
+  return after_launch(b, "3D RK stage kernel");
+}
+
+int launch3_stage(emu_box* b, int s, int dry) {
+  const size_t P = (size_t)b->S.Ptot;
+  const double* rnu = (s == 1) ? b->pt.rho : b->pt.stage;
+  const double* rnb = (s == 1) ? b->pt.rhobar : b->pt.stage + 9 * P;
+  const int* srow = b->shift + (size_t)(s - 1) * 3 * b->S.MT;
+  if (int rc = launch3_deposit(b, 5, rnu, rnb, srow, kStageFrac[s - 1], b->At)) return rc;
+  return launch3_rk(b, s, srow, dry);
+}
+
+int launch3_step(emu_box* b, int dry) {
+  if (int rc = launch3_shifts(b, kStageFrac, 4)) return rc;
+  for (int s = 1; s <= 4; ++s)
+    if (int rc = launch3_stage(b, s, dry)) return rc;
+  return EMU_OK;
+}
+
+int run3_moments(emu_box* b) {
+  const double zero = 0.0;
+  if (int rc = launch3_shifts(b, &zero, 1)) return rc;
+  if (int rc = launch3_deposit(b, 1, b->pt.rho, b->pt.rhobar, b->shift, 0.0, b->mom)) return rc;
+  return launch3_deposit(b, 2, b->pt.rho, b->pt.rhobar, b->shift, 0.0, b->mom + (size_t)kNA * b->S.NZ);
+}
+
+int rebuild_dirtable3(emu_box* b) {
+  before_launch(b, CLS_OTHER);
+  k3_dirtable<<<(unsigned)((b->S.Ptot + kThreads - 1) / kThreads), kThreads, 0, b->stream>>>(box3_view(b), b->pt,
+                                                                                               b->dirtab, b->err);
+  return after_launch(b, "3D direction table kernel");
+}
+
+int no_3d(emu_box* b, const char* what) {
+  return fail(b, EMU_EINVAL, "%s is not available for a 3D box", what);
+}
+
+int bind_common(emu_box* b, const emu_particles* parts, void* workspace, int64_t workspace_bytes, void* stream);
 
 int create_common(const emu_config* cfgs, int nbox, emu_box** out) {
   if (!out) return fail(nullptr, EMU_EINVAL, "out is NULL");
@@ -767,6 +1028,14 @@ int emu_batch_create(const emu_config* cfgs, int32_t nbox, emu_box** out) { retu
 
 int emu_bind(emu_box* b, const emu_particles* parts, void* workspace, int64_t workspace_bytes, void* stream) {
   if (!b) return EMU_EINVAL;
+  if (b->is3d) return fail(b, EMU_EINVAL, "a 3D box is bound with emu3_bind");
+  return bind_common(b, parts, workspace, workspace_bytes, stream);
+}
+
+}  // extern "C"
+
+namespace {
+int bind_common(emu_box* b, const emu_particles* parts, void* workspace, int64_t workspace_bytes, void* stream) {
   if (!parts || !workspace) return fail(b, EMU_EINVAL, "particles or workspace is NULL");
   if (parts->P != b->S.Ptot)
     return fail(b, EMU_EINVAL, "parts->P = %lld, expected %lld particles", (long long)parts->P,
@@ -797,6 +1066,7 @@ int emu_bind(emu_box* b, const emu_particles* parts, void* workspace, int64_t wo
   b->shift = (int*)(b->ws + L.shift);
   b->shift2 = (int*)(b->ws + L.shift2);
   b->bar = (unsigned*)(b->ws + L.bar);
+  b->rows_d = b->is3d ? (BoxGeo*)(b->ws + L.rowgeo) : nullptr;
   b->species = (double*)(b->ws + L.species);
   b->dirs = (double*)(b->ws + L.dirs);
   b->diag = (double*)(b->ws + L.diag);
@@ -804,22 +1074,31 @@ int emu_bind(emu_box* b, const emu_particles* parts, void* workspace, int64_t wo
   invalidate_graph(b);
   if (int rc = cuda_check(b, cudaMemsetAsync(workspace, 0, L.total, b->stream), "clear workspace")) return rc;
   if (int rc = upload_geo(b)) return rc;
+  if (b->is3d)
+    if (int rc = cuda_check(b, cudaMemcpyAsync(b->rows_d, b->rows.data(), sizeof(BoxGeo) * b->rows.size(),
+                                               cudaMemcpyHostToDevice, b->stream), "upload row descriptors"))
+      return rc;
   b->dt_set = false;
   b->step_valid = false;
   b->bound = true;
   b->next_stage = 1;
   return EMU_OK;
 }
+}  // namespace
+
+extern "C" {
 
 int emu_init_particles(emu_box* b, const double* n_nu, const double* n_nubar, const double* f_nu,
                        const double* f_nubar, const double* dirs, double alpha, uint64_t seed) {
   if (int rc = check_single(b)) return rc;
+  if (b->is3d) return fail(b, EMU_EINVAL, "a 3D box is initialised with emu3_init_particles");
   return init_common(b, n_nu, n_nubar, f_nu, f_nubar, dirs, &alpha, &seed);
 }
 
 int emu_batch_init_particles(emu_box* b, const double* n_nu, const double* n_nubar, const double* f_nu,
                              const double* f_nubar, const double* dirs, const double* alpha, const uint64_t* seed) {
   if (int rc = check_bound(b)) return rc;
+  if (b->is3d) return fail(b, EMU_EINVAL, "a 3D box is initialised with emu3_init_particles");
   return init_common(b, n_nu, n_nubar, f_nu, f_nubar, dirs, alpha, seed);
 }
 
@@ -866,11 +1145,16 @@ int emu_deposit(emu_box* b, int src, double pos_dt, double* A_out, int on_host) 
   if (!std::isfinite(pos_dt)) return fail(b, EMU_EINVAL, "pos_dt must be finite");
   if (int rc = set_dts(b, &pos_dt)) return rc;
   const double one = 1.0;
-  if (int rc = launch_shifts(b, &one, 1)) return rc;
   const size_t P = (size_t)b->S.Ptot;
   const double* rnu = src ? b->pt.stage : b->pt.rho;
   const double* rnb = src ? b->pt.stage + 9 * P : b->pt.rhobar;
-  if (int rc = launch_deposit(b, 0, rnu, rnb, b->shift, 1.0, b->A)) return rc;
+  if (b->is3d) {
+    if (int rc = launch3_shifts(b, &one, 1)) return rc;
+    if (int rc = launch3_deposit(b, 0, rnu, rnb, b->shift, 1.0, b->A)) return rc;
+  } else {
+    if (int rc = launch_shifts(b, &one, 1)) return rc;
+    if (int rc = launch_deposit(b, 0, rnu, rnb, b->shift, 1.0, b->A)) return rc;
+  }
   b->next_stage = 1;
   if (A_out) return copy_out(b, A_out, b->A, sizeof(double) * kNA * b->S.NZ, on_host);
   return EMU_OK;
@@ -882,13 +1166,17 @@ int emu_interpolate_H(emu_box* b, double pos_dt, double* H_out, int on_host) {
   if (!std::isfinite(pos_dt)) return fail(b, EMU_EINVAL, "pos_dt must be finite");
   if (int rc = set_dts(b, &pos_dt)) return rc;
   const double one = 1.0;
-  if (int rc = launch_shifts(b, &one, 1)) return rc;
+  if (int rc = b->is3d ? launch3_shifts(b, &one, 1) : launch_shifts(b, &one, 1)) return rc;
   double* dst = H_out;
   if (on_host) dst = b->pt.acc;  // staging: the RK scratch holds 18 P doubles
   before_launch(b, CLS_OTHER);
   by_order(b->S.order, [&](auto O) {
-    k_interpolate<decltype(O)::value><<<persist_grid(b), kThreads, 0, b->stream>>>(
-        batch_view(b), b->pt.z, b->dirtab, b->shift, b->A, 1.0, dst, b->err);
+    if (b->is3d)
+      k3_interpolate<decltype(O)::value><<<persist_grid(b), kThreads, 0, b->stream>>>(
+          box3_view(b), b->x3, b->y3, b->pt.z, b->dirtab, b->shift, b->A, 1.0, dst, b->err);
+    else
+      k_interpolate<decltype(O)::value><<<persist_grid(b), kThreads, 0, b->stream>>>(
+          batch_view(b), b->pt.z, b->dirtab, b->shift, b->A, 1.0, dst, b->err);
     return 0;
   });
   if (int rc = after_launch(b, "interpolation kernel")) return rc;
@@ -905,9 +1193,9 @@ int emu_rk_stage(emu_box* b, int s, double dt) {
   if (s > 1 && dt != b->dt_h[0]) return fail(b, EMU_EINVAL, "dt changed within a step");
   if (s == 1) {
     if (int rc = set_dts(b, &dt)) return rc;
-    if (int rc = launch_shifts(b, kStageFrac, 4)) return rc;
+    if (int rc = b->is3d ? launch3_shifts(b, kStageFrac, 4) : launch_shifts(b, kStageFrac, 4)) return rc;
   }
-  if (int rc = launch_stage(b, s, 0)) return rc;
+  if (int rc = b->is3d ? launch3_stage(b, s, 0) : launch_stage(b, s, 0)) return rc;
   b->next_stage = s == 4 ? 1 : s + 1;
   return EMU_OK;
 }
@@ -969,8 +1257,13 @@ int emu_batch_diagnostics(emu_box* b, double* out, int on_host) {
   if (!out) return fail(b, EMU_EINVAL, "out is NULL");
   // the diagnostics read n, f_x, nbar, fbar_x: one deposit pass of both species
   const double zero = 0.0;
-  if (int rc = launch_shifts(b, &zero, 1)) return rc;
-  if (int rc = launch_deposit(b, 4, b->pt.rho, b->pt.rhobar, b->shift, 0.0, b->mom)) return rc;
+  if (b->is3d) {
+    if (int rc = launch3_shifts(b, &zero, 1)) return rc;
+    if (int rc = launch3_deposit(b, 4, b->pt.rho, b->pt.rhobar, b->shift, 0.0, b->mom)) return rc;
+  } else {
+    if (int rc = launch_shifts(b, &zero, 1)) return rc;
+    if (int rc = launch_deposit(b, 4, b->pt.rho, b->pt.rhobar, b->shift, 0.0, b->mom)) return rc;
+  }
   before_launch(b, CLS_OTHER);
   k_diagnostics<<<dim3((unsigned)b->S.nbox, 63), kThreads, 0, b->stream>>>(batch_view(b), b->mom, b->diag);
   if (int rc = after_launch(b, "diagnostics kernel")) return rc;
@@ -1024,7 +1317,7 @@ int emu_autotune(emu_box* b, int trial_steps, int32_t* choice_out, double* ms_ou
     b->blocks = grids[c];
     b->rk_form = c % 2;
     b->step_form = c >= 6 ? 1 : 0;
-    if (b->step_form == 1 && b->blocks > maxb) {   // not every block could be resident: not a candidate
+    if (b->step_form == 1 && (b->is3d || b->blocks > maxb)) {   // not every block could be resident: not a candidate
       if (ms_out) ms_out[c] = -1.0;
       continue;
     }
@@ -1056,6 +1349,7 @@ int emu_autotune(emu_box* b, int trial_steps, int32_t* choice_out, double* ms_ou
 int emu_set_step_form(emu_box* b, int32_t form) {
   if (int rc = check_bound(b)) return rc;
   if (form < 0 || form > 1) return fail(b, EMU_EINVAL, "form must be 0 or 1");
+  if (form == 1 && b->is3d) return no_3d(b, "the fused step form");
   if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
   if (form == 1) {
     const int maxb = fused_max_blocks(b);
@@ -1075,6 +1369,113 @@ int emu_set_barrier_timeout(emu_box* b, int64_t ns) {
   b->limit_ns = (unsigned long long)ns;
   invalidate_graph(b);
   return EMU_OK;
+}
+
+int64_t emu3_workspace_bytes(const emu3_config* cfg) {
+  Shape S;
+  std::vector<BoxGeo> rows;
+  int ntz = 0;
+  if (make_shape3(cfg, S, rows, ntz)) return EMU_EINVAL;
+  return (int64_t)layout3(S, rows.size()).total;
+}
+
+int emu3_create(const emu3_config* cfg, emu_box** out) {
+  if (!out) return fail(nullptr, EMU_EINVAL, "out is NULL");
+  *out = nullptr;
+  Shape S;
+  std::vector<BoxGeo> rows;
+  int ntz = 0;
+  if (const char* why = make_shape3(cfg, S, rows, ntz)) return fail(nullptr, EMU_EINVAL, "%s", why);
+  emu_box* b = new (std::nothrow) emu_box();
+  if (!b) return fail(nullptr, EMU_EINVAL, "host allocation failed");
+  b->is3d = true;
+  b->c3 = *cfg;
+  b->S = std::move(S);
+  b->rows = std::move(rows);
+  b->ntz = ntz;
+  b->L = layout3(b->S, b->rows.size());
+  emu_config c{};   // the physics values the shared calls read (kappa for the matter term)
+  c.nz = cfg->nz;
+  c.ndir = cfg->ndir;
+  c.Lz = cfg->Lz;
+  c.area = cfg->Lx * cfg->Ly;
+  c.kappa = cfg->kappa;
+  c.c_light = cfg->c_light;
+  c.cfl_adv = cfg->cfl_adv;
+  c.cfl_flavor = cfg->cfl_flavor;
+  c.shape_order = cfg->shape_order;
+  b->cfg.assign(1, c);
+  *out = b;
+  return EMU_OK;
+}
+
+int emu3_bind(emu_box* b, const emu_particles* parts, double* x, double* y, void* workspace, int64_t workspace_bytes,
+              void* stream) {
+  if (!b) return EMU_EINVAL;
+  if (!b->is3d) return fail(b, EMU_EINVAL, "emu3_bind takes a box made by emu3_create");
+  if (!x || !y) return fail(b, EMU_EINVAL, "x or y is NULL");
+  b->x3 = x;
+  b->y3 = y;
+  return bind_common(b, parts, workspace, workspace_bytes, stream);
+}
+
+int emu3_init_particles(emu_box* b, const double* n_nu, const double* n_nubar, const double* f_nu,
+                        const double* f_nubar, const double* dirs, double alpha, uint64_t seed) {
+  if (int rc = check_bound(b)) return rc;
+  if (!b->is3d) return fail(b, EMU_EINVAL, "emu3_init_particles takes a 3D box");
+  if (!n_nu || !n_nubar || !f_nu || !f_nubar) return fail(b, EMU_EINVAL, "species arrays must not be NULL");
+  const size_t C = (size_t)b->S.NZ, M = (size_t)b->S.MT;
+  std::vector<double> sp(8 * C);
+  std::memcpy(sp.data(), n_nu, sizeof(double) * C);
+  std::memcpy(sp.data() + C, n_nubar, sizeof(double) * C);
+  std::memcpy(sp.data() + 2 * C, f_nu, sizeof(double) * 3 * C);
+  std::memcpy(sp.data() + 5 * C, f_nubar, sizeof(double) * 3 * C);
+  BoxGeo& g = b->S.geo[0];
+  g.use_dirs = dirs ? 1 : 0;
+  g.alpha = alpha;
+  g.seed = seed;
+  if (int rc = upload_geo(b)) return rc;
+  if (int rc = cuda_check(b, cudaMemcpyAsync(b->species, sp.data(), sizeof(double) * sp.size(),
+                                             cudaMemcpyHostToDevice, b->stream), "copy species"))
+    return rc;
+  if (dirs)
+    if (int rc = cuda_check(b, cudaMemcpyAsync(b->dirs, dirs, sizeof(double) * 3 * M, cudaMemcpyHostToDevice,
+                                               b->stream), "copy directions"))
+      return rc;
+  before_launch(b, CLS_OTHER);
+  k3_init<<<(unsigned)((b->S.Ptot + kThreads - 1) / kThreads), kThreads, 0, b->stream>>>(
+      box3_view(b), b->pt, b->x3, b->y3, b->species, b->dirs, b->err);
+  if (int rc = after_launch(b, "3D init kernel")) return rc;
+  if (int rc = rebuild_dirtable3(b)) return rc;
+  b->next_stage = 1;
+  b->step_valid = false;
+  return read_errors(b);   // synchronises: the host staging vector may go
+}
+
+static int positions3(emu_box* b, double* xd, double* yd, const double* xs, const double* ys, cudaMemcpyKind kind,
+                      int sync) {
+  const size_t bytes = sizeof(double) * (size_t)b->S.Ptot;
+  if (xs && xd)
+    if (int rc = cuda_check(b, cudaMemcpyAsync(xd, xs, bytes, kind, b->stream), "copy x")) return rc;
+  if (ys && yd)
+    if (int rc = cuda_check(b, cudaMemcpyAsync(yd, ys, bytes, kind, b->stream), "copy y")) return rc;
+  if (sync) return cuda_check(b, cudaStreamSynchronize(b->stream), "synchronise after copy");
+  return EMU_OK;
+}
+
+int emu3_get_positions(emu_box* b, double* x, double* y, int on_host) {
+  if (int rc = check_bound(b)) return rc;
+  if (!b->is3d) return fail(b, EMU_EINVAL, "emu3_get_positions takes a 3D box");
+  return positions3(b, x, y, x ? b->x3 : nullptr, y ? b->y3 : nullptr,
+                    on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, on_host);
+}
+
+int emu3_set_positions(emu_box* b, const double* x, const double* y, int on_host) {
+  if (int rc = check_bound(b)) return rc;
+  if (!b->is3d) return fail(b, EMU_EINVAL, "emu3_set_positions takes a 3D box");
+  b->next_stage = 1;
+  return positions3(b, x ? b->x3 : nullptr, y ? b->y3 : nullptr, x, y,
+                    on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, on_host);
 }
 
 int emu_set_oscillation(emu_box* b, int32_t box, const emu_oscillation* osc) {
@@ -1321,6 +1722,7 @@ int64_t emu_batch_adjoint_workspace_bytes(const emu_config* cfgs, int32_t nbox) 
 
 int emu_adjoint_seed(emu_box* b, const double* dmom, double* lambda, double* gN, double* gNbar) {
   if (int rc = check_bound(b)) return rc;
+  if (b->is3d) return no_3d(b, "the adjoint");
   if (!dmom || !lambda || !gN || !gNbar) return fail(b, EMU_EINVAL, "adjoint seed: NULL pointer");
   if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
   const double zero = 0.0;
@@ -1337,6 +1739,7 @@ int emu_adjoint_seed(emu_box* b, const double* dmom, double* lambda, double* gN,
 int emu_adjoint_step(emu_box* b, double dt, double* lambda, double* gN, double* gNbar, void* adj_ws,
                      int64_t adj_ws_bytes) {
   if (int rc = check_bound(b)) return rc;
+  if (b->is3d) return no_3d(b, "the adjoint");
   if (dt != 0.0) {
     if (b->S.nbox != 1) return fail(b, EMU_EINVAL, "a batch takes dt = 0 (each box's own step size)");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(b, EMU_EINVAL, "dt must be positive and finite, or 0");
@@ -1376,6 +1779,7 @@ int64_t emu_batch_adjoint_record_bytes(const emu_config* cfgs, int32_t nbox) {
 // each box's own), a buffer of at least `need` bytes, 256-byte aligned.
 static int record_checks(emu_box* b, double dt, const void* buf, int64_t bytes, size_t need, const char* what) {
   if (int rc = check_bound(b)) return rc;
+  if (b->is3d) return no_3d(b, "the adjoint");
   if (dt != 0.0) {
     if (b->S.nbox != 1) return fail(b, EMU_EINVAL, "a batch takes dt = 0 (each box's own step size)");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(b, EMU_EINVAL, "dt must be positive and finite, or 0");
@@ -1417,6 +1821,7 @@ int emu_adjoint_step_recorded(emu_box* b, double dt, const void* rec, double* la
 
 int emu_weight_gradient(emu_box* b, const double* gN, const double* gNbar, double* out, int on_host) {
   if (int rc = check_bound(b)) return rc;
+  if (b->is3d) return no_3d(b, "the adjoint");
   if (!gN || !gNbar || !out) return fail(b, EMU_EINVAL, "weight gradient: NULL pointer");
   double* dst = on_host ? b->mom : out;  // staging: the moments buffer holds 72 NZ doubles
   const int blocks = (b->S.NZ + kThreads - 1) / kThreads;

@@ -53,6 +53,13 @@ class emu_oscillation(ctypes.Structure):
                 ("theta12", "theta13", "theta23", "delta_cp", "energy_erg", "n_e", "hbar", "erg_per_eV")]
 
 
+class emu3_config(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("ndir", ctypes.c_int32),
+                ("Lx", ctypes.c_double), ("Ly", ctypes.c_double), ("Lz", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("c_light", ctypes.c_double), ("cfl_adv", ctypes.c_double),
+                ("cfl_flavor", ctypes.c_double), ("shape_order", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class emu_particles(ctypes.Structure):
     _fields_ = [(name, ctypes.c_void_p) for name in
                 ("z", "ox", "oy", "oz", "N", "Nbar", "rho", "rhobar", "acc", "stage")] + [("P", ctypes.c_int64)]
@@ -120,6 +127,12 @@ def load(build_if_missing: bool = False):
         "emu_adjoint_record_step": (i32, [vp, dbl, vp, i64]),
         "emu_adjoint_step_recorded": (i32, [vp, dbl, vp, vp, vp, vp, vp, i64]),
         "emu_weight_gradient": (i32, [vp, vp, vp, vp, i32]),
+        "emu3_workspace_bytes": (i64, [ctypes.POINTER(emu3_config)]),
+        "emu3_create": (i32, [ctypes.POINTER(emu3_config), ctypes.POINTER(vp)]),
+        "emu3_bind": (i32, [vp, ctypes.POINTER(emu_particles), vp, vp, vp, i64, vp]),
+        "emu3_init_particles": (i32, [vp, vp, vp, vp, vp, vp, dbl, ctypes.c_uint64]),
+        "emu3_get_positions": (i32, [vp, vp, vp, i32]),
+        "emu3_set_positions": (i32, [vp, vp, vp, i32]),
         "emu_last_error": (ctypes.c_char_p, [vp]),
         "emu_destroy": (None, [vp]),
     }
@@ -768,3 +781,106 @@ class PingPongFeed:
         self.install(1 - k)
         self.turn += 1
         return b
+
+
+# ------------------------------------------------------------------ 3D boxes
+
+def make_config3(nx, ny, nz, ndir, Lx, Ly, Lz, kappa, c_light, cfl_adv=0.4, cfl_flavor=0.4,
+                 shape_order=2) -> emu3_config:
+    return emu3_config(int(nx), int(ny), int(nz), int(ndir), float(Lx), float(Ly), float(Lz), float(kappa),
+                       float(c_light), float(cfl_adv), float(cfl_flavor), int(shape_order), 0)
+
+
+def emu3_workspace_bytes(cfg: emu3_config) -> int:
+    n = load().emu3_workspace_bytes(ctypes.byref(cfg))
+    if n < 0:
+        raise EmuError(int(n), "invalid configuration")
+    return int(n)
+
+
+def emu3_create(cfg: emu3_config):
+    box = ctypes.c_void_p()
+    _check(None, load().emu3_create(ctypes.byref(cfg), ctypes.byref(box)))
+    return box
+
+
+def emu3_bind(box, parts: emu_particles, x_ptr: int, y_ptr: int, workspace_ptr: int, workspace_bytes: int,
+              stream_ptr: int):
+    _check(box, load().emu3_bind(box, ctypes.byref(parts), x_ptr, y_ptr, workspace_ptr, workspace_bytes,
+                                 stream_ptr))
+
+
+def emu3_init_particles(box, n_nu, n_nubar, f_nu, f_nubar, dirs, alpha: float, seed: int):
+    arrs = [np.ascontiguousarray(a, np.float64) for a in (n_nu, n_nubar, f_nu, f_nubar)]
+    d = None if dirs is None else np.ascontiguousarray(dirs, np.float64)
+    _check(box, load().emu3_init_particles(box, *map(_host_ptr, arrs), _host_ptr(d), float(alpha), int(seed)))
+
+
+def emu3_get_positions(box, x, y, on_host: int):
+    _check(box, load().emu3_get_positions(box, x, y, int(on_host)))
+
+
+def emu3_set_positions(box, x, y, on_host: int):
+    _check(box, load().emu3_set_positions(box, x, y, int(on_host)))
+
+
+class Box3D(Box):
+    """One 3D box (emu3_create) with its caller-owned device memory as torch
+    tensors; the Box methods that the C ABI supports for 3D boxes apply."""
+
+    FIELDS = ("z", "ox", "oy", "oz", "N", "Nbar")
+
+    def __init__(self, nx, ny, nz, ndir, Lx, Ly, Lz, kappa, c_light, cfl_adv=0.4, cfl_flavor=0.4,
+                 device="cuda", stream=None, shape_order=2):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        self.cfg3 = make_config3(nx, ny, nz, ndir, Lx, Ly, Lz, kappa, c_light, cfl_adv, cfl_flavor, shape_order)
+        self.cfgs = []
+        self.nbox = 1
+        self.C = nx * ny * nz
+        self.nz = self.C            # cells: the moments are [72][C]
+        self.ndir = ndir
+        self.P = self.C * ndir
+        f64 = dict(dtype=torch.float64, device=self.device)
+        self.t = {k: torch.zeros(self.P, **f64) for k in self.FIELDS + ("x", "y")}
+        self.t["rho"] = torch.zeros(9, self.P, **f64)
+        self.t["rhobar"] = torch.zeros(9, self.P, **f64)
+        self.t["acc"] = torch.zeros(18, self.P, **f64)
+        self.t["stage"] = torch.zeros(18, self.P, **f64)
+        self.ws_bytes = emu3_workspace_bytes(self.cfg3)
+        self._ws_raw = torch.zeros(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+        self.ws_ptr = (self._ws_raw.data_ptr() + 255) & ~255
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.parts = emu_particles(*[self.t[k].data_ptr() for k in
+                                     ("z", "ox", "oy", "oz", "N", "Nbar", "rho", "rhobar", "acc", "stage")],
+                                   self.P)
+        self.box = emu3_create(self.cfg3)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        emu3_bind(self.box, self.parts, self.t["x"].data_ptr(), self.t["y"].data_ptr(), self.ws_ptr, self.ws_bytes,
+                  self.stream.cuda_stream)
+
+    @classmethod
+    def from_workload(cls, wl, device="cuda", init=True, stream=None):
+        b = cls(wl.nx, wl.ny, wl.nz, wl.ndir, wl.Lx, wl.Ly, wl.Lz, wl.kappa, wl.c_light, wl.cfl_adv, wl.cfl_flavor,
+                device=device, stream=stream, shape_order=wl.shape_order)
+        if init:
+            b.init(wl.n_nu, wl.n_nubar, wl.f_nu, wl.f_nubar, wl.dirs, wl.alpha, wl.seed)
+        return b
+
+    @_ordered
+    def init(self, n_nu, n_nubar, f_nu, f_nubar, dirs=None, alpha=1e-6, seed=0):
+        C = self.C
+        emu3_init_particles(self.box, np.broadcast_to(np.asarray(n_nu, float), (C,)),
+                            np.broadcast_to(np.asarray(n_nubar, float), (C,)),
+                            np.broadcast_to(np.asarray(f_nu, float), (C, 3)),
+                            np.broadcast_to(np.asarray(f_nubar, float), (C, 3)), dirs, alpha, seed)
+
+    @_ordered
+    def get_host(self) -> dict:
+        h = Box.get_host.__wrapped__(self)
+        x, y = np.zeros(self.P), np.zeros(self.P)
+        emu3_get_positions(self.box, _host_ptr(x), _host_ptr(y), 1)
+        h["x"], h["y"] = x, y
+        return h

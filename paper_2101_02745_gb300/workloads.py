@@ -244,3 +244,70 @@ def by_name(name: str) -> Workload:
         "throughput_1d": throughput_1d,
     }
     return table[name]()
+
+
+@dataclass
+class Workload3:
+    """One 3D periodic box: nx x ny x nz cells, directions and per-cell
+    species inputs in cell-index order c = (jx * ny + jy) * nz + jz."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    ndir: int
+    Lx: float
+    Ly: float
+    Lz: float
+    n_nu: np.ndarray               # (C,)
+    n_nubar: np.ndarray            # (C,)
+    f_nu: np.ndarray               # (C, 3)
+    f_nubar: np.ndarray            # (C, 3)
+    dirs: Optional[np.ndarray] = None
+    alpha: float = 1e-6
+    seed: int = 0
+    steps: int = 10
+    cfl_adv: float = 0.4
+    cfl_flavor: float = 0.4
+    kappa: float = KAPPA
+    c_light: float = C_LIGHT
+    shape_order: int = 2
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def C(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def P(self) -> int:
+        return self.C * self.ndir
+
+
+def random_box3(nx: int, ny: int, nz: int, ndir: int, seed: int = 0, h: float = 1.0 / 16.0,
+                shape_order: int = 2) -> Workload3:
+    """Randomised 3D box: cells of edge h (the paper's converged 1D resolution
+    by default), per-cell densities in [1e32, 1e33] and flux factors in
+    [0, 1/3) with random 3D directions, numpy PCG64(2000 + seed)."""
+    rng = np.random.Generator(np.random.PCG64(2000 + seed))
+    C = nx * ny * nz
+    n = rng.uniform(1e32, 1e33, C)
+    nb = rng.uniform(1e32, 1e33, C)
+
+    def flux(dens):
+        v = rng.normal(size=(C, 3))
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        return v * (rng.uniform(0.0, 0.33, C) * dens)[:, None]
+
+    f, fb = flux(n), flux(nb)
+    return Workload3(f"random3_{nx}x{ny}x{nz}x{ndir}_s{seed}", nx, ny, nz, ndir, nx * h, ny * h, nz * h, n, nb, f, fb,
+                     seed=seed, shape_order=shape_order)
+
+
+def fiducial_3d(nx: int = 32, ny: int = 32, nz: int = 32, ndir: int = 16) -> Workload3:
+    """3D box of tiny_fiducial's species (n = 4.9e32, nbar = 6.1e32 cm^-3,
+    nubar flux -nbar/3 along z, the ELN crossing of Sec. 3.2) with its cell
+    edge (13.42/32 cm) on every axis."""
+    C = nx * ny * nz
+    n, nb = 4.9e32, 6.1e32
+    sp = (np.full(C, n), np.full(C, nb), np.zeros((C, 3)), np.tile([0.0, 0.0, -nb / 3.0], (C, 1)))
+    h = 13.42 / 32
+    return Workload3(f"fiducial3d_{nx}x{ny}x{nz}x{ndir}", nx, ny, nz, ndir, nx * h, ny * h, nz * h, *sp, steps=50)
