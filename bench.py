@@ -67,6 +67,20 @@ TRAFFIC_RK = 719.4   # k_rk_stage32 (32 cells per warp, traceless potential, aut
 TRAFFIC_DEPOSIT = 296.7   # k_deposit<5> (traceless potential)
 
 
+# 3D boxes (quadratic shape: each particle reaches 3 x 3 neighbour rows), FP64
+# flops per particle of one launch, counted from the kernels' formulation:
+#   deposit: per neighbour row, the particle's weights on 3 axes (3 x 12), its
+#     share toward the warp's row (1) and its two weights scaled by it (2), the
+#     8 traceless components of B (29), the z-spread (40) and their sum (8):
+#     116; x 9 rows, plus the direction's moments (1, Omega) x S (56);
+#   RK stage: the weights (36); per neighbour row the x-y weight (1), G =
+#     A0 - Omega.A (48), the z-gather (40) and its weighted sum (16): 105;
+#     x 9 rows; the third diagonal difference (1), two commutators (162), RK
+#     update (72).
+FLOPS3_DEPOSIT = 9 * 116 + 56
+FLOPS3_RK = 36 + 9 * 105 + 1 + 162 + 72
+
+
 def measured_peaks():
     p = ROOT / "MEASURED_PEAKS.json"
     if p.exists():
@@ -455,10 +469,98 @@ def run_gpu(args, rank, world, local_rank):
         extras["batched"] = measure_sweep(args, dist, device, rank, world, min(args.steps, 20))
         extras["adjoint"] = measure_adjoint(dist, device, world, reps=1)
         extras["paper_shape"] = measure_paper_shape(args, dist, device, world)
+        extras["box_3d"] = measure_box3d(args, dist, device, world, steps=min(args.steps, 10),
+                                         fp64_peak_tflops=roofline["peak"] if pk else None)
     if rank == 0:
         line.update(extras)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl, osc=W.oscillation(**OSC_BENCH) if args.osc else None)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_box3d(args, dist, device, world, steps=20, fp64_peak_tflops=None):
+    """A 3D box (Sec. 5's future-work geometry): 64 x 64 x 64 cells of 1/16 cm,
+    16 directions per cell (4.19M particles, 2.1 GB of state: larger than L2),
+    per-cell densities and 3D flux vectors from a seeded generator, quadratic
+    shape.  Autotuned grid, `steps` steps timed with CUDA events on the box's
+    stream, the per-kernel launch times recorded by the library in the same
+    window, and the dominant kernel's FP64 roofline."""
+    import torch
+
+    from paper_2101_02745_gb300 import emu as E
+    from paper_2101_02745_gb300 import workloads as W
+
+    n3 = args.n3 or 64
+    wl = W.random_box3(n3, n3, n3, args.ndir3 or 16, seed=0)
+    box = E.Box3D.from_workload(wl, device=device)
+    dt = box.timestep()
+    choice, cand_ms = box.autotune(trial_steps=2)
+    box.step(args.warmup, dt)
+    barrier(dist, device)
+    torch.cuda.synchronize(device)
+    E.emu_profile(box.box, True)
+    n0 = box.launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(box.stream)
+    box.step(steps, dt)
+    ev1.record(box.stream)
+    torch.cuda.synchronize(device)
+    ms = max_over_ranks(dist, ev0.elapsed_time(ev1), device)
+    launches = box.launches() - n0
+    kt = E.emu_kernel_times(box.box)
+    E.emu_profile(box.box, False)
+    box.sync()
+    per = {k: (t / n if n else 0.0, n, t) for k, (t, n) in kt.items()}
+    total = sum(t for (_, _, t) in per.values()) or 1.0
+    dominant = "rk_stage" if per["rk_stage"][2] >= per["deposit"][2] else "deposit"
+    avg = per[dominant][0]
+    flops = (FLOPS3_RK if dominant == "rk_stage" else FLOPS3_DEPOSIT) * wl.P
+    achieved = flops / (avg * 1e-3) / 1e12
+    peak = fp64_peak_tflops or PEAK_FP64_DERIVED_TFLOPS
+    out = {"workload": wl.name, "particles_per_gpu": wl.P, "cells": [wl.nx, wl.ny, wl.nz], "ndir": wl.ndir,
+           "steps": steps, "value": world * wl.P * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+           "note": "launches bracketed by the library's timing events (no graph replay) in this window",
+           "autotune_choice": choice, "autotune_ms": [round(float(x), 4) for x in cand_ms],
+           "gpu_launches": launches,
+           "kernels": {k: {"launches": n, "avg_ms": a, "share": t / total} for k, (a, n, t) in per.items() if n},
+           "roofline": {"bound": "alu", "kernel": f"k3_{dominant}", "achieved": achieved, "peak": peak,
+                        "unit": "TFLOP/s", "frac": achieved / peak, "flops_per_launch": flops,
+                        "avg_launch_ms": avg,
+                        "peak_source": "measured in this run (DGEMM)" if fp64_peak_tflops else "derived"}}
+    del box
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_box3d(args, rank, world, local_rank):
+    """--workload box_3d: the 3D box's own line (value = its particle-updates/s)."""
+    import torch
+
+    from paper_2101_02745_gb300 import build as B
+
+    if rank == 0:
+        B.build()
+    dist = dist_init(world, True)
+    device = torch.device("cuda", local_rank)
+    torch.cuda.set_device(device)
+    barrier(dist, device)
+    pk = fp64_peak(device) if not args.no_fp64_peak else None
+    clocks = ClockSampler(device.index).start()
+    r = measure_box3d(args, dist, device, world, args.steps, pk["tflops"] if pk else None)
+    clk = clocks.stop()
+    if rank == 0:
+        line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": r["workload"], "cells": r["cells"], "ndir": r["ndir"],
+                           "particles_per_gpu": r["particles_per_gpu"],
+                           "l2": "inputs larger than L2 (particle state %.2f GB per GPU vs 129 MB L2)"
+                                 % (r["particles_per_gpu"] * 496 / 1e9)},
+                "roofline": r["roofline"], "box_3d": r, "gpu_launches": r["gpu_launches"], "clocks": clk,
+                "fp64_peak": pk}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -674,8 +776,11 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="throughput_1d",
-                    choices=["throughput_1d", "paper_1d", "paper_1d_asym", "tiny_fiducial", "sweep", "adjoint"])
+                    choices=["throughput_1d", "paper_1d", "paper_1d_asym", "tiny_fiducial", "sweep", "adjoint",
+                             "box_3d"])
     ap.add_argument("--nbox", type=int, default=256, help="boxes of the sweep workload")
+    ap.add_argument("--n3", type=int, default=0, help="cells per axis of the 3D box (default 64)")
+    ap.add_argument("--ndir3", type=int, default=0, help="directions per cell of the 3D box (default 16)")
     ap.add_argument("--nz", type=int, default=0, help="cells of the throughput workload (profiling runs)")
     ap.add_argument("--ndir", type=int, default=0, help="directions of the throughput workload (profiling runs)")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
@@ -705,6 +810,8 @@ def main(argv=None):
         return run_sweep(args, rank, world, local_rank)
     if args.workload == "adjoint":
         return run_adjoint(args, rank, world, local_rank)
+    if args.workload == "box_3d":
+        return run_box3d(args, rank, world, local_rank)
     return run_gpu(args, rank, world, local_rank)
 
 
