@@ -469,6 +469,7 @@ def run_gpu(args, rank, world, local_rank):
         extras["batched"] = measure_sweep(args, dist, device, rank, world, min(args.steps, 20))
         extras["adjoint"] = measure_adjoint(dist, device, world, reps=1)
         extras["paper_shape"] = measure_paper_shape(args, dist, device, world)
+        extras["anywhere"] = measure_anywhere(args, dist, device, world, steps=min(args.steps, 20))
         extras["box_3d"] = measure_box3d(args, dist, device, world, steps=min(args.steps, 10),
                                          fp64_peak_tflops=roofline["peak"] if pk else None)
     if rank == 0:
@@ -565,6 +566,58 @@ def run_box3d(args, rank, world, local_rank):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def measure_anywhere(args, dist, device, world, steps=20):
+    """Particles anywhere: the paper's 1D run shape (1024 cells x 378
+    directions, 387,072 particles) with every position moved by U(-0.45, 0.45)
+    cells and every particle given its own random direction (numpy PCG64(0)),
+    so no ring keeps the lattice contract and the box steps with the sorted
+    path (per stage a stable radix sort by cell and a deposit by one warp per
+    cell).  `steps` steps timed with CUDA events; the lattice path on the
+    unscattered box beside it."""
+    import numpy as np
+    import torch
+
+    from paper_2101_02745_gb300 import emu as E
+    from paper_2101_02745_gb300 import workloads as W
+
+    wl = W.paper_1d()
+    rng = np.random.Generator(np.random.PCG64(0))
+    out = {"workload": wl.name + "_anywhere", "particles_per_gpu": wl.P, "steps": steps,
+           "scatter": "positions + U(-0.45, 0.45) cells, one random direction per particle"}
+    for general in (True, False):
+        box = E.Box.from_workload(wl, device=device)
+        if general:
+            h = box.get_host()
+            z = h["z"] + rng.uniform(-0.45, 0.45, wl.P) * wl.dz
+            z = np.mod(z, wl.Lz)
+            om = rng.normal(size=(wl.P, 3))
+            om /= np.linalg.norm(om, axis=1, keepdims=True)
+            box.set_host(z=z, ox=om[:, 0].copy(), oy=om[:, 1].copy(), oz=om[:, 2].copy())
+            assert box.general()
+        dt = box.timestep()
+        box.step(args.warmup, dt)
+        barrier(dist, device)
+        torch.cuda.synchronize(device)
+        n0 = box.launches()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(box.stream)
+        box.step(steps, dt)
+        ev1.record(box.stream)
+        torch.cuda.synchronize(device)
+        ms = max_over_ranks(dist, ev0.elapsed_time(ev1), device)
+        box.sync()
+        r = {"value": world * wl.P * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+             "launches_per_step": (box.launches() - n0) / steps}
+        if general:
+            out.update(r)
+        else:
+            out["lattice_path"] = r
+        del box
+    out["vs_lattice"] = out["value"] / out["lattice_path"]["value"]
+    torch.cuda.empty_cache()
+    return out
 
 
 def measure_paper_shape(args, dist, device, world, steps=100):

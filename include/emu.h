@@ -135,7 +135,9 @@ int emu_init_particles(emu_box* box, const double* n_nu, const double* n_nubar, 
 /* Copy particle fields in from (set) or out to (get) caller buffers laid out
  * like emu_particles (rho/rhobar as [9][P]).  Any pointer may be NULL to skip
  * that field.  on_host = 1: host pointers (the call synchronises for get);
- * 0: device pointers.  emu_set_particles re-validates the rings. */
+ * 0: device pointers.  emu_set_particles re-validates the rings; with
+ * positions from host memory or with directions it also chooses the particle
+ * layout (see emu_set_layout), which synchronises the stream. */
 int emu_set_particles(emu_box* box, const double* z, const double* ox, const double* oy,
                       const double* oz, const double* N, const double* Nbar, const double* rho,
                       const double* rhobar, int on_host);
@@ -272,6 +274,31 @@ int emu_autotune(emu_box* box, int trial_steps, int32_t* choice_out, double* ms_
  * that supports cooperative launches.  Errors: EMU_EINVAL (bad form, grid too
  * large, step in progress). */
 int emu_set_step_form(emu_box* box, int32_t form);
+
+/* Particle layout.  The paper places one particle per direction at every cell
+ * centre and moves all at constant velocity (Sec. 3.1, Eq. 4), so every box
+ * keeps the lattice contract (see the conventions) and the lattice path
+ * runs.  Particles may also sit anywhere, with any direction each (installed
+ * by emu_set_particles): the deposit (Eq. 5) and interpolation (Eq. 6) are
+ * defined for any positions.  Their path sorts the particles by cell at every
+ * stage (a stable radix sort of the library's own), deposits with one warp per
+ * cell over its stencil's cells in that order (no float atomics: bitwise
+ * reproducible), and runs the RK stage with one thread per particle; it is
+ * slower than the lattice path.
+ *   layout  0: the lattice path (particles off their sites give EMU_ELATTICE);
+ *           1: the path for particles anywhere;
+ *          -1 (default): chosen when particles are installed: emu_set_particles
+ *              with positions from host memory, or with directions, checks
+ *              the contract on the device and synchronises the stream to read
+ *              the result (a device-to-device copy of positions alone, such as
+ *              a checkpoint of the same box, keeps the path in use; call
+ *              emu_set_layout(box, -1) to check again); initialised particles
+ *              take the lattice path.
+ * emu_get_layout reports the path in use (1 = particles anywhere).  The
+ * adjoint calls, the fused step form and 3D boxes need the lattice path.
+ * Errors: EMU_EINVAL. */
+int emu_set_layout(emu_box* box, int32_t layout);
+int emu_get_layout(emu_box* box, int32_t* general);
 
 /* Bound [ns] of every grid-barrier wait of the fused step (default 1e9: far
  * above any phase of a box that fits the GPU).  A wait that exceeds it stops

@@ -22,6 +22,7 @@
 
 #include "kernels.cuh"
 #include "kernels3d.cuh"
+#include "kernels_general.cuh"
 
 using namespace emu_dev;
 
@@ -131,6 +132,9 @@ const char* make_shape(const emu_config* cfgs, int nbox, Shape& S) {
 struct Layout {
   size_t geo, dts, nmax, A, At, mom, partial, W, err, dirtab, shift, shift2, bar, species, dirs, diag, scalar, total;
   size_t rowgeo = 0;   // 3D boxes: one descriptor per cell row (the deposit combination's batch view)
+  // particles anywhere (kernels_general.cuh): sort keys and values (two of
+  // each), digit histogram, cell starts, lattice-check flag
+  size_t gkeys = 0, gkeys2 = 0, gids = 0, gids2 = 0, ghist = 0, gstart = 0, gflag = 0;
 };
 
 Layout layout(const Shape& S) {
@@ -155,6 +159,14 @@ Layout layout(const Shape& S) {
   L.dirs = take(sizeof(double) * 3 * MT);
   L.diag = take(sizeof(double) * 63 * nb);
   L.scalar = take(sizeof(double) * 4);
+  const size_t P = (size_t)S.Ptot, nblk = (P + kRadixTile - 1) / kRadixTile;
+  L.gkeys = take(sizeof(unsigned) * P);
+  L.gkeys2 = take(sizeof(unsigned) * P);
+  L.gids = take(sizeof(int) * P);
+  L.gids2 = take(sizeof(int) * P);
+  L.ghist = take(sizeof(int) * kRadixBuckets * (nblk ? nblk : 1));
+  L.gstart = take(sizeof(int) * ((size_t)NZ + 1));
+  L.gflag = take(sizeof(int));
   L.total = off;
   return L;
 }
@@ -185,6 +197,8 @@ struct emu_box {
   unsigned long long limit_ns = 1000000000ull;   // bound of each grid-barrier wait of k_step
   // 3D boxes (emu3_create): the box is S's single box (cells in 3D index order),
   // positions x, y beside the particle arrays, and one descriptor per cell row
+  int layout = -1;        // particle layout: 0 lattice, 1 anywhere, -1 checked when particles are installed
+  bool general = false;   // the step runs the path for particles anywhere (kernels_general.cuh)
   bool is3d = false;
   emu3_config c3{};
   double *x3 = nullptr, *y3 = nullptr;
@@ -503,6 +517,10 @@ int launch3_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, 
                     double* out);
 int run3_moments(emu_box* b);
 int rebuild_dirtable3(emu_box* b);
+// The launches for particles anywhere (defined below).
+int launch_gstep(emu_box* b, int dry);
+int launch_gstage(emu_box* b, int s, int dry);
+int launch_gdeposit(emu_box* b, int mode, const double* rnu, const double* rnb, double frac, double* out);
 
 int launch_stage(emu_box* b, int s, int dry) {
   const size_t P = (size_t)b->S.Ptot;
@@ -619,6 +637,7 @@ int launch_rk(emu_box* b, int s, const int* srow, int dry) {
 
 int launch_step(emu_box* b, int dry) {
   if (b->is3d) return launch3_step(b, dry);
+  if (b->general) return launch_gstep(b, dry);
   if (b->step_form == 1) return launch_fused(b, dry, 1);
   if (int rc = launch_shifts(b, kStageFrac, 4)) return rc;
   for (int s = 1; s <= 4; ++s)
@@ -645,6 +664,10 @@ int run_steps(emu_box* b, int64_t nsteps) {
 
 int run_moments(emu_box* b) {
   if (b->is3d) return run3_moments(b);
+  if (b->general) {
+    if (int rc = launch_gdeposit(b, 1, b->pt.rho, b->pt.rhobar, 0.0, b->mom)) return rc;
+    return launch_gdeposit(b, 2, b->pt.rho, b->pt.rhobar, 0.0, b->mom + (size_t)kNA * b->S.NZ);
+  }
   const double zero = 0.0;
   if (int rc = launch_shifts(b, &zero, 1)) return rc;
   if (int rc = launch_deposit(b, 1, b->pt.rho, b->pt.rhobar, b->shift, 0.0, b->mom)) return rc;
@@ -943,6 +966,130 @@ int no_3d(emu_box* b, const char* what) {
   return fail(b, EMU_EINVAL, "%s is not available for a 3D box", what);
 }
 
+
+// ------------------------------------------------- particles anywhere (1D)
+//
+// The path of kernels_general.cuh: per stage, sort the particles by the cell
+// containing their stage position (stable radix sort), deposit with one warp
+// per cell in sorted order, then one thread per particle for the RK stage.
+
+// Stable sort of the particles by containing cell at z + frac dt c Omega_z;
+// leaves the cell starts in b->gstart and returns the sorted particle ids.
+int gsort(emu_box* b, double frac, const int** ids_out) {
+  const Batch B = batch_view(b);
+  const int64_t P = b->S.Ptot;
+  unsigned* k0 = (unsigned*)(b->ws + b->L.gkeys);
+  unsigned* k1 = (unsigned*)(b->ws + b->L.gkeys2);
+  int* v0 = (int*)(b->ws + b->L.gids);
+  int* v1 = (int*)(b->ws + b->L.gids2);
+  int* hist = (int*)(b->ws + b->L.ghist);
+  int* start = (int*)(b->ws + b->L.gstart);
+  const unsigned pblocks = (unsigned)((P + kThreads - 1) / kThreads);
+  before_launch(b, CLS_OTHER);
+  pdl(b->stream, k_gkeys, dim3(pblocks), B, b->pt.z, b->pt.oz, frac, k0, v0, b->err);
+  if (int rc = after_launch(b, "sort key kernel")) return rc;
+  int bits = 0;
+  while (bits < 31 && (int64_t(1) << bits) < (int64_t)b->S.NZ) ++bits;
+  const int nblk = (int)((P + kRadixTile - 1) / kRadixTile);
+  for (int shift = 0; shift < bits; shift += kRadixBits) {
+    before_launch(b, CLS_OTHER);
+    k_radix_hist<<<nblk, kThreads, 0, b->stream>>>(k0, P, shift, hist, nblk);
+    if (int rc = after_launch(b, "radix histogram kernel")) return rc;
+    before_launch(b, CLS_OTHER);
+    k_scan_exclusive<<<1, kThreads, 0, b->stream>>>(hist, (int64_t)kRadixBuckets * nblk);
+    if (int rc = after_launch(b, "radix scan kernel")) return rc;
+    before_launch(b, CLS_OTHER);
+    k_radix_scatter<<<nblk, kThreads, 0, b->stream>>>(k0, v0, P, shift, hist, nblk, k1, v1);
+    if (int rc = after_launch(b, "radix scatter kernel")) return rc;
+    std::swap(k0, k1);
+    std::swap(v0, v1);
+  }
+  before_launch(b, CLS_OTHER);
+  k_cell_start<<<(unsigned)((P + 1 + kThreads - 1) / kThreads), kThreads, 0, b->stream>>>(k0, P, b->S.NZ, start);
+  if (int rc = after_launch(b, "cell start kernel")) return rc;
+  *ids_out = v0;
+  return EMU_OK;
+}
+
+// Deposit of particles anywhere (modes as k_deposit) into out.
+int launch_gdeposit(emu_box* b, int mode, const double* rnu, const double* rnb, double frac, double* out) {
+  const int* ids = nullptr;
+  if (int rc = gsort(b, frac, &ids)) return rc;
+  const Batch B = batch_view(b);
+  const int* start = (const int*)(b->ws + b->L.gstart);
+  const int64_t wb = ((int64_t)B.NZ + kWarps - 1) / kWarps;
+  const dim3 grid((unsigned)(wb < 8 * kPersistBlocks ? wb : 8 * kPersistBlocks));
+  before_launch(b, CLS_DEPOSIT);
+  by_order(b->S.order, [&](auto O) {
+    constexpr int R = decltype(O)::value;
+    cudaStream_t st = b->stream;
+    if (mode == 0) pdl(st, k_gdeposit<0, R>, grid, B, b->pt, rnu, rnb, frac, ids, start, out, b->err);
+    else if (mode == 1) pdl(st, k_gdeposit<1, R>, grid, B, b->pt, rnu, rnb, frac, ids, start, out, b->err);
+    else if (mode == 2) pdl(st, k_gdeposit<2, R>, grid, B, b->pt, rnu, rnb, frac, ids, start, out, b->err);
+    else if (mode == 4) pdl(st, k_gdeposit<4, R>, grid, B, b->pt, rnu, rnb, frac, ids, start, out, b->err);
+    else pdl(st, k_gdeposit<5, R>, grid, B, b->pt, rnu, rnb, frac, ids, start, out, b->err);
+    return 0;
+  });
+  return after_launch(b, "deposit kernel (particles anywhere)");
+}
+
+int launch_gstage(emu_box* b, int s, int dry) {
+  const size_t P = (size_t)b->S.Ptot;
+  const double* rnu = (s == 1) ? b->pt.rho : b->pt.stage;
+  const double* rnb = (s == 1) ? b->pt.rhobar : b->pt.stage + 9 * P;
+  if (int rc = launch_gdeposit(b, 5, rnu, rnb, kStageFrac[s - 1], b->At)) return rc;
+  before_launch(b, CLS_RK);
+  by_order(b->S.order, [&](auto O) {
+    constexpr int R = decltype(O)::value;
+    const dim3 grid((unsigned)((P + kThreads - 1) / kThreads));
+    if (b->pot) pdl(b->stream, k_grk_stage<true, R>, grid, batch_view(b), b->pt, (const double*)b->At, s, dry);
+    else pdl(b->stream, k_grk_stage<false, R>, grid, batch_view(b), b->pt, (const double*)b->At, s, dry);
+    return 0;
+  });
+  return after_launch(b, "RK stage kernel (particles anywhere)");
+}
+
+int launch_gstep(emu_box* b, int dry) {
+  for (int s = 1; s <= 4; ++s)
+    if (int rc = launch_gstage(b, s, dry)) return rc;
+  return EMU_OK;
+}
+
+// Does every particle keep the lattice contract?  (Synchronises.)  Returns
+// EMU_OK and sets *on_lattice.
+int check_lattice(emu_box* b, bool* on_lattice) {
+  int* flag = (int*)(b->ws + b->L.gflag);
+  if (int rc = cuda_check(b, cudaMemsetAsync(flag, 0, sizeof(int), b->stream), "clear lattice flag")) return rc;
+  before_launch(b, CLS_OTHER);
+  k_lattice_check<<<(unsigned)((b->S.Ptot + kThreads - 1) / kThreads), kThreads, 0, b->stream>>>(batch_view(b),
+                                                                                                 b->pt, flag);
+  if (int rc = after_launch(b, "lattice check kernel")) return rc;
+  int h = 0;
+  if (int rc = cuda_check(b, cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, b->stream),
+                          "read lattice flag"))
+    return rc;
+  if (int rc = cuda_check(b, cudaStreamSynchronize(b->stream), "synchronise after lattice check")) return rc;
+  *on_lattice = h == 0;
+  return EMU_OK;
+}
+
+// Chooses the path after particles were installed (layout -1: by the check).
+int choose_layout(emu_box* b) {
+  bool general = b->layout == 1;
+  if (b->layout == -1) {
+    bool on = true;
+    if (int rc = check_lattice(b, &on)) return rc;
+    general = !on;
+  }
+  if (general != b->general) invalidate_graph(b);
+  b->general = general;
+  return EMU_OK;
+}
+
+int needs_lattice(emu_box* b, const char* what) {
+  return fail(b, EMU_EINVAL, "%s needs the particles on their lattice sites (emu_set_layout)", what);
+}
+
 int bind_common(emu_box* b, const emu_particles* parts, void* workspace, int64_t workspace_bytes, void* stream);
 
 int create_common(const emu_config* cfgs, int nbox, emu_box** out) {
@@ -993,6 +1140,8 @@ int init_common(emu_box* b, const double* n_nu, const double* n_nubar, const dou
   if (int rc = after_launch(b, "init kernel")) return rc;
   if (int rc = rebuild_dirtable(b)) return rc;
   b->next_stage = 1;
+  if ((b->layout == 1) != b->general) invalidate_graph(b);
+  b->general = b->layout == 1;   // initial particles sit on their lattice sites
   return read_errors(b);  // synchronises: the host staging vector may go
 }
 
@@ -1116,7 +1265,12 @@ int emu_set_particles(emu_box* b, const double* z, const double* ox, const doubl
                               "copy particles in"))
         return rc;
   b->next_stage = 1;
-  if (ox || oy || oz)
+  // the layout is checked when positions come from host memory or directions
+  // change; a device-to-device copy of positions alone (a checkpoint of this
+  // box restored) keeps the layout in use
+  if (!b->is3d && ((z && on_host) || ox || oy || oz))
+    if (int rc = choose_layout(b)) return rc;
+  if ((ox || oy || oz) && !b->general)
     if (int rc = rebuild_dirtable(b)) return rc;
   if (on_host) return cuda_check(b, cudaStreamSynchronize(b->stream), "synchronise after copy in");
   return EMU_OK;
@@ -1151,6 +1305,8 @@ int emu_deposit(emu_box* b, int src, double pos_dt, double* A_out, int on_host) 
   if (b->is3d) {
     if (int rc = launch3_shifts(b, &one, 1)) return rc;
     if (int rc = launch3_deposit(b, 0, rnu, rnb, b->shift, 1.0, b->A)) return rc;
+  } else if (b->general) {
+    if (int rc = launch_gdeposit(b, 0, rnu, rnb, 1.0, b->A)) return rc;
   } else {
     if (int rc = launch_shifts(b, &one, 1)) return rc;
     if (int rc = launch_deposit(b, 0, rnu, rnb, b->shift, 1.0, b->A)) return rc;
@@ -1166,12 +1322,16 @@ int emu_interpolate_H(emu_box* b, double pos_dt, double* H_out, int on_host) {
   if (!std::isfinite(pos_dt)) return fail(b, EMU_EINVAL, "pos_dt must be finite");
   if (int rc = set_dts(b, &pos_dt)) return rc;
   const double one = 1.0;
-  if (int rc = b->is3d ? launch3_shifts(b, &one, 1) : launch_shifts(b, &one, 1)) return rc;
+  if (!b->general)
+    if (int rc = b->is3d ? launch3_shifts(b, &one, 1) : launch_shifts(b, &one, 1)) return rc;
   double* dst = H_out;
   if (on_host) dst = b->pt.acc;  // staging: the RK scratch holds 18 P doubles
   before_launch(b, CLS_OTHER);
   by_order(b->S.order, [&](auto O) {
-    if (b->is3d)
+    if (b->general)
+      k_ginterpolate<decltype(O)::value><<<(unsigned)((b->S.Ptot + kThreads - 1) / kThreads), kThreads, 0,
+                                           b->stream>>>(batch_view(b), b->pt, b->A, 1.0, dst);
+    else if (b->is3d)
       k3_interpolate<decltype(O)::value><<<persist_grid(b), kThreads, 0, b->stream>>>(
           box3_view(b), b->x3, b->y3, b->pt.z, b->dirtab, b->shift, b->A, 1.0, dst, b->err);
     else
@@ -1193,9 +1353,11 @@ int emu_rk_stage(emu_box* b, int s, double dt) {
   if (s > 1 && dt != b->dt_h[0]) return fail(b, EMU_EINVAL, "dt changed within a step");
   if (s == 1) {
     if (int rc = set_dts(b, &dt)) return rc;
-    if (int rc = b->is3d ? launch3_shifts(b, kStageFrac, 4) : launch_shifts(b, kStageFrac, 4)) return rc;
+    if (!b->general)
+      if (int rc = b->is3d ? launch3_shifts(b, kStageFrac, 4) : launch_shifts(b, kStageFrac, 4)) return rc;
   }
-  if (int rc = b->is3d ? launch3_stage(b, s, 0) : launch_stage(b, s, 0)) return rc;
+  if (int rc = b->general ? launch_gstage(b, s, 0) : b->is3d ? launch3_stage(b, s, 0) : launch_stage(b, s, 0))
+    return rc;
   b->next_stage = s == 4 ? 1 : s + 1;
   return EMU_OK;
 }
@@ -1260,6 +1422,8 @@ int emu_batch_diagnostics(emu_box* b, double* out, int on_host) {
   if (b->is3d) {
     if (int rc = launch3_shifts(b, &zero, 1)) return rc;
     if (int rc = launch3_deposit(b, 4, b->pt.rho, b->pt.rhobar, b->shift, 0.0, b->mom)) return rc;
+  } else if (b->general) {
+    if (int rc = launch_gdeposit(b, 4, b->pt.rho, b->pt.rhobar, 0.0, b->mom)) return rc;
   } else {
     if (int rc = launch_shifts(b, &zero, 1)) return rc;
     if (int rc = launch_deposit(b, 4, b->pt.rho, b->pt.rhobar, b->shift, 0.0, b->mom)) return rc;
@@ -1317,7 +1481,7 @@ int emu_autotune(emu_box* b, int trial_steps, int32_t* choice_out, double* ms_ou
     b->blocks = grids[c];
     b->rk_form = c % 2;
     b->step_form = c >= 6 ? 1 : 0;
-    if (b->step_form == 1 && (b->is3d || b->blocks > maxb)) {   // not every block could be resident: not a candidate
+    if (b->step_form == 1 && (b->is3d || b->general || b->blocks > maxb)) {   // not a candidate here
       if (ms_out) ms_out[c] = -1.0;
       continue;
     }
@@ -1350,6 +1514,7 @@ int emu_set_step_form(emu_box* b, int32_t form) {
   if (int rc = check_bound(b)) return rc;
   if (form < 0 || form > 1) return fail(b, EMU_EINVAL, "form must be 0 or 1");
   if (form == 1 && b->is3d) return no_3d(b, "the fused step form");
+  if (form == 1 && b->general) return needs_lattice(b, "the fused step form");
   if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
   if (form == 1) {
     const int maxb = fused_max_blocks(b);
@@ -1360,6 +1525,24 @@ int emu_set_step_form(emu_box* b, int32_t form) {
   }
   b->step_form = form;
   invalidate_graph(b);
+  return EMU_OK;
+}
+
+int emu_set_layout(emu_box* b, int32_t layout) {
+  if (int rc = check_bound(b)) return rc;
+  if (b->is3d) return no_3d(b, "a particle layout other than the lattice");
+  if (layout < -1 || layout > 1) return fail(b, EMU_EINVAL, "layout must be -1, 0 or 1");
+  if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
+  b->layout = layout;
+  if (int rc = choose_layout(b)) return rc;
+  if (!b->general) return rebuild_dirtable(b);
+  return EMU_OK;
+}
+
+int emu_get_layout(emu_box* b, int32_t* general) {
+  if (int rc = check_bound(b)) return rc;
+  if (!general) return fail(b, EMU_EINVAL, "general is NULL");
+  *general = b->general ? 1 : 0;
   return EMU_OK;
 }
 
@@ -1723,6 +1906,7 @@ int64_t emu_batch_adjoint_workspace_bytes(const emu_config* cfgs, int32_t nbox) 
 int emu_adjoint_seed(emu_box* b, const double* dmom, double* lambda, double* gN, double* gNbar) {
   if (int rc = check_bound(b)) return rc;
   if (b->is3d) return no_3d(b, "the adjoint");
+  if (b->general) return needs_lattice(b, "the adjoint");
   if (!dmom || !lambda || !gN || !gNbar) return fail(b, EMU_EINVAL, "adjoint seed: NULL pointer");
   if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
   const double zero = 0.0;
@@ -1740,6 +1924,7 @@ int emu_adjoint_step(emu_box* b, double dt, double* lambda, double* gN, double* 
                      int64_t adj_ws_bytes) {
   if (int rc = check_bound(b)) return rc;
   if (b->is3d) return no_3d(b, "the adjoint");
+  if (b->general) return needs_lattice(b, "the adjoint");
   if (dt != 0.0) {
     if (b->S.nbox != 1) return fail(b, EMU_EINVAL, "a batch takes dt = 0 (each box's own step size)");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(b, EMU_EINVAL, "dt must be positive and finite, or 0");
@@ -1780,6 +1965,7 @@ int64_t emu_batch_adjoint_record_bytes(const emu_config* cfgs, int32_t nbox) {
 static int record_checks(emu_box* b, double dt, const void* buf, int64_t bytes, size_t need, const char* what) {
   if (int rc = check_bound(b)) return rc;
   if (b->is3d) return no_3d(b, "the adjoint");
+  if (b->general) return needs_lattice(b, "the adjoint");
   if (dt != 0.0) {
     if (b->S.nbox != 1) return fail(b, EMU_EINVAL, "a batch takes dt = 0 (each box's own step size)");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(b, EMU_EINVAL, "dt must be positive and finite, or 0");

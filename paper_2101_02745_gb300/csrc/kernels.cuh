@@ -780,7 +780,7 @@ __device__ __forceinline__ void rk_particle(const BoxGeo& g, const Parts& pt, co
     }
   }
   if (s == 4) {
-    const double vzv = __ldg(vz);
+    const double vzv = *vz;   // (a plain load: vz may point at a caller's local value)
     const double zn = wrap_z(fma(dtb, vzv, ldp<COH>(pt.z + p)), g.Lz);
     if (dry) pt.stage[p] = zn;  // (only to keep the work of the real stage)
     else pt.z[p] = zn;

@@ -118,6 +118,8 @@ def load(build_if_missing: bool = False):
         "emu_set_rk_form": (i32, [vp, ctypes.c_int32]),
         "emu_set_step_form": (i32, [vp, ctypes.c_int32]),
         "emu_set_barrier_timeout": (i32, [vp, i64]),
+        "emu_set_layout": (i32, [vp, ctypes.c_int32]),
+        "emu_get_layout": (i32, [vp, ctypes.POINTER(ctypes.c_int32)]),
         "emu_set_oscillation": (i32, [vp, ctypes.c_int32, ctypes.POINTER(emu_oscillation)]),
         "emu_adjoint_workspace_bytes": (i64, [cfgp]),
         "emu_batch_adjoint_workspace_bytes": (i64, [cfgp, ctypes.c_int32]),
@@ -343,6 +345,18 @@ def emu_set_step_form(box, form: int):
 
 def emu_set_barrier_timeout(box, ns: int):
     _check(box, load().emu_set_barrier_timeout(box, int(ns)))
+
+
+def emu_set_layout(box, layout: int):
+    """0: particles on their lattice sites, 1: anywhere, -1: checked when particles are installed."""
+    _check(box, load().emu_set_layout(box, int(layout)))
+
+
+def emu_get_layout(box) -> int:
+    """1 if the box steps with the path for particles anywhere, else 0."""
+    g = ctypes.c_int32()
+    _check(box, load().emu_get_layout(box, ctypes.byref(g)))
+    return int(g.value)
 
 
 # (step form, grid blocks, RK form) of each autotuner candidate, as emu.h lists them
@@ -608,6 +622,13 @@ class Box:
 
     def set_barrier_timeout(self, ns: int):
         emu_set_barrier_timeout(self.box, ns)
+
+    @_ordered
+    def set_layout(self, layout: int):
+        emu_set_layout(self.box, layout)
+
+    def general(self) -> bool:
+        return bool(emu_get_layout(self.box))
 
     def apply_choice(self, choice: int):
         apply_choice(self.box, choice)

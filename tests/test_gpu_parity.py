@@ -226,18 +226,28 @@ def test_diagnostics_match_oracle(torch, order):
 
 
 def test_lattice_violation_is_reported(torch):
+    """With the lattice layout fixed (emu_set_layout 0), a particle off its
+    site is reported; with the default (checked when particles are installed)
+    the box takes the path for particles anywhere instead."""
     from paper_2101_02745_gb300.emu import EmuError, EMU_ELATTICE
     wl = W.random_box(31, 4, seed=6)
     box = _box(wl)
+    box.set_layout(0)
     h = box.get_host()
     z = h["z"].copy()
     z[40] += 0.7 * wl.dz      # out of the cell its ring position assigns
     box.set_host(z=z)
+    assert not box.general()
     box.step(1, 1e-13)
     with pytest.raises(EmuError) as ei:
         box.sync()
     assert ei.value.code == EMU_ELATTICE
     box.sync()  # the error word was cleared
+    auto = _box(wl)
+    auto.set_host(z=z)
+    assert auto.general()
+    auto.step(1, 1e-13)
+    auto.sync()
 
 
 def test_lattice_with_per_direction_offsets_and_ties(torch):
