@@ -620,6 +620,36 @@ def measure_anywhere(args, dist, device, world, steps=20):
     return out
 
 
+def run_anywhere(args, rank, world, local_rank):
+    """--workload anywhere: the scattered paper-shaped box's own line."""
+    import torch
+
+    from paper_2101_02745_gb300 import build as B
+
+    if rank == 0:
+        B.build()
+    dist = dist_init(world, True)
+    device = torch.device("cuda", local_rank)
+    torch.cuda.set_device(device)
+    barrier(dist, device)
+    clocks = ClockSampler(device.index).start()
+    r = measure_anywhere(args, dist, device, world, args.steps)
+    clk = clocks.stop()
+    if rank == 0:
+        line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": r["workload"], "particles_per_gpu": r["particles_per_gpu"],
+                           "scatter": r["scatter"],
+                           "l2": "inputs larger than L2 (particle state %.2f GB per GPU vs 129 MB L2)"
+                                 % (r["particles_per_gpu"] * 480 / 1e9)},
+                "anywhere": r, "gpu_launches": int(r["launches_per_step"] * args.steps), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def measure_paper_shape(args, dist, device, world, steps=100):
     """The paper's 1D run shape (1024 cells x 378 directions, 387,072 particles;
     the nubar flux along z, and tilted to normalize(0.1, 0, -1)): `steps` steps
@@ -830,7 +860,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="throughput_1d",
                     choices=["throughput_1d", "paper_1d", "paper_1d_asym", "tiny_fiducial", "sweep", "adjoint",
-                             "box_3d"])
+                             "box_3d", "anywhere"])
     ap.add_argument("--nbox", type=int, default=256, help="boxes of the sweep workload")
     ap.add_argument("--n3", type=int, default=0, help="cells per axis of the 3D box (default 64)")
     ap.add_argument("--ndir3", type=int, default=0, help="directions per cell of the 3D box (default 16)")
@@ -865,6 +895,8 @@ def main(argv=None):
         return run_adjoint(args, rank, world, local_rank)
     if args.workload == "box_3d":
         return run_box3d(args, rank, world, local_rank)
+    if args.workload == "anywhere":
+        return run_anywhere(args, rank, world, local_rank)
     return run_gpu(args, rank, world, local_rank)
 
 
