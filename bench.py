@@ -69,16 +69,19 @@ TRAFFIC_DEPOSIT = 296.7   # k_deposit<5> (traceless potential)
 
 # 3D boxes (quadratic shape: each particle reaches 3 x 3 neighbour rows), FP64
 # flops per particle of one launch, counted from the kernels' formulation:
-#   deposit: per neighbour row, the particle's weights on 3 axes (3 x 12), its
-#     share toward the warp's row (1) and its two weights scaled by it (2), the
-#     8 traceless components of B (29), the z-spread (40) and their sum (8):
-#     116; x 9 rows, plus the direction's moments (1, Omega) x S (56);
-#   RK stage: the weights (36); per neighbour row the x-y weight (1), G =
-#     A0 - Omega.A (48), the z-gather (40) and its weighted sum (16): 105;
-#     x 9 rows; the third diagonal difference (1), two commutators (162), RK
-#     update (72).
-FLOPS3_DEPOSIT = 9 * 116 + 56
-FLOPS3_RK = 36 + 9 * 105 + 1 + 162 + 72
+#   prep (k3_prep, once per particle and stage): the weights on 3 axes (3 x 12)
+#     and the 8 traceless components of B (29);
+#   deposit (k3_deposit_bw): per neighbour row, the particle's x-y share (1),
+#     its z-weights scaled by it (3), the z-spread (40) and the sum (8): 52;
+#     x 9 rows, plus the direction's moments (1, Omega) x S (56);
+#   G field (k3_gfield, once per direction and cell): A0 - Omega . A (48);
+#   RK stage: per neighbour row the x-y weight (1), the z-gather (40) and its
+#     weighted sum (16): 57; x 9 rows; the third diagonal difference (1), two
+#     commutators (162), RK update (72).
+FLOPS3_PREP = 36 + 29
+FLOPS3_DEPOSIT = 9 * 52 + 56
+FLOPS3_GFIELD = 48
+FLOPS3_RK = 9 * 57 + 1 + 162 + 72
 
 
 def measured_peaks():

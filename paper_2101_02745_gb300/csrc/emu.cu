@@ -135,6 +135,8 @@ struct Layout {
   // particles anywhere (kernels_general.cuh): sort keys and values (two of
   // each), digit histogram, cell starts, lattice-check flag
   size_t gkeys = 0, gkeys2 = 0, gids = 0, gids2 = 0, ghist = 0, gstart = 0, gflag = 0;
+  size_t bw3 = 0;   // 3D boxes: every particle's B and axis weights at the stage positions (k3_prep)
+  size_t gf3 = 0;   // 3D boxes: G = A0 - Omega . A of every (direction, cell) (k3_gfield)
 };
 
 Layout layout(const Shape& S) {
@@ -832,6 +834,9 @@ Layout layout3(const Shape& S, size_t nrows) {
   L.diag = take(sizeof(double) * 63);
   L.scalar = take(sizeof(double) * 4);
   L.rowgeo = take(sizeof(BoxGeo) * nrows);
+  const int nw = S.order == 3 ? Sten<3>::NW : Sten<2>::NW;
+  L.bw3 = take(sizeof(double) * (size_t)(kNC + 3 * nw) * (size_t)S.Ptot);
+  L.gf3 = take(sizeof(double) * (size_t)kNC * (size_t)S.Ptot);
   L.total = off;
   return L;
 }
@@ -918,26 +923,62 @@ int launch3_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, 
 
 int launch3_rk(emu_box* b, int s, const int* srow, int dry) {
   const Box3 v = box3_view(b);
+  const double* Bw = (const double*)(b->ws + b->L.bw3);
+  double* Gf = (double*)(b->ws + b->L.gf3);
+  before_launch(b, CLS_OTHER);
+  pdl(b->stream, k3_gfield, dim3((unsigned)((b->S.Ptot + kThreads - 1) / kThreads)), v, (const double*)b->At,
+      (const double*)b->dirtab, Gf);
+  if (int rc = after_launch(b, "3D G field kernel")) return rc;
   before_launch(b, CLS_RK);
   by_order(b->S.order, [&](auto O) {
     constexpr int R = decltype(O)::value;
     if (b->pot)
-      pdl(b->stream, k3_rk_stage<true, R>, persist_grid(b), v, b->pt, b->x3, b->y3, b->dirtab, srow, b->At, s, dry,
-          b->err);
+      pdl(b->stream, k3_rk_stage<true, R>, persist_grid(b), v, b->pt, b->x3, b->y3, b->dirtab, srow,
+          (const double*)Gf, Bw, s, dry);
     else
-      pdl(b->stream, k3_rk_stage<false, R>, persist_grid(b), v, b->pt, b->x3, b->y3, b->dirtab, srow, b->At, s,
-          dry, b->err);
+      pdl(b->stream, k3_rk_stage<false, R>, persist_grid(b), v, b->pt, b->x3, b->y3, b->dirtab, srow,
+          (const double*)Gf, Bw, s, dry);
     return 0;
   });
   return after_launch(b, "3D RK stage kernel");
 }
 
-int launch3_stage(emu_box* b, int s, int dry) {
+// The step's deposit of stage s: every particle's B and weights (k3_prep),
+// the gather from them (k3_deposit_bw), the combination into the traceless
+// potential At.
+int launch3_step_deposit(emu_box* b, int s, const int* srow) {
   const size_t P = (size_t)b->S.Ptot;
   const double* rnu = (s == 1) ? b->pt.rho : b->pt.stage;
   const double* rnb = (s == 1) ? b->pt.rhobar : b->pt.stage + 9 * P;
+  double* Bw = (double*)(b->ws + b->L.bw3);
+  const Box3 v = box3_view(b);
+  before_launch(b, CLS_OTHER);
+  by_order(b->S.order, [&](auto O) {
+    constexpr int R = decltype(O)::value;
+    pdl(b->stream, k3_prep<R>, dim3((unsigned)((P + kThreads - 1) / kThreads)), v, (const double*)b->x3,
+        (const double*)b->y3, (const double*)b->pt.z, (const double*)b->pt.N, (const double*)b->pt.Nbar, rnu, rnb,
+        (const double*)b->dirtab, srow, kStageFrac[s - 1], Bw, b->err);
+    return 0;
+  });
+  if (int rc = after_launch(b, "3D prep kernel")) return rc;
+  before_launch(b, CLS_DEPOSIT);
+  by_order(b->S.order, [&](auto O) {
+    constexpr int R = decltype(O)::value;
+    pdl(b->stream, k3_deposit_bw<R>, persist_grid(b), v, (const double*)Bw, (const double*)b->dirtab, srow,
+        b->partial);
+    return 0;
+  });
+  if (int rc = after_launch(b, "3D deposit kernel")) return rc;
+  const Batch B = row_view(b);
+  const int split = combine_split(b->S, B.nw);
+  before_launch(b, CLS_COMBINE);
+  pdl(b->stream, k_combine, dim3(combine_blocks(kNT, B.NZ, split)), B, b->partial, b->At, kNT, 1, split, b->err);
+  return after_launch(b, "deposit combine kernel");
+}
+
+int launch3_stage(emu_box* b, int s, int dry) {
   const int* srow = b->shift + (size_t)(s - 1) * 3 * b->S.MT;
-  if (int rc = launch3_deposit(b, 5, rnu, rnb, srow, kStageFrac[s - 1], b->At)) return rc;
+  if (int rc = launch3_step_deposit(b, s, srow)) return rc;
   return launch3_rk(b, s, srow, dry);
 }
 

@@ -242,6 +242,172 @@ k3_deposit(Box3 b, const double* __restrict__ x, const double* __restrict__ y, c
   if (bad) atomicOr(err, ERR_LATTICE);
 }
 
+// The step's deposit in two parts.  k3_prep: one thread per particle, its
+// shape weights on the three axes at the stage position (checked against the
+// cell its site assigns) and the 8 traceless components of B = N rho - Nbar
+// rhobar^* (Eq. 5), stored as Bw[row][P]: rows 0-7 B, then NW rows each of the
+// x, y and z weights.  k3_deposit_bw: the gather of k3_deposit<5> from them,
+// so that each particle's weights and B are computed once per stage instead
+// of once for every neighbour row it feeds; the RK stage reads the weights too.
+template <int ORDER>
+__global__ void __launch_bounds__(kThreads)
+k3_prep(Box3 b, const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ z,
+        const double* __restrict__ N, const double* __restrict__ Nbar, const double* __restrict__ r_nu,
+        const double* __restrict__ r_nb, const double* __restrict__ dirtab, const int* __restrict__ srow,
+        double frac, double* __restrict__ Bw, int* __restrict__ err) {
+  griddep_wait();
+  constexpr int NW = Sten<ORDER>::NW;
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= b.P) return;
+  const int64_t P = b.P;
+  const int M = b.M;
+  const int d = (int)(p / b.C);
+  const int c0 = (int)(p - (int64_t)d * b.C);
+  const int iz = c0 % b.n[2], iy = (c0 / b.n[2]) % b.n[1], ix = c0 / (b.n[2] * b.n[1]);
+  const int jx = wrapn(ix + __ldg(srow + d), b.n[0]);
+  const int jy = wrapn(iy + __ldg(srow + M + d), b.n[1]);
+  const int jz = wrapn(iz + __ldg(srow + 2 * M + d), b.n[2]);
+  const double pos_dt = frac * *b.dt;
+  double wx[NW], wy[NW], wz[NW];
+  int bad = shape_weights<ORDER>(fma(pos_dt, __ldg(dirtab + 3 * M + d), x[p]), (double)jx + 0.5, b.inv_h[0],
+                                 b.n_d[0], wx);
+  bad |= shape_weights<ORDER>(fma(pos_dt, __ldg(dirtab + 4 * M + d), y[p]), (double)jy + 0.5, b.inv_h[1], b.n_d[1],
+                              wy);
+  bad |= shape_weights<ORDER>(fma(pos_dt, __ldg(dirtab + 5 * M + d), z[p]), (double)jz + 0.5, b.inv_h[2], b.n_d[2],
+                              wz);
+  const double n1 = N[p], n2 = Nbar[p];
+  double bprev = 0.0;
+#pragma unroll
+  for (int c = 0; c < kNC; ++c) {
+    double bv;
+    if (c < 2) {
+      if (c == 0) bprev = fma(-n2, r_nb[p], n1 * r_nu[p]);
+      const double bn = fma(-n2, r_nb[(c + 1) * P + p], n1 * r_nu[(c + 1) * P + p]);
+      bv = bprev - bn;
+      bprev = bn;
+    } else {
+      const int k = c + 1;
+      const double xv = r_nu[k * P + p], yv = r_nb[k * P + p];
+      bv = (k == 4 || k == 6 || k == 8) ? fma(n2, yv, n1 * xv) : fma(-n2, yv, n1 * xv);
+    }
+    Bw[c * P + p] = bv;
+  }
+#pragma unroll
+  for (int q = 0; q < NW; ++q) {
+    Bw[(kNC + q) * P + p] = wx[q];
+    Bw[(kNC + NW + q) * P + p] = wy[q];
+    Bw[(kNC + 2 * NW + q) * P + p] = wz[q];
+  }
+  if (bad) atomicOr(err, ERR_LATTICE);
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(kThreads, 2)
+k3_deposit_bw(Box3 b, const double* __restrict__ Bw, const double* __restrict__ dirtab, const int* __restrict__ srow,
+              double* __restrict__ partial) {
+  griddep_wait();
+  constexpr int H = Sten<ORDER>::H, T = Sten<ORDER>::T, NW = Sten<ORDER>::NW;
+  const int lane = threadIdx.x & 31;
+  const int64_t w = logical_warp();
+  const int64_t u0 = unit3_begin(w, b), u1 = unit3_begin(w + 1, b);
+  if (u0 >= u1) return;
+  const int64_t P = b.P;
+  const int M = b.M, nx = b.n[0], ny = b.n[1], nz = b.n[2];
+  for (int64_t u = u0; u < u1;) {          // one segment per (row, tile)
+    const int64_t gtile = u / M;
+    const int row = (int)(gtile / b.ntz), tile = (int)(gtile - (int64_t)row * b.ntz);
+    const int jx = row / ny, jy = row - jx * ny;
+    const int dfirst = (int)(u - gtile * M);
+    const int64_t uend = min(u1, (gtile + 1) * M);
+    const int dlast = (int)(uend - gtile * M);
+    u = uend;
+    const int craw = tile * T - H + lane;
+    const int jz = wrapc(craw, nz);
+    double acc[kNT];
+#pragma unroll
+    for (int c = 0; c < kNT; ++c) acc[c] = 0.0;
+    for (int d = dfirst; d < dlast; ++d) {
+      const double ox = __ldg(dirtab + d), oy = __ldg(dirtab + M + d), oz = __ldg(dirtab + 2 * M + d);
+      const int sx = __ldg(srow + d), sy = __ldg(srow + M + d), sz = __ldg(srow + 2 * M + d);
+      double S[kNC];
+#pragma unroll
+      for (int c = 0; c < kNC; ++c) S[c] = 0.0;
+#pragma unroll 1
+      for (int a = -H; a <= H; ++a) {
+#pragma unroll 1
+        for (int bb = -H; bb <= H; ++bb) {
+          if (ORDER == 0 && (a != 0 || bb != 0)) continue;
+          const int64_t p = site3(b, d, wrapn(jx + a, nx), wrapn(jy + bb, ny), jz, sx, sy, sz);
+          // this particle's share of the warp's row, folded into its z-weights
+          const double f = __ldg(Bw + (kNC + H - a) * P + p) * __ldg(Bw + (kNC + NW + H - bb) * P + p);
+          double wz[NW];
+#pragma unroll
+          for (int q = 0; q < NW; ++q) wz[q] = f * __ldg(Bw + (kNC + 2 * NW + q) * P + p);
+          Spread<ORDER> spread;
+          spread.init(wz);
+#pragma unroll
+          for (int c = 0; c < kNC; ++c) S[c] += spread.apply(__ldg(Bw + c * P + p));
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < kNC; ++c) {
+        acc[c] += S[c];
+        acc[kNC + c] = fma(ox, S[c], acc[kNC + c]);
+        acc[2 * kNC + c] = fma(oy, S[c], acc[2 * kNC + c]);
+        acc[3 * kNC + c] = fma(oz, S[c], acc[3 * kNC + c]);
+      }
+    }
+    flush_tile<ORDER>(acc, gtile, craw, nz, w, lane, partial);
+  }
+}
+
+// G = A0 - Omega_d . A of every (direction, cell) from the traceless
+// potential, once per stage: Gf[c][d][cell] (component c, M C values each).
+// The RK stage's interpolation reads the G of its neighbour rows instead of
+// forming it for each of the (2H+1)^2 rows that need it.
+__global__ void __launch_bounds__(kThreads)
+k3_gfield(Box3 b, const double* __restrict__ At, const double* __restrict__ dirtab, double* __restrict__ Gf) {
+  griddep_wait();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t MC = (int64_t)b.M * b.C;
+  if (i >= MC) return;
+  const int d = (int)(i / b.C);
+  const int64_t cell = i - (int64_t)d * b.C;
+  const double ox = __ldg(dirtab + d), oy = __ldg(dirtab + b.M + d), oz = __ldg(dirtab + 2 * b.M + d);
+  const double* Aj = At + cell;
+  const int64_t Cn = b.C;
+#pragma unroll
+  for (int c = 0; c < kNC; ++c)
+    Gf[c * MC + i] = fma(-oz, Aj[(3 * kNC + c) * Cn],
+                         fma(-oy, Aj[(2 * kNC + c) * Cn], fma(-ox, Aj[(kNC + c) * Cn], Aj[c * Cn])));
+}
+
+// H of the lane's particle from the G field (traceless components): its x- and
+// y-weights over the neighbour rows times the z-interpolation along each row.
+// Every lane must call it.
+template <int ORDER>
+__device__ __forceinline__ void interp3g(const Box3& b, const double* __restrict__ Gf, int d, int jx, int jy, int jz,
+                                         const double (&wx)[Sten<ORDER>::NW], const double (&wy)[Sten<ORDER>::NW],
+                                         const double (&wz)[Sten<ORDER>::NW], double (&Hm)[kNC]) {
+  constexpr int H = Sten<ORDER>::H;
+  const int64_t MC = (int64_t)b.M * b.C;
+  const double* Gd = Gf + (int64_t)d * b.C + jz;
+#pragma unroll
+  for (int c = 0; c < kNC; ++c) Hm[c] = 0.0;
+#pragma unroll 1
+  for (int a = -H; a <= H; ++a) {
+#pragma unroll 1
+    for (int bb = -H; bb <= H; ++bb) {
+      if (ORDER == 0 && (a != 0 || bb != 0)) continue;
+      const int row = wrapn(jx + a, b.n[0]) * b.n[1] + wrapn(jy + bb, b.n[1]);
+      const double* G = Gd + (int64_t)row * b.n[2];
+      const double wab = pick(wx, H + a) * pick(wy, H + bb);
+#pragma unroll
+      for (int c = 0; c < kNC; ++c) Hm[c] = fma(wab, gather<ORDER>(wz, __ldg(G + c * MC)), Hm[c]);
+    }
+  }
+}
+
 // H of the lane's particle (traceless components, Eq. 6 then Eq. 2): its
 // x- and y-weights over the neighbour rows times the z-interpolation of
 // G = A0 - Omega . A along each row.  Every lane must call it.
@@ -276,15 +442,15 @@ __device__ __forceinline__ void interp3(const Box3& b, const double* A, int jx, 
 // One RK4 stage s (1..4) on the 3D grid after the deposit of the stage state
 // (as k_rk_stage): interpolation, H and Hbar, commutators, RK update; stage 4
 // also moves the particle on every axis (dry: the results of stage 4 go to the
-// RK scratch, for the autotuner's timing).  The shape weights are recomputed
-// from the stage positions (the same function and inputs as the deposit, so
-// the same weights), by the lanes that own a particle only: a halo lane's
-// particle belongs to another warp, which may already have moved it (stage 4);
-// halo lanes supply only the G values of their cells to the z-interpolation.
+// RK scratch, for the autotuner's timing).  The shape weights are those k3_prep
+// stored for the stage positions (the deposit's), read by the lanes that own a
+// particle; halo lanes supply only the G values of their cells to the
+// z-interpolation.
 template <bool POT, int ORDER>
 __global__ void __launch_bounds__(kThreads, 2)
 k3_rk_stage(Box3 b, Parts pt, double* __restrict__ x, double* __restrict__ y, const double* __restrict__ dirtab,
-            const int* __restrict__ srow, const double* __restrict__ At, int s, int dry, int* __restrict__ err) {
+            const int* __restrict__ srow, const double* __restrict__ Gf, const double* __restrict__ Bw, int s,
+            int dry) {
   griddep_wait();
   constexpr int H = Sten<ORDER>::H, T = Sten<ORDER>::T, NW = Sten<ORDER>::NW;
   const int lane = threadIdx.x & 31;
@@ -296,10 +462,8 @@ k3_rk_stage(Box3 b, Parts pt, double* __restrict__ x, double* __restrict__ y, co
   const double dt = *b.dt;
   const double bdt = (s == 1 || s == 4) ? dt / 6.0 : dt / 3.0;
   const double cdt = (s == 3) ? dt : 0.5 * dt;
-  const double pos_dt = stage_frac(s - 1) * dt;
   const double* src_b = (s == 1) ? pt.rhobar : pt.stage + 9 * P;
   const double* src_r = (s == 1) ? pt.rho : pt.stage;
-  int bad = 0;
   for (int64_t u = u0; u < u1; ++u) {
     const int64_t gtile = u / M;
     const int d = (int)(u - gtile * M);
@@ -314,14 +478,16 @@ k3_rk_stage(Box3 b, Parts pt, double* __restrict__ x, double* __restrict__ y, co
     zero_weights<ORDER>(wx);
     zero_weights<ORDER>(wy);
     zero_weights<ORDER>(wz);
-    if (active) {
-      bad |= shape_weights<ORDER>(fma(pos_dt, vx, x[p]), (double)jx + 0.5, b.inv_h[0], b.n_d[0], wx);
-      bad |= shape_weights<ORDER>(fma(pos_dt, vy, y[p]), (double)jy + 0.5, b.inv_h[1], b.n_d[1], wy);
-      bad |= shape_weights<ORDER>(fma(pos_dt, __ldg(dirtab + 5 * M + d), pt.z[p]), (double)jz + 0.5, b.inv_h[2],
-                                  b.n_d[2], wz);
+    if (active) {   // the weights of this stage's positions, from k3_prep
+#pragma unroll
+      for (int q = 0; q < NW; ++q) {
+        wx[q] = __ldg(Bw + (kNC + q) * P + p);
+        wy[q] = __ldg(Bw + (kNC + NW + q) * P + p);
+        wz[q] = __ldg(Bw + (kNC + 2 * NW + q) * P + p);
+      }
     }
     double Hm[kNC];
-    interp3<ORDER, kNC>(b, At, jx, jy, jz, ox, oy, oz, wx, wy, wz, Hm);
+    interp3g<ORDER>(b, Gf, d, jx, jy, jz, wx, wy, wz, Hm);
     if (!active) continue;
     double r[9];
 #pragma unroll
@@ -333,7 +499,6 @@ k3_rk_stage(Box3 b, Parts pt, double* __restrict__ x, double* __restrict__ y, co
       else { x[p] = xn; y[p] = yn; }
     }
   }
-  if (bad) atomicOr(err, ERR_LATTICE);
 }
 
 // Interpolation only (Eq. 6 then Eq. 2) of the full 36-row potential A at the
