@@ -173,3 +173,15 @@ def test_step_form_validation(torch):
     box.set_grid(608)                  # a grid too large for the fused form drops it
     box.step(1, box.timestep())
     box.sync()
+
+
+def test_fused_equals_separate_on_the_paper_shape(torch):
+    """The paper's 1024 x 378 run shape (387,072 particles), 3 steps: the fused
+    step with the 32-cell and the halo-lane RK stage equals the separate
+    launches of the same grid bitwise."""
+    wl = W.paper_1d()
+    for rk_form in (1, 0):
+        ref, _ = _steps(wl, 304, rk_form, 0, 3)
+        got, _ = _steps(wl, 304, rk_form, 1, 3)
+        for k in ("rho", "rhobar", "z"):
+            assert np.array_equal(got[k], ref[k]), (rk_form, k)
