@@ -223,7 +223,7 @@ int emu_batch_timestep(emu_box* box, double* dt_out);
 int emu_batch_set_dt(emu_box* box, const double* dt);
 
 /* nsteps classic RK4 steps of every box with its own step size (Eq. 7 values
- * unless set), all boxes advanced by the same launches.  Two step forms
+ * unless set), all boxes advanced by the same launches.  Three step forms
  * (emu_set_step_form; emu_autotune picks one):
  *   0  one launch per phase: per step one lattice-shift launch and per stage
  *      one deposit, one deposit combination and one RK-stage launch (13), with
@@ -236,9 +236,22 @@ int emu_batch_set_dt(emu_box* box, const double* dt);
  *      wait that gives up stops the launch; the next synchronising call
  *      reports EMU_ETIMEOUT, the particle state is then that of an unfinished
  *      step, and later launches run normally.
- * Both forms give bitwise the same results for the same grid.  The first call
- * captures one step as a CUDA graph (make that call outside any other stream
- * capture) and every step replays it: on the box's stream, or for a box bound
+ *   2  RK stages that deposit (Eq. 5) the state they compute at the next
+ *      stage's positions (stage 4: the next step's first stage): per step one
+ *      lattice-shift launch and per stage one deposit combination and one
+ *      RK-stage launch (9), plus one deposit of the state before the first
+ *      step of each call.  Units are 32-cell tiles x directions, tile-major; a
+ *      warp sums its deposits per tile over 36 cells (the tile and two on each
+ *      side), and the combination adds, per cell, the sums of every tile that
+ *      reaches it in a fixed order.  Shape orders 0-2 of the lattice path (1D
+ *      boxes); a call whose step sizes have dt c >= 1.9 dz in some box (a ring
+ *      could then move two cells between stages) runs form 0 instead.  Its
+ *      deposit sums in another order than forms 0 and 1: the results agree
+ *      with theirs to rounding and are bitwise reproducible for a fixed grid.
+ * Forms 0 and 1 give bitwise the same results for the same grid.  The first
+ * call captures one step as a CUDA graph (make that call outside any other
+ * stream capture; form 2 captures its first step and a later step) and every
+ * step replays it: on the box's stream, or for a box bound
  * to the legacy default stream on a blocking stream the library creates,
  * which the legacy stream orders implicitly before and after its own work.
  * With per-kernel timing on, the kernels are launched directly.  Binding,
@@ -261,18 +274,23 @@ int emu_batch_diagnostics(emu_box* box, double* out, int on_host);
  * 32 cells per warp (form 1):
  *   c = 0..5  one launch per phase, grid {304, 152, 608}[c / 2], RK form c % 2
  *   c = 6..9  one cooperative launch per step, grid {304, 152}[(c - 6) / 2],
- *             RK form c % 2.
+ *             RK form c % 2;
+ *   c = 10..12  step form 2, grid {304, 152, 608}[c - 10] (its RK stage has
+ *             32 cells per warp); -1 where form 2 does not run (3D boxes,
+ *             particles anywhere, the cubic shape, dt c >= 1.9 dz).
  * The deposit's summation order depends on the grid, so results are bitwise
- * reproducible for a fixed grid; the step forms and the RK forms give bitwise
- * the same results.  Synchronises. */
-#define EMU_AUTOTUNE_CANDIDATES 10
+ * reproducible for a fixed grid; step forms 0 and 1 and the RK forms give
+ * bitwise the same results, form 2 the same to rounding.  Synchronises. */
+#define EMU_AUTOTUNE_CANDIDATES 13
 int emu_autotune(emu_box* box, int trial_steps, int32_t* choice_out, double* ms_out);
 
 /* Step form of emu_batch_step / emu_step: 0 = one launch per phase, 1 = one
- * persistent cooperative launch per step.  Form 1 needs every block of the
- * grid resident at once (at most 2 blocks per SM: 304 on GB300) and a device
- * that supports cooperative launches.  Errors: EMU_EINVAL (bad form, grid too
- * large, step in progress). */
+ * persistent cooperative launch per step, 2 = RK stages that deposit the next
+ * stage (see emu_batch_step).  Form 1 needs every block of the grid resident
+ * at once (at most 2 blocks per SM: 304 on GB300) and a device that supports
+ * cooperative launches; form 2 the shape orders 0-2.  Forms 1 and 2 need the
+ * lattice path of a 1D box.  Errors: EMU_EINVAL (bad form, grid too large,
+ * cubic shape for form 2, step in progress). */
 int emu_set_step_form(emu_box* box, int32_t form);
 
 /* Particle layout.  The paper places one particle per direction at every cell
@@ -488,9 +506,10 @@ int64_t emu_kernel_launches(const emu_box* box);
 /* Per-launch device timing.  With enable != 0 every later kernel launch of
  * the box is bracketed by two CUDA events recorded on the box's stream.
  * emu_kernel_times synchronises the stream, writes the summed duration [ms]
- * and the number of recorded launches of each kernel class to ms_out[6] and
- * count_out[6] (0: lattice-shift table, 1: deposit, 2: RK stage, 3: deposit
- * combination, 4: other, 5: fused step), and clears the record.  Timing is a
+ * and the number of recorded launches of each kernel class to ms_out[7] and
+ * count_out[7] (0: lattice-shift table, 1: deposit, 2: RK stage, 3: deposit
+ * combination, 4: other, 5: fused step, 6: RK stage with the next deposit of
+ * step form 2), and clears the record.  Timing is a
  * measurement aid with no other effect. */
 int emu_profile(emu_box* box, int enable);
 int emu_kernel_times(emu_box* box, double* ms_out, int64_t* count_out);

@@ -15,6 +15,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <type_traits>
@@ -37,6 +38,7 @@ struct Shape {
   int nbox = 0;
   int64_t Ptot = 0, U = 0, U32 = 0;
   int NZ = 0, MT = 0, NT = 0;
+  int NT32 = 0;    // 32-cell tiles of all boxes
   int order = 2;   // shape order of every box (Sec. 2.2.1)
   int Mmax = 0;    // most directions of a box
   int T = 30;      // cells per tile for that order
@@ -98,6 +100,7 @@ const char* make_shape(const emu_config* cfgs, int nbox, Shape& S) {
     g.uoff = S.U;
     g.ntiles32 = (c->nz + kLanes - 1) / kLanes;
     g.uoff32 = S.U32;
+    g.toff32 = S.NT32;
     g.coff = (int)NZ;
     g.toff = (int)NT;
     g.doff = (int)MT;
@@ -121,6 +124,7 @@ const char* make_shape(const emu_config* cfgs, int nbox, Shape& S) {
     NZ += c->nz;
     MT += c->ndir;
     NT += g.ntiles;
+    S.NT32 += g.ntiles32;
     if (NZ > INT32_MAX / kNM || MT > INT32_MAX / 4 || S.Ptot > ((int64_t)1 << 40)) return "batch too large";
   }
   S.NZ = (int)NZ;
@@ -135,6 +139,7 @@ struct Layout {
   // particles anywhere (kernels_general.cuh): sort keys and values (two of
   // each), digit histogram, cell starts, lattice-check flag
   size_t gkeys = 0, gkeys2 = 0, gids = 0, gids2 = 0, ghist = 0, gstart = 0, gflag = 0;
+  size_t frame = 0; // step form 2: the frame sums of every 32-cell tile (k_frame_sum)
   size_t bw3 = 0;   // 3D boxes: every particle's B and axis weights at the stage positions (k3_prep)
   size_t gf3 = 0;   // 3D boxes: G = A0 - Omega . A of every (direction, cell) (k3_gfield)
 };
@@ -150,11 +155,14 @@ Layout layout(const Shape& S) {
   L.A = take(sizeof(double) * kNA * NZ);
   L.At = take(sizeof(double) * kNT * NZ);
   L.mom = take(sizeof(double) * kNM * NZ);
-  L.partial = take(sizeof(double) * (size_t)(kMaxWarps + S.NT) * kSlot);
+  // per-warp partial sums of k_deposit, or of k_rk_deposit (step form 2)
+  const size_t slots = (size_t)(kMaxWarps + S.NT) * kSlot, slots32 = (size_t)(kMaxWarps + S.NT32) * kSlotF;
+  L.partial = take(sizeof(double) * (slots > slots32 ? slots : slots32));
   L.W = take(sizeof(double) * kept_weights(S.order) * (size_t)S.Ptot);
   L.err = take(sizeof(int));
   L.dirtab = take(sizeof(double) * 4 * MT);
-  L.shift = take(sizeof(int) * 4 * MT);
+  L.shift = take(sizeof(int) * 5 * MT);    // rows: the four stages, the next step's first (step form 2)
+  L.frame = take(sizeof(double) * (size_t)S.NT32 * kSlotF);
   L.shift2 = take(sizeof(int) * 4 * MT);   // the fused step's shift rows of the next step
   L.bar = take(sizeof(unsigned) * 2);       // the fused step's grid barrier: arrival word, abort word
   L.species = take(sizeof(double) * 8 * NZ);
@@ -173,7 +181,9 @@ Layout layout(const Shape& S) {
   return L;
 }
 
-enum : int { CLS_SHIFT = 0, CLS_DEPOSIT = 1, CLS_RK = 2, CLS_COMBINE = 3, CLS_OTHER = 4, CLS_STEP = 5, N_CLS = 6 };
+enum : int {
+  CLS_SHIFT = 0, CLS_DEPOSIT = 1, CLS_RK = 2, CLS_COMBINE = 3, CLS_OTHER = 4, CLS_STEP = 5, CLS_RKDEP = 6, N_CLS = 7
+};
 
 const double kStageFrac[4] = {0.0, 0.5, 0.5, 1.0};  // position offset of RK stage s, in units of dt
 
@@ -190,12 +200,14 @@ struct emu_box {
   BoxGeo* geo_d = nullptr;
   // A: full grid potential of emu_deposit; At: the step's traceless potential
   double *dts = nullptr, *nmax = nullptr, *A = nullptr, *At = nullptr, *mom = nullptr, *partial = nullptr,
-         *W = nullptr, *dirtab = nullptr, *species = nullptr, *dirs = nullptr, *diag = nullptr, *scalar = nullptr;
+         *W = nullptr, *dirtab = nullptr, *species = nullptr, *dirs = nullptr, *diag = nullptr, *scalar = nullptr,
+         *frame = nullptr;
   int *err = nullptr, *shift = nullptr, *shift2 = nullptr;
   unsigned* bar = nullptr;
   int blocks = kPersistBlocks;  // grid of the step kernels (autotuned); its warps split the units
   int rk_form = -1;             // RK stage: 0 halo-lane, 1 32-cell, -1 by units per warp (autotuned)
-  int step_form = 0;            // 0: one launch per phase, 1: one cooperative launch per step (k_step)
+  int step_form = 0;            // 0: one launch per phase, 1: one cooperative launch per step (k_step),
+                                // 2: RK stages that deposit the next stage (k_rk_deposit)
   unsigned long long limit_ns = 1000000000ull;   // bound of each grid-barrier wait of k_step
   // 3D boxes (emu3_create): the box is S's single box (cells in 3D index order),
   // positions x, y beside the particle arrays, and one descriptor per cell row
@@ -222,6 +234,9 @@ struct emu_box {
   std::vector<cudaEvent_t> pool;
   cudaGraphExec_t graph = nullptr;   // one step of every box
   int64_t graph_launches = 0;
+  cudaGraphExec_t graph1 = nullptr;  // step form 2: the first step of a call (with the first deposit)
+  int64_t graph1_launches = 0;
+  bool graph_rd = false;             // the step graphs run step form 2
   // one adjoint step, for the buffers and step size it was captured with
   cudaGraphExec_t adj_graph = nullptr;
   int64_t adj_launches = 0;
@@ -237,6 +252,7 @@ struct emu_box {
     for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : pool) cudaEventDestroy(e);
     if (graph) cudaGraphExecDestroy(graph);
+    if (graph1) cudaGraphExecDestroy(graph1);
     if (adj_graph) cudaGraphExecDestroy(adj_graph);
     for (auto& g : rec_graphs) cudaGraphExecDestroy(g.exec);
     if (cap) cudaStreamDestroy(cap);
@@ -310,11 +326,12 @@ dim3 persist_grid(const emu_box* b) { return dim3((unsigned)b->blocks, 1, 1); }
 // over more warps, as far as needed to fill about one wave of the persistent
 // grid (304 blocks x 8 warps); short sums keep one warp (coalesced, latency
 // hidden by the other warps).
-int combine_split(const Shape& S, int64_t nw) {
-  const int64_t per_warp = nw > 0 && S.U / nw > 0 ? S.U / nw : 1;   // fewest units a warp takes
+int combine_split(const Shape& S, int64_t nw, bool frame = false) {
+  const int64_t U = frame ? S.U32 : S.U;
+  const int64_t per_warp = nw > 0 && U / nw > 0 ? U / nw : 1;       // fewest units a warp takes
   const int64_t most = (S.Mmax + per_warp - 1) / per_warp + 1;        // most warps over one tile
   if (most <= 8) return 1;
-  const int64_t out_warps = ((int64_t)kNA * S.NZ + kLanes - 1) / kLanes;
+  const int64_t out_warps = ((int64_t)(frame ? kNT : kNA) * S.NZ + kLanes - 1) / kLanes;
   int split = 1;
   while (split < kWarps && out_warps * split * 2 <= (int64_t)kPersistBlocks * kWarps && split * 8 < most)
     split <<= 1;
@@ -343,6 +360,10 @@ void invalidate_graph(emu_box* b) {
   if (b->graph) {
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
+  }
+  if (b->graph1) {
+    cudaGraphExecDestroy(b->graph1);
+    b->graph1 = nullptr;
   }
   if (b->adj_graph) {
     cudaGraphExecDestroy(b->adj_graph);
@@ -453,9 +474,25 @@ void pdl(cudaStream_t st, void (*kernel)(KArgs...), dim3 grid, Args... args) {
   (void)cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+template <typename... KArgs, typename... Args>
+void pdl_smem(cudaStream_t st, void (*kernel)(KArgs...), dim3 grid, int smem, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  (void)cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// nrows = 5: the four stages' rows and the next step's first (k_shifts).
 int launch_shifts(emu_box* b, const double* fracs, int nrows) {
   Fracs f{};
-  for (int s = 0; s < nrows; ++s) f.v[s] = fracs[s];
+  for (int s = 0; s < nrows && s < 4; ++s) f.v[s] = fracs[s];
   const int blocks = (b->S.MT + kThreads - 1) / kThreads;
   before_launch(b, CLS_SHIFT);
   pdl(b->stream, k_shifts, dim3(blocks), batch_view(b), b->pt.z, b->dirtab, f, nrows, b->shift);
@@ -637,10 +674,108 @@ int launch_rk(emu_box* b, int s, const int* srow, int dry) {
   return launch_rk_on(b, s, srow, dry, b->pt, b->W, b->At, b->pt.stage);
 }
 
-int launch_step(emu_box* b, int dry) {
+// Step form 2 (k_rk_deposit, k_combine_frame) covers 1D boxes on the lattice
+// path with shape orders 0-2 ...
+bool rd_possible(const emu_box* b) { return !b->is3d && !b->general && b->S.order <= 2; }
+
+// ... and step sizes with dt c < 1.9 dz in every box: a ring then moves at
+// most one cell between two stages (half a step).
+bool rd_step_sizes_ok(const emu_box* b) {
+  if (!b->dt_set) return false;
+  for (int i = 0; i < b->S.nbox; ++i) {
+    const BoxGeo& g = b->S.geo[i];
+    if (!(b->dt_h[i] * g.c_light < 1.9 * g.dz)) return false;
+  }
+  return true;
+}
+
+// Whether the steps run form 2: chosen, and possible for these boxes and step
+// sizes (otherwise form 0 runs, with the same results to rounding).
+bool use_rd(const emu_box* b) { return b->step_form == 2 && rd_possible(b) && rd_step_sizes_ok(b); }
+
+// Raises the dynamic shared memory limit of k_rk_deposit (its frame sums)
+// once per device; outside any stream capture.
+template <bool POT, int R, bool D>
+int rd_attr(emu_box* b) {
+  static std::atomic<unsigned> done{0};
+  int dev = 0;
+  if (int rc = cuda_check(b, cudaGetDevice(&dev), "get device")) return rc;
+  if (dev < 32 && ((done.load() >> dev) & 1u)) return EMU_OK;
+  if (int rc = cuda_check(b, cudaFuncSetAttribute(k_rk_deposit<POT, R, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  kFrameSmem), "set shared memory of the RK-deposit kernel"))
+    return rc;
+  if (dev < 32) done.fetch_or(1u << dev);
+  return EMU_OK;
+}
+
+int rd_prepare(emu_box* b) {
+  return by_order(b->S.order, [&](auto O) {
+    constexpr int R = decltype(O)::value;
+    if constexpr (R <= 2) {
+      if (int rc = rd_attr<false, R, true>(b)) return rc;
+      return b->pot ? rd_attr<true, R, false>(b) : rd_attr<false, R, false>(b);
+    }
+    return fail(b, EMU_EINVAL, "step form 2 covers the shape orders 0-2");
+  });
+}
+
+// Stage s (1..4) of form 2 with the deposit of the next stage, or (s = 0)
+// the first deposit of a run of steps.
+int launch_rd(emu_box* b, int s, int dry) {
+  before_launch(b, s == 0 ? CLS_DEPOSIT : CLS_RKDEP);
+  const Batch Bv = batch_view(b);
+  const dim3 grid = persist_grid(b);
+  by_order(b->S.order, [&](auto O) {
+    constexpr int R = decltype(O)::value;
+    if constexpr (R <= 2) {
+      if (s == 0)
+        pdl_smem(b->stream, k_rk_deposit<false, R, true>, grid, kFrameSmem, Bv, b->pt, b->W, b->dirtab, b->shift,
+                 b->frame, 0, 0, b->partial, b->err);
+      else if (b->pot)
+        pdl_smem(b->stream, k_rk_deposit<true, R, false>, grid, kFrameSmem, Bv, b->pt, b->W, b->dirtab, b->shift,
+                 b->frame, s, dry, b->partial, b->err);
+      else
+        pdl_smem(b->stream, k_rk_deposit<false, R, false>, grid, kFrameSmem, Bv, b->pt, b->W, b->dirtab, b->shift,
+                 b->frame, s, dry, b->partial, b->err);
+    }
+    return 0;
+  });
+  return after_launch(b, s == 0 ? "first deposit kernel" : "RK stage and deposit kernel");
+}
+
+// The frame sums of every tile (k_frame_sum) from k_rk_deposit's partials.
+int launch_combine_frame(emu_box* b) {
+  const Batch B = batch_view(b);
+  before_launch(b, CLS_COMBINE);
+  const int split = combine_split(b->S, B.nw32, true);
+  const int64_t n = (int64_t)b->S.NT32 * kSlotF, per_block = (int64_t)(kWarps / split) * kLanes;
+  const int64_t blocks = (n + per_block - 1) / per_block;
+  pdl(b->stream, k_frame_sum, dim3((unsigned)(blocks < 8 * kPersistBlocks ? blocks : 8 * kPersistBlocks)), B,
+      b->partial, b->frame, (int64_t)b->S.NT32, split, b->err);
+  return after_launch(b, "frame sum kernel");
+}
+
+// One step of form 2: the shift rows (with the next step's first), then four
+// (combination, RK stage with the next deposit) pairs; the first step of a
+// run deposits its state first.
+int launch_step_rd(emu_box* b, int dry, bool first) {
+  if (int rc = launch_shifts(b, kStageFrac, 5)) return rc;
+  if (first)
+    if (int rc = launch_rd(b, 0, 0)) return rc;
+  for (int s = 1; s <= 4; ++s) {
+    if (int rc = launch_combine_frame(b)) return rc;
+    if (int rc = launch_rd(b, s, dry)) return rc;
+  }
+  return EMU_OK;
+}
+
+// One step of every box (first: the first of a run of steps, which form 2
+// needs to know).
+int launch_step(emu_box* b, int dry, bool first = true) {
   if (b->is3d) return launch3_step(b, dry);
   if (b->general) return launch_gstep(b, dry);
   if (b->step_form == 1) return launch_fused(b, dry, 1);
+  if (use_rd(b)) return launch_step_rd(b, dry, first);
   if (int rc = launch_shifts(b, kStageFrac, 4)) return rc;
   for (int s = 1; s <= 4; ++s)
     if (int rc = launch_stage(b, s, dry)) return rc;
@@ -649,12 +784,30 @@ int launch_step(emu_box* b, int dry) {
 
 // nsteps steps of every box with the step sizes on the device: one step is
 // captured as a CUDA graph and replayed (kernels launched directly while
-// per-kernel timing is on).
+// per-kernel timing is on).  Form 2 replays a graph of its first step (which
+// deposits the state first) and then one of the later steps.
 int run_steps(emu_box* b, int64_t nsteps) {
   if (nsteps == 0) return EMU_OK;
+  const bool rd = use_rd(b);
+  if (rd)
+    if (int rc = rd_prepare(b)) return rc;
   if (b->prof) {
     for (int64_t n = 0; n < nsteps; ++n)
-      if (int rc = launch_step(b, 0)) return rc;
+      if (int rc = launch_step(b, 0, n == 0)) return rc;
+    return EMU_OK;
+  }
+  if (rd != b->graph_rd) {   // the step sizes moved the steps into or out of form 2
+    invalidate_graph(b);
+    b->graph_rd = rd;
+  }
+  if (rd) {
+    if (!b->graph1)
+      if (int rc = capture(b, &b->graph1, &b->graph1_launches, [&] { return launch_step(b, 0, true); })) return rc;
+    if (int rc = launch_graph(b, b->graph1, b->graph1_launches)) return rc;
+    if (nsteps > 1 && !b->graph)
+      if (int rc = capture(b, &b->graph, &b->graph_launches, [&] { return launch_step(b, 0, false); })) return rc;
+    for (int64_t n = 1; n < nsteps; ++n)
+      if (int rc = launch_graph(b, b->graph, b->graph_launches)) return rc;
     return EMU_OK;
   }
   if (!b->graph)
@@ -704,6 +857,7 @@ int read_errors(emu_box* b) {
                 "is that of an unfinished step", b->limit_ns);
   }
   if (h & ERR_WEIGHT) return fail(b, EMU_EINVAL, "negative particle weight: a flux factor exceeds 1/3");
+  if (h & ERR_STEP) return fail(b, EMU_EINVAL, "a ring moved more than one cell between two stages of step form 2");
   if (h & ERR_RING) return fail(b, EMU_ELATTICE, "a ring of particles does not share one direction");
   if (h & ERR_LATTICE) return fail(b, EMU_ELATTICE, "a particle is off its lattice site");
   if (h & ERR_NONFINITE) return fail(b, EMU_ENUMERIC, "non-finite value on the grid");
@@ -1251,6 +1405,7 @@ int bind_common(emu_box* b, const emu_particles* parts, void* workspace, int64_t
   b->mom = (double*)(b->ws + L.mom);
   b->partial = (double*)(b->ws + L.partial);
   b->W = (double*)(b->ws + L.W);
+  b->frame = (double*)(b->ws + L.frame);
   b->err = (int*)(b->ws + L.err);
   b->dirtab = (double*)(b->ws + L.dirtab);
   b->shift = (int*)(b->ws + L.shift);
@@ -1510,8 +1665,17 @@ int emu_autotune(emu_box* b, int trial_steps, int32_t* choice_out, double* ms_ou
   // candidate c: step form, grid and RK form (see emu.h)
   const int grids[EMU_AUTOTUNE_CANDIDATES] = {kPersistBlocks, kPersistBlocks, kPersistBlocks / 2, kPersistBlocks / 2,
                                               kMaxBlocks, kMaxBlocks, kPersistBlocks, kPersistBlocks,
-                                              kPersistBlocks / 2, kPersistBlocks / 2};
+                                              kPersistBlocks / 2, kPersistBlocks / 2, kPersistBlocks,
+                                              kPersistBlocks / 2, kMaxBlocks};
+  auto apply = [&](int c) {
+    b->blocks = grids[c];
+    b->rk_form = c < 10 ? c % 2 : -1;
+    b->step_form = c >= 10 ? 2 : c >= 6 ? 1 : 0;
+  };
   const int maxb = fused_max_blocks(b);
+  const bool rd_ok = rd_possible(b) && rd_step_sizes_ok(b);
+  if (rd_ok)
+    if (int rc = rd_prepare(b)) return rc;
   const bool prof = b->prof;
   b->prof = false;
   cudaEvent_t e0 = take_event(b), e1 = take_event(b);
@@ -1519,17 +1683,16 @@ int emu_autotune(emu_box* b, int trial_steps, int32_t* choice_out, double* ms_ou
   float best_ms = 0.f;
   int rc = EMU_OK;
   for (int c = 0; c < EMU_AUTOTUNE_CANDIDATES && rc == EMU_OK; ++c) {
-    b->blocks = grids[c];
-    b->rk_form = c % 2;
-    b->step_form = c >= 6 ? 1 : 0;
-    if (b->step_form == 1 && (b->is3d || b->general || b->blocks > maxb)) {   // not a candidate here
+    apply(c);
+    if ((b->step_form == 1 && (b->is3d || b->general || b->blocks > maxb)) ||
+        (b->step_form == 2 && !rd_ok)) {   // not a candidate here
       if (ms_out) ms_out[c] = -1.0;
       continue;
     }
-    rc = launch_step(b, 1);  // warm-up (dry: the particle state is left as it was)
+    rc = launch_step(b, 1, true);  // warm-up (dry: the particle state is left as it was)
     if (rc) break;
     cudaEventRecord(e0, b->stream);
-    for (int n = 0; n < trial_steps && rc == EMU_OK; ++n) rc = launch_step(b, 1);
+    for (int n = 0; n < trial_steps && rc == EMU_OK; ++n) rc = launch_step(b, 1, false);
     cudaEventRecord(e1, b->stream);
     if (rc) break;
     rc = cuda_check(b, cudaEventSynchronize(e1), "autotune timing");
@@ -1542,9 +1705,7 @@ int emu_autotune(emu_box* b, int trial_steps, int32_t* choice_out, double* ms_ou
   b->pool.push_back(e0);
   b->pool.push_back(e1);
   b->prof = prof;
-  b->blocks = grids[best];
-  b->rk_form = best % 2;
-  b->step_form = best >= 6 ? 1 : 0;
+  apply(best);
   invalidate_graph(b);
   if (rc) return rc;
   if (choice_out) *choice_out = best;
@@ -1553,9 +1714,10 @@ int emu_autotune(emu_box* b, int trial_steps, int32_t* choice_out, double* ms_ou
 
 int emu_set_step_form(emu_box* b, int32_t form) {
   if (int rc = check_bound(b)) return rc;
-  if (form < 0 || form > 1) return fail(b, EMU_EINVAL, "form must be 0 or 1");
-  if (form == 1 && b->is3d) return no_3d(b, "the fused step form");
-  if (form == 1 && b->general) return needs_lattice(b, "the fused step form");
+  if (form < 0 || form > 2) return fail(b, EMU_EINVAL, "form must be 0, 1 or 2");
+  if (form >= 1 && b->is3d) return no_3d(b, form == 1 ? "the fused step form" : "step form 2");
+  if (form >= 1 && b->general) return needs_lattice(b, form == 1 ? "the fused step form" : "step form 2");
+  if (form == 2 && b->S.order > 2) return fail(b, EMU_EINVAL, "step form 2 covers the shape orders 0-2");
   if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
   if (form == 1) {
     const int maxb = fused_max_blocks(b);

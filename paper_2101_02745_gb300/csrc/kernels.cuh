@@ -57,7 +57,7 @@ constexpr int kPersistBlocks = 2 * 152;  // default grid: 2 resident blocks on e
 constexpr int kMaxBlocks = 4 * 152;      // largest grid the autotuner tries
 constexpr int kMaxWarps = kMaxBlocks * kWarps;
 
-enum : int { ERR_LATTICE = 1, ERR_NONFINITE = 2, ERR_WEIGHT = 4, ERR_RING = 8 };
+enum : int { ERR_LATTICE = 1, ERR_NONFINITE = 2, ERR_WEIGHT = 4, ERR_RING = 8, ERR_STEP = 32 };
 
 // Stencil of the shape of order ORDER (Sec. 2.2.1, orders 0-3): a particle on
 // lattice site h (the cell containing it) reaches cells h-H .. h+H, weight
@@ -77,6 +77,7 @@ struct Sten {
 struct BoxGeo {
   int nz, M, ntiles, use_dirs;
   int coff, toff, doff, ntiles32;  // ntiles32: 32-cell tiles of the RK stage
+  int toff32, reserved_;           // toff32: first 32-cell tile of the box among all boxes'
   int64_t P, poff, uoff, uoff32;   // uoff32: first 32-cell unit of the box
   double Lz, dz, inv_dz, nz_d, dV, c_light;
   double kappa_dV;   // kappa / dV: scale of the grid potential
@@ -413,6 +414,9 @@ __global__ void k_dirtable(Batch B, Parts pt, double* __restrict__ dirtab, int* 
 
 // Lattice shift of every direction for up to 4 position offsets frac[s] * dt_b:
 // the cell of the ring's first particle at z + frac[s] dt_b v_z ([nrows][MT]).
+// A fifth row (nrows = 5) holds the shift of the next step's first stage: the
+// cell of wrap(z + dt_b v_z), the position stage 4 writes, computed exactly as
+// the RK stage computes it.
 struct Fracs { double v[4]; };
 
 // Position offset of RK stage s (0-based), in units of dt (Sec. 2.3, classic tableau).
@@ -435,6 +439,7 @@ __device__ __forceinline__ void shifts_phase(const Batch& B, int gd, const doubl
 #pragma unroll
   for (int s = 0; s < 4; ++s)
     if (s < nrows) shift[s * B.MT + gd] = lattice_cell(z0, fr.v[s] * dt, vz, g);
+  if (nrows > 4) shift[4 * B.MT + gd] = lattice_cell(wrap_z(fma(dt, vz, z0), g.Lz), 0.0, vz, g);
 }
 
 __global__ void k_shifts(Batch B, const double* __restrict__ z, const double* __restrict__ dirtab, Fracs fr,
@@ -710,12 +715,16 @@ k_interpolate(Batch B, const double* __restrict__ z, const double* __restrict__ 
 // the new state and position).  vz points at the particle's v_z in the
 // direction table.  With shift_next (fused step), the first particle of each
 // ring also writes the lattice shifts of the next step's four stages
-// ([4][MTtot], as k_shifts computes them from its new position).
-template <bool POT, bool COH>
+// ([4][MTtot], as k_shifts computes them from its new position).  With KEEP
+// the state it stores (the next stage's, or at stage 4 the new one), rho and
+// rhobar, is also combined as B = n1 rho - n2 rhobar^* into keep[9] (the
+// arithmetic of the deposit, Eq. 5) and the new position returned in *zkeep.
+template <bool POT, bool COH, bool KEEP = false>
 __device__ __forceinline__ void rk_particle(const BoxGeo& g, const Parts& pt, const double* src_b, int64_t P,
                                             int64_t p, int s, int dry, double bdt, double cdt, double dtb,
                                             const double* __restrict__ vz, double (&Hm)[kNC], const double (&r)[9],
-                                            int* shift_next, int gd, int MTtot) {
+                                            int* shift_next, int gd, int MTtot, double* keep = nullptr,
+                                            double* zkeep = nullptr, double n1 = 0.0, double n2 = 0.0) {
   const double bdt2 = 2.0 * bdt, cdt2 = 2.0 * cdt;   // diagonal K are returned halved
   // Hm: H in the traceless components.  Antineutrinos: Hbar = -H^* (diagonal
   // differences and real parts flip sign, imaginary parts stay)
@@ -755,28 +764,71 @@ __device__ __forceinline__ void rk_particle(const BoxGeo& g, const Parts& pt, co
     if (which == 0) commutator(d12, d13, d23, Hm[2], Hm[3], Hm[4], Hm[5], Hm[6], Hm[7], rr, kd, ko);
     else if (POT) commutator(Hb[0], Hb[0] + Hb[1], Hb[1], Hb[2], Hb[3], Hb[4], Hb[5], Hb[6], Hb[7], rr, kd, ko);
     else commutator(-d12, -d13, -d23, -Hm[2], Hm[3], -Hm[4], Hm[5], -Hm[6], Hm[7], rr, kd, ko);
-    if (s == 1) {
+    if constexpr (!KEEP) {
+      if (s == 1) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) { av[k * P + p] = fma(bdt2, kd[k], rr[k]); sv[k * P + p] = fma(cdt2, kd[k], rr[k]); }
+        for (int k = 0; k < 3; ++k) {
+          av[k * P + p] = fma(bdt2, kd[k], rr[k]);
+          sv[k * P + p] = fma(cdt2, kd[k], rr[k]);
+        }
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        av[(k + 3) * P + p] = fma(bdt, ko[k], rr[k + 3]);
-        sv[(k + 3) * P + p] = fma(cdt, ko[k], rr[k + 3]);
-      }
-    } else if (s < 4) {
+        for (int k = 0; k < 6; ++k) {
+          av[(k + 3) * P + p] = fma(bdt, ko[k], rr[k + 3]);
+          sv[(k + 3) * P + p] = fma(cdt, ko[k], rr[k + 3]);
+        }
+      } else if (s < 4) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) { av[k * P + p] = fma(bdt2, kd[k], a[k]); sv[k * P + p] = fma(cdt2, kd[k], y[k]); }
+        for (int k = 0; k < 3; ++k) {
+          av[k * P + p] = fma(bdt2, kd[k], a[k]);
+          sv[k * P + p] = fma(cdt2, kd[k], y[k]);
+        }
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        av[(k + 3) * P + p] = fma(bdt, ko[k], a[k + 3]);
-        sv[(k + 3) * P + p] = fma(cdt, ko[k], y[k + 3]);
+        for (int k = 0; k < 6; ++k) {
+          av[(k + 3) * P + p] = fma(bdt, ko[k], a[k + 3]);
+          sv[(k + 3) * P + p] = fma(cdt, ko[k], y[k + 3]);
+        }
+      } else {
+        double* __restrict__ dst = dry ? sv : yv;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dst[k * P + p] = fma(bdt2, kd[k], a[k]);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) dst[(k + 3) * P + p] = fma(bdt, ko[k], a[k + 3]);
       }
     } else {
-      double* __restrict__ dst = dry ? sv : yv;
+      double nv[9];   // the state stored as the next stage's (stage 4: the new state)
+      if (s == 1) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) dst[k * P + p] = fma(bdt2, kd[k], a[k]);
+        for (int k = 0; k < 3; ++k) { av[k * P + p] = fma(bdt2, kd[k], rr[k]); nv[k] = fma(cdt2, kd[k], rr[k]); }
 #pragma unroll
-      for (int k = 0; k < 6; ++k) dst[(k + 3) * P + p] = fma(bdt, ko[k], a[k + 3]);
+        for (int k = 0; k < 6; ++k) {
+          av[(k + 3) * P + p] = fma(bdt, ko[k], rr[k + 3]);
+          nv[k + 3] = fma(cdt, ko[k], rr[k + 3]);
+        }
+      } else if (s < 4) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { av[k * P + p] = fma(bdt2, kd[k], a[k]); nv[k] = fma(cdt2, kd[k], y[k]); }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          av[(k + 3) * P + p] = fma(bdt, ko[k], a[k + 3]);
+          nv[k + 3] = fma(cdt, ko[k], y[k + 3]);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) nv[k] = fma(bdt2, kd[k], a[k]);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) nv[k + 3] = fma(bdt, ko[k], a[k + 3]);
+      }
+      double* __restrict__ dst = (s < 4 || dry) ? sv : yv;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) dst[k * P + p] = nv[k];
+      // B = n1 rho - n2 rhobar^*: conj(rhobar) flips the sign of the imaginary components 4, 6, 8
+      if (which == 0) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) keep[k] = n1 * nv[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) keep[k] = fma((k == 4 || k == 6 || k == 8) ? n2 : -n2, nv[k], keep[k]);
+      }
     }
   }
   if (s == 4) {
@@ -784,6 +836,7 @@ __device__ __forceinline__ void rk_particle(const BoxGeo& g, const Parts& pt, co
     const double zn = wrap_z(fma(dtb, vzv, ldp<COH>(pt.z + p)), g.Lz);
     if (dry) pt.stage[p] = zn;  // (only to keep the work of the real stage)
     else pt.z[p] = zn;
+    if constexpr (KEEP) *zkeep = zn;
     if (shift_next != nullptr && p == g.poff + (int64_t)(gd - g.doff) * g.nz) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) shift_next[q * MTtot + gd] = lattice_cell(zn, stage_frac(q) * dtb, vzv, g);
@@ -1088,6 +1141,419 @@ k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __re
              const int* __restrict__ shift, const double* __restrict__ A, const double* stage_src, int s, int dry) {
   griddep_wait();
   rk32_phase<POT, ORDER, false>(B, logical_warp(), pt, W, dirtab, shift, A, stage_src, s, dry, nullptr);
+}
+
+// ------------------------------------------- RK stage with the next deposit
+//
+// Step form 2: every RK stage also deposits (Eq. 5) the state it has just
+// computed, at the positions of the next stage (at stage 4: the first stage of
+// the next step), so a step is four (combination, RK stage) launch pairs and
+// the separate deposit kernel with its re-read of the state is gone.  Units
+// are (32-cell tile, direction), TILE-major: a warp walks directions of one
+// tile and sums their deposits in shared memory.  Lane l holds the particle on
+// cell tile * 32 + l at the stage's positions; every lane owns its particle
+// (the G values left of lane 0 and right of the last lane are formed by 16
+// lanes, one component each).  Between two stages a ring moves rigidly by
+// delta cells, |delta| <= 1 when dt c < 2 dz (the host runs this form only
+// then), so the particles of one unit deposit onto cells
+// tile * 32 + delta - 1 .. tile * 32 + n + delta: a warp's sums for one tile
+// cover the frame of kFrame cells tile * 32 - 2 .. tile * 32 + 33 and go to
+// slot (warp + global 32-cell tile) of the partial buffer (unique, as for
+// k_deposit).  k_frame_sum adds the slots of each tile in warp order (the
+// tile's frame sums), and the next RK stage adds, for each cell, the frame
+// entries of the tiles that reach it in a fixed order: bitwise reproducible
+// for a fixed grid.  For the shapes of one cell of reach (orders 0-2).
+constexpr int kFrame = kLanes + 4;
+constexpr int kSlotF = kNT * kFrame;   // doubles in one warp's frame sums for one tile
+constexpr int kFrameSmem = (int)sizeof(double) * kWarps * kSlotF;   // dynamic shared memory of k_rk_deposit
+
+__device__ __forceinline__ int64_t warp_of_unit32(int64_t x, const Batch& B) {
+  return ((x + 1) * B.nw32 - 1) / B.U32;
+}
+
+// Writes a warp's frame sums to its slot and clears them.
+__device__ __forceinline__ void flush_frame(double* acc, double* __restrict__ dst, int lane) {
+  __syncwarp();
+  for (int k = lane; k < kSlotF; k += kLanes) {
+    dst[k] = acc[k];
+    acc[k] = 0.0;
+  }
+  __syncwarp();
+}
+
+// The frame entries that add up to the potential at cell x of box g: Fr
+// offsets of component row 0 in o[0..4] (-1: none).  A tile's frame covers
+// cell tile * 32 - 2 + k for k < (its cells) + 4, modulo nz.  When the box has
+// at least three tiles and its last tile at least two cells, only the tile of
+// x (entry x - tile * 32 + 2) and, for the two cells at either end of a tile,
+// the adjacent tile reach x.  Otherwise (rings of few tiles) the tiles of
+// cells x - 2 .. x + 2 are taken in that order, once each, with every entry
+// of theirs that covers x.
+__device__ __forceinline__ bool frame_fast(const BoxGeo& g) {
+  return g.ntiles32 >= 3 && g.nz - (g.ntiles32 - 1) * kLanes >= 2;
+}
+__device__ __forceinline__ void frame_sources(const BoxGeo& g, int x, int (&o)[5]) {
+  const int nz = g.nz, nt = g.ntiles32;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) o[q] = -1;
+  if (frame_fast(g)) {
+    const int t = x / kLanes, i = x - t * kLanes, n = min(kLanes, nz - t * kLanes);
+    o[0] = (g.toff32 + t) * kSlotF + i + 2;
+    if (i < 2) {
+      const int tl = t == 0 ? nt - 1 : t - 1;
+      o[1] = (g.toff32 + tl) * kSlotF + min(kLanes, nz - tl * kLanes) + 2 + i;
+    }
+    if (i >= n - 2) {
+      const int tr = t == nt - 1 ? 0 : t + 1;
+      o[2] = (g.toff32 + tr) * kSlotF + i - n + 2;
+    }
+    return;
+  }
+  int cnt = 0;
+  int prev[4] = {-1, -1, -1, -1};
+#pragma unroll
+  for (int d = -2; d <= 2; ++d) {
+    const int tau = wrapc(x + d, nz) / kLanes;
+    bool seen = false;
+#pragma unroll
+    for (int q = 0; q < d + 2; ++q) seen |= prev[q] == tau;
+    if (d < 2) prev[d + 2] = tau;
+    if (seen) continue;
+    const int ntau = min(kLanes, nz - tau * kLanes);
+    const int base = (g.toff32 + tau) * kSlotF;
+    for (int k = wrapc(x - tau * kLanes + 2, nz); k < ntau + 4; k += nz) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q)
+        if (q == cnt) o[q] = base + k;
+      ++cnt;
+    }
+  }
+}
+
+// Value of component row r of the potential from its frame entries.
+__device__ __forceinline__ double frame_value(const double* __restrict__ Fr, const int (&o)[5], int r) {
+  double v = __ldg(Fr + o[0] + r * kFrame);
+#pragma unroll
+  for (int q = 1; q < 5; ++q)
+    if (o[q] >= 0) v += __ldg(Fr + o[q] + r * kFrame);
+  return v;
+}
+
+// Stage s (1..4) of every box: the RK4 update of k_rk_stage32 (same
+// arithmetic; the potential of a cell is the sum of the frame entries of
+// k_frame_sum that cover it, Fr), then the
+// deposit of its result at the next stage's positions: the shape weights
+// (kept in W for the next stage), B = N rho - Nbar rhobar^* in the traceless
+// components (Eq. 5, Eq. 2) and w (1, Omega) B summed per frame cell.
+// DEP_ONLY: no RK update; the deposit of the state in rho, rhobar at the first
+// stage's positions (the first launch of a run of steps).  Shift rows: this
+// stage's s - 1, the deposit's s (row 4: the next step's first stage).
+template <bool POT, int ORDER, bool DEP_ONLY>
+__global__ void __launch_bounds__(kThreads, 2)
+k_rk_deposit(Batch B, Parts pt, double* __restrict__ W, const double* __restrict__ dirtab,
+             const int* __restrict__ shift, const double* __restrict__ Fr, int s, int dry,
+             double* __restrict__ partial, int* __restrict__ err) {
+  static_assert(Sten<ORDER>::H == 1, "the frame covers the shapes of one cell of reach");
+  constexpr int NW = Sten<ORDER>::NW, NWS = Sten<ORDER>::NWS;
+  extern __shared__ double frame_sm[];
+  __shared__ double gsm[kWarps][kNC][kLanes];   // G of the unit's cells
+  __shared__ double gedge[kWarps][2 * kNC];      // G left of lane 0, right of lane n - 1
+  griddep_wait();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  double* acc = frame_sm + wib * kSlotF;
+  const int64_t w = logical_warp();
+  const int64_t u0 = unit32_begin(w, B), u1 = unit32_begin(w + 1, B);
+  if (u0 >= u1) return;
+  for (int k = lane; k < kSlotF; k += kLanes) acc[k] = 0.0;
+  __syncwarp();
+  const int64_t P = B.Ptot;
+  const int MT = B.MT;
+  const bool first = DEP_ONLY || s == 1;
+  const double* src_r = first ? pt.rho : pt.stage;
+  const double* src_b = first ? pt.rhobar : pt.stage + 9 * P;
+  const int* sh_cur = shift + (DEP_ONLY ? 0 : s - 1) * MT;
+  const int* sh_next = shift + (DEP_ONLY ? 0 : s) * MT;
+  // arrays read per particle, for the L2 prefetch of the next unit: the state
+  // (18), y (18, s = 2, 3), acc (18, s >= 2), W (NWS), z, N, Nbar
+  const int ny = (!DEP_ONLY && (s == 2 || s == 3)) ? 18 : 0, nacc = (!DEP_ONLY && s >= 2) ? 18 : 0;
+  const int nw_ = DEP_ONLY ? 0 : NWS;
+  const int narr = 18 + ny + nacc + nw_ + 3;
+  int lat = 0, far = 0;
+  int b = box_of_unit32(B, u0);
+  int bcur = -1;
+  double dtb = 0.0, bdt = 0.0, cdt = 0.0;
+  int64_t stile = -1;   // global tile whose sums acc holds
+  for (int64_t u = u0; u < u1; ++u) {
+    while (u >= B.box[b].uoff32 + (int64_t)B.box[b].ntiles32 * B.box[b].M) ++b;
+    const BoxGeo& g = B.box[b];
+    const int nz = g.nz, M = g.M;
+    const int lu = (int)(u - g.uoff32);
+    const int tile = lu / M, d = lu - tile * M;
+    const int64_t gtile = g.toff32 + tile;
+    if (gtile != stile) {
+      if (stile >= 0) flush_frame(acc, partial + (w + stile) * kSlotF, lane);
+      stile = gtile;
+    }
+    if (b != bcur) {
+      bcur = b;
+      dtb = B.dt[b];
+      bdt = (s == 1 || s == 4) ? dtb / 6.0 : dtb / 3.0;   // weight of K in acc
+      cdt = (s == 3) ? dtb : 0.5 * dtb;                   // offset of the next stage
+    }
+    if (u + 1 < u1 && lu + 1 < g.ntiles32 * M) {   // prefetch the next unit of the same box
+      const int tn = (lu + 1) / M, dn = lu + 1 - tn * M;
+      const int i0 = tn * kLanes - __ldg(sh_cur + g.doff + dn);
+      const int cnt = min(kLanes, nz - tn * kLanes);
+      if (i0 >= 0 && i0 + cnt <= nz) {
+        const int64_t base = g.poff + (int64_t)dn * nz + i0;
+        for (int a = lane; a < narr; a += kLanes) {
+          const double* arr;
+          if (a < 18) arr = a < 9 ? src_r + (int64_t)a * P : src_b + (int64_t)(a - 9) * P;
+          else if (a < 18 + ny) arr = a - 18 < 9 ? pt.rho + (int64_t)(a - 18) * P : pt.rhobar + (int64_t)(a - 27) * P;
+          else if (a < 18 + ny + nacc) arr = pt.acc + (int64_t)(a - 18 - ny) * P;
+          else if (a < 18 + ny + nacc + nw_) arr = W + (int64_t)(a - 18 - ny - nacc) * P;
+          else {
+            const int k = a - 18 - ny - nacc - nw_;
+            arr = k == 0 ? pt.z : k == 1 ? pt.N : pt.Nbar;
+          }
+          prefetch_l2(arr, base, cnt);
+        }
+      }
+    }
+    const int n = min(kLanes, nz - tile * kLanes);
+    const bool active = lane < n;
+    const int j = tile * kLanes + lane;   // this lane's cell at the stage's positions
+    const int gd = g.doff + d;
+    const double ox = __ldg(dirtab + gd), oy = __ldg(dirtab + MT + gd), oz = __ldg(dirtab + 2 * MT + gd);
+    const double vz = __ldg(dirtab + 3 * MT + gd);
+    const int sc = __ldg(sh_cur + gd);
+    const int64_t p = g.poff + (int64_t)d * nz + wrapc(j - sc, nz);
+    double bm[9];       // B = N rho - Nbar rhobar^* of the state deposited (Eq. 5)
+    double zs = 0.0;    // and its position
+    double n1 = 0.0, n2 = 0.0;
+    if (active) {
+      n1 = __ldg(pt.N + p);
+      n2 = __ldg(pt.Nbar + p);
+    }
+    if constexpr (DEP_ONLY) {
+      if (active) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          const double x = __ldg(src_r + k * P + p), y = __ldg(src_b + k * P + p);
+          bm[k] = (k == 4 || k == 6 || k == 8) ? fma(n2, y, n1 * x) : fma(-n2, y, n1 * x);
+        }
+        zs = __ldg(pt.z + p);
+      }
+    } else {
+      // G = A0 - Omega . A of this lane's cell into shared memory
+      if (frame_fast(g)) {
+        // its tile's frame entry lane + 2, then (one value per lane) the
+        // adjacent tiles' entries for the two cells at each end of the tile:
+        // lanes 0-15 cells 0, 1 from the tile before, lanes 16-31 cells
+        // n - 2, n - 1 from the tile after, added in that order
+        const double* f0 = Fr + (int64_t)(g.toff32 + tile) * kSlotF + lane + 2;
+#pragma unroll
+        for (int c = 0; c < kNC; ++c)
+          gsm[wib][c][lane] = fma(-oz, __ldg(f0 + (3 * kNC + c) * kFrame),
+                                  fma(-oy, __ldg(f0 + (2 * kNC + c) * kFrame),
+                                      fma(-ox, __ldg(f0 + (kNC + c) * kFrame), __ldg(f0 + c * kFrame))));
+        const int nt = g.ntiles32, c = lane & (kNC - 1), right = lane >> 4;
+        const int ce = right ? n - 2 + ((lane >> 3) & 1) : (lane >> 3) & 1;
+        const int tn = right ? (tile == nt - 1 ? 0 : tile + 1) : (tile == 0 ? nt - 1 : tile - 1);
+        const int k = right ? ce - n + 2 : min(kLanes, nz - tn * kLanes) + 2 + ce;
+        const double* f1 = Fr + (int64_t)(g.toff32 + tn) * kSlotF + k;
+        const double gc = fma(-oz, __ldg(f1 + (3 * kNC + c) * kFrame),
+                              fma(-oy, __ldg(f1 + (2 * kNC + c) * kFrame),
+                                  fma(-ox, __ldg(f1 + (kNC + c) * kFrame), __ldg(f1 + c * kFrame))));
+        __syncwarp();
+        if (!right) gsm[wib][c][ce] += gc;
+        __syncwarp();
+        if (right) gsm[wib][c][ce] += gc;
+      } else {
+        int off[5];
+        frame_sources(g, active ? j : wrapc(j, nz), off);
+#pragma unroll
+        for (int c = 0; c < kNC; ++c)
+          gsm[wib][c][lane] = fma(-oz, frame_value(Fr, off, 3 * kNC + c),
+                                  fma(-oy, frame_value(Fr, off, 2 * kNC + c),
+                                      fma(-ox, frame_value(Fr, off, kNC + c), frame_value(Fr, off, c))));
+      }
+      // lanes 0-15 (component lane mod 8): G of the cell left of lane 0
+      // (lanes 0-7) and right of lane n - 1 (lanes 8-15)
+      if (ORDER > 0 && lane < 2 * kNC) {
+        const int c = lane & (kNC - 1);
+        const int right = tile * kLanes + n;
+        const int cell = lane < kNC ? (tile == 0 ? nz - 1 : tile * kLanes - 1) : (right == nz ? 0 : right);
+        int off[5];
+        frame_sources(g, cell, off);
+        gedge[wib][lane] = fma(-oz, frame_value(Fr, off, 3 * kNC + c),
+                               fma(-oy, frame_value(Fr, off, 2 * kNC + c),
+                                   fma(-ox, frame_value(Fr, off, kNC + c), frame_value(Fr, off, c))));
+      }
+      __syncwarp();
+      if (active) {
+        double wt[NW];
+        double r[9];
+        load_weights<ORDER>(W, P, p, wt);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) r[k] = src_r[k * P + p];
+        double Hm[kNC];
+#pragma unroll
+        for (int c = 0; c < kNC; ++c) {
+          if constexpr (ORDER == 0) {
+            Hm[c] = gsm[wib][c][lane];
+          } else {
+            const double gl = lane == 0 ? gedge[wib][c] : gsm[wib][c][lane - 1];
+            const double gr = lane == n - 1 ? gedge[wib][kNC + c] : gsm[wib][c][lane + 1];
+            Hm[c] = fma(wt[0], gl, fma(wt[1], gsm[wib][c][lane], wt[2] * gr));
+          }
+        }
+        double zn = 0.0;
+        rk_particle<POT, false, true>(g, pt, src_b, P, p, s, dry, bdt, cdt, dtb, dirtab + 3 * MT + gd, Hm, r,
+                                      nullptr, gd, MT, bm, &zn, n1, n2);
+        zs = s < 4 ? fma(stage_frac(s) * dtb, vz, pt.z[p]) : zn;
+      }
+      __syncwarp();   // (gsm is rewritten by the next unit)
+    }
+    // the ring's move to the next stage's positions
+    int delta = 0;
+    if constexpr (!DEP_ONLY) {
+      delta = wrapc(__ldg(sh_next + gd) - sc, nz);
+      if (2 * delta > nz) delta -= nz;
+      if (delta < -1 || delta > 1) {   // (excluded by the host; the unit's deposit is skipped)
+        far = 1;
+        continue;
+      }
+    }
+    double wn[NW];
+    zero_weights<ORDER>(wn);
+    double bv[kNC];
+#pragma unroll
+    for (int c = 0; c < kNC; ++c) bv[c] = 0.0;
+    if (active) {
+      lat |= shape_weights<ORDER>(zs, (double)wrapc(j + delta, nz) + 0.5, g.inv_dz, g.nz_d, wn);
+#pragma unroll
+      for (int q = 0; q < NWS; ++q) W[q * P + p] = wn[q];
+      bv[0] = bm[0] - bm[1];   // the traceless components
+      bv[1] = bm[1] - bm[2];
+#pragma unroll
+      for (int k = 3; k < 9; ++k) bv[k - 1] = bm[k];
+    }
+    // this lane's cell tile * 32 + lane + delta receives from the particles on
+    // lanes lane - 1, lane, lane + 1 of this unit
+    const double wup = __shfl_up_sync(kFull, wn[2], 1), wdn = __shfl_down_sync(kFull, wn[0], 1);
+    const double fl = lane == 0 ? 0.0 : wup;
+    const double fr = lane == kLanes - 1 ? 0.0 : wdn;
+    double* a = acc + lane + delta + 2;
+#pragma unroll
+    for (int c = 0; c < kNC; ++c) {
+      const double v = bv[c];
+      double cc;
+      if constexpr (ORDER == 0) {
+        cc = wn[1] * v;
+      } else {
+        const double vl = __shfl_up_sync(kFull, v, 1), vr = __shfl_down_sync(kFull, v, 1);
+        cc = fma(fr, vr, fma(wn[1], v, fl * vl));
+      }
+      if (active) {
+        a[c * kFrame] += cc;
+        a[(kNC + c) * kFrame] = fma(ox, cc, a[(kNC + c) * kFrame]);
+        a[(2 * kNC + c) * kFrame] = fma(oy, cc, a[(2 * kNC + c) * kFrame]);
+        a[(3 * kNC + c) * kFrame] = fma(oz, cc, a[(3 * kNC + c) * kFrame]);
+      }
+    }
+    if constexpr (ORDER > 0) {
+      // the cells left of lane 0's and right of lane n - 1's: only those two
+      // particles' outer weights; lane f * 8 + c adds component c of moment f
+      // (1, Omega_x, Omega_y, Omega_z) of both
+      __syncwarp();
+      const int c = lane & (kNC - 1), f = lane >> 3;
+      double bl = 0.0, br = 0.0;
+#pragma unroll
+      for (int k = 0; k < kNC; ++k) {
+        const double x0 = __shfl_sync(kFull, bv[k], 0), x1 = __shfl_sync(kFull, bv[k], n - 1);
+        if (k == c) {
+          bl = x0;
+          br = x1;
+        }
+      }
+      const double wl = __shfl_sync(kFull, wn[0], 0), wr = __shfl_sync(kFull, wn[2], n - 1);
+      const double of = f == 0 ? 1.0 : f == 1 ? ox : f == 2 ? oy : oz;
+      double* row = acc + lane * kFrame;
+      row[delta + 1] = fma(of, wl * bl, row[delta + 1]);
+      row[n + delta + 2] = fma(of, wr * br, row[n + delta + 2]);
+    }
+    __syncwarp();
+  }
+  flush_frame(acc, partial + (w + stile) * kSlotF, lane);
+  if (lat) atomicOr(err, ERR_LATTICE);
+  if (far) atomicOr(err, ERR_STEP);
+}
+
+__device__ __forceinline__ int box_of_tile32(const Batch& B, int64_t t) {
+  int lo = 0, hi = B.nbox - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (B.box[mid].toff32 <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Deposit combination of step form 2: the frame sums of every 32-cell tile,
+// Fr[gtile * kSlotF + e] = kappa_b / dV_b x (sum over the warps that own
+// units of the tile of their slot's entry e), in warp order.  A group of 32
+// lanes takes 32 consecutive entries of one tile (kSlotF = 36 x 32), so every
+// lane of a warp walks the same warps.  Split over warps and running sums as
+// in combine_phase.  The potential at a cell is the sum of the frame entries
+// that cover it (frame_sources).
+__global__ void k_frame_sum(Batch B, const double* __restrict__ partial, double* __restrict__ Fr, int64_t NT32,
+                            int split, int* __restrict__ err) {
+  __shared__ double sums[kWarps][kLanes];
+  griddep_wait();
+  const int64_t n = NT32 * kSlotF;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int grp = wib / split, wi = wib - grp * split;
+  const int groups = kWarps / split;
+  int bad = 0;
+  for (int64_t base = (int64_t)blockIdx.x * groups * kLanes; base < n; base += (int64_t)gridDim.x * groups * kLanes) {
+    const int64_t e0 = base + (int64_t)grp * kLanes;   // first entry of this group (one tile)
+    double v = 0.0;
+    const BoxGeo* g = nullptr;
+    if (e0 < n) {
+      const int64_t gtile = e0 / kSlotF;
+      g = &B.box[box_of_tile32(B, gtile)];
+      const int64_t tau = gtile - g->toff32;
+      const int64_t wf = warp_of_unit32(g->uoff32 + tau * g->M, B);
+      const int64_t wl = warp_of_unit32(g->uoff32 + (tau + 1) * g->M - 1, B);
+      const double* src = partial + (e0 - gtile * kSlotF) + lane;
+      double a[kCombineILP] = {};
+      int64_t q = wf + wi;
+      for (; q + (kCombineILP - 1) * split <= wl; q += kCombineILP * split) {
+#pragma unroll
+        for (int i = 0; i < kCombineILP; ++i) a[i] += __ldcg(src + (q + i * split + gtile) * kSlotF);
+      }
+      for (; q <= wl; q += split) a[0] += __ldcg(src + (q + gtile) * kSlotF);
+#pragma unroll
+      for (int h = kCombineILP / 2; h >= 1; h /= 2) {
+#pragma unroll
+        for (int i = 0; i < h; ++i) a[i] += a[i + h];
+      }
+      v = a[0];
+    }
+    if (split > 1) {
+      sums[wib][lane] = v;
+      __syncthreads();
+      if (wi == 0)
+        for (int i = 1; i < split; ++i) v += sums[wib + i][lane];
+      __syncthreads();
+    }
+    if (e0 < n && wi == 0) {
+      v *= g->kappa_dV;
+      bad |= !isfinite(v);
+      Fr[e0 + lane] = v;
+    }
+  }
+  if (bad) atomicOr(err, ERR_NONFINITE);
 }
 
 // ------------------------------------------------------- fused step kernel

@@ -24,7 +24,7 @@ EMU_ENUMERIC = -3
 EMU_ETIMEOUT = -4
 EMU_ELATTICE = -5
 N_DIAG = 63
-AUTOTUNE_CANDIDATES = 10   # EMU_AUTOTUNE_CANDIDATES
+AUTOTUNE_CANDIDATES = 13   # EMU_AUTOTUNE_CANDIDATES
 
 
 class EmuError(RuntimeError):
@@ -236,7 +236,7 @@ def emu_kernel_launches(box) -> int:
     return int(load().emu_kernel_launches(box))
 
 
-KERNEL_CLASSES = ("shifts", "deposit", "rk_stage", "combine", "other", "step")
+KERNEL_CLASSES = ("shifts", "deposit", "rk_stage", "combine", "other", "step", "rk_deposit")
 
 
 def emu_profile(box, enable: bool):
@@ -361,7 +361,7 @@ def emu_get_layout(box) -> int:
 
 # (step form, grid blocks, RK form) of each autotuner candidate, as emu.h lists them
 AUTOTUNE_GRID_FORMS = tuple((0, g, f) for g in (304, 152, 608) for f in (0, 1)) + \
-    tuple((1, g, f) for g in (304, 152) for f in (0, 1))
+    tuple((1, g, f) for g in (304, 152) for f in (0, 1)) + tuple((2, g, -1) for g in (304, 152, 608))
 
 
 def apply_choice(box, choice: int):
@@ -617,7 +617,8 @@ class Box:
         emu_set_rk_form(self.box, form)
 
     def set_step_form(self, form: int):
-        """1: one cooperative launch per step, 0: one launch per phase."""
+        """0: one launch per phase, 1: one cooperative launch per step, 2: RK
+        stages that deposit the next stage (shape orders 0-2)."""
         emu_set_step_form(self.box, form)
 
     def set_barrier_timeout(self, ns: int):
