@@ -160,7 +160,7 @@ def test_barrier_timeout_reports_and_recovers(torch):
 def test_step_form_validation(torch):
     from paper_2101_02745_gb300.emu import EmuError
     box = _box(W.random_box(40, 8, seed=1), 304, -1, 0)
-    for bad in (-1, 2):
+    for bad in (-1, 3):
         with pytest.raises(EmuError):
             box.set_step_form(bad)
     with pytest.raises(EmuError):
