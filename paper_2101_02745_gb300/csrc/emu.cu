@@ -695,28 +695,51 @@ bool use_rd(const emu_box* b) { return b->step_form == 2 && rd_possible(b) && rd
 
 // Raises the dynamic shared memory limit of k_rk_deposit (its frame sums)
 // once per device; outside any stream capture.
-template <bool POT, int R, bool D>
+template <bool POT, int R, int STAGE>
 int rd_attr(emu_box* b) {
   static std::atomic<unsigned> done{0};
   int dev = 0;
   if (int rc = cuda_check(b, cudaGetDevice(&dev), "get device")) return rc;
   if (dev < 32 && ((done.load() >> dev) & 1u)) return EMU_OK;
-  if (int rc = cuda_check(b, cudaFuncSetAttribute(k_rk_deposit<POT, R, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  kFrameSmem), "set shared memory of the RK-deposit kernel"))
+  if (int rc = cuda_check(b, cudaFuncSetAttribute(k_rk_deposit<POT, R, STAGE>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kFrameSmem),
+                          "set shared memory of the RK-deposit kernel"))
     return rc;
   if (dev < 32) done.fetch_or(1u << dev);
   return EMU_OK;
+}
+
+template <bool POT, int R>
+int rd_attr_stages(emu_box* b) {
+  if (int rc = rd_attr<POT, R, 1>(b)) return rc;
+  if (int rc = rd_attr<POT, R, 2>(b)) return rc;
+  if (int rc = rd_attr<POT, R, 3>(b)) return rc;
+  return rd_attr<POT, R, 4>(b);
 }
 
 int rd_prepare(emu_box* b) {
   return by_order(b->S.order, [&](auto O) {
     constexpr int R = decltype(O)::value;
     if constexpr (R <= 2) {
-      if (int rc = rd_attr<false, R, true>(b)) return rc;
-      return b->pot ? rd_attr<true, R, false>(b) : rd_attr<false, R, false>(b);
+      if (int rc = rd_attr<false, R, 0>(b)) return rc;
+      return b->pot ? rd_attr_stages<true, R>(b) : rd_attr_stages<false, R>(b);
     }
     return fail(b, EMU_EINVAL, "step form 2 covers the shape orders 0-2");
   });
+}
+
+template <bool POT, int R>
+void launch_rd_stage(emu_box* b, const Batch& Bv, dim3 grid, int s, int dry) {
+  auto go = [&](auto kernel) {
+    pdl_smem(b->stream, kernel, grid, kFrameSmem, Bv, b->pt, b->W, b->dirtab, b->shift, b->frame, dry, b->partial,
+             b->err);
+  };
+  switch (s) {
+    case 1: go(k_rk_deposit<POT, R, 1>); break;
+    case 2: go(k_rk_deposit<POT, R, 2>); break;
+    case 3: go(k_rk_deposit<POT, R, 3>); break;
+    default: go(k_rk_deposit<POT, R, 4>); break;
+  }
 }
 
 // Stage s (1..4) of form 2 with the deposit of the next stage, or (s = 0)
@@ -729,14 +752,12 @@ int launch_rd(emu_box* b, int s, int dry) {
     constexpr int R = decltype(O)::value;
     if constexpr (R <= 2) {
       if (s == 0)
-        pdl_smem(b->stream, k_rk_deposit<false, R, true>, grid, kFrameSmem, Bv, b->pt, b->W, b->dirtab, b->shift,
-                 b->frame, 0, 0, b->partial, b->err);
+        pdl_smem(b->stream, k_rk_deposit<false, R, 0>, grid, kFrameSmem, Bv, b->pt, b->W, b->dirtab, b->shift,
+                 b->frame, 0, b->partial, b->err);
       else if (b->pot)
-        pdl_smem(b->stream, k_rk_deposit<true, R, false>, grid, kFrameSmem, Bv, b->pt, b->W, b->dirtab, b->shift,
-                 b->frame, s, dry, b->partial, b->err);
+        launch_rd_stage<true, R>(b, Bv, grid, s, dry);
       else
-        pdl_smem(b->stream, k_rk_deposit<false, R, false>, grid, kFrameSmem, Bv, b->pt, b->W, b->dirtab, b->shift,
-                 b->frame, s, dry, b->partial, b->err);
+        launch_rd_stage<false, R>(b, Bv, grid, s, dry);
     }
     return 0;
   });

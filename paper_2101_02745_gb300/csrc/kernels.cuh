@@ -1245,15 +1245,20 @@ __device__ __forceinline__ double frame_value(const double* __restrict__ Fr, con
 // deposit of its result at the next stage's positions: the shape weights
 // (kept in W for the next stage), B = N rho - Nbar rhobar^* in the traceless
 // components (Eq. 5, Eq. 2) and w (1, Omega) B summed per frame cell.
-// DEP_ONLY: no RK update; the deposit of the state in rho, rhobar at the first
+// STAGE 0: no RK update; the deposit of the state in rho, rhobar at the first
 // stage's positions (the first launch of a run of steps).  Shift rows: this
-// stage's s - 1, the deposit's s (row 4: the next step's first stage).
-template <bool POT, int ORDER, bool DEP_ONLY>
+// stage's s - 1, the deposit's s (row 4: the next step's first stage).  The
+// stage is a template parameter: each instance keeps only its own stage's
+// loads live (fewer registers than one kernel for all four).
+template <bool POT, int ORDER, int STAGE>
 __global__ void __launch_bounds__(kThreads, 2)
 k_rk_deposit(Batch B, Parts pt, double* __restrict__ W, const double* __restrict__ dirtab,
-             const int* __restrict__ shift, const double* __restrict__ Fr, int s, int dry,
+             const int* __restrict__ shift, const double* __restrict__ Fr, int dry,
              double* __restrict__ partial, int* __restrict__ err) {
   static_assert(Sten<ORDER>::H == 1, "the frame covers the shapes of one cell of reach");
+  static_assert(STAGE >= 0 && STAGE <= 4, "stages 1-4, or 0 for the first deposit");
+  constexpr bool DEP_ONLY = STAGE == 0;
+  constexpr int s = STAGE;
   constexpr int NW = Sten<ORDER>::NW, NWS = Sten<ORDER>::NWS;
   extern __shared__ double frame_sm[];
   __shared__ double gsm[kWarps][kNC][kLanes];   // G of the unit's cells
