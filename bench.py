@@ -341,8 +341,14 @@ def run_gpu(args, rank, world, local_rank):
         box.set_oscillation(W.oscillation(**OSC_BENCH))
     stream = box.stream
     dt = box.timestep()
-    # launch configuration: grid x RK-stage form, timed on dry steps (state untouched)
-    tune_choice, tune_ms = box.autotune(trial_steps=2)
+    # launch configuration: grid x RK-stage form, timed on dry steps (state untouched);
+    # --choice fixes it instead (profiling runs, where timings under the profiler
+    # would pick another candidate)
+    if args.choice >= 0:
+        box.apply_choice(args.choice)
+        tune_choice, tune_ms = args.choice, [-1.0] * E.AUTOTUNE_CANDIDATES
+    else:
+        tune_choice, tune_ms = box.autotune(trial_steps=2)
     box.step(args.warmup, dt)
     box.sync()
 
@@ -872,6 +878,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-cells", type=int, default=256, help="cells per oracle step in --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--choice", type=int, default=-1,
+                    help="launch configuration of the main box (autotuner candidate index; default: autotune)")
     ap.add_argument("--adj-steps", type=int, default=0, help="steps of the adjoint workload (default 400)")
     ap.add_argument("--adj-record", choices=["auto", "on", "off"], default="auto",
                     help="adjoint backward with per-step records (auto: large boxes)")
