@@ -78,10 +78,16 @@ TRAFFIC_DEPOSIT = 296.7   # k_deposit<5> (traceless potential)
 #   RK stage: per neighbour row the x-y weight (1), the z-gather (40) and its
 #     weighted sum (16): 57; x 9 rows; the third diagonal difference (1), two
 #     commutators (162), RK update (72).
+# 3D step, algorithmic FP64 flops per particle (= per direction and cell):
+# k3_prep (lattice check 36, B 29); each separable pass along one axis (8
+# components x one multiply and two FMA); k3_spread_x_sum, the deposit's last
+# pass with the sum over directions (x pass 40 + moments 56); the G field; the
+# RK stage (z interpolation 40, third diagonal difference 1, commutators 162, RK 72)
 FLOPS3_PREP = 36 + 29
-FLOPS3_DEPOSIT = 9 * 52 + 56
+FLOPS3_PASS = 8 * 5
+FLOPS3_DEPOSIT = FLOPS3_PASS + 56
 FLOPS3_GFIELD = 48
-FLOPS3_RK = 9 * 57 + 1 + 162 + 72
+FLOPS3_RK = FLOPS3_PASS + 1 + 162 + 72
 
 
 def measured_peaks():

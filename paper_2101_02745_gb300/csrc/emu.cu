@@ -140,8 +140,9 @@ struct Layout {
   // each), digit histogram, cell starts, lattice-check flag
   size_t gkeys = 0, gkeys2 = 0, gids = 0, gids2 = 0, ghist = 0, gstart = 0, gflag = 0;
   size_t frame = 0; // step form 2: the frame sums of every 32-cell tile (k_frame_sum)
-  size_t bw3 = 0;   // 3D boxes: every particle's B and axis weights at the stage positions (k3_prep)
-  size_t gf3 = 0;   // 3D boxes: G = A0 - Omega . A of every (direction, cell) (k3_gfield)
+  size_t bw3 = 0;   // 3D boxes: 8-component field of every (direction, cell): B, its spread passes (k3_prep, k3_pass)
+  size_t gf3 = 0;   // 3D boxes: a second such field: G = A0 - Omega . A and its gather passes (k3_gfield, k3_pass)
+  size_t wdir3 = 0; // 3D boxes: every direction's shape weights per stage and axis (k3_shifts)
 };
 
 Layout layout(const Shape& S) {
@@ -1009,9 +1010,9 @@ Layout layout3(const Shape& S, size_t nrows) {
   L.diag = take(sizeof(double) * 63);
   L.scalar = take(sizeof(double) * 4);
   L.rowgeo = take(sizeof(BoxGeo) * nrows);
-  const int nw = S.order == 3 ? Sten<3>::NW : Sten<2>::NW;
-  L.bw3 = take(sizeof(double) * (size_t)(kNC + 3 * nw) * (size_t)S.Ptot);
+  L.bw3 = take(sizeof(double) * (size_t)kNC * (size_t)S.Ptot);
   L.gf3 = take(sizeof(double) * (size_t)kNC * (size_t)S.Ptot);
+  L.wdir3 = take(sizeof(double) * 4 * 3 * 5 * MT);
   L.total = off;
   return L;
 }
@@ -1054,13 +1055,35 @@ Batch row_view(const emu_box* b) {
   return B;
 }
 
+// The lattice shifts of nrows position offsets and the directions' weights there.
 int launch3_shifts(emu_box* b, const double* fracs, int nrows) {
   Fracs f{};
   for (int s = 0; s < nrows; ++s) f.v[s] = fracs[s];
+  double* wtab = (double*)(b->ws + b->L.wdir3);
   before_launch(b, CLS_SHIFT);
-  pdl(b->stream, k3_shifts, dim3((unsigned)((b->c3.ndir + kThreads - 1) / kThreads)), box3_view(b), b->x3, b->y3,
-      b->pt.z, b->dirtab, f, nrows, b->shift);
+  by_order(b->S.order, [&](auto O) {
+    pdl(b->stream, k3_shifts<decltype(O)::value>, dim3((unsigned)((b->c3.ndir + kThreads - 1) / kThreads)),
+        box3_view(b), b->x3, b->y3, b->pt.z, b->dirtab, f, nrows, b->shift, wtab);
+    return 0;
+  });
   return after_launch(b, "3D shift kernel");
+}
+
+// The stage's rows of the direction weight table (k3_shifts).
+const double* wrow3(const emu_box* b, int s) {
+  return (const double*)(b->ws + b->L.wdir3) + (size_t)(s - 1) * 3 * 5 * b->S.MT;
+}
+
+// One separable pass (k3_pass) over every (direction, cell).
+template <int AXIS, bool SPREAD>
+int launch3_pass(emu_box* b, const double* in, const double* wrow, double* out) {
+  before_launch(b, CLS_OTHER);
+  by_order(b->S.order, [&](auto O) {
+    pdl(b->stream, k3_pass<decltype(O)::value, AXIS, SPREAD>, dim3((unsigned)((b->S.Ptot + kThreads - 1) / kThreads)),
+        box3_view(b), in, wrow, out);
+    return 0;
+  });
+  return after_launch(b, "3D separable pass kernel");
 }
 
 // Deposit of the state (rnu, rnb) at positions x + frac dt c Omega with the
@@ -1096,59 +1119,64 @@ int launch3_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, 
   return after_launch(b, "deposit combine kernel");
 }
 
+// The RK stage of stage s: G = A0 - Omega . A of every (direction, cell)
+// (k3_gfield), interpolated along x and y (k3_pass), then k3_rk_stage
+// (along z, commutators, RK update).
 int launch3_rk(emu_box* b, int s, const int* srow, int dry) {
   const Box3 v = box3_view(b);
-  const double* Bw = (const double*)(b->ws + b->L.bw3);
-  double* Gf = (double*)(b->ws + b->L.gf3);
+  double* F0 = (double*)(b->ws + b->L.bw3);
+  double* F1 = (double*)(b->ws + b->L.gf3);
+  const double* wrow = wrow3(b, s);
   before_launch(b, CLS_OTHER);
   pdl(b->stream, k3_gfield, dim3((unsigned)((b->S.Ptot + kThreads - 1) / kThreads)), v, (const double*)b->At,
-      (const double*)b->dirtab, Gf);
+      (const double*)b->dirtab, F1);
   if (int rc = after_launch(b, "3D G field kernel")) return rc;
+  if (int rc = launch3_pass<0, false>(b, F1, wrow, F0)) return rc;
+  if (int rc = launch3_pass<1, false>(b, F0, wrow, F1)) return rc;
   before_launch(b, CLS_RK);
   by_order(b->S.order, [&](auto O) {
     constexpr int R = decltype(O)::value;
     if (b->pot)
       pdl(b->stream, k3_rk_stage<true, R>, persist_grid(b), v, b->pt, b->x3, b->y3, b->dirtab, srow,
-          (const double*)Gf, Bw, s, dry);
+          (const double*)F1, wrow, s, dry);
     else
       pdl(b->stream, k3_rk_stage<false, R>, persist_grid(b), v, b->pt, b->x3, b->y3, b->dirtab, srow,
-          (const double*)Gf, Bw, s, dry);
+          (const double*)F1, wrow, s, dry);
     return 0;
   });
   return after_launch(b, "3D RK stage kernel");
 }
 
-// The step's deposit of stage s: every particle's B and weights (k3_prep),
-// the gather from them (k3_deposit_bw), the combination into the traceless
-// potential At.
+// The step's deposit of stage s, separable: every particle's B at its cell
+// (k3_prep, with the lattice check), spread along z and y (k3_pass), then
+// along x and summed over directions into the traceless potential At
+// (k3_spread_x_sum).
 int launch3_step_deposit(emu_box* b, int s, const int* srow) {
   const size_t P = (size_t)b->S.Ptot;
   const double* rnu = (s == 1) ? b->pt.rho : b->pt.stage;
   const double* rnb = (s == 1) ? b->pt.rhobar : b->pt.stage + 9 * P;
-  double* Bw = (double*)(b->ws + b->L.bw3);
+  double* F0 = (double*)(b->ws + b->L.bw3);
+  double* F1 = (double*)(b->ws + b->L.gf3);
+  const double* wrow = wrow3(b, s);
   const Box3 v = box3_view(b);
   before_launch(b, CLS_OTHER);
   by_order(b->S.order, [&](auto O) {
     constexpr int R = decltype(O)::value;
     pdl(b->stream, k3_prep<R>, dim3((unsigned)((P + kThreads - 1) / kThreads)), v, (const double*)b->x3,
         (const double*)b->y3, (const double*)b->pt.z, (const double*)b->pt.N, (const double*)b->pt.Nbar, rnu, rnb,
-        (const double*)b->dirtab, srow, kStageFrac[s - 1], Bw, b->err);
+        (const double*)b->dirtab, srow, kStageFrac[s - 1], F0, b->err);
     return 0;
   });
   if (int rc = after_launch(b, "3D prep kernel")) return rc;
+  if (int rc = launch3_pass<2, true>(b, F0, wrow, F1)) return rc;
+  if (int rc = launch3_pass<1, true>(b, F1, wrow, F0)) return rc;
   before_launch(b, CLS_DEPOSIT);
   by_order(b->S.order, [&](auto O) {
-    constexpr int R = decltype(O)::value;
-    pdl(b->stream, k3_deposit_bw<R>, persist_grid(b), v, (const double*)Bw, (const double*)b->dirtab, srow,
-        b->partial);
+    pdl(b->stream, k3_spread_x_sum<decltype(O)::value>, dim3((unsigned)((v.C + kThreads - 1) / kThreads)), v,
+        (const double*)F0, wrow, (const double*)b->dirtab, b->At, b->err);
     return 0;
   });
-  if (int rc = after_launch(b, "3D deposit kernel")) return rc;
-  const Batch B = row_view(b);
-  const int split = combine_split(b->S, B.nw);
-  before_launch(b, CLS_COMBINE);
-  pdl(b->stream, k_combine, dim3(combine_blocks(kNT, B.NZ, split)), B, b->partial, b->At, kNT, 1, split, b->err);
-  return after_launch(b, "deposit combine kernel");
+  return after_launch(b, "3D deposit sum kernel");
 }
 
 int launch3_stage(emu_box* b, int s, int dry) {

@@ -10,9 +10,10 @@
 // per cell, Sec. 3.1).  The particles of one direction translate rigidly
 // (constant velocity c Omega, Eq. 4), so they stay a lattice: the particle on
 // cell (jx, jy, jz) is the one of site (jx - sx_d, jy - sy_d, jz - sz_d) (mod
-// the cell counts), with one shift per axis, direction and RK stage.  Each
-// particle still uses its own position for its weights, checked against the
-// cell its site assigns (ERR_LATTICE otherwise).
+// the cell counts), with one shift per axis, direction and RK stage.  The
+// generic kernels (k3_deposit, k3_interpolate) use each particle's own position
+// for its weights, checked against the cell its site assigns (ERR_LATTICE
+// otherwise).
 //
 // Shape: the tensor product of the 1D shape of order ORDER on each axis, so
 // a particle reaches (2H+1)^3 cells.  Work units are (row, z tile of T cells,
@@ -25,9 +26,16 @@
 //     directions stays in registers and goes out as one partial per (warp,
 //     row tile), added in warp order by k_combine (each row is one "box" of
 //     that kernel's batch view);
-//   RK stage (Eq. 6, 2, 4, Sec. 2.3): each lane's particle interpolates
-//     G = A0 - Omega . A of the (2H+1)^2 neighbour rows along z through
-//     shuffles, weighted by its x- and y-weights, then rk_particle.
+//   interpolation (Eq. 6): the same gather transposed.
+// The step itself is separable: all particles of a direction sit at the same
+// offset inside their cells (up to rounding), so their weights on each axis
+// are the direction's (k3_shifts computes them from the site-0 particle), and
+// the deposit of one direction is a 3-tap convolution along z, then y, then x
+// of its B field (k3_spread), summed over directions with (1, Omega) into the
+// potential (k3_spread_x_sum); the interpolation of G = A0 - Omega . A is the
+// transposed convolution (k3_gather along x and y, then z by shuffles in
+// k3_rk_stage).  Three 3-tap passes per direction and cell instead of a
+// (2H+1)^2-row gather per particle.
 #pragma once
 
 namespace emu_dev {
@@ -84,11 +92,16 @@ __global__ void k3_dirtable(Box3 b, Parts pt, double* __restrict__ dirtab, int* 
 
 // Lattice shifts of every direction for up to 4 position offsets frac[s] dt:
 // the cell, on each axis, of the direction's site-0 particle at x + frac dt c
-// Omega; shift[(s * 3 + axis) * M + d].
+// Omega; shift[(s * 3 + axis) * M + d].  With wtab, also that particle's
+// shape weights there, the direction's weights on each axis (all its
+// particles share the offset inside their cells): wtab[((s * 3 + axis) * 5 +
+// q) * M + d], q < NW.
+template <int ORDER>
 __global__ void k3_shifts(Box3 b, const double* __restrict__ x, const double* __restrict__ y,
                           const double* __restrict__ z, const double* __restrict__ dirtab, Fracs fr, int nrows,
-                          int* __restrict__ shift) {
+                          int* __restrict__ shift, double* __restrict__ wtab) {
   griddep_wait();
+  constexpr int NW = Sten<ORDER>::NW;
   const int d = blockIdx.x * blockDim.x + threadIdx.x;
   if (d >= b.M) return;
   const int64_t p0 = (int64_t)d * b.C;
@@ -100,7 +113,14 @@ __global__ void k3_shifts(Box3 b, const double* __restrict__ x, const double* __
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const double xs = fma(fr.v[s] * dt, dirtab[(3 + a) * b.M + d], pos[a]);
-      shift[(s * 3 + a) * b.M + d] = wrapn((int)floor(xs * b.inv_h[a]), b.n[a]);
+      const int cell = wrapn((int)floor(xs * b.inv_h[a]), b.n[a]);
+      shift[(s * 3 + a) * b.M + d] = cell;
+      if (wtab != nullptr) {
+        double w[NW];
+        (void)shape_weights<ORDER>(xs, (double)cell + 0.5, b.inv_h[a], b.n_d[a], w);
+#pragma unroll
+        for (int q = 0; q < NW; ++q) wtab[((s * 3 + a) * 5 + q) * b.M + d] = w[q];
+      }
     }
   }
 }
@@ -242,19 +262,17 @@ k3_deposit(Box3 b, const double* __restrict__ x, const double* __restrict__ y, c
   if (bad) atomicOr(err, ERR_LATTICE);
 }
 
-// The step's deposit in two parts.  k3_prep: one thread per particle, its
-// shape weights on the three axes at the stage position (checked against the
-// cell its site assigns) and the 8 traceless components of B = N rho - Nbar
-// rhobar^* (Eq. 5), stored as Bw[row][P]: rows 0-7 B, then NW rows each of the
-// x, y and z weights.  k3_deposit_bw: the gather of k3_deposit<5> from them,
-// so that each particle's weights and B are computed once per stage instead
-// of once for every neighbour row it feeds; the RK stage reads the weights too.
+// The step's deposit (MODE 5 of k3_deposit), separable.  k3_prep: one thread
+// per particle; checks its position against the cell its site assigns at the
+// stage (ERR_LATTICE) and writes the 8 traceless components of
+// B = N rho - Nbar rhobar^* (Eq. 5) at that cell of its direction's field:
+// Bf[c * P + d * C + cell].
 template <int ORDER>
 __global__ void __launch_bounds__(kThreads)
 k3_prep(Box3 b, const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ z,
         const double* __restrict__ N, const double* __restrict__ Nbar, const double* __restrict__ r_nu,
         const double* __restrict__ r_nb, const double* __restrict__ dirtab, const int* __restrict__ srow,
-        double frac, double* __restrict__ Bw, int* __restrict__ err) {
+        double frac, double* __restrict__ Bf, int* __restrict__ err) {
   griddep_wait();
   constexpr int NW = Sten<ORDER>::NW;
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -268,13 +286,14 @@ k3_prep(Box3 b, const double* __restrict__ x, const double* __restrict__ y, cons
   const int jy = wrapn(iy + __ldg(srow + M + d), b.n[1]);
   const int jz = wrapn(iz + __ldg(srow + 2 * M + d), b.n[2]);
   const double pos_dt = frac * *b.dt;
-  double wx[NW], wy[NW], wz[NW];
+  double w[NW];
   int bad = shape_weights<ORDER>(fma(pos_dt, __ldg(dirtab + 3 * M + d), x[p]), (double)jx + 0.5, b.inv_h[0],
-                                 b.n_d[0], wx);
+                                 b.n_d[0], w);
   bad |= shape_weights<ORDER>(fma(pos_dt, __ldg(dirtab + 4 * M + d), y[p]), (double)jy + 0.5, b.inv_h[1], b.n_d[1],
-                              wy);
+                              w);
   bad |= shape_weights<ORDER>(fma(pos_dt, __ldg(dirtab + 5 * M + d), z[p]), (double)jz + 0.5, b.inv_h[2], b.n_d[2],
-                              wz);
+                              w);
+  const int64_t out = (int64_t)d * b.C + ((int64_t)jx * b.n[1] + jy) * b.n[2] + jz;
   const double n1 = N[p], n2 = Nbar[p];
   double bprev = 0.0;
 #pragma unroll
@@ -290,75 +309,102 @@ k3_prep(Box3 b, const double* __restrict__ x, const double* __restrict__ y, cons
       const double xv = r_nu[k * P + p], yv = r_nb[k * P + p];
       bv = (k == 4 || k == 6 || k == 8) ? fma(n2, yv, n1 * xv) : fma(-n2, yv, n1 * xv);
     }
-    Bw[c * P + p] = bv;
-  }
-#pragma unroll
-  for (int q = 0; q < NW; ++q) {
-    Bw[(kNC + q) * P + p] = wx[q];
-    Bw[(kNC + NW + q) * P + p] = wy[q];
-    Bw[(kNC + 2 * NW + q) * P + p] = wz[q];
+    Bf[c * P + out] = bv;
   }
   if (bad) atomicOr(err, ERR_LATTICE);
 }
 
-template <int ORDER>
-__global__ void __launch_bounds__(kThreads, 2)
-k3_deposit_bw(Box3 b, const double* __restrict__ Bw, const double* __restrict__ dirtab, const int* __restrict__ srow,
-              double* __restrict__ partial) {
+// Neighbour of cell (jx, jy, jz) at offset o along AXIS (periodic).
+template <int AXIS>
+__device__ __forceinline__ int64_t cell_along(const Box3& b, int jx, int jy, int jz, int o) {
+  if (AXIS == 0) jx = wrapn(jx + o, b.n[0]);
+  else if (AXIS == 1) jy = wrapn(jy + o, b.n[1]);
+  else jz = wrapn(jz + o, b.n[2]);
+  return ((int64_t)jx * b.n[1] + jy) * b.n[2] + jz;
+}
+
+// One 3-tap (NW-tap) pass along AXIS of the 8-component field of every
+// direction, thread per (direction, cell) i = d C + cell:
+//   SPREAD (deposit, Eq. 5): out(cell) = sum_q w_d[q] in(cell - (q - H))
+//     (a particle's weight q goes to the cell q - H away from its own);
+//   otherwise (interpolation, Eq. 6): out(cell) = sum_q w_d[q] in(cell + q - H).
+// w_d: the direction's weights on AXIS at the stage (wrow = wtab + stage rows).
+template <int ORDER, int AXIS, bool SPREAD>
+__global__ void __launch_bounds__(kThreads)
+k3_pass(Box3 b, const double* __restrict__ in, const double* __restrict__ wrow, double* __restrict__ out) {
   griddep_wait();
-  constexpr int H = Sten<ORDER>::H, T = Sten<ORDER>::T, NW = Sten<ORDER>::NW;
-  const int lane = threadIdx.x & 31;
-  const int64_t w = logical_warp();
-  const int64_t u0 = unit3_begin(w, b), u1 = unit3_begin(w + 1, b);
-  if (u0 >= u1) return;
+  constexpr int H = Sten<ORDER>::H, NW = Sten<ORDER>::NW;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t P = b.P;
-  const int M = b.M, nx = b.n[0], ny = b.n[1], nz = b.n[2];
-  for (int64_t u = u0; u < u1;) {          // one segment per (row, tile)
-    const int64_t gtile = u / M;
-    const int row = (int)(gtile / b.ntz), tile = (int)(gtile - (int64_t)row * b.ntz);
-    const int jx = row / ny, jy = row - jx * ny;
-    const int dfirst = (int)(u - gtile * M);
-    const int64_t uend = min(u1, (gtile + 1) * M);
-    const int dlast = (int)(uend - gtile * M);
-    u = uend;
-    const int craw = tile * T - H + lane;
-    const int jz = wrapc(craw, nz);
-    double acc[kNT];
+  if (i >= P) return;
+  const int d = (int)(i / b.C);
+  const int cell = (int)(i - (int64_t)d * b.C);
+  const int jz = cell % b.n[2], jy = (cell / b.n[2]) % b.n[1], jx = cell / (b.n[2] * b.n[1]);
+  const double* src = in + (int64_t)d * b.C;
+  double w[NW];
+  int64_t nb[NW];
 #pragma unroll
-    for (int c = 0; c < kNT; ++c) acc[c] = 0.0;
-    for (int d = dfirst; d < dlast; ++d) {
-      const double ox = __ldg(dirtab + d), oy = __ldg(dirtab + M + d), oz = __ldg(dirtab + 2 * M + d);
-      const int sx = __ldg(srow + d), sy = __ldg(srow + M + d), sz = __ldg(srow + 2 * M + d);
-      double S[kNC];
-#pragma unroll
-      for (int c = 0; c < kNC; ++c) S[c] = 0.0;
-#pragma unroll 1
-      for (int a = -H; a <= H; ++a) {
-#pragma unroll 1
-        for (int bb = -H; bb <= H; ++bb) {
-          if (ORDER == 0 && (a != 0 || bb != 0)) continue;
-          const int64_t p = site3(b, d, wrapn(jx + a, nx), wrapn(jy + bb, ny), jz, sx, sy, sz);
-          // this particle's share of the warp's row, folded into its z-weights
-          const double f = __ldg(Bw + (kNC + H - a) * P + p) * __ldg(Bw + (kNC + NW + H - bb) * P + p);
-          double wz[NW];
-#pragma unroll
-          for (int q = 0; q < NW; ++q) wz[q] = f * __ldg(Bw + (kNC + 2 * NW + q) * P + p);
-          Spread<ORDER> spread;
-          spread.init(wz);
-#pragma unroll
-          for (int c = 0; c < kNC; ++c) S[c] += spread.apply(__ldg(Bw + c * P + p));
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < kNC; ++c) {
-        acc[c] += S[c];
-        acc[kNC + c] = fma(ox, S[c], acc[kNC + c]);
-        acc[2 * kNC + c] = fma(oy, S[c], acc[2 * kNC + c]);
-        acc[3 * kNC + c] = fma(oz, S[c], acc[3 * kNC + c]);
-      }
-    }
-    flush_tile<ORDER>(acc, gtile, craw, nz, w, lane, partial);
+  for (int q = 0; q < NW; ++q) {
+    w[q] = __ldg(wrow + ((AXIS * 5) + q) * b.M + d);
+    nb[q] = cell_along<AXIS>(b, jx, jy, jz, SPREAD ? H - q : q - H);
   }
+#pragma unroll
+  for (int c = 0; c < kNC; ++c) {
+    const double* sc = src + c * P;
+    double v = w[0] * __ldg(sc + nb[0]);
+#pragma unroll
+    for (int q = 1; q < NW; ++q) v = fma(w[q], __ldg(sc + nb[q]), v);
+    out[c * P + i] = v;
+  }
+}
+
+// The last deposit pass: along x, summed over directions in order with
+// (1, Omega_x, Omega_y, Omega_z) into the traceless potential (thread per
+// cell): At[(m * 8 + c) * C + cell] = kappa / dV sum_d Omega~_m,d (the
+// direction's x-spread of its y- and z-spread B field).  No partial sums.
+template <int ORDER>
+__global__ void __launch_bounds__(kThreads)
+k3_spread_x_sum(Box3 b, const double* __restrict__ in, const double* __restrict__ wrow,
+                const double* __restrict__ dirtab, double* __restrict__ At, int* __restrict__ err) {
+  griddep_wait();
+  constexpr int H = Sten<ORDER>::H, NW = Sten<ORDER>::NW;
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= b.C) return;
+  const int64_t P = b.P;
+  const int M = b.M;
+  const int jz = cell % b.n[2], jy = (cell / b.n[2]) % b.n[1], jx = cell / (b.n[2] * b.n[1]);
+  int64_t nb[NW];
+#pragma unroll
+  for (int q = 0; q < NW; ++q) nb[q] = cell_along<0>(b, jx, jy, jz, H - q);
+  double acc[kNT];
+#pragma unroll
+  for (int c = 0; c < kNT; ++c) acc[c] = 0.0;
+  for (int d = 0; d < M; ++d) {
+    const double ox = __ldg(dirtab + d), oy = __ldg(dirtab + M + d), oz = __ldg(dirtab + 2 * M + d);
+    double w[NW];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) w[q] = __ldg(wrow + q * M + d);
+    const double* src = in + (int64_t)d * b.C;
+#pragma unroll
+    for (int c = 0; c < kNC; ++c) {
+      const double* sc = src + c * P;
+      double v = w[0] * __ldg(sc + nb[0]);
+#pragma unroll
+      for (int q = 1; q < NW; ++q) v = fma(w[q], __ldg(sc + nb[q]), v);
+      acc[c] += v;
+      acc[kNC + c] = fma(ox, v, acc[kNC + c]);
+      acc[2 * kNC + c] = fma(oy, v, acc[2 * kNC + c]);
+      acc[3 * kNC + c] = fma(oz, v, acc[3 * kNC + c]);
+    }
+  }
+  int bad = 0;
+#pragma unroll
+  for (int c = 0; c < kNT; ++c) {
+    const double v = acc[c] * b.kappa_dV;
+    bad |= !isfinite(v);
+    At[(int64_t)c * b.C + cell] = v;
+  }
+  if (bad) atomicOr(err, ERR_NONFINITE);
 }
 
 // G = A0 - Omega_d . A of every (direction, cell) from the traceless
@@ -380,32 +426,6 @@ k3_gfield(Box3 b, const double* __restrict__ At, const double* __restrict__ dirt
   for (int c = 0; c < kNC; ++c)
     Gf[c * MC + i] = fma(-oz, Aj[(3 * kNC + c) * Cn],
                          fma(-oy, Aj[(2 * kNC + c) * Cn], fma(-ox, Aj[(kNC + c) * Cn], Aj[c * Cn])));
-}
-
-// H of the lane's particle from the G field (traceless components): its x- and
-// y-weights over the neighbour rows times the z-interpolation along each row.
-// Every lane must call it.
-template <int ORDER>
-__device__ __forceinline__ void interp3g(const Box3& b, const double* __restrict__ Gf, int d, int jx, int jy, int jz,
-                                         const double (&wx)[Sten<ORDER>::NW], const double (&wy)[Sten<ORDER>::NW],
-                                         const double (&wz)[Sten<ORDER>::NW], double (&Hm)[kNC]) {
-  constexpr int H = Sten<ORDER>::H;
-  const int64_t MC = (int64_t)b.M * b.C;
-  const double* Gd = Gf + (int64_t)d * b.C + jz;
-#pragma unroll
-  for (int c = 0; c < kNC; ++c) Hm[c] = 0.0;
-#pragma unroll 1
-  for (int a = -H; a <= H; ++a) {
-#pragma unroll 1
-    for (int bb = -H; bb <= H; ++bb) {
-      if (ORDER == 0 && (a != 0 || bb != 0)) continue;
-      const int row = wrapn(jx + a, b.n[0]) * b.n[1] + wrapn(jy + bb, b.n[1]);
-      const double* G = Gd + (int64_t)row * b.n[2];
-      const double wab = pick(wx, H + a) * pick(wy, H + bb);
-#pragma unroll
-      for (int c = 0; c < kNC; ++c) Hm[c] = fma(wab, gather<ORDER>(wz, __ldg(G + c * MC)), Hm[c]);
-    }
-  }
 }
 
 // H of the lane's particle (traceless components, Eq. 6 then Eq. 2): its
@@ -440,16 +460,15 @@ __device__ __forceinline__ void interp3(const Box3& b, const double* A, int jx, 
 }
 
 // One RK4 stage s (1..4) on the 3D grid after the deposit of the stage state
-// (as k_rk_stage): interpolation, H and Hbar, commutators, RK update; stage 4
-// also moves the particle on every axis (dry: the results of stage 4 go to the
-// RK scratch, for the autotuner's timing).  The shape weights are those k3_prep
-// stored for the stage positions (the deposit's), read by the lanes that own a
-// particle; halo lanes supply only the G values of their cells to the
-// z-interpolation.
+// (as k_rk_stage): H from Gxy (G = A0 - Omega . A interpolated along x and y
+// by k3_gather) interpolated along z through shuffles with the direction's
+// z-weights, H and Hbar, commutators, RK update; stage 4 also moves the
+// particle on every axis (dry: the results of stage 4 go to the RK scratch,
+// for the autotuner's timing).  Halo lanes only supply their cells' values.
 template <bool POT, int ORDER>
 __global__ void __launch_bounds__(kThreads, 2)
 k3_rk_stage(Box3 b, Parts pt, double* __restrict__ x, double* __restrict__ y, const double* __restrict__ dirtab,
-            const int* __restrict__ srow, const double* __restrict__ Gf, const double* __restrict__ Bw, int s,
+            const int* __restrict__ srow, const double* __restrict__ Gxy, const double* __restrict__ wrow, int s,
             int dry) {
   griddep_wait();
   constexpr int H = Sten<ORDER>::H, T = Sten<ORDER>::T, NW = Sten<ORDER>::NW;
@@ -471,23 +490,15 @@ k3_rk_stage(Box3 b, Parts pt, double* __restrict__ x, double* __restrict__ y, co
     const int jx = row / ny, jy = row - jx * ny;
     const int craw = tile * T - H + lane, jz = wrapc(craw, nz);
     const bool active = lane >= H && lane < H + T && craw < nz;
-    const double ox = __ldg(dirtab + d), oy = __ldg(dirtab + M + d), oz = __ldg(dirtab + 2 * M + d);
     const double vx = __ldg(dirtab + 3 * M + d), vy = __ldg(dirtab + 4 * M + d);
     const int64_t p = site3(b, d, jx, jy, jz, __ldg(srow + d), __ldg(srow + M + d), __ldg(srow + 2 * M + d));
-    double wx[NW], wy[NW], wz[NW];
-    zero_weights<ORDER>(wx);
-    zero_weights<ORDER>(wy);
-    zero_weights<ORDER>(wz);
-    if (active) {   // the weights of this stage's positions, from k3_prep
+    double wz[NW];
 #pragma unroll
-      for (int q = 0; q < NW; ++q) {
-        wx[q] = __ldg(Bw + (kNC + q) * P + p);
-        wy[q] = __ldg(Bw + (kNC + NW + q) * P + p);
-        wz[q] = __ldg(Bw + (kNC + 2 * NW + q) * P + p);
-      }
-    }
+    for (int q = 0; q < NW; ++q) wz[q] = active ? __ldg(wrow + (2 * 5 + q) * M + d) : 0.0;
+    const double* G = Gxy + (int64_t)d * b.C + (int64_t)row * nz + jz;
     double Hm[kNC];
-    interp3g<ORDER>(b, Gf, d, jx, jy, jz, wx, wy, wz, Hm);
+#pragma unroll
+    for (int c = 0; c < kNC; ++c) Hm[c] = gather<ORDER>(wz, __ldg(G + c * P));
     if (!active) continue;
     double r[9];
 #pragma unroll
