@@ -1027,6 +1027,12 @@ Box3 box3_view(const emu_box* b) {
   v.ntz = b->ntz;
   v.T = b->S.T;
   v.nw = batch_view(b).nw;
+  v.ntz32 = (c.nz + kLanes - 1) / kLanes;
+  v.U32 = (int64_t)v.ntz32 * c.nx * c.ny * c.ndir;
+  {
+    const int64_t warps = (int64_t)b->blocks * kWarps;
+    v.nw32 = (int)(v.U32 < warps ? v.U32 : warps);
+  }
   v.use_dirs = b->S.geo[0].use_dirs;
   v.U = b->S.U;
   v.P = b->S.Ptot;

@@ -45,6 +45,8 @@ struct Box3 {
   int M, C, R;         // directions, cells, rows (nx ny)
   int ntz, T;          // z tiles per row, cells per tile
   int nw;              // warps that split the units
+  int ntz32, nw32;     // the RK stage's 32-cell z tiles per row, warps that split its units
+  int64_t U32;         // its units (R ntz32 M)
   int use_dirs;
   int64_t U, P;        // units (R ntz M), particles (M C)
   double L[3], inv_h[3], n_d[3], h[3];
@@ -461,20 +463,22 @@ __device__ __forceinline__ void interp3(const Box3& b, const double* A, int jx, 
 
 // One RK4 stage s (1..4) on the 3D grid after the deposit of the stage state
 // (as k_rk_stage): H from Gxy (G = A0 - Omega . A interpolated along x and y
-// by k3_gather) interpolated along z through shuffles with the direction's
-// z-weights, H and Hbar, commutators, RK update; stage 4 also moves the
-// particle on every axis (dry: the results of stage 4 go to the RK scratch,
-// for the autotuner's timing).  Halo lanes only supply their cells' values.
+// by k3_pass) interpolated along z with the direction's z-weights, H and Hbar,
+// commutators, RK update; stage 4 also moves the particle on every axis (dry:
+// the results of stage 4 go to the RK scratch, for the autotuner's timing).
+// Units are (row, 32-cell z tile, direction), every lane on its own cell: the
+// z neighbours' G come from the field in memory (L1), not from halo lanes, so
+// no lane idles except past the end of a row.
 template <bool POT, int ORDER>
 __global__ void __launch_bounds__(kThreads, 2)
 k3_rk_stage(Box3 b, Parts pt, double* __restrict__ x, double* __restrict__ y, const double* __restrict__ dirtab,
             const int* __restrict__ srow, const double* __restrict__ Gxy, const double* __restrict__ wrow, int s,
             int dry) {
   griddep_wait();
-  constexpr int H = Sten<ORDER>::H, T = Sten<ORDER>::T, NW = Sten<ORDER>::NW;
+  constexpr int H = Sten<ORDER>::H, NW = Sten<ORDER>::NW;
   const int lane = threadIdx.x & 31;
   const int64_t w = logical_warp();
-  const int64_t u0 = unit3_begin(w, b), u1 = unit3_begin(w + 1, b);
+  const int64_t u0 = w >= b.nw32 ? b.U32 : w * b.U32 / b.nw32, u1 = w + 1 >= b.nw32 ? b.U32 : (w + 1) * b.U32 / b.nw32;
   if (u0 >= u1) return;
   const int64_t P = b.P;
   const int M = b.M, ny = b.n[1], nz = b.n[2];
@@ -486,20 +490,28 @@ k3_rk_stage(Box3 b, Parts pt, double* __restrict__ x, double* __restrict__ y, co
   for (int64_t u = u0; u < u1; ++u) {
     const int64_t gtile = u / M;
     const int d = (int)(u - gtile * M);
-    const int row = (int)(gtile / b.ntz), tile = (int)(gtile - (int64_t)row * b.ntz);
+    const int row = (int)(gtile / b.ntz32), tile = (int)(gtile - (int64_t)row * b.ntz32);
     const int jx = row / ny, jy = row - jx * ny;
-    const int craw = tile * T - H + lane, jz = wrapc(craw, nz);
-    const bool active = lane >= H && lane < H + T && craw < nz;
+    const int jz = tile * kLanes + lane;
+    if (jz >= nz) continue;
     const double vx = __ldg(dirtab + 3 * M + d), vy = __ldg(dirtab + 4 * M + d);
     const int64_t p = site3(b, d, jx, jy, jz, __ldg(srow + d), __ldg(srow + M + d), __ldg(srow + 2 * M + d));
     double wz[NW];
 #pragma unroll
-    for (int q = 0; q < NW; ++q) wz[q] = active ? __ldg(wrow + (2 * 5 + q) * M + d) : 0.0;
-    const double* G = Gxy + (int64_t)d * b.C + (int64_t)row * nz + jz;
+    for (int q = 0; q < NW; ++q) wz[q] = __ldg(wrow + (2 * 5 + q) * M + d);
+    const double* G = Gxy + (int64_t)d * b.C + (int64_t)row * nz;
+    int cz[NW];   // the stencil's z cells, cell jz + q - H (periodic)
+#pragma unroll
+    for (int q = 0; q < NW; ++q) cz[q] = wrapn(jz + q - H, nz);
     double Hm[kNC];
 #pragma unroll
-    for (int c = 0; c < kNC; ++c) Hm[c] = gather<ORDER>(wz, __ldg(G + c * P));
-    if (!active) continue;
+    for (int c = 0; c < kNC; ++c) {   // (the taps in gather's order)
+      const double* Gc = G + c * P;
+      double h = wz[NW - 1] * __ldg(Gc + cz[NW - 1]);
+#pragma unroll
+      for (int q = NW - 2; q >= 0; --q) h = fma(wz[q], __ldg(Gc + cz[q]), h);
+      Hm[c] = h;
+    }
     double r[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) r[k] = src_r[k * P + p];
