@@ -1166,13 +1166,9 @@ int launch3_step_deposit(emu_box* b, int s, const int* srow) {
   const double* wrow = wrow3(b, s);
   const Box3 v = box3_view(b);
   before_launch(b, CLS_OTHER);
-  by_order(b->S.order, [&](auto O) {
-    constexpr int R = decltype(O)::value;
-    pdl(b->stream, k3_prep<R>, dim3((unsigned)((P + kThreads - 1) / kThreads)), v, (const double*)b->x3,
-        (const double*)b->y3, (const double*)b->pt.z, (const double*)b->pt.N, (const double*)b->pt.Nbar, rnu, rnb,
-        (const double*)b->dirtab, srow, kStageFrac[s - 1], F0, b->err);
-    return 0;
-  });
+  pdl(b->stream, k3_prep, dim3((unsigned)((P + kThreads - 1) / kThreads)), v, (const double*)b->x3,
+      (const double*)b->y3, (const double*)b->pt.z, (const double*)b->pt.N, (const double*)b->pt.Nbar, rnu, rnb,
+      (const double*)b->dirtab, srow, kStageFrac[s - 1], F0, b->err);
   if (int rc = after_launch(b, "3D prep kernel")) return rc;
   if (int rc = launch3_pass<2, true>(b, F0, wrow, F1)) return rc;
   if (int rc = launch3_pass<1, true>(b, F1, wrow, F0)) return rc;

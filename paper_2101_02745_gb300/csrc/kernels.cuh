@@ -224,6 +224,17 @@ __device__ __forceinline__ int shape_weights(double zs, double hp, double inv_dz
   return bad;
 }
 
+// The lattice test of shape_weights alone: nonzero if the particle at zs is
+// off the cell whose centre is hp (in cells), up to the periodic image.
+__device__ __forceinline__ int off_site(double zs, double hp, double inv_dz, double nz_d) {
+  double d = fma(zs, inv_dz, -hp);
+  if (fabs(d) > 0.5 + kLatticeTol) {
+    d -= nz_d * rint(d / nz_d);
+    return fabs(d) > 0.5 + kLatticeTol;
+  }
+  return 0;
+}
+
 // Loads of data that a fused step launch (k_step) writes before it reads
 // them (positions, stage states, shape weights, grid potential, lattice
 // shifts) must not take the read-only (non-coherent) path, which is only

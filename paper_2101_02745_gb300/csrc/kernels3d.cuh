@@ -269,14 +269,12 @@ k3_deposit(Box3 b, const double* __restrict__ x, const double* __restrict__ y, c
 // stage (ERR_LATTICE) and writes the 8 traceless components of
 // B = N rho - Nbar rhobar^* (Eq. 5) at that cell of its direction's field:
 // Bf[c * P + d * C + cell].
-template <int ORDER>
 __global__ void __launch_bounds__(kThreads)
 k3_prep(Box3 b, const double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ z,
         const double* __restrict__ N, const double* __restrict__ Nbar, const double* __restrict__ r_nu,
         const double* __restrict__ r_nb, const double* __restrict__ dirtab, const int* __restrict__ srow,
         double frac, double* __restrict__ Bf, int* __restrict__ err) {
   griddep_wait();
-  constexpr int NW = Sten<ORDER>::NW;
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= b.P) return;
   const int64_t P = b.P;
@@ -288,13 +286,9 @@ k3_prep(Box3 b, const double* __restrict__ x, const double* __restrict__ y, cons
   const int jy = wrapn(iy + __ldg(srow + M + d), b.n[1]);
   const int jz = wrapn(iz + __ldg(srow + 2 * M + d), b.n[2]);
   const double pos_dt = frac * *b.dt;
-  double w[NW];
-  int bad = shape_weights<ORDER>(fma(pos_dt, __ldg(dirtab + 3 * M + d), x[p]), (double)jx + 0.5, b.inv_h[0],
-                                 b.n_d[0], w);
-  bad |= shape_weights<ORDER>(fma(pos_dt, __ldg(dirtab + 4 * M + d), y[p]), (double)jy + 0.5, b.inv_h[1], b.n_d[1],
-                              w);
-  bad |= shape_weights<ORDER>(fma(pos_dt, __ldg(dirtab + 5 * M + d), z[p]), (double)jz + 0.5, b.inv_h[2], b.n_d[2],
-                              w);
+  int bad = off_site(fma(pos_dt, __ldg(dirtab + 3 * M + d), x[p]), (double)jx + 0.5, b.inv_h[0], b.n_d[0]);
+  bad |= off_site(fma(pos_dt, __ldg(dirtab + 4 * M + d), y[p]), (double)jy + 0.5, b.inv_h[1], b.n_d[1]);
+  bad |= off_site(fma(pos_dt, __ldg(dirtab + 5 * M + d), z[p]), (double)jz + 0.5, b.inv_h[2], b.n_d[2]);
   const int64_t out = (int64_t)d * b.C + ((int64_t)jx * b.n[1] + jy) * b.n[2] + jz;
   const double n1 = N[p], n2 = Nbar[p];
   double bprev = 0.0;
