@@ -139,6 +139,7 @@ struct Layout {
   // particles anywhere (kernels_general.cuh): sort keys and values (two of
   // each), digit histogram, cell starts, lattice-check flag
   size_t gkeys = 0, gkeys2 = 0, gids = 0, gids2 = 0, ghist = 0, gstart = 0, gflag = 0;
+  size_t gprep = 0;  // particles anywhere: B (8) and Omega (3) of every particle in sorted order (k_gprep)
   size_t frame = 0; // step form 2: the frame sums of every 32-cell tile (k_frame_sum)
   size_t bw3 = 0;   // 3D boxes: 8-component field of every (direction, cell): B, its spread passes (k3_prep, k3_pass)
   size_t gf3 = 0;   // 3D boxes: a second such field: G = A0 - Omega . A and its gather passes (k3_gfield, k3_pass)
@@ -178,6 +179,7 @@ Layout layout(const Shape& S) {
   L.ghist = take(sizeof(int) * kRadixBuckets * (nblk ? nblk : 1));
   L.gstart = take(sizeof(int) * ((size_t)NZ + 1));
   L.gflag = take(sizeof(int));
+  L.gprep = take(sizeof(double) * (size_t)(kNC + 3) * P);
   L.total = off;
   return L;
 }
@@ -1279,11 +1281,40 @@ int launch_gdeposit(emu_box* b, int mode, const double* rnu, const double* rnb, 
   return after_launch(b, "deposit kernel (particles anywhere)");
 }
 
+// The step's deposit of particles anywhere: sort, every particle's weights,
+// B and direction in sorted order (k_gprep; the weights in the lattice path's
+// weight buffer, unused here), then the deposit from them (k_gdeposit_sorted).
+int launch_gstep_deposit(emu_box* b, const double* rnu, const double* rnb, double frac) {
+  const int* ids = nullptr;
+  if (int rc = gsort(b, frac, &ids)) return rc;
+  const Batch B = batch_view(b);
+  const int64_t P = b->S.Ptot;
+  const int* start = (const int*)(b->ws + b->L.gstart);
+  double* Bs = (double*)(b->ws + b->L.gprep);
+  double* Os = Bs + (size_t)kNC * P;
+  before_launch(b, CLS_OTHER);
+  by_order(b->S.order, [&](auto O) {
+    pdl(b->stream, k_gprep<decltype(O)::value>, dim3((unsigned)((P + kThreads - 1) / kThreads)), B, b->pt, rnu, rnb,
+        frac, ids, b->W, Bs, Os, b->err);
+    return 0;
+  });
+  if (int rc = after_launch(b, "deposit prep kernel (particles anywhere)")) return rc;
+  const int64_t groups = kWarps / kGSplit, nb = ((int64_t)B.NZ + groups - 1) / groups;
+  before_launch(b, CLS_DEPOSIT);
+  by_order(b->S.order, [&](auto O) {
+    pdl(b->stream, k_gdeposit_sorted<decltype(O)::value>,
+        dim3((unsigned)(nb < 8 * kPersistBlocks ? nb : 8 * kPersistBlocks)), B, (const double*)b->W,
+        (const double*)Bs, (const double*)Os, start, b->At, b->err);
+    return 0;
+  });
+  return after_launch(b, "deposit kernel (particles anywhere)");
+}
+
 int launch_gstage(emu_box* b, int s, int dry) {
   const size_t P = (size_t)b->S.Ptot;
   const double* rnu = (s == 1) ? b->pt.rho : b->pt.stage;
   const double* rnb = (s == 1) ? b->pt.rhobar : b->pt.stage + 9 * P;
-  if (int rc = launch_gdeposit(b, 5, rnu, rnb, kStageFrac[s - 1], b->At)) return rc;
+  if (int rc = launch_gstep_deposit(b, rnu, rnb, kStageFrac[s - 1])) return rc;
   before_launch(b, CLS_RK);
   by_order(b->S.order, [&](auto O) {
     constexpr int R = decltype(O)::value;

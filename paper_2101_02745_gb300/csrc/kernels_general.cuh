@@ -265,6 +265,135 @@ k_gdeposit(Batch B, Parts pt, const double* __restrict__ r_nu, const double* __r
   if (bad & 2) atomicOr(err, ERR_NONFINITE);
 }
 
+// The step's deposit (MODE 5) in two parts.  k_gprep: one thread per sorted
+// position i (particle p = ids[i]): its weights at its stage position (as
+// k_gdeposit forms them), the 8 traceless components of B = N rho - Nbar
+// rhobar^* (Eq. 5) and its direction, stored in sorted order (Ws[q][i],
+// Bs[c][i], Os[a][i]) so that the deposit reads each particle's data once per
+// stage and contiguously instead of forming it for every cell that gathers it.
+template <int ORDER>
+__global__ void __launch_bounds__(kThreads)
+k_gprep(Batch B, Parts pt, const double* __restrict__ r_nu, const double* __restrict__ r_nb, double frac,
+        const int* __restrict__ ids, double* __restrict__ Ws, double* __restrict__ Bs, double* __restrict__ Os,
+        int* __restrict__ err) {
+  griddep_wait();
+  constexpr int NW = Sten<ORDER>::NW, NWS = Sten<ORDER>::NWS;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t P = B.Ptot;
+  if (i >= P) return;
+  const int64_t p = ids[i];
+  const int b = box_of_particle(B, p);
+  const BoxGeo& g = B.box[b];
+  const double ox = pt.ox[p], oy = pt.oy[p], oz = pt.oz[p];
+  const double zs = fma(frac * B.dt[b], g.c_light * oz, pt.z[p]);
+  const int h = wrapc((int)floor(zs * g.inv_dz), g.nz);
+  double wt[NW];
+  const int bad = shape_weights<ORDER>(zs, (double)h + 0.5, g.inv_dz, g.nz_d, wt);
+#pragma unroll
+  for (int q = 0; q < NWS; ++q) Ws[q * P + i] = wt[q];
+  Os[i] = ox;
+  Os[P + i] = oy;
+  Os[2 * P + i] = oz;
+  const double n1 = pt.N[p], n2 = pt.Nbar[p];
+  double bprev = 0.0;
+#pragma unroll
+  for (int c = 0; c < kNC; ++c) {
+    double bv;
+    if (c < 2) {
+      if (c == 0) bprev = fma(-n2, r_nb[p], n1 * r_nu[p]);
+      const double bn = fma(-n2, r_nb[(c + 1) * P + p], n1 * r_nu[(c + 1) * P + p]);
+      bv = bprev - bn;
+      bprev = bn;
+    } else {
+      const int k = c + 1;
+      const double xv = r_nu[k * P + p], yv = r_nb[k * P + p];
+      bv = (k == 4 || k == 6 || k == 8) ? fma(n2, yv, n1 * xv) : fma(-n2, yv, n1 * xv);
+    }
+    Bs[c * P + i] = bv;
+  }
+  if (bad) atomicOr(err, ERR_LATTICE);
+}
+
+// The step's deposit from k_gprep's sorted data: kGSplit warps per global
+// cell (one group of warps of a block), warp k of a group taking every
+// kGSplit-th run of 32 particles of each source cell; each warp's sums are
+// added over its lanes in a fixed order (a transpose through shared memory)
+// and the group's warps in warp order: no float atomics, the same order on
+// every run.
+// out as k_gdeposit<5>: the traceless potential (kNT rows x NZ, kappa / dV).
+constexpr int kGSplit = 4;
+template <int ORDER>
+__global__ void __launch_bounds__(kThreads)
+k_gdeposit_sorted(Batch B, const double* __restrict__ Ws, const double* __restrict__ Bs,
+                  const double* __restrict__ Os, const int* __restrict__ start, double* __restrict__ out,
+                  int* __restrict__ err) {
+  __shared__ double part[kWarps][kNT];
+  __shared__ double tr[kWarps][kLanes][17];   // a warp's sums, 16 rows at a time (padded: no bank conflicts)
+  griddep_wait();
+  constexpr int H = Sten<ORDER>::H;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int grp = wib / kGSplit, k = wib - grp * kGSplit;
+  constexpr int kGroups = kWarps / kGSplit;
+  const int64_t P = B.Ptot;
+  int bad = 0;
+  // every block runs the same number of rounds (it synchronises inside)
+  for (int64_t base = (int64_t)blockIdx.x * kGroups; base < B.NZ; base += (int64_t)gridDim.x * kGroups) {
+    const int64_t gc = base + grp;
+    double acc[kNT];
+#pragma unroll
+    for (int c = 0; c < kNT; ++c) acc[c] = 0.0;
+    const BoxGeo* g = nullptr;
+    if (gc < B.NZ) {
+      g = &B.box[box_of_cell(B, (int)gc)];
+      const int j = (int)gc - g->coff;
+      for (int o = -H; o <= H; ++o) {           // source cells j - o: their particles' weight slot H + o
+        if (ORDER == 0 && o != 0) continue;
+        const int sc = g->coff + wrapc(j - o, g->nz);
+        const int i0 = start[sc], i1 = start[sc + 1];
+        for (int i = i0 + k * kLanes + lane; i < i1; i += kGSplit * kLanes) {
+          const double w = ORDER == 0 ? 1.0 : __ldg(Ws + (int64_t)(H + o) * P + i);
+          const double wx = w * __ldg(Os + i), wy = w * __ldg(Os + P + i), wz = w * __ldg(Os + 2 * P + i);
+#pragma unroll
+          for (int c = 0; c < kNC; ++c) {
+            const double bv = __ldg(Bs + (int64_t)c * P + i);
+            acc[c] = fma(w, bv, acc[c]);
+            acc[kNC + c] = fma(wx, bv, acc[kNC + c]);
+            acc[2 * kNC + c] = fma(wy, bv, acc[2 * kNC + c]);
+            acc[3 * kNC + c] = fma(wz, bv, acc[3 * kNC + c]);
+          }
+        }
+      }
+    }
+    // the sum over the lanes of each of the 32 rows, 16 rows at a time through
+    // shared memory: lane l adds column l mod 16 over rows 16 (l / 16) .. +15,
+    // then the two halves (lanes l and l + 16) are added
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+#pragma unroll
+      for (int c = 0; c < 16; ++c) tr[wib][lane][c] = acc[half * 16 + c];
+      __syncwarp();
+      const int col = lane & 15, r0 = (lane >> 4) * 16;
+      double v = tr[wib][r0][col];
+#pragma unroll
+      for (int r = 1; r < 16; ++r) v += tr[wib][r0 + r][col];
+      v += __shfl_down_sync(kFull, v, 16);
+      if (lane < 16) part[wib][half * 16 + lane] = v;
+      __syncwarp();
+    }
+    __syncthreads();
+    if (gc < B.NZ && k == 0) {
+      const int c = lane;   // kNT = 32 rows, one per lane
+      double v = part[wib][c];
+      for (int q = 1; q < kGSplit; ++q) v += part[wib + q][c];
+      v *= g->kappa_dV;
+      bad |= !isfinite(v);
+      out[(int64_t)c * B.NZ + gc] = v;
+    }
+    __syncthreads();
+  }
+  if (bad) atomicOr(err, ERR_NONFINITE);
+}
+
 // H (traceless components, or all 9 with NC = 9) of particle p at its stage
 // position from the potential A (NC rows per moment): its weights and
 // G = A0 - Omega_p . A at the cells it reaches.
