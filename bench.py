@@ -382,21 +382,30 @@ def run_gpu(args, rank, world, local_rank):
     # ---- end to end through the public API with host buffers: every step the
     # state (z, rho, rhobar) comes from pinned host memory through the C ABI's
     # host-buffer path (emu_set_particles, on_host = 1) and the step's
-    # diagnostics are read back to the host (emu_diagnostics, on_host = 1).
-    # Two boxes with their own streams take turns (E.PingPongFeed): the next
-    # step's upload into the idle box overlaps the other box's step.
+    # diagnostics are read back to pinned host memory (emu_diagnostics into a
+    # device buffer, then a copy on the box's stream; all arrive before the
+    # timed region ends).  Two boxes with their own streams take turns
+    # (E.PingPongFeed): the next step's upload into the idle box overlaps the
+    # other box's step, and neither step waits for the other's diagnostics.
     host = box.get_host()
     pin = {k: torch.from_numpy(host[k]).pin_memory() for k in ("z", "rho", "rhobar")}
-    diag = torch.zeros(E.N_DIAG, dtype=torch.float64).pin_memory()
+    diag_dev = [torch.zeros(E.N_DIAG, dtype=torch.float64, device=device) for _ in range(2)]
+    diag = [torch.zeros(E.N_DIAG, dtype=torch.float64).pin_memory() for _ in range(2)]
     box2 = E.Box.from_workload(wl, device=device, stream=torch.cuda.Stream(device))
     if args.osc:
         box2.set_oscillation(W.oscillation(**OSC_BENCH))
     box2.apply_choice(tune_choice)   # the first box's tuned configuration
     feed = E.PingPongFeed([box, box2], pin)
 
+    def step_and_read(bx):
+        k = 0 if bx is box else 1
+        E.emu_step(bx.box, 1, dt)
+        E.emu_diagnostics(bx.box, diag_dev[k].data_ptr(), 0)
+        with torch.cuda.stream(bx.stream):
+            diag[k].copy_(diag_dev[k], non_blocking=True)
+
     def e2e_step():
-        b = feed.step(lambda bx: E.emu_step(bx.box, 1, dt))
-        E.emu_diagnostics(b.box, diag.data_ptr(), 1)
+        feed.step(step_and_read)
 
     # the host link's copy rate alone (the e2e step cannot beat the copy of its
     # inputs), timed on the second upload (the first touches the pinned pages)
