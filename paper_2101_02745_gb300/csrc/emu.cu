@@ -1095,7 +1095,7 @@ int launch3_pass(emu_box* b, const double* in, const double* wrow, double* out) 
 }
 
 // Deposit of the state (rnu, rnb) at positions x + frac dt c Omega with the
-// shift rows srow ([3][M]) into out; modes as k3_deposit.
+// shift rows srow ([3][M]) into out; modes as k3_deposit (0, 1, 2, 4).
 int launch3_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, const int* srow, double frac,
                     double* out) {
   const Box3 v = box3_view(b);
@@ -1111,17 +1111,15 @@ int launch3_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, 
       pdl(st, k3_deposit<1, R>, grid, v, x, y, z, N, Nb, rnu, rnb, b->dirtab, srow, frac, b->partial, b->err);
     else if (mode == 2)
       pdl(st, k3_deposit<2, R>, grid, v, x, y, z, N, Nb, rnu, rnb, b->dirtab, srow, frac, b->partial, b->err);
-    else if (mode == 4)
-      pdl(st, k3_deposit<4, R>, grid, v, x, y, z, N, Nb, rnu, rnb, b->dirtab, srow, frac, b->partial, b->err);
     else
-      pdl(st, k3_deposit<5, R>, grid, v, x, y, z, N, Nb, rnu, rnb, b->dirtab, srow, frac, b->partial, b->err);
+      pdl(st, k3_deposit<4, R>, grid, v, x, y, z, N, Nb, rnu, rnb, b->dirtab, srow, frac, b->partial, b->err);
     return 0;
   });
   if (int rc = after_launch(b, "3D deposit kernel")) return rc;
   const Batch B = row_view(b);
   const int split = combine_split(b->S, B.nw);
-  const int rows = mode == 5 ? kNT : kNA;
-  const int potential = (mode == 0 || mode == 5) ? 1 : 0;
+  const int rows = kNA;
+  const int potential = mode == 0 ? 1 : 0;
   before_launch(b, CLS_COMBINE);
   pdl(st, k_combine, dim3(combine_blocks(rows, B.NZ, split)), B, b->partial, out, rows, potential, split, b->err);
   return after_launch(b, "deposit combine kernel");

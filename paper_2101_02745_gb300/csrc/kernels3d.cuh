@@ -135,7 +135,7 @@ __device__ __forceinline__ int64_t site3(const Box3& b, int d, int jx, int jy, i
 
 // Deposit (Eq. 5) on the 3D grid, first phase.  MODE as k_deposit: 0 the
 // potential's B = N rho - Nbar rhobar^* (36 rows), 1 N rho, 2 Nbar rhobar,
-// 4 the diagnostics' n, f_x, nbar, fbar_x, 5 the traceless potential (32 rows).
+// 4 the diagnostics' n, f_x, nbar, fbar_x.
 // Positions x + frac dt c Omega.  srow: the shift rows (3 x M) of these positions.
 template <int MODE, int ORDER>
 __global__ void __launch_bounds__(kThreads, 2)
@@ -145,7 +145,7 @@ k3_deposit(Box3 b, const double* __restrict__ x, const double* __restrict__ y, c
            double frac, double* __restrict__ partial, int* __restrict__ err) {
   griddep_wait();
   constexpr int H = Sten<ORDER>::H, T = Sten<ORDER>::T, NW = Sten<ORDER>::NW;
-  constexpr int NA = MODE == 5 ? kNT : kNA;
+  constexpr int NA = kNA;
   const int lane = threadIdx.x & 31;
   const int64_t w = logical_warp();
   const int64_t u0 = unit3_begin(w, b), u1 = unit3_begin(w + 1, b);
@@ -171,7 +171,7 @@ k3_deposit(Box3 b, const double* __restrict__ x, const double* __restrict__ y, c
       const double ox = __ldg(dirtab + d), oy = __ldg(dirtab + M + d), oz = __ldg(dirtab + 2 * M + d);
       const double vx = __ldg(dirtab + 3 * M + d), vy = __ldg(dirtab + 4 * M + d), vz = __ldg(dirtab + 5 * M + d);
       const int sx = __ldg(srow + d), sy = __ldg(srow + M + d), sz = __ldg(srow + 2 * M + d);
-      constexpr int NS = MODE == 4 ? 18 : MODE == 5 ? kNC : 9;   // components summed over neighbour rows
+      constexpr int NS = MODE == 4 ? 18 : 9;   // components summed over neighbour rows
       double S[NS];
 #pragma unroll
       for (int c = 0; c < NS; ++c) S[c] = 0.0;
@@ -189,25 +189,7 @@ k3_deposit(Box3 b, const double* __restrict__ x, const double* __restrict__ y, c
           const double f = pick(wx, H - a) * pick(wy, H - bb);   // this particle's share of the warp's row
           Spread<ORDER> spread;
           spread.init(wz);
-          if constexpr (MODE == 5) {
-            const double n1 = f * __ldg(N + p), n2 = f * __ldg(Nbar + p);
-            double bprev = 0.0;
-#pragma unroll
-            for (int c = 0; c < kNC; ++c) {
-              double bv;
-              if (c < 2) {
-                if (c == 0) bprev = fma(-n2, __ldg(r_nb + p), n1 * __ldg(r_nu + p));
-                const double bn = fma(-n2, __ldg(r_nb + (c + 1) * P + p), n1 * __ldg(r_nu + (c + 1) * P + p));
-                bv = bprev - bn;
-                bprev = bn;
-              } else {
-                const int k = c + 1;
-                const double xv = __ldg(r_nu + k * P + p), yv = __ldg(r_nb + k * P + p);
-                bv = (k == 4 || k == 6 || k == 8) ? fma(n2, yv, n1 * xv) : fma(-n2, yv, n1 * xv);
-              }
-              S[c] += spread.apply(bv);
-            }
-          } else if constexpr (MODE == 4) {
+          if constexpr (MODE == 4) {
 #pragma unroll
             for (int k = 0; k < 9; ++k) {
               S[k] += spread.apply(f * __ldg(N + p) * __ldg(r_nu + k * P + p));
@@ -233,15 +215,7 @@ k3_deposit(Box3 b, const double* __restrict__ x, const double* __restrict__ y, c
         }
       }
       // moments of this direction: (1, Omega) x S (Omega is the direction's)
-      if constexpr (MODE == 5) {
-#pragma unroll
-        for (int c = 0; c < kNC; ++c) {
-          acc[c] += S[c];
-          acc[kNC + c] = fma(ox, S[c], acc[kNC + c]);
-          acc[2 * kNC + c] = fma(oy, S[c], acc[2 * kNC + c]);
-          acc[3 * kNC + c] = fma(oz, S[c], acc[3 * kNC + c]);
-        }
-      } else if constexpr (MODE == 4) {
+      if constexpr (MODE == 4) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
           acc[k] += S[k];
