@@ -975,6 +975,17 @@ __device__ __forceinline__ void ring_cell_G(const double* A, int NZ, int coff, i
                    fma(-ox, ldd<COH>(Aj + (int64_t)(kNC + c) * NZ), ldd<COH>(Aj + (int64_t)c * NZ))));
 }
 
+// Component c of G at one cell, the arithmetic of ring_cell_G (for one lane
+// per component).
+template <bool COH>
+__device__ __forceinline__ double cell_G_component(const double* A, int NZ, int coff, int cell, int c, double ox,
+                                                   double oy, double oz) {
+  const double* Aj = A + coff + cell;
+  return fma(-oz, ldd<COH>(Aj + (int64_t)(3 * kNC + c) * NZ),
+             fma(-oy, ldd<COH>(Aj + (int64_t)(2 * kNC + c) * NZ),
+                 fma(-ox, ldd<COH>(Aj + (int64_t)(kNC + c) * NZ), ldd<COH>(Aj + (int64_t)c * NZ))));
+}
+
 // Cell index on a ring of nz cells for cells within two rings of it (the
 // stencil reaches at most two cells past a tile; rings may be shorter).
 __device__ __forceinline__ int ring_wrap(int cell, int nz) {
@@ -1048,17 +1059,14 @@ __device__ __forceinline__ void rk32_phase(const Batch& B, int64_t w, const Part
       const double ox = __ldg(dirtab + pgd), oy = __ldg(dirtab + MT + pgd), oz = __ldg(dirtab + 2 * MT + pgd);
       // the H cells right of the finished unit's last cell: from this unit's
       // first cells when it continues the ring and has them, else computed
+      // (lane k < 8 forms component k, in ring_cell_G's order)
 #pragma unroll
       for (int o = 0; o < H; ++o) {
         if (!(next_in_ring && (H == 1 || o < cn))) {   // (a unit that continues a ring has a first cell)
-          double G[kNC];
           const int cell = pt_ * kLanes + pn + o;
-          ring_cell_G<COH>(A, NZ, g.coff, H == 1 ? (cell >= g.nz ? cell - g.nz : cell) : ring_wrap(cell, g.nz), ox,
-                           oy, oz, G);
-          if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < kNC; ++k) edge[wib][1][o][k] = G[k];
-          }
+          if (lane < kNC)
+            edge[wib][1][o][lane] = cell_G_component<COH>(
+                A, NZ, g.coff, H == 1 ? (cell >= g.nz ? cell - g.nz : cell) : ring_wrap(cell, g.nz), lane, ox, oy, oz);
         }
       }
       __syncwarp();
@@ -1130,14 +1138,11 @@ __device__ __forceinline__ void rk32_phase(const Batch& B, int64_t w, const Part
         const BoxGeo& g = B.box[cb];
 #pragma unroll
         for (int o = 1; o <= H; ++o) {
-          double G[kNC];
           const int cell = ct * kLanes - o;
-          ring_cell_G<COH>(A, NZ, g.coff, H == 1 ? (cell < 0 ? cell + g.nz : cell) : ring_wrap(cell, g.nz),
-                           __ldg(dirtab + cgd), __ldg(dirtab + MT + cgd), __ldg(dirtab + 2 * MT + cgd), G);
-          if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < kNC; ++k) edge[wib][0][o - 1][k] = G[k];
-          }
+          if (lane < kNC)
+            edge[wib][0][o - 1][lane] = cell_G_component<COH>(
+                A, NZ, g.coff, H == 1 ? (cell < 0 ? cell + g.nz : cell) : ring_wrap(cell, g.nz), lane,
+                __ldg(dirtab + cgd), __ldg(dirtab + MT + cgd), __ldg(dirtab + 2 * MT + cgd));
         }
       }
       __syncwarp();
