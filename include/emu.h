@@ -134,10 +134,17 @@ int emu_init_particles(emu_box* box, const double* n_nu, const double* n_nubar, 
 
 /* Copy particle fields in from (set) or out to (get) caller buffers laid out
  * like emu_particles (rho/rhobar as [9][P]).  Any pointer may be NULL to skip
- * that field.  on_host = 1: host pointers (the call synchronises for get);
- * 0: device pointers.  emu_set_particles re-validates the rings; with
- * positions from host memory or with directions it also chooses the particle
- * layout (see emu_set_layout), which synchronises the stream. */
+ * that field.  on_host = 1: host pointers; the call returns once the copy is
+ * done (it synchronises the box's stream).  0: device pointers.
+ * emu_set_particles also takes on_host = 2: host pointers, asynchronous: the
+ * copies are enqueued on the box's stream and the call returns at once
+ * (pinned host memory lets them overlap other work); the caller keeps the
+ * host arrays valid and unchanged until the stream has passed the copies
+ * (an event recorded after the call, or a later synchronising call).
+ * emu_set_particles re-validates the rings; with positions from host memory
+ * or with directions it also chooses the particle layout when the layout is
+ * -1 (see emu_set_layout), which synchronises the stream whatever on_host is;
+ * with a fixed layout (0 or 1) it does not check. */
 int emu_set_particles(emu_box* box, const double* z, const double* ox, const double* oy,
                       const double* oz, const double* N, const double* Nbar, const double* rho,
                       const double* rhobar, int on_host);

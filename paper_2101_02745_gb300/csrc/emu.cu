@@ -1530,6 +1530,7 @@ int emu_batch_init_particles(emu_box* b, const double* n_nu, const double* n_nub
 int emu_set_particles(emu_box* b, const double* z, const double* ox, const double* oy, const double* oz,
                       const double* N, const double* Nbar, const double* rho, const double* rhobar, int on_host) {
   if (int rc = check_bound(b)) return rc;
+  if (on_host < 0 || on_host > 2) return fail(b, EMU_EINVAL, "on_host must be 0, 1 or 2");
   const size_t P = (size_t)b->S.Ptot;
   const cudaMemcpyKind kind = on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   const double* src[8] = {z, ox, oy, oz, N, Nbar, rho, rhobar};
@@ -1548,8 +1549,8 @@ int emu_set_particles(emu_box* b, const double* z, const double* ox, const doubl
     if (int rc = choose_layout(b)) return rc;
   if ((ox || oy || oz) && !b->general)
     if (int rc = rebuild_dirtable(b)) return rc;
-  if (on_host) return cuda_check(b, cudaStreamSynchronize(b->stream), "synchronise after copy in");
-  return EMU_OK;
+  if (on_host == 1) return cuda_check(b, cudaStreamSynchronize(b->stream), "synchronise after copy in");
+  return EMU_OK;   // (on_host = 2: the copies stay in flight on the stream)
 }
 
 int emu_get_particles(emu_box* b, double* z, double* ox, double* oy, double* oz, double* N, double* Nbar,

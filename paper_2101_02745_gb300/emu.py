@@ -756,8 +756,8 @@ class Box:
 class PingPongFeed:
     """Per-step particle state from host memory for two boxes of one
     configuration that take turns, through the host-buffer path of the C ABI
-    (emu_set_particles with on_host = 1).  While one box steps, the next step's
-    state (z, rho, rhobar) is copied from the host into the other box's
+    (emu_set_particles with host pointers).  While one box steps, the next
+    step's state (z, rho, rhobar) is copied from the host into the other box's
     particle arrays on that box's own stream, so the copy overlaps the step.
     The boxes need distinct streams; the host arrays should be pinned (page-
     locked) for the copy to run asynchronously.
@@ -765,18 +765,22 @@ class PingPongFeed:
     `prime()` installs the first step's state in box 0; `step(enqueue)` calls
     enqueue(box) on the box that holds this step's state (the caller enqueues
     that box's work, asynchronously), then installs the next step's state in
-    the other box (the call returns once that copy is done) and returns the box
-    that was stepped."""
+    the other box and returns the box that was stepped.  The install returns
+    once the copy is done (on_host = 1), or with asynchronous=True once it is
+    enqueued (on_host = 2): then the host arrays must stay unchanged until the
+    boxes' streams have passed the copies, and the boxes should have a fixed
+    particle layout (emu_set_layout 0 or 1), since choosing one synchronises."""
 
     KEYS = ("z", "rho", "rhobar")
 
-    def __init__(self, boxes, host: dict):
+    def __init__(self, boxes, host: dict, asynchronous: bool = False):
         if len(boxes) != 2 or boxes[0].P != boxes[1].P:
             raise ValueError("two boxes of the same configuration")
         if boxes[0].stream == boxes[1].stream:
             raise ValueError("the two boxes need distinct streams")
         self.boxes = list(boxes)
         self.host = {k: host[k] for k in self.KEYS}
+        self.on_host = 2 if asynchronous else 1
         self.turn = 0
 
     @staticmethod
@@ -791,7 +795,7 @@ class PingPongFeed:
     def install(self, k: int):
         h = self.host
         emu_set_particles(self.boxes[k].box, self._ptr(h["z"]), None, None, None, None, None, self._ptr(h["rho"]),
-                          self._ptr(h["rhobar"]), 1)
+                          self._ptr(h["rhobar"]), self.on_host)
 
     def prime(self):
         self.install(0)
