@@ -134,7 +134,7 @@ const char* make_shape(const emu_config* cfgs, int nbox, Shape& S) {
 }
 
 struct Layout {
-  size_t geo, dts, nmax, A, At, mom, partial, W, err, dirtab, shift, shift2, bar, species, dirs, diag, scalar, total;
+  size_t geo, dts, nmax, A, At, mom, partial, W, err, dirtab, shift, wtab, bar, species, dirs, diag, scalar, total;
   size_t rowgeo = 0;   // 3D boxes: one descriptor per cell row (the deposit combination's batch view)
   // particles anywhere (kernels_general.cuh): sort keys and values (two of
   // each), digit histogram, cell starts, lattice-check flag
@@ -165,7 +165,7 @@ Layout layout(const Shape& S) {
   L.dirtab = take(sizeof(double) * 4 * MT);
   L.shift = take(sizeof(int) * 5 * MT);    // rows: the four stages, the next step's first (step form 2)
   L.frame = take(sizeof(double) * (size_t)S.NT32 * kSlotF);
-  L.shift2 = take(sizeof(int) * 4 * MT);   // the fused step's shift rows of the next step
+  L.wtab = take(sizeof(double) * 5 * kWSlots * MT);   // the rings' shape weights at each shift row
   L.bar = take(sizeof(unsigned) * 2);       // the fused step's grid barrier: arrival word, abort word
   L.species = take(sizeof(double) * 8 * NZ);
   L.dirs = take(sizeof(double) * 3 * MT);
@@ -205,7 +205,8 @@ struct emu_box {
   double *dts = nullptr, *nmax = nullptr, *A = nullptr, *At = nullptr, *mom = nullptr, *partial = nullptr,
          *W = nullptr, *dirtab = nullptr, *species = nullptr, *dirs = nullptr, *diag = nullptr, *scalar = nullptr,
          *frame = nullptr;
-  int *err = nullptr, *shift = nullptr, *shift2 = nullptr;
+  int *err = nullptr, *shift = nullptr;
+  double* wtab = nullptr;   // the rings' shape weights at each shift row [5 x kWSlots][MT] (k_shifts)
   unsigned* bar = nullptr;
   int blocks = kPersistBlocks;  // grid of the step kernels (autotuned); its warps split the units
   int rk_form = -1;             // RK stage: 0 halo-lane, 1 32-cell, -1 by units per warp (autotuned)
@@ -492,14 +493,40 @@ void pdl_smem(cudaStream_t st, void (*kernel)(KArgs...), dim3 grid, int smem, Ar
   (void)cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
-// nrows = 5: the four stages' rows and the next step's first (k_shifts).
+// Whether the deposit takes the rings' weights from the weight table: when
+// every warp walks at least 4 units (on boxes whose warps take one or two
+// units the table's loads lengthen each warp's chain more than the weights'
+// arithmetic they replace: 256 x 96 +4%, 2048 x 1000 -1.5% per step).  The
+// rule depends only on the batch and the grid, as the summation order does.
+bool use_wtab(const emu_box* b) {
+  const Batch B = batch_view(b);
+  return B.U >= 4 * (int64_t)B.nw;
+}
+
+// nrows = 5: the four stages' rows and the next step's first (k_shifts); the
+// rings' shape weights at every row go to the weight table.
 int launch_shifts(emu_box* b, const double* fracs, int nrows) {
   Fracs f{};
   for (int s = 0; s < nrows && s < 4; ++s) f.v[s] = fracs[s];
-  const int blocks = (b->S.MT + kThreads - 1) / kThreads;
+  const int blocks = (int)(((int64_t)b->S.MT * nrows + kThreads - 1) / kThreads);
   before_launch(b, CLS_SHIFT);
-  pdl(b->stream, k_shifts, dim3(blocks), batch_view(b), b->pt.z, b->dirtab, f, nrows, b->shift);
+  by_order(b->S.order, [&](auto O) {
+    pdl(b->stream, k_shifts<decltype(O)::value>, dim3(blocks), batch_view(b), b->pt.z, b->dirtab, f, nrows, b->shift,
+        use_wtab(b) ? b->wtab : nullptr);
+    return 0;
+  });
   return after_launch(b, "shift kernel");
+}
+
+// The weight-table row matching a shift row of the box's table (nullptr for
+// other shift rows, or when the table is not used: the deposit then forms
+// each particle's weights).
+const double* weight_row(const emu_box* b, const int* shift_row) {
+  if (!use_wtab(b)) return nullptr;
+  const int64_t MT = b->S.MT;
+  const int64_t off = shift_row - b->shift;
+  if (MT <= 0 || off < 0 || off >= 5 * MT || off % MT != 0) return nullptr;
+  return b->wtab + (off / MT) * kWSlots * MT;
 }
 
 // Deposit (two launches) of the state (rnu, rnb) at positions z + frac dt_b v_z
@@ -515,26 +542,31 @@ int launch_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, c
   const double* z = b->pt.z;
   const double* N = b->pt.N;
   const double* Nb = b->pt.Nbar;
+  const double* wrow = weight_row(b, shift_row);
   by_order(b->S.order, [&](auto O) {
     constexpr int R = decltype(O)::value;
     if (mode == 0)
-      pdl(st, k_deposit<0, R>, grid, B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
-          W, b->err);
+      pdl(st, k_deposit<0, R>, grid, B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, wrow, frac, b->partial, W, b->err);
     else if (mode == 1)
-      pdl(st, k_deposit<1, R>, grid, B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
-          nullptr, b->err);
+      pdl(st, k_deposit<1, R>, grid, B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, wrow, frac, b->partial, nullptr,
+          b->err);
     else if (mode == 2)
-      pdl(st, k_deposit<2, R>, grid, B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
+      pdl(st, k_deposit<2, R>, grid, B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, wrow, frac, b->partial, nullptr,
+          b->err);
+    else if (mode == 3 && wrow != nullptr)   // (the adjoint's deposit: the weights its forward step used)
+      pdl(st, k_deposit<3, R, true>, grid, B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, wrow, frac, b->partial,
           nullptr, b->err);
     else if (mode == 3)
-      pdl(st, k_deposit<3, R>, grid, B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
-          nullptr, b->err);
+      pdl(st, k_deposit<3, R>, grid, B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, wrow, frac, b->partial, nullptr,
+          b->err);
     else if (mode == 4)
-      pdl(st, k_deposit<4, R>, grid, B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
-          nullptr, b->err);
+      pdl(st, k_deposit<4, R>, grid, B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, wrow, frac, b->partial, nullptr,
+          b->err);
+    else if (wrow != nullptr)
+      pdl(st, k_deposit<5, R, true>, grid, B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, wrow, frac, b->partial, W,
+          b->err);
     else
-      pdl(st, k_deposit<5, R>, grid, B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, frac, b->partial,
-          W, b->err);
+      pdl(st, k_deposit<5, R>, grid, B, z, N, Nb, rnu, rnb, b->dirtab, shift_row, wrow, frac, b->partial, W, b->err);
     return 0;
   });
   if (int rc = after_launch(b, "deposit kernel")) return rc;
@@ -607,7 +639,7 @@ int launch_fused(emu_box* b, int dry, int64_t nsteps) {
   StepArgs a{};
   a.dirtab = b->dirtab;
   a.shift = b->shift;
-  a.shift2 = b->shift2;
+  a.wtab = use_wtab(b) ? b->wtab : nullptr;
   a.W = b->W;
   a.At = b->At;
   a.partial = b->partial;
@@ -1005,7 +1037,7 @@ Layout layout3(const Shape& S, size_t nrows) {
   L.err = take(sizeof(int));
   L.dirtab = take(sizeof(double) * 6 * MT);
   L.shift = take(sizeof(int) * 12 * MT);
-  L.shift2 = take(0);
+  L.wtab = take(0);
   L.bar = take(sizeof(unsigned) * 2);
   L.species = take(sizeof(double) * 8 * NZ);
   L.dirs = take(sizeof(double) * 3 * MT);
@@ -1489,7 +1521,7 @@ int bind_common(emu_box* b, const emu_particles* parts, void* workspace, int64_t
   b->err = (int*)(b->ws + L.err);
   b->dirtab = (double*)(b->ws + L.dirtab);
   b->shift = (int*)(b->ws + L.shift);
-  b->shift2 = (int*)(b->ws + L.shift2);
+  b->wtab = (double*)(b->ws + L.wtab);
   b->bar = (unsigned*)(b->ws + L.bar);
   b->rows_d = b->is3d ? (BoxGeo*)(b->ws + L.rowgeo) : nullptr;
   b->species = (double*)(b->ws + L.species);
@@ -2468,10 +2500,10 @@ extern "C" int emu_deposit_static(const emu_config* cfg, const double* z, const 
   if (int rc = check(cudaGetLastError(), "direction table kernel")) return rc;
   Fracs f{};
   f.v[0] = 1.0;
-  k_shifts<<<(S.MT + kThreads - 1) / kThreads, kThreads, 0, st>>>(B, z, dirtab, f, 1, shift);
+  k_shifts<2><<<(S.MT + kThreads - 1) / kThreads, kThreads, 0, st>>>(B, z, dirtab, f, 1, shift, nullptr);
   if (int rc = check(cudaGetLastError(), "shift kernel")) return rc;
-  k_deposit<0, 2><<<dim3(kPersistBlocks), kThreads, 0, st>>>(B, z, N, Nbar, rho, rhobar, dirtab, shift, 1.0, partial,
-                                                            nullptr, err);
+  k_deposit<0, 2><<<dim3(kPersistBlocks), kThreads, 0, st>>>(B, z, N, Nbar, rho, rhobar, dirtab, shift, nullptr, 1.0,
+                                                            partial, nullptr, err);
   if (int rc = check(cudaGetLastError(), "deposit kernel")) return rc;
   const int split = combine_split(S, B.nw);
   k_combine<<<combine_blocks(kNA, S.NZ, split), kThreads, 0, st>>>(B, partial, A_out, kNA, 1, split, err);

@@ -50,6 +50,7 @@ constexpr int kNA = 36;            // components of the grid potential (and of a
 constexpr int kNT = 32;
 constexpr int kNC = 8;             // components of one traceless matrix
 constexpr int kNM = 72;            // components of the per-species moments
+constexpr int kWSlots = 5;         // weight slots per stage row of the direction weight table (the cubic shape's 5)
 constexpr int kSlot = kNA * kTileMax; // doubles in one warp's partial sums for one tile
 constexpr double kLatticeTol = 1e-6;
 constexpr unsigned kFull = 0xffffffffu;
@@ -427,7 +428,9 @@ __global__ void k_dirtable(Batch B, Parts pt, double* __restrict__ dirtab, int* 
 // the cell of the ring's first particle at z + frac[s] dt_b v_z ([nrows][MT]).
 // A fifth row (nrows = 5) holds the shift of the next step's first stage: the
 // cell of wrap(z + dt_b v_z), the position stage 4 writes, computed exactly as
-// the RK stage computes it.
+// the RK stage computes it.  Beside each shift row the ring's shape weights
+// (the direction weight table, kWSlots per row): a ring translates rigidly, so
+// all its particles sit at its first particle's offset inside their cells.
 struct Fracs { double v[4]; };
 
 // Position offset of RK stage s (0-based), in units of dt (Sec. 2.3, classic tableau).
@@ -438,25 +441,44 @@ __device__ __forceinline__ int lattice_cell(double z0, double frac_dt, double vz
   return wrapc((int)floor(zs * g.inv_dz), g.nz);
 }
 
-template <bool COH>
-__device__ __forceinline__ void shifts_phase(const Batch& B, int gd, const double* z, const double* __restrict__ dirtab,
-                                             const Fracs& fr, int nrows, int* shift) {
-  if (gd >= B.MT) return;
+// Row `row` of the tables for direction gd: the shift (the cell of the ring's
+// first particle at its row position) and, with wtab, that particle's shape
+// weights there.  Rows 0-3: z + frac[row] dt_b v_z; row 4: wrap(z + dt_b v_z).
+template <bool COH, int ORDER>
+__device__ __forceinline__ void shifts_row(const Batch& B, int gd, const double* z, const double* __restrict__ dirtab,
+                                           const Fracs& fr, int row, int* shift, double* wtab) {
   const int b = box_of_direction(B, gd);
   const BoxGeo& g = B.box[b];
   const double z0 = ldp<COH>(z + g.poff + (int64_t)(gd - g.doff) * g.nz);
   const double vz = dirtab[3 * B.MT + gd];
   const double dt = B.dt[b];
+  const double zs = row < 4 ? fma(fr.v[row] * dt, vz, z0) : wrap_z(fma(dt, vz, z0), g.Lz);
+  const int cell = lattice_cell(zs, 0.0, vz, g);
+  shift[row * B.MT + gd] = cell;
+  if (wtab != nullptr) {   // the ring's weights: its first particle's, at the cell the shift assigns it
+    double w[Sten<ORDER>::NW];
+    (void)shape_weights<ORDER>(zs, (double)cell + 0.5, g.inv_dz, g.nz_d, w);
 #pragma unroll
-  for (int s = 0; s < 4; ++s)
-    if (s < nrows) shift[s * B.MT + gd] = lattice_cell(z0, fr.v[s] * dt, vz, g);
-  if (nrows > 4) shift[4 * B.MT + gd] = lattice_cell(wrap_z(fma(dt, vz, z0), g.Lz), 0.0, vz, g);
+    for (int q = 0; q < Sten<ORDER>::NWS; ++q) wtab[(row * kWSlots + q) * B.MT + gd] = w[q];
+  }
 }
 
+template <bool COH, int ORDER>
+__device__ __forceinline__ void shifts_phase(const Batch& B, int gd, const double* z, const double* __restrict__ dirtab,
+                                             const Fracs& fr, int nrows, int* shift, double* wtab) {
+  if (gd >= B.MT) return;
+  for (int row = 0; row < nrows && row < 5; ++row) shifts_row<COH, ORDER>(B, gd, z, dirtab, fr, row, shift, wtab);
+}
+
+// One thread per (direction, row): the rows' chains run side by side.
+template <int ORDER>
 __global__ void k_shifts(Batch B, const double* __restrict__ z, const double* __restrict__ dirtab, Fracs fr,
-                         int nrows, int* __restrict__ shift) {
+                         int nrows, int* __restrict__ shift, double* __restrict__ wtab) {
   griddep_wait();
-  shifts_phase<false>(B, blockIdx.x * blockDim.x + threadIdx.x, z, dirtab, fr, nrows, shift);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = t / B.MT, gd = t - row * B.MT;
+  if (row >= nrows) return;
+  shifts_row<false, ORDER>(B, gd, z, dirtab, fr, row, shift, wtab);
 }
 
 // A warp's sums for one tile go to slot (warp + global tile) of the partial
@@ -484,12 +506,17 @@ __device__ __forceinline__ void flush_tile(const double (&acc)[NA], int64_t gtil
 // w_pj (1, Omega_p) B_p over directions in registers (lane l owns cell
 // tile * T - H + l) and writing one partial per tile it touches; MODES 0 and 5
 // also store every particle's weights for the RK stage.  Positions: z + frac dt_b v_z.
+// With wrow (the stage's row of the direction weight table k_shifts writes)
+// every particle of a ring takes the ring's weights: the ring translates
+// rigidly, so its particles share their offset inside the cells (to
+// rounding); each particle's position is still checked against its cell.
 template <int MODE, int ORDER, bool COH>
 __device__ __forceinline__ void deposit_phase(const Batch& B, int64_t w, int lane, const double* z,
                                               const double* __restrict__ N, const double* __restrict__ Nbar,
                                               const double* r_nu, const double* r_nb,
-                                              const double* __restrict__ dirtab, const int* shift, double frac,
-                                              double* __restrict__ partial, double* W, int* err) {
+                                              const double* __restrict__ dirtab, const int* shift,
+                                              const double* wrow, double frac, double* __restrict__ partial,
+                                              double* W, int* err) {
   const int64_t u0 = unit_begin(w, B), u1 = unit_begin(w + 1, B);
   if (u0 >= u1) return;
   const int64_t P = B.Ptot;
@@ -523,7 +550,18 @@ __device__ __forceinline__ void deposit_phase(const Batch& B, int64_t w, int lan
       const double vz = __ldg(dirtab + 3 * MT + gd);
       const int64_t p = pbase + (int64_t)d * nz + wrapc(j - ldi<COH>(shift + gd), nz);
       double wt[Sten<ORDER>::NW];
-      bad |= shape_weights<ORDER>(fma(pos_dt, vz, ldd<COH>(z + p)), hp, __ldg(&g.inv_dz), __ldg(&g.nz_d), wt);
+      const double zs = fma(pos_dt, vz, ldd<COH>(z + p));
+      if (wrow != nullptr) {
+        bad |= off_site(zs, hp, __ldg(&g.inv_dz), __ldg(&g.nz_d));
+        if constexpr (ORDER == 0) {
+          wt[0] = 0.0; wt[1] = 1.0; wt[2] = 0.0;
+        } else {
+#pragma unroll
+          for (int q = 0; q < Sten<ORDER>::NW; ++q) wt[q] = ldp<COH>(wrow + q * B.MT + gd);
+        }
+      } else {
+        bad |= shape_weights<ORDER>(zs, hp, __ldg(&g.inv_dz), __ldg(&g.nz_d), wt);
+      }
       if ((MODE == 0 || MODE == 5) && W != nullptr && own) {   // the RK stage of these positions reads them back
 #pragma unroll
         for (int q = 0; q < Sten<ORDER>::NWS; ++q) W[q * P + p] = wt[q];
@@ -594,15 +632,17 @@ __device__ __forceinline__ void deposit_phase(const Batch& B, int64_t w, int lan
   if (bad) atomicOr(err, ERR_LATTICE);
 }
 
-template <int MODE, int ORDER>
+// TAB: the rings' weights from the weight row wrow; otherwise each
+// particle's own (wrow unused, and the table's code compiled out).
+template <int MODE, int ORDER, bool TAB = false>
 __global__ void __launch_bounds__(kThreads, 2)
 k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, const double* __restrict__ Nbar,
           const double* __restrict__ r_nu, const double* __restrict__ r_nb, const double* __restrict__ dirtab,
-          const int* __restrict__ shift, double frac, double* __restrict__ partial, double* __restrict__ W,
-          int* __restrict__ err) {
+          const int* __restrict__ shift, const double* __restrict__ wrow, double frac, double* __restrict__ partial,
+          double* __restrict__ W, int* __restrict__ err) {
   griddep_wait();
-  deposit_phase<MODE, ORDER, false>(B, logical_warp(), threadIdx.x & 31, z, N, Nbar, r_nu, r_nb, dirtab, shift, frac,
-                                    partial, W, err);
+  deposit_phase<MODE, ORDER, false>(B, logical_warp(), threadIdx.x & 31, z, N, Nbar, r_nu, r_nb, dirtab, shift,
+                                    TAB ? wrow : nullptr, frac, partial, W, err);
 }
 
 // Deposit, second phase: fixed-order sum of the per-warp partials.
@@ -724,9 +764,7 @@ k_interpolate(Batch B, const double* __restrict__ z, const double* __restrict__ 
 // Kbar = -i[Hbar, rhobar] (Eq. 4) with Hbar = -H^* (plus the vacuum and
 // matter terms with POT), then the accumulator and next stage state (stage 4:
 // the new state and position).  vz points at the particle's v_z in the
-// direction table.  With shift_next (fused step), the first particle of each
-// ring also writes the lattice shifts of the next step's four stages
-// ([4][MTtot], as k_shifts computes them from its new position).  With KEEP
+// direction table.  With KEEP
 // the state it stores (the next stage's, or at stage 4 the new one), rho and
 // rhobar, is also combined as B = n1 rho - n2 rhobar^* into keep[9] (the
 // arithmetic of the deposit, Eq. 5) and the new position returned in *zkeep.
@@ -734,8 +772,8 @@ template <bool POT, bool COH, bool KEEP = false>
 __device__ __forceinline__ void rk_particle(const BoxGeo& g, const Parts& pt, const double* src_b, int64_t P,
                                             int64_t p, int s, int dry, double bdt, double cdt, double dtb,
                                             const double* __restrict__ vz, double (&Hm)[kNC], const double (&r)[9],
-                                            int* shift_next, int gd, int MTtot, double* keep = nullptr,
-                                            double* zkeep = nullptr, double n1 = 0.0, double n2 = 0.0) {
+                                            double* keep = nullptr, double* zkeep = nullptr, double n1 = 0.0,
+                                            double n2 = 0.0) {
   const double bdt2 = 2.0 * bdt, cdt2 = 2.0 * cdt;   // diagonal K are returned halved
   // Hm: H in the traceless components.  Antineutrinos: Hbar = -H^* (diagonal
   // differences and real parts flip sign, imaginary parts stay)
@@ -848,10 +886,6 @@ __device__ __forceinline__ void rk_particle(const BoxGeo& g, const Parts& pt, co
     if (dry) pt.stage[p] = zn;  // (only to keep the work of the real stage)
     else pt.z[p] = zn;
     if constexpr (KEEP) *zkeep = zn;
-    if (shift_next != nullptr && p == g.poff + (int64_t)(gd - g.doff) * g.nz) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) shift_next[q * MTtot + gd] = lattice_cell(zn, stage_frac(q) * dtb, vzv, g);
-    }
   }
 }
 
@@ -873,7 +907,7 @@ __device__ __forceinline__ void rk_particle(const BoxGeo& g, const Parts& pt, co
 template <bool POT, int ORDER, bool COH>
 __device__ __forceinline__ void rk_phase(const Batch& B, int64_t w, int lane, const Parts& pt, const double* W,
                                          const double* __restrict__ dirtab, const int* shift, const double* A,
-                                         const double* stage_src, int s, int dry, int* shift_next) {
+                                         const double* stage_src, int s, int dry) {
   const int64_t u0 = unit_begin(w, B), u1 = unit_begin(w + 1, B);
   if (u0 >= u1) return;
   const int64_t P = B.Ptot;
@@ -941,8 +975,7 @@ __device__ __forceinline__ void rk_phase(const Batch& B, int64_t w, int lane, co
       Hm[c] = gather<ORDER>(wt, G);
     }
     if (!active) continue;
-    rk_particle<POT, COH>(g, pt, src_b, P, p, s, dry, bdt, cdt, B.dt[b], dirtab + 3 * MT + gd, Hm, r, shift_next,
-                          gd, MT);
+    rk_particle<POT, COH>(g, pt, src_b, P, p, s, dry, bdt, cdt, B.dt[b], dirtab + 3 * MT + gd, Hm, r);
   }
 }
 
@@ -951,8 +984,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 k_rk_stage(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
            const int* __restrict__ shift, const double* __restrict__ A, const double* stage_src, int s, int dry) {
   griddep_wait();
-  rk_phase<POT, ORDER, false>(B, logical_warp(), threadIdx.x & 31, pt, W, dirtab, shift, A, stage_src, s, dry,
-                              nullptr);
+  rk_phase<POT, ORDER, false>(B, logical_warp(), threadIdx.x & 31, pt, W, dirtab, shift, A, stage_src, s, dry);
 }
 
 // The RK stage with 32 cells per warp: the same arithmetic as k_rk_stage,
@@ -997,7 +1029,7 @@ __device__ __forceinline__ int ring_wrap(int cell, int nz) {
 template <bool POT, int ORDER, bool COH>
 __device__ __forceinline__ void rk32_phase(const Batch& B, int64_t w, const Parts& pt, const double* W,
                                            const double* __restrict__ dirtab, const int* shift, const double* A,
-                                           const double* stage_src, int s, int dry, int* shift_next) {
+                                           const double* stage_src, int s, int dry) {
   constexpr int H = Sten<ORDER>::H, NW = Sten<ORDER>::NW;
   __shared__ double gsm[kWarps][2][kNC][kLanes];   // G of the last two units, per warp
   __shared__ double edge[kWarps][2][H][kNC];       // the H cells left / right of the unit being finished
@@ -1117,8 +1149,7 @@ __device__ __forceinline__ void rk32_phase(const Batch& B, int64_t w, const Part
           bdt = (s == 1 || s == 4) ? dtb / 6.0 : dtb / 3.0;   // weight of K in acc
           cdt = (s == 3) ? dtb : 0.5 * dtb;                   // offset of the next stage
         }
-        rk_particle<POT, COH>(g, pt, src_b, P, p, s, dry, bdt, cdt, dtb, dirtab + 3 * MT + pgd, Hm, r, shift_next,
-                              pgd, MT);
+        rk_particle<POT, COH>(g, pt, src_b, P, p, s, dry, bdt, cdt, dtb, dirtab + 3 * MT + pgd, Hm, r);
       }
       __syncwarp();
     }
@@ -1156,7 +1187,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 k_rk_stage32(Batch B, Parts pt, const double* __restrict__ W, const double* __restrict__ dirtab,
              const int* __restrict__ shift, const double* __restrict__ A, const double* stage_src, int s, int dry) {
   griddep_wait();
-  rk32_phase<POT, ORDER, false>(B, logical_warp(), pt, W, dirtab, shift, A, stage_src, s, dry, nullptr);
+  rk32_phase<POT, ORDER, false>(B, logical_warp(), pt, W, dirtab, shift, A, stage_src, s, dry);
 }
 
 // ------------------------------------------- RK stage with the next deposit
@@ -1431,7 +1462,7 @@ k_rk_deposit(Batch B, Parts pt, double* __restrict__ W, const double* __restrict
         }
         double zn = 0.0;
         rk_particle<POT, false, true>(g, pt, src_b, P, p, s, dry, bdt, cdt, dtb, dirtab + 3 * MT + gd, Hm, r,
-                                      nullptr, gd, MT, bm, &zn, n1, n2);
+                                      bm, &zn, n1, n2);
         zs = s < 4 ? fma(stage_frac(s) * dtb, vz, pt.z[p]) : zn;
       }
       __syncwarp();   // (gsm is rewritten by the next unit)
@@ -1580,10 +1611,8 @@ __global__ void k_frame_sum(Batch B, const double* __restrict__ partial, double*
 // ------------------------------------------------------- fused step kernel
 //
 // All phases of nsteps RK4 steps in one cooperative launch (every block
-// resident): the lattice shifts of the first step, then per stage the deposit,
-// its combination and the RK stage, separated by grid barriers.  The first
-// particle of each ring writes the next step's shifts during stage 4 (into the
-// other of two shift tables), so later steps need no shift phase.  The
+// resident): per step the lattice shifts and ring weights, then per stage the
+// deposit, its combination and the RK stage, separated by grid barriers.  The
 // arithmetic and the order of every sum are those of the separate kernels with
 // the same grid: results are bitwise the same.
 //
@@ -1599,8 +1628,8 @@ enum : int { ERR_TIMEOUT = 16 };
 
 struct StepArgs {
   const double* dirtab;
-  int* shift;          // [4][MT] shift rows of the current step
-  int* shift2;         // [4][MT] rows of the next step
+  int* shift;          // [4][MT] shift rows of the step
+  double* wtab;        // [4 x kWSlots][MT] the rings' weights at those rows (nullptr: each particle's own)
   double* W;           // kept shape weights
   double* At;          // traceless grid potential
   double* partial;     // per-warp deposit partials
@@ -1654,9 +1683,10 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned long long l
 // and restores registers around every call, was 4-5% slower per step).
 template <int ORDER>
 __device__ __forceinline__ void fused_deposit(const Batch& B, int64_t w, int lane, const Parts& pt, const double* rnu,
-                                           const double* rnb, const StepArgs& a, const int* srow, double frac) {
-  deposit_phase<5, ORDER, true>(B, w, lane, pt.z, pt.N, pt.Nbar, rnu, rnb, a.dirtab, srow, frac, a.partial, a.W,
-                                a.err);
+                                           const double* rnb, const StepArgs& a, const int* srow,
+                                           const double* wrow, double frac) {
+  deposit_phase<5, ORDER, true>(B, w, lane, pt.z, pt.N, pt.Nbar, rnu, rnb, a.dirtab, srow, wrow, frac, a.partial,
+                                a.W, a.err);
 }
 
 __device__ __forceinline__ void fused_combine(const Batch& B, const StepArgs& a) {
@@ -1665,9 +1695,9 @@ __device__ __forceinline__ void fused_combine(const Batch& B, const StepArgs& a)
 
 template <bool POT, int ORDER, bool RK32>
 __device__ __forceinline__ void fused_rk(const Batch& B, int64_t w, int lane, const Parts& pt, const StepArgs& a,
-                                     const int* srow, int s, int* nxt) {
-  if constexpr (RK32) rk32_phase<POT, ORDER, true>(B, w, pt, a.W, a.dirtab, srow, a.At, pt.stage, s, a.dry, nxt);
-  else rk_phase<POT, ORDER, true>(B, w, lane, pt, a.W, a.dirtab, srow, a.At, pt.stage, s, a.dry, nxt);
+                                     const int* srow, int s) {
+  if constexpr (RK32) rk32_phase<POT, ORDER, true>(B, w, pt, a.W, a.dirtab, srow, a.At, pt.stage, s, a.dry);
+  else rk_phase<POT, ORDER, true>(B, w, lane, pt, a.W, a.dirtab, srow, a.At, pt.stage, s, a.dry);
 }
 
 template <bool POT, int ORDER, bool RK32>
@@ -1682,25 +1712,23 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(Batch B, Parts pt, StepArg
   Fracs fr;
 #pragma unroll
   for (int q = 0; q < 4; ++q) fr.v[q] = stage_frac(q);
-  for (int gd = blockIdx.x * blockDim.x + threadIdx.x; gd < MT; gd += gridDim.x * blockDim.x)
-    shifts_phase<true>(B, gd, pt.z, a.dirtab, fr, 4, a.shift);
-  if (grid_barrier(a.bar, a.limit_ns, a.err)) return;
-  int* sh = a.shift;
-  int* shn = a.shift2;
   const int64_t P = B.Ptot;
   for (int64_t n = 0; n < a.nsteps; ++n) {
+    for (int gd = blockIdx.x * blockDim.x + threadIdx.x; gd < MT; gd += gridDim.x * blockDim.x)
+      shifts_phase<true, ORDER>(B, gd, pt.z, a.dirtab, fr, 4, a.shift, a.wtab);
+    if (grid_barrier(a.bar, a.limit_ns, a.err)) return;
     for (int s = 1; s <= 4; ++s) {
-      const int* srow = sh + (s - 1) * MT;
+      const int* srow = a.shift + (s - 1) * MT;
+      const double* wrow = a.wtab != nullptr ? a.wtab + (s - 1) * kWSlots * MT : nullptr;
       const double* rnu = s == 1 ? pt.rho : pt.stage;
       const double* rnb = s == 1 ? pt.rhobar : pt.stage + 9 * P;
-      fused_deposit<ORDER>(B, w, lane, pt, rnu, rnb, a, srow, stage_frac(s - 1));
+      fused_deposit<ORDER>(B, w, lane, pt, rnu, rnb, a, srow, wrow, stage_frac(s - 1));
       if (grid_barrier(a.bar, a.limit_ns, a.err)) return;
       fused_combine(B, a);
       if (grid_barrier(a.bar, a.limit_ns, a.err)) return;
-      fused_rk<POT, ORDER, RK32>(B, w, lane, pt, a, srow, s, s == 4 ? shn : nullptr);
+      fused_rk<POT, ORDER, RK32>(B, w, lane, pt, a, srow, s);
       if (grid_barrier(a.bar, a.limit_ns, a.err)) return;
     }
-    int* t = sh; sh = shn; shn = t;
   }
 }
 

@@ -483,7 +483,7 @@ k3_rk_stage(Box3 b, Parts pt, double* __restrict__ x, double* __restrict__ y, co
     double r[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) r[k] = src_r[k * P + p];
-    rk_particle<POT, false>(*b.g, pt, src_b, P, p, s, dry, bdt, cdt, dt, dirtab + 5 * M + d, Hm, r, nullptr, 0, 0);
+    rk_particle<POT, false>(*b.g, pt, src_b, P, p, s, dry, bdt, cdt, dt, dirtab + 5 * M + d, Hm, r);
     if (s == 4) {   // x and y move as z does (rk_particle moved z; dry: into the RK scratch)
       const double xn = wrap_z(fma(dt, vx, x[p]), b.L[0]), yn = wrap_z(fma(dt, vy, y[p]), b.L[1]);
       if (dry) { pt.acc[p] = xn; pt.acc[P + p] = yn; }

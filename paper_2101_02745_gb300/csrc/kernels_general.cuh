@@ -443,7 +443,7 @@ k_grk_stage(Batch B, Parts pt, const double* __restrict__ At, int s, int dry) {
   double r[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) r[k] = src_r[k * P + p];
-  rk_particle<POT, false>(g, pt, src_b, P, p, s, dry, bdt, cdt, dt, &vz, Hm, r, nullptr, 0, 0);
+  rk_particle<POT, false>(g, pt, src_b, P, p, s, dry, bdt, cdt, dt, &vz, Hm, r);
 }
 
 // Interpolation only (Eq. 6 then Eq. 2) for particles anywhere: H[k * P + p].
