@@ -63,8 +63,8 @@ BYTES_DEPOSIT = 24 * 8
 # DRAM read + write per particle of one launch, from an ncu capture of the current
 # kernels (2048 cells x 1000 directions, 2.048M particles, stages 1-4 averaged):
 # scaled by the particles of the timed launch.
-TRAFFIC_RK = 685.2   # k_rk_stage32 (32 cells per warp, traceless potential, autotuned grid)
-TRAFFIC_DEPOSIT = 301.7   # k_deposit<5> (traceless potential)
+TRAFFIC_RK = 691.7   # k_rk_stage32 (32 cells per warp, traceless potential, autotuned grid)
+TRAFFIC_DEPOSIT = 304.0   # k_deposit<5> (traceless potential)
 
 
 # 3D boxes (quadratic shape: each particle reaches 3 x 3 neighbour rows), FP64
