@@ -212,3 +212,66 @@ def test_lattice_violation_and_unsupported_calls_3d(torch):
         box.set_step_form(1)
     with pytest.raises(E.EmuError):
         E.emu3_create(E.make_config3(0, 1, 1, 1, 1.0, 1.0, 1.0, wl.kappa, wl.c_light))
+
+
+def test_box3d_full_size_sampled(torch):
+    """The 3D benchmark box at full size (64^3 cells x 16 directions, 4.19M
+    particles) in the launch configuration the benchmark times: the full
+    deposit against the oracle, then each of the four RK stages on 2000
+    sampled particles against the oracle's right-hand side (its deposit of the
+    whole stage state, per-particle H and commutators) at the stage states of
+    the classic tableau built from its own derivatives; then two full steps
+    checked through the exact invariants."""
+    wl = W.random_box3(64, 64, 64, 16, seed=0)
+    box = _box(wl)
+    cfg, parts = _oracle(wl)
+    grid = O.deposit3(cfg, parts)
+    A = box.deposit(0, 0.0).cpu().numpy()
+    assert _potential_err(A, grid, wl.kappa) < 1e-12
+    dt = O.timestep3(cfg, grid)
+    del grid, A
+    assert abs(box.timestep() - dt) <= 1e-13 * dt
+    box.autotune(trial_steps=1)   # dry steps: the state is untouched
+    P = len(parts)
+    sample = np.sort(np.random.default_rng(1).choice(P, 2000, replace=False))
+    cstage = (0.0, 0.5, 0.5, 1.0)
+    bweight = (1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0)
+    L = np.array([wl.Lx, wl.Ly, wl.Lz])
+    acc_r, acc_b = parts["rho"][sample].copy(), parts["rhobar"][sample].copy()
+    ystage = parts.copy()
+    for s in range(1, 5):
+        dr, db, _ = O.rhs3(cfg, ystage)
+        box.rk_stage(s, dt)
+        acc_r = acc_r + bweight[s - 1] * dt * dr[sample]
+        acc_b = acc_b + bweight[s - 1] * dt * db[sample]
+        if s < 4:
+            c = cstage[s]
+            ystage["rho"] = parts["rho"] + c * dt * dr
+            ystage["rhobar"] = parts["rhobar"] + c * dt * db
+            xs = parts["x"] + c * dt * wl.c_light * parts["omega"]
+            xs = xs - L * np.floor(xs / L)
+            ystage["x"] = np.where(xs >= L, xs - L, xs)
+            stage = box.t["stage"][:, sample].cpu().numpy()
+            accv = box.t["acc"][:, sample].cpu().numpy()
+            assert family_err(stage[:9], pack(ystage["rho"][sample])) < 1e-13, s
+            assert family_err(stage[9:], pack(ystage["rhobar"][sample])) < 1e-13, s
+            assert family_err(accv[:9], pack(acc_r)) < 1e-13, s
+            assert family_err(accv[9:], pack(acc_b)) < 1e-13, s
+        del dr, db
+    h = box.get_host()
+    assert family_err(h["rho"][:, sample], pack(acc_r)) < 1e-13
+    assert family_err(h["rhobar"][:, sample], pack(acc_b)) < 1e-13
+    xn = parts["x"][sample] + dt * wl.c_light * parts["omega"][sample]
+    xn = xn - L * np.floor(xn / L)
+    for i, k in enumerate(("x", "y", "z")):
+        assert np.abs(h[k][sample] - xn[:, i]).max() <= 1e-13 * L[i], k
+    del parts, ystage, h
+    d0 = box.diagnostics()
+    box.step(2, dt)
+    d1 = box.diagnostics()
+    scale = np.abs(d0[36:45]).max() + np.abs(d0[45:54]).max()
+    assert np.abs(d1[54:63] - d0[54:63]).max() < 1e-12 * scale
+    h = box.get_host()
+    for k in ("rho", "rhobar"):
+        assert np.abs(h[k][0] + h[k][1] + h[k][2] - 1.0).max() < 1e-12
+    box.sync()
