@@ -622,7 +622,8 @@ def measure_anywhere(args, dist, device, world, steps=20):
         if general:
             h = box.get_host()
             z = h["z"] + rng.uniform(-0.45, 0.45, wl.P) * wl.dz
-            z = np.mod(z, wl.Lz)
+            z = z - wl.Lz * np.floor(z / wl.Lz)
+            z = np.where(z >= wl.Lz, z - wl.Lz, z)   # (rounding can land a tiny negative on Lz)
             om = rng.normal(size=(wl.P, 3))
             om /= np.linalg.norm(om, axis=1, keepdims=True)
             box.set_host(z=z, ox=om[:, 0].copy(), oy=om[:, 1].copy(), oz=om[:, 2].copy())

@@ -199,3 +199,33 @@ def test_anywhere_refuses_lattice_only_calls(torch):
         box.step(1, 1e-13)
         box.sync()
     assert ei.value.code == E.EMU_ELATTICE
+
+
+def test_anywhere_paper_shape_full_size(torch):
+    """The benchmark's scattered workload at full size: the paper's 1024 x 378
+    run shape (387,072 particles), every position moved by U(-0.45, 0.45)
+    cells and every direction replaced (the same draws as the benchmark):
+    deposit, moments and H at 1e-12, then each of 10 steps at 1e-10 against
+    the oracle."""
+    wl = W.paper_1d()
+    cfg, parts = _scatter(wl, seed=0)
+    box = _box(wl, parts)
+    assert box.general()
+    grid = O.deposit(cfg, parts)
+    A = box.deposit(0, 0.0).cpu().numpy()
+    Aref = oracle_potential(grid, wl.kappa)
+    s = wl.kappa * density_scales(grid)[2]
+    assert max(family_err(A[9 * f:9 * (f + 1)], Aref[9 * f:9 * (f + 1)], s) for f in range(4)) < 1e-12
+    assert max(_moment_errs(box, grid)) < 1e-12
+    H = box.interpolate_H(0.0).cpu().numpy()
+    assert family_err(H, pack(O.hamiltonian(cfg, grid, parts)), s) < 1e-12
+    dt = O.timestep(cfg, grid)
+    assert abs(box.timestep() - dt) <= 1e-13 * dt
+    for n in range(10):
+        box.step(1, dt)
+        O.rk4_step(cfg, parts, dt)
+        h = box.get_host()
+        errs = [family_err(h["rho"], pack(parts["rho"])), family_err(h["rhobar"], pack(parts["rhobar"]))]
+        assert max(errs) < 1e-10, (n, errs)
+        assert np.abs(h["z"] - parts["z"]).max() <= 1e-13 * wl.Lz
+    box.sync()
