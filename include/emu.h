@@ -263,7 +263,8 @@ int emu_batch_set_dt(emu_box* box, const double* dt);
  * which the legacy stream orders implicitly before and after its own work.
  * With per-kernel timing on, the kernels are launched directly.  Binding,
  * autotuning, emu_set_grid, emu_set_rk_form, emu_set_step_form,
- * emu_set_barrier_timeout and emu_set_oscillation drop the graph. */
+ * emu_set_deposit_form, emu_set_barrier_timeout and emu_set_oscillation drop
+ * the graph. */
 int emu_batch_step(emu_box* box, int64_t nsteps);
 
 /* emu_diagnostics of every box: out [nbox][63]. */
@@ -284,11 +285,16 @@ int emu_batch_diagnostics(emu_box* box, double* out, int on_host);
  *             RK form c % 2;
  *   c = 10..12  step form 2, grid {304, 152, 608}[c - 10] (its RK stage has
  *             32 cells per warp); -1 where form 2 does not run (3D boxes,
- *             particles anywhere, the cubic shape, dt c >= 1.9 dz).
+ *             particles anywhere, the cubic shape, dt c >= 1.9 dz);
+ *   c = 13..16  one launch per phase, grid 304, RK form c % 2, with the
+ *             cluster deposit of 8 (c = 13, 14) or 16 blocks (c = 15, 16;
+ *             emu_set_deposit_form 1, 2); -1 for 3D boxes, particles
+ *             anywhere and cluster sizes the device cannot run.
  * The deposit's summation order depends on the grid, so results are bitwise
  * reproducible for a fixed grid; step forms 0 and 1 and the RK forms give
- * bitwise the same results, form 2 the same to rounding.  Synchronises. */
-#define EMU_AUTOTUNE_CANDIDATES 13
+ * bitwise the same results, form 2 and the cluster deposit the same to
+ * rounding.  Candidates 0-12 keep the per-warp deposit.  Synchronises. */
+#define EMU_AUTOTUNE_CANDIDATES 17
 int emu_autotune(emu_box* box, int trial_steps, int32_t* choice_out, double* ms_out);
 
 /* Step form of emu_batch_step / emu_step: 0 = one launch per phase, 1 = one
@@ -331,6 +337,21 @@ int emu_get_layout(emu_box* box, int32_t* general);
  * every wait that has to wait give up at once (for tests of that path).
  * Errors: EMU_EINVAL (negative). */
 int emu_set_barrier_timeout(emu_box* box, int64_t ns);
+
+/* Deposit of the step's stages in step form 0 and of emu_rk_stage (Eq. 5;
+ * step forms 1 and 2 keep their own): 0 = every warp sums its rings of a tile
+ * and writes a partial sum, a second launch adds the partials of each cell
+ * (the default); 1, 2 = thread-block clusters of 8 or 16 blocks (64 or 128
+ * warps) take one tile at a time, split its rings, add their sums through
+ * shared and distributed shared memory and write the potential in the same
+ * launch.  The clusters save the second launch and its reads; their summation
+ * order depends only on the box and the cluster size, so results are bitwise
+ * reproducible and agree with form 0's to rounding.  They run the lattice
+ * path of 1D boxes on devices with thread-block clusters (16 blocks: where the
+ * device allows clusters beyond the portable size).  Errors: EMU_EINVAL (bad
+ * form, a 3D box, particles anywhere, a cluster size the device cannot run,
+ * step in progress). */
+int emu_set_deposit_form(emu_box* box, int32_t form);
 
 /* Form of the RK stage kernel: 1 = 32 cells per warp, 0 = the halo-lane form
  * (both give bitwise the same results), -1 = chosen by units per warp (the

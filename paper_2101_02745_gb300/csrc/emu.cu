@@ -9,13 +9,14 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
-#include <atomic>
 #include <mutex>
 #include <new>
 #include <type_traits>
@@ -210,6 +211,9 @@ struct emu_box {
   unsigned* bar = nullptr;
   int blocks = kPersistBlocks;  // grid of the step kernels (autotuned); its warps split the units
   int rk_form = -1;             // RK stage: 0 halo-lane, 1 32-cell, -1 by units per warp (autotuned)
+  int dep_form = 0;             // the form-0 step's deposit: 0 per-warp partials and their combination,
+                                // 1, 2 thread-block clusters of 8, 16 blocks writing the potential
+  int dep_clusters[2] = {-1, -1};   // clusters of 8, 16 blocks resident at once (-1: not asked yet)
   int step_form = 0;            // 0: one launch per phase, 1: one cooperative launch per step (k_step),
                                 // 2: RK stages that deposit the next stage (k_rk_deposit)
   unsigned long long limit_ns = 1000000000ull;   // bound of each grid-barrier wait of k_step
@@ -529,12 +533,105 @@ const double* weight_row(const emu_box* b, const int* shift_row) {
   return b->wtab + (off / MT) * kWSlots * MT;
 }
 
+// Launch of a cluster kernel (clusters of `cl` blocks along x) with
+// programmatic dependent launch and `smem` bytes of dynamic shared memory.
+template <typename... KArgs, typename... Args>
+cudaError_t cluster_pdl(cudaStream_t st, void (*kernel)(KArgs...), int clusters, int cl, int smem, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(clusters * cl));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+using DepClusterKernel = void (*)(Batch, const double*, const double*, const double*, const double*, const double*,
+                                  const double*, const int*, const double*, double, double*, double*, int*);
+
+int dep_cluster_size(int form) { return form == 2 ? 16 : 8; }
+
+// The cluster deposit's instance for the box's shape order, the weight table
+// and the cluster size of deposit form `form` (1: 8 blocks, 2: 16), with its
+// attributes set for the current device (64 KB of shared memory; 16-block
+// clusters are beyond the portable size).
+DepClusterKernel dep_cluster_kernel(const emu_box* b, int form, bool tab, cudaError_t* e) {
+  DepClusterKernel k = nullptr;
+  by_order(b->S.order, [&](auto O) {
+    constexpr int R = decltype(O)::value;
+    if (form == 2) k = tab ? k_deposit_cluster<R, true, 16> : k_deposit_cluster<R, false, 16>;
+    else k = tab ? k_deposit_cluster<R, true, 8> : k_deposit_cluster<R, false, 8>;
+    return 0;
+  });
+  *e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kDepClusterSmem);
+  if (*e == cudaSuccess && form == 2) *e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return k;
+}
+
+// Clusters of the cluster deposit of form 1 or 2 that fit on the device at
+// once (0: it cannot run here).  Asked once per box.
+int dep_cluster_capacity(emu_box* b, int form) {
+  int& cached = b->dep_clusters[form == 2 ? 1 : 0];
+  if (cached >= 0) return cached;
+  int n = 0;
+  cudaError_t e;
+  DepClusterKernel k = dep_cluster_kernel(b, form, false, &e);
+  if (e == cudaSuccess) {
+    const int cl = dep_cluster_size(form);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(64 * cl));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kDepClusterSmem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) n = 0;
+  }
+  (void)cudaGetLastError();   // a refusal above is an answer, not a pending error
+  cached = n;
+  return n;
+}
+
+// The step's deposit (mode 5) by clusters: one launch, the potential written
+// directly (no combination).  The clusters stay resident: as many as fit, at
+// most one per tile.
+int launch_deposit_cluster(emu_box* b, const double* rnu, const double* rnb, const int* shift_row, double frac,
+                           double* out, double* W) {
+  const int form = b->dep_form;
+  const int cap = dep_cluster_capacity(b, form);
+  if (cap <= 0) return fail(b, EMU_EINVAL, "the device cannot run the cluster deposit");
+  const Batch B = batch_view(b);
+  const int clusters = (int)std::min<int64_t>(B.NT, cap);
+  const double* wrow = weight_row(b, shift_row);
+  before_launch(b, CLS_DEPOSIT);
+  cudaError_t e;
+  DepClusterKernel k = dep_cluster_kernel(b, form, wrow != nullptr, &e);
+  if (e == cudaSuccess)
+    e = cluster_pdl(b->stream, k, clusters, dep_cluster_size(form), kDepClusterSmem, B, b->pt.z, b->pt.N,
+                    b->pt.Nbar, rnu, rnb, b->dirtab, shift_row, wrow, frac, out, W, b->err);
+  if (e != cudaSuccess) return cuda_check(b, e, "cluster deposit launch");
+  return after_launch(b, "cluster deposit kernel");
+}
+
 // Deposit (two launches) of the state (rnu, rnb) at positions z + frac dt_b v_z
 // with the shift row shift_row, into out ([36][NZ]; mode 5: [32][NZ]).  Modes as k_deposit; the
 // potential scale kappa/dV for modes 0 and 3, 1/dV for the moments.
 int launch_deposit(emu_box* b, int mode, const double* rnu, const double* rnb, const int* shift_row, double frac,
                    double* out, double* W = nullptr) {
   if (!W) W = b->W;   // where modes 0 and 5 keep the shape weights
+  if (mode == 5 && b->dep_form != 0) return launch_deposit_cluster(b, rnu, rnb, shift_row, frac, out, W);
   const Batch B = batch_view(b);
   before_launch(b, CLS_DEPOSIT);
   const dim3 grid = persist_grid(b);
@@ -1768,6 +1865,19 @@ int emu_set_rk_form(emu_box* b, int32_t form) {
   return EMU_OK;
 }
 
+int emu_set_deposit_form(emu_box* b, int32_t form) {
+  if (int rc = check_bound(b)) return rc;
+  if (form < 0 || form > 2) return fail(b, EMU_EINVAL, "form must be 0, 1 or 2");
+  if (form != 0 && b->is3d) return no_3d(b, "the cluster deposit");
+  if (form != 0 && b->general) return needs_lattice(b, "the cluster deposit");
+  if (b->next_stage != 1) return fail(b, EMU_EINVAL, "a step is in progress (stage %d next)", b->next_stage);
+  if (form != 0 && dep_cluster_capacity(b, form) <= 0)
+    return fail(b, EMU_EINVAL, "the device cannot run clusters of %d blocks for the deposit", dep_cluster_size(form));
+  b->dep_form = form;
+  invalidate_graph(b);
+  return EMU_OK;
+}
+
 int emu_autotune(emu_box* b, int trial_steps, int32_t* choice_out, double* ms_out) {
   if (int rc = check_bound(b)) return rc;
   if (trial_steps < 1) return fail(b, EMU_EINVAL, "trial_steps must be >= 1");
@@ -1779,12 +1889,16 @@ int emu_autotune(emu_box* b, int trial_steps, int32_t* choice_out, double* ms_ou
   const int grids[EMU_AUTOTUNE_CANDIDATES] = {kPersistBlocks, kPersistBlocks, kPersistBlocks / 2, kPersistBlocks / 2,
                                               kMaxBlocks, kMaxBlocks, kPersistBlocks, kPersistBlocks,
                                               kPersistBlocks / 2, kPersistBlocks / 2, kPersistBlocks,
-                                              kPersistBlocks / 2, kMaxBlocks};
+                                              kPersistBlocks / 2, kMaxBlocks, kPersistBlocks, kPersistBlocks,
+                                              kPersistBlocks, kPersistBlocks};
   auto apply = [&](int c) {
     b->blocks = grids[c];
-    b->rk_form = c < 10 ? c % 2 : -1;
-    b->step_form = c >= 10 ? 2 : c >= 6 ? 1 : 0;
+    b->rk_form = c < 10 || c >= 13 ? c % 2 : -1;
+    b->step_form = c >= 13 ? 0 : c >= 10 ? 2 : c >= 6 ? 1 : 0;
+    b->dep_form = c >= 15 ? 2 : c >= 13 ? 1 : 0;
   };
+  const bool dep_ok[2] = {!b->is3d && !b->general && dep_cluster_capacity(b, 1) > 0,
+                          !b->is3d && !b->general && dep_cluster_capacity(b, 2) > 0};
   const int maxb = fused_max_blocks(b);
   const bool rd_ok = rd_possible(b) && rd_step_sizes_ok(b);
   if (rd_ok)
@@ -1798,7 +1912,7 @@ int emu_autotune(emu_box* b, int trial_steps, int32_t* choice_out, double* ms_ou
   for (int c = 0; c < EMU_AUTOTUNE_CANDIDATES && rc == EMU_OK; ++c) {
     apply(c);
     if ((b->step_form == 1 && (b->is3d || b->general || b->blocks > maxb)) ||
-        (b->step_form == 2 && !rd_ok)) {   // not a candidate here
+        (b->step_form == 2 && !rd_ok) || (b->dep_form != 0 && !dep_ok[b->dep_form - 1])) {   // not a candidate
       if (ms_out) ms_out[c] = -1.0;
       continue;
     }

@@ -494,6 +494,114 @@ __device__ __forceinline__ void flush_tile(const double (&acc)[NA], int64_t gtil
   }
 }
 
+// The direction loop of the deposit for one tile: warp lane `lane` of a tile
+// of box b (lane l owns cell tile * T - H + l) adds the rings dfirst..dlast-1
+// of the tile, in order, to acc (MODES as deposit_phase).  Shared by the
+// per-warp deposit and the cluster deposit.
+template <int MODE, int ORDER, bool COH, int NA>
+__device__ __forceinline__ void deposit_tile_dirs(const Batch& B, int b, int tile, int dfirst, int dlast, int lane,
+                                                  const double* z, const double* __restrict__ N,
+                                                  const double* __restrict__ Nbar, const double* r_nu,
+                                                  const double* r_nb, const double* __restrict__ dirtab,
+                                                  const int* shift, const double* wrow, double frac, double* W,
+                                                  double (&acc)[NA], int& bad) {
+  const BoxGeo& g = B.box[b];
+  const int nz = g.nz;
+  const int64_t P = B.Ptot;
+  const int MT = B.MT;
+  constexpr int H = Sten<ORDER>::H, T = Sten<ORDER>::T;
+  const int craw = tile * T - H + lane;
+  const int j = wrapc(craw, nz);
+  const double hp = (double)j + 0.5;
+  const bool own = lane >= H && lane < H + T && craw < nz;
+  const double pos_dt = frac * B.dt[b];
+  const int64_t pbase = g.poff;
+  const int dbase = g.doff;
+  for (int d = dfirst; d < dlast; ++d) {
+    const int gd = dbase + d;
+    const double ox = __ldg(dirtab + gd), oy = __ldg(dirtab + MT + gd), oz = __ldg(dirtab + 2 * MT + gd);
+    const double vz = __ldg(dirtab + 3 * MT + gd);
+    const int64_t p = pbase + (int64_t)d * nz + wrapc(j - ldi<COH>(shift + gd), nz);
+    double wt[Sten<ORDER>::NW];
+    const double zs = fma(pos_dt, vz, ldd<COH>(z + p));
+    if (wrow != nullptr) {
+      bad |= off_site(zs, hp, __ldg(&g.inv_dz), __ldg(&g.nz_d));
+      if constexpr (ORDER == 0) {
+        wt[0] = 0.0; wt[1] = 1.0; wt[2] = 0.0;
+      } else {
+#pragma unroll
+        for (int q = 0; q < Sten<ORDER>::NW; ++q) wt[q] = ldp<COH>(wrow + q * B.MT + gd);
+      }
+    } else {
+      bad |= shape_weights<ORDER>(zs, hp, __ldg(&g.inv_dz), __ldg(&g.nz_d), wt);
+    }
+    if ((MODE == 0 || MODE == 5) && W != nullptr && own) {   // the RK stage of these positions reads them back
+#pragma unroll
+      for (int q = 0; q < Sten<ORDER>::NWS; ++q) W[q * P + p] = wt[q];
+    }
+    Spread<ORDER> spread;
+    spread.init(wt);
+    if constexpr (MODE == 5) {
+      const double n1 = __ldg(N + p), n2 = __ldg(Nbar + p);
+      double bprev = 0.0;   // B of the previous diagonal entry
+#pragma unroll
+      for (int c = 0; c < kNC; ++c) {
+        double bv;
+        if (c < 2) {
+          if (c == 0) bprev = fma(-n2, ldd<COH>(r_nb + p), n1 * ldd<COH>(r_nu + p));
+          const double bn =
+              fma(-n2, ldd<COH>(r_nb + (c + 1) * P + p), n1 * ldd<COH>(r_nu + (c + 1) * P + p));
+          bv = bprev - bn;
+          bprev = bn;
+        } else {
+          const int k = c + 1;
+          const double x = ldd<COH>(r_nu + k * P + p), y = ldd<COH>(r_nb + k * P + p);
+          bv = (k == 4 || k == 6 || k == 8) ? fma(n2, y, n1 * x) : fma(-n2, y, n1 * x);
+        }
+        const double cc = spread.apply(bv);
+        acc[c] += cc;
+        acc[kNC + c] = fma(ox, cc, acc[kNC + c]);
+        acc[2 * kNC + c] = fma(oy, cc, acc[2 * kNC + c]);
+        acc[3 * kNC + c] = fma(oz, cc, acc[3 * kNC + c]);
+      }
+    } else if constexpr (MODE == 4) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const double c1 = spread.apply(__ldg(N + p) * ldd<COH>(r_nu + k * P + p));
+        const double c2 = spread.apply(__ldg(Nbar + p) * ldd<COH>(r_nb + k * P + p));
+        acc[k] += c1;
+        acc[9 + k] = fma(ox, c1, acc[9 + k]);
+        acc[18 + k] += c2;
+        acc[27 + k] = fma(ox, c2, acc[27 + k]);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        // (the weights are read inside the loop: fewer live registers across it)
+        const double n1 = (MODE == 0 || MODE == 1) ? __ldg(N + p) : 0.0;
+        const double n2 = (MODE == 0 || MODE == 2) ? __ldg(Nbar + p) : 0.0;
+        double bv;
+        if (MODE == 0) {
+          const double x = ldd<COH>(r_nu + k * P + p), y = ldd<COH>(r_nb + k * P + p);
+          // conj(rhobar) flips the sign of the imaginary components 4, 6, 8
+          bv = (k == 4 || k == 6 || k == 8) ? fma(n2, y, n1 * x) : fma(-n2, y, n1 * x);
+        } else if (MODE == 1) {
+          bv = n1 * ldd<COH>(r_nu + k * P + p);
+        } else if (MODE == 2) {
+          bv = n2 * ldd<COH>(r_nb + k * P + p);
+        } else {
+          bv = ldd<COH>(r_nu + k * P + p);
+        }
+        const double c = spread.apply(bv);
+        acc[k] += c;
+        acc[9 + k] = fma(ox, c, acc[9 + k]);
+        acc[18 + k] = fma(oy, c, acc[18 + k]);
+        acc[27 + k] = fma(oz, c, acc[27 + k]);
+      }
+    }
+  }
+}
+
 // Deposit (Eq. 5), first phase.  MODE 0: B = N rho - Nbar rhobar^* (the
 // combination that enters H, Eq. 2); MODE 1: B = N rho; MODE 2: B = Nbar rhobar;
 // MODE 3: B = r_nu (packed matrices given per particle: the adjoint's Gamma);
@@ -519,24 +627,14 @@ __device__ __forceinline__ void deposit_phase(const Batch& B, int64_t w, int lan
                                               double* W, int* err) {
   const int64_t u0 = unit_begin(w, B), u1 = unit_begin(w + 1, B);
   if (u0 >= u1) return;
-  const int64_t P = B.Ptot;
-  const int MT = B.MT;
   int bad = 0;
   int b = box_of_unit(B, u0);
   for (int64_t u = u0; u < u1;) {        // one segment per (box, tile) the warp touches
     while (u >= B.box[b].uoff + (int64_t)B.box[b].ntiles * B.box[b].M) ++b;
     const BoxGeo& g = B.box[b];
-    const int nz = g.nz, M = g.M;
+    const int M = g.M;
     const int tile = (int)((u - g.uoff) / M);
     const int64_t uend = min(u1, g.uoff + (int64_t)(tile + 1) * M);
-    constexpr int H = Sten<ORDER>::H, T = Sten<ORDER>::T;
-    const int craw = tile * T - H + lane;
-    const int j = wrapc(craw, nz);
-    const double hp = (double)j + 0.5;
-    const bool own = lane >= H && lane < H + T && craw < nz;
-    const double pos_dt = frac * B.dt[b];
-    const int64_t pbase = g.poff;
-    const int dbase = g.doff;
     const int64_t ubase = g.uoff + (int64_t)tile * M;
     const int dfirst = (int)(u - ubase), dlast = (int)(uend - ubase);
     u = uend;
@@ -544,90 +642,10 @@ __device__ __forceinline__ void deposit_phase(const Batch& B, int64_t w, int lan
     double acc[NA];
 #pragma unroll
     for (int c = 0; c < NA; ++c) acc[c] = 0.0;
-    for (int d = dfirst; d < dlast; ++d) {
-      const int gd = dbase + d;
-      const double ox = __ldg(dirtab + gd), oy = __ldg(dirtab + MT + gd), oz = __ldg(dirtab + 2 * MT + gd);
-      const double vz = __ldg(dirtab + 3 * MT + gd);
-      const int64_t p = pbase + (int64_t)d * nz + wrapc(j - ldi<COH>(shift + gd), nz);
-      double wt[Sten<ORDER>::NW];
-      const double zs = fma(pos_dt, vz, ldd<COH>(z + p));
-      if (wrow != nullptr) {
-        bad |= off_site(zs, hp, __ldg(&g.inv_dz), __ldg(&g.nz_d));
-        if constexpr (ORDER == 0) {
-          wt[0] = 0.0; wt[1] = 1.0; wt[2] = 0.0;
-        } else {
-#pragma unroll
-          for (int q = 0; q < Sten<ORDER>::NW; ++q) wt[q] = ldp<COH>(wrow + q * B.MT + gd);
-        }
-      } else {
-        bad |= shape_weights<ORDER>(zs, hp, __ldg(&g.inv_dz), __ldg(&g.nz_d), wt);
-      }
-      if ((MODE == 0 || MODE == 5) && W != nullptr && own) {   // the RK stage of these positions reads them back
-#pragma unroll
-        for (int q = 0; q < Sten<ORDER>::NWS; ++q) W[q * P + p] = wt[q];
-      }
-      Spread<ORDER> spread;
-      spread.init(wt);
-      if constexpr (MODE == 5) {
-        const double n1 = __ldg(N + p), n2 = __ldg(Nbar + p);
-        double bprev = 0.0;   // B of the previous diagonal entry
-#pragma unroll
-        for (int c = 0; c < kNC; ++c) {
-          double bv;
-          if (c < 2) {
-            if (c == 0) bprev = fma(-n2, ldd<COH>(r_nb + p), n1 * ldd<COH>(r_nu + p));
-            const double bn =
-                fma(-n2, ldd<COH>(r_nb + (c + 1) * P + p), n1 * ldd<COH>(r_nu + (c + 1) * P + p));
-            bv = bprev - bn;
-            bprev = bn;
-          } else {
-            const int k = c + 1;
-            const double x = ldd<COH>(r_nu + k * P + p), y = ldd<COH>(r_nb + k * P + p);
-            bv = (k == 4 || k == 6 || k == 8) ? fma(n2, y, n1 * x) : fma(-n2, y, n1 * x);
-          }
-          const double cc = spread.apply(bv);
-          acc[c] += cc;
-          acc[kNC + c] = fma(ox, cc, acc[kNC + c]);
-          acc[2 * kNC + c] = fma(oy, cc, acc[2 * kNC + c]);
-          acc[3 * kNC + c] = fma(oz, cc, acc[3 * kNC + c]);
-        }
-      } else if constexpr (MODE == 4) {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-          const double c1 = spread.apply(__ldg(N + p) * ldd<COH>(r_nu + k * P + p));
-          const double c2 = spread.apply(__ldg(Nbar + p) * ldd<COH>(r_nb + k * P + p));
-          acc[k] += c1;
-          acc[9 + k] = fma(ox, c1, acc[9 + k]);
-          acc[18 + k] += c2;
-          acc[27 + k] = fma(ox, c2, acc[27 + k]);
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-          // (the weights are read inside the loop: fewer live registers across it)
-          const double n1 = (MODE == 0 || MODE == 1) ? __ldg(N + p) : 0.0;
-          const double n2 = (MODE == 0 || MODE == 2) ? __ldg(Nbar + p) : 0.0;
-          double bv;
-          if (MODE == 0) {
-            const double x = ldd<COH>(r_nu + k * P + p), y = ldd<COH>(r_nb + k * P + p);
-            // conj(rhobar) flips the sign of the imaginary components 4, 6, 8
-            bv = (k == 4 || k == 6 || k == 8) ? fma(n2, y, n1 * x) : fma(-n2, y, n1 * x);
-          } else if (MODE == 1) {
-            bv = n1 * ldd<COH>(r_nu + k * P + p);
-          } else if (MODE == 2) {
-            bv = n2 * ldd<COH>(r_nb + k * P + p);
-          } else {
-            bv = ldd<COH>(r_nu + k * P + p);
-          }
-          const double c = spread.apply(bv);
-          acc[k] += c;
-          acc[9 + k] = fma(ox, c, acc[9 + k]);
-          acc[18 + k] = fma(oy, c, acc[18 + k]);
-          acc[27 + k] = fma(oz, c, acc[27 + k]);
-        }
-      }
-    }
-    flush_tile<ORDER>(acc, g.toff + tile, craw, nz, w, lane, partial);
+    deposit_tile_dirs<MODE, ORDER, COH>(B, b, tile, dfirst, dlast, lane, z, N, Nbar, r_nu, r_nb, dirtab, shift, wrow,
+                                        frac, W, acc, bad);
+    constexpr int H = Sten<ORDER>::H, T = Sten<ORDER>::T;
+    flush_tile<ORDER>(acc, g.toff + tile, tile * T - H + lane, g.nz, w, lane, partial);
   }
   if (bad) atomicOr(err, ERR_LATTICE);
 }
@@ -643,6 +661,115 @@ k_deposit(Batch B, const double* __restrict__ z, const double* __restrict__ N, c
   griddep_wait();
   deposit_phase<MODE, ORDER, false>(B, logical_warp(), threadIdx.x & 31, z, N, Nbar, r_nu, r_nb, dirtab, shift,
                                     TAB ? wrow : nullptr, frac, partial, W, err);
+}
+
+// ------------------------------------------------------- cluster deposit
+//
+// The step's deposit (MODE 5) by thread-block clusters of CL blocks (8 or 16),
+// with no separate combination: cluster c takes the tiles c, c + clusters,
+// ... (all boxes' tiles in order).  For each tile the cluster's W =
+// CL x kWarps warps split its rings (warp i: rings [i M / W,
+// (i + 1) M / W), summed in order in registers as in deposit_phase); the
+// warps of each block are added in warp order through shared memory, then the
+// blocks in rank order through distributed shared memory, and the potential
+// of the tile's cells is written.  The summation order depends only on the
+// box and the cluster size, not on the grid: results are bitwise reproducible.
+// All blocks of a cluster walk the same tiles, so every block reaches every
+// cluster barrier (hardware barriers, as __syncthreads: no spin on memory).
+constexpr int kDepClusterSmem = kWarps * kNT * kLanes * (int)sizeof(double);   // 64 KB
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_index() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_count() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+// Barrier of all threads of the cluster; shared-memory writes before it are
+// visible to every block of the cluster after it.  (The non-.aligned form:
+// correct whether or not the threads of a warp arrive together.)
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+// The double at this block's shared address a, read from block `rank` of the cluster.
+__device__ __forceinline__ double ld_cluster(const double* a, unsigned rank) {
+  const unsigned local = (unsigned)__cvta_generic_to_shared(a);
+  unsigned remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(remote) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int box_of_tile(const Batch& B, int64_t t) {
+  int lo = 0, hi = B.nbox - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (B.box[mid].toff <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// out: the potential ([kNT][NZ], scale kappa / dV of each box); W as k_deposit.
+template <int ORDER, bool TAB, int CL>
+__global__ void __launch_bounds__(kThreads, 2)
+k_deposit_cluster(Batch B, const double* __restrict__ z, const double* __restrict__ N,
+                  const double* __restrict__ Nbar, const double* __restrict__ r_nu, const double* __restrict__ r_nb,
+                  const double* __restrict__ dirtab, const int* __restrict__ shift, const double* __restrict__ wrow,
+                  double frac, double* __restrict__ out, double* __restrict__ W, int* __restrict__ err) {
+  griddep_wait();
+  extern __shared__ double red[];   // [kWarps][kNT][kLanes]: each warp's sums of the tile
+  constexpr int H = Sten<ORDER>::H, T = Sten<ORDER>::T;
+  constexpr int NE = kNT * kLanes, per = NE / CL, nwc = CL * kWarps;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const unsigned rank = cluster_rank();
+  const int gw = (int)rank * kWarps + wib;
+  int bad = 0, nonfinite = 0;
+  for (int64_t gt = cluster_index(); gt < B.NT; gt += cluster_count()) {
+    const int b = box_of_tile(B, gt);
+    const BoxGeo& g = B.box[b];
+    const int tile = (int)(gt - g.toff);
+    const int d0 = (int)((int64_t)gw * g.M / nwc), d1 = (int)((int64_t)(gw + 1) * g.M / nwc);
+    double acc[kNT];
+#pragma unroll
+    for (int c = 0; c < kNT; ++c) acc[c] = 0.0;
+    if (d0 < d1)
+      deposit_tile_dirs<5, ORDER, false>(B, b, tile, d0, d1, lane, z, N, Nbar, r_nu, r_nb, dirtab, shift,
+                                         TAB ? wrow : nullptr, frac, W, acc, bad);
+#pragma unroll
+    for (int c = 0; c < kNT; ++c) red[(wib * kNT + c) * kLanes + lane] = acc[c];
+    __syncthreads();
+    for (int e = threadIdx.x; e < NE; e += kThreads) {   // the block's warps, in warp order
+      double v = red[e];
+#pragma unroll
+      for (int i = 1; i < kWarps; ++i) v += red[i * NE + e];
+      red[e] = v;
+    }
+    cluster_sync();
+    if (threadIdx.x < per) {   // the cluster's blocks, in rank order; this block's share of the outputs
+      const int e = (int)rank * per + threadIdx.x;
+      double v = ld_cluster(red + e, 0);
+#pragma unroll
+      for (unsigned q = 1; q < CL; ++q) v += ld_cluster(red + e, q);
+      const int c = e / kLanes, l = e - c * kLanes, craw = tile * T - H + l;
+      if (l >= H && l < H + T && craw < g.nz) {
+        v *= g.kappa_dV;
+        nonfinite |= !isfinite(v);
+        out[(int64_t)c * B.NZ + g.coff + craw] = v;
+      }
+    }
+    cluster_sync();   // the slots are free for the next tile, and no block leaves while read
+  }
+  if (bad) atomicOr(err, ERR_LATTICE);
+  if (nonfinite) atomicOr(err, ERR_NONFINITE);
 }
 
 // Deposit, second phase: fixed-order sum of the per-warp partials.

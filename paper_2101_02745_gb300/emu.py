@@ -24,7 +24,7 @@ EMU_ENUMERIC = -3
 EMU_ETIMEOUT = -4
 EMU_ELATTICE = -5
 N_DIAG = 63
-AUTOTUNE_CANDIDATES = 13   # EMU_AUTOTUNE_CANDIDATES
+AUTOTUNE_CANDIDATES = 17   # EMU_AUTOTUNE_CANDIDATES
 
 
 class EmuError(RuntimeError):
@@ -116,6 +116,7 @@ def load(build_if_missing: bool = False):
         "emu_autotune": (i32, [vp, i32, vp, vp]),
         "emu_set_grid": (i32, [vp, ctypes.c_int32]),
         "emu_set_rk_form": (i32, [vp, ctypes.c_int32]),
+        "emu_set_deposit_form": (i32, [vp, ctypes.c_int32]),
         "emu_set_step_form": (i32, [vp, ctypes.c_int32]),
         "emu_set_barrier_timeout": (i32, [vp, i64]),
         "emu_set_layout": (i32, [vp, ctypes.c_int32]),
@@ -343,6 +344,10 @@ def emu_set_step_form(box, form: int):
     _check(box, load().emu_set_step_form(box, int(form)))
 
 
+def emu_set_deposit_form(box, form: int):
+    _check(box, load().emu_set_deposit_form(box, int(form)))
+
+
 def emu_set_barrier_timeout(box, ns: int):
     _check(box, load().emu_set_barrier_timeout(box, int(ns)))
 
@@ -359,17 +364,19 @@ def emu_get_layout(box) -> int:
     return int(g.value)
 
 
-# (step form, grid blocks, RK form) of each autotuner candidate, as emu.h lists them
-AUTOTUNE_GRID_FORMS = tuple((0, g, f) for g in (304, 152, 608) for f in (0, 1)) + \
-    tuple((1, g, f) for g in (304, 152) for f in (0, 1)) + tuple((2, g, -1) for g in (304, 152, 608))
+# (step form, grid blocks, RK form, deposit form) of each autotuner candidate, as emu.h lists them
+AUTOTUNE_GRID_FORMS = tuple((0, g, f, 0) for g in (304, 152, 608) for f in (0, 1)) + \
+    tuple((1, g, f, 0) for g in (304, 152) for f in (0, 1)) + tuple((2, g, -1, 0) for g in (304, 152, 608)) + \
+    tuple((0, 304, f, c) for c in (1, 2) for f in (0, 1))
 
 
 def apply_choice(box, choice: int):
     """Set a box to autotuner candidate `choice` (e.g. the choice made on a twin box)."""
-    form, grid, rk = AUTOTUNE_GRID_FORMS[choice]
+    form, grid, rk, dep = AUTOTUNE_GRID_FORMS[choice]
     emu_set_grid(box, grid)
     emu_set_rk_form(box, rk)
     emu_set_step_form(box, form)
+    emu_set_deposit_form(box, dep)
 
 
 def make_oscillation(d: dict) -> emu_oscillation:
@@ -620,6 +627,12 @@ class Box:
         """0: one launch per phase, 1: one cooperative launch per step, 2: RK
         stages that deposit the next stage (shape orders 0-2)."""
         emu_set_step_form(self.box, form)
+
+    def set_deposit_form(self, form: int):
+        """0: per-warp partial sums and their combination, 1, 2: thread-block
+        clusters of 8, 16 blocks that write the potential (step form 0 and the
+        stage calls)."""
+        emu_set_deposit_form(self.box, form)
 
     def set_barrier_timeout(self, ns: int):
         emu_set_barrier_timeout(self.box, ns)
