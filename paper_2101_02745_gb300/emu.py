@@ -367,7 +367,7 @@ def emu_get_layout(box) -> int:
 # (step form, grid blocks, RK form, deposit form) of each autotuner candidate, as emu.h lists them
 AUTOTUNE_GRID_FORMS = tuple((0, g, f, 0) for g in (304, 152, 608) for f in (0, 1)) + \
     tuple((1, g, f, 0) for g in (304, 152) for f in (0, 1)) + tuple((2, g, -1, 0) for g in (304, 152, 608)) + \
-    tuple((0, 304, f, c) for c in (1, 2) for f in (0, 1))
+    tuple((0, 304, c % 2, 1 if c < 15 else 2) for c in range(13, 17))
 
 
 def apply_choice(box, choice: int):

@@ -101,3 +101,22 @@ def test_oracle_builds_and_is_separate():
     import subprocess
     out = subprocess.run(["nm", "-D", "--defined-only", str(O._LIB)], capture_output=True, text=True).stdout
     assert "or_rk4_step" in out and "emu_step" not in out
+
+
+def test_autotune_candidate_table_matches_the_header():
+    """The binding's table of autotuner candidates (used to put a twin box in
+    the configuration the autotuner chose) against the list in include/emu.h:
+    its count and, per candidate, the step form, grid, RK form and deposit form."""
+    text = (ROOT / "include" / "emu.h").read_text()
+    assert int(re.search(r"#define EMU_AUTOTUNE_CANDIDATES (\d+)", text).group(1)) == E.AUTOTUNE_CANDIDATES
+    expect = []
+    for c in range(E.AUTOTUNE_CANDIDATES):
+        if c < 6:
+            expect.append((0, (304, 152, 608)[c // 2], c % 2, 0))
+        elif c < 10:
+            expect.append((1, (304, 152)[(c - 6) // 2], c % 2, 0))
+        elif c < 13:
+            expect.append((2, (304, 152, 608)[c - 10], -1, 0))
+        else:
+            expect.append((0, 304, c % 2, 1 if c < 15 else 2))
+    assert list(E.AUTOTUNE_GRID_FORMS) == expect
