@@ -615,14 +615,14 @@ int launch_deposit_cluster(emu_box* b, const double* rnu, const double* rnb, con
   const Batch B = batch_view(b);
   const int clusters = (int)std::min<int64_t>(B.NT, cap);
   const double* wrow = weight_row(b, shift_row);
-  before_launch(b, CLS_DEPOSIT);
   cudaError_t e;
   DepClusterKernel k = dep_cluster_kernel(b, form, wrow != nullptr, &e);
-  if (e == cudaSuccess)
-    e = cluster_pdl(b->stream, k, clusters, dep_cluster_size(form), kDepClusterSmem, B, b->pt.z, b->pt.N,
-                    b->pt.Nbar, rnu, rnb, b->dirtab, shift_row, wrow, frac, out, W, b->err);
-  if (e != cudaSuccess) return cuda_check(b, e, "cluster deposit launch");
-  return after_launch(b, "cluster deposit kernel");
+  if (e != cudaSuccess) return cuda_check(b, e, "cluster deposit attributes");
+  before_launch(b, CLS_DEPOSIT);
+  e = cluster_pdl(b->stream, k, clusters, dep_cluster_size(form), kDepClusterSmem, B, b->pt.z, b->pt.N, b->pt.Nbar,
+                  rnu, rnb, b->dirtab, shift_row, wrow, frac, out, W, b->err);
+  const int rc = after_launch(b, "cluster deposit kernel");   // (closes the timing record either way)
+  return e != cudaSuccess ? cuda_check(b, e, "cluster deposit launch") : rc;
 }
 
 // Deposit (two launches) of the state (rnu, rnb) at positions z + frac dt_b v_z
