@@ -203,6 +203,27 @@ def test_invariants_on_gpu(torch):
     box.sync()
 
 
+@pytest.mark.parametrize("dep_form", [0, 1])
+def test_unperturbed_state_stays_exactly_diagonal(torch, dep_form):
+    """Degenerate case: no perturbation (alpha = 0).  Every rho starts as
+    diag(1, 0, 0) exactly (Eq. 9 with eps_x = 0), every deposit of the
+    off-diagonal components is a sum of exact zeros, so H stays diagonal,
+    commutes with rho (Eq. 4) and nothing evolves: after 20 steps every
+    density matrix is bitwise its initial value, while the positions move."""
+    wl = W.random_box(67, 21, seed=11)
+    wl.alpha = 0.0
+    box = _box(wl)
+    box.set_deposit_form(dep_form)
+    h0 = box.get_host()
+    assert np.all(h0["rho"][0] == 1.0) and not h0["rho"][1:].any() and not h0["rhobar"][1:].any()
+    box.step(20, box.timestep())
+    h = box.get_host()
+    box.sync()
+    for k in ("rho", "rhobar"):
+        assert np.array_equal(h[k], h0[k]), k
+    assert not np.array_equal(h["z"], h0["z"])
+
+
 @pytest.mark.parametrize("order", [2, 0, 1, 3])
 def test_diagnostics_match_oracle(torch, order):
     """The one-pass deposit of n, f_x, nbar, fbar_x behind the diagnostics, at
